@@ -1,0 +1,505 @@
+/*
+ * CPU oracle for the extruded-mesh numbering and par_loop.
+ *
+ * TEST INFRASTRUCTURE ONLY: a plain, slow, serial FP64 restatement of the
+ * paper's algorithms, used to check the CUDA library.  Nothing in the CUDA
+ * path includes, links or calls this file.  Compiled with -O2
+ * -ffp-contract=off (no fused multiply-add, no fast-math).
+ *
+ * Sections followed:
+ *   - entities and adjacency of the base mesh: Sec. 2.2 (all adjacencies are
+ *     derivable from cell-vertex; edges are derived here);
+ *   - extruded entity sets V_{d1,d2}, 0 <= l <= lambda - d2: Sec. 3.1.3;
+ *   - Algorithm 1 (vertical-innermost numbering): Sec. 3.2;
+ *   - explicit lists reduced to the bottom layer, Algorithm 2 (offsets) and
+ *     Algorithm 3 (iteration of a stencil over the extruded mesh): Sec. 3.3;
+ *   - the residual I = int f v dx with the coordinate field as a vector at
+ *     every vertex: Sec. 4.1.1; the element pairs of Sec. 4.1.2.
+ *
+ * Readings where the paper is silent (stated once here, used throughout):
+ *   - base entities are visited dimension-major (vertices, edges, cells),
+ *     index ascending, in Algorithm 1;
+ *   - the stencil of a cell lists its local base entities in the order
+ *     vertices, edges, cell interior; per entity: the delta(d,0) DoFs of the
+ *     bottom horizontal entity, the delta(d,0) DoFs of the top one, then the
+ *     delta(d,1) DoFs of the vertical entity;
+ *   - local edge e_k joins local vertices k and (k+1) mod nvc;
+ *   - quadrature: prisms use the 3-point degree-2 triangle rule times the
+ *     2-point Gauss rule; hexahedra use the n-point Gauss rule per direction
+ *     (n = 4 unless changed), which integrates every integrand used here
+ *     exactly on straight-sided columns.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Base-mesh edges (Sec. 2.2: derivable from cell-vertex adjacency).        */
+/* An open-addressing table keyed by the unordered vertex pair; a pair seen */
+/* for the first time gets the next edge number.                           */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_derive_edges(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                            int64_t nverts, int32_t *cell_edges) {
+  int64_t cap = 16;
+  while (cap < 4 * ncells * nvc + 16) cap *= 2;
+  int64_t *key_lo = (int64_t *)malloc(sizeof(int64_t) * cap);
+  int64_t *key_hi = (int64_t *)malloc(sizeof(int64_t) * cap);
+  int64_t *val = (int64_t *)malloc(sizeof(int64_t) * cap);
+  if (!key_lo || !key_hi || !val) {
+    free(key_lo); free(key_hi); free(val);
+    return -1;
+  }
+  for (int64_t s = 0; s < cap; ++s) key_lo[s] = -1;
+  int64_t nedges = 0;
+  for (int64_t c = 0; c < ncells; ++c) {
+    for (int32_t k = 0; k < nvc; ++k) {
+      int64_t a = cell_verts[c * nvc + k];
+      int64_t b = cell_verts[c * nvc + (k + 1) % nvc];
+      if (a < 0 || b < 0 || a >= nverts || b >= nverts) {
+        free(key_lo); free(key_hi); free(val);
+        return -1;
+      }
+      int64_t lo = a < b ? a : b, hi = a < b ? b : a;
+      uint64_t h = (uint64_t)lo * 1000003ULL + (uint64_t)hi * 998244353ULL;
+      int64_t s = (int64_t)(h & (uint64_t)(cap - 1));
+      while (key_lo[s] != -1 && !(key_lo[s] == lo && key_hi[s] == hi)) s = (s + 1) & (cap - 1);
+      if (key_lo[s] == -1) {
+        key_lo[s] = lo;
+        key_hi[s] = hi;
+        val[s] = nedges++;
+      }
+      cell_edges[c * nvc + k] = (int32_t)val[s];
+    }
+  }
+  free(key_lo); free(key_hi); free(val);
+  return nedges;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: number every extruded entity, vertical innermost.           */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_alg1(const int64_t N[3], int32_t layers, const int32_t delta[6],
+                    int64_t *const first[6]) {
+  int64_t c = 0;
+  for (int d1 = 0; d1 <= 2; ++d1) {           /* base entities, dimension-major */
+    for (int64_t i = 0; i < N[d1]; ++i) {     /* ... index ascending            */
+      for (int32_t l = 0; l < layers; ++l) {  /* layers                          */
+        for (int d2 = 0; d2 <= 1; ++d2) {     /* horizontal entity, then vertical */
+          int t = 2 * d1 + d2;
+          if (first[t]) first[t][i * (layers + 1 - d2) + l] = c;
+          c += delta[t];
+        }
+      }
+      /* the top horizontal entity of the column */
+      int t = 2 * d1;
+      if (first[t]) first[t][i * (layers + 1) + layers] = c;
+      c += delta[t];
+    }
+  }
+  return c;
+}
+
+static int32_t nentities(int32_t nvc, int d) { return d == 2 ? 1 : nvc; }
+
+int32_t oracle_stencil_size(int32_t nvc, const int32_t delta[6]) {
+  int32_t k = 0;
+  for (int d = 0; d <= 2; ++d) k += nentities(nvc, d) * (2 * delta[2 * d] + delta[2 * d + 1]);
+  return k;
+}
+
+int oracle_base_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                    const int32_t *cell_edges, int32_t layers, const int32_t delta[6],
+                    int64_t *const first[6], int32_t *map) {
+  int32_t k = oracle_stencil_size(nvc, delta);
+  for (int64_t c = 0; c < ncells; ++c) {
+    int32_t j = 0;
+    for (int d = 0; d <= 2; ++d) {
+      for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+        int64_t id;
+        if (d == 0) id = cell_verts[c * nvc + e];
+        else if (d == 1) {
+          if ((delta[2] || delta[3]) && !cell_edges) return -1;
+          id = (delta[2] || delta[3]) ? cell_edges[c * nvc + e] : 0;
+        } else id = c;
+        /* bottom horizontal entity ((d,0),(id,0)) */
+        for (int32_t q = 0; q < delta[2 * d]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d][id * (layers + 1) + 0] + q);
+        /* top horizontal entity ((d,0),(id,1)) */
+        for (int32_t q = 0; q < delta[2 * d]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d][id * (layers + 1) + 1] + q);
+        /* vertical entity ((d,1),(id,0)) */
+        for (int32_t q = 0; q < delta[2 * d + 1]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d + 1][id * layers + 0] + q);
+      }
+    }
+  }
+  return 0;
+}
+
+/* Algorithm 2: offset of stencil DoF i = delta((d,0)) + delta((d,1)) where d
+ * is the base entity dimension E_S(i) of that DoF. */
+void oracle_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
+  int32_t i = 0;
+  for (int d = 0; d <= 2; ++d) {
+    int32_t per = 2 * delta[2 * d] + delta[2 * d + 1];
+    for (int32_t e = 0; e < nentities(nvc, d); ++e)
+      for (int32_t q = 0; q < per; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reference elements.                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Gauss-Legendre rule on [0,1]: roots of P_n by Newton's method from the
+ * Chebyshev-like initial guesses, weights 2/((1-t^2) P_n'(t)^2) halved. */
+void oracle_gauss_legendre(int32_t n, double *x, double *w) {
+  const double pi = 3.14159265358979323846;
+  for (int32_t i = 0; i < n; ++i) {
+    double t = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int32_t k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      double dt = p1 / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-17) break;
+    }
+    /* recompute derivative at the converged root */
+    {
+      double p0 = 1.0, p1 = t;
+      for (int32_t k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+    }
+    /* t in (-1,1) descending with i; map to [0,1] ascending */
+    x[n - 1 - i] = 0.5 * (1.0 + t);
+    w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+static int32_t g_hex_rule = 4;
+void oracle_set_hex_rule(int32_t n) { g_hex_rule = (n >= 1 && n <= 16) ? n : 4; }
+
+/* Prism P1 x P1 (triangle (0,0),(1,0),(0,1) times [0,1]).  Stencil DoF
+ * i = 2a + b: vertex a of the triangle, b = 0 bottom / 1 top. */
+static double tri_lam(int a, double xi, double eta) {
+  return a == 0 ? 1.0 - xi - eta : (a == 1 ? xi : eta);
+}
+static void tri_dlam(int a, double *dxi, double *deta) {
+  if (a == 0) { *dxi = -1.0; *deta = -1.0; }
+  else if (a == 1) { *dxi = 1.0; *deta = 0.0; }
+  else { *dxi = 0.0; *deta = 1.0; }
+}
+static double lin(int b, double z) { return b == 0 ? 1.0 - z : z; }
+static double dlin(int b) { return b == 0 ? -1.0 : 1.0; }
+
+static void prism_basis(double xi, double eta, double zeta, double phi[6], double grad[6][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double dx, de;
+      tri_dlam(a, &dx, &de);
+      phi[2 * a + b] = tri_lam(a, xi, eta) * lin(b, zeta);
+      grad[2 * a + b][0] = dx * lin(b, zeta);
+      grad[2 * a + b][1] = de * lin(b, zeta);
+      grad[2 * a + b][2] = tri_lam(a, xi, eta) * dlin(b);
+    }
+}
+
+/* 6-point prism rule: triangle points (1/6,1/6),(2/3,1/6),(1/6,2/3) with
+ * weights 1/6 each, times 2-point Gauss on [0,1] (weights 1/2). */
+static void prism_rule(double pts[6][3], double wts[6]) {
+  const double tp[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+  double gz[2], gw[2];
+  oracle_gauss_legendre(2, gz, gw);
+  int q = 0;
+  for (int t = 0; t < 3; ++t)
+    for (int g = 0; g < 2; ++g) {
+      pts[q][0] = tp[t][0];
+      pts[q][1] = tp[t][1];
+      pts[q][2] = gz[g];
+      wts[q] = (1.0 / 6.0) * gw[g];
+      ++q;
+    }
+}
+
+/* Hexahedron, reference [0,1]^3.  Geometry is Q1 x P1: coordinate stencil
+ * DoF 2a+b, base-quad vertex a -> (0,0),(1,0),(1,1),(0,1), b bottom/top. */
+static const int quad_vx[4] = {0, 1, 1, 0};
+static const int quad_vy[4] = {0, 0, 1, 1};
+static void hex_geom_basis(double xi, double eta, double zeta, double phi[8], double grad[8][3]) {
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double nx = lin(quad_vx[a], xi), ny = lin(quad_vy[a], eta);
+      int i = 2 * a + b;
+      phi[i] = nx * ny * lin(b, zeta);
+      grad[i][0] = dlin(quad_vx[a]) * ny * lin(b, zeta);
+      grad[i][1] = nx * dlin(quad_vy[a]) * lin(b, zeta);
+      grad[i][2] = nx * ny * dlin(b);
+    }
+}
+
+/* 1-D P2 Lagrange basis on nodes t0 = 0, t1 = 1, t2 = 1/2. */
+static double p2(int k, double t) {
+  const double nodes[3] = {0.0, 1.0, 0.5};
+  double v = 1.0;
+  for (int m = 0; m < 3; ++m)
+    if (m != k) v *= (t - nodes[m]) / (nodes[k] - nodes[m]);
+  return v;
+}
+
+/* Q2 x P2 on the hexahedron.  Stencil DoF i = 3e + v: horizontal entity e in
+ * the order (v0,v1,v2,v3, e0=(v0v1), e1=(v1v2), e2=(v2v3), e3=(v3v0), centre),
+ * vertical node v in the order (bottom, top, middle).  Horizontal nodes as
+ * 1-D node index pairs (0 -> 0, 1 -> 1, 2 -> 1/2).  The same 27 functions in
+ * the same order are the DG2 basis (all DoFs interior to the cell). */
+static const int q2_ix[9] = {0, 1, 1, 0, 2, 1, 2, 0, 2};
+static const int q2_iy[9] = {0, 0, 1, 1, 0, 2, 1, 2, 2};
+static void q2_basis(double xi, double eta, double zeta, double phi[27]) {
+  for (int e = 0; e < 9; ++e)
+    for (int v = 0; v < 3; ++v) phi[3 * e + v] = p2(q2_ix[e], xi) * p2(q2_iy[e], eta) * p2(v, zeta);
+}
+
+static double det3(const double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+/* |det J| at reference point from coordinate values X[i][r] and geometry
+ * basis gradients. */
+static double abs_detJ(int ngeo, const double *X, double grad[][3]) {
+  double J[3][3] = {{0}};
+  for (int i = 0; i < ngeo; ++i)
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) J[r][s] += X[3 * i + r] * grad[i][s];
+  return fabs(det3(J));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local kernels (the stencil function S of Algorithm 3).                   */
+/* vals[a] holds the gathered values of argument a (k x ncomp); outputs are  */
+/* written into out[a] (zeroed by the driver), |contributions| into absv[a]. */
+/* ------------------------------------------------------------------------ */
+
+/* int f phi_i dx on a P1xP1 prism with general (possibly non-straight)
+ * coordinates; used for both the RHS (f interpolated) and the mass action. */
+static void k_mass_prism(double *const *vals, double *const *out, double *const *absv) {
+  double pts[6][3], wts[6];
+  prism_rule(pts, wts);
+  const double *X = vals[0], *f = vals[1];
+  for (int q = 0; q < 6; ++q) {
+    double phi[6], grad[6][3];
+    prism_basis(pts[q][0], pts[q][1], pts[q][2], phi, grad);
+    double dj = abs_detJ(6, X, grad);
+    double fq = 0.0, fa = 0.0;
+    for (int j = 0; j < 6; ++j) {
+      fq += phi[j] * f[j];
+      fa += fabs(phi[j] * f[j]);
+    }
+    for (int i = 0; i < 6; ++i) {
+      out[2][i] += wts[q] * dj * fq * phi[i];
+      absv[2][i] += wts[q] * dj * fa * fabs(phi[i]);
+    }
+  }
+}
+
+/* Nodal interpolation of a P1xP1 field into DG1xDG1: DG1 node j = 2a+b sits
+ * at prism vertex a, level b; its value is the P1xP1 field evaluated there. */
+static void k_interp(double *const *vals, double *const *out) {
+  const double node[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double phi[6], grad[6][3];
+      prism_basis(node[a][0], node[a][1], (double)b, phi, grad);
+      double v = 0.0;
+      for (int j = 0; j < 6; ++j)
+        if (phi[j] != 0.0) v += phi[j] * vals[0][j];
+      out[1][2 * a + b] = v;
+    }
+}
+
+/* Quadrature points/weights and basis tables for int u^2 v on prism or hex. */
+typedef struct {
+  int nq, nb, ngeo;
+  double w[16 * 16 * 16];
+  double phi[16 * 16 * 16][27];
+  double ggrad[16 * 16 * 16][8][3];
+} u2v_tab;
+
+static void u2v_setup(int32_t nvc, u2v_tab *T) {
+  if (nvc == 3) {
+    double pts[6][3], wts[6];
+    prism_rule(pts, wts);
+    T->nq = 6; T->nb = 6; T->ngeo = 6;
+    for (int q = 0; q < 6; ++q) {
+      double phi[6], grad[6][3];
+      prism_basis(pts[q][0], pts[q][1], pts[q][2], phi, grad);
+      T->w[q] = wts[q];
+      for (int i = 0; i < 6; ++i) {
+        T->phi[q][i] = phi[i];
+        for (int s = 0; s < 3; ++s) T->ggrad[q][i][s] = grad[i][s];
+      }
+    }
+  } else {
+    int n = g_hex_rule;
+    double gx[16], gw[16];
+    oracle_gauss_legendre(n, gx, gw);
+    T->nq = n * n * n; T->nb = 27; T->ngeo = 8;
+    int q = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          double phi8[8], grad8[8][3];
+          T->w[q] = gw[i] * gw[j] * gw[k];
+          q2_basis(gx[i], gx[j], gx[k], T->phi[q]);
+          hex_geom_basis(gx[i], gx[j], gx[k], phi8, grad8);
+          for (int a = 0; a < 8; ++a)
+            for (int s = 0; s < 3; ++s) T->ggrad[q][a][s] = grad8[a][s];
+          ++q;
+        }
+  }
+}
+
+/* F_i += sum_q w_q |detJ_q| u(x_q)^2 phi_i(x_q). */
+static void k_u2v(const u2v_tab *T, double *const *vals, double *const *out, double *const *absv) {
+  const double *X = vals[0], *u = vals[1];
+  for (int q = 0; q < T->nq; ++q) {
+    double dj = abs_detJ(T->ngeo, X, (double(*)[3])T->ggrad[q]);
+    double uq = 0.0, ua = 0.0;
+    for (int j = 0; j < T->nb; ++j) {
+      uq += T->phi[q][j] * u[j];
+      ua += fabs(T->phi[q][j] * u[j]);
+    }
+    for (int i = 0; i < T->nb; ++i) {
+      out[2][i] += T->w[q] * dj * uq * uq * T->phi[q][i];
+      absv[2][i] += T->w[q] * dj * ua * ua * fabs(T->phi[q][i]);
+    }
+  }
+}
+
+/* Adjoint of k_u2v applied to a cotangent w on F's space:
+ * g_j += sum_q w_q |detJ_q| 2 u(x_q) w(x_q) phi_j(x_q)  (the transpose of
+ * dF_i/du_j = sum_q w_q |detJ_q| 2 u(x_q) phi_j(x_q) phi_i(x_q)). */
+static void k_u2v_adj(const u2v_tab *T, double *const *vals, double *const *out, double *const *absv) {
+  const double *X = vals[0], *u = vals[1], *w = vals[2];
+  for (int q = 0; q < T->nq; ++q) {
+    double dj = abs_detJ(T->ngeo, X, (double(*)[3])T->ggrad[q]);
+    double uq = 0.0, ua = 0.0, wq = 0.0, wa = 0.0;
+    for (int j = 0; j < T->nb; ++j) {
+      uq += T->phi[q][j] * u[j];
+      ua += fabs(T->phi[q][j] * u[j]);
+      wq += T->phi[q][j] * w[j];
+      wa += fabs(T->phi[q][j] * w[j]);
+    }
+    for (int j = 0; j < T->nb; ++j) {
+      out[3][j] += T->w[q] * dj * 2.0 * uq * wq * T->phi[q][j];
+      absv[3][j] += T->w[q] * dj * 2.0 * ua * wa * fabs(T->phi[q][j]);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3: for every base cell, read its explicit list once; for every */
+/* layer apply the stencil function, then add the vertical offsets.         */
+/* ------------------------------------------------------------------------ */
+#define ORC_MAXARGS 6
+#define ORC_MAXVALS (27 * 3)
+
+int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
+                    const int32_t *cell_verts, const double *base_xy, int32_t nargs,
+                    const orc_arg *args) {
+  if (nargs < 1 || nargs > ORC_MAXARGS || layers < 1) return -1;
+  for (int a = 0; a < nargs; ++a)
+    if (args[a].k < 1 || args[a].k > 27 || args[a].ncomp < 1 || args[a].ncomp > 3) return -2;
+  u2v_tab *T = NULL;
+  if (kernel == ORC_K_U2V || kernel == ORC_K_U2V_ADJ) {
+    T = (u2v_tab *)malloc(sizeof(u2v_tab));
+    if (!T) return -3;
+    u2v_setup(nvc, T);
+  }
+  int64_t dofs[ORC_MAXARGS][27];
+  double vbuf[ORC_MAXARGS][ORC_MAXVALS], obuf[ORC_MAXARGS][ORC_MAXVALS], abuf[ORC_MAXARGS][ORC_MAXVALS];
+  double *vals[ORC_MAXARGS], *outv[ORC_MAXARGS], *absv[ORC_MAXARGS];
+  for (int a = 0; a < ORC_MAXARGS; ++a) {
+    vals[a] = vbuf[a];
+    outv[a] = obuf[a];
+    absv[a] = abuf[a];
+  }
+  for (int64_t c = 0; c < ncells; ++c) {
+    /* (dof_0 .. dof_{k-1}) <- L(v) */
+    for (int a = 0; a < nargs; ++a)
+      for (int j = 0; j < args[a].k; ++j) dofs[a][j] = args[a].map[c * args[a].k + j];
+    for (int32_t l = 0; l < layers; ++l) { /* cells: d2 = 1, l = 0 .. lambda-1 */
+      for (int a = 0; a < nargs; ++a) {
+        int n = args[a].k * args[a].ncomp;
+        for (int t = 0; t < n; ++t) obuf[a][t] = abuf[a][t] = 0.0;
+        if (args[a].access == ORC_READ)
+          for (int j = 0; j < args[a].k; ++j)
+            for (int r = 0; r < args[a].ncomp; ++r)
+              vbuf[a][j * args[a].ncomp + r] = args[a].data[dofs[a][j] * args[a].ncomp + r];
+      }
+      switch (kernel) {
+        case ORC_K_EXTRUDE: {
+          /* stencil DoF 2a+b of the coordinate space: vertex a, level l+b */
+          for (int a = 0; a < nvc; ++a)
+            for (int b = 0; b < 2; ++b) {
+              int64_t v = cell_verts[c * nvc + a];
+              obuf[0][3 * (2 * a + b) + 0] = base_xy[2 * v + 0];
+              obuf[0][3 * (2 * a + b) + 1] = base_xy[2 * v + 1];
+              obuf[0][3 * (2 * a + b) + 2] = (double)(l + b) / (double)layers;
+            }
+          break;
+        }
+        case ORC_K_COPY:
+          for (int j = 0; j < args[1].k; ++j) obuf[1][j] = vbuf[0][j];
+          break;
+        case ORC_K_MASS:
+          k_mass_prism(vals, outv, absv);
+          break;
+        case ORC_K_INTERP:
+          k_interp(vals, outv);
+          break;
+        case ORC_K_U2V:
+          k_u2v(T, vals, outv, absv);
+          break;
+        case ORC_K_U2V_ADJ:
+          k_u2v_adj(T, vals, outv, absv);
+          break;
+        default:
+          free(T);
+          return -4;
+      }
+      /* write back */
+      for (int a = 0; a < nargs; ++a) {
+        if (args[a].access == ORC_READ) continue;
+        for (int j = 0; j < args[a].k; ++j)
+          for (int r = 0; r < args[a].ncomp; ++r) {
+            int64_t g = dofs[a][j] * args[a].ncomp + r;
+            int t = j * args[a].ncomp + r;
+            if (args[a].access == ORC_INC) args[a].data[g] += obuf[a][t];
+            else args[a].data[g] = obuf[a][t];
+            if (args[a].absdata) {
+              if (args[a].access == ORC_INC) args[a].absdata[g] += abuf[a][t];
+              else args[a].absdata[g] = abuf[a][t];
+            }
+          }
+      }
+      /* dof_j <- dof_j + offset(j) */
+      for (int a = 0; a < nargs; ++a)
+        for (int j = 0; j < args[a].k; ++j) dofs[a][j] += args[a].offset[j];
+    }
+  }
+  free(T);
+  return 0;
+}

@@ -1,0 +1,82 @@
+/*
+ * CPU oracle for the extruded-mesh numbering and par_loop.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, serial FP64 implementation
+ * written from the paper (Bercea et al., "A structure-exploiting numbering
+ * algorithm for finite elements on extruded meshes"): Algorithm 1 (Sec. 3.2),
+ * Algorithm 2 and Algorithm 3 (Sec. 3.3), and the residual I = int f v dx of
+ * Sec. 4.1.1 plus the nonlinear residual int u^2 v dx and its adjoint.  Only
+ * tests, the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * CUDA library never does, and the two share no code.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Access descriptors of Algorithm 3 arguments. */
+enum { ORC_READ = 0, ORC_WRITE = 1, ORC_INC = 2 };
+
+/* Local kernels available to oracle_par_loop. */
+enum {
+  ORC_K_EXTRUDE = 0, /* coords WRITE: (x_v, y_v, level/layers)                   */
+  ORC_K_COPY = 1,    /* in READ, out WRITE: out_j = in_j                           */
+  ORC_K_MASS = 2,    /* coords READ, f READ, b INC: b_i += int f phi_i (P1xP1)     */
+  ORC_K_INTERP = 3,  /* x READ (P1xP1), out WRITE (DG1xDG1): nodal interpolation   */
+  ORC_K_U2V = 4,     /* coords READ, u READ, F INC|WRITE: F_i += int u^2 phi_i     */
+  ORC_K_U2V_ADJ = 5  /* coords READ, u READ, w READ, g INC|WRITE: (dF/du)^T w      */
+};
+
+typedef struct {
+  const int32_t *map;    /* ncells x k, the layer-0 explicit lists L(c)          */
+  const int32_t *offset; /* k vertical offsets (Algorithm 2)                     */
+  int32_t k;             /* DoFs per stencil                                      */
+  int32_t ncomp;         /* values per DoF (3 for coordinates, else 1)           */
+  double *data;          /* field values, ndofs x ncomp                          */
+  double *absdata;       /* optional: accumulates |contribution| for INC outputs */
+  int32_t access;        /* ORC_READ / ORC_WRITE / ORC_INC                        */
+} orc_arg;
+
+/* Edges of the base mesh, numbered by first appearance when cells are scanned
+ * in order and local edges e_k = (v_k, v_{(k+1) mod nvc}) in order.  Writes
+ * cell_edges (ncells x nvc); returns the number of edges or -1. */
+int64_t oracle_derive_edges(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                            int64_t nverts, int32_t *cell_edges);
+
+/* Algorithm 1.  first[2*d1+d2] (may be NULL when delta[2*d1+d2]==0) receives
+ * N[d1] x (layers+1-d2) int64 entries: the first global number given to entity
+ * ((d1,d2),(i,l)) at index i*(layers+1-d2)+l.  Returns the number of DoFs. */
+int64_t oracle_alg1(const int64_t N[3], int32_t layers, const int32_t delta[6],
+                    int64_t *const first[6]);
+
+/* Stencil length k of a cell with nvc vertices for the given delta. */
+int32_t oracle_stencil_size(int32_t nvc, const int32_t delta[6]);
+
+/* Explicit layer-0 lists L(c) read off the entity tables of oracle_alg1. */
+int oracle_base_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                    const int32_t *cell_edges, int32_t layers, const int32_t delta[6],
+                    int64_t *const first[6], int32_t *map);
+
+/* Algorithm 2. */
+void oracle_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset);
+
+/* Algorithm 3 over cells [0, ncells) with the chosen local kernel.  For
+ * ORC_K_EXTRUDE, base_xy (nverts x 2) and cell_verts are read; otherwise they
+ * may be NULL.  Returns 0 or a negative error. */
+int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
+                    const int32_t *cell_verts, const double *base_xy, int32_t nargs,
+                    const orc_arg *args);
+
+/* n-point Gauss-Legendre rule on [0,1] (Newton iteration on P_n). */
+void oracle_gauss_legendre(int32_t n, double *x, double *w);
+
+/* Select the 1-D Gauss rule used by the hexahedral kernels (default 4). */
+void oracle_set_hex_rule(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

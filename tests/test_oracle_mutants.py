@@ -1,0 +1,74 @@
+"""The oracle's pins must be strong enough that a plausible mistake anywhere
+in it fails at least one of them.  Each case plants one mistake in a copy of
+oracle.c (on the CPU), builds it, and runs the numbering and kernel pins
+against it in a subprocess; the run must fail."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    # Algorithm 1
+    "top_entity_numbered_late": ("first[t][i * (layers + 1) + layers] = c;",
+                                 "first[t][i * (layers + 1) + layers] = c + 1;"),
+    "vertical_before_horizontal": ("for (int d2 = 0; d2 <= 1; ++d2) {", "for (int d2 = 1; d2 >= 0; --d2) {"),
+    "top_not_counted": ("      c += delta[t];\n    }\n  }\n  return c;", "    }\n  }\n  return c;"),
+    # explicit lists and Algorithm 2
+    "top_slot_reads_bottom": ("first[2 * d][id * (layers + 1) + 1] + q", "first[2 * d][id * (layers + 1) + 0] + q"),
+    "offset_drops_horizontal": ("offset[i++] = delta[2 * d] + delta[2 * d + 1];", "offset[i++] = delta[2 * d + 1];"),
+    "edge_wrong_neighbour": ("cell_verts[c * nvc + (k + 1) % nvc]", "cell_verts[c * nvc + (k + nvc - 1) % nvc]"),
+    # quadrature and elements
+    "prism_weight": ("wts[q] = (1.0 / 6.0) * gw[g];", "wts[q] = (1.0 / 3.0) * gw[g];"),
+    "triangle_point": ("{2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}", "{2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 6.0}"),
+    "det_sign_term": ("J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -",
+                      "J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) +"),
+    "no_abs_detJ": ("return fabs(det3(J));", "return det3(J);"),
+    "jacobian_transposed": ("J[r][s] += X[3 * i + r] * grad[i][s];", "J[s][r] += X[3 * i + r] * grad[i][s] * (r == 2 ? 2.0 : 1.0);"),
+    "p2_node_order": ("const double nodes[3] = {0.0, 1.0, 0.5};", "const double nodes[3] = {0.0, 0.5, 1.0};"),
+    "q2_edge_table": ("static const int q2_ix[9] = {0, 1, 1, 0, 2, 1, 2, 0, 2};",
+                      "static const int q2_ix[9] = {0, 1, 1, 0, 1, 2, 2, 0, 2};"),
+    "gauss_weight": ("w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - t * t) * dp * dp);",
+                     "w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - t * t) * dp);"),
+    "u2v_linear": ("out[2][i] += T->w[q] * dj * uq * uq * T->phi[q][i];",
+                   "out[2][i] += T->w[q] * dj * uq * T->phi[q][i];"),
+    "adjoint_factor": ("out[3][j] += T->w[q] * dj * 2.0 * uq * wq * T->phi[q][j];",
+                       "out[3][j] += T->w[q] * dj * uq * wq * T->phi[q][j];"),
+    "adjoint_uses_u_twice": ("out[3][j] += T->w[q] * dj * 2.0 * uq * wq * T->phi[q][j];",
+                             "out[3][j] += T->w[q] * dj * 2.0 * uq * uq * T->phi[q][j];"),
+    "extrude_level": ("(double)(l + b) / (double)layers;", "(double)(l) / (double)layers;"),
+    "interp_node_swap": ("out[1][2 * a + b] = v;", "out[1][2 * a + (1 - b)] = v;"),
+    "mass_wrong_basis": ("out[2][i] += wts[q] * dj * fq * phi[i];", "out[2][i] += wts[q] * dj * fq * phi[(i + 2) % 6];"),
+}
+
+
+def _run_pins(source: str, tmp_path):
+    c = tmp_path / "oracle_mut.c"
+    c.write_text(source)
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(c), "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_numbering.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_kernels.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r
+
+
+def test_unmutated_copy_passes(tmp_path):
+    r = _run_pins(open(SRC).read(), tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    r = _run_pins(src.replace(old, new, 1), tmp_path)
+    assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-2000:]}"
