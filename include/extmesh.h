@@ -1,0 +1,224 @@
+/*
+ * extmesh: numbering and parallel iteration (par_loop) over extruded meshes on
+ * one GB300 GPU.  C ABI.
+ *
+ * Method: Bercea et al., "A structure-exploiting numbering algorithm for
+ * finite elements on extruded meshes, and its performance evaluation in
+ * Firedrake".  An extruded mesh is a base mesh replicated over `layers`
+ * intervals (Sec. 3.1); the degrees of freedom (DoFs) of a function space are
+ * numbered vertical-innermost (Algorithm 1, Sec. 3.2) so that only the
+ * bottom-layer stencil list of each column is stored; the DoFs of layer l are
+ * base_map[c][i] + l * offset[i] (Algorithm 2 and the direct-addressing
+ * formula, Sec. 3.3), and a stencil (local kernel) is applied to every cell of
+ * every column with the layers innermost (Algorithm 3, Sec. 3.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_host are host memory; every other data pointer is
+ *     device memory of the current CUDA device.  Field data are FP64.
+ *   - The library owns meshes, spaces, stencil maps and batch plans (device
+ *     copies included); destroy functions free them.  The caller owns field
+ *     buffers and streams; `stream` is a cudaStream_t (NULL = legacy default
+ *     stream).
+ *   - Launches are asynchronous on the given stream.  A validation error
+ *     returns before anything is launched (nothing is partially applied).
+ *     Device-side conditions (bounded waits that expired, inputs a kernel
+ *     cannot handle) set a device error word that ext_sync_check reports.
+ *   - Every function returns EXT_OK or an error code; ext_last_error() gives
+ *     a message for the calling thread's most recent error.
+ *   - Entity and DoF indices are int32; a space with 2^31 or more DoFs is
+ *     rejected with EXT_EOVERFLOW.
+ */
+#ifndef EXTMESH_H
+#define EXTMESH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EXT_ABI_VERSION 1
+
+typedef enum {
+  EXT_OK = 0,
+  EXT_EINVAL = 1,        /* invalid argument or inconsistent inputs        */
+  EXT_ENOMEM = 2,        /* device or host allocation failed               */
+  EXT_ECUDA = 3,         /* a CUDA runtime call failed                     */
+  EXT_EOVERFLOW = 4,     /* a count does not fit the int32 index type      */
+  EXT_ETIMEOUT = 5,      /* a bounded device-side wait expired             */
+  EXT_EDEVICE = 6,       /* the device error word reported a condition     */
+  EXT_EUNSUPPORTED = 7   /* valid request this build does not implement    */
+} ext_status;
+
+/* Base-mesh cell kinds: triangles extrude to prisms, quadrilaterals to
+ * hexahedra (tensor-product cells, Sec. 3.1.1). */
+typedef enum { EXT_TRI = 3, EXT_QUAD = 4 } ext_cell_kind;
+
+/* Access descriptors of a par_loop argument (Sec. 3.3, PyOP2 semantics):
+ * READ is never written; WRITE overwrites every DoF the loop reaches; INC
+ * adds into the existing values (the caller zeroes them first). */
+typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
+
+/* Local kernels (stencil functions S of Algorithm 3).  Each fixes its
+ * argument list; spaces are identified by their delta table:
+ *   CG1xCG1  delta = {1,0, 0,0, 0,0}          (P1 x P1, "coords" with ncomp 3)
+ *   DG0xDG0  delta = {0,0, 0,0, 0,1}
+ *   DG1xDG1  delta = {0,0, 0,0, 0,6}          (prisms)
+ *   Q2xP2    delta = {1,1, 1,1, 1,1}          (hexahedra, continuous)
+ *   DG2      delta = {0,0, 0,0, 0,27}         (hexahedra, discontinuous)
+ *
+ * EXT_K_EXTRUDE     [coords WRITE]                       coordinates (x_v, y_v, level/layers)
+ *                   of the unit-height column over every base vertex (Sec. 4.1.1).
+ * EXT_K_COPY_DG     [in READ, out WRITE], one space with DoFs only on cells
+ *                   (delta(2,1) > 0, all other deltas 0): out = in.
+ * EXT_K_RHS_P1P1    [coords READ, f READ, b INC] on prisms, all CG1xCG1:
+ *                   b_i += int_cell f_h phi_i dx  (the residual I_1, Sec. 4.1.1).
+ * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
+ * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
+ *                   interpolation, out at DG1 node (vertex a, level b) = x there.
+ * EXT_K_U2V_FWD     [coords READ, u READ, F INC|WRITE]: F_i += int u_h^2 phi_i dx,
+ *                   u and F on the same space: CG1xCG1 on prisms, Q2xP2 or DG2 on
+ *                   hexahedra; INC for continuous spaces, WRITE for DG2.
+ * EXT_K_U2V_ADJ     [coords READ, u READ, w READ, g INC|WRITE]: g = (dF/du)^T w,
+ *                   the hand-written adjoint of EXT_K_U2V_FWD (gathers become
+ *                   scatter-adds; F's INC output becomes the READ cotangent w).
+ * EXT_K_U2V_FWDADJ  [coords READ, u READ, w READ, F INC|WRITE, g INC|WRITE]:
+ *                   both of the above in one pass.
+ * Quadrature: prisms use the 6-point rule (3-point degree-2 triangle rule x
+ * 2-point Gauss); hexahedra use 4x4x4 Gauss points. */
+typedef enum {
+  EXT_K_EXTRUDE = 0,
+  EXT_K_COPY_DG = 1,
+  EXT_K_RHS_P1P1 = 2,
+  EXT_K_MASS_P1P1 = 3,
+  EXT_K_INTERP_DG1 = 4,
+  EXT_K_U2V_FWD = 5,
+  EXT_K_U2V_ADJ = 6,
+  EXT_K_U2V_FWDADJ = 7
+} ext_kernel_id;
+
+typedef struct ext_mesh ext_mesh;
+typedef struct ext_space ext_space;
+typedef struct ext_batch ext_batch;
+
+/* One par_loop argument: a field on `space` (data: device, FP64,
+ * ndofs * ncomp values, DoF-major) with its access descriptor. */
+typedef struct {
+  const ext_space *space;
+  void *data;
+  int32_t access; /* ext_access */
+} ext_arg;
+
+/* Launch parameters of the batched persistent loop (and its autotuner). */
+typedef struct {
+  int32_t cols_per_item; /* base columns per work item                    */
+  int32_t layer_tile;    /* layers per work item; 0 = the whole column     */
+  int32_t use_atomics;   /* 1: FP64 atomic increments; 0: colour phases    */
+  int32_t threads;       /* threads per CTA                                */
+  int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid    */
+} ext_tune_params;
+
+/* Library ABI version (EXT_ABI_VERSION of the build). */
+int32_t ext_abi_version(void);
+
+/* Message of the calling thread's most recent error ("" if none).  The
+ * string stays valid until the thread's next failing call. */
+const char *ext_last_error(void);
+
+/* Creates an extruded mesh (Sec. 3.1): the base mesh's cell-vertex lists
+ * (the only topology input; every other adjacency is derived from it, Sec.
+ * 2.2) and the number of layers lambda >= 1.
+ *   kind            EXT_TRI or EXT_QUAD
+ *   nverts, ncells  base vertex and cell counts (ncells may be 0)
+ *   cell_verts_host ncells x kind int32, vertex ids in [0, nverts), counter-
+ *                   clockwise when base_xy_host is given
+ *   base_xy_host    nverts x 2 FP64 vertex coordinates, or NULL (then
+ *                   EXT_K_EXTRUDE is unavailable and orientation is unchecked)
+ * Edges are numbered by first appearance when scanning cells in order with
+ * local edge k = (vertex k, vertex k+1 mod kind).  The topology is copied to
+ * the device (synchronously).  Errors: EXT_EINVAL (ids out of range, repeated
+ * vertex in a cell, clockwise or degenerate cell, layers < 1), EXT_EOVERFLOW,
+ * EXT_ENOMEM, EXT_ECUDA. */
+ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,
+                           const int32_t *cell_verts_host, const double *base_xy_host,
+                           int32_t layers, ext_mesh **out);
+
+/* Entity counts N_0, N_1, N_2 (vertices, edges, cells) of the base mesh, the
+ * cell kind and the number of layers (Sec. 2.2, 3.1). */
+ext_status ext_mesh_info(const ext_mesh *mesh, int32_t *kind, int64_t n[3], int32_t *layers);
+
+void ext_mesh_destroy(ext_mesh *mesh);
+
+/* Numbers the DoFs of a function space (Algorithm 1, Sec. 3.2) and builds its
+ * bottom-layer stencil map and vertical offsets (Sec. 3.3, Algorithm 2).
+ *   delta_host  6 int32: delta((d1,d2)) at index 2*d1+d2, DoFs per extruded
+ *               entity of horizontal dimension d1 and vertical dimension d2
+ *   ncomp       values per DoF (1, or 3 for a coordinate field)
+ * Numbering: base entities dimension-major (vertices, edges, cells), index
+ * ascending; in each column, layer by layer, the horizontal entity's
+ * delta(d,0) numbers then the vertical entity's delta(d,1) numbers, and the
+ * top horizontal entity last.  Stencil order: the cell's vertices, edges,
+ * then the cell itself; per entity the bottom horizontal DoFs, the top
+ * horizontal DoFs, then the vertical DoFs.  The map is computed by a kernel
+ * on `stream` (asynchronous).  Errors: EXT_EINVAL, EXT_EOVERFLOW (2^31 DoFs or
+ * more), EXT_ENOMEM, EXT_ECUDA. */
+ext_status ext_number_dofs(ext_mesh *mesh, const int32_t delta_host[6], int32_t ncomp,
+                           void *stream, ext_space **out);
+
+/* DoF count, stencil length k, ncomp and the device stencil data of a space:
+ * base_map (ncells x k int32, row-major, global DoFs at layer 0) and offset
+ * (k int32).  Any output pointer may be NULL.  The device arrays belong to the
+ * space. */
+ext_status ext_space_info(const ext_space *space, int64_t *ndofs, int32_t *k, int32_t *ncomp,
+                          const int32_t **base_map_dev, const int32_t **offset_dev);
+
+/* Copies the stencil map (ncells x k) and offsets (k) to host arrays
+ * (synchronous on the space's creation stream; either pointer may be NULL). */
+ext_status ext_space_copy_map_to_host(const ext_space *space, int32_t *map_host, int32_t *offset_host);
+
+void ext_space_destroy(ext_space *space);
+
+/* Algorithm 3: applies local kernel `kernel_id` to every cell of every column
+ * of `mesh`, columns in parallel and layers innermost, reading each column's
+ * stencil lists once and reaching layer l by base_map + l * offset.  `args`
+ * must match the kernel's argument list (spaces of this mesh, access
+ * descriptors).  Asynchronous on `stream`.  Errors: EXT_EINVAL (argument
+ * list, spaces or modes do not match), EXT_EUNSUPPORTED, EXT_ECUDA. */
+ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int32_t nargs,
+                        const ext_arg *args, void *stream);
+
+/* Batched form: one persistent launch applies `kernel_id` over `nmesh`
+ * extruded meshes of different base sizes and layer counts.  `args` holds
+ * nmesh x nargs entries (mesh-major).  Work items are (mesh, column range,
+ * layer range) tiles taken from a device work counter; every spin-wait in
+ * the kernel is bounded.  `params` NULL selects parameters by autotuning
+ * (timed trial launches on `stream`, which overwrite the INC/WRITE outputs;
+ * the caller zeroes INC outputs before each real launch).  The launch is
+ * captured into a CUDA graph; ext_batch_launch replays it.  Supported
+ * kernels: EXT_K_U2V_FWD, EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ on CG1xCG1 prisms.
+ * Errors: as ext_par_loop, plus EXT_ENOMEM. */
+ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id,
+                            int32_t nargs, const ext_arg *args, const ext_tune_params *params,
+                            void *stream, ext_batch **out);
+
+/* Replays the captured batched launch on `stream`. */
+ext_status ext_batch_launch(ext_batch *batch, void *stream);
+
+/* Runs the batched work queue with an uncaptured launch and explicit
+ * parameters (used by the autotuner; also a plain entry point). */
+ext_status ext_batch_launch_params(ext_batch *batch, const ext_tune_params *params, void *stream);
+
+/* Parameters in use by the batch (chosen or autotuned). */
+ext_status ext_batch_params(const ext_batch *batch, ext_tune_params *out);
+
+void ext_batch_destroy(ext_batch *batch);
+
+/* Waits for `stream`, then reads and clears the device error word:
+ * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device
+ * condition; see ext_last_error), or EXT_ECUDA (an asynchronous CUDA error). */
+ext_status ext_sync_check(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXTMESH_H */

@@ -1,0 +1,769 @@
+// Host implementation of the extmesh C ABI (include/extmesh.h): validation,
+// base-mesh entity derivation, space numbering set-up, par_loop dispatch and
+// the batched plan (autotuning, colouring, CUDA-graph capture).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "ext_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_last_error;
+
+ext_status ext_fail(ext_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define EXT_CUDA(call, what)                                                                   \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return ext_fail(EXT_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char *ext_last_error(void) { return g_last_error.c_str(); }
+extern "C" int32_t ext_abi_version(void) { return EXT_ABI_VERSION; }
+
+static std::mutex g_word_mu;
+static unsigned int *g_word[128];
+
+unsigned int *ext_device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  std::lock_guard<std::mutex> lk(g_word_mu);
+  if (!g_word[dev]) {
+    unsigned int *p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(unsigned int)) != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
+    }
+    g_word[dev] = p;
+  }
+  return g_word[dev];
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+
+struct ext_mesh_host {
+  std::vector<int32_t> cell_verts;
+};
+
+// Edges numbered by first appearance (cells in order, local edge k joins
+// local vertices k and k+1 mod kind): sort (vertex pair, position) records,
+// take each pair's earliest position, and rank pairs by it.
+static int64_t derive_edges(int kind, int64_t ncells, const int32_t *cv, std::vector<int32_t> &ce) {
+  const int64_t n = ncells * kind;
+  std::vector<std::pair<uint64_t, int64_t>> rec((size_t)n);
+  for (int64_t c = 0; c < ncells; ++c)
+    for (int k = 0; k < kind; ++k) {
+      const uint32_t a = (uint32_t)cv[c * kind + k], b = (uint32_t)cv[c * kind + (k + 1) % kind];
+      const uint64_t key = a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
+      rec[(size_t)(c * kind + k)] = {key, c * kind + k};
+    }
+  std::sort(rec.begin(), rec.end());
+  std::vector<std::pair<int64_t, int64_t>> first;  // (earliest position, index of group start)
+  for (int64_t i = 0; i < n; ++i)
+    if (i == 0 || rec[(size_t)i].first != rec[(size_t)i - 1].first) first.push_back({rec[(size_t)i].second, i});
+  std::sort(first.begin(), first.end());
+  ce.assign((size_t)n, -1);
+  for (size_t id = 0; id < first.size(); ++id) {
+    const int64_t s = first[id].second;
+    for (int64_t j = s; j < n && rec[(size_t)j].first == rec[(size_t)s].first; ++j)
+      ce[(size_t)rec[(size_t)j].second] = (int32_t)id;
+  }
+  return (int64_t)first.size();
+}
+
+static void free_mesh(ext_mesh *m) {
+  if (!m) return;
+  cudaFree(m->d_cell_verts);
+  cudaFree(m->d_cell_edges);
+  cudaFree(m->d_base_xy);
+  delete reinterpret_cast<ext_mesh_host *>(m->host);
+  delete m;
+}
+
+extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,
+                                      const int32_t *cell_verts_host, const double *base_xy_host,
+                                      int32_t layers, ext_mesh **out) {
+  if (!out) return ext_fail(EXT_EINVAL, "ext_mesh_create: out is NULL");
+  *out = nullptr;
+  if (kind != EXT_TRI && kind != EXT_QUAD) return ext_fail(EXT_EINVAL, "ext_mesh_create: kind must be 3 or 4");
+  if (layers < 1) return ext_fail(EXT_EINVAL, "ext_mesh_create: layers must be >= 1 (got %d)", layers);
+  if (nverts < 0 || ncells < 0) return ext_fail(EXT_EINVAL, "ext_mesh_create: negative count");
+  if (nverts >= INT32_MAX || ncells * kind >= INT32_MAX)
+    return ext_fail(EXT_EOVERFLOW, "ext_mesh_create: base mesh too large for int32 indices");
+  if (ncells > 0 && !cell_verts_host) return ext_fail(EXT_EINVAL, "ext_mesh_create: cell_verts is NULL");
+  for (int64_t c = 0; c < ncells; ++c) {
+    for (int a = 0; a < kind; ++a) {
+      const int32_t v = cell_verts_host[c * kind + a];
+      if (v < 0 || v >= nverts)
+        return ext_fail(EXT_EINVAL, "ext_mesh_create: cell %lld vertex %d = %d out of range", (long long)c, a, v);
+      for (int b = 0; b < a; ++b)
+        if (cell_verts_host[c * kind + b] == v)
+          return ext_fail(EXT_EINVAL, "ext_mesh_create: cell %lld repeats vertex %d", (long long)c, v);
+    }
+    if (base_xy_host) {
+      for (int a = 0; a < kind; ++a) {
+        const int64_t p = cell_verts_host[c * kind + a];
+        const int64_t n = cell_verts_host[c * kind + (a + 1) % kind];
+        const int64_t q = cell_verts_host[c * kind + (a + kind - 1) % kind];
+        const double ux = base_xy_host[2 * n] - base_xy_host[2 * p], uy = base_xy_host[2 * n + 1] - base_xy_host[2 * p + 1];
+        const double vx = base_xy_host[2 * q] - base_xy_host[2 * p], vy = base_xy_host[2 * q + 1] - base_xy_host[2 * p + 1];
+        if (!(ux * vy - uy * vx > 0.0))
+          return ext_fail(EXT_EINVAL, "ext_mesh_create: cell %lld is clockwise, non-convex or degenerate", (long long)c);
+      }
+    }
+  }
+  std::vector<int32_t> ce;
+  const int64_t nedges = derive_edges(kind, ncells, cell_verts_host, ce);
+
+  ext_mesh *m = new ext_mesh();
+  m->kind = kind;
+  m->N[0] = nverts;
+  m->N[1] = nedges;
+  m->N[2] = ncells;
+  m->layers = layers;
+  cudaGetDevice(&m->device);
+  auto *h = new ext_mesh_host();
+  h->cell_verts.assign(cell_verts_host, cell_verts_host + ncells * kind);
+  m->host = h;
+  const size_t nb = (size_t)(ncells * kind) * sizeof(int32_t);
+  cudaError_t e = cudaSuccess;
+  if (nb) {
+    if ((e = cudaMalloc(&m->d_cell_verts, nb)) == cudaSuccess &&
+        (e = cudaMalloc(&m->d_cell_edges, nb)) == cudaSuccess &&
+        (e = cudaMemcpy(m->d_cell_verts, cell_verts_host, nb, cudaMemcpyHostToDevice)) == cudaSuccess)
+      e = cudaMemcpy(m->d_cell_edges, ce.data(), nb, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess && base_xy_host && nverts > 0) {
+    if ((e = cudaMalloc(&m->d_base_xy, (size_t)nverts * 2 * sizeof(double))) == cudaSuccess)
+      e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  m->has_xy = base_xy_host != nullptr;
+  if (e != cudaSuccess) {
+    free_mesh(m);
+    return ext_fail(e == cudaErrorMemoryAllocation ? EXT_ENOMEM : EXT_ECUDA, "ext_mesh_create: %s",
+                    cudaGetErrorString(e));
+  }
+  *out = m;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_mesh_info(const ext_mesh *mesh, int32_t *kind, int64_t n[3], int32_t *layers) {
+  if (!mesh) return ext_fail(EXT_EINVAL, "ext_mesh_info: mesh is NULL");
+  if (kind) *kind = mesh->kind;
+  if (n) for (int d = 0; d < 3; ++d) n[d] = mesh->N[d];
+  if (layers) *layers = mesh->layers;
+  return EXT_OK;
+}
+
+extern "C" void ext_mesh_destroy(ext_mesh *mesh) { free_mesh(mesh); }
+
+// ---------------------------------------------------------------------------
+// spaces
+
+static int classify(const ext_mesh *m, const int32_t d[6]) {
+  if (d[0] == 1 && d[1] == 0 && d[2] == 0 && d[3] == 0 && d[4] == 0 && d[5] == 0) return ELEM_P1P1;
+  if (d[0] == 0 && d[1] == 0 && d[2] == 0 && d[3] == 0 && d[4] == 0 && d[5] > 0) return ELEM_DGCELL;
+  if (m->kind == 4 && d[0] == 1 && d[1] == 1 && d[2] == 1 && d[3] == 1 && d[4] == 1 && d[5] == 1) return ELEM_Q2P2;
+  return ELEM_GENERIC;
+}
+
+extern "C" ext_status ext_number_dofs(ext_mesh *mesh, const int32_t delta_host[6], int32_t ncomp, void *stream,
+                                      ext_space **out) {
+  if (!out) return ext_fail(EXT_EINVAL, "ext_number_dofs: out is NULL");
+  *out = nullptr;
+  if (!mesh || !delta_host) return ext_fail(EXT_EINVAL, "ext_number_dofs: mesh or delta is NULL");
+  if (ncomp < 1 || ncomp > 3) return ext_fail(EXT_EINVAL, "ext_number_dofs: ncomp must be 1..3");
+  for (int t = 0; t < 6; ++t)
+    if (delta_host[t] < 0 || delta_host[t] > 4096) return ext_fail(EXT_EINVAL, "ext_number_dofs: delta[%d] out of range", t);
+  const int nvc = mesh->kind;
+  const int nent[3] = {nvc, nvc, 1};
+  int64_t k = 0;
+  for (int d = 0; d < 3; ++d) k += (int64_t)nent[d] * (2 * delta_host[2 * d] + delta_host[2 * d + 1]);
+  if (k == 0) return ext_fail(EXT_EINVAL, "ext_number_dofs: the space has no DoFs");
+  if (k > EXT_MAXK) return ext_fail(EXT_EUNSUPPORTED, "ext_number_dofs: stencil of %lld DoFs exceeds %d", (long long)k, EXT_MAXK);
+
+  NumberLaunch nl;
+  memset(&nl, 0, sizeof(nl));
+  const int64_t L = mesh->layers;
+  int64_t start = 0;
+  for (int d = 0; d < 3; ++d) {
+    nl.colsize[d] = L * (delta_host[2 * d] + delta_host[2 * d + 1]) + delta_host[2 * d];
+    nl.block_start[d] = start;
+    start += mesh->N[d] * nl.colsize[d];
+  }
+  const int64_t ndofs = start;
+  if (ndofs >= INT32_MAX || ndofs * ncomp >= INT32_MAX || mesh->N[2] * k >= INT32_MAX)
+    return ext_fail(EXT_EOVERFLOW, "ext_number_dofs: %lld DoFs do not fit int32 indices", (long long)ndofs);
+
+  ext_space *s = new ext_space();
+  s->mesh = mesh;
+  memcpy(s->delta, delta_host, sizeof(s->delta));
+  s->ncomp = ncomp;
+  s->k = (int32_t)k;
+  s->ndofs = ndofs;
+  s->elem = classify(mesh, delta_host);
+  s->stream = (cudaStream_t)stream;
+  int i = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int a = delta_host[2 * d], b = delta_host[2 * d + 1];
+    for (int e = 0; e < nent[d]; ++e) {
+      for (int q = 0; q < a; ++q, ++i) {  // bottom horizontal entity
+        nl.slot_dim[i] = (int8_t)d; nl.slot_ent[i] = (int8_t)e; nl.slot_add[i] = q;
+        s->h_offset[i] = a + b;
+      }
+      for (int q = 0; q < a; ++q, ++i) {  // top horizontal entity
+        nl.slot_dim[i] = (int8_t)d; nl.slot_ent[i] = (int8_t)e; nl.slot_add[i] = a + b + q;
+        s->h_offset[i] = a + b;
+      }
+      for (int q = 0; q < b; ++q, ++i) {  // vertical entity
+        nl.slot_dim[i] = (int8_t)d; nl.slot_ent[i] = (int8_t)e; nl.slot_add[i] = a + q;
+        s->h_offset[i] = a + b;
+      }
+    }
+  }
+  nl.ncells = mesh->N[2];
+  nl.nvc = nvc;
+  nl.k = (int32_t)k;
+  nl.cell_verts = mesh->d_cell_verts;
+  nl.cell_edges = mesh->d_cell_edges;
+  cudaError_t e = cudaMalloc(&s->d_offset, sizeof(int32_t) * k);
+  if (e == cudaSuccess && nl.ncells > 0) e = cudaMalloc(&s->d_map, sizeof(int32_t) * k * nl.ncells);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_offset, s->h_offset, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s->stream);
+  nl.map = s->d_map;
+  if (e == cudaSuccess) e = launch_number(nl, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_map);
+    cudaFree(s->d_offset);
+    delete s;
+    return ext_fail(e == cudaErrorMemoryAllocation ? EXT_ENOMEM : EXT_ECUDA, "ext_number_dofs: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_space_info(const ext_space *space, int64_t *ndofs, int32_t *k, int32_t *ncomp,
+                                     const int32_t **base_map_dev, const int32_t **offset_dev) {
+  if (!space) return ext_fail(EXT_EINVAL, "ext_space_info: space is NULL");
+  if (ndofs) *ndofs = space->ndofs;
+  if (k) *k = space->k;
+  if (ncomp) *ncomp = space->ncomp;
+  if (base_map_dev) *base_map_dev = space->d_map;
+  if (offset_dev) *offset_dev = space->d_offset;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_space_copy_map_to_host(const ext_space *space, int32_t *map_host, int32_t *offset_host) {
+  if (!space) return ext_fail(EXT_EINVAL, "ext_space_copy_map_to_host: space is NULL");
+  if (map_host && space->mesh->N[2] > 0)
+    EXT_CUDA(cudaMemcpy(map_host, space->d_map, sizeof(int32_t) * space->k * space->mesh->N[2], cudaMemcpyDeviceToHost),
+             "ext_space_copy_map_to_host");
+  if (offset_host) memcpy(offset_host, space->h_offset, sizeof(int32_t) * space->k);
+  return EXT_OK;
+}
+
+extern "C" void ext_space_destroy(ext_space *space) {
+  if (!space) return;
+  cudaFree(space->d_map);
+  cudaFree(space->d_offset);
+  delete space;
+}
+
+// ---------------------------------------------------------------------------
+// par_loop
+
+static ext_status check_arg(const ext_mesh *mesh, const ext_arg *args, int i, const char *kn, int elem, int ncomp,
+                            int access) {
+  const ext_arg &a = args[i];
+  if (!a.space) return ext_fail(EXT_EINVAL, "%s: argument %d has no space", kn, i);
+  if (a.space->mesh != mesh) return ext_fail(EXT_EINVAL, "%s: argument %d is on another mesh", kn, i);
+  if (!a.data && a.space->ndofs > 0) return ext_fail(EXT_EINVAL, "%s: argument %d has no data", kn, i);
+  if (elem >= 0 && a.space->elem != elem) return ext_fail(EXT_EINVAL, "%s: argument %d is on the wrong space", kn, i);
+  if (a.space->ncomp != ncomp) return ext_fail(EXT_EINVAL, "%s: argument %d must have %d values per DoF", kn, i, ncomp);
+  if (a.access != access) {
+    static const char *nm[3] = {"READ", "WRITE", "INC"};
+    return ext_fail(EXT_EINVAL, "%s: argument %d must be %s", kn, i, (access >= 0 && access < 3) ? nm[access] : "?");
+  }
+  return EXT_OK;
+}
+
+static bool same_numbering(const ext_space *a, const ext_space *b) {
+  return a->mesh == b->mesh && memcmp(a->delta, b->delta, sizeof(a->delta)) == 0;
+}
+
+#define EXT_CHECK(x)                   \
+  do {                                 \
+    ext_status st_ = (x);              \
+    if (st_ != EXT_OK) return st_;     \
+  } while (0)
+
+extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int32_t nargs, const ext_arg *args,
+                                   void *stream) {
+  if (!mesh) return ext_fail(EXT_EINVAL, "ext_par_loop: mesh is NULL");
+  if (nargs > 0 && !args) return ext_fail(EXT_EINVAL, "ext_par_loop: args is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t C = mesh->N[2];
+  const int L = mesh->layers;
+  cudaError_t e = cudaSuccess;
+  switch (kernel_id) {
+    case EXT_K_EXTRUDE: {
+      const char *kn = "EXT_K_EXTRUDE";
+      if (nargs != 1) return ext_fail(EXT_EINVAL, "%s: expects 1 argument", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_WRITE));
+      if (!mesh->has_xy) return ext_fail(EXT_EINVAL, "%s: the mesh has no base coordinates", kn);
+      ExtrudeLaunch p;
+      p.ncells = C;
+      p.nvc = mesh->kind;
+      p.layers = L;
+      p.cell_verts = mesh->d_cell_verts;
+      p.base_xy = mesh->d_base_xy;
+      p.map = args[0].space->d_map;
+      p.off = args[0].space->h_offset[0];
+      p.X = (double *)args[0].data;
+      e = launch_extrude(p, s);
+      break;
+    }
+    case EXT_K_COPY_DG: {
+      const char *kn = "EXT_K_COPY_DG";
+      if (nargs != 2) return ext_fail(EXT_EINVAL, "%s: expects 2 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_DGCELL, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_DGCELL, 1, EXT_WRITE));
+      if (!same_numbering(args[0].space, args[1].space))
+        return ext_fail(EXT_EINVAL, "%s: input and output must share one numbering", kn);
+      CopyDGLaunch p;
+      p.ncells = C;
+      p.k = args[0].space->k;
+      p.layers = L;
+      p.map = args[0].space->d_map;
+      p.in = (const double *)args[0].data;
+      p.out = (double *)args[1].data;
+      e = launch_copy_dg(p, s);
+      break;
+    }
+    case EXT_K_RHS_P1P1:
+    case EXT_K_MASS_P1P1: {
+      const char *kn = kernel_id == EXT_K_RHS_P1P1 ? "EXT_K_RHS_P1P1" : "EXT_K_MASS_P1P1";
+      if (mesh->kind != EXT_TRI) return ext_fail(EXT_EINVAL, "%s: needs a triangular base mesh", kn);
+      if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_P1P1, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 2, kn, ELEM_P1P1, 1, EXT_INC));
+      MassP1Launch p;
+      p.ncells = C;
+      p.layers = L;
+      p.cmap = args[0].space->d_map;
+      p.fmap = args[1].space->d_map;
+      p.bmap = args[2].space->d_map;
+      for (int i = 0; i < 6; ++i) {
+        p.coff[i] = args[0].space->h_offset[i];
+        p.foff[i] = args[1].space->h_offset[i];
+        p.boff[i] = args[2].space->h_offset[i];
+      }
+      p.X = (const double *)args[0].data;
+      p.f = (const double *)args[1].data;
+      p.b = (double *)args[2].data;
+      p.err = ext_device_error_word();
+      e = launch_mass_p1(p, s);
+      break;
+    }
+    case EXT_K_INTERP_DG1: {
+      const char *kn = "EXT_K_INTERP_DG1";
+      if (mesh->kind != EXT_TRI) return ext_fail(EXT_EINVAL, "%s: needs a triangular base mesh", kn);
+      if (nargs != 2) return ext_fail(EXT_EINVAL, "%s: expects 2 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_DGCELL, 1, EXT_WRITE));
+      if (args[1].space->delta[5] != 6) return ext_fail(EXT_EINVAL, "%s: output must be DG1xDG1 (delta(2,1)=6)", kn);
+      InterpDG1Launch p;
+      p.ncells = C;
+      p.layers = L;
+      p.xmap = args[0].space->d_map;
+      p.xoff = args[0].space->h_offset[0];
+      p.omap = args[1].space->d_map;
+      p.x = (const double *)args[0].data;
+      p.out = (double *)args[1].data;
+      if ((((uintptr_t)p.out) & 15) != 0) return ext_fail(EXT_EINVAL, "%s: output data must be 16-byte aligned", kn);
+      e = launch_interp_dg1(p, s);
+      break;
+    }
+    case EXT_K_U2V_FWD:
+    case EXT_K_U2V_ADJ:
+    case EXT_K_U2V_FWDADJ: {
+      const char *kn = kernel_id == EXT_K_U2V_FWD ? "EXT_K_U2V_FWD"
+                                                  : (kernel_id == EXT_K_U2V_ADJ ? "EXT_K_U2V_ADJ" : "EXT_K_U2V_FWDADJ");
+      const int mode = kernel_id == EXT_K_U2V_FWD ? 1 : (kernel_id == EXT_K_U2V_ADJ ? 2 : 3);
+      const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
+      if (nargs != want) return ext_fail(EXT_EINVAL, "%s: expects %d arguments", kn, want);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
+      const ext_space *us = args[1].space;
+      if (!us) return ext_fail(EXT_EINVAL, "%s: argument 1 has no space", kn);
+      bool dg = false;
+      if (mesh->kind == EXT_TRI) {
+        if (us->elem != ELEM_P1P1) return ext_fail(EXT_EUNSUPPORTED, "%s: prisms support CG1xCG1 only", kn);
+      } else {
+        if (us->elem == ELEM_DGCELL && us->delta[5] == 27) dg = true;
+        else if (us->elem != ELEM_Q2P2) return ext_fail(EXT_EUNSUPPORTED, "%s: hexahedra support Q2xP2 and DG2", kn);
+      }
+      const int out_access = dg ? EXT_WRITE : EXT_INC;
+      EXT_CHECK(check_arg(mesh, args, 1, kn, us->elem, 1, EXT_READ));
+      int ai = 2;
+      if (mode & 2) EXT_CHECK(check_arg(mesh, args, ai++, kn, us->elem, 1, EXT_READ));
+      const int fo = ai;
+      if (mode & 1) EXT_CHECK(check_arg(mesh, args, ai++, kn, us->elem, 1, out_access));
+      const int go = ai;
+      if (mode & 2) EXT_CHECK(check_arg(mesh, args, ai++, kn, us->elem, 1, out_access));
+      for (int j = 2; j < nargs; ++j)
+        if (!same_numbering(us, args[j].space)) return ext_fail(EXT_EINVAL, "%s: u, w, F and g must share one numbering", kn);
+      U2VLaunch p;
+      memset(&p, 0, sizeof(p));
+      p.ncells = C;
+      p.layers = L;
+      p.nvc = mesh->kind;
+      p.dg = dg;
+      p.mode = mode;
+      p.cmap = args[0].space->d_map;
+      for (int i = 0; i < 2 * mesh->kind; ++i) p.coff[i] = args[0].space->h_offset[i];
+      p.umap = us->d_map;
+      p.k = us->k;
+      for (int i = 0; i < us->k && i < 27; ++i) p.uoff[i] = us->h_offset[i];
+      p.X = (const double *)args[0].data;
+      p.u = (const double *)args[1].data;
+      p.w = (mode & 2) ? (const double *)args[2].data : nullptr;
+      p.F = (mode & 1) ? (double *)args[fo].data : nullptr;
+      p.g = (mode & 2) ? (double *)args[go].data : nullptr;
+      p.err = ext_device_error_word();
+      e = launch_u2v(p, s);
+      break;
+    }
+    default:
+      return ext_fail(EXT_EINVAL, "ext_par_loop: unknown kernel id %d", kernel_id);
+  }
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_par_loop: launch failed: %s", cudaGetErrorString(e));
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_sync_check(void *stream) {
+  EXT_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "ext_sync_check");
+  unsigned int *w = ext_device_error_word();
+  if (!w) return ext_fail(EXT_ECUDA, "ext_sync_check: no device error word");
+  unsigned int v = 0;
+  EXT_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost), "ext_sync_check");
+  if (v) EXT_CUDA(cudaMemset(w, 0, sizeof(v)), "ext_sync_check");
+  if (v & EXT_DERR_TIMEOUT) return ext_fail(EXT_ETIMEOUT, "a bounded device-side wait expired (word 0x%x)", v);
+  if (v) return ext_fail(EXT_EDEVICE, "device error word 0x%x", v);
+  return EXT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched plan
+
+struct BatchPhaseDev {
+  void *d_descs = nullptr;
+  int64_t nitems = 0;
+};
+
+struct ext_batch {
+  int nmesh = 0;
+  int mode = 0;
+  std::vector<const ext_mesh *> meshes;
+  std::vector<ext_arg> args;  // nmesh x nargs
+  int nargs = 0;
+  // colouring: per mesh, cells sorted by colour and the colour offsets
+  std::vector<int32_t *> d_cells;
+  std::vector<std::vector<int64_t>> colour_off;
+  int ncolours = 0;
+  unsigned long long *d_counter = nullptr;
+  ext_tune_params params{};
+  std::vector<BatchPhaseDev> phases;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int sms = 152;
+};
+
+static void free_phases(std::vector<BatchPhaseDev> &ph) {
+  for (auto &p : ph) cudaFree(p.d_descs);
+  ph.clear();
+}
+
+// Greedy colouring: each cell takes the smallest colour not yet used by a
+// cell sharing one of its vertices.
+static int colour_cells(const ext_mesh *m, std::vector<int32_t> &order, std::vector<int64_t> &off) {
+  const auto &cv = reinterpret_cast<const ext_mesh_host *>(m->host)->cell_verts;
+  const int64_t C = m->N[2];
+  const int k = m->kind;
+  std::vector<uint64_t> used((size_t)m->N[0], 0);
+  std::vector<int> col((size_t)C);
+  int ncol = 0;
+  for (int64_t c = 0; c < C; ++c) {
+    uint64_t mask = 0;
+    for (int a = 0; a < k; ++a) mask |= used[(size_t)cv[(size_t)(c * k + a)]];
+    int q = 0;
+    while (q < 64 && (mask >> q) & 1ull) ++q;
+    if (q >= 64) return -1;
+    col[(size_t)c] = q;
+    for (int a = 0; a < k; ++a) used[(size_t)cv[(size_t)(c * k + a)]] |= 1ull << q;
+    ncol = std::max(ncol, q + 1);
+  }
+  off.assign((size_t)ncol + 1, 0);
+  for (int64_t c = 0; c < C; ++c) off[(size_t)col[(size_t)c] + 1]++;
+  for (int q = 0; q < ncol; ++q) off[(size_t)q + 1] += off[(size_t)q];
+  order.assign((size_t)C, 0);
+  std::vector<int64_t> pos(off.begin(), off.end() - 1);
+  for (int64_t c = 0; c < C; ++c) order[(size_t)pos[(size_t)col[(size_t)c]]++] = (int32_t)c;
+  return ncol;
+}
+
+static ext_status build_phases(ext_batch *b, const ext_tune_params &tp, std::vector<BatchPhaseDev> &out) {
+  out.clear();
+  const bool colour = tp.use_atomics == 0;
+  const int nph = colour ? b->ncolours : 1;
+  const size_t dsz = batch_desc_size();
+  std::vector<unsigned char> host((size_t)b->nmesh * dsz);
+  for (int ph = 0; ph < nph; ++ph) {
+    int64_t item = 0;
+    for (int mi = 0; mi < b->nmesh; ++mi) {
+      const ext_mesh *m = b->meshes[(size_t)mi];
+      const ext_arg *a = &b->args[(size_t)mi * b->nargs];
+      int64_t ncells = m->N[2];
+      const int32_t *cells = nullptr;
+      if (colour) {
+        const auto &off = b->colour_off[(size_t)mi];
+        const int64_t lo = ph < (int)off.size() - 1 ? off[(size_t)ph] : 0;
+        const int64_t hi = ph < (int)off.size() - 1 ? off[(size_t)ph + 1] : 0;
+        ncells = hi - lo;
+        cells = b->d_cells[(size_t)mi] + lo;
+      }
+      const int tile = tp.layer_tile > 0 ? std::min(tp.layer_tile, m->layers) : m->layers;
+      const int32_t ncol_items = (int32_t)((ncells + tp.cols_per_item - 1) / tp.cols_per_item);
+      const int32_t nlay_items = (m->layers + tile - 1) / tile;
+      int ai = 2;
+      const double *w = (b->mode & 2) ? (const double *)a[ai++].data : nullptr;
+      double *F = (b->mode & 1) ? (double *)a[ai++].data : nullptr;
+      double *G = (b->mode & 2) ? (double *)a[ai++].data : nullptr;
+      batch_fill_desc(host.data(), mi, ncells, item, m->layers, ncol_items, nlay_items, cells, a[0].space->d_map,
+                      a[1].space->d_map, a[0].space->h_offset, a[1].space->h_offset, (const double *)a[0].data,
+                      (const double *)a[1].data, w, F, G);
+      item += (int64_t)ncol_items * nlay_items;
+    }
+    BatchPhaseDev pd;
+    pd.nitems = item;
+    cudaError_t e = cudaMalloc(&pd.d_descs, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(pd.d_descs, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(pd.d_descs);
+      free_phases(out);
+      return ext_fail(EXT_ENOMEM, "ext_batch: descriptor upload failed: %s", cudaGetErrorString(e));
+    }
+    out.push_back(pd);
+  }
+  return EXT_OK;
+}
+
+static cudaError_t run_phases(ext_batch *b, const std::vector<BatchPhaseDev> &ph, const ext_tune_params &tp,
+                              cudaStream_t s) {
+  const int grid = std::max(1, tp.ctas_per_sm) * b->sms;
+  for (const auto &p : ph) {
+    cudaError_t e = launch_batch_phase(p.d_descs, b->nmesh, p.nitems, b->mode, tp.use_atomics == 0, tp.cols_per_item,
+                                       tp.layer_tile, b->d_counter, tp.threads, grid, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static ext_status check_params(const ext_tune_params &tp) {
+  if (tp.cols_per_item < 1 || tp.cols_per_item > 32) return ext_fail(EXT_EINVAL, "ext_batch: cols_per_item must be 1..32");
+  if (tp.layer_tile < 0) return ext_fail(EXT_EINVAL, "ext_batch: layer_tile must be >= 0");
+  if (tp.threads != 64 && tp.threads != 128 && tp.threads != 256)
+    return ext_fail(EXT_EINVAL, "ext_batch: threads must be 64, 128 or 256");
+  if (tp.ctas_per_sm < 1 || tp.ctas_per_sm > 32) return ext_fail(EXT_EINVAL, "ext_batch: ctas_per_sm must be 1..32");
+  return EXT_OK;
+}
+
+static void destroy_batch(ext_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  free_phases(b->phases);
+  for (auto p : b->d_cells) cudaFree(p);
+  cudaFree(b->d_counter);
+  delete b;
+}
+
+static ext_status capture(ext_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaStream_t cs;
+  EXT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "ext_batch: capture stream");
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = run_phases(b, b->phases, b->params, cs);
+    e = cudaStreamEndCapture(cs, &b->graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_batch: graph capture failed: %s", cudaGetErrorString(e));
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id, int32_t nargs,
+                                       const ext_arg *args, const ext_tune_params *params, void *stream,
+                                       ext_batch **out) {
+  if (!out) return ext_fail(EXT_EINVAL, "ext_batch_create: out is NULL");
+  *out = nullptr;
+  if (nmesh < 1 || !meshes || !args) return ext_fail(EXT_EINVAL, "ext_batch_create: no meshes");
+  int mode;
+  if (kernel_id == EXT_K_U2V_FWD) mode = 1;
+  else if (kernel_id == EXT_K_U2V_ADJ) mode = 2;
+  else if (kernel_id == EXT_K_U2V_FWDADJ) mode = 3;
+  else return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: kernel %d is not batched", kernel_id);
+  const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
+  if (nargs != want) return ext_fail(EXT_EINVAL, "ext_batch_create: expects %d arguments per mesh", want);
+  for (int mi = 0; mi < nmesh; ++mi) {
+    const ext_mesh *m = meshes[mi];
+    const ext_arg *a = args + (size_t)mi * nargs;
+    if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d: prisms only", mi);
+    EXT_CHECK(check_arg(m, a, 0, "ext_batch_create", ELEM_P1P1, 3, EXT_READ));
+    for (int j = 1; j < nargs; ++j) {
+      const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);
+      EXT_CHECK(check_arg(m, a, j, "ext_batch_create", ELEM_P1P1, 1, is_out ? EXT_INC : EXT_READ));
+    }
+  }
+  if (params) EXT_CHECK(check_params(*params));
+  ext_batch *b = new ext_batch();
+  b->nmesh = nmesh;
+  b->mode = mode;
+  b->nargs = nargs;
+  b->meshes.assign(meshes, meshes + nmesh);
+  b->args.assign(args, args + (size_t)nmesh * nargs);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    destroy_batch(b);
+    return ext_fail(EXT_ENOMEM, "ext_batch_create: %s", cudaGetErrorString(e));
+  }
+  // colour classes of every mesh (used when a candidate asks for them)
+  b->d_cells.assign((size_t)nmesh, nullptr);
+  b->colour_off.resize((size_t)nmesh);
+  for (int mi = 0; mi < nmesh; ++mi) {
+    std::vector<int32_t> order;
+    const int nc = colour_cells(meshes[mi], order, b->colour_off[(size_t)mi]);
+    if (nc < 0) {
+      destroy_batch(b);
+      return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d needs more than 64 colours", mi);
+    }
+    b->ncolours = std::max(b->ncolours, nc);
+    if (!order.empty()) {
+      e = cudaMalloc(&b->d_cells[(size_t)mi], order.size() * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_cells[(size_t)mi], order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        destroy_batch(b);
+        return ext_fail(EXT_ENOMEM, "ext_batch_create: %s", cudaGetErrorString(e));
+      }
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params) {
+    b->params = *params;
+  } else {
+    // autotune: time each candidate once after one warm-up launch
+    std::vector<ext_tune_params> cand;
+    const int cpis[] = {1, 2, 4, 8};
+    const int tiles[] = {0, 32};
+    for (int use_atomics = 1; use_atomics >= 0; --use_atomics)
+      for (int cpi : cpis)
+        for (int t : tiles) {
+          if (!use_atomics && cpi < 8) continue;  // colour phases need many columns per item
+          ext_tune_params tp;
+          tp.cols_per_item = use_atomics ? cpi : 32;
+          tp.layer_tile = t;
+          tp.use_atomics = use_atomics;
+          tp.threads = 256;
+          tp.ctas_per_sm = 4;
+          cand.push_back(tp);
+        }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (const auto &tp : cand) {
+      std::vector<BatchPhaseDev> ph;
+      if (build_phases(b, tp, ph) != EXT_OK) continue;
+      cudaError_t le = run_phases(b, ph, tp, s);
+      le = le == cudaSuccess ? cudaEventRecord(e0, s) : le;
+      le = le == cudaSuccess ? run_phases(b, ph, tp, s) : le;
+      le = le == cudaSuccess ? cudaEventRecord(e1, s) : le;
+      le = le == cudaSuccess ? cudaEventSynchronize(e1) : le;
+      float ms = 1e30f;
+      if (le == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      free_phases(ph);
+      if (le != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        destroy_batch(b);
+        return ext_fail(EXT_ECUDA, "ext_batch_create: autotune launch failed: %s", cudaGetErrorString(le));
+      }
+      if (ms < best) {
+        best = ms;
+        b->params = tp;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  ext_status st = build_phases(b, b->params, b->phases);
+  if (st == EXT_OK) st = capture(b);
+  if (st != EXT_OK) {
+    destroy_batch(b);
+    return st;
+  }
+  *out = b;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_launch(ext_batch *batch, void *stream) {
+  if (!batch || !batch->exec) return ext_fail(EXT_EINVAL, "ext_batch_launch: invalid batch");
+  EXT_CUDA(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "ext_batch_launch");
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_launch_params(ext_batch *batch, const ext_tune_params *params, void *stream) {
+  if (!batch || !params) return ext_fail(EXT_EINVAL, "ext_batch_launch_params: invalid arguments");
+  EXT_CHECK(check_params(*params));
+  std::vector<BatchPhaseDev> ph;
+  EXT_CHECK(build_phases(batch, *params, ph));
+  cudaError_t e = run_phases(batch, ph, *params, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  free_phases(ph);
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_batch_launch_params: %s", cudaGetErrorString(e));
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_params(const ext_batch *batch, ext_tune_params *out) {
+  if (!batch || !out) return ext_fail(EXT_EINVAL, "ext_batch_params: invalid arguments");
+  *out = batch->params;
+  return EXT_OK;
+}
+
+extern "C" void ext_batch_destroy(ext_batch *batch) { destroy_batch(batch); }

@@ -1,0 +1,149 @@
+// Internal declarations of the extmesh CUDA library (not installed; the public
+// ABI is include/extmesh.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/extmesh.h"
+
+#define EXT_MAXK 64  // longest stencil handled (Q2/DG2 hexahedra use 27)
+
+// Bits of the device error word (ext_sync_check maps them to statuses).
+enum : unsigned int {
+  EXT_DERR_TIMEOUT = 1u,   // a bounded spin-wait gave up
+  EXT_DERR_BOUNDS = 2u,    // an index failed a device-side range check
+  EXT_DERR_INPUT = 4u      // an input a kernel cannot handle (e.g. bad map row)
+};
+
+// Element recognised from a space's delta table.
+enum ElemKind : int {
+  ELEM_GENERIC = 0,
+  ELEM_P1P1 = 1,    // delta(0,0)=1 only: CG1 x CG1 (coordinates when ncomp=3)
+  ELEM_DGCELL = 2,  // only delta(2,1) > 0: every DoF interior to the cell
+  ELEM_Q2P2 = 3,    // all six deltas 1 on quadrilateral base: Q2 x P2
+};
+
+struct ext_mesh {
+  int32_t kind;        // vertices per base cell (3 or 4)
+  int64_t N[3];        // base entity counts: vertices, edges, cells
+  int32_t layers;      // lambda
+  int device;
+  int32_t *d_cell_verts = nullptr;  // ncells x kind
+  int32_t *d_cell_edges = nullptr;  // ncells x kind
+  double *d_base_xy = nullptr;      // nverts x 2 (may be null)
+  bool has_xy = false;              // base coordinates were given
+  void *host = nullptr;             // host-side copies (ext_api.cu)
+};
+
+struct ext_space {
+  const ext_mesh *mesh;
+  int32_t delta[6];
+  int32_t ncomp;
+  int32_t k;
+  int64_t ndofs;
+  int32_t *d_map = nullptr;     // ncells x k
+  int32_t *d_offset = nullptr;  // k
+  int32_t h_offset[EXT_MAXK];
+  int elem;
+  cudaStream_t stream;  // creation stream (map ready after it)
+};
+
+// ---------------------------------------------------------------------------
+// error reporting (ext_api.cu)
+ext_status ext_fail(ext_status st, const char *fmt, ...);
+unsigned int *ext_device_error_word();  // per-device word, allocated lazily
+
+// ---------------------------------------------------------------------------
+// kernel launchers; each returns cudaGetLastError() after the launch.
+
+// Closed-form Algorithm 1 / Algorithm 2 for one space (k_number.cu).
+struct NumberLaunch {
+  int64_t ncells;
+  int32_t nvc, k;
+  int64_t block_start[3];  // first number of dimension-d entities
+  int64_t colsize[3];      // numbers per column of a dimension-d entity
+  int8_t slot_dim[EXT_MAXK];
+  int8_t slot_ent[EXT_MAXK];
+  int32_t slot_add[EXT_MAXK];  // position inside the column at layer 0
+  const int32_t *cell_verts, *cell_edges;
+  int32_t *map;
+};
+cudaError_t launch_number(const NumberLaunch &p, cudaStream_t s);
+
+struct ExtrudeLaunch {
+  int64_t ncells;
+  int32_t nvc, layers;
+  const int32_t *cell_verts;
+  const double *base_xy;
+  const int32_t *map;  // coords space, k = 2 nvc
+  int32_t off;         // vertical offset of every slot (1 for CG1xCG1)
+  double *X;
+};
+cudaError_t launch_extrude(const ExtrudeLaunch &p, cudaStream_t s);
+
+// DG copy and DG1 interpolation (k_dg.cu).
+struct CopyDGLaunch {
+  int64_t ncells;
+  int32_t k, layers;
+  const int32_t *map;
+  const double *in;
+  double *out;
+};
+cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s);
+
+struct InterpDG1Launch {
+  int64_t ncells;
+  int32_t layers;
+  const int32_t *xmap;  // CG1xCG1 map, k = 6
+  int32_t xoff;         // vertical offset of every slot (Algorithm 2: 1 for CG1xCG1)
+  const int32_t *omap;  // DG1xDG1 map, k = 6
+  const double *x;
+  double *out;
+};
+cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s);
+
+// P1 x P1 prism mass action / RHS (k_p1.cu).
+struct MassP1Launch {
+  int64_t ncells;
+  int32_t layers;
+  const int32_t *cmap, *fmap, *bmap;  // coords, input, output maps (k = 6)
+  int32_t coff[6], foff[6], boff[6];
+  const double *X, *f;
+  double *b;
+  unsigned int *err;
+};
+cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
+
+// u^2 v residual and adjoint (k_u2v.cu): prisms (P1 x P1) and hexahedra (Q2 x P2, DG2).
+struct U2VLaunch {
+  int64_t ncells;
+  int32_t layers;
+  int32_t nvc;         // 3: prism P1xP1, 4: hexahedron Q2/DG2
+  int32_t dg;          // outputs WRITE (DG2) instead of INC
+  int32_t mode;        // bit 0: forward F, bit 1: adjoint g
+  const int32_t *cmap; // coords map (k = 2 nvc)
+  int32_t coff[8];
+  const int32_t *umap; // u/w/F/g map (same space)
+  int32_t uoff[27];
+  int32_t k;
+  const double *X, *u, *w;
+  double *F, *g;
+  unsigned int *err;
+};
+cudaError_t launch_u2v(const U2VLaunch &p, cudaStream_t s);
+
+// Batched persistent u^2 v on prisms (k_batch.cu).  Descriptors are opaque
+// to the host code: batch_fill_desc writes one into a host array of
+// nmesh * batch_desc_size() bytes, which is then copied to the device.
+size_t batch_desc_size();
+void batch_fill_desc(void *host_descs, int mi, int64_t ncells, int64_t item_begin, int32_t layers,
+                     int32_t ncol_items, int32_t nlay_items, const int32_t *cells, const int32_t *cmap,
+                     const int32_t *umap, const int32_t coff[6], const int32_t uoff[6], const double *X,
+                     const double *u, const double *w, double *F, double *G);
+cudaError_t launch_batch_phase(const void *d_descs, int nmesh, int64_t nitems, int mode, bool colour,
+                               int cpi, int lt, unsigned long long *counter, int threads, int grid,
+                               cudaStream_t s);

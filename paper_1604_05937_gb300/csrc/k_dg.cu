@@ -1,0 +1,138 @@
+// Streaming par_loops over spaces with cell-interior DoFs only: the DG copy
+// and the P1xP1 -> DG1xDG1 nodal interpolation.  Neither does floating-point
+// arithmetic; both are bound by HBM bandwidth.
+//
+// For a space whose DoFs all sit on the cells (delta(2,1) = k, every other
+// delta 0), Algorithm 1 gives cell c's column the k*layers consecutive
+// numbers starting at base_map[c][0], and base_map[c][j] = base_map[c][0] + j
+// with offset k, so Algorithm 3's direct addressing base_map[c][j] + l*k
+// walks that range in order (t = l*k + j).  The kernels flatten (cell, layer,
+// stencil slot) into one index so that consecutive threads touch consecutive
+// DoFs and move 16 bytes each.
+#include "ext_internal.cuh"
+#include "fastdiv.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+__device__ __forceinline__ double2 ld_stream2(const double *p) {
+  return __ldcs(reinterpret_cast<const double2 *>(p));
+}
+__device__ __forceinline__ void st_stream2(double *p, double2 v) {
+  __stcs(reinterpret_cast<double2 *>(p), v);
+}
+
+// out = in over the columns of a cell-interior space.  `pairs` 16-byte pairs
+// when the column length is even, single values otherwise.
+__global__ void __launch_bounds__(kThreads) k_copy_dg_vec(const CopyDGLaunch p, FastDiv col,
+                                                          uint32_t npairs) {
+  const uint32_t stride = gridDim.x * kThreads;
+  uint32_t v = blockIdx.x * kThreads + threadIdx.x;
+  for (; v < npairs; v += kUnroll * stride) {
+    double2 val[kUnroll];
+    uint32_t dst[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t vv = v + u * stride;
+      if (vv < npairs) {
+        const uint32_t t = 2u * vv;
+        const uint32_t c = fdiv(t, col);
+        const uint32_t r = t - c * col.d;
+        const uint32_t base = (uint32_t)__ldg(p.map + (int64_t)c * p.k);
+        dst[u] = base + r;
+        val[u] = ld_stream2(p.in + dst[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t vv = v + u * stride;
+      if (vv < npairs) st_stream2(p.out + dst[u], val[u]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_copy_dg_scalar(const CopyDGLaunch p, FastDiv col,
+                                                             uint32_t n) {
+  const uint32_t stride = gridDim.x * kThreads;
+  for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n; t += stride) {
+    const uint32_t c = fdiv(t, col);
+    const uint32_t r = t - c * col.d;
+    const uint32_t base = (uint32_t)__ldg(p.map + (int64_t)c * p.k);
+    __stcs(p.out + base + r, __ldcs(p.in + base + r));
+  }
+}
+
+// out(DG1xDG1 node 2a+b of cell c, layer l) = x(vertex a, level l+b).  Pair
+// index v covers slots (2a, 2a+1) of one layer: t = 2v = c*6L + 6l + 2a.  The
+// P1xP1 DoFs are x_map[c][2a] + l*offset (bottom) and x_map[c][2a+1] +
+// l*offset (top), reached by direct addressing as in Algorithm 3 (every slot
+// of a CG1xCG1 stencil has the same offset, delta(0,0) = 1).
+__global__ void __launch_bounds__(kThreads) k_interp_dg1(const InterpDG1Launch p, FastDiv col,
+                                                         FastDiv six, uint32_t npairs) {
+  const uint32_t stride = gridDim.x * kThreads;
+  uint32_t v = blockIdx.x * kThreads + threadIdx.x;
+  for (; v < npairs; v += kUnroll * stride) {
+    double2 val[kUnroll];
+    uint32_t dst[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t vv = v + u * stride;
+      if (vv < npairs) {
+        const uint32_t t = 2u * vv;
+        const uint32_t c = fdiv(t, col);
+        const uint32_t r = t - c * col.d;
+        const uint32_t l = fdiv(r, six);
+        const uint32_t j = r - 6u * l;  // 0, 2 or 4
+        const int32_t *xm = p.xmap + (int64_t)c * 6;
+        const int2 xb = __ldg(reinterpret_cast<const int2 *>(xm + j));
+        const int ob = __ldg(p.omap + (int64_t)c * 6);
+        const double lo = __ldg(p.x + (uint32_t)xb.x + l * (uint32_t)p.xoff);
+        const double hi = __ldg(p.x + (uint32_t)xb.y + l * (uint32_t)p.xoff);
+        val[u] = make_double2(lo, hi);
+        dst[u] = (uint32_t)ob + r;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t vv = v + u * stride;
+      if (vv < npairs) st_stream2(p.out + dst[u], val[u]);
+    }
+  }
+}
+
+unsigned grid_for(uint64_t work, int per_thread) {
+  uint64_t blocks = (work + (uint64_t)kThreads * per_thread - 1) / ((uint64_t)kThreads * per_thread);
+  const uint64_t cap = 152ull * 16;  // 16 resident CTAs per SM is plenty for a stream
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  return (unsigned)blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s) {
+  const uint64_t colsize = (uint64_t)p.k * p.layers;
+  const uint64_t n = colsize * (uint64_t)p.ncells;
+  if (n == 0) return cudaSuccess;
+  const FastDiv col = make_fastdiv((uint32_t)colsize);
+  const bool aligned = ((((uintptr_t)p.in) | ((uintptr_t)p.out)) & 15) == 0;
+  if (colsize % 2 == 0 && aligned) {
+    const uint32_t npairs = (uint32_t)(n / 2);
+    k_copy_dg_vec<<<grid_for(npairs, kUnroll), kThreads, 0, s>>>(p, col, npairs);
+  } else {
+    k_copy_dg_scalar<<<grid_for(n, 4), kThreads, 0, s>>>(p, col, (uint32_t)n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s) {
+  const uint64_t colsize = 6ull * p.layers;
+  const uint64_t n = colsize * (uint64_t)p.ncells;
+  if (n == 0) return cudaSuccess;
+  const uint32_t npairs = (uint32_t)(n / 2);
+  k_interp_dg1<<<grid_for(npairs, kUnroll), kThreads, 0, s>>>(p, make_fastdiv((uint32_t)colsize),
+                                                              make_fastdiv(6u), npairs);
+  return cudaGetLastError();
+}

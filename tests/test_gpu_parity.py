@@ -1,0 +1,353 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same
+seeded inputs: numbering and maps bit-exact, data moves bit-exact, FP64
+assembly within 1e-12 of the oracle's absolute contribution sums A_i
+(|y_i - y_i^oracle| <= 1e-12 * A_i + 1e-300, which allows any summation
+order, FMA contraction and atomic ordering)."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1604_05937_gb300 as E  # noqa: E402
+
+RTOL = 1e-12
+dev = torch.device("cuda:0")
+
+
+def close(got, want, absref, rtol=RTOL):
+    got = np.asarray(got)
+    err = np.abs(got - want)
+    bound = rtol * absref + 1e-300
+    bad = np.nonzero(~(err <= bound))[0]
+    assert bad.size == 0, (f"{bad.size} entries off; worst rel "
+                           f"{(err / (absref + 1e-300)).max():.3e} at {bad[:5]}")
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def mesh_pair(m, layers):
+    """(GPU Mesh, oracle coords space, oracle coords) for a base mesh."""
+    gm = E.Mesh(m.cells, m.xy, layers)
+    csp, X = O.coords(m.cells, m.xy, layers)
+    return gm, csp, X
+
+
+TRI_SPACES = ["CG1xCG1", "CG1xDG0", "CG1xDG1", "DG0xCG1", "DG0xDG0", "DG0xDG1", "DG1xCG1", "DG1xDG0",
+              "DG1xDG1"]
+
+
+# ------------------------------------------------------------------ numbering
+@pytest.mark.parametrize("name", TRI_SPACES + ["ALL1"])
+@pytest.mark.parametrize("n,layers,order", [(3, 1, "rcm"), (7, 5, "random"), (13, 33, "rcm")])
+def test_numbering_bit_exact_prisms(name, n, layers, order):
+    m = meshgen.tri_mesh(n, seed=100 + n, order=order)
+    delta = (1, 1, 1, 1, 1, 1) if name == "ALL1" else O.DELTA[name]
+    gm = E.Mesh(m.cells, m.xy, layers)
+    gs = E.Space(gm, delta)
+    osp = O.number(m.cells, m.nverts, layers, delta)
+    gmap, goff = gs.stencil_map()
+    assert gs.ndofs == osp.ndofs and gs.k == osp.k
+    np.testing.assert_array_equal(gmap, osp.map)
+    np.testing.assert_array_equal(goff, osp.offset)
+
+
+@pytest.mark.parametrize("name", ["Q2xP2", "DG2hex", "CG1xCG1"])
+@pytest.mark.parametrize("n,layers", [(2, 1), (5, 7), (9, 40)])
+def test_numbering_bit_exact_hexes(name, n, layers):
+    m = meshgen.quad_mesh(n, seed=200 + n, order="random")
+    gm = E.Mesh(m.cells, m.xy, layers)
+    gs = E.Space(gm, O.DELTA[name])
+    osp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    gmap, goff = gs.stencil_map()
+    assert gs.ndofs == osp.ndofs
+    np.testing.assert_array_equal(gmap, osp.map)
+    np.testing.assert_array_equal(goff, osp.offset)
+    assert gm.N[1] == O.derive_edges(m.cells, m.nverts)[1]
+
+
+@pytest.mark.parametrize("kind", [3, 4])
+def test_extrusion_bit_exact(kind):
+    layers = 11
+    m = meshgen.tri_mesh(9, seed=5, order="random") if kind == 3 else meshgen.quad_mesh(8, seed=5)
+    gm, csp, X = mesh_pair(m, layers)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    Xg = E.extrude_coords(gm, cs)
+    np.testing.assert_array_equal(host(Xg), X)
+
+
+# ------------------------------------------------------------------ moves
+@pytest.mark.parametrize("name", ["DG0xDG0", "DG1xDG1", "DG1xDG0"])
+@pytest.mark.parametrize("layers", [1, 7, 64])
+def test_dg_copy_bit_exact(name, layers):
+    m = meshgen.tri_mesh(10, seed=7, order="random")
+    gm = E.Mesh(m.cells, m.xy, layers)
+    gs = E.Space(gm, O.DELTA[name])
+    a = meshgen.uniform_field(gs.ndofs, 8)
+    out = torch.full((gs.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_COPY_DG, (gs, to_dev(a), E.EXT_READ), (gs, out, E.EXT_WRITE))
+    osp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    ref = np.full(osp.ndofs, np.nan)
+    O.par_loop(O.K_COPY, m.cells, layers, [(osp, a, 1, O.READ), (osp, ref, 1, O.WRITE)])
+    np.testing.assert_array_equal(host(out), ref)
+
+
+@pytest.mark.parametrize("layers", [1, 5, 32, 100])
+def test_dg1_interpolation_bit_exact(layers):
+    m = meshgen.tri_mesh(12, seed=9, order="random")
+    gm = E.Mesh(m.cells, m.xy, layers)
+    p1 = E.Space(gm, "CG1xCG1")
+    dg = E.Space(gm, "DG1xDG1")
+    x = meshgen.uniform_field(p1.ndofs, 10)
+    out = torch.full((dg.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_INTERP_DG1, (p1, to_dev(x), E.EXT_READ), (dg, out, E.EXT_WRITE))
+    op1 = O.number(m.cells, m.nverts, layers, P1)
+    odg = O.number(m.cells, m.nverts, layers, O.DELTA["DG1xDG1"])
+    ref = np.full(odg.ndofs, np.nan)
+    O.par_loop(O.K_INTERP, m.cells, layers, [(op1, x, 1, O.READ), (odg, ref, 1, O.WRITE)])
+    np.testing.assert_array_equal(host(out), ref)
+
+
+P1 = O.DELTA["CG1xCG1"]
+
+
+# ------------------------------------------------------------------ P1xP1 mass / RHS
+def _mass_case(m, layers, f_of_X=None, seed=1, perturb=0.0, kernel=None):
+    gm, csp, X = mesh_pair(m, layers)
+    if perturb:
+        rng = np.random.default_rng(seed + 99)
+        X = X + perturb * rng.uniform(-1, 1, X.size) / (m.n * max(layers, 1))
+    osp = O.number(m.cells, m.nverts, layers, P1)
+    Xr = X.reshape(-1, 3)
+    f = f_of_X(Xr) if f_of_X is not None else meshgen.uniform_field(osp.ndofs, seed)
+    ref = np.zeros(osp.ndofs)
+    absr = np.zeros(osp.ndofs)
+    O.par_loop(O.K_MASS, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    ps = E.Space(gm, "CG1xCG1")
+    b = ps.zeros()
+    k = kernel if kernel is not None else E.EXT_K_MASS_P1P1
+    E.par_loop(gm, k, (cs, to_dev(X), E.EXT_READ), (ps, to_dev(f), E.EXT_READ), (ps, b, E.EXT_INC))
+    E.ext_sync_check()
+    return host(b), ref, absr
+
+
+@pytest.mark.parametrize("n,layers,order", [(4, 1, "rcm"), (9, 3, "random"), (17, 31, "rcm"), (23, 32, "random"),
+                                            (11, 100, "rcm"), (6, 257, "rcm")])
+def test_mass_action_parity(n, layers, order):
+    m = meshgen.tri_mesh(n, seed=300 + n, order=order)
+    got, ref, absr = _mass_case(m, layers)
+    close(got, ref, absr)
+
+
+def test_rhs_sin_cos_z_parity():
+    m = meshgen.tri_mesh(30, seed=1604, order="rcm")  # the 1,800-triangle, 10-layer case
+    f = lambda X: np.sin(X[:, 0]) * np.cos(X[:, 1]) * X[:, 2]
+    got, ref, absr = _mass_case(m, 10, f_of_X=f, kernel=E.EXT_K_RHS_P1P1)
+    close(got, ref, absr)
+    assert abs(got.sum() - ref.sum()) < 1e-14
+
+
+def test_mass_general_geometry_fallback():
+    """Perturbed (non-straight) coordinates take the full-quadrature path."""
+    m = meshgen.tri_mesh(8, seed=41, order="random")
+    got, ref, absr = _mass_case(m, 9, perturb=0.05)
+    close(got, ref, absr)
+
+
+def test_mass_volume_pin_on_gpu():
+    m = meshgen.tri_mesh(20, seed=42)
+    got, ref, absr = _mass_case(m, 13, f_of_X=lambda X: np.ones(X.shape[0]))
+    assert abs(got.sum() - 1.0) < 1e-13
+
+
+# ------------------------------------------------------------------ u^2 v and adjoint
+def _u2v_case(m, layers, delta, mode, perturb=0.0, seed=3):
+    gm, csp, X = mesh_pair(m, layers)
+    if perturb:
+        rng = np.random.default_rng(seed + 7)
+        X = X + perturb * rng.uniform(-1, 1, X.size) / (m.n * layers)
+    osp = O.number(m.cells, m.nverts, layers, delta)
+    dg = delta == O.DELTA["DG2hex"]
+    acc = O.WRITE if dg else O.INC
+    u = meshgen.uniform_field(osp.ndofs, seed)
+    w = meshgen.uniform_field(osp.ndofs, seed + 1)
+    F = np.zeros(osp.ndofs); aF = np.zeros(osp.ndofs)
+    G = np.zeros(osp.ndofs); aG = np.zeros(osp.ndofs)
+    O.par_loop(O.K_U2V, m.cells, layers, [(csp, X, 3, O.READ), (osp, u, 1, O.READ), (osp, F, 1, acc, aF)])
+    O.par_loop(O.K_U2V_ADJ, m.cells, layers,
+               [(csp, X, 3, O.READ), (osp, u, 1, O.READ), (osp, w, 1, O.READ), (osp, G, 1, acc, aG)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    sp = E.Space(gm, delta)
+    Xd, ud, wd = to_dev(X), to_dev(u), to_dev(w)
+    gacc = E.EXT_WRITE if dg else E.EXT_INC
+    Fg = sp.zeros(); Gg = sp.zeros()
+    if mode == "separate":
+        E.par_loop(gm, E.EXT_K_U2V_FWD, (cs, Xd, E.EXT_READ), (sp, ud, E.EXT_READ), (sp, Fg, gacc))
+        E.par_loop(gm, E.EXT_K_U2V_ADJ, (cs, Xd, E.EXT_READ), (sp, ud, E.EXT_READ), (sp, wd, E.EXT_READ),
+                   (sp, Gg, gacc))
+    else:
+        E.par_loop(gm, E.EXT_K_U2V_FWDADJ, (cs, Xd, E.EXT_READ), (sp, ud, E.EXT_READ), (sp, wd, E.EXT_READ),
+                   (sp, Fg, gacc), (sp, Gg, gacc))
+    E.ext_sync_check()
+    close(host(Fg), F, aF)
+    close(host(Gg), G, aG)
+
+
+@pytest.mark.parametrize("mode", ["separate", "fused"])
+@pytest.mark.parametrize("n,layers", [(5, 1), (9, 7), (13, 40)])
+def test_u2v_prism_parity(mode, n, layers):
+    _u2v_case(meshgen.tri_mesh(n, seed=400 + n, order="random"), layers, P1, mode)
+
+
+@pytest.mark.parametrize("name", ["Q2xP2", "DG2hex"])
+@pytest.mark.parametrize("mode", ["separate", "fused"])
+@pytest.mark.parametrize("n,layers", [(3, 1), (6, 5), (9, 33)])
+def test_u2v_hex_parity(name, mode, n, layers):
+    _u2v_case(meshgen.quad_mesh(n, seed=500 + n, order="random"), layers, O.DELTA[name], mode)
+
+
+@pytest.mark.parametrize("kind,delta", [(3, P1), (4, O.DELTA["Q2xP2"]), (4, O.DELTA["DG2hex"])])
+def test_u2v_general_geometry_fallback(kind, delta):
+    m = meshgen.tri_mesh(6, seed=61) if kind == 3 else meshgen.quad_mesh(4, seed=61)
+    _u2v_case(m, 4, delta, "fused", perturb=0.05)
+
+
+def test_residual_autograd_gradcheck():
+    m = meshgen.quad_mesh(2, seed=71)
+    layers = 2
+    gm = E.Mesh(m.cells, m.xy, layers)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    X = E.extrude_coords(gm, cs)
+    sp = E.Space(gm, "Q2xP2")
+    Fn = E.ResidualFn()
+    u = torch.tensor(meshgen.uniform_field(sp.ndofs, 72), device=dev, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda v: Fn.apply(v, gm, cs, X, sp), (u,), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+def test_residual_adjoint_matches_finite_differences():
+    m = meshgen.tri_mesh(10, seed=73, order="random")
+    layers = 8
+    gm = E.Mesh(m.cells, m.xy, layers)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    X = E.extrude_coords(gm, cs)
+    sp = E.Space(gm, "CG1xCG1")
+    u = to_dev(meshgen.uniform_field(sp.ndofs, 74))
+    w = to_dev(meshgen.uniform_field(sp.ndofs, 75))
+    d = to_dev(meshgen.uniform_field(sp.ndofs, 76))
+    g = E.residual_u2v_adjoint(gm, cs, X, sp, u, w)
+    h = 1e-6
+    jd = (E.residual_u2v(gm, cs, X, sp, u + h * d) - E.residual_u2v(gm, cs, X, sp, u - h * d)) / (2 * h)
+    lhs, rhs = float(w @ jd), float(g @ d)
+    assert abs(lhs - rhs) <= 1e-8 * float(w.abs() @ jd.abs())
+    # Euler identity: F homogeneous of degree 2
+    F = E.residual_u2v(gm, cs, X, sp, u)
+    assert abs(float(g @ u) - 2 * float(w @ F)) <= 1e-12 * float(g.abs() @ u.abs())
+
+
+# ------------------------------------------------------------------ batched
+def _batch_case(params, count=5, mode=E.EXT_K_U2V_FWDADJ):
+    bp = meshgen.batched_params(count=count, seed=1700, cmin=50, cmax=3000, lmin=1, lmax=40)
+    meshes, per, refs, keep = [], [], [], []
+    for i, (n, L) in enumerate(zip(bp.n, bp.layers)):
+        m = meshgen.tri_mesh(n, seed=1800 + i, order="rcm" if i % 2 else "random")
+        gm, csp, X = mesh_pair(m, L)
+        osp = O.number(m.cells, m.nverts, L, P1)
+        u = meshgen.uniform_field(osp.ndofs, 1900 + i)
+        w = meshgen.uniform_field(osp.ndofs, 2000 + i)
+        F = np.zeros(osp.ndofs); aF = np.zeros(osp.ndofs)
+        G = np.zeros(osp.ndofs); aG = np.zeros(osp.ndofs)
+        O.par_loop(O.K_U2V, m.cells, L, [(csp, X, 3, O.READ), (osp, u, 1, O.READ), (osp, F, 1, O.INC, aF)])
+        O.par_loop(O.K_U2V_ADJ, m.cells, L, [(csp, X, 3, O.READ), (osp, u, 1, O.READ), (osp, w, 1, O.READ),
+                                             (osp, G, 1, O.INC, aG)])
+        cs = E.Space(gm, "CG1xCG1", ncomp=3)
+        sp = E.Space(gm, "CG1xCG1")
+        Fg, Gg = sp.zeros(), sp.zeros()
+        args = [(cs, to_dev(X), E.EXT_READ), (sp, to_dev(u), E.EXT_READ), (sp, to_dev(w), E.EXT_READ),
+                (sp, Fg, E.EXT_INC), (sp, Gg, E.EXT_INC)]
+        meshes.append(gm)
+        per.append(args)
+        refs.append((F, aF, G, aG, Fg, Gg))
+        keep.append((cs, sp))
+    b = E.Batch(meshes, mode, per, params=params)
+    for (_, _, _, _, Fg, Gg) in refs:  # autotuning/capture leaves partial sums behind
+        Fg.zero_()
+        Gg.zero_()
+    b.launch()
+    E.ext_sync_check()
+    for (F, aF, G, aG, Fg, Gg) in refs:
+        close(host(Fg), F, aF)
+        close(host(Gg), G, aG)
+    return b
+
+
+@pytest.mark.parametrize("params", [
+    dict(cols_per_item=1, layer_tile=0, use_atomics=1, threads=256, ctas_per_sm=2),
+    dict(cols_per_item=4, layer_tile=8, use_atomics=1, threads=128, ctas_per_sm=4),
+    dict(cols_per_item=32, layer_tile=0, use_atomics=0, threads=256, ctas_per_sm=2),
+    dict(cols_per_item=16, layer_tile=5, use_atomics=0, threads=64, ctas_per_sm=8),
+])
+def test_batched_parity_explicit_params(params):
+    b = _batch_case(params)
+    assert b.params == params
+
+
+def test_batched_parity_autotuned_and_replayed():
+    b = _batch_case(None)
+    p = b.params
+    assert p["cols_per_item"] >= 1 and p["threads"] in (64, 128, 256)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_mesh_and_single_cell():
+    cells = np.zeros((0, 3), dtype=np.int32)
+    gm = E.Mesh(cells, np.zeros((0, 2)), 3, )
+    sp = E.Space(gm, "DG0xDG0")
+    assert sp.ndofs == 0
+    cells = np.array([[0, 1, 2]], dtype=np.int32)
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    gm = E.Mesh(cells, xy, 1)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    X = E.extrude_coords(gm, cs)
+    ps = E.Space(gm, "CG1xCG1")
+    b = ps.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (ps, torch.ones(ps.ndofs, dtype=torch.float64, device=dev),
+                                                             E.EXT_READ), (ps, b, E.EXT_INC))
+    assert abs(float(b.sum()) - 0.5) < 1e-15
+
+
+def test_argument_validation():
+    m = meshgen.tri_mesh(3, seed=1)
+    gm = E.Mesh(m.cells, m.xy, 2)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    ps = E.Space(gm, "CG1xCG1")
+    dg = E.Space(gm, "DG0xDG0")
+    X = E.extrude_coords(gm, cs)
+    b = ps.zeros()
+    with pytest.raises(E.ExtError, match="EXT_EINVAL"):
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (ps, b, E.EXT_READ), (ps, b, E.EXT_WRITE))
+    with pytest.raises(E.ExtError, match="wrong space"):
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (dg, dg.zeros(), E.EXT_READ), (ps, b, E.EXT_INC))
+    with pytest.raises(E.ExtError, match="unknown kernel"):
+        E.ext_par_loop(gm.handle, 99, [])
+    other = E.Mesh(m.cells, m.xy, 3)
+    os_ = E.Space(other, "CG1xCG1")
+    with pytest.raises(E.ExtError, match="another mesh"):
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (os_, os_.zeros(), E.EXT_READ), (ps, b, E.EXT_INC))
+    deep = E.Mesh(np.array([[0, 1, 2]], dtype=np.int32), np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]),
+                  100_000_000)
+    with pytest.raises(E.ExtError, match="EXT_EOVERFLOW"):
+        E.Space(deep, (0, 0, 0, 0, 0, 27))  # 2.7e9 DoFs do not fit int32
