@@ -213,6 +213,33 @@ ext_status ext_batch_params(const ext_batch *batch, ext_tune_params *out);
 
 void ext_batch_destroy(ext_batch *batch);
 
+/* Batched launch for callers that cannot allocate device memory (the paper
+ * has no counterpart; this is a deployment variant of ext_batch_launch).
+ * Some callers cannot call cudaMalloc: code running under a device-memory
+ * budget owned by someone else (a framework's caching allocator that has
+ * reserved the device, or a service that forbids allocation after start-up),
+ * and latency-sensitive loops that cannot take cudaMalloc's implicit device
+ * synchronisation.  This entry point runs the batched u^2 v work-queue kernel
+ * (FP64-atomic form only) directly, without a plan, and allocates nothing:
+ * its scratch (work counter and per-mesh descriptors) lives in a 64 KiB
+ * static device array of the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   nmesh <= EXT_NOALLOC_MAX_MESHES; larger batches fail with EXT_EINVAL.
+ *   args, kernels and argument rules: as ext_batch_create.  INC outputs are
+ *   added to; the caller zeroes them.
+ *   params NULL = {cols_per_item 4, layer_tile 0, use_atomics 1, threads 256,
+ *   ctas_per_sm 4}; use_atomics must be 1 (EXT_EUNSUPPORTED otherwise).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * on a device shares the array and it keeps the last call's contents, so calls
+ * whose launches overlap on the GPU race: order them (e.g. one stream).
+ * Asynchronous on `stream`; errors as ext_batch_create. */
+#define EXT_NOALLOC_MAX_MESHES 256
+#define EXT_NOALLOC_SCRATCH_BYTES 65536
+ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id,
+                                 int32_t nargs, const ext_arg *args, const ext_tune_params *params,
+                                 void *stream);
+
 /* Waits for `stream`, then reads and clears the device error word:
  * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device
  * condition; see ext_last_error), or EXT_ECUDA (an asynchronous CUDA error). */

@@ -223,3 +223,20 @@ def ext_batch_destroy(batch: int) -> None:
 
 def ext_sync_check(stream=None) -> None:
     _check(lib.ext_sync_check(_stream(stream)))
+
+
+# ---- batched launch without allocation (ext_batch_run_noalloc)
+lib.ext_batch_run_noalloc.restype = ctypes.c_int
+lib.ext_batch_run_noalloc.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.POINTER(ext_arg), ctypes.POINTER(ext_tune_params),
+                                      ctypes.c_void_p]
+EXT_NOALLOC_MAX_MESHES = 256
+
+
+def ext_batch_run_noalloc(meshes, kernel_id: int, nargs: int, args, params=None, stream=None) -> None:
+    """Batched u^2 v launch that allocates no device memory, for callers that
+    cannot call cudaMalloc; args is the flat mesh-major list of (space, data,
+    access).  Calls that overlap on the GPU share one scratch array and race."""
+    ms = (ctypes.c_void_p * len(meshes))(*meshes)
+    _check(lib.ext_batch_run_noalloc(len(meshes), ms, kernel_id, nargs, _args(args), _params(params),
+                                     _stream(stream)))

@@ -767,3 +767,37 @@ extern "C" ext_status ext_batch_params(const ext_batch *batch, ext_tune_params *
 }
 
 extern "C" void ext_batch_destroy(ext_batch *batch) { destroy_batch(batch); }
+
+// Argument checks of a batched u^2 v launch (the same rules as
+// ext_batch_create), for the entry point that runs without allocating.
+ext_status ext_batch_validate(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id, int32_t nargs,
+                              const ext_arg *args, int *mode_out) {
+  if (nmesh < 1 || !meshes || !args) return ext_fail(EXT_EINVAL, "batched launch: no meshes");
+  int mode;
+  if (kernel_id == EXT_K_U2V_FWD) mode = 1;
+  else if (kernel_id == EXT_K_U2V_ADJ) mode = 2;
+  else if (kernel_id == EXT_K_U2V_FWDADJ) mode = 3;
+  else return ext_fail(EXT_EUNSUPPORTED, "batched launch: kernel %d is not batched", kernel_id);
+  const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
+  if (nargs != want) return ext_fail(EXT_EINVAL, "batched launch: expects %d arguments per mesh", want);
+  for (int mi = 0; mi < nmesh; ++mi) {
+    const ext_mesh *m = meshes[mi];
+    const ext_arg *a = args + (size_t)mi * nargs;
+    if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d: prisms only", mi);
+    EXT_CHECK(check_arg(m, a, 0, "batched launch", ELEM_P1P1, 3, EXT_READ));
+    for (int j = 1; j < nargs; ++j) {
+      const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);
+      EXT_CHECK(check_arg(m, a, j, "batched launch", ELEM_P1P1, 1, is_out ? EXT_INC : EXT_READ));
+    }
+  }
+  *mode_out = mode;
+  return EXT_OK;
+}
+
+// Stencil map, offsets and layer count of a space/mesh for code outside this
+// file (the entry point that runs without allocating builds its descriptors
+// from them).
+const int32_t *ext_space_map_dev(const ext_space *s) { return s->d_map; }
+const int32_t *ext_space_offsets_host(const ext_space *s) { return s->h_offset; }
+int64_t ext_mesh_ncells(const ext_mesh *m) { return m->N[2]; }
+int32_t ext_mesh_layers(const ext_mesh *m) { return m->layers; }

@@ -147,3 +147,11 @@ void batch_fill_desc(void *host_descs, int mi, int64_t ncells, int64_t item_begi
 cudaError_t launch_batch_phase(const void *d_descs, int nmesh, int64_t nitems, int mode, bool colour,
                                int cpi, int lt, unsigned long long *counter, int threads, int grid,
                                cudaStream_t s);
+
+// Helpers for the batched launch that runs without allocating (k_batch.cu).
+ext_status ext_batch_validate(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id, int32_t nargs,
+                              const ext_arg *args, int *mode_out);
+const int32_t *ext_space_map_dev(const ext_space *s);
+const int32_t *ext_space_offsets_host(const ext_space *s);
+int64_t ext_mesh_ncells(const ext_mesh *m);
+int32_t ext_mesh_layers(const ext_mesh *m);

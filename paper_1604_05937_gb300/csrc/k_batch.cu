@@ -210,3 +210,114 @@ cudaError_t launch_batch_phase(const void *d_descs, int nmesh, int64_t nitems, i
 #undef EXT_LAUNCH_BATCH
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Batched launch that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code that runs under a device-memory
+// budget owned by someone else (a framework's caching allocator that has
+// reserved the device, or a service that forbids allocation once it has
+// started), and latency-sensitive loops that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.  ext_batch_run_noalloc serves
+// them: it runs the same persistent work-queue kernel as a batch plan, in its
+// FP64-atomic form, but keeps the kernel's scratch memory -- the work counter
+// and the per-mesh descriptor table -- in the file-scope array below instead
+// of allocating it.  The array is part of the module image: every GPU that
+// loads this library holds its 64 KiB until the process exits.  All calls on
+// a device share it and it keeps the last call's contents; calls whose
+// launches overlap on the GPU race on it, so issue them in one stream or
+// otherwise order them.
+
+#include <mutex>
+
+#define EXT_NOALLOC_COUNTER_BYTES 256
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EXT_NOALLOC_SCRATCH_BYTES];
+
+static_assert(EXT_NOALLOC_COUNTER_BYTES + EXT_NOALLOC_MAX_MESHES * sizeof(BatchDesc) <= EXT_NOALLOC_SCRATCH_BYTES,
+              "scratch array too small for the descriptor table");
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_dev[128];  // device address of the array, per device
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in; the address is looked up once
+// per device, with that device current, on the first call.
+static ext_status noalloc_scratch(unsigned char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_batch_run_noalloc: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 128) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_run_noalloc: device %d", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_dev[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return ext_fail(EXT_ECUDA, "ext_batch_run_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_dev[dev] = reinterpret_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_dev[dev];
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id,
+                                            int32_t nargs, const ext_arg *args, const ext_tune_params *params,
+                                            void *stream) {
+  int mode = 0;
+  ext_status st = ext_batch_validate(nmesh, meshes, kernel_id, nargs, args, &mode);
+  if (st != EXT_OK) return st;
+  if (nmesh > EXT_NOALLOC_MAX_MESHES)
+    return ext_fail(EXT_EINVAL, "ext_batch_run_noalloc: %d meshes exceed the limit of %d", nmesh,
+                    EXT_NOALLOC_MAX_MESHES);
+  ext_tune_params tp;
+  if (params) {
+    tp = *params;
+  } else {
+    tp.cols_per_item = 4;
+    tp.layer_tile = 0;
+    tp.use_atomics = 1;
+    tp.threads = 256;
+    tp.ctas_per_sm = 4;
+  }
+  if (tp.use_atomics != 1)
+    return ext_fail(EXT_EUNSUPPORTED, "ext_batch_run_noalloc: only the FP64-atomic form runs without allocating");
+  if (tp.cols_per_item < 1 || tp.cols_per_item > 32 || tp.layer_tile < 0 ||
+      (tp.threads != 64 && tp.threads != 128 && tp.threads != 256) || tp.ctas_per_sm < 1 || tp.ctas_per_sm > 32)
+    return ext_fail(EXT_EINVAL, "ext_batch_run_noalloc: invalid launch parameters");
+  unsigned char *scratch = nullptr;
+  st = noalloc_scratch(&scratch);
+  if (st != EXT_OK) return st;
+
+  // descriptors staged in a per-thread host buffer, then copied into the array
+  static thread_local BatchDesc stage[EXT_NOALLOC_MAX_MESHES];
+  int64_t item = 0;
+  for (int mi = 0; mi < nmesh; ++mi) {
+    const ext_arg *a = args + (size_t)mi * nargs;
+    const int64_t ncells = ext_mesh_ncells(meshes[mi]);
+    const int32_t layers = ext_mesh_layers(meshes[mi]);
+    const int tile = tp.layer_tile > 0 ? (tp.layer_tile < layers ? tp.layer_tile : layers) : layers;
+    const int32_t ncol_items = (int32_t)((ncells + tp.cols_per_item - 1) / tp.cols_per_item);
+    const int32_t nlay_items = (layers + tile - 1) / tile;
+    int ai = 2;
+    const double *w = (mode & 2) ? (const double *)a[ai++].data : nullptr;
+    double *F = (mode & 1) ? (double *)a[ai++].data : nullptr;
+    double *G = (mode & 2) ? (double *)a[ai++].data : nullptr;
+    batch_fill_desc(stage, mi, ncells, item, layers, ncol_items, nlay_items, nullptr, ext_space_map_dev(a[0].space),
+                    ext_space_map_dev(a[1].space), ext_space_offsets_host(a[0].space),
+                    ext_space_offsets_host(a[1].space), (const double *)a[0].data, (const double *)a[1].data, w, F,
+                    G);
+    item += (int64_t)ncol_items * nlay_items;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(scratch + EXT_NOALLOC_COUNTER_BYTES, stage, sizeof(BatchDesc) * (size_t)nmesh,
+                                  cudaMemcpyHostToDevice, s);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // launch_batch_phase zeroes the counter before the launch
+  if (e == cudaSuccess)
+    e = launch_batch_phase(scratch + EXT_NOALLOC_COUNTER_BYTES, nmesh, item, mode, false, tp.cols_per_item,
+                           tp.layer_tile, reinterpret_cast<unsigned long long *>(scratch), tp.threads,
+                           tp.ctas_per_sm * sms, s);
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_batch_run_noalloc: %s", cudaGetErrorString(e));
+  return EXT_OK;
+}
