@@ -15,7 +15,16 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+#ifndef EXT_DG_UNROLL
+#define EXT_DG_UNROLL 4  // 16-byte moves in flight per thread (copy, flat interpolation)
+#endif
+constexpr int kUnroll = EXT_DG_UNROLL;
+#ifndef EXT_INTERP_TILE
+#define EXT_INTERP_TILE 128  // base columns per CTA tile (0: flat grid-stride kernel)
+#endif
+#ifndef EXT_INTERP_UNROLL
+#define EXT_INTERP_UNROLL 8  // pairs in flight per thread in the tiled interpolation
+#endif
 
 __device__ __forceinline__ double2 ld_stream2(const double *p) {
   return __ldcs(reinterpret_cast<const double2 *>(p));
@@ -102,6 +111,50 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1(const InterpDG1Launch p
   }
 }
 
+// Tiled form of k_interp_dg1: a CTA takes EXT_INTERP_TILE consecutive base
+// columns, stages their two stencil rows in shared memory once, then streams
+// the tile's pairs with the same flattened order; the x loads no longer wait
+// on a map load.
+template <int TILE, int UNROLL>
+__global__ void __launch_bounds__(kThreads) k_interp_dg1_tile(const InterpDG1Launch p, FastDiv three,
+                                                              int64_t ntiles) {
+  __shared__ int32_t xrow[TILE][6];
+  __shared__ int32_t obase[TILE];
+  const uint32_t npl = 3u * (uint32_t)p.layers;  // pairs per column
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c0 = tile * TILE;
+    const int ncol = (int)(p.ncells - c0 < TILE ? p.ncells - c0 : TILE);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol * 6; i += kThreads) xrow[i / 6][i % 6] = __ldg(p.xmap + c0 * 6 + i);
+    for (int i = threadIdx.x; i < ncol; i += kThreads) obase[i] = __ldg(p.omap + (c0 + i) * 6);
+    __syncthreads();
+    const uint32_t npairs = npl * (uint32_t)ncol;
+    for (uint32_t v = threadIdx.x; v < npairs; v += UNROLL * kThreads) {
+      double2 val[UNROLL];
+      uint32_t dst[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < npairs) {
+          const uint32_t cl = vv / npl;            // column within the tile
+          const uint32_t q = vv - cl * npl;        // pair within the column: 3 l + a
+          const uint32_t l = fdiv(q, three);
+          const uint32_t a = q - 3u * l;
+          const double lo = __ldg(p.x + (uint32_t)xrow[cl][2 * a] + l * (uint32_t)p.xoff);
+          const double hi = __ldg(p.x + (uint32_t)xrow[cl][2 * a + 1] + l * (uint32_t)p.xoff);
+          val[u] = make_double2(lo, hi);
+          dst[u] = (uint32_t)obase[cl] + 2u * q;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < npairs) st_stream2(p.out + dst[u], val[u]);
+      }
+    }
+  }
+}
+
 unsigned grid_for(uint64_t work, int per_thread) {
   uint64_t blocks = (work + (uint64_t)kThreads * per_thread - 1) / ((uint64_t)kThreads * per_thread);
   const uint64_t cap = 152ull * 16;  // 16 resident CTAs per SM is plenty for a stream
@@ -132,7 +185,13 @@ cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s) {
   const uint64_t n = colsize * (uint64_t)p.ncells;
   if (n == 0) return cudaSuccess;
   const uint32_t npairs = (uint32_t)(n / 2);
+#if EXT_INTERP_TILE > 0
+  const int64_t ntiles = (p.ncells + EXT_INTERP_TILE - 1) / EXT_INTERP_TILE;
+  const int64_t grid = ntiles < 152 * 8 ? ntiles : 152 * 8;
+  k_interp_dg1_tile<EXT_INTERP_TILE, EXT_INTERP_UNROLL><<<(unsigned)grid, kThreads, 0, s>>>(p, make_fastdiv(3u), ntiles);
+#else
   k_interp_dg1<<<grid_for(npairs, kUnroll), kThreads, 0, s>>>(p, make_fastdiv((uint32_t)colsize),
                                                               make_fastdiv(6u), npairs);
+#endif
   return cudaGetLastError();
 }

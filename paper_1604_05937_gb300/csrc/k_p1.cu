@@ -16,15 +16,19 @@
 // Arithmetic.  On a straight prism (vertical edges, flat horizontal faces)
 // the P1xP1 mass matrix is (A h / 72)(1 + [a = a'])(1 + [b = b']) with A the
 // triangle area and h the layer height, i.e. (Mt (x) Ml) with
-// Mt = A/12 (1 + [a=a']) and Ml = h/6 (1 + [b=b']).  Writing
-// T_m = Mt-shape applied to level m (T_a = f_a + f_0 + f_1 + f_2) and
-// s_l = A h_l / 72, the contribution to vertex a at level m is
-//   s_{m-1} T_{m-1,a} + 2 (s_{m-1} + s_m) T_{m,a} + s_m T_{m+1,a},
-// 18 FP64 operations per item.  The kernel checks straightness exactly
-// (bitwise compares of the loaded coordinates against the column's level-0
-// x, y and of the three z values of a level); a warp step touching any other
-// prism evaluates the element integrals with the full 6-point rule and the
-// general Jacobian instead, so any coordinate field is handled.
+// Mt = A/12 (1 + [a=a']) and Ml = h/6 (1 + [b=b']).  With s_l = A h_l / 72,
+// sigma_m = 2 (s_{m-1} + s_m) and S_m = f_{m,0} + f_{m,1} + f_{m,2}, the
+// contribution of a cell column to vertex a at level m is
+//   s_{m-1} (f_{m-1,a} + S_{m-1}) + sigma_m (f_{m,a} + S_m) + s_m (f_{m+1,a} + S_{m+1})
+//   = fma(s_{m-1}, f_{m-1,a}, fma(sigma_m, f_{m,a}, fma(s_m, f_{m+1,a}, K_m))),
+//   K_m = s_{m-1} S_{m-1} + sigma_m S_m + s_m S_{m+1},
+// 18 FP64 operations per item of which 11 are FMAs (GB300 issues DADD and
+// DMUL at about 0.85 of its DFMA rate, so FMAs are the cheap form).  The
+// kernel checks straightness exactly (bitwise compares of the loaded
+// coordinates against the column's level-0 x, y and of the three z values of
+// a level); a warp step touching any other prism evaluates the element
+// integrals with the full 6-point rule and the general Jacobian instead, so
+// any coordinate field is handled.
 #include "ext_internal.cuh"
 
 namespace {
@@ -33,16 +37,37 @@ constexpr int kWarps = 8;
 constexpr int kMaxCols = 32;  // columns per warp (lane j sets up column j)
 constexpr unsigned kFull = 0xffffffffu;
 
+#ifndef EXT_MASS_MINB
+#define EXT_MASS_MINB 2  // resident CTAs per SM the register budget must allow
+#endif
+#ifndef EXT_MASS_ITEMS
+#define EXT_MASS_ITEMS 3232  // target items (column levels) per warp
+#endif
+
+// a + b on the FP64 pipe; with EXT_MASS_ADD_AS_FMA as fma(a, 1, b), which
+// rounds identically
+__device__ __forceinline__ double dadd(double a, double b) {
+#ifdef EXT_MASS_ADD_AS_FMA
+  double r;
+  asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+#else
+  return a + b;
+#endif
+}
+
 struct ColInfo {
   int32_t cbot[3], ctop[3];  // coords DoF: vertex a at level 0, and at level `layers`
   int32_t fbot[3], ftop[3];
   int32_t bbot[3], btop[3];
   double alpha;              // |2 A| / 144, so that s = alpha * |h| = A h / 72
+  double alpha2;             // 2 alpha
   long long rx[3], ry[3];    // bit patterns of the level-0 x, y of the vertices
 };
 
 struct Level {
-  double T[3];   // T_a = f_a + (f_0 + f_1 + f_2)
+  double f[3];   // field values of the three vertices
+  double S;      // f_0 + f_1 + f_2
   double z;      // z of vertex 0
   int ok;        // level is horizontal and above the column's base vertices
 };
@@ -87,7 +112,7 @@ __device__ void prism_general(const double X[6][3], const double f[6], double ou
 
 __device__ __forceinline__ bool same_bits(double a, long long b) { return __double_as_longlong(a) == b; }
 
-__global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, int cpw) {
+__global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const MassP1Launch p, int cpw) {
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -121,6 +146,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
     }
     const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
     ci.alpha = fabs(det2) * (1.0 / 144.0);
+    ci.alpha2 = fabs(det2) * (1.0 / 72.0);
   }
   __syncwarp();
 
@@ -130,7 +156,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
   int m = lane - cl * L1;
 
   auto load_level = [&](int item, int clx, int mx, Level &lv) {
-    lv.T[0] = lv.T[1] = lv.T[2] = 0.0;
+    lv.f[0] = lv.f[1] = lv.f[2] = 0.0;
+    lv.S = 0.0;
     lv.z = 0.0;
     lv.ok = 1;
     if (item < nitems) {
@@ -148,10 +175,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
       }
       ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
             (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
-      const double S = (f[0] + f[1]) + f[2];
-      lv.T[0] = f[0] + S;
-      lv.T[1] = f[1] + S;
-      lv.T[2] = f[2] + S;
+      lv.S = dadd(dadd(f[0], f[1]), f[2]);
+      lv.f[0] = f[0];
+      lv.f[1] = f[1];
+      lv.f[2] = f[2];
       lv.z = zz[0];
       lv.ok = ok;
     }
@@ -160,8 +187,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
   Level cur, nxt;
   int item = lane;
   load_level(item, cl, m, cur);
-  // carry from the previous step's last lane: s_{m-1}, 2 s_{m-1}, T_{m-1}
-  double carry_s = 0.0, carry_s2 = 0.0, carry_T[3] = {0.0, 0.0, 0.0};
+  // carry from the previous step's last lane: s_{m-1}, 2 s_{m-1}, f_{m-1}, S_{m-1}
+  double carry_s = 0.0, carry_s2 = 0.0, carry_f[3] = {0.0, 0.0, 0.0}, carry_S = 0.0;
   int carry_ok = 1;
 
   for (int base = 0; base < nitems; base += 32) {
@@ -170,54 +197,58 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
     while (nm >= L1) { nm -= L1; ++ncl; }
     const int nitem = item + 32;
     if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
-    else { nxt.T[0] = nxt.T[1] = nxt.T[2] = 0.0; nxt.z = 0.0; nxt.ok = 1; }
+    else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.S = 0.0; nxt.z = 0.0; nxt.ok = 1; }
 
     const bool valid = item < nitems;
     const ColInfo &ci = cols[warp][valid ? cl : 0];
 
     // neighbours: level m+1 (next lane or lookahead), level m-1 (previous lane or carry)
-    double Tn[3], zn;
+    const bool top = (m == layers);
+    const bool bottom = (m == 0);
+    double fn[3], Sn, zn;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double dn = __shfl_down_sync(kFull, cur.T[a], 1);
-      const double la = __shfl_sync(kFull, nxt.T[a], 0);
-      Tn[a] = lane == 31 ? la : dn;
+      const double dn = __shfl_down_sync(kFull, cur.f[a], 1);
+      const double la = __shfl_sync(kFull, nxt.f[a], 0);
+      fn[a] = top ? 0.0 : (lane == 31 ? la : dn);
     }
     {
-      const double dn = __shfl_down_sync(kFull, cur.z, 1);
-      const double la = __shfl_sync(kFull, nxt.z, 0);
-      zn = lane == 31 ? la : dn;
+      const double dn = __shfl_down_sync(kFull, cur.S, 1);
+      const double la = __shfl_sync(kFull, nxt.S, 0);
+      Sn = top ? 0.0 : (lane == 31 ? la : dn);
+      const double dz = __shfl_down_sync(kFull, cur.z, 1);
+      const double lz = __shfl_sync(kFull, nxt.z, 0);
+      zn = lane == 31 ? lz : dz;
     }
     const int nxt_ok0 = __shfl_sync(kFull, nxt.ok, 0);
-    const bool top = (m == layers);
     double s = 0.0, s2 = 0.0;
     if (!top) {
-      const double h = fabs(zn - cur.z);
+      const double h = fabs(dadd(zn, -cur.z));
       s = ci.alpha * h;
-      s2 = (2.0 * ci.alpha) * h;
+      s2 = ci.alpha2 * h;
     }
-    double Tp[3], sp, sp2;
+    double fp[3], Sp, sp, sp2;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double up = __shfl_up_sync(kFull, cur.T[a], 1);
-      Tp[a] = lane == 0 ? carry_T[a] : up;
+      const double up = __shfl_up_sync(kFull, cur.f[a], 1);
+      fp[a] = bottom ? 0.0 : (lane == 0 ? carry_f[a] : up);
     }
     {
-      const double up = __shfl_up_sync(kFull, s, 1);
-      const double up2 = __shfl_up_sync(kFull, s2, 1);
-      sp = lane == 0 ? carry_s : up;
-      sp2 = lane == 0 ? carry_s2 : up2;
+      const double up = __shfl_up_sync(kFull, cur.S, 1);
+      Sp = bottom ? 0.0 : (lane == 0 ? carry_S : up);
+      const double us = __shfl_up_sync(kFull, s, 1);
+      const double us2 = __shfl_up_sync(kFull, s2, 1);
+      sp = bottom ? 0.0 : (lane == 0 ? carry_s : us);
+      sp2 = lane == 0 ? carry_s2 : us2;
     }
-    const bool bottom = (m == 0);
 
     const bool step_ok = __all_sync(kFull, cur.ok) && carry_ok && nxt_ok0;
     double val[3];
     if (step_ok) {
-      const double sig = bottom ? s2 : sp2 + s2;
-      for (int a = 0; a < 3; ++a) {
-        const double tn = top ? 0.0 : Tn[a];
-        double v = fma(sig, cur.T[a], s * tn);
-        if (!bottom) v = fma(sp, Tp[a], v);
-        val[a] = v;
-      }
+      const double sig = bottom ? s2 : dadd(sp2, s2);
+      const double K = fma(sp, Sp, fma(sig, cur.S, s * Sn));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) val[a] = fma(sp, fp[a], fma(sig, cur.f[a], fma(s, fn[a], K)));
     } else if (valid) {
       // general geometry: evaluate the two element integrals touching level m
       val[0] = val[1] = val[2] = 0.0;
@@ -247,7 +278,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
     // carry this step's last lane into the next step, shift the lookahead in
     carry_s = __shfl_sync(kFull, s, 31);
     carry_s2 = __shfl_sync(kFull, s2, 31);
-    for (int a = 0; a < 3; ++a) carry_T[a] = __shfl_sync(kFull, cur.T[a], 31);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) carry_f[a] = __shfl_sync(kFull, cur.f[a], 31);
+    carry_S = __shfl_sync(kFull, cur.S, 31);
     carry_ok = __shfl_sync(kFull, cur.ok, 31);
     cur = nxt;
     cl = ncl;
@@ -261,7 +294,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_p1(const MassP1Launch p, i
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const int L1 = p.layers + 1;
-  int cpw = (512 + L1 - 1) / L1;
+  int cpw = (EXT_MASS_ITEMS + L1 - 1) / L1;
   if (cpw < 1) cpw = 1;
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
