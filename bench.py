@@ -165,8 +165,8 @@ def run_ours(args, rank, world, local):
     init_dist(world, local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    m = meshgen.tri_mesh(args.n, seed=SEED + rank, order=args.order)
-    L = args.layers
+    m = meshgen.tri_mesh(args.n or N_CFG2, seed=SEED + rank, order=args.order)
+    L = args.layers or LAYERS_CFG2
     gm = E.Mesh(m.cells, m.xy, L)
     cs = E.Space(gm, P1_DELTA, ncomp=3)
     p1 = E.Space(gm, P1_DELTA)
@@ -362,6 +362,270 @@ def cpu_baseline(m, L, seconds: float, steps: int = 1):
                       f"min of {steps} run(s), {t:.2f} s"}
 
 
+# ----------------------------------------------------------------------------- other workloads
+class Flusher:
+    """Writes a buffer twice the L2 size between timed repetitions."""
+
+    def __init__(self, dev):
+        import torch
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        self.buf = torch.empty(max(2 * l2, 64 << 20) // 8, dtype=torch.float64, device=dev)
+
+    def __call__(self):
+        self.buf.fill_(1.0)
+
+
+def time_kernel(fn, reps, stream, flush=None, pre=None):
+    """min and median device time (ms) of fn() over reps, flushing L2 before each."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if pre is not None:
+            pre()
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return min(ts), statistics.median(ts)
+
+
+def _common(args, world, metric, value, unit, cfg, extra, clocks, launches, ms_step=None):
+    line = {"metric": metric, "value": round(value, 2), "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None if ms_step is None else round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clocks}
+    line.update(extra)
+    return line
+
+
+def run_cfg3(args, rank, world, local):
+    """Layer sweep on the 250k-triangle base: P1xP1 RHS, DG0 copy, DG1xDG1 copy,
+    RCM and random base orderings, L2 flushed before every timed launch."""
+    import torch
+    import paper_1604_05937_gb300 as E
+    init_dist(world, local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = Flusher(dev)
+    sweep = {}
+    launches = 0
+    clk = ClockSampler(local)
+    clk.start()
+    for order in ("rcm", "random"):
+        m = meshgen.tri_mesh(354, seed=SEED + 3, order=order)
+        V, C = m.nverts, m.ncells
+        sweep[order] = {}
+        for L in (1, 2, 5, 10, 20, 50, 100, 200):
+            gm = E.Mesh(m.cells, m.xy, L)
+            cs = E.Space(gm, P1_DELTA, ncomp=3)
+            p1 = E.Space(gm, P1_DELTA)
+            d0 = E.Space(gm, (0, 0, 0, 0, 0, 1))
+            d1 = E.Space(gm, DG1_DELTA)
+            X = E.extrude_coords(gm, cs)
+            Xr = X.view(-1, 3)
+            f = (torch.sin(Xr[:, 0]) * torch.cos(Xr[:, 1]) * Xr[:, 2]).contiguous()
+            b = p1.zeros()
+            a0 = torch.rand(d0.ndofs, dtype=torch.float64, device=dev)
+            o0 = d0.zeros()
+            a1 = torch.rand(d1.ndofs, dtype=torch.float64, device=dev)
+            o1 = d1.zeros()
+            rhs = lambda: E.ext_par_loop(gm.handle, E.EXT_K_RHS_P1P1, [(cs.handle, X, E.EXT_READ),
+                                         (p1.handle, f, E.EXT_READ), (p1.handle, b, E.EXT_INC)], s)
+            c0 = lambda: E.ext_par_loop(gm.handle, E.EXT_K_COPY_DG, [(d0.handle, a0, E.EXT_READ),
+                                        (d0.handle, o0, E.EXT_WRITE)], s)
+            c1 = lambda: E.ext_par_loop(gm.handle, E.EXT_K_COPY_DG, [(d1.handle, a1, E.EXT_READ),
+                                        (d1.handle, o1, E.EXT_WRITE)], s)
+            for fn in (rhs, c0, c1):
+                for _ in range(args.warmup):
+                    fn()
+            reps = max(5, args.steps)
+            t_rhs = time_kernel(rhs, reps, stream, flush, pre=b.zero_)
+            t_c0 = time_kernel(c0, reps, stream, flush)
+            t_c1 = time_kernel(c1, reps, stream, flush)
+            launches += 3 * (reps + args.warmup)
+            nP1 = V * (L + 1)
+            vb_rhs = 40 * nP1 + 48 * C
+            vb_c0 = 16 * C * L + 4 * C
+            vb_c1 = 96 * C * L + 24 * C
+            items = C * (L + 1)
+            sweep[order][L] = {
+                "rhs_ms": round(t_rhs[0], 4), "rhs_gbs": round(vb_rhs / t_rhs[0] / 1e6, 1),
+                "rhs_gops": round(MASS_OPS_PER_ITEM * items / t_rhs[0] / 1e6, 1),
+                "dg0_ms": round(t_c0[0], 4), "dg0_gbs": round(vb_c0 / t_c0[0] / 1e6, 1),
+                "dg1_ms": round(t_c1[0], 4), "dg1_gbs": round(vb_c1 / t_c1[0] / 1e6, 1)}
+            E.ext_sync_check(s)
+            del gm, cs, p1, d0, d1, X, f, b, a0, o0, a1, o1
+            torch.cuda.empty_cache()
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    hbm, hbm_kind, _ = peaks()
+    top = sweep["rcm"][100]
+    extra = {"sweep": sweep, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind,
+             "timing": "min over reps, L2 flushed (2x L2 buffer written) before every timed launch"}
+    return _common(args, world, "layer sweep: P1xP1 RHS valuable GB/s at 100 layers (RCM); sweep of RHS, DG0, DG1 copy",
+                   top["rhs_gbs"], "GB/s",
+                   {"workload": "extruded prisms: 250632 base triangles x {1,2,5,10,20,50,100,200} layers, RCM and "
+                                "random base order; P1xP1 RHS, DG0 copy, DG1xDG1 copy", "l2": "flushed"},
+                   extra, clocks, launches)
+
+
+# FP64 operations per hexahedral cell-layer (straight columns) of the Q2/DG2
+# u^2 v kernels, counted from the sum-factorised pipeline: per vertical Gauss
+# point 18 (A) + 30 (C) + 40 (D) + 16 (P) + 16 (r) + 114 (projection) for the
+# residual, plus 1 (h) + 18 (differences) + 27 (scaling); the adjoint
+# evaluates two fields and forms 2 P w; the fused pass shares P.
+HEX_OPS = {1: 1 + 18 + 4 * 234 + 27, 2: 1 + 36 + 4 * 338 + 27, 3: 1 + 36 + 4 * 468 + 54}
+# per prism cell-layer of the fused P1xP1 u^2 v residual + adjoint (straight)
+PRISM_U2V_OPS = {1: 59, 2: 81, 3: 117}
+
+
+def run_cfg4(args, rank, world, local):
+    """Q2xP2 and DG2 u^2 v residual and adjoint on the 500k-quad base, 64 layers."""
+    import torch
+    import paper_1604_05937_gb300 as E
+    init_dist(world, local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    m = meshgen.quad_mesh(args.n or 707, seed=SEED + 4, order="rcm")
+    L = args.layers or 64
+    V, C = m.nverts, m.ncells
+    gm = E.Mesh(m.cells, m.xy, L)
+    E_ = gm.N[1]
+    cs = E.Space(gm, P1_DELTA, ncomp=3)
+    X = E.extrude_coords(gm, cs)
+    res = {}
+    launches = 0
+    clk = ClockSampler(local)
+    clk.start()
+    tot_bytes, tot_ms = 0, 0.0
+    for name, delta, acc in (("Q2xP2", (1, 1, 1, 1, 1, 1), E.EXT_INC), ("DG2", (0, 0, 0, 0, 0, 27), E.EXT_WRITE)):
+        sp = E.Space(gm, delta)
+        u = torch.from_numpy(meshgen.uniform_field(sp.ndofs, SEED + 40)).to(dev)
+        w = torch.from_numpy(meshgen.uniform_field(sp.ndofs, SEED + 41)).to(dev)
+        F, G = sp.zeros(), sp.zeros()
+        R = E.EXT_READ
+        fwd = lambda: E.ext_par_loop(gm.handle, E.EXT_K_U2V_FWD, [(cs.handle, X, R), (sp.handle, u, R),
+                                     (sp.handle, F, acc)], s)
+        adj = lambda: E.ext_par_loop(gm.handle, E.EXT_K_U2V_ADJ, [(cs.handle, X, R), (sp.handle, u, R),
+                                     (sp.handle, w, R), (sp.handle, G, acc)], s)
+        both = lambda: E.ext_par_loop(gm.handle, E.EXT_K_U2V_FWDADJ, [(cs.handle, X, R), (sp.handle, u, R),
+                                      (sp.handle, w, R), (sp.handle, F, acc), (sp.handle, G, acc)], s)
+        for fn in (fwd, adj, both):
+            fn()
+        reps = max(3, min(args.steps, 10))
+        tf = time_kernel(fwd, reps, stream)
+        ta = time_kernel(adj, reps, stream)
+        tb = time_kernel(both, reps, stream)
+        launches += 3 * (reps + 1)
+        E.ext_sync_check(s)
+        n = sp.ndofs
+        coords_b = 24 * V * (L + 1) + 32 * C
+        umap_b = 4 * 27 * C
+        vb_f = coords_b + umap_b + 16 * n
+        vb_a = coords_b + umap_b + 24 * n
+        vb_b = coords_b + umap_b + 32 * n
+        cells = C * L
+        res[name] = {"ndofs": n,
+                     "fwd_ms": round(tf[0], 3), "fwd_gbs": round(vb_f / tf[0] / 1e6, 1),
+                     "fwd_gops": round(HEX_OPS[1] * cells / tf[0] / 1e6, 1),
+                     "adj_ms": round(ta[0], 3), "adj_gbs": round(vb_a / ta[0] / 1e6, 1),
+                     "adj_gops": round(HEX_OPS[2] * cells / ta[0] / 1e6, 1),
+                     "fwdadj_ms": round(tb[0], 3), "fwdadj_gbs": round(vb_b / tb[0] / 1e6, 1),
+                     "fwdadj_gops": round(HEX_OPS[3] * cells / tb[0] / 1e6, 1)}
+        tot_bytes += vb_b
+        tot_ms += tb[0]
+        del sp, u, w, F, G
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    extra = {"hex": res, "fp64_ops_per_cell": HEX_OPS, "fp64_peak_gops_nominal": 2 * SMS * SM_MAX_MHZ / 1e3}
+    return _common(args, world, "u^2 v residual + adjoint on hexahedra: valuable GB/s (Q2xP2 and DG2, fused pass)",
+                   world * tot_bytes / tot_ms / 1e6, "GB/s",
+                   {"workload": f"extruded hexahedra: {C} base quads x {L} layers, RCM; Q2xP2 ({E_} edges) and DG2"},
+                   extra, clocks, launches, ms_step=tot_ms)
+
+
+def run_cfg5(args, rank, world, local):
+    """64 prism meshes (log-uniform base sizes, uniform layer counts): u^2 v
+    residual + adjoint in one captured persistent launch vs 64 plain launches."""
+    import torch
+    import paper_1604_05937_gb300 as E
+    init_dist(world, local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    bp = meshgen.batched_params(count=args.count, seed=SEED + 5 + 1000 * rank, cmax=args.cmax)
+    meshes, per, keep = [], [], []
+    vb, ops, cells_total = 0, 0, 0
+    for i, (n, L) in enumerate(zip(bp.n, bp.layers)):
+        m = meshgen.tri_mesh(n, seed=SEED + 500 + i, order="rcm")
+        gm = E.Mesh(m.cells, m.xy, L)
+        cs = E.Space(gm, P1_DELTA, ncomp=3)
+        sp = E.Space(gm, P1_DELTA)
+        X = E.extrude_coords(gm, cs)
+        u = torch.rand(sp.ndofs, dtype=torch.float64, device=dev) * 2 - 1
+        w = torch.rand(sp.ndofs, dtype=torch.float64, device=dev) * 2 - 1
+        F, G = sp.zeros(), sp.zeros()
+        meshes.append(gm)
+        per.append([(cs, X, E.EXT_READ), (sp, u, E.EXT_READ), (sp, w, E.EXT_READ), (sp, F, E.EXT_INC),
+                    (sp, G, E.EXT_INC)])
+        keep.append((cs, sp))
+        vb += 56 * m.nverts * (L + 1) + 48 * m.ncells
+        ops += PRISM_U2V_OPS[3] * m.ncells * L
+        cells_total += m.ncells * L
+    t0 = time.time()
+    batch = E.Batch(meshes, E.EXT_K_U2V_FWDADJ, per, params=None)
+    tune_s = time.time() - t0
+
+    def plain():
+        for gm, args_ in zip(meshes, per):
+            E.ext_par_loop(gm.handle, E.EXT_K_U2V_FWDADJ, [(sp.handle, t, a) for sp, t, a in args_], s)
+
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plain()  # warm-up on the side stream before capture
+    stream.wait_stream(side)
+    with torch.cuda.graph(g, stream=side):
+        for gm, args_ in zip(meshes, per):
+            E.ext_par_loop(gm.handle, E.EXT_K_U2V_FWDADJ, [(sp.handle, t, a) for sp, t, a in args_],
+                           side.cuda_stream)
+    reps = max(3, min(args.steps, 10))
+    for _ in range(args.warmup):
+        batch.launch(s)
+        plain()
+    clk = ClockSampler(local)
+    clk.start()
+    tb = time_kernel(lambda: batch.launch(s), reps, stream)
+    tp = time_kernel(plain, reps, stream)
+    tg = time_kernel(g.replay, reps, stream)
+    clocks = clk.stop()
+    E.ext_sync_check(s)
+    if rank != 0:
+        return None
+    extra = {"batched_ms": round(tb[0], 3), "plain_64_launches_ms": round(tp[0], 3),
+             "plain_captured_graph_ms": round(tg[0], 3),
+             "speedup_vs_plain": round(tp[0] / tb[0], 3), "speedup_vs_captured_plain": round(tg[0] / tb[0], 3),
+             "autotuned_params": batch.params, "autotune_seconds": round(tune_s, 2),
+             "fp64_gops": round(ops / tb[0] / 1e6, 1), "cells": cells_total,
+             "meshes": {"count": args.count, "base_cells": [2 * n * n for n in bp.n], "layers": bp.layers}}
+    return _common(args, world, f"batched u^2 v residual + adjoint over {args.count} prism meshes: valuable GB/s "
+                   "(one captured persistent launch)", world * vb / tb[0] / 1e6, "GB/s",
+                   {"workload": f"{args.count} extruded prism meshes, {cells_total} prisms, P1xP1 u^2 v forward + adjoint",
+                    "valuable_bytes": vb},
+                   extra, clocks, args.count * (2 * reps + args.warmup) + reps, ms_step=tb[0])
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -393,9 +657,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--n", type=int, default=N_CFG2, help="base grid size (2 n^2 triangles)")
-    ap.add_argument("--layers", type=int, default=LAYERS_CFG2)
+    ap.add_argument("--n", type=int, default=None, help="base grid size (config 2: 707, config 4: 707)")
+    ap.add_argument("--layers", type=int, default=None, help="layers (config 2: 100, config 4: 64)")
+    ap.add_argument("--count", type=int, default=64, help="config 5: number of meshes")
+    ap.add_argument("--cmax", type=float, default=5e5, help="config 5: largest base cell count")
     ap.add_argument("--order", choices=["rcm", "random"], default="rcm")
+    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5], default=2,
+                    help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "
+                         "5: 64-mesh batched vs plain")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -405,7 +674,8 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build_library_only()
-        line = run_ours(args, rank, world, local)
+        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5}[args.config]
+        line = runner(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1 and args.impl == "ours":

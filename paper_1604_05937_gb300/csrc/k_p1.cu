@@ -41,7 +41,7 @@ constexpr unsigned kFull = 0xffffffffu;
 #define EXT_MASS_MINB 2  // resident CTAs per SM the register budget must allow
 #endif
 #ifndef EXT_MASS_ITEMS
-#define EXT_MASS_ITEMS 3232  // target items (column levels) per warp
+#define EXT_MASS_ITEMS 1616  // target items (column levels) per column group
 #endif
 
 // a + b on the FP64 pipe; with EXT_MASS_ADD_AS_FMA as fma(a, 1, b), which
@@ -116,176 +116,183 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t c0 = ((int64_t)blockIdx.x * kWarps + warp) * cpw;
-  if (c0 >= p.ncells) return;
-  const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
-  const int layers = p.layers;
-  const int L1 = layers + 1;
+  // Persistent grid: warps take groups of cpw columns round-robin, so all
+  // resident warps advance through the base mesh together and vertex
+  // columns shared by nearby cells are reused from L2.
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    const int layers = p.layers;
+    const int L1 = layers + 1;
 
-  // ---- per-column set-up: read the three stencil lists once (Algorithm 3's
-  // outer loop), the level-0 corner coordinates and the area factor.
-  if (lane < ncol) {
-    const int64_t c = c0 + lane;
-    ColInfo &ci = cols[warp][lane];
-    double x[3], y[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int32_t cb = __ldg(p.cmap + c * 6 + 2 * a), ct = __ldg(p.cmap + c * 6 + 2 * a + 1);
-      const int32_t fb = __ldg(p.fmap + c * 6 + 2 * a), ft = __ldg(p.fmap + c * 6 + 2 * a + 1);
-      const int32_t bb = __ldg(p.bmap + c * 6 + 2 * a), bt = __ldg(p.bmap + c * 6 + 2 * a + 1);
-      ci.cbot[a] = cb;
-      ci.ctop[a] = ct + (layers - 1) * p.coff[2 * a + 1];
-      ci.fbot[a] = fb;
-      ci.ftop[a] = ft + (layers - 1) * p.foff[2 * a + 1];
-      ci.bbot[a] = bb;
-      ci.btop[a] = bt + (layers - 1) * p.boff[2 * a + 1];
-      x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
-      y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
-      ci.rx[a] = __double_as_longlong(x[a]);
-      ci.ry[a] = __double_as_longlong(y[a]);
-    }
-    const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
-    ci.alpha = fabs(det2) * (1.0 / 144.0);
-    ci.alpha2 = fabs(det2) * (1.0 / 72.0);
-  }
-  __syncwarp();
-
-  const int nitems = ncol * L1;
-  // lane's item: column cl (local), level m
-  int cl = lane / L1;
-  int m = lane - cl * L1;
-
-  auto load_level = [&](int item, int clx, int mx, Level &lv) {
-    lv.f[0] = lv.f[1] = lv.f[2] = 0.0;
-    lv.S = 0.0;
-    lv.z = 0.0;
-    lv.ok = 1;
-    if (item < nitems) {
-      const ColInfo &ci = cols[warp][clx];
-      double f[3], zz[3];
-      int ok = 1;
-#pragma unroll
+    // ---- per-column set-up: read the three stencil lists once (Algorithm 3's
+    // outer loop), the level-0 corner coordinates and the area factor.
+    if (lane < ncol) {
+      const int64_t c = c0 + lane;
+      ColInfo &ci = cols[warp][lane];
+      double x[3], y[3];
+  #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, layers);
-        const double xa = __ldg(p.X + 3 * cd + 0);
-        const double ya = __ldg(p.X + 3 * cd + 1);
-        zz[a] = __ldg(p.X + 3 * cd + 2);
-        ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
-        f[a] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, layers));
+        const int32_t cb = __ldg(p.cmap + c * 6 + 2 * a), ct = __ldg(p.cmap + c * 6 + 2 * a + 1);
+        const int32_t fb = __ldg(p.fmap + c * 6 + 2 * a), ft = __ldg(p.fmap + c * 6 + 2 * a + 1);
+        const int32_t bb = __ldg(p.bmap + c * 6 + 2 * a), bt = __ldg(p.bmap + c * 6 + 2 * a + 1);
+        ci.cbot[a] = cb;
+        ci.ctop[a] = ct + (layers - 1) * p.coff[2 * a + 1];
+        ci.fbot[a] = fb;
+        ci.ftop[a] = ft + (layers - 1) * p.foff[2 * a + 1];
+        ci.bbot[a] = bb;
+        ci.btop[a] = bt + (layers - 1) * p.boff[2 * a + 1];
+        x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
+        y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
+        ci.rx[a] = __double_as_longlong(x[a]);
+        ci.ry[a] = __double_as_longlong(y[a]);
       }
-      ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
-            (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
-      lv.S = dadd(dadd(f[0], f[1]), f[2]);
-      lv.f[0] = f[0];
-      lv.f[1] = f[1];
-      lv.f[2] = f[2];
-      lv.z = zz[0];
-      lv.ok = ok;
+      const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+      ci.alpha = fabs(det2) * (1.0 / 144.0);
+      ci.alpha2 = fabs(det2) * (1.0 / 72.0);
     }
-  };
+    __syncwarp();
 
-  Level cur, nxt;
-  int item = lane;
-  load_level(item, cl, m, cur);
-  // carry from the previous step's last lane: s_{m-1}, 2 s_{m-1}, f_{m-1}, S_{m-1}
-  double carry_s = 0.0, carry_s2 = 0.0, carry_f[3] = {0.0, 0.0, 0.0}, carry_S = 0.0;
-  int carry_ok = 1;
+    const int nitems = ncol * L1;
+    // lane's item: column cl (local), level m
+    int cl = lane / L1;
+    int m = lane - cl * L1;
 
-  for (int base = 0; base < nitems; base += 32) {
-    // advance (cl, m) by 32 items for the lookahead
-    int ncl = cl, nm = m + 32;
-    while (nm >= L1) { nm -= L1; ++ncl; }
-    const int nitem = item + 32;
-    if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
-    else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.S = 0.0; nxt.z = 0.0; nxt.ok = 1; }
+    auto load_level = [&](int item, int clx, int mx, Level &lv) {
+      lv.f[0] = lv.f[1] = lv.f[2] = 0.0;
+      lv.S = 0.0;
+      lv.z = 0.0;
+      lv.ok = 1;
+      if (item < nitems) {
+        const ColInfo &ci = cols[warp][clx];
+        double f[3], zz[3];
+        int ok = 1;
+  #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, layers);
+          const double xa = __ldg(p.X + 3 * cd + 0);
+          const double ya = __ldg(p.X + 3 * cd + 1);
+          zz[a] = __ldg(p.X + 3 * cd + 2);
+          ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
+          f[a] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, layers));
+        }
+        ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
+              (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
+        lv.S = dadd(dadd(f[0], f[1]), f[2]);
+        lv.f[0] = f[0];
+        lv.f[1] = f[1];
+        lv.f[2] = f[2];
+        lv.z = zz[0];
+        lv.ok = ok;
+      }
+    };
 
-    const bool valid = item < nitems;
-    const ColInfo &ci = cols[warp][valid ? cl : 0];
+    Level cur, nxt;
+    int item = lane;
+    load_level(item, cl, m, cur);
+    // carry from the previous step's last lane: s_{m-1}, 2 s_{m-1}, f_{m-1}, S_{m-1}
+    double carry_s = 0.0, carry_s2 = 0.0, carry_f[3] = {0.0, 0.0, 0.0}, carry_S = 0.0;
+    int carry_ok = 1;
 
-    // neighbours: level m+1 (next lane or lookahead), level m-1 (previous lane or carry)
-    const bool top = (m == layers);
-    const bool bottom = (m == 0);
-    double fn[3], Sn, zn;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double dn = __shfl_down_sync(kFull, cur.f[a], 1);
-      const double la = __shfl_sync(kFull, nxt.f[a], 0);
-      fn[a] = top ? 0.0 : (lane == 31 ? la : dn);
-    }
-    {
-      const double dn = __shfl_down_sync(kFull, cur.S, 1);
-      const double la = __shfl_sync(kFull, nxt.S, 0);
-      Sn = top ? 0.0 : (lane == 31 ? la : dn);
-      const double dz = __shfl_down_sync(kFull, cur.z, 1);
-      const double lz = __shfl_sync(kFull, nxt.z, 0);
-      zn = lane == 31 ? lz : dz;
-    }
-    const int nxt_ok0 = __shfl_sync(kFull, nxt.ok, 0);
-    double s = 0.0, s2 = 0.0;
-    if (!top) {
-      const double h = fabs(dadd(zn, -cur.z));
-      s = ci.alpha * h;
-      s2 = ci.alpha2 * h;
-    }
-    double fp[3], Sp, sp, sp2;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double up = __shfl_up_sync(kFull, cur.f[a], 1);
-      fp[a] = bottom ? 0.0 : (lane == 0 ? carry_f[a] : up);
-    }
-    {
-      const double up = __shfl_up_sync(kFull, cur.S, 1);
-      Sp = bottom ? 0.0 : (lane == 0 ? carry_S : up);
-      const double us = __shfl_up_sync(kFull, s, 1);
-      const double us2 = __shfl_up_sync(kFull, s2, 1);
-      sp = bottom ? 0.0 : (lane == 0 ? carry_s : us);
-      sp2 = lane == 0 ? carry_s2 : us2;
-    }
+    for (int base = 0; base < nitems; base += 32) {
+      // advance (cl, m) by 32 items for the lookahead
+      int ncl = cl, nm = m + 32;
+      while (nm >= L1) { nm -= L1; ++ncl; }
+      const int nitem = item + 32;
+      if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
+      else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.S = 0.0; nxt.z = 0.0; nxt.ok = 1; }
 
-    const bool step_ok = __all_sync(kFull, cur.ok) && carry_ok && nxt_ok0;
-    double val[3];
-    if (step_ok) {
-      const double sig = bottom ? s2 : dadd(sp2, s2);
-      const double K = fma(sp, Sp, fma(sig, cur.S, s * Sn));
-#pragma unroll
-      for (int a = 0; a < 3; ++a) val[a] = fma(sp, fp[a], fma(sig, cur.f[a], fma(s, fn[a], K)));
-    } else if (valid) {
-      // general geometry: evaluate the two element integrals touching level m
-      val[0] = val[1] = val[2] = 0.0;
-      for (int half = 0; half < 2; ++half) {
-        const int l = half == 0 ? m - 1 : m;  // layer below / above level m
-        if (l < 0 || l >= layers) continue;
-        double X[6][3], f6[6], out[6];
+      const bool valid = item < nitems;
+      const ColInfo &ci = cols[warp][valid ? cl : 0];
+
+      // neighbours: level m+1 (next lane or lookahead), level m-1 (previous lane or carry)
+      const bool top = (m == layers);
+      const bool bottom = (m == 0);
+      double fn[3], Sn, zn;
+  #pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double dn = __shfl_down_sync(kFull, cur.f[a], 1);
+        const double la = __shfl_sync(kFull, nxt.f[a], 0);
+        fn[a] = top ? 0.0 : (lane == 31 ? la : dn);
+      }
+      {
+        const double dn = __shfl_down_sync(kFull, cur.S, 1);
+        const double la = __shfl_sync(kFull, nxt.S, 0);
+        Sn = top ? 0.0 : (lane == 31 ? la : dn);
+        const double dz = __shfl_down_sync(kFull, cur.z, 1);
+        const double lz = __shfl_sync(kFull, nxt.z, 0);
+        zn = lane == 31 ? lz : dz;
+      }
+      const int nxt_ok0 = __shfl_sync(kFull, nxt.ok, 0);
+      double s = 0.0, s2 = 0.0;
+      if (!top) {
+        const double h = fabs(dadd(zn, -cur.z));
+        s = ci.alpha * h;
+        s2 = ci.alpha2 * h;
+      }
+      double fp[3], Sp, sp, sp2;
+  #pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double up = __shfl_up_sync(kFull, cur.f[a], 1);
+        fp[a] = bottom ? 0.0 : (lane == 0 ? carry_f[a] : up);
+      }
+      {
+        const double up = __shfl_up_sync(kFull, cur.S, 1);
+        Sp = bottom ? 0.0 : (lane == 0 ? carry_S : up);
+        const double us = __shfl_up_sync(kFull, s, 1);
+        const double us2 = __shfl_up_sync(kFull, s2, 1);
+        sp = bottom ? 0.0 : (lane == 0 ? carry_s : us);
+        sp2 = lane == 0 ? carry_s2 : us2;
+      }
+
+      const bool step_ok = __all_sync(kFull, cur.ok) && carry_ok && nxt_ok0;
+      double val[3];
+      if (step_ok) {
+        const double sig = bottom ? s2 : dadd(sp2, s2);
+        const double K = fma(sp, Sp, fma(sig, cur.S, s * Sn));
+  #pragma unroll
+        for (int a = 0; a < 3; ++a) val[a] = fma(sp, fp[a], fma(sig, cur.f[a], fma(s, fn[a], K)));
+      } else if (valid) {
+        // general geometry: evaluate the two element integrals touching level m
+        val[0] = val[1] = val[2] = 0.0;
+        for (int half = 0; half < 2; ++half) {
+          const int l = half == 0 ? m - 1 : m;  // layer below / above level m
+          if (l < 0 || l >= layers) continue;
+          double X[6][3], f6[6], out[6];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 2; ++b) {
+              const int lev = l + b;
+              const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], lev, layers);
+              X[2 * a + b][0] = __ldg(p.X + 3 * cd + 0);
+              X[2 * a + b][1] = __ldg(p.X + 3 * cd + 1);
+              X[2 * a + b][2] = __ldg(p.X + 3 * cd + 2);
+              f6[2 * a + b] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], lev, layers));
+            }
+          prism_general(X, f6, out);
+          for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
+        }
+      }
+      if (valid) {
+  #pragma unroll
         for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 2; ++b) {
-            const int lev = l + b;
-            const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], lev, layers);
-            X[2 * a + b][0] = __ldg(p.X + 3 * cd + 0);
-            X[2 * a + b][1] = __ldg(p.X + 3 * cd + 1);
-            X[2 * a + b][2] = __ldg(p.X + 3 * cd + 2);
-            f6[2 * a + b] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], lev, layers));
-          }
-        prism_general(X, f6, out);
-        for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
+          atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers), val[a]);
       }
-    }
-    if (valid) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers), val[a]);
-    }
 
-    // carry this step's last lane into the next step, shift the lookahead in
-    carry_s = __shfl_sync(kFull, s, 31);
-    carry_s2 = __shfl_sync(kFull, s2, 31);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) carry_f[a] = __shfl_sync(kFull, cur.f[a], 31);
-    carry_S = __shfl_sync(kFull, cur.S, 31);
-    carry_ok = __shfl_sync(kFull, cur.ok, 31);
-    cur = nxt;
-    cl = ncl;
-    m = nm;
-    item = nitem;
+      // carry this step's last lane into the next step, shift the lookahead in
+      carry_s = __shfl_sync(kFull, s, 31);
+      carry_s2 = __shfl_sync(kFull, s2, 31);
+  #pragma unroll
+      for (int a = 0; a < 3; ++a) carry_f[a] = __shfl_sync(kFull, cur.f[a], 31);
+      carry_S = __shfl_sync(kFull, cur.S, 31);
+      carry_ok = __shfl_sync(kFull, cur.ok, 31);
+      cur = nxt;
+      cl = ncl;
+      m = nm;
+      item = nitem;
+    }
+    __syncwarp();  // the next group's set-up overwrites cols[warp]
   }
 }
 
@@ -298,7 +305,16 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw < 1) cpw = 1;
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
-  const int64_t blocks = (warps + kWarps - 1) / kWarps;
+  int64_t blocks = (warps + kWarps - 1) / kWarps;
+  static int resident = 0, sms = 0;  // per process: one GPU model
+  if (resident == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_p1, kWarps * 32, 0);
+    if (resident < 1) resident = 1;
+  }
+  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
   k_mass_p1<<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
