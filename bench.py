@@ -204,6 +204,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         step()
     E.ext_sync_check(s)
+    rates = E.ext_fp64_rates(s)  # FP64 issue rates of this GPU, for the roofline
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     clk = ClockSampler(local)
     barrier(world)
@@ -233,7 +234,7 @@ def run_ours(args, rank, world, local):
     d2h = (b.numel() + y.numel() + out.numel()) * 8
     if rank != 0:
         return None
-    return report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h)
+    return report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates)
 
 
 def e2e_time(args, world, stream, step, X, f, x, b, y, out):
@@ -266,7 +267,7 @@ def e2e_time(args, world, stream, step, X, f, x, b, y, out):
     return max_over_ranks(c0.elapsed_time(c1) / e2e_steps, world)
 
 
-def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h):
+def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates):
     hbm, hbm_kind, sm_max = peaks()
     V, C = m.nverts, m.ncells
     value = world * vb["total"] / (ms * 1e-3) / 1e9
@@ -275,6 +276,10 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
     achieved_ops = MASS_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     traffic = load_traffic("k_mass_p1")
+    # ceiling of this kernel's instruction mix at the measured issue rates
+    n_fma = MASS_FMA_PER_ITEM
+    n_other = MASS_OPS_PER_ITEM - n_fma
+    mix_peak = MASS_OPS_PER_ITEM / (n_fma / rates["dfma"] + 4 / rates["dadd"] + (n_other - 4) / rates["dmul"])
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -299,7 +304,11 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                      "algorithmic": f"{MASS_OPS_PER_ITEM} FP64 ops ({MASS_FLOPS_PER_ITEM} flops) per "
                                     f"(column, level) item x {items} items per launch",
                      "achieved_tflops": round(MASS_FLOPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e12, 4),
-                     "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)"},
+                     "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
+                     "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
+                     "peak_measured_mix": round(mix_peak, 2),
+                     "frac_of_measured_mix": round(achieved_ops / mix_peak, 4),
+                     "mix": f"{n_fma} DFMA + 4 DADD + {n_other - 4} DMUL per item"},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
@@ -312,12 +321,17 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
 
 
 def load_traffic(kernel: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, or None."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel's source has changed since the counters were taken."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
-            t = json.load(f)
-        return t.get(kernel)
+            t = json.load(f)[kernel]
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+                return None
+        return t["bytes_per_launch"]
     except Exception:
         return None
 

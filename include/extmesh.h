@@ -240,6 +240,13 @@ ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, i
                                  int32_t nargs, const ext_arg *args, const ext_tune_params *params,
                                  void *stream);
 
+/* Measured FP64 issue rates of this GPU, in G operations per second:
+ * gops_host[0] DFMA, [1] DADD, [2] DMUL (eight independent chains per thread,
+ * 4 CTAs of 256 threads per SM, best of two timed launches).  A measurement
+ * helper for the FP64 roofline of the assembly kernels; the paper has no
+ * counterpart.  Synchronous on `stream`; allocates a small scratch buffer. */
+ext_status ext_fp64_rates(double gops_host[3], void *stream);
+
 /* Waits for `stream`, then reads and clears the device error word:
  * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device
  * condition; see ext_last_error), or EXT_ECUDA (an asynchronous CUDA error). */

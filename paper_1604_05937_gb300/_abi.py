@@ -240,3 +240,15 @@ def ext_batch_run_noalloc(meshes, kernel_id: int, nargs: int, args, params=None,
     ms = (ctypes.c_void_p * len(meshes))(*meshes)
     _check(lib.ext_batch_run_noalloc(len(meshes), ms, kernel_id, nargs, _args(args), _params(params),
                                      _stream(stream)))
+
+
+# ---- FP64 issue rates (roofline denominator of the FP64-bound kernels)
+lib.ext_fp64_rates.restype = ctypes.c_int
+lib.ext_fp64_rates.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+
+
+def ext_fp64_rates(stream=None) -> dict:
+    """Measured DFMA, DADD and DMUL issue rates (G ops/s) of the current GPU."""
+    out = np.zeros(3)
+    _check(lib.ext_fp64_rates(_ptr(out), _stream(stream)))
+    return {"dfma": float(out[0]), "dadd": float(out[1]), "dmul": float(out[2])}
