@@ -21,7 +21,8 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 READ, WRITE, INC = 0, 1, 2
-K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ = range(6)
+K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ, K_MASS_TP = range(7)
+CG1, DG0, DG1 = 0, 1, 2
 
 # delta((d1,d2)) flattened as [d(0,0), d(0,1), d(1,0), d(1,1), d(2,0), d(2,1)]
 DELTA = {
@@ -95,6 +96,8 @@ def lib():
         L.oracle_gauss_legendre.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_set_hex_rule.restype = None
         L.oracle_set_hex_rule.argtypes = [ctypes.c_int32]
+        L.oracle_set_tp_element.restype = None
+        L.oracle_set_tp_element.argtypes = [ctypes.c_int32, ctypes.c_int32]
         _lib = L
     return _lib
 
@@ -206,6 +209,16 @@ def gauss_legendre(n: int) -> tuple[np.ndarray, np.ndarray]:
 
 def set_hex_rule(n: int) -> None:
     lib().oracle_set_hex_rule(n)
+
+
+def set_tp_element(h: int, v: int) -> None:
+    """Horizontal and vertical element (CG1, DG0, DG1) of K_MASS_TP."""
+    lib().oracle_set_tp_element(h, v)
+
+
+# the nine prism spaces of the paper's Sec. 4.1.2 as (name, h, v)
+TP_PAIRS = [(f"{a}x{b}", ha, vb) for a, ha in (("CG1", CG1), ("DG0", DG0), ("DG1", DG1))
+            for b, vb in (("CG1", CG1), ("DG0", DG0), ("DG1", DG1))]
 
 
 # ---------------------------------------------------------------------------

@@ -409,6 +409,92 @@ static void k_u2v_adj(const u2v_tab *T, double *const *vals, double *const *out,
   }
 }
 
+/* Tensor-product spaces on the prism (Sec. 4.1.2: the pairs (h, v) of
+ * CG1, DG0, DG1).  The horizontal element carries dh[d] DoFs on each base
+ * entity of dimension d (CG1: one per vertex; DG0: one per cell; DG1: three
+ * per cell, at the vertex positions); the vertical element carries dv0 DoFs
+ * on each interval end and dv1 inside (CG1: 1, 0; DG0: 0, 1; DG1: 0, 2 at
+ * the two end positions).  The space's delta is dh[d1] * (dv0, dv1)[d2].  A
+ * local DoF is identified by walking the stencil as ext_number/oracle_base_map
+ * do: entities in order (vertices, edges, cell), per entity the bottom
+ * horizontal DoFs, the top horizontal DoFs, then the vertical entity's DoFs
+ * (horizontal index major, vertical index minor). */
+static int32_t g_tp_h = ORC_CG1, g_tp_v = ORC_CG1;
+void oracle_set_tp_element(int32_t h, int32_t v) {
+  g_tp_h = h;
+  g_tp_v = v;
+}
+
+/* hfun[i]: horizontal basis of local DoF i (0..2 = barycentric lambda_a, 3 =
+ * constant); vfun[i]: vertical basis (0 = 1 - zeta, 1 = zeta, 2 = constant).
+ * Returns the number of local DoFs. */
+static int tp_layout(int h, int v, int hfun[27], int vfun[27]) {
+  const int dh[3] = {h == ORC_CG1 ? 1 : 0, 0, h == ORC_DG0 ? 1 : (h == ORC_DG1 ? 3 : 0)};
+  const int dv0 = v == ORC_CG1 ? 1 : 0;
+  const int dv1 = v == ORC_DG0 ? 1 : (v == ORC_DG1 ? 2 : 0);
+  int i = 0;
+  for (int d = 0; d <= 2; ++d)
+    for (int e = 0; e < (d == 2 ? 1 : 3); ++e) {
+      /* horizontal function of the entity's j-th horizontal DoF */
+      for (int part = 0; part < 3; ++part) {
+        const int nv = part < 2 ? dv0 : dv1;
+        for (int j = 0; j < dh[d]; ++j)
+          for (int beta = 0; beta < nv; ++beta) {
+            int hf;
+            if (h == ORC_DG0) hf = 3;
+            else if (d == 0) hf = e;  /* CG1 vertex */
+            else hf = j;              /* DG1 node at vertex j */
+            int vf;
+            if (part == 0) vf = 0;
+            else if (part == 1) vf = 1;
+            else vf = (v == ORC_DG0) ? 2 : beta;
+            hfun[i] = hf;
+            vfun[i] = vf;
+            ++i;
+          }
+      }
+    }
+  return i;
+}
+
+static double tp_phi(int hf, int vf, double xi, double eta, double zeta, double g[3]) {
+  double H, Hx, He, V, Vz;
+  if (hf == 3) { H = 1.0; Hx = 0.0; He = 0.0; }
+  else { H = tri_lam(hf, xi, eta); tri_dlam(hf, &Hx, &He); }
+  if (vf == 2) { V = 1.0; Vz = 0.0; }
+  else { V = lin(vf, zeta); Vz = dlin(vf); }
+  g[0] = Hx * V;
+  g[1] = He * V;
+  g[2] = H * Vz;
+  return H * V;
+}
+
+/* int f phi_i dx on one prism of a tensor-product space; the coordinates are
+ * the P1xP1 vector field (stencil DoF 2a+b) and define a general Jacobian. */
+static void k_mass_tp(double *const *vals, double *const *out, double *const *absv) {
+  int hfun[27], vfun[27];
+  const int k = tp_layout(g_tp_h, g_tp_v, hfun, vfun);
+  double pts[6][3], wts[6];
+  prism_rule(pts, wts);
+  const double *X = vals[0], *f = vals[1];
+  for (int q = 0; q < 6; ++q) {
+    double gphi[6], ggrad[6][3];
+    prism_basis(pts[q][0], pts[q][1], pts[q][2], gphi, ggrad);
+    const double dj = abs_detJ(6, X, ggrad);
+    double phi[27], fq = 0.0, fa = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double g[3];
+      phi[j] = tp_phi(hfun[j], vfun[j], pts[q][0], pts[q][1], pts[q][2], g);
+      fq += phi[j] * f[j];
+      fa += fabs(phi[j] * f[j]);
+    }
+    for (int i = 0; i < k; ++i) {
+      out[2][i] += wts[q] * dj * fq * phi[i];
+      absv[2][i] += wts[q] * dj * fa * fabs(phi[i]);
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 3: for every base cell, read its explicit list once; for every */
 /* layer apply the stencil function, then add the vertical offsets.         */
@@ -475,6 +561,9 @@ int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
           break;
         case ORC_K_U2V_ADJ:
           k_u2v_adj(T, vals, outv, absv);
+          break;
+        case ORC_K_MASS_TP:
+          k_mass_tp(vals, outv, absv);
           break;
         default:
           free(T);

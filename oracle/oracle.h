@@ -27,8 +27,13 @@ enum {
   ORC_K_MASS = 2,    /* coords READ, f READ, b INC: b_i += int f phi_i (P1xP1)     */
   ORC_K_INTERP = 3,  /* x READ (P1xP1), out WRITE (DG1xDG1): nodal interpolation   */
   ORC_K_U2V = 4,     /* coords READ, u READ, F INC|WRITE: F_i += int u^2 phi_i     */
-  ORC_K_U2V_ADJ = 5  /* coords READ, u READ, w READ, g INC|WRITE: (dF/du)^T w      */
+  ORC_K_U2V_ADJ = 5, /* coords READ, u READ, w READ, g INC|WRITE: (dF/du)^T w      */
+  ORC_K_MASS_TP = 6  /* coords READ, f READ, b INC: b_i += int f phi_i on a prism
+                        tensor-product space chosen by oracle_set_tp_element      */
 };
+
+/* Horizontal / vertical elements of the prism spaces of Sec. 4.1.2. */
+enum { ORC_CG1 = 0, ORC_DG0 = 1, ORC_DG1 = 2 };
 
 typedef struct {
   const int32_t *map;    /* ncells x k, the layer-0 explicit lists L(c)          */
@@ -75,6 +80,10 @@ void oracle_gauss_legendre(int32_t n, double *x, double *w);
 
 /* Select the 1-D Gauss rule used by the hexahedral kernels (default 4). */
 void oracle_set_hex_rule(int32_t n);
+
+/* Select the space of ORC_K_MASS_TP: horizontal element h on the triangle and
+ * vertical element v on the interval, each ORC_CG1, ORC_DG0 or ORC_DG1. */
+void oracle_set_tp_element(int32_t h, int32_t v);
 
 #ifdef __cplusplus
 }

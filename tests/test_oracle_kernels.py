@@ -341,3 +341,139 @@ def test_dg2_single_cell_equals_q2():
     for l in range(layers):
         np.add.at(acc, q2.map[0] + l * q2.offset, Fd[dg.map[0] + l * dg.offset])
     np.testing.assert_allclose(acc, Fq, rtol=1e-14, atol=1e-17)
+
+
+# ----------------------------------------------------------------------------- the nine prism spaces
+def _tp_local_nodes(h, v):
+    """(horizontal node, vertical node) of every stencil slot, read off the
+    stencil rule: entities vertices, edges, cell; per entity bottom, top,
+    vertical DoFs; horizontal index major.  Horizontal node: vertex a or 'c'
+    (cell constant); vertical node: 0 (z=0), 1 (z=h) or 'i' (constant)."""
+    dh = {O.CG1: (1, 0, 0), O.DG0: (0, 0, 1), O.DG1: (0, 0, 3)}[h]
+    dv0 = 1 if v == O.CG1 else 0
+    dv1 = {O.CG1: 0, O.DG0: 1, O.DG1: 2}[v]
+    out = []
+    for d, ents in ((0, 3), (1, 3), (2, 1)):
+        for e in range(ents):
+            for part, nv in ((0, dv0), (1, dv0), (2, dv1)):
+                for j in range(dh[d]):
+                    for beta in range(nv):
+                        hn = "c" if h == O.DG0 else (e if d == 0 else j)
+                        vn = part if part < 2 else ("i" if v == O.DG0 else beta)
+                        out.append((hn, vn))
+    return out
+
+
+@pytest.mark.parametrize("name,h,v", O.TP_PAIRS)
+def test_tp_element_matrix_closed_form(name, h, v):
+    """Straight prism: M = Mh (x) Mv with Mh = A/12 (1 + [a=a']) (CG1, DG1) or A
+    (DG0) and Mv = hz/6 (1 + [b=b']) (CG1, DG1) or hz (DG0)."""
+    tri = [(0.1, 0.2), (0.9, 0.35), (0.3, 0.8)]
+    cells = np.array([[0, 1, 2]], dtype=np.int32)
+    xy = np.array(tri)
+    L = 2
+    sp = O.number(cells, 3, L, O.DELTA[name])
+    csp, X = O.coords(cells, xy, L)
+    O.set_tp_element(h, v)
+    p = np.array(tri)
+    A = 0.5 * abs((p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1]) - (p[2, 0] - p[0, 0]) * (p[1, 1] - p[0, 1]))
+    hz = 1.0 / L
+    nodes = _tp_local_nodes(h, v)
+    assert len(nodes) == sp.k
+    # assemble column by column on layer 0 only (a one-layer slice of the stencil)
+    M = np.zeros((sp.k, sp.k))
+    for j in range(sp.k):
+        e = np.zeros(sp.ndofs)
+        e[sp.map[0, j]] = 1.0
+        b = np.zeros(sp.ndofs)
+        O.par_loop(O.K_MASS_TP, cells, 1, [(csp, X, 3, O.READ), (sp, e, 1, O.READ), (sp, b, 1, O.INC)])
+        M[:, j] = b[sp.map[0]]
+    want = np.zeros_like(M)
+    for i, (ha, va) in enumerate(nodes):
+        for j, (hb, vb) in enumerate(nodes):
+            mh = A if ha == "c" else A / 12 * (1 + (ha == hb))
+            mv = hz if va == "i" else hz / 6 * (1 + (va == vb))
+            want[i, j] = mh * mv
+    np.testing.assert_allclose(M, want, rtol=1e-13, atol=1e-18)
+
+
+@pytest.mark.parametrize("name,h,v", O.TP_PAIRS)
+def test_tp_volume_and_symmetry(name, h, v):
+    layers = 3
+    m = meshgen.tri_mesh(5, seed=31, order="random")
+    sp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    csp, X = O.coords(m.cells, m.xy, layers)
+    O.set_tp_element(h, v)
+
+    def apply(f):
+        b = np.zeros(sp.ndofs)
+        O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (sp, f, 1, O.READ), (sp, b, 1, O.INC)])
+        return b
+    assert abs(apply(np.ones(sp.ndofs)).sum() - 1.0) < 1e-14
+    x = meshgen.uniform_field(sp.ndofs, 32)
+    y = meshgen.uniform_field(sp.ndofs, 33)
+    assert abs(y @ apply(x) - x @ apply(y)) < 1e-14 * (np.abs(x).sum() + np.abs(y).sum()) / sp.ndofs
+
+
+def test_tp_cg1xcg1_equals_p1_kernel():
+    layers = 4
+    m = meshgen.tri_mesh(6, seed=34)
+    sp, csp, X = _mesh_space(m, layers, P1)
+    f = meshgen.uniform_field(sp.ndofs, 35)
+    O.set_tp_element(O.CG1, O.CG1)
+    b = np.zeros(sp.ndofs)
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (sp, f, 1, O.READ), (sp, b, 1, O.INC)])
+    np.testing.assert_allclose(b, _mass(m.cells, layers, csp, X, sp, f), rtol=1e-14, atol=1e-18)
+
+
+def _perturbed_coords(m, layers, seed):
+    csp, X = O.coords(m.cells, m.xy, layers)
+    rng = np.random.default_rng(seed)
+    return csp, X + 0.3 * rng.uniform(-1, 1, X.size) / (m.n * layers)
+
+
+def test_tp_matches_p1_kernel_on_general_prisms():
+    """On non-straight prisms the element matrix depends on which basis function
+    sits at which vertex, so the tensor-product kernel must reproduce the
+    P1xP1 kernel exactly there as well."""
+    layers = 3
+    m = meshgen.tri_mesh(5, seed=36, order="random")
+    sp = O.number(m.cells, m.nverts, layers, P1)
+    csp, X = _perturbed_coords(m, layers, 37)
+    f = meshgen.uniform_field(sp.ndofs, 38)
+    O.set_tp_element(O.CG1, O.CG1)
+    b = np.zeros(sp.ndofs)
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (sp, f, 1, O.READ), (sp, b, 1, O.INC)])
+    np.testing.assert_allclose(b, _mass(m.cells, layers, csp, X, sp, f), rtol=1e-14, atol=1e-18)
+
+
+@pytest.mark.parametrize("dgname,h,v", [("DG1xDG1", O.DG1, O.DG1), ("DG1xCG1", O.DG1, O.CG1),
+                                        ("CG1xDG1", O.CG1, O.DG1)])
+def test_tp_broken_space_assembles_to_continuous(dgname, h, v):
+    """Restrict a continuous P1xP1 field to a broken space (same nodes), apply
+    the broken mass operator, sum every broken DoF back onto the continuous
+    DoF at the same node: the result is the continuous mass action.  Holds on
+    general prisms only if the broken space's nodes sit where the stencil rule
+    puts them."""
+    layers = 3
+    m = meshgen.tri_mesh(4, seed=39, order="random")
+    cg = O.number(m.cells, m.nverts, layers, P1)
+    br = O.number(m.cells, m.nverts, layers, O.DELTA[dgname])
+    csp, X = _perturbed_coords(m, layers, 40)
+    f = meshgen.uniform_field(cg.ndofs, 41)
+    nodes = _tp_local_nodes(h, v)           # broken slot -> (vertex a, level 0/1)
+    slot_cg = [2 * a + b for a, b in nodes]  # the continuous slot at that node
+    fb = np.zeros(br.ndofs)
+    for l in range(layers):
+        fb[br.map[:, :] + l * br.offset[None, :]] = f[cg.map[:, slot_cg] + l * cg.offset[None, slot_cg]]
+    O.set_tp_element(h, v)
+    bb = np.zeros(br.ndofs)
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (br, fb, 1, O.READ), (br, bb, 1, O.INC)])
+    # every broken DoF once, onto the continuous DoF at its node
+    cg_of = np.full(br.ndofs, -1, dtype=np.int64)
+    for l in range(layers):
+        cg_of[br.map + l * br.offset[None, :]] = cg.map[:, slot_cg] + l * cg.offset[None, slot_cg]
+    assert np.all(cg_of >= 0)
+    back = np.zeros(cg.ndofs)
+    np.add.at(back, cg_of, bb)
+    np.testing.assert_allclose(back, _mass(m.cells, layers, csp, X, cg, f), rtol=1e-13, atol=1e-17)

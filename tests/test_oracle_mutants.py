@@ -42,6 +42,9 @@ MUTANTS = {
                              "out[3][j] += T->w[q] * dj * 2.0 * uq * uq * T->phi[q][j];"),
     "extrude_level": ("(double)(l + b) / (double)layers;", "(double)(l) / (double)layers;"),
     "interp_node_swap": ("out[1][2 * a + b] = v;", "out[1][2 * a + (1 - b)] = v;"),
+    "tp_dg0_vertical_not_constant": ("else vf = (v == ORC_DG0) ? 2 : beta;", "else vf = (v == ORC_DG0) ? 0 : beta;"),
+    "tp_cg1_vertex_shift": ("else if (d == 0) hf = e;  /* CG1 vertex */", "else if (d == 0) hf = (e + 1) % 3;"),
+    "tp_bottom_top_same": ("            if (part == 0) vf = 0;", "            if (part == 0) vf = 1;"),
     "mass_wrong_basis": ("out[2][i] += wts[q] * dj * fq * phi[i];", "out[2][i] += wts[q] * dj * fq * phi[(i + 2) % 6];"),
 }
 
