@@ -9,7 +9,7 @@ f = sin(x) cos(y) z (INC), P1xP1 mass-matrix action y += M x with x ~ U(-1,1)
 entry moved once) / device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2|3|4|5]
+                    [--config 2|3|4|5|6]
 
 --impl reference times the CPU oracle on a bounded sample of the same
 workload (the reference arm: there is no reference GPU code).  Under torchrun
@@ -690,6 +690,87 @@ def run_cfg5(args, rank, world, local):
                    extra, clocks, args.count * (2 * reps + args.warmup) + reps, ms_step=tb[0])
 
 
+# FP64 ops per unit of the nine-space mass kernels (straight prisms); unit =
+# (column, level) item for CG1xCG1, cell-layer otherwise (see k_tp.cu)
+TP_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), 18), ("CG1xDG0", (0, 1, 0, 0, 0, 0), 8),
+             ("CG1xDG1", (0, 2, 0, 0, 0, 0), 23), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 7),
+             ("DG0xDG0", (0, 0, 0, 0, 0, 1), 3), ("DG0xDG1", (0, 0, 0, 0, 0, 2), 7),
+             ("DG1xCG1", (0, 0, 0, 0, 3, 0), 23), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 8),
+             ("DG1xDG1", (0, 0, 0, 0, 0, 6), 23)]
+
+
+def run_cfg6(args, rank, world, local):
+    """The paper's Sec. 4.1 experiment on GB300: I_1 = int f v dx on all nine
+    prism spaces (CG1/DG0/DG1 horizontal x vertical), ~15M cells; (a) at 100
+    layers on a 150k-triangle base (the Tables 4/5 analogue), (b) with the
+    total cell count held near 15M while the layers vary (Sec. 4.1.3), RCM and
+    random base orders, L2 flushed before every timed launch."""
+    import torch
+    import paper_1604_05937_gb300 as E
+    init_dist(world, local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = Flusher(dev)
+    rates = E.ext_fp64_rates(s)
+    hbm, hbm_kind, sm_max = peaks()
+    nominal = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max / 1e3
+    layer_set = [int(x) for x in args.sweep.split(",")] if args.sweep else [1, 2, 5, 10, 20, 50, 100]
+    results = {}
+    launches = 0
+    clk = ClockSampler(local)
+    clk.start()
+    for order in ("rcm", "random"):
+        results[order] = {}
+        for L in layer_set:
+            n = max(2, int(round(math.sqrt(15e6 / (2 * L)))))
+            m = meshgen.tri_mesh(n, seed=SEED + 6, order=order)
+            V, C = m.nverts, m.ncells
+            gm = E.Mesh(m.cells, m.xy, L)
+            cs = E.Space(gm, P1_DELTA, ncomp=3)
+            X = E.extrude_coords(gm, cs)
+            row = {"base_cells": C, "cells": C * L}
+            for name, delta, ops in TP_SPACES:
+                sp = E.Space(gm, delta)
+                f = torch.rand(sp.ndofs, dtype=torch.float64, device=dev)
+                b = sp.zeros()
+                fn = lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_TP, [(cs.handle, X, E.EXT_READ),
+                                            (sp.handle, f, E.EXT_READ), (sp.handle, b, E.EXT_INC)], s)
+                fn()
+                reps = max(3, min(args.steps, 10))
+                t = time_kernel(fn, reps, stream, flush, pre=b.zero_)[0]
+                launches += reps + 1
+                units = C * (L + 1) if name == "CG1xCG1" else C * L
+                vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
+                vb = vb_paper + 24 * C + 4 * sp.k * C
+                gops = ops * units / t / 1e6
+                row[name] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
+                             "hbm_pct": round(100 * vb / t / 1e6 / hbm, 2),
+                             "hbm_pct_paper_bytes": round(100 * vb_paper / t / 1e6 / hbm, 2),
+                             "fp64_gops": round(gops, 1), "fp64_pct_nominal": round(100 * gops / nominal, 2)}
+                del sp, f, b
+            results[order][L] = row
+            E.ext_sync_check(s)
+            del gm, cs, X
+            torch.cuda.empty_cache()
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    top = results["rcm"][100] if 100 in results["rcm"] else results["rcm"][layer_set[-1]]
+    tot_b = sum(top[nm]["gbs"] * top[nm]["ms"] for nm, _, _ in TP_SPACES)
+    tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES)
+    extra = {"spaces": results, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
+             "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
+             "fp64_ops_per_unit": {nm: ops for nm, _, ops in TP_SPACES},
+             "timing": "min over reps, L2 flushed before every timed launch"}
+    return _common(args, world, "I_1 = int f v dx on the nine prism spaces at 100 layers (~15M cells, RCM): valuable "
+                   "GB/s over the nine launches", world * tot_b / tot_t, "GB/s",
+                   {"workload": "~15M prisms: base n = sqrt(15e6 / (2 layers)), layers " +
+                                ",".join(map(str, layer_set)) + "; nine CG1/DG0/DG1 x CG1/DG0/DG1 spaces; "
+                                "RCM and random base order", "l2": "flushed"},
+                   extra, clocks, launches)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -726,9 +807,10 @@ def main():
     ap.add_argument("--count", type=int, default=64, help="config 5: number of meshes")
     ap.add_argument("--cmax", type=float, default=5e5, help="config 5: largest base cell count")
     ap.add_argument("--order", choices=["rcm", "random"], default="rcm")
-    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5], default=2,
+    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6], default=2,
                     help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "
-                         "5: 64-mesh batched vs plain")
+                         "5: 64-mesh batched vs plain; 6: the nine prism spaces at ~15M cells")
+    ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -738,7 +820,7 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build_library_only()
-        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5}[args.config]
+        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6}[args.config]
         line = runner(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)

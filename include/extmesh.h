@@ -84,6 +84,12 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   scatter-adds; F's INC output becomes the READ cotangent w).
  * EXT_K_U2V_FWDADJ  [coords READ, u READ, w READ, F INC|WRITE, g INC|WRITE]:
  *                   both of the above in one pass.
+ * EXT_K_MASS_TP     [coords READ, f READ, b INC] on prisms: b_i += int f_h phi_i dx
+ *                   on any of the nine spaces h x v, h, v in {CG1, DG0, DG1}, of
+ *                   Sec. 4.1.2 (delta: CG1xCG1 {1,0,0,0,0,0}, CG1xDG0 {0,1,..},
+ *                   CG1xDG1 {0,2,..}, DG0xCG1 {..,1,0}, DG0xDG0 {..,0,1},
+ *                   DG0xDG1 {..,0,2}, DG1xCG1 {..,3,0}, DG1xDG0 {..,0,3},
+ *                   DG1xDG1 {..,0,6}); f and b share one numbering.
  * Quadrature: prisms use the 6-point rule (3-point degree-2 triangle rule x
  * 2-point Gauss); hexahedra use 4x4x4 Gauss points. */
 typedef enum {
@@ -94,7 +100,8 @@ typedef enum {
   EXT_K_INTERP_DG1 = 4,
   EXT_K_U2V_FWD = 5,
   EXT_K_U2V_ADJ = 6,
-  EXT_K_U2V_FWDADJ = 7
+  EXT_K_U2V_FWDADJ = 7,
+  EXT_K_MASS_TP = 8
 } ext_kernel_id;
 
 typedef struct ext_mesh ext_mesh;

@@ -20,7 +20,7 @@ STATUS_NAMES = ["EXT_OK", "EXT_EINVAL", "EXT_ENOMEM", "EXT_ECUDA", "EXT_EOVERFLO
 EXT_TRI, EXT_QUAD = 3, 4
 EXT_READ, EXT_WRITE, EXT_INC = 0, 1, 2
 (EXT_K_EXTRUDE, EXT_K_COPY_DG, EXT_K_RHS_P1P1, EXT_K_MASS_P1P1, EXT_K_INTERP_DG1, EXT_K_U2V_FWD,
- EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ) = range(8)
+ EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ, EXT_K_MASS_TP) = range(9)
 
 
 class ExtError(RuntimeError):

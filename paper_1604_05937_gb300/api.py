@@ -15,6 +15,13 @@ DELTA = {
     "DG1xDG1": (0, 0, 0, 0, 0, 6),
     "Q2xP2": (1, 1, 1, 1, 1, 1),
     "DG2": (0, 0, 0, 0, 0, 27),
+    # the nine prism spaces of Sec. 4.1.2 (CG1xCG1 and DG0xDG0, DG1xDG1 above)
+    "CG1xDG0": (0, 1, 0, 0, 0, 0),
+    "CG1xDG1": (0, 2, 0, 0, 0, 0),
+    "DG0xCG1": (0, 0, 0, 0, 1, 0),
+    "DG0xDG1": (0, 0, 0, 0, 0, 2),
+    "DG1xCG1": (0, 0, 0, 0, 3, 0),
+    "DG1xDG0": (0, 0, 0, 0, 0, 3),
 }
 
 

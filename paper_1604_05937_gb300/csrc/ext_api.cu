@@ -289,6 +289,41 @@ extern "C" void ext_space_destroy(ext_space *space) {
 // ---------------------------------------------------------------------------
 // par_loop
 
+// The nine prism spaces of Sec. 4.1.2 by their delta: horizontal element h
+// and vertical element v (0 CG1, 1 DG0, 2 DG1); -1 if delta is none of them.
+static int prism_pair(const int32_t d[6], int *h, int *v) {
+  static const int32_t tab[9][6] = {{1, 0, 0, 0, 0, 0}, {0, 1, 0, 0, 0, 0}, {0, 2, 0, 0, 0, 0},
+                                    {0, 0, 0, 0, 1, 0}, {0, 0, 0, 0, 0, 1}, {0, 0, 0, 0, 0, 2},
+                                    {0, 0, 0, 0, 3, 0}, {0, 0, 0, 0, 0, 3}, {0, 0, 0, 0, 0, 6}};
+  for (int i = 0; i < 9; ++i)
+    if (memcmp(tab[i], d, sizeof(tab[i])) == 0) {
+      *h = i / 3;
+      *v = i % 3;
+      return i;
+    }
+  return -1;
+}
+
+// Stencil slot of every (horizontal node, vertical node) of a prism pair,
+// following the stencil order of ext_number_dofs: entities vertices, edges,
+// cell; per entity bottom, top, then vertical DoFs; horizontal index major.
+static void prism_pair_slots(int h, int v, int nh, int nv, int32_t *slot) {
+  const int dh[3] = {h == 0 ? 1 : 0, 0, h == 1 ? 1 : (h == 2 ? 3 : 0)};
+  const int dv0 = v == 0 ? 1 : 0, dv1 = v == 1 ? 1 : (v == 2 ? 2 : 0);
+  int i = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < (d == 2 ? 1 : 3); ++e)
+      for (int part = 0; part < 3; ++part) {
+        const int nvp = part < 2 ? dv0 : dv1;
+        for (int j = 0; j < dh[d]; ++j)
+          for (int beta = 0; beta < nvp; ++beta, ++i) {
+            const int a = nh == 1 ? 0 : (d == 0 ? e : j);
+            const int b = nv == 1 ? 0 : (part < 2 ? part : beta);
+            slot[a * nv + b] = i;
+          }
+      }
+}
+
 static ext_status check_arg(const ext_mesh *mesh, const ext_arg *args, int i, const char *kn, int elem, int ncomp,
                             int access) {
   const ext_arg &a = args[i];
@@ -449,6 +484,38 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.g = (mode & 2) ? (double *)args[go].data : nullptr;
       p.err = ext_device_error_word();
       e = launch_u2v(p, s);
+      break;
+    }
+    case EXT_K_MASS_TP: {
+      const char *kn = "EXT_K_MASS_TP";
+      if (mesh->kind != EXT_TRI) return ext_fail(EXT_EINVAL, "%s: needs a triangular base mesh", kn);
+      if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, -1, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 2, kn, -1, 1, EXT_INC));
+      if (!same_numbering(args[1].space, args[2].space))
+        return ext_fail(EXT_EINVAL, "%s: f and b must share one numbering", kn);
+      int h = 0, v = 0;
+      if (prism_pair(args[1].space->delta, &h, &v) < 0)
+        return ext_fail(EXT_EUNSUPPORTED, "%s: not one of the nine CG1/DG0/DG1 prism spaces", kn);
+      if (h == 0 && v == 0) return ext_par_loop(mesh, EXT_K_MASS_P1P1, nargs, args, stream);
+      MassTPLaunch p;
+      memset(&p, 0, sizeof(p));
+      p.ncells = C;
+      p.layers = L;
+      p.nh = h == 1 ? 1 : 3;
+      p.nv = v == 1 ? 1 : 2;
+      p.k = args[1].space->k;
+      p.cmap = args[0].space->d_map;
+      for (int i = 0; i < 6; ++i) p.coff[i] = args[0].space->h_offset[i];
+      p.fmap = args[1].space->d_map;
+      prism_pair_slots(h, v, p.nh, p.nv, p.slot);
+      for (int i = 0; i < p.nh * p.nv; ++i) p.off[i] = args[1].space->h_offset[p.slot[i]];
+      p.scale = 0.5 * (p.nh == 3 ? 1.0 / 12.0 : 1.0) * (p.nv == 2 ? 1.0 / 6.0 : 1.0);
+      p.X = (const double *)args[0].data;
+      p.f = (const double *)args[1].data;
+      p.b = (double *)args[2].data;
+      e = launch_mass_tp(p, s);
       break;
     }
     default:

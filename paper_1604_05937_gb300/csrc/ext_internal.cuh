@@ -118,6 +118,23 @@ struct MassP1Launch {
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 
+// Mass action on the nine prism tensor-product spaces (k_tp.cu).
+struct MassTPLaunch {
+  int64_t ncells;
+  int32_t layers;
+  int32_t nh, nv;        // horizontal nodes (1: DG0, 3: CG1/DG1), vertical nodes (1: DG0, 2: CG1/DG1)
+  int32_t k;             // stencil length of the f/b space
+  const int32_t *cmap;   // coords map (k = 6)
+  int32_t coff[6];
+  const int32_t *fmap;   // f and b share this numbering
+  int32_t slot[6];       // stencil slot of node (a, b), index a * nv + b
+  int32_t off[6];        // vertical offsets of those slots
+  double scale;          // 1/2 x (1/12 if nh = 3) x (1/6 if nv = 2)
+  const double *X, *f;
+  double *b;
+};
+cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
+
 // u^2 v residual and adjoint (k_u2v.cu): prisms (P1 x P1) and hexahedra (Q2 x P2, DG2).
 struct U2VLaunch {
   int64_t ncells;

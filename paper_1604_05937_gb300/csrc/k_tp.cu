@@ -1,0 +1,181 @@
+// Mass action / RHS assembly b_i += int f phi_i dx (the residual I_1 of
+// Sec. 4.1.1) on the prism spaces of Sec. 4.1.2: horizontal element CG1, DG0
+// or DG1 on the triangle times vertical element CG1, DG0 or DG1 on the layer.
+// On a straight prism the element matrix is Mh (x) Mv with
+//   Mh = A/12 (1 + [a = a'])  (CG1, DG1: three nodes at the vertices) or A (DG0),
+//   Mv = h/6 (1 + [b = b'])   (CG1, DG1: nodes at the two ends)      or h (DG0),
+// so the kernel is templated on the node counts NH in {1, 3} and NV in {1, 2};
+// continuity only changes the addresses (the stencil slots) and whether
+// neighbouring cells share a DoF, and every increment is an FP64 atomic add
+// executed in L2, which is correct for shared and private DoFs alike.
+// One lane per (column, layer) item, lanes along the layers of a warp's
+// column group (coalesced column-contiguous accesses); a persistent grid hands
+// out column groups round-robin so resident warps sweep the mesh together.
+// Straightness is checked exactly as in the P1xP1 kernel; other prisms use the
+// 6-point rule with the general Jacobian.
+#include "ext_internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kMaxCols = 32;
+#ifndef EXT_TP_ITEMS
+#define EXT_TP_ITEMS 1600  // target items (column layers) per column group
+#endif
+
+struct TPCol {
+  double alpha;              // |2A| * (1/2)(1/12 if NH=3)(1/6 if NV=2): c = alpha |h|
+  long long rx[3], ry[3];    // level-0 x, y bit patterns
+};
+
+// element vector of a general prism: out[a*NV+b] = sum_q w_q |detJ| f(x_q) H_a V_b
+template <int NH, int NV>
+__device__ void tp_general(const double X[6][3], const double f[NH * NV], double out[NH * NV]) {
+  const double tp[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+  const double gz[2] = {0.5 - 0.28867513459481288225, 0.5 + 0.28867513459481288225};
+  for (int i = 0; i < NH * NV; ++i) out[i] = 0.0;
+  for (int t = 0; t < 3; ++t) {
+    const double lam[3] = {1.0 - tp[t][0] - tp[t][1], tp[t][0], tp[t][1]};
+    const double dlx[3] = {-1.0, 1.0, 0.0}, dly[3] = {-1.0, 0.0, 1.0};
+    for (int g = 0; g < 2; ++g) {
+      const double psi[2] = {1.0 - gz[g], gz[g]};
+      const double dpsi[2] = {-1.0, 1.0};
+      double J[3][3] = {{0.0}};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const double gr[3] = {dlx[a] * psi[b], dly[a] * psi[b], lam[a] * dpsi[b]};
+          for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) J[r][s] += X[2 * a + b][r] * gr[s];
+        }
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      double phi[NH * NV], fq = 0.0;
+      for (int a = 0; a < NH; ++a)
+        for (int b = 0; b < NV; ++b) {
+          phi[a * NV + b] = (NH == 3 ? lam[a] : 1.0) * (NV == 2 ? psi[b] : 1.0);
+          fq += phi[a * NV + b] * f[a * NV + b];
+        }
+      const double wq = (1.0 / 12.0) * fabs(det) * fq;
+      for (int i = 0; i < NH * NV; ++i) out[i] += wq * phi[i];
+    }
+  }
+}
+
+template <int NH, int NV>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
+  __shared__ TPCol cols[kWarps][kMaxCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int layers = p.layers;
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    if (lane < ncol) {
+      const int64_t c = c0 + lane;
+      double x[3], y[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t cd = __ldg(p.cmap + c * 6 + 2 * a);
+        x[a] = __ldg(p.X + 3 * cd + 0);
+        y[a] = __ldg(p.X + 3 * cd + 1);
+        cols[warp][lane].rx[a] = __double_as_longlong(x[a]);
+        cols[warp][lane].ry[a] = __double_as_longlong(y[a]);
+      }
+      const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+      cols[warp][lane].alpha = fabs(det2) * p.scale;
+    }
+    __syncwarp();
+    const int nitems = ncol * layers;
+    int cl = lane / layers, l = lane - (lane / layers) * layers;
+    for (int base = 0; base < nitems; base += 32) {
+      if (base + lane < nitems) {
+        const int64_t c = c0 + cl;
+        const TPCol &ci = cols[warp][cl];
+        double Xl[6][3];
+        int ok = 1;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const int64_t cd = (int64_t)__ldg(p.cmap + c * 6 + i) + (int64_t)l * p.coff[i];
+          Xl[i][0] = __ldg(p.X + 3 * cd + 0);
+          Xl[i][1] = __ldg(p.X + 3 * cd + 1);
+          Xl[i][2] = __ldg(p.X + 3 * cd + 2);
+          ok &= (__double_as_longlong(Xl[i][0]) == ci.rx[i >> 1]) & (__double_as_longlong(Xl[i][1]) == ci.ry[i >> 1]);
+        }
+        ok &= (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[2][2])) &
+              (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[4][2])) &
+              (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
+              (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
+        int32_t dof[NH * NV];
+        double f[NH * NV], b[NH * NV];
+#pragma unroll
+        for (int i = 0; i < NH * NV; ++i) {
+          dof[i] = __ldg(p.fmap + c * p.k + p.slot[i]) + l * p.off[i];
+          f[i] = __ldg(p.f + dof[i]);
+        }
+        if (ok) {
+          const double cc = ci.alpha * fabs(Xl[1][2] - Xl[0][2]);
+          if (NH == 1 && NV == 1) {
+            b[0] = cc * f[0];
+          } else if (NH == 1) {  // NV == 2
+            const double c2 = cc + cc;
+            b[0] = fma(c2, f[0], cc * f[1]);
+            b[1] = fma(c2, f[1], cc * f[0]);
+          } else if (NV == 1) {  // NH == 3
+            const double cS = cc * ((f[0] + f[1]) + f[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
+          } else {  // NH == 3, NV == 2: b_{a,beta} = c (2 T_{a,beta} + T_{a,1-beta})
+            const double c2 = cc + cc;
+            const double S0 = (f[0] + f[2]) + f[4], S1 = (f[1] + f[3]) + f[5];
+            const double K0 = cc * fma(2.0, S0, S1), K1 = cc * fma(2.0, S1, S0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              b[2 * a] = fma(c2, f[2 * a], fma(cc, f[2 * a + 1], K0));
+              b[2 * a + 1] = fma(c2, f[2 * a + 1], fma(cc, f[2 * a], K1));
+            }
+          }
+        } else {
+          tp_general<NH, NV>(Xl, f, b);
+        }
+#pragma unroll
+        for (int i = 0; i < NH * NV; ++i) atomicAdd(p.b + dof[i], b[i]);
+      }
+      l += 32;
+      while (l >= layers) { l -= layers; ++cl; }
+    }
+    __syncwarp();
+  }
+}
+
+template <int NH, int NV>
+cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
+  int cpw = (EXT_TP_ITEMS + p.layers - 1) / p.layers;
+  if (cpw < 1) cpw = 1;
+  if (cpw > kMaxCols) cpw = kMaxCols;
+  const int64_t warps = (p.ncells + cpw - 1) / cpw;
+  int64_t blocks = (warps + kWarps - 1) / kWarps;
+  static int resident[4] = {0, 0, 0, 0}, sms = 0;
+  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0);
+  if (resident[slot] == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV>, kWarps * 32, 0);
+    if (resident[slot] < 1) resident[slot] = 1;
+  }
+  if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
+  k_mass_tp<NH, NV><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
+  if (p.ncells == 0) return cudaSuccess;
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1>(p, s);
+  return launch_tp<3, 2>(p, s);
+}

@@ -351,3 +351,26 @@ def test_argument_validation():
                   100_000_000)
     with pytest.raises(E.ExtError, match="EXT_EOVERFLOW"):
         E.Space(deep, (0, 0, 0, 0, 0, 27))  # 2.7e9 DoFs do not fit int32
+
+
+# ------------------------------------------------------------------ the nine prism spaces (Sec. 4.1.2)
+@pytest.mark.parametrize("name,h,v", O.TP_PAIRS)
+@pytest.mark.parametrize("n,layers,order,perturb", [(5, 1, "rcm", 0.0), (9, 7, "random", 0.0),
+                                                    (13, 33, "rcm", 0.0), (6, 5, "random", 0.05)])
+def test_mass_tp_parity(name, h, v, n, layers, order, perturb):
+    m = meshgen.tri_mesh(n, seed=600 + n, order=order)
+    gm, csp, X = mesh_pair(m, layers)
+    if perturb:
+        rng = np.random.default_rng(601)
+        X = X + perturb * rng.uniform(-1, 1, X.size) / (m.n * layers)
+    osp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    f = meshgen.uniform_field(osp.ndofs, 602)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.set_tp_element(h, v)
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    sp = E.Space(gm, O.DELTA[name])
+    b = sp.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, to_dev(X), E.EXT_READ), (sp, to_dev(f), E.EXT_READ), (sp, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(host(b), ref, absr)
