@@ -138,13 +138,21 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The slowest rank's time (the job finishes when its last rank does)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(bytes_per_rank: float, ms_per_rank: float, world: int) -> float:
+    """Whole-job GB/s under weak scaling: every rank moves bytes_per_rank; the
+    job takes as long as the slowest rank."""
+    return world * bytes_per_rank / (max_over_ranks(ms_per_rank, world) * 1e-3) / 1e9
 
 
 # ----------------------------------------------------------------------------- workload (config 2)
