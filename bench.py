@@ -42,12 +42,16 @@ FP64_OPS_PER_CLK_PER_SM = 2.0  # 1.25 TFLOP/s nominal = 2 FMA/clk/SM x 152 SMs x
 SM_MAX_MHZ = 2070.0
 P1_DELTA = (1, 0, 0, 0, 0, 0)
 DG1_DELTA = (0, 0, 0, 0, 0, 6)
-# FP64 operations (DADD/DMUL/DFMA instructions per item) of the straight-prism
-# P1xP1 kernel: 2 (S) + 1 (h) + 2 (s, 2s) + 1 (sigma) + 3 (K) + 9 (three rows)
-# = 18, of which 11 are FMAs: 29 flops.
+# Algorithmic FP64 work of one (column, level) item of the straight-prism
+# P1xP1 kernel, with every sum done in registers: 2 (S) + 1 (h) + 2 (s, 2s) +
+# 1 (sigma) + 3 (K) + 9 (three rows) = 18 operations, 11 of them FMAs: 29
+# flops.  The kernel executes 13 of them on the SM's FP64 pipe (3 DMUL + 6
+# DFMA + 2 DADD + 2 DMUL) and hands the horizontal sum to L2 as 12 FP64 atomic
+# adds per item (value_a = 2 c_a + c_b + c_c).
 MASS_OPS_PER_ITEM = 18
 MASS_FLOPS_PER_ITEM = 29
-MASS_FMA_PER_ITEM = 11
+MASS_SM_OPS_PER_ITEM = 13
+MASS_L2_ADDS_PER_ITEM = 12
 
 
 def peaks():
@@ -334,10 +338,8 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
     achieved_ops = MASS_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     traffic = load_traffic("k_mass_p1")
-    # ceiling of this kernel's instruction mix at the measured issue rates
-    n_fma = MASS_FMA_PER_ITEM
-    n_other = MASS_OPS_PER_ITEM - n_fma
-    mix_peak = MASS_OPS_PER_ITEM / (n_fma / rates["dfma"] + 4 / rates["dadd"] + (n_other - 4) / rates["dmul"])
+    sm_ops = MASS_SM_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
+    l2_adds = MASS_L2_ADDS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -364,9 +366,9 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                      "achieved_tflops": round(MASS_FLOPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e12, 4),
                      "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-                     "peak_measured_mix": round(mix_peak, 2),
-                     "frac_of_measured_mix": round(achieved_ops / mix_peak, 4),
-                     "mix": f"{n_fma} DFMA + 4 DADD + {n_other - 4} DMUL per item"},
+                     "executed": {"sm_fp64_ops_per_item": MASS_SM_OPS_PER_ITEM,
+                                  "l2_fp64_atomic_adds_per_item": MASS_L2_ADDS_PER_ITEM,
+                                  "sm_fp64_gops": round(sm_ops, 1), "l2_atomic_adds_g_per_s": round(l2_adds, 1)}},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},

@@ -16,19 +16,23 @@
 // Arithmetic.  On a straight prism (vertical edges, flat horizontal faces)
 // the P1xP1 mass matrix is (A h / 72)(1 + [a = a'])(1 + [b = b']) with A the
 // triangle area and h the layer height, i.e. (Mt (x) Ml) with
-// Mt = A/12 (1 + [a=a']) and Ml = h/6 (1 + [b=b']).  With s_l = A h_l / 72,
-// sigma_m = 2 (s_{m-1} + s_m) and S_m = f_{m,0} + f_{m,1} + f_{m,2}, the
-// contribution of a cell column to vertex a at level m is
-//   s_{m-1} (f_{m-1,a} + S_{m-1}) + sigma_m (f_{m,a} + S_m) + s_m (f_{m+1,a} + S_{m+1})
-//   = fma(s_{m-1}, f_{m-1,a}, fma(sigma_m, f_{m,a}, fma(s_m, f_{m+1,a}, K_m))),
-//   K_m = s_{m-1} S_{m-1} + sigma_m S_m + s_m S_{m+1},
-// 18 FP64 operations per item of which 11 are FMAs (GB300 issues DADD and
-// DMUL at about 0.85 of its DFMA rate, so FMAs are the cheap form).  The
-// kernel checks straightness exactly (bitwise compares of the loaded
-// coordinates against the column's level-0 x, y and of the three z values of
-// a level); a warp step touching any other prism evaluates the element
-// integrals with the full 6-point rule and the general Jacobian instead, so
-// any coordinate field is handled.
+// Mt = A/12 (1 + [a=a']) and Ml = h/6 (1 + [b=b']).  With s_l = A h_l / 72
+// and sigma_m = 2 (s_{m-1} + s_m), the contribution of a cell column to
+// vertex a at level m is 2 c_a + c_b + c_c ({a, b, c} = {0, 1, 2}) with
+//   c_a = s_{m-1} f_{m-1,a} + sigma_m f_{m,a} + s_m f_{m+1,a}
+// (the horizontal factor 1 + [a = a'] applied to the vertical sums c).  The
+// kernel computes the three c_a on the FP64 pipe (13 operations per item: 3
+// DMUL + 6 DFMA for c, 4 for the layer factors) and leaves the horizontal
+// sum to L2: every vertex receives c_a twice and the two other c once as FP64
+// atomic adds.  GB300's FP64 pipe (about 2 DFMA per clock per SM) is the
+// scarce unit; its L2 executes FP64 atomic adds at about 0.4 T/s, so moving
+// the 9 additions of the horizontal sum there shortens the kernel.  The
+// algorithmic count of the item is 18 FP64 operations / 29 flops (the same
+// sums done in registers).  The kernel checks straightness exactly (bitwise
+// compares of the loaded coordinates against the column's level-0 x, y and of
+// the three z values of a level); a warp step touching any other prism
+// evaluates the element integrals with the full 6-point rule and the general
+// Jacobian instead, so any coordinate field is handled.
 #include "ext_internal.cuh"
 
 namespace {
@@ -67,7 +71,6 @@ struct ColInfo {
 
 struct Level {
   double f[3];   // field values of the three vertices
-  double S;      // f_0 + f_1 + f_2
   double z;      // z of vertex 0
   int ok;        // level is horizontal and above the column's base vertices
 };
@@ -162,7 +165,6 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
 
     auto load_level = [&](int item, int clx, int mx, Level &lv) {
       lv.f[0] = lv.f[1] = lv.f[2] = 0.0;
-      lv.S = 0.0;
       lv.z = 0.0;
       lv.ok = 1;
       if (item < nitems) {
@@ -180,7 +182,6 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
         }
         ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
               (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
-        lv.S = dadd(dadd(f[0], f[1]), f[2]);
         lv.f[0] = f[0];
         lv.f[1] = f[1];
         lv.f[2] = f[2];
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
     int item = lane;
     load_level(item, cl, m, cur);
     // carry from the previous step's last lane: s_{m-1}, 2 s_{m-1}, f_{m-1}, S_{m-1}
-    double carry_s = 0.0, carry_s2 = 0.0, carry_f[3] = {0.0, 0.0, 0.0}, carry_S = 0.0;
+    double carry_s = 0.0, carry_s2 = 0.0, carry_f[3] = {0.0, 0.0, 0.0};
     int carry_ok = 1;
 
     for (int base = 0; base < nitems; base += 32) {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       while (nm >= L1) { nm -= L1; ++ncl; }
       const int nitem = item + 32;
       if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
-      else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.S = 0.0; nxt.z = 0.0; nxt.ok = 1; }
+      else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.z = 0.0; nxt.ok = 1; }
 
       const bool valid = item < nitems;
       const ColInfo &ci = cols[warp][valid ? cl : 0];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       // neighbours: level m+1 (next lane or lookahead), level m-1 (previous lane or carry)
       const bool top = (m == layers);
       const bool bottom = (m == 0);
-      double fn[3], Sn, zn;
+      double fn[3], zn;
   #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double dn = __shfl_down_sync(kFull, cur.f[a], 1);
@@ -218,9 +219,6 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
         fn[a] = top ? 0.0 : (lane == 31 ? la : dn);
       }
       {
-        const double dn = __shfl_down_sync(kFull, cur.S, 1);
-        const double la = __shfl_sync(kFull, nxt.S, 0);
-        Sn = top ? 0.0 : (lane == 31 ? la : dn);
         const double dz = __shfl_down_sync(kFull, cur.z, 1);
         const double lz = __shfl_sync(kFull, nxt.z, 0);
         zn = lane == 31 ? lz : dz;
@@ -232,15 +230,13 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
         s = ci.alpha * h;
         s2 = ci.alpha2 * h;
       }
-      double fp[3], Sp, sp, sp2;
+      double fp[3], sp, sp2;
   #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double up = __shfl_up_sync(kFull, cur.f[a], 1);
         fp[a] = bottom ? 0.0 : (lane == 0 ? carry_f[a] : up);
       }
       {
-        const double up = __shfl_up_sync(kFull, cur.S, 1);
-        Sp = bottom ? 0.0 : (lane == 0 ? carry_S : up);
         const double us = __shfl_up_sync(kFull, s, 1);
         const double us2 = __shfl_up_sync(kFull, s2, 1);
         sp = bottom ? 0.0 : (lane == 0 ? carry_s : us);
@@ -251,9 +247,9 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       double val[3];
       if (step_ok) {
         const double sig = bottom ? s2 : dadd(sp2, s2);
-        const double K = fma(sp, Sp, fma(sig, cur.S, s * Sn));
+        // c_a = s_{m-1} f_{m-1,a} + sigma f_{m,a} + s_m f_{m+1,a}
   #pragma unroll
-        for (int a = 0; a < 3; ++a) val[a] = fma(sp, fp[a], fma(sig, cur.f[a], fma(s, fn[a], K)));
+        for (int a = 0; a < 3; ++a) val[a] = fma(sp, fp[a], fma(sig, cur.f[a], s * fn[a]));
       } else if (valid) {
         // general geometry: evaluate the two element integrals touching level m
         val[0] = val[1] = val[2] = 0.0;
@@ -276,8 +272,16 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       }
       if (valid) {
   #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers), val[a]);
+        for (int a = 0; a < 3; ++a) {
+          // straight: value_a = 2 c_a + c_b + c_c, the horizontal sum done by L2
+          double *dst = p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers);
+          atomicAdd(dst, val[a]);
+          if (step_ok) {
+            atomicAdd(dst, val[0]);
+            atomicAdd(dst, val[1]);
+            atomicAdd(dst, val[2]);
+          }
+        }
       }
 
       // carry this step's last lane into the next step, shift the lookahead in
@@ -285,7 +289,6 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       carry_s2 = __shfl_sync(kFull, s2, 31);
   #pragma unroll
       for (int a = 0; a < 3; ++a) carry_f[a] = __shfl_sync(kFull, cur.f[a], 31);
-      carry_S = __shfl_sync(kFull, cur.S, 31);
       carry_ok = __shfl_sync(kFull, cur.ok, 31);
       cur = nxt;
       cl = ncl;
