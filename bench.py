@@ -339,6 +339,8 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     achieved_ops = MASS_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     traffic = load_traffic("k_mass_p1")
     sm_ops = MASS_SM_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
+    # ceiling of the executed SM mix (6 DFMA, 2 DADD, 5 DMUL per item) at the measured rates
+    sm_mix_peak = MASS_SM_OPS_PER_ITEM / (6 / rates["dfma"] + 2 / rates["dadd"] + 5 / rates["dmul"])
     l2_adds = MASS_L2_ADDS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
@@ -368,7 +370,11 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
                      "executed": {"sm_fp64_ops_per_item": MASS_SM_OPS_PER_ITEM,
                                   "l2_fp64_atomic_adds_per_item": MASS_L2_ADDS_PER_ITEM,
-                                  "sm_fp64_gops": round(sm_ops, 1), "l2_atomic_adds_g_per_s": round(l2_adds, 1)}},
+                                  "sm_fp64_gops": round(sm_ops, 1), "l2_atomic_adds_g_per_s": round(l2_adds, 1),
+                                  "sm_fp64_frac_of_mix_ceiling": round(sm_ops / sm_mix_peak, 4),
+                                  "l2_atomic_frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
+                     "frac_note": "above 1 because 12 of the item's additions run in L2 atomic units, "
+                                  "outside the SM FP64 pipe whose nominal rate is the denominator"},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},

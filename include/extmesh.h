@@ -247,12 +247,14 @@ ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, i
                                  int32_t nargs, const ext_arg *args, const ext_tune_params *params,
                                  void *stream);
 
-/* Measured FP64 issue rates of this GPU, in G operations per second:
- * gops_host[0] DFMA, [1] DADD, [2] DMUL (eight independent chains per thread,
- * 4 CTAs of 256 threads per SM, best of two timed launches).  A measurement
- * helper for the FP64 roofline of the assembly kernels; the paper has no
- * counterpart.  Synchronous on `stream`; allocates a small scratch buffer. */
-ext_status ext_fp64_rates(double gops_host[3], void *stream);
+/* Measured FP64 rates of this GPU, in G operations per second:
+ * gops_host[0] DFMA, [1] DADD, [2] DMUL issued by the SMs (eight independent
+ * chains per thread, 4 CTAs of 256 threads per SM), [3] FP64 atomic adds
+ * executed by L2 (coalesced, to a 64 MiB buffer resident in L2); best of two
+ * timed launches each.  A measurement helper for the roofline of the FP64
+ * assembly kernels; the paper has no counterpart.  Synchronous on `stream`;
+ * allocates and frees scratch buffers. */
+ext_status ext_fp64_rates(double gops_host[4], void *stream);
 
 /* Waits for `stream`, then reads and clears the device error word:
  * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device

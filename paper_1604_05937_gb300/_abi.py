@@ -248,7 +248,7 @@ lib.ext_fp64_rates.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
 
 
 def ext_fp64_rates(stream=None) -> dict:
-    """Measured DFMA, DADD and DMUL issue rates (G ops/s) of the current GPU."""
-    out = np.zeros(3)
+    """Measured DFMA, DADD, DMUL issue rates and L2 FP64 atomic-add rate (G/s)."""
+    out = np.zeros(4)
     _check(lib.ext_fp64_rates(_ptr(out), _stream(stream)))
-    return {"dfma": float(out[0]), "dadd": float(out[1]), "dmul": float(out[2])}
+    return {"dfma": float(out[0]), "dadd": float(out[1]), "dmul": float(out[2]), "l2_atomic_add": float(out[3])}
