@@ -21,7 +21,7 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 READ, WRITE, INC = 0, 1, 2
-K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ, K_MASS_TP = range(7)
+K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ, K_MASS_TP, K_HFACET_MASS, K_HFACET_JUMP = range(9)
 CG1, DG0, DG1 = 0, 1, 2
 
 # delta((d1,d2)) flattened as [d(0,0), d(0,1), d(1,0), d(1,1), d(2,0), d(2,1)]
@@ -98,6 +98,28 @@ def lib():
         L.oracle_set_hex_rule.argtypes = [ctypes.c_int32]
         L.oracle_set_tp_element.restype = None
         L.oracle_set_tp_element.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        L.oracle_var_ranges.restype = ctypes.c_int
+        L.oracle_var_ranges.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_alg1_var.restype = ctypes.c_int64
+        L.oracle_alg1_var.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_base_map_var.restype = ctypes.c_int
+        L.oracle_base_map_var.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]
+        L.oracle_hfacet_size.restype = ctypes.c_int32
+        L.oracle_hfacet_size.argtypes = [ctypes.c_int32, ctypes.c_void_p]
+        L.oracle_hfacet_map.restype = ctypes.c_int
+        L.oracle_hfacet_map.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+        L.oracle_hfacet_alg2.restype = None
+        L.oracle_hfacet_alg2.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_par_loop_var.restype = ctypes.c_int
+        L.oracle_par_loop_var.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -126,6 +148,18 @@ class Space:
     map: np.ndarray       # (C, k) int32, layer-0 explicit lists
     offset: np.ndarray    # (k,) int32, Algorithm 2
     first: dict = field(default_factory=dict)  # t=2*d1+d2 -> (N_d1, layers+1-d2) int64
+    hmap: np.ndarray | None = None     # (C, hk) horizontal-facet lists (closure DoFs), if any
+    hoffset: np.ndarray | None = None  # (hk,) their offsets
+    cell_first: np.ndarray | None = None   # variable layers: first level of each column
+    cell_layers: np.ndarray | None = None  # variable layers: layers of each column
+
+    def facet(self) -> "Space":
+        """The same numbering seen through the horizontal-facet lists."""
+        if self.hmap is None:
+            raise ValueError("the space has no DoFs on horizontal facets")
+        return Space(delta=self.delta, layers=self.layers, ndofs=self.ndofs, k=int(self.hmap.shape[1]),
+                     map=self.hmap, offset=self.hoffset, cell_first=self.cell_first,
+                     cell_layers=self.cell_layers)
 
 
 def entity_counts(cells: np.ndarray, nverts: int) -> tuple[int, int, int, np.ndarray]:
@@ -165,15 +199,87 @@ def number(cells: np.ndarray, nverts: int, layers: int, delta, keep_tables: bool
     off = np.empty(k, dtype=np.int32)
     L.oracle_alg2(nvc, _p(d), _p(off))
     first = {t: tabs[t] for t in range(6) if tabs[t] is not None} if keep_tables else {}
-    return Space(delta=delta, layers=layers, ndofs=int(ndofs), k=int(k), map=m, offset=off, first=first)
+    hmap, hoff = _facet_lists(cells, ce, layers, None, d, ptrs)
+    return Space(delta=delta, layers=layers, ndofs=int(ndofs), k=int(k), map=m, offset=off, first=first,
+                 hmap=hmap, hoffset=hoff)
+
+
+def _facet_lists(cells, ce, maxlevel, cell_first, d, ptrs):
+    nvc = cells.shape[1]
+    L = lib()
+    hk = L.oracle_hfacet_size(nvc, _p(d))
+    if hk == 0:
+        return None, None
+    hm = np.empty((cells.shape[0], hk), dtype=np.int32)
+    if L.oracle_hfacet_map(nvc, cells.shape[0], _p(cells), _p(ce), maxlevel, _p(cell_first), _p(d), ptrs,
+                           _p(hm)) != 0:
+        raise ValueError("oracle_hfacet_map failed")
+    ho = np.empty(hk, dtype=np.int32)
+    L.oracle_hfacet_alg2(nvc, _p(d), _p(ho))
+    return hm, ho
+
+
+def var_ranges(cells: np.ndarray, nverts: int, cell_first, cell_layers):
+    """Level ranges (lo, hi) of every base entity, dimension-major."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    ce, ne = derive_edges(cells, nverts)
+    cf = np.ascontiguousarray(cell_first, dtype=np.int32)
+    cl = np.ascontiguousarray(cell_layers, dtype=np.int32)
+    N = np.array([nverts, ne, cells.shape[0]], dtype=np.int64)
+    lo = np.empty(int(N.sum()), dtype=np.int32)
+    hi = np.empty_like(lo)
+    rc = lib().oracle_var_ranges(cells.shape[1], _p(N), _p(cells), _p(ce), _p(cf), _p(cl), _p(lo), _p(hi))
+    if rc != 0:
+        raise ValueError(f"oracle_var_ranges failed: {rc}")
+    return lo, hi, N, ce
+
+
+def number_var(cells: np.ndarray, nverts: int, cell_first, cell_layers, delta,
+               keep_tables: bool = False) -> Space:
+    """Algorithm 1 with a variable number of layers per column."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    delta = tuple(int(x) for x in delta)
+    d = np.array(delta, dtype=np.int32)
+    cf = np.ascontiguousarray(cell_first, dtype=np.int32)
+    cl = np.ascontiguousarray(cell_layers, dtype=np.int32)
+    lo, hi, N, ce = var_ranges(cells, nverts, cf, cl)
+    maxlevel = int((cf + cl).max())
+    nvc = cells.shape[1]
+    L = lib()
+    nul = (ctypes.c_void_p * 6)()
+    if L.oracle_alg1_var(_p(N), maxlevel, _p(lo), _p(hi), _p(d), nul) >= 2**31:
+        raise OverflowError("DoF count does not fit int32")
+    tabs = []
+    ptrs = (ctypes.c_void_p * 6)()
+    for t in range(6):
+        d1, d2 = divmod(t, 2)
+        if delta[t] > 0:
+            a = np.full((int(N[d1]), maxlevel + 1 - d2), -1, dtype=np.int64)
+            tabs.append(a)
+            ptrs[t] = a.ctypes.data
+        else:
+            tabs.append(None)
+            ptrs[t] = None
+    ndofs = L.oracle_alg1_var(_p(N), maxlevel, _p(lo), _p(hi), _p(d), ptrs)
+    k = L.oracle_stencil_size(nvc, _p(d))
+    m = np.empty((cells.shape[0], k), dtype=np.int32)
+    if L.oracle_base_map_var(nvc, cells.shape[0], _p(cells), _p(ce), maxlevel, _p(cf), _p(d), ptrs, _p(m)) != 0:
+        raise ValueError("oracle_base_map_var failed")
+    off = np.empty(k, dtype=np.int32)
+    L.oracle_alg2(nvc, _p(d), _p(off))
+    first = {t: tabs[t] for t in range(6) if tabs[t] is not None} if keep_tables else {}
+    hmap, hoff = _facet_lists(cells, ce, maxlevel, cf, d, ptrs)
+    return Space(delta=delta, layers=maxlevel, ndofs=int(ndofs), k=int(k), map=m, offset=off, first=first,
+                 hmap=hmap, hoffset=hoff, cell_first=cf, cell_layers=cl)
 
 
 def par_loop(kernel: int, cells: np.ndarray, layers: int, args, base_xy: np.ndarray | None = None,
-             ncells: int | None = None) -> None:
+             ncells: int | None = None, cell_first=None, cell_layers=None) -> None:
     """Algorithm 3 over the first ``ncells`` cells (all by default).
 
     ``args`` is a list of (Space, data ndarray float64, ncomp, access[, absdata]).
-    Data arrays are updated in place.
+    Data arrays are updated in place.  With ``cell_first``/``cell_layers``
+    the columns have variable layers and ``layers`` is the highest level.
     """
     cells = np.ascontiguousarray(cells, dtype=np.int32)
     n = cells.shape[0] if ncells is None else int(ncells)
@@ -195,7 +301,13 @@ def par_loop(kernel: int, cells: np.ndarray, layers: int, args, base_xy: np.ndar
         arr[i].absdata = None if absd is None else absd.ctypes.data
         arr[i].access = acc
     xy = None if base_xy is None else np.ascontiguousarray(base_xy, dtype=np.float64)
-    rc = lib().oracle_par_loop(kernel, cells.shape[1], n, layers, _p(cells), _p(xy), len(args), arr)
+    if cell_first is None:
+        rc = lib().oracle_par_loop(kernel, cells.shape[1], n, layers, _p(cells), _p(xy), len(args), arr)
+    else:
+        cf = np.ascontiguousarray(cell_first, dtype=np.int32)
+        cl = np.ascontiguousarray(cell_layers, dtype=np.int32)
+        rc = lib().oracle_par_loop_var(kernel, cells.shape[1], n, _p(cf), _p(cl), layers, _p(cells), _p(xy),
+                                       len(args), arr)
     if rc != 0:
         raise RuntimeError(f"oracle_par_loop failed: {rc}")
 
@@ -230,4 +342,14 @@ def coords(cells: np.ndarray, xy: np.ndarray, layers: int) -> tuple[Space, np.nd
     sp = number(cells, xy.shape[0], layers, DELTA["CG1xCG1"])
     X = np.zeros(sp.ndofs * 3)
     par_loop(K_EXTRUDE, cells, layers, [(sp, X, 3, WRITE)], base_xy=xy)
+    return sp, X
+
+
+def coords_var(cells: np.ndarray, xy: np.ndarray, cell_first, cell_layers) -> tuple[Space, np.ndarray]:
+    """Coordinate space and field of a mesh with variable layers per column
+    (z = level / highest level)."""
+    sp = number_var(cells, xy.shape[0], cell_first, cell_layers, DELTA["CG1xCG1"])
+    X = np.zeros(sp.ndofs * 3)
+    par_loop(K_EXTRUDE, cells, sp.layers, [(sp, X, 3, WRITE)], base_xy=xy,
+             cell_first=sp.cell_first, cell_layers=sp.cell_layers)
     return sp, X

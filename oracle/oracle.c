@@ -150,6 +150,142 @@ void oracle_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Variable layers per column (Sec. 3.1 footnote; Sec. 5: a constant number */
+/* of layers is not needed by the numbering).  Base cell c spans the levels */
+/* cell_first[c] .. cell_first[c] + cell_layers[c]; a vertex or edge column  */
+/* spans the levels from the lowest bottom to the highest top of the cells  */
+/* that contain it.  Entity ranges lo..hi are indexed dimension-major:      */
+/* vertices, then edges, then cells.                                         */
+/* ------------------------------------------------------------------------ */
+int oracle_var_ranges(int32_t nvc, const int64_t N[3], const int32_t *cell_verts,
+                      const int32_t *cell_edges, const int32_t *cell_first,
+                      const int32_t *cell_layers, int32_t *lo, int32_t *hi) {
+  const int64_t nent = N[0] + N[1] + N[2];
+  for (int64_t e = 0; e < nent; ++e) {
+    lo[e] = -1;
+    hi[e] = -1;
+  }
+  for (int64_t c = 0; c < N[2]; ++c) {
+    const int32_t bottom = cell_first[c], top = cell_first[c] + cell_layers[c];
+    if (cell_first[c] < 0 || cell_layers[c] < 1) return -1;
+    for (int d = 0; d <= 2; ++d) {
+      for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+        int64_t id;
+        if (d == 0) id = cell_verts[c * nvc + e];
+        else if (d == 1) {
+          if (!cell_edges) continue;
+          id = N[0] + cell_edges[c * nvc + e];
+        } else id = N[0] + N[1] + c;
+        if (lo[id] < 0 || bottom < lo[id]) lo[id] = bottom;
+        if (hi[id] < 0 || top > hi[id]) hi[id] = top;
+      }
+    }
+  }
+  for (int64_t e = 0; e < N[0]; ++e)
+    if (lo[e] < 0) return -2; /* a vertex that no cell contains */
+  if (cell_edges)
+    for (int64_t e = N[0]; e < N[0] + N[1]; ++e)
+      if (lo[e] < 0) return -2;
+  return 0;
+}
+
+/* Algorithm 1 with per-entity level ranges: the column of entity (d1, i)
+ * holds, for every layer l of its range, the DoFs of ((d1,0),(i,l)) then of
+ * ((d1,1),(i,l)), and last those of the top horizontal entity.  first[t] is
+ * indexed by absolute level: i * (maxlevel + 1 - d2) + l. */
+int64_t oracle_alg1_var(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
+                        const int32_t *hi, const int32_t delta[6], int64_t *const first[6]) {
+  int64_t c = 0, ent = 0;
+  for (int d1 = 0; d1 <= 2; ++d1) {
+    for (int64_t i = 0; i < N[d1]; ++i, ++ent) {
+      for (int32_t l = lo[ent]; l < hi[ent]; ++l) {
+        for (int d2 = 0; d2 <= 1; ++d2) {
+          int t = 2 * d1 + d2;
+          if (first[t]) first[t][i * (maxlevel + 1 - d2) + l] = c;
+          c += delta[t];
+        }
+      }
+      int t = 2 * d1;
+      if (first[t]) first[t][i * (maxlevel + 1) + hi[ent]] = c;
+      c += delta[t];
+    }
+  }
+  return c;
+}
+
+/* Explicit lists L(c) at the bottom layer of each column (level
+ * cell_first[c]), read off the tables of oracle_alg1_var. */
+int oracle_base_map_var(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                        const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                        const int32_t delta[6], int64_t *const first[6], int32_t *map) {
+  int32_t k = oracle_stencil_size(nvc, delta);
+  for (int64_t c = 0; c < ncells; ++c) {
+    const int64_t s = cell_first[c];
+    int32_t j = 0;
+    for (int d = 0; d <= 2; ++d) {
+      for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+        int64_t id;
+        if (d == 0) id = cell_verts[c * nvc + e];
+        else if (d == 1) {
+          if ((delta[2] || delta[3]) && !cell_edges) return -1;
+          id = (delta[2] || delta[3]) ? cell_edges[c * nvc + e] : 0;
+        } else id = c;
+        for (int32_t q = 0; q < delta[2 * d]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s] + q);
+        for (int32_t q = 0; q < delta[2 * d]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s + 1] + q);
+        for (int32_t q = 0; q < delta[2 * d + 1]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d + 1][id * maxlevel + s] + q);
+      }
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Horizontal facets (the (2,0) entities, iterated with d2 = 0 in           */
+/* Algorithm 3).  The explicit list of facet ((2,0),(c,l)) is its closure:  */
+/* per base entity of the cell (vertices, edges, cell) the delta(d,0) DoFs  */
+/* of that entity's horizontal copy at level l.  Algorithm 2's rule gives   */
+/* every facet DoF the offset delta(d,0) + delta(d,1).                      */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_hfacet_size(int32_t nvc, const int32_t delta[6]) {
+  int32_t k = 0;
+  for (int d = 0; d <= 2; ++d) k += nentities(nvc, d) * delta[2 * d];
+  return k;
+}
+
+int oracle_hfacet_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                      const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                      const int32_t delta[6], int64_t *const first[6], int32_t *map) {
+  int32_t k = oracle_hfacet_size(nvc, delta);
+  for (int64_t c = 0; c < ncells; ++c) {
+    const int64_t s = cell_first ? cell_first[c] : 0;
+    int32_t j = 0;
+    for (int d = 0; d <= 2; ++d) {
+      for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+        int64_t id;
+        if (d == 0) id = cell_verts[c * nvc + e];
+        else if (d == 1) {
+          if (delta[2] && !cell_edges) return -1;
+          id = delta[2] ? cell_edges[c * nvc + e] : 0;
+        } else id = c;
+        for (int32_t q = 0; q < delta[2 * d]; ++q)
+          map[c * k + j++] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s] + q);
+      }
+    }
+  }
+  return 0;
+}
+
+void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
+  int32_t i = 0;
+  for (int d = 0; d <= 2; ++d)
+    for (int32_t e = 0; e < nentities(nvc, d); ++e)
+      for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];
+}
+
+/* ------------------------------------------------------------------------ */
 /* Reference elements.                                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -495,26 +631,105 @@ static void k_mass_tp(double *const *vals, double *const *out, double *const *ab
   }
 }
 
+/* Degree-2 rule on the reference triangle (exact for products of two
+ * linear functions), shared by the facet kernels. */
+static const double tri_pts[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+static const double tri_w = 1.0 / 6.0;
+
+/* Area element |dx/dxi x dx/deta| of the flat triangle through P0, P1, P2
+ * (three consecutive 3-vectors at P, stride `stride` doubles). */
+static double tri_area_element(const double *P, int stride) {
+  double e1[3], e2[3];
+  for (int r = 0; r < 3; ++r) {
+    e1[r] = P[stride + r] - P[r];
+    e2[r] = P[2 * stride + r] - P[r];
+  }
+  const double n0 = e1[1] * e2[2] - e1[2] * e2[1];
+  const double n1 = e1[2] * e2[0] - e1[0] * e2[2];
+  const double n2 = e1[0] * e2[1] - e1[1] * e2[0];
+  return sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+}
+
+/* int_F f phi_i ds on a horizontal facet F, for the spaces whose DoFs sit on
+ * horizontal facets (vertical element CG1; horizontal CG1, DG0 or DG1).  The
+ * facet list holds the closure DoFs (CG1: one per vertex; DG0: one; DG1:
+ * three at the vertex positions); the coordinate list holds the facet's three
+ * vertices. */
+static void k_hfacet_mass(double *const *vals, double *const *out, double *const *absv) {
+  const double *X = vals[0], *f = vals[1];
+  const double ds = tri_area_element(X, 3);
+  const int k = g_tp_h == ORC_DG0 ? 1 : 3;
+  for (int q = 0; q < 3; ++q) {
+    double phi[3], fq = 0.0, fa = 0.0;
+    for (int j = 0; j < k; ++j) {
+      phi[j] = (g_tp_h == ORC_DG0) ? 1.0 : tri_lam(j, tri_pts[q][0], tri_pts[q][1]);
+      fq += phi[j] * f[j];
+      fa += fabs(phi[j] * f[j]);
+    }
+    for (int i = 0; i < k; ++i) {
+      out[2][i] += tri_w * ds * fq * phi[i];
+      absv[2][i] += tri_w * ds * fa * fabs(phi[i]);
+    }
+  }
+}
+
+/* Interior horizontal facet between the cell below (first k DoFs of the
+ * two-cell list) and the cell above (last k): the jump term
+ *   r_i += int_F [u] [phi_i] ds,   [w] = w(below, zeta = 1) - w(above, zeta = 0),
+ * on the tensor-product space chosen by oracle_set_tp_element.  The facet is
+ * the top face of the cell below (coordinate DoFs 2a+1 of the first cell). */
+static void k_hfacet_jump(int k, double *const *vals, double *const *out, double *const *absv) {
+  int hfun[27], vfun[27];
+  tp_layout(g_tp_h, g_tp_v, hfun, vfun);
+  const double *X = vals[0], *u = vals[1];
+  const double ds = tri_area_element(X + 3, 6);
+  for (int q = 0; q < 3; ++q) {
+    double pb[27], pa[27], g[3], jump = 0.0, ja = 0.0;
+    for (int j = 0; j < k; ++j) {
+      pb[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 1.0, g);
+      pa[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 0.0, g);
+      jump += u[j] * pb[j] - u[k + j] * pa[j];
+      ja += fabs(u[j] * pb[j]) + fabs(u[k + j] * pa[j]);
+    }
+    for (int i = 0; i < k; ++i) {
+      out[2][i] += tri_w * ds * jump * pb[i];
+      out[2][k + i] -= tri_w * ds * jump * pa[i];
+      absv[2][i] += tri_w * ds * ja * fabs(pb[i]);
+      absv[2][k + i] += tri_w * ds * ja * fabs(pa[i]);
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 3: for every base cell, read its explicit list once; for every */
 /* layer apply the stencil function, then add the vertical offsets.         */
 /* ------------------------------------------------------------------------ */
 #define ORC_MAXARGS 6
-#define ORC_MAXVALS (27 * 3)
+#define ORC_MAXVALS (2 * 27 * 3)
 
-int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
-                    const int32_t *cell_verts, const double *base_xy, int32_t nargs,
-                    const orc_arg *args) {
+/* Cells (d2 = 1) are visited at l = 0 .. lambda_c - 1; horizontal facets
+ * (d2 = 0) at l = 0 .. lambda_c; interior horizontal facets at
+ * l = 1 .. lambda_c - 1 with the two-cell list (L(c), L(c) + offset), which
+ * advances by (offset, offset).  lambda_c = cell_layers[c] (or `layers`), and
+ * level s + l of a column has z = (s + l) / layers with s = cell_first[c]
+ * (or 0). */
+static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
+                         const int32_t *cell_layers, int32_t layers, const int32_t *cell_verts,
+                         const double *base_xy, int32_t nargs, const orc_arg *args) {
   if (nargs < 1 || nargs > ORC_MAXARGS || layers < 1) return -1;
   for (int a = 0; a < nargs; ++a)
     if (args[a].k < 1 || args[a].k > 27 || args[a].ncomp < 1 || args[a].ncomp > 3) return -2;
+  if (kernel == ORC_K_HFACET_MASS && (g_tp_v != ORC_CG1 || nvc != 3)) return -5;
+  if (kernel == ORC_K_HFACET_JUMP && nvc != 3) return -5;
+  const int twocell = kernel == ORC_K_HFACET_JUMP;
   u2v_tab *T = NULL;
   if (kernel == ORC_K_U2V || kernel == ORC_K_U2V_ADJ) {
     T = (u2v_tab *)malloc(sizeof(u2v_tab));
     if (!T) return -3;
     u2v_setup(nvc, T);
   }
-  int64_t dofs[ORC_MAXARGS][27];
+  int64_t dofs[ORC_MAXARGS][2 * 27], offs[ORC_MAXARGS][2 * 27];
+  int kk[ORC_MAXARGS];
   double vbuf[ORC_MAXARGS][ORC_MAXVALS], obuf[ORC_MAXARGS][ORC_MAXVALS], abuf[ORC_MAXARGS][ORC_MAXVALS];
   double *vals[ORC_MAXARGS], *outv[ORC_MAXARGS], *absv[ORC_MAXARGS];
   for (int a = 0; a < ORC_MAXARGS; ++a) {
@@ -522,28 +737,38 @@ int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
     outv[a] = obuf[a];
     absv[a] = abuf[a];
   }
+  for (int a = 0; a < nargs; ++a) {
+    kk[a] = twocell ? 2 * args[a].k : args[a].k;
+    for (int j = 0; j < kk[a]; ++j) offs[a][j] = args[a].offset[j % args[a].k];
+  }
   for (int64_t c = 0; c < ncells; ++c) {
+    const int32_t s = cell_first ? cell_first[c] : 0;
+    const int32_t lam = cell_layers ? cell_layers[c] : layers;
+    int32_t l0 = 0, l1 = lam;                       /* cells: d2 = 1        */
+    if (kernel == ORC_K_HFACET_MASS) l1 = lam + 1;  /* facets: d2 = 0       */
+    if (twocell) l0 = 1;                            /* interior facets only */
     /* (dof_0 .. dof_{k-1}) <- L(v) */
     for (int a = 0; a < nargs; ++a)
-      for (int j = 0; j < args[a].k; ++j) dofs[a][j] = args[a].map[c * args[a].k + j];
-    for (int32_t l = 0; l < layers; ++l) { /* cells: d2 = 1, l = 0 .. lambda-1 */
+      for (int j = 0; j < kk[a]; ++j)
+        dofs[a][j] = args[a].map[c * args[a].k + j % args[a].k] + (j >= args[a].k ? offs[a][j] : 0);
+    for (int32_t l = l0; l < l1; ++l) {
       for (int a = 0; a < nargs; ++a) {
-        int n = args[a].k * args[a].ncomp;
+        int n = kk[a] * args[a].ncomp;
         for (int t = 0; t < n; ++t) obuf[a][t] = abuf[a][t] = 0.0;
         if (args[a].access == ORC_READ)
-          for (int j = 0; j < args[a].k; ++j)
+          for (int j = 0; j < kk[a]; ++j)
             for (int r = 0; r < args[a].ncomp; ++r)
               vbuf[a][j * args[a].ncomp + r] = args[a].data[dofs[a][j] * args[a].ncomp + r];
       }
       switch (kernel) {
         case ORC_K_EXTRUDE: {
-          /* stencil DoF 2a+b of the coordinate space: vertex a, level l+b */
+          /* stencil DoF 2a+b of the coordinate space: vertex a, level s+l+b */
           for (int a = 0; a < nvc; ++a)
             for (int b = 0; b < 2; ++b) {
               int64_t v = cell_verts[c * nvc + a];
               obuf[0][3 * (2 * a + b) + 0] = base_xy[2 * v + 0];
               obuf[0][3 * (2 * a + b) + 1] = base_xy[2 * v + 1];
-              obuf[0][3 * (2 * a + b) + 2] = (double)(l + b) / (double)layers;
+              obuf[0][3 * (2 * a + b) + 2] = (double)(s + l + b) / (double)layers;
             }
           break;
         }
@@ -565,6 +790,12 @@ int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
         case ORC_K_MASS_TP:
           k_mass_tp(vals, outv, absv);
           break;
+        case ORC_K_HFACET_MASS:
+          k_hfacet_mass(vals, outv, absv);
+          break;
+        case ORC_K_HFACET_JUMP:
+          k_hfacet_jump(args[1].k, vals, outv, absv);
+          break;
         default:
           free(T);
           return -4;
@@ -572,7 +803,7 @@ int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
       /* write back */
       for (int a = 0; a < nargs; ++a) {
         if (args[a].access == ORC_READ) continue;
-        for (int j = 0; j < args[a].k; ++j)
+        for (int j = 0; j < kk[a]; ++j)
           for (int r = 0; r < args[a].ncomp; ++r) {
             int64_t g = dofs[a][j] * args[a].ncomp + r;
             int t = j * args[a].ncomp + r;
@@ -586,9 +817,25 @@ int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
       }
       /* dof_j <- dof_j + offset(j) */
       for (int a = 0; a < nargs; ++a)
-        for (int j = 0; j < args[a].k; ++j) dofs[a][j] += args[a].offset[j];
+        for (int j = 0; j < kk[a]; ++j) dofs[a][j] += offs[a][j];
     }
   }
   free(T);
   return 0;
+}
+
+int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
+                    const int32_t *cell_verts, const double *base_xy, int32_t nargs,
+                    const orc_arg *args) {
+  return par_loop_impl(kernel, nvc, ncells, NULL, NULL, layers, cell_verts, base_xy, nargs, args);
+}
+
+int oracle_par_loop_var(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
+                        const int32_t *cell_layers, int32_t maxlevel, const int32_t *cell_verts,
+                        const double *base_xy, int32_t nargs, const orc_arg *args) {
+  if (!cell_first || !cell_layers) return -1;
+  for (int64_t c = 0; c < ncells; ++c)
+    if (cell_first[c] < 0 || cell_layers[c] < 1 || cell_first[c] + cell_layers[c] > maxlevel) return -1;
+  return par_loop_impl(kernel, nvc, ncells, cell_first, cell_layers, maxlevel, cell_verts, base_xy, nargs,
+                       args);
 }

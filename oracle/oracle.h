@@ -28,8 +28,14 @@ enum {
   ORC_K_INTERP = 3,  /* x READ (P1xP1), out WRITE (DG1xDG1): nodal interpolation   */
   ORC_K_U2V = 4,     /* coords READ, u READ, F INC|WRITE: F_i += int u^2 phi_i     */
   ORC_K_U2V_ADJ = 5, /* coords READ, u READ, w READ, g INC|WRITE: (dF/du)^T w      */
-  ORC_K_MASS_TP = 6  /* coords READ, f READ, b INC: b_i += int f phi_i on a prism
+  ORC_K_MASS_TP = 6, /* coords READ, f READ, b INC: b_i += int f phi_i on a prism
                         tensor-product space chosen by oracle_set_tp_element      */
+  ORC_K_HFACET_MASS = 7, /* horizontal facets, l = 0 .. lambda (d2 = 0), facet lists:
+                            coords READ, f READ, b INC: b_i += int_F f phi_i ds;
+                            space (h, CG1) chosen by oracle_set_tp_element         */
+  ORC_K_HFACET_JUMP = 8  /* interior horizontal facets, l = 1 .. lambda-1, two-cell
+                            lists built from the cell lists: coords READ, u READ,
+                            r INC: r_i += int_F [u][phi_i] ds                      */
 };
 
 /* Horizontal / vertical elements of the prism spaces of Sec. 4.1.2. */
@@ -74,6 +80,43 @@ void oracle_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset);
 int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
                     const int32_t *cell_verts, const double *base_xy, int32_t nargs,
                     const orc_arg *args);
+
+/* Variable layers per column: base cell c spans levels cell_first[c] ..
+ * cell_first[c] + cell_layers[c] (cell_layers[c] >= 1).  oracle_var_ranges
+ * writes the level range lo..hi of every base entity (dimension-major index:
+ * vertices, edges, cells; a vertex or edge spans its cells' union hull); it
+ * returns -2 if a vertex or edge belongs to no cell.  cell_edges may be NULL
+ * when no edge carries DoFs (edge ranges are then left at -1). */
+int oracle_var_ranges(int32_t nvc, const int64_t N[3], const int32_t *cell_verts,
+                      const int32_t *cell_edges, const int32_t *cell_first,
+                      const int32_t *cell_layers, int32_t *lo, int32_t *hi);
+
+/* Algorithm 1 over per-entity level ranges; first[t] (t = 2*d1+d2) has
+ * N[d1] x (maxlevel + 1 - d2) entries indexed by absolute level. */
+int64_t oracle_alg1_var(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
+                        const int32_t *hi, const int32_t delta[6], int64_t *const first[6]);
+
+/* Explicit lists at each column's bottom layer (level cell_first[c]). */
+int oracle_base_map_var(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                        const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                        const int32_t delta[6], int64_t *const first[6], int32_t *map);
+
+/* Explicit lists of the horizontal facets at each column's bottom level
+ * (cell_first NULL: level 0): the closure DoFs delta(d,0) of the cell's
+ * vertices, edges and cell at that level; oracle_hfacet_alg2 gives their
+ * offsets by Algorithm 2's rule. */
+int32_t oracle_hfacet_size(int32_t nvc, const int32_t delta[6]);
+int oracle_hfacet_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                      const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                      const int32_t delta[6], int64_t *const first[6], int32_t *map);
+void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset);
+
+/* Algorithm 3 with lambda_c = cell_layers[c] layers in column c, starting at
+ * level cell_first[c]; maxlevel is the highest level (coordinates use
+ * z = level / maxlevel). */
+int oracle_par_loop_var(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
+                        const int32_t *cell_layers, int32_t maxlevel, const int32_t *cell_verts,
+                        const double *base_xy, int32_t nargs, const orc_arg *args);
 
 /* n-point Gauss-Legendre rule on [0,1] (Newton iteration on P_n). */
 void oracle_gauss_legendre(int32_t n, double *x, double *w);

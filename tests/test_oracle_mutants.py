@@ -40,12 +40,37 @@ MUTANTS = {
                        "out[3][j] += T->w[q] * dj * uq * wq * T->phi[q][j];"),
     "adjoint_uses_u_twice": ("out[3][j] += T->w[q] * dj * 2.0 * uq * wq * T->phi[q][j];",
                              "out[3][j] += T->w[q] * dj * 2.0 * uq * uq * T->phi[q][j];"),
-    "extrude_level": ("(double)(l + b) / (double)layers;", "(double)(l) / (double)layers;"),
+    "extrude_level": ("(double)(s + l + b) / (double)layers;", "(double)(s + l) / (double)layers;"),
     "interp_node_swap": ("out[1][2 * a + b] = v;", "out[1][2 * a + (1 - b)] = v;"),
     "tp_dg0_vertical_not_constant": ("else vf = (v == ORC_DG0) ? 2 : beta;", "else vf = (v == ORC_DG0) ? 0 : beta;"),
     "tp_cg1_vertex_shift": ("else if (d == 0) hf = e;  /* CG1 vertex */", "else if (d == 0) hf = (e + 1) % 3;"),
     "tp_bottom_top_same": ("            if (part == 0) vf = 0;", "            if (part == 0) vf = 1;"),
     "mass_wrong_basis": ("out[2][i] += wts[q] * dj * fq * phi[i];", "out[2][i] += wts[q] * dj * fq * phi[(i + 2) % 6];"),
+    # variable layers per column
+    "var_hull_max_bottom": ("if (lo[id] < 0 || bottom < lo[id]) lo[id] = bottom;",
+                            "if (lo[id] < 0 || bottom > lo[id]) lo[id] = bottom;"),
+    "var_top_at_last_layer": ("first[t][i * (maxlevel + 1) + hi[ent]] = c;",
+                              "first[t][i * (maxlevel + 1) + hi[ent] - 1] = c;"),
+    "var_list_at_level_0": ("map[c * k + j++] = (int32_t)(first[2 * d + 1][id * maxlevel + s] + q);",
+                            "map[c * k + j++] = (int32_t)(first[2 * d + 1][id * maxlevel + 0] + q);"),
+    "var_uniform_trip_count": ("const int32_t lam = cell_layers ? cell_layers[c] : layers;",
+                               "const int32_t lam = layers;"),
+    "extrude_ignores_first": ("(double)(s + l + b) / (double)layers;", "(double)(l + b) / (double)layers;"),
+    # horizontal facets
+    "facet_loop_skips_top": ("if (kernel == ORC_K_HFACET_MASS) l1 = lam + 1;", "if (kernel == ORC_K_HFACET_MASS) l1 = lam;"),
+    "facet_offset_horizontal_only": ("for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];",
+                                     "for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d];"),
+    "facet_normal_sign": ("const double n1 = e1[2] * e2[0] - e1[0] * e2[2];",
+                          "const double n1 = e1[2] * e2[0] + e1[0] * e2[2];"),
+    "facet_weight": ("static const double tri_w = 1.0 / 6.0;", "static const double tri_w = 1.0 / 3.0;"),
+    "facet_dg1_wrong_node": ("phi[j] = (g_tp_h == ORC_DG0) ? 1.0 : tri_lam(j, tri_pts[q][0], tri_pts[q][1]);",
+                              "phi[j] = (g_tp_h == ORC_DG0) ? 1.0 : tri_lam(j % 2, tri_pts[q][0], tri_pts[q][1]);"),
+    "jump_sign": ("jump += u[j] * pb[j] - u[k + j] * pa[j];", "jump += u[j] * pb[j] + u[k + j] * pa[j];"),
+    "jump_trace_of_bottom": ("pb[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 1.0, g);",
+                             "pb[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 0.0, g);"),
+    "jump_above_added": ("out[2][k + i] -= tri_w * ds * jump * pa[i];", "out[2][k + i] += tri_w * ds * jump * pa[i];"),
+    "jump_same_cell_twice": ("+ (j >= args[a].k ? offs[a][j] : 0);", "+ 0;"),
+    "jump_base_face": ("const double ds = tri_area_element(X + 3, 6);", "const double ds = tri_area_element(X, 6);"),
 }
 
 
@@ -58,7 +83,9 @@ def _run_pins(source: str, tmp_path):
     env = dict(os.environ, ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_numbering.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_kernels.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_kernels.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_var.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_facets.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r
 
