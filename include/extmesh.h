@@ -90,8 +90,21 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   CG1xDG1 {0,2,..}, DG0xCG1 {..,1,0}, DG0xDG0 {..,0,1},
  *                   DG0xDG1 {..,0,2}, DG1xCG1 {..,3,0}, DG1xDG0 {..,0,3},
  *                   DG1xDG1 {..,0,6}); f and b share one numbering.
+ * EXT_K_HFACET_MASS [coords READ, f READ, b INC] on prisms, over the horizontal
+ *                   facets ((2,0),(c,m)), m = 0..lambda, of every column
+ *                   (Algorithm 3 with d2 = 0): b_i += int_F f_h phi_i ds on the
+ *                   spaces whose DoFs sit on horizontal facets, CG1xCG1, DG0xCG1,
+ *                   DG1xCG1.  A facet's DoFs are the bottom horizontal DoFs of
+ *                   layer m (the top ones of the last layer for m = lambda).
+ * EXT_K_HFACET_JUMP [coords READ, u READ, r INC] on prisms, over the interior
+ *                   horizontal facets m = 1..lambda-1 of every column, each with
+ *                   the two cells it separates: r_i += int_F [u_h] [phi_i] ds,
+ *                   [w] = w(cell below, at the facet) - w(cell above, at the
+ *                   facet), on any of the nine spaces of EXT_K_MASS_TP (zero for
+ *                   the vertically continuous ones); u and r share one numbering.
  * Quadrature: prisms use the 6-point rule (3-point degree-2 triangle rule x
- * 2-point Gauss); hexahedra use 4x4x4 Gauss points. */
+ * 2-point Gauss); hexahedra use 4x4x4 Gauss points; facets are flat triangles
+ * whose P1 surface integrals are evaluated exactly. */
 typedef enum {
   EXT_K_EXTRUDE = 0,
   EXT_K_COPY_DG = 1,
@@ -101,7 +114,9 @@ typedef enum {
   EXT_K_U2V_FWD = 5,
   EXT_K_U2V_ADJ = 6,
   EXT_K_U2V_FWDADJ = 7,
-  EXT_K_MASS_TP = 8
+  EXT_K_MASS_TP = 8,
+  EXT_K_HFACET_MASS = 9,
+  EXT_K_HFACET_JUMP = 10
 } ext_kernel_id;
 
 typedef struct ext_mesh ext_mesh;
@@ -150,8 +165,33 @@ ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,
                            const int32_t *cell_verts_host, const double *base_xy_host,
                            int32_t layers, ext_mesh **out);
 
+/* Creates an extruded mesh whose columns have their own layer ranges: base
+ * cell c spans the levels cell_first_host[c] .. cell_first_host[c] +
+ * cell_layers_host[c] (the paper fixes one lambda for exposition and notes
+ * that this is not a limitation of the method, Sec. 3.1 footnote and Sec. 5).
+ * A vertex or edge column spans the hull of the ranges of the cells containing
+ * it, so Algorithm 1 gives entity columns their own sizes; the numbering
+ * prefix-sums those sizes on the device.  Each cell's stencil list is taken at
+ * its own bottom layer, and a par_loop visits layers 0..cell_layers[c]-1 of
+ * column c.  Entity levels inside the hull that no cell around spans (a gap
+ * between disjoint ranges) are numbered but reached by no stencil.
+ *   cell_first_host   ncells int32 >= 0
+ *   cell_layers_host  ncells int32 >= 1
+ * The highest level first + layers over all cells is reported as the mesh's
+ * `layers` by ext_mesh_info, and EXT_K_EXTRUDE places level l at z = l / that
+ * level.  Other arguments and errors as ext_mesh_create, plus EXT_EINVAL when
+ * a vertex belongs to no cell.  Kernels on such meshes: EXT_K_EXTRUDE,
+ * EXT_K_COPY_DG, EXT_K_RHS_P1P1, EXT_K_MASS_P1P1, EXT_K_INTERP_DG1,
+ * EXT_K_MASS_TP, EXT_K_HFACET_MASS, EXT_K_HFACET_JUMP (others, and batches,
+ * return EXT_EUNSUPPORTED). */
+ext_status ext_mesh_create_var(int32_t kind, int64_t nverts, int64_t ncells,
+                               const int32_t *cell_verts_host, const double *base_xy_host,
+                               const int32_t *cell_first_host, const int32_t *cell_layers_host,
+                               ext_mesh **out);
+
 /* Entity counts N_0, N_1, N_2 (vertices, edges, cells) of the base mesh, the
- * cell kind and the number of layers (Sec. 2.2, 3.1). */
+ * cell kind and the number of layers (Sec. 2.2, 3.1); for a mesh with
+ * variable layers, the highest level. */
 ext_status ext_mesh_info(const ext_mesh *mesh, int32_t *kind, int64_t n[3], int32_t *layers);
 
 void ext_mesh_destroy(ext_mesh *mesh);

@@ -196,3 +196,27 @@ def batched_params(count: int = 64, seed: int = 1605, cmin: float = 1e4, cmax: f
     n = [max(1, int(round(math.sqrt(x / 2.0)))) for x in c]
     layers = [int(v) for v in rng.integers(lmin, lmax + 1, size=count)]
     return BatchedParams(n=n, layers=layers, seed=seed)
+
+
+def column_layers(m: BaseMesh, maxlevel: int, seed: int, kind: str = "bathymetry") -> tuple[np.ndarray, np.ndarray]:
+    """Per-column layer ranges (first level, layer count), int32, for meshes
+    with a variable number of layers per column.
+
+    ``bathymetry``: a smooth depth field d(x, y) in [0.15, 0.95] over the
+    base (evaluated at cell centroids); column c has round(d * maxlevel)
+    layers (at least 1) hanging from a flat top at ``maxlevel`` (an ocean-like
+    terrain-following layout, so neighbouring columns overlap and no entity
+    column has a gap).  ``random``: independent random ranges inside
+    [0, maxlevel], which may leave gaps between neighbouring columns."""
+    rng = np.random.default_rng(seed)
+    if kind == "random":
+        first = rng.integers(0, maxlevel, m.ncells)
+        lay = 1 + rng.integers(0, maxlevel - first)
+        return first.astype(np.int32), lay.astype(np.int32)
+    if kind != "bathymetry":
+        raise ValueError(kind)
+    ph = rng.uniform(0.0, 2.0 * np.pi, 2)
+    cxy = m.xy[m.cells].mean(axis=1)
+    depth = 0.55 + 0.4 * np.sin(3.0 * cxy[:, 0] + ph[0]) * np.cos(2.0 * cxy[:, 1] + ph[1])
+    lay = np.clip(np.rint(depth * maxlevel), 1, maxlevel).astype(np.int32)
+    return (maxlevel - lay).astype(np.int32), lay

@@ -20,7 +20,7 @@ STATUS_NAMES = ["EXT_OK", "EXT_EINVAL", "EXT_ENOMEM", "EXT_ECUDA", "EXT_EOVERFLO
 EXT_TRI, EXT_QUAD = 3, 4
 EXT_READ, EXT_WRITE, EXT_INC = 0, 1, 2
 (EXT_K_EXTRUDE, EXT_K_COPY_DG, EXT_K_RHS_P1P1, EXT_K_MASS_P1P1, EXT_K_INTERP_DG1, EXT_K_U2V_FWD,
- EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ, EXT_K_MASS_TP) = range(9)
+ EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ, EXT_K_MASS_TP, EXT_K_HFACET_MASS, EXT_K_HFACET_JUMP) = range(11)
 
 
 class ExtError(RuntimeError):
@@ -51,6 +51,7 @@ def _load():
         "ext_abi_version": (i32, []),
         "ext_last_error": (ctypes.c_char_p, []),
         "ext_mesh_create": (ctypes.c_int, [i32, i64, i64, vp, vp, i32, ctypes.POINTER(vp)]),
+        "ext_mesh_create_var": (ctypes.c_int, [i32, i64, i64, vp, vp, vp, vp, ctypes.POINTER(vp)]),
         "ext_mesh_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "ext_mesh_destroy": (None, [vp]),
         "ext_number_dofs": (ctypes.c_int, [vp, vp, i32, vp, ctypes.POINTER(vp)]),
@@ -124,6 +125,21 @@ def ext_mesh_create(kind: int, nverts: int, ncells: int, cell_verts, base_xy, la
     out = ctypes.c_void_p()
     _check(lib.ext_mesh_create(kind, nverts, ncells, _ptr(cv) if cv.size else None,
                                None if xy is None else _ptr(xy), layers, ctypes.byref(out)))
+    return out.value
+
+
+def ext_mesh_create_var(kind: int, nverts: int, ncells: int, cell_verts, base_xy, cell_first,
+                        cell_layers) -> int:
+    cv = np.ascontiguousarray(cell_verts, dtype=np.int32)
+    xy = None if base_xy is None else np.ascontiguousarray(base_xy, dtype=np.float64)
+    cf = np.ascontiguousarray(cell_first, dtype=np.int32)
+    cl = np.ascontiguousarray(cell_layers, dtype=np.int32)
+    if cf.shape != (ncells,) or cl.shape != (ncells,):
+        raise ValueError("cell_first and cell_layers need one entry per base cell")
+    out = ctypes.c_void_p()
+    _check(lib.ext_mesh_create_var(kind, nverts, ncells, _ptr(cv) if cv.size else None,
+                                   None if xy is None else _ptr(xy), _ptr(cf) if cf.size else None,
+                                   _ptr(cl) if cl.size else None, ctypes.byref(out)))
     return out.value
 
 

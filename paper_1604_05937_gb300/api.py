@@ -32,14 +32,23 @@ def _torch():
 
 class Mesh:
     """Extruded mesh: base cells (C, 3|4) int32, optional base coordinates
-    (V, 2) float64, and the number of layers."""
+    (V, 2) float64, and the number of layers: an int, or per-column
+    ``cell_first``/``cell_layers`` arrays for variable layers (then
+    ``layers`` is ignored and reports the highest level)."""
 
-    def __init__(self, cells, xy=None, layers: int = 1, nverts: int | None = None):
+    def __init__(self, cells, xy=None, layers: int = 1, nverts: int | None = None, cell_first=None,
+                 cell_layers=None):
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         if cells.ndim != 2 or cells.shape[1] not in (3, 4):
             raise ValueError("cells must be (C, 3) or (C, 4)")
         nv = int(xy.shape[0]) if xy is not None else int(nverts if nverts is not None else cells.max() + 1)
-        self.handle = A.ext_mesh_create(cells.shape[1], nv, cells.shape[0], cells, xy, layers)
+        if cell_layers is not None:
+            first = np.zeros(cells.shape[0], np.int32) if cell_first is None else cell_first
+            self.handle = A.ext_mesh_create_var(cells.shape[1], nv, cells.shape[0], cells, xy, first, cell_layers)
+            self.variable = True
+        else:
+            self.handle = A.ext_mesh_create(cells.shape[1], nv, cells.shape[0], cells, xy, layers)
+            self.variable = False
         self.kind, self.N, self.layers = A.ext_mesh_info(self.handle)
 
     @property

@@ -92,16 +92,37 @@ static void free_mesh(ext_mesh *m) {
   cudaFree(m->d_cell_verts);
   cudaFree(m->d_cell_edges);
   cudaFree(m->d_base_xy);
+  cudaFree(m->d_cell_first);
+  cudaFree(m->d_cell_layers);
+  cudaFree(m->d_ent_lo);
+  cudaFree(m->d_ent_hi);
   delete reinterpret_cast<ext_mesh_host *>(m->host);
   delete m;
 }
 
-extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,
-                                      const int32_t *cell_verts_host, const double *base_xy_host,
-                                      int32_t layers, ext_mesh **out) {
+// Shared by ext_mesh_create and ext_mesh_create_var (first/lay non-null:
+// variable layers, `layers` ignored).
+static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, const int32_t *cell_verts_host,
+                              const double *base_xy_host, int32_t layers, const int32_t *first,
+                              const int32_t *lay, ext_mesh **out) {
   if (!out) return ext_fail(EXT_EINVAL, "ext_mesh_create: out is NULL");
   *out = nullptr;
   if (kind != EXT_TRI && kind != EXT_QUAD) return ext_fail(EXT_EINVAL, "ext_mesh_create: kind must be 3 or 4");
+  const bool var = first != nullptr;
+  double mean = 0.0;
+  if (var) {
+    if (ncells > 0 && !lay) return ext_fail(EXT_EINVAL, "ext_mesh_create_var: cell_layers is NULL");
+    int64_t top = 1, sum = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+      if (first[c] < 0 || lay[c] < 1 || (int64_t)first[c] + lay[c] >= (int64_t)1 << 30)
+        return ext_fail(EXT_EINVAL, "ext_mesh_create_var: cell %lld has first %d, layers %d", (long long)c,
+                        first[c], lay[c]);
+      top = std::max(top, (int64_t)first[c] + lay[c]);
+      sum += lay[c];
+    }
+    layers = (int32_t)top;
+    mean = ncells > 0 ? (double)sum / (double)ncells : 1.0;
+  }
   if (layers < 1) return ext_fail(EXT_EINVAL, "ext_mesh_create: layers must be >= 1 (got %d)", layers);
   if (nverts < 0 || ncells < 0) return ext_fail(EXT_EINVAL, "ext_mesh_create: negative count");
   if (nverts >= INT32_MAX || ncells * kind >= INT32_MAX)
@@ -127,6 +148,13 @@ extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncel
           return ext_fail(EXT_EINVAL, "ext_mesh_create: cell %lld is clockwise, non-convex or degenerate", (long long)c);
       }
     }
+  }
+  if (var) {
+    std::vector<char> used((size_t)nverts, 0);
+    for (int64_t t = 0; t < ncells * kind; ++t) used[(size_t)cell_verts_host[t]] = 1;
+    for (int64_t v = 0; v < nverts; ++v)
+      if (!used[(size_t)v])
+        return ext_fail(EXT_EINVAL, "ext_mesh_create_var: vertex %lld belongs to no cell", (long long)v);
   }
   std::vector<int32_t> ce;
   const int64_t nedges = derive_edges(kind, ncells, cell_verts_host, ce);
@@ -154,6 +182,20 @@ extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncel
       e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->has_xy = base_xy_host != nullptr;
+  if (e == cudaSuccess && var) {
+    m->var = true;
+    m->mean_layers = mean;
+    const int64_t nent = nverts + nedges + ncells;
+    const size_t cb = sizeof(int32_t) * (size_t)std::max<int64_t>(ncells, 1);
+    const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nent, 1);
+    if ((e = cudaMalloc(&m->d_cell_first, cb)) == cudaSuccess && (e = cudaMalloc(&m->d_cell_layers, cb)) == cudaSuccess &&
+        (e = cudaMalloc(&m->d_ent_lo, eb)) == cudaSuccess && (e = cudaMalloc(&m->d_ent_hi, eb)) == cudaSuccess &&
+        ncells > 0 &&
+        (e = cudaMemcpy(m->d_cell_first, first, sizeof(int32_t) * ncells, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(m->d_cell_layers, lay, sizeof(int32_t) * ncells, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = launch_var_ranges(m, 0)) == cudaSuccess)
+      e = cudaStreamSynchronize(0);
+  }
   if (e != cudaSuccess) {
     free_mesh(m);
     return ext_fail(e == cudaErrorMemoryAllocation ? EXT_ENOMEM : EXT_ECUDA, "ext_mesh_create: %s",
@@ -161,6 +203,25 @@ extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncel
   }
   *out = m;
   return EXT_OK;
+}
+
+extern "C" ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,
+                                      const int32_t *cell_verts_host, const double *base_xy_host,
+                                      int32_t layers, ext_mesh **out) {
+  return create_mesh(kind, nverts, ncells, cell_verts_host, base_xy_host, layers, nullptr, nullptr, out);
+}
+
+extern "C" ext_status ext_mesh_create_var(int32_t kind, int64_t nverts, int64_t ncells,
+                                          const int32_t *cell_verts_host, const double *base_xy_host,
+                                          const int32_t *cell_first_host, const int32_t *cell_layers_host,
+                                          ext_mesh **out) {
+  if (!cell_first_host && ncells > 0) {
+    if (out) *out = nullptr;
+    return ext_fail(EXT_EINVAL, "ext_mesh_create_var: cell_first is NULL");
+  }
+  static const int32_t none = 0;
+  return create_mesh(kind, nverts, ncells, cell_verts_host, base_xy_host, 1,
+                     cell_first_host ? cell_first_host : &none, cell_layers_host, out);
 }
 
 extern "C" ext_status ext_mesh_info(const ext_mesh *mesh, int32_t *kind, int64_t n[3], int32_t *layers) {
@@ -207,9 +268,38 @@ extern "C" ext_status ext_number_dofs(ext_mesh *mesh, const int32_t delta_host[6
     nl.block_start[d] = start;
     start += mesh->N[d] * nl.colsize[d];
   }
-  const int64_t ndofs = start;
-  if (ndofs >= INT32_MAX || ndofs * ncomp >= INT32_MAX || mesh->N[2] * k >= INT32_MAX)
+  int64_t ndofs = start;
+  // Variable layers: entity column sizes from the entities' level ranges,
+  // prefix-summed on the device into column starts (Algorithm 1's counter).
+  int64_t *d_starts = nullptr, *d_scratch = nullptr;
+  if (mesh->var) {
+    const int64_t nent = mesh->N[0] + mesh->N[1] + mesh->N[2];
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc(&d_starts, sizeof(int64_t) * (nent + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_scratch, sizeof(int64_t) * scan_scratch_elems(nent));
+    if (e == cudaSuccess) e = launch_var_colsize(mesh, delta_host, d_starts, st);
+    if (e == cudaSuccess) e = launch_scan_i64(d_starts, nent, d_scratch, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ndofs, d_starts + nent, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(d_starts);
+      cudaFree(d_scratch);
+      return ext_fail(e == cudaErrorMemoryAllocation ? EXT_ENOMEM : EXT_ECUDA, "ext_number_dofs: %s",
+                      cudaGetErrorString(e));
+    }
+    nl.ent_start = d_starts;
+    nl.ent_lo = mesh->d_ent_lo;
+    nl.cell_first = mesh->d_cell_first;
+    nl.ent_base[0] = 0;
+    nl.ent_base[1] = mesh->N[0];
+    nl.ent_base[2] = mesh->N[0] + mesh->N[1];
+    for (int d = 0; d < 3; ++d) nl.colstep[d] = delta_host[2 * d] + delta_host[2 * d + 1];
+  }
+  if (ndofs >= INT32_MAX || ndofs * ncomp >= INT32_MAX || mesh->N[2] * k >= INT32_MAX) {
+    cudaFree(d_starts);
+    cudaFree(d_scratch);
     return ext_fail(EXT_EOVERFLOW, "ext_number_dofs: %lld DoFs do not fit int32 indices", (long long)ndofs);
+  }
 
   ext_space *s = new ext_space();
   s->mesh = mesh;
@@ -249,6 +339,8 @@ extern "C" ext_status ext_number_dofs(ext_mesh *mesh, const int32_t delta_host[6
   nl.map = s->d_map;
   if (e == cudaSuccess) e = launch_number(nl, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(d_starts);
+  cudaFree(d_scratch);
   if (e != cudaSuccess) {
     cudaFree(s->d_map);
     cudaFree(s->d_offset);
@@ -372,6 +464,8 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.map = args[0].space->d_map;
       p.off = args[0].space->h_offset[0];
       p.X = (double *)args[0].data;
+      p.cell_first = mesh->d_cell_first;
+      p.cell_layers = mesh->d_cell_layers;
       e = launch_extrude(p, s);
       break;
     }
@@ -389,6 +483,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.map = args[0].space->d_map;
       p.in = (const double *)args[0].data;
       p.out = (double *)args[1].data;
+      p.cell_layers = mesh->d_cell_layers;
       e = launch_copy_dg(p, s);
       break;
     }
@@ -415,6 +510,8 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.f = (const double *)args[1].data;
       p.b = (double *)args[2].data;
       p.err = ext_device_error_word();
+      p.cell_layers = mesh->d_cell_layers;
+      p.mean_layers = mesh->mean_layers;
       e = launch_mass_p1(p, s);
       break;
     }
@@ -434,6 +531,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.x = (const double *)args[0].data;
       p.out = (double *)args[1].data;
       if ((((uintptr_t)p.out) & 15) != 0) return ext_fail(EXT_EINVAL, "%s: output data must be 16-byte aligned", kn);
+      p.cell_layers = mesh->d_cell_layers;
       e = launch_interp_dg1(p, s);
       break;
     }
@@ -444,6 +542,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
                                                   : (kernel_id == EXT_K_U2V_ADJ ? "EXT_K_U2V_ADJ" : "EXT_K_U2V_FWDADJ");
       const int mode = kernel_id == EXT_K_U2V_FWD ? 1 : (kernel_id == EXT_K_U2V_ADJ ? 2 : 3);
       const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
+      if (mesh->var) return ext_fail(EXT_EUNSUPPORTED, "%s: not available on meshes with variable layers", kn);
       if (nargs != want) return ext_fail(EXT_EINVAL, "%s: expects %d arguments", kn, want);
       EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
       const ext_space *us = args[1].space;
@@ -515,7 +614,54 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.X = (const double *)args[0].data;
       p.f = (const double *)args[1].data;
       p.b = (double *)args[2].data;
+      p.cell_layers = mesh->d_cell_layers;
+      p.mean_layers = mesh->mean_layers;
       e = launch_mass_tp(p, s);
+      break;
+    }
+    case EXT_K_HFACET_MASS:
+    case EXT_K_HFACET_JUMP: {
+      const bool jump = kernel_id == EXT_K_HFACET_JUMP;
+      const char *kn = jump ? "EXT_K_HFACET_JUMP" : "EXT_K_HFACET_MASS";
+      if (mesh->kind != EXT_TRI) return ext_fail(EXT_EINVAL, "%s: needs a triangular base mesh", kn);
+      if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, -1, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 2, kn, -1, 1, EXT_INC));
+      if (!same_numbering(args[1].space, args[2].space))
+        return ext_fail(EXT_EINVAL, "%s: input and output must share one numbering", kn);
+      int h = 0, v = 0;
+      if (prism_pair(args[1].space->delta, &h, &v) < 0)
+        return ext_fail(EXT_EUNSUPPORTED, "%s: not one of the nine CG1/DG0/DG1 prism spaces", kn);
+      if (!jump && v != 0)
+        return ext_fail(EXT_EINVAL, "%s: the space has no DoFs on horizontal facets (vertical element must be CG1)", kn);
+      FacetLaunch p;
+      memset(&p, 0, sizeof(p));
+      p.ncells = C;
+      p.layers = L;
+      p.nh = h == 1 ? 1 : 3;
+      p.jump = jump ? 1 : 0;
+      const int nv = v == 1 ? 1 : 2;
+      int32_t slot[6];
+      prism_pair_slots(h, v, p.nh, nv, slot);
+      for (int a = 0; a < p.nh; ++a) {
+        // facet mass: bottom / top slot of node a; jump: the trace from the
+        // cell below (its top node, or its only vertical node) and from above
+        p.slot_lo[a] = slot[a * nv + (nv == 2 && jump ? 1 : 0)];
+        p.slot_hi[a] = slot[a * nv + (nv == 2 && !jump ? 1 : 0)];
+        p.off_lo[a] = args[1].space->h_offset[p.slot_lo[a]];
+        p.off_hi[a] = args[1].space->h_offset[p.slot_hi[a]];
+      }
+      p.k = args[1].space->k;
+      p.cmap = args[0].space->d_map;
+      for (int i = 0; i < 6; ++i) p.coff[i] = args[0].space->h_offset[i];
+      p.fmap = args[1].space->d_map;
+      p.X = (const double *)args[0].data;
+      p.f = (const double *)args[1].data;
+      p.b = (double *)args[2].data;
+      p.cell_layers = mesh->d_cell_layers;
+      p.mean_layers = mesh->mean_layers;
+      e = launch_facet(p, s);
       break;
     }
     default:
@@ -708,6 +854,7 @@ extern "C" ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *mes
     const ext_mesh *m = meshes[mi];
     const ext_arg *a = args + (size_t)mi * nargs;
     if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d: prisms only", mi);
+    if (m->var) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d has variable layers", mi);
     EXT_CHECK(check_arg(m, a, 0, "ext_batch_create", ELEM_P1P1, 3, EXT_READ));
     for (int j = 1; j < nargs; ++j) {
       const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);
@@ -851,6 +998,7 @@ ext_status ext_batch_validate(int32_t nmesh, const ext_mesh *const *meshes, int3
     const ext_mesh *m = meshes[mi];
     const ext_arg *a = args + (size_t)mi * nargs;
     if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d: prisms only", mi);
+    if (m->var) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d has variable layers", mi);
     EXT_CHECK(check_arg(m, a, 0, "batched launch", ELEM_P1P1, 3, EXT_READ));
     for (int j = 1; j < nargs; ++j) {
       const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);

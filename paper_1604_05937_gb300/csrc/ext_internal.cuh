@@ -30,12 +30,19 @@ enum ElemKind : int {
 struct ext_mesh {
   int32_t kind;        // vertices per base cell (3 or 4)
   int64_t N[3];        // base entity counts: vertices, edges, cells
-  int32_t layers;      // lambda
+  int32_t layers;      // lambda; with variable layers the highest level
   int device;
   int32_t *d_cell_verts = nullptr;  // ncells x kind
   int32_t *d_cell_edges = nullptr;  // ncells x kind
   double *d_base_xy = nullptr;      // nverts x 2 (may be null)
   bool has_xy = false;              // base coordinates were given
+  // variable layers per column: cell c spans levels first[c] .. first[c] + layers[c]
+  bool var = false;
+  int32_t *d_cell_first = nullptr;   // ncells
+  int32_t *d_cell_layers = nullptr;  // ncells
+  int32_t *d_ent_lo = nullptr;       // level range of every base entity,
+  int32_t *d_ent_hi = nullptr;       // dimension-major (vertices, edges, cells)
+  double mean_layers = 0.0;
   void *host = nullptr;             // host-side copies (ext_api.cu)
 };
 
@@ -71,8 +78,22 @@ struct NumberLaunch {
   int32_t slot_add[EXT_MAXK];  // position inside the column at layer 0
   const int32_t *cell_verts, *cell_edges;
   int32_t *map;
+  // variable layers: entity column starts (dimension-major global entity
+  // index), entity bottom levels, the cells' bottom levels; null otherwise
+  const int64_t *ent_start = nullptr;
+  const int32_t *ent_lo = nullptr, *cell_first = nullptr;
+  int64_t ent_base[3];   // global index of the first entity of dimension d
+  int32_t colstep[3];    // delta(d,0) + delta(d,1)
 };
 cudaError_t launch_number(const NumberLaunch &p, cudaStream_t s);
+
+// Variable layers (k_number.cu, k_scan.cu): entity level ranges from the
+// cells' ranges, entity column sizes, and an exclusive int64 prefix sum with
+// the total written to data[n].
+cudaError_t launch_var_ranges(const ext_mesh *m, cudaStream_t s);
+cudaError_t launch_var_colsize(const ext_mesh *m, const int32_t delta[6], int64_t *sizes, cudaStream_t s);
+cudaError_t launch_scan_i64(int64_t *data, int64_t n, int64_t *scratch, cudaStream_t s);
+int64_t scan_scratch_elems(int64_t n);
 
 struct ExtrudeLaunch {
   int64_t ncells;
@@ -82,6 +103,7 @@ struct ExtrudeLaunch {
   const int32_t *map;  // coords space, k = 2 nvc
   int32_t off;         // vertical offset of every slot (1 for CG1xCG1)
   double *X;
+  const int32_t *cell_first = nullptr, *cell_layers = nullptr;  // variable layers
 };
 cudaError_t launch_extrude(const ExtrudeLaunch &p, cudaStream_t s);
 
@@ -92,6 +114,7 @@ struct CopyDGLaunch {
   const int32_t *map;
   const double *in;
   double *out;
+  const int32_t *cell_layers = nullptr;  // variable layers
 };
 cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s);
 
@@ -103,6 +126,7 @@ struct InterpDG1Launch {
   const int32_t *omap;  // DG1xDG1 map, k = 6
   const double *x;
   double *out;
+  const int32_t *cell_layers = nullptr;  // variable layers
 };
 cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s);
 
@@ -115,6 +139,8 @@ struct MassP1Launch {
   const double *X, *f;
   double *b;
   unsigned int *err;
+  const int32_t *cell_layers = nullptr;  // variable layers
+  double mean_layers = 0.0;
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 
@@ -132,8 +158,36 @@ struct MassTPLaunch {
   double scale;          // 1/2 x (1/12 if nh = 3) x (1/6 if nv = 2)
   const double *X, *f;
   double *b;
+  const int32_t *cell_layers = nullptr;  // variable layers
+  double mean_layers = 0.0;
 };
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
+
+// Horizontal-facet loops (k_facet.cu).  Facet m of a column (m = 0..lambda)
+// reads the bottom stencil slots at layer m, or the top slots of the last
+// layer for m = lambda.  FACET_MASS: b_a += int_F f phi_a ds on a space
+// (h, CG1); FACET_JUMP: r += int_F [u][phi] ds over the interior facets
+// m = 1..lambda-1 on a prism tensor-product space.
+struct FacetLaunch {
+  int64_t ncells;
+  int32_t layers;
+  int32_t nh;             // horizontal nodes: 1 (DG0) or 3 (CG1, DG1)
+  int32_t jump;           // 0: facet mass, 1: interior-facet jump
+  const int32_t *cmap;    // coords map (k = 6)
+  int32_t coff[6];
+  const int32_t *fmap;    // f/u and b/r share this numbering
+  int32_t k;
+  // facet mass: slot of node a at the bottom (lo) and top (hi) of a layer
+  // jump: slot of node a's trace from below (lo: top of the cell under the
+  // facet) and from above (hi: bottom of the cell over it)
+  int32_t slot_lo[3], slot_hi[3];
+  int32_t off_lo[3], off_hi[3];
+  const double *X, *f;
+  double *b;
+  const int32_t *cell_layers = nullptr;  // variable layers
+  double mean_layers = 0.0;
+};
+cudaError_t launch_facet(const FacetLaunch &p, cudaStream_t s);
 
 // u^2 v residual and adjoint (k_u2v.cu): prisms (P1 x P1) and hexahedra (Q2 x P2, DG2).
 struct U2VLaunch {

@@ -155,6 +155,135 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1_tile(const InterpDG1Lau
   }
 }
 
+// ---------------------------------------------------------------------------
+// Variable layers: column c has layers[c] layers, so a CTA tile of TILE
+// consecutive columns first forms the prefix sums pre[0..ncol] of its
+// columns' unit counts (elements for the copy, pairs for the interpolation)
+// in shared memory; a flattened unit index v of the tile then belongs to the
+// column cl with pre[cl] <= v < pre[cl + 1] (binary search).
+
+template <int TILE>
+__device__ void tile_prefix(const int32_t *lay, int64_t c0, int ncol, uint32_t per_layer, uint32_t *pre,
+                            uint32_t *wsum) {
+  static_assert(TILE % 32 == 0 && TILE <= kThreads, "tile must be whole warps of the CTA");
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  uint32_t x = 0;
+  if (t < TILE) {
+    x = t < ncol ? (uint32_t)__ldg(lay + c0 + t) * per_layer : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+  }
+  __syncthreads();
+  if (t < TILE) {
+    uint32_t add = 0;
+    for (int j = 0; j < w; ++j) add += wsum[j];
+    pre[t + 1] = x + add;
+  }
+  if (t == 0) pre[0] = 0;
+  __syncthreads();
+}
+
+template <int TILE>
+__device__ __forceinline__ int tile_find(const uint32_t *pre, int ncol, uint32_t v) {
+  int lo = 0, hi = ncol;  // pre[lo] <= v < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int TILE, int UNROLL>
+__global__ void __launch_bounds__(kThreads) k_copy_dg_var(const CopyDGLaunch p, int64_t ntiles) {
+  __shared__ uint32_t pre[TILE + 1];
+  __shared__ uint32_t wsum[TILE / 32];
+  __shared__ int32_t base[TILE];
+  __shared__ int contiguous;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c0 = tile * TILE;
+    const int ncol = (int)(p.ncells - c0 < TILE ? p.ncells - c0 : TILE);
+    __syncthreads();  // the previous tile's readers are done
+    if (threadIdx.x == 0) contiguous = 1;
+    for (int i = threadIdx.x; i < ncol; i += kThreads) base[i] = __ldg(p.map + (c0 + i) * p.k);
+    tile_prefix<TILE>(p.cell_layers, c0, ncol, (uint32_t)p.k, pre, wsum);
+    // columns numbered back to back (as Algorithm 1 numbers a cell-interior
+    // space) make the tile one range: no search
+    for (int i = threadIdx.x; i < ncol; i += kThreads)
+      if ((uint32_t)(base[i] - base[0]) != pre[i]) contiguous = 0;
+    __syncthreads();
+    const uint32_t total = pre[ncol];
+    const bool flat = contiguous != 0;
+    for (uint32_t v = threadIdx.x; v < total; v += UNROLL * kThreads) {
+      double val[UNROLL];
+      uint32_t dst[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < total) {
+          if (flat) {
+            dst[u] = (uint32_t)base[0] + vv;
+          } else {
+            const int cl = tile_find<TILE>(pre, ncol, vv);
+            dst[u] = (uint32_t)base[cl] + (vv - pre[cl]);
+          }
+          val[u] = __ldcs(p.in + dst[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < total) __stcs(p.out + dst[u], val[u]);
+      }
+    }
+  }
+}
+
+template <int TILE, int UNROLL>
+__global__ void __launch_bounds__(kThreads) k_interp_dg1_var(const InterpDG1Launch p, FastDiv three,
+                                                             int64_t ntiles) {
+  __shared__ uint32_t pre[TILE + 1];
+  __shared__ uint32_t wsum[TILE / 32];
+  __shared__ int32_t xrow[TILE][6];
+  __shared__ int32_t obase[TILE];
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c0 = tile * TILE;
+    const int ncol = (int)(p.ncells - c0 < TILE ? p.ncells - c0 : TILE);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol * 6; i += kThreads) xrow[i / 6][i % 6] = __ldg(p.xmap + c0 * 6 + i);
+    for (int i = threadIdx.x; i < ncol; i += kThreads) obase[i] = __ldg(p.omap + (c0 + i) * 6);
+    tile_prefix<TILE>(p.cell_layers, c0, ncol, 3u, pre, wsum);  // three pairs per layer
+    const uint32_t npairs = pre[ncol];
+    for (uint32_t v = threadIdx.x; v < npairs; v += UNROLL * kThreads) {
+      double2 val[UNROLL];
+      uint32_t dst[UNROLL];
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < npairs) {
+          const int cl = tile_find<TILE>(pre, ncol, vv);
+          const uint32_t q = vv - pre[cl];  // pair within the column: 3 l + a
+          const uint32_t l = fdiv(q, three);
+          const uint32_t a = q - 3u * l;
+          const double lo = __ldg(p.x + (uint32_t)xrow[cl][2 * a] + l * (uint32_t)p.xoff);
+          const double hi = __ldg(p.x + (uint32_t)xrow[cl][2 * a + 1] + l * (uint32_t)p.xoff);
+          val[u] = make_double2(lo, hi);
+          dst[u] = (uint32_t)obase[cl] + 2u * q;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t vv = v + u * kThreads;
+        if (vv < npairs) st_stream2(p.out + dst[u], val[u]);
+      }
+    }
+  }
+}
+
 unsigned grid_for(uint64_t work, int per_thread) {
   uint64_t blocks = (work + (uint64_t)kThreads * per_thread - 1) / ((uint64_t)kThreads * per_thread);
   const uint64_t cap = 152ull * 16;  // 16 resident CTAs per SM is plenty for a stream
@@ -166,6 +295,13 @@ unsigned grid_for(uint64_t work, int per_thread) {
 }  // namespace
 
 cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s) {
+  if (p.cell_layers) {
+    if (p.ncells == 0) return cudaSuccess;
+    const int64_t ntiles = (p.ncells + 127) / 128;
+    const int64_t grid = ntiles < 152 * 8 ? ntiles : 152 * 8;
+    k_copy_dg_var<128, 8><<<(unsigned)grid, kThreads, 0, s>>>(p, ntiles);
+    return cudaGetLastError();
+  }
   const uint64_t colsize = (uint64_t)p.k * p.layers;
   const uint64_t n = colsize * (uint64_t)p.ncells;
   if (n == 0) return cudaSuccess;
@@ -181,6 +317,13 @@ cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s) {
 }
 
 cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s) {
+  if (p.cell_layers) {
+    if (p.ncells == 0) return cudaSuccess;
+    const int64_t ntiles = (p.ncells + 127) / 128;
+    const int64_t grid = ntiles < 152 * 8 ? ntiles : 152 * 8;
+    k_interp_dg1_var<128, EXT_INTERP_UNROLL><<<(unsigned)grid, kThreads, 0, s>>>(p, make_fastdiv(3u), ntiles);
+    return cudaGetLastError();
+  }
   const uint64_t colsize = 6ull * p.layers;
   const uint64_t n = colsize * (uint64_t)p.ncells;
   if (n == 0) return cudaSuccess;

@@ -1,0 +1,190 @@
+// Horizontal-facet par_loops: Algorithm 3 with d2 = 0, i.e. over the facets
+// ((2,0),(c,m)) of each column at levels m = 0..lambda, and its interior form
+// over the facets m = 1..lambda-1 shared by the layers m-1 and m.
+//
+//   FACET_MASS  b_a += int_F f phi_a ds      on a space (CG1|DG0|DG1) x CG1,
+//               whose facet DoFs are the bottom horizontal DoFs of layer m
+//               (the top ones of the last layer for m = lambda);
+//   FACET_JUMP  r += int_F [u][phi] ds,  [w] = w(below, top) - w(above, bottom),
+//               on any prism tensor-product space.
+//
+// On the flat triangle F with area element |n| = |dx/dxi x dx/deta| (twice
+// the area) the P1 surface mass matrix is |n|/24 (1 + [a = b]) and a constant
+// integrates to |n|/2, so with c = |n|/24:  v_a = c (g_a + sum_b g_b)  (three
+// nodes) or v = |n|/2 g (one node).  One lane per (column, facet) item, lanes
+// along the facets of a warp's column group; a straight column (x, y of every
+// level bit-equal to level 0, z equal on the three vertices of the facet) uses
+// the column's |n| = |2A|, any other facet the cross product of its edges.
+// Increments are FP64 atomic adds (executed in L2): facet DoFs of CG1
+// horizontal spaces are shared with neighbouring columns, and under the jump
+// a vertically-DG0 DoF receives the terms of both of its facets.
+#include "ext_internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kMaxCols = 32;
+constexpr unsigned kFull = 0xffffffffu;
+#ifndef EXT_FACET_ITEMS
+#define EXT_FACET_ITEMS 1600  // target items per column group
+#endif
+
+struct FacetCol {
+  int32_t cb[3], ct[3];  // coords DoF of vertex a at the bottom level, at the top level
+  int32_t flo[3], fhi[3];
+  double n2;             // |2A| of the base triangle
+  long long rx[3], ry[3];
+  int lay;
+};
+
+template <int NH, bool JUMP, bool VAR>
+__global__ void __launch_bounds__(kWarps * 32) k_facet(const FacetLaunch p, int cpw) {
+  __shared__ FacetCol cols[kWarps][kMaxCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    int my_items = 0;
+    if (lane < ncol) {
+      const int64_t c = c0 + lane;
+      FacetCol &ci = cols[warp][lane];
+      const int lay = VAR ? __ldg(p.cell_layers + c) : p.layers;
+      ci.lay = lay;
+      my_items = JUMP ? lay - 1 : lay + 1;
+      double x[3], y[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ci.cb[a] = __ldg(p.cmap + c * 6 + 2 * a);
+        ci.ct[a] = __ldg(p.cmap + c * 6 + 2 * a + 1) + (lay - 1) * p.coff[2 * a + 1];
+        x[a] = __ldg(p.X + 3 * (int64_t)ci.cb[a] + 0);
+        y[a] = __ldg(p.X + 3 * (int64_t)ci.cb[a] + 1);
+        ci.rx[a] = __double_as_longlong(x[a]);
+        ci.ry[a] = __double_as_longlong(y[a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NH; ++a) {
+        ci.flo[a] = __ldg(p.fmap + c * p.k + p.slot_lo[a]);
+        ci.fhi[a] = __ldg(p.fmap + c * p.k + p.slot_hi[a]);
+      }
+      ci.n2 = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]));
+    }
+    __syncwarp();
+    const int nitems = __reduce_add_sync(kFull, my_items);
+    // lane's item: column cl, item index i within the column
+    int cl = 0, i = lane;
+    while (cl < ncol) {
+      const int n = JUMP ? cols[warp][cl].lay - 1 : cols[warp][cl].lay + 1;
+      if (i < n) break;
+      i -= n;
+      ++cl;
+    }
+    for (int base = 0; base < nitems; base += 32) {
+      if (base + lane < nitems) {
+        const FacetCol &ci = cols[warp][cl];
+        const int lay = ci.lay;
+        const int m = JUMP ? i + 1 : i;  // facet level
+        double X[3][3];
+        int ok = 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int64_t cd = m < lay ? (int64_t)ci.cb[a] + (int64_t)m * p.coff[2 * a] : (int64_t)ci.ct[a];
+          X[a][0] = __ldg(p.X + 3 * cd + 0);
+          X[a][1] = __ldg(p.X + 3 * cd + 1);
+          X[a][2] = __ldg(p.X + 3 * cd + 2);
+          ok &= (__double_as_longlong(X[a][0]) == ci.rx[a]) & (__double_as_longlong(X[a][1]) == ci.ry[a]);
+        }
+        ok &= (__double_as_longlong(X[0][2]) == __double_as_longlong(X[1][2])) &
+              (__double_as_longlong(X[0][2]) == __double_as_longlong(X[2][2]));
+        double ds;
+        if (ok) {
+          ds = ci.n2;
+        } else {
+          double e1[3], e2[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            e1[r] = X[1][r] - X[0][r];
+            e2[r] = X[2][r] - X[0][r];
+          }
+          const double n0 = e1[1] * e2[2] - e1[2] * e2[1];
+          const double n1 = e1[2] * e2[0] - e1[0] * e2[2];
+          const double nz = e1[0] * e2[1] - e1[1] * e2[0];
+          ds = sqrt(n0 * n0 + n1 * n1 + nz * nz);
+        }
+        int32_t dlo[NH], dhi[NH];
+        double g[NH];
+        if (JUMP) {
+#pragma unroll
+          for (int a = 0; a < NH; ++a) {
+            dlo[a] = ci.flo[a] + (m - 1) * p.off_lo[a];  // top trace of the layer below
+            dhi[a] = ci.fhi[a] + m * p.off_hi[a];        // bottom trace of the layer above
+            g[a] = __ldg(p.f + dlo[a]) - __ldg(p.f + dhi[a]);
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < NH; ++a) {
+            dlo[a] = m < lay ? ci.flo[a] + m * p.off_lo[a] : ci.fhi[a] + (lay - 1) * p.off_hi[a];
+            g[a] = __ldg(p.f + dlo[a]);
+          }
+        }
+        double v[NH];
+        if (NH == 3) {
+          const double cc = ds * (1.0 / 24.0);
+          const double cs = cc * ((g[0] + g[1]) + g[2]);
+#pragma unroll
+          for (int a = 0; a < NH; ++a) v[a] = fma(cc, g[a], cs);
+        } else {
+          v[0] = (0.5 * ds) * g[0];
+        }
+#pragma unroll
+        for (int a = 0; a < NH; ++a) {
+          atomicAdd(p.b + dlo[a], v[a]);
+          if (JUMP) atomicAdd(p.b + dhi[a], -v[a]);
+        }
+      }
+      i += 32;
+      while (cl < ncol) {
+        const int n = JUMP ? cols[warp][cl].lay - 1 : cols[warp][cl].lay + 1;
+        if (i < n) break;
+        i -= n;
+        ++cl;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int NH, bool JUMP, bool VAR>
+cudaError_t launch_k(const FacetLaunch &p, cudaStream_t s) {
+  const double per = (VAR ? p.mean_layers : (double)p.layers) + (JUMP ? -1.0 : 1.0);
+  int cpw = per > 0.5 ? (int)((EXT_FACET_ITEMS + per - 1.0) / per) : kMaxCols;
+  if (cpw < 1) cpw = 1;
+  if (cpw > kMaxCols) cpw = kMaxCols;
+  const int64_t warps = (p.ncells + cpw - 1) / cpw;
+  int64_t blocks = (warps + kWarps - 1) / kWarps;
+  static int resident = 0, sms = 0;
+  if (resident == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_facet<NH, JUMP, VAR>, kWarps * 32, 0);
+    if (resident < 1) resident = 1;
+  }
+  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
+  k_facet<NH, JUMP, VAR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  return cudaGetLastError();
+}
+
+template <bool VAR>
+cudaError_t launch_v(const FacetLaunch &p, cudaStream_t s) {
+  if (p.jump) return p.nh == 3 ? launch_k<3, true, VAR>(p, s) : launch_k<1, true, VAR>(p, s);
+  return p.nh == 3 ? launch_k<3, false, VAR>(p, s) : launch_k<1, false, VAR>(p, s);
+}
+
+}  // namespace
+
+cudaError_t launch_facet(const FacetLaunch &p, cudaStream_t s) {
+  if (p.ncells == 0) return cudaSuccess;
+  return p.cell_layers ? launch_v<true>(p, s) : launch_v<false>(p, s);
+}

@@ -27,12 +27,95 @@ __global__ void __launch_bounds__(256) k_number(const NumberLaunch p) {
   }
 }
 
+// Variable layers: entity (d, id) has the column start ent_start[g] (g its
+// dimension-major global index, a prefix sum of the column sizes) and bottom
+// level ent_lo[g]; cell c's list is taken at its own bottom level first[c],
+// (first[c] - ent_lo[g]) layers of (delta(d,0) + delta(d,1)) numbers above
+// the entity's bottom.
+__global__ void __launch_bounds__(256) k_number_var(const NumberLaunch p) {
+  const int64_t total = p.ncells * p.k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / p.k;
+    const int i = (int)(t - c * p.k);
+    const int d = p.slot_dim[i];
+    const int e = p.slot_ent[i];
+    int64_t id;
+    if (d == 0) id = p.cell_verts[c * p.nvc + e];
+    else if (d == 1) id = p.cell_edges[c * p.nvc + e];
+    else id = c;
+    const int64_t g = p.ent_base[d] + id;
+    const int64_t lift = (int64_t)(p.cell_first[c] - p.ent_lo[g]) * p.colstep[d];
+    p.map[t] = (int32_t)(p.ent_start[g] + lift + p.slot_add[i]);
+  }
+}
+
 cudaError_t launch_number(const NumberLaunch &p, cudaStream_t s) {
   const int64_t total = p.ncells * p.k;
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  k_number<<<(unsigned)blocks, 256, 0, s>>>(p);
+  if (p.ent_start) k_number_var<<<(unsigned)blocks, 256, 0, s>>>(p);
+  else k_number<<<(unsigned)blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Level range of every base entity: a cell spans first .. first + layers; a
+// vertex or edge the hull of the ranges of the cells containing it (integer
+// atomics, so the result does not depend on the order).
+__global__ void __launch_bounds__(256) k_var_ranges(int64_t ncells, int nvc, int64_t nv, int64_t ne,
+                                                    const int32_t *cell_verts, const int32_t *cell_edges,
+                                                    const int32_t *first, const int32_t *layers, int32_t *lo,
+                                                    int32_t *hi) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = first[c], t = first[c] + layers[c];
+    for (int a = 0; a < nvc; ++a) {
+      const int64_t v = cell_verts[c * nvc + a];
+      const int64_t e = nv + cell_edges[c * nvc + a];
+      atomicMin(lo + v, b);
+      atomicMax(hi + v, t);
+      atomicMin(lo + e, b);
+      atomicMax(hi + e, t);
+    }
+    lo[nv + ne + c] = b;
+    hi[nv + ne + c] = t;
+  }
+}
+
+cudaError_t launch_var_ranges(const ext_mesh *m, cudaStream_t s) {
+  const int64_t nent = m->N[0] + m->N[1] + m->N[2];
+  cudaError_t e = cudaMemsetAsync(m->d_ent_lo, 0x7f, sizeof(int32_t) * nent, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_ent_hi, 0xff, sizeof(int32_t) * nent, s);
+  if (e != cudaSuccess || m->N[2] == 0) return e;
+  int64_t blocks = (m->N[2] + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_var_ranges<<<(unsigned)blocks, 256, 0, s>>>(m->N[2], m->kind, m->N[0], m->N[1], m->d_cell_verts,
+                                                 m->d_cell_edges, m->d_cell_first, m->d_cell_layers,
+                                                 m->d_ent_lo, m->d_ent_hi);
+  return cudaGetLastError();
+}
+
+// Column size of every entity: (hi - lo) (delta(d,0) + delta(d,1)) + delta(d,0).
+__global__ void __launch_bounds__(256) k_var_colsize(int64_t n0, int64_t n01, int64_t nent, const int32_t *lo,
+                                                     const int32_t *hi, int4 a, int4 b, int64_t *sizes) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nent;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int d = g < n0 ? 0 : (g < n01 ? 1 : 2);
+    const int h = d == 0 ? a.x : (d == 1 ? a.y : a.z);
+    const int v = d == 0 ? b.x : (d == 1 ? b.y : b.z);
+    sizes[g] = (int64_t)(hi[g] - lo[g]) * (h + v) + h;
+  }
+}
+
+cudaError_t launch_var_colsize(const ext_mesh *m, const int32_t delta[6], int64_t *sizes, cudaStream_t s) {
+  const int64_t nent = m->N[0] + m->N[1] + m->N[2];
+  if (nent == 0) return cudaSuccess;
+  int64_t blocks = (nent + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_var_colsize<<<(unsigned)blocks, 256, 0, s>>>(m->N[0], m->N[0] + m->N[1], nent, m->d_ent_lo, m->d_ent_hi,
+                                                  make_int4(delta[0], delta[2], delta[4], 0),
+                                                  make_int4(delta[1], delta[3], delta[5], 0), sizes);
   return cudaGetLastError();
 }
 
@@ -61,7 +144,36 @@ __global__ void __launch_bounds__(256) k_extrude(const ExtrudeLaunch p) {
   }
 }
 
+// Variable layers: one warp per cell, lanes along the levels m = 0..layers[c]
+// of the column; level m sits at z = (first[c] + m) / maxlevel.
+__global__ void __launch_bounds__(256) k_extrude_var(const ExtrudeLaunch p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < p.ncells; c += wstride) {
+    const int lay = p.cell_layers[c], f0 = p.cell_first[c];
+    const int k = 2 * p.nvc;
+    for (int m = lane; m <= lay; m += 32) {
+      const double z = (double)(f0 + m) / (double)p.layers;
+      for (int a = 0; a < p.nvc; ++a) {
+        const int v = p.cell_verts[c * p.nvc + a];
+        const int64_t dof = (m < lay) ? (int64_t)p.map[c * k + 2 * a] + (int64_t)m * p.off
+                                      : (int64_t)p.map[c * k + 2 * a + 1] + (int64_t)(lay - 1) * p.off;
+        p.X[3 * dof + 0] = p.base_xy[2 * (int64_t)v + 0];
+        p.X[3 * dof + 1] = p.base_xy[2 * (int64_t)v + 1];
+        p.X[3 * dof + 2] = z;
+      }
+    }
+  }
+}
+
 cudaError_t launch_extrude(const ExtrudeLaunch &p, cudaStream_t s) {
+  if (p.cell_layers) {
+    if (p.ncells == 0) return cudaSuccess;
+    int64_t blocks = (p.ncells + 7) / 8;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_extrude_var<<<(unsigned)blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   const int64_t total = p.ncells * (p.layers + 1);
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;

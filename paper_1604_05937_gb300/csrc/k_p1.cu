@@ -67,6 +67,7 @@ struct ColInfo {
   double alpha;              // |2 A| / 144, so that s = alpha * |h| = A h / 72
   double alpha2;             // 2 alpha
   long long rx[3], ry[3];    // bit patterns of the level-0 x, y of the vertices
+  int lay;                   // layers of this column
 };
 
 struct Level {
@@ -115,6 +116,10 @@ __device__ void prism_general(const double X[6][3], const double f[6], double ou
 
 __device__ __forceinline__ bool same_bits(double a, long long b) { return __double_as_longlong(a) == b; }
 
+// VAR: column c has cell_layers[c] layers (its stencil lists are taken at its
+// own bottom layer), so a group's item count and the (column, level) walk
+// read each column's layer count from shared memory.
+template <bool VAR>
 __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const MassP1Launch p, int cpw) {
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
@@ -129,12 +134,16 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
     const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
     const int layers = p.layers;
     const int L1 = layers + 1;
+    int my_items = 0;
 
     // ---- per-column set-up: read the three stencil lists once (Algorithm 3's
     // outer loop), the level-0 corner coordinates and the area factor.
     if (lane < ncol) {
       const int64_t c = c0 + lane;
       ColInfo &ci = cols[warp][lane];
+      const int lay = VAR ? __ldg(p.cell_layers + c) : layers;
+      ci.lay = lay;
+      my_items = lay + 1;
       double x[3], y[3];
   #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -142,11 +151,11 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
         const int32_t fb = __ldg(p.fmap + c * 6 + 2 * a), ft = __ldg(p.fmap + c * 6 + 2 * a + 1);
         const int32_t bb = __ldg(p.bmap + c * 6 + 2 * a), bt = __ldg(p.bmap + c * 6 + 2 * a + 1);
         ci.cbot[a] = cb;
-        ci.ctop[a] = ct + (layers - 1) * p.coff[2 * a + 1];
+        ci.ctop[a] = ct + (lay - 1) * p.coff[2 * a + 1];
         ci.fbot[a] = fb;
-        ci.ftop[a] = ft + (layers - 1) * p.foff[2 * a + 1];
+        ci.ftop[a] = ft + (lay - 1) * p.foff[2 * a + 1];
         ci.bbot[a] = bb;
-        ci.btop[a] = bt + (layers - 1) * p.boff[2 * a + 1];
+        ci.btop[a] = bt + (lay - 1) * p.boff[2 * a + 1];
         x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
         y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
         ci.rx[a] = __double_as_longlong(x[a]);
@@ -158,10 +167,17 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
     }
     __syncwarp();
 
-    const int nitems = ncol * L1;
+    const int nitems = VAR ? __reduce_add_sync(kFull, my_items) : ncol * L1;
     // lane's item: column cl (local), level m
-    int cl = lane / L1;
-    int m = lane - cl * L1;
+    int cl, m;
+    if (VAR) {
+      cl = 0;
+      m = lane;
+      while (cl < ncol && m > cols[warp][cl].lay) { m -= cols[warp][cl].lay + 1; ++cl; }
+    } else {
+      cl = lane / L1;
+      m = lane - cl * L1;
+    }
 
     auto load_level = [&](int item, int clx, int mx, Level &lv) {
       lv.f[0] = lv.f[1] = lv.f[2] = 0.0;
@@ -169,16 +185,17 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
       lv.ok = 1;
       if (item < nitems) {
         const ColInfo &ci = cols[warp][clx];
+        const int lay = VAR ? ci.lay : layers;
         double f[3], zz[3];
         int ok = 1;
   #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, layers);
+          const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, lay);
           const double xa = __ldg(p.X + 3 * cd + 0);
           const double ya = __ldg(p.X + 3 * cd + 1);
           zz[a] = __ldg(p.X + 3 * cd + 2);
           ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
-          f[a] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, layers));
+          f[a] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
         }
         ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
               (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
@@ -200,16 +217,21 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
     for (int base = 0; base < nitems; base += 32) {
       // advance (cl, m) by 32 items for the lookahead
       int ncl = cl, nm = m + 32;
-      while (nm >= L1) { nm -= L1; ++ncl; }
+      if (VAR) {
+        while (ncl < ncol && nm > cols[warp][ncl].lay) { nm -= cols[warp][ncl].lay + 1; ++ncl; }
+      } else {
+        while (nm >= L1) { nm -= L1; ++ncl; }
+      }
       const int nitem = item + 32;
       if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
       else { nxt.f[0] = nxt.f[1] = nxt.f[2] = 0.0; nxt.z = 0.0; nxt.ok = 1; }
 
       const bool valid = item < nitems;
       const ColInfo &ci = cols[warp][valid ? cl : 0];
+      const int lay = VAR ? ci.lay : layers;
 
       // neighbours: level m+1 (next lane or lookahead), level m-1 (previous lane or carry)
-      const bool top = (m == layers);
+      const bool top = (m == lay);
       const bool bottom = (m == 0);
       double fn[3], zn;
   #pragma unroll
@@ -255,16 +277,16 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
         val[0] = val[1] = val[2] = 0.0;
         for (int half = 0; half < 2; ++half) {
           const int l = half == 0 ? m - 1 : m;  // layer below / above level m
-          if (l < 0 || l >= layers) continue;
+          if (l < 0 || l >= lay) continue;
           double X[6][3], f6[6], out[6];
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 2; ++b) {
               const int lev = l + b;
-              const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], lev, layers);
+              const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], lev, lay);
               X[2 * a + b][0] = __ldg(p.X + 3 * cd + 0);
               X[2 * a + b][1] = __ldg(p.X + 3 * cd + 1);
               X[2 * a + b][2] = __ldg(p.X + 3 * cd + 2);
-              f6[2 * a + b] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], lev, layers));
+              f6[2 * a + b] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], lev, lay));
             }
           prism_general(X, f6, out);
           for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
@@ -274,7 +296,7 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
   #pragma unroll
         for (int a = 0; a < 3; ++a) {
           // straight: value_a = 2 c_a + c_b + c_c, the horizontal sum done by L2
-          double *dst = p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers);
+          double *dst = p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, lay);
           atomicAdd(dst, val[a]);
           if (step_ok) {
             atomicAdd(dst, val[0]);
@@ -303,21 +325,25 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
 
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
-  const int L1 = p.layers + 1;
-  int cpw = (EXT_MASS_ITEMS + L1 - 1) / L1;
+  const bool var = p.cell_layers != nullptr;
+  // columns per group: about EXT_MASS_ITEMS items (mean items with variable layers)
+  const double L1 = var ? p.mean_layers + 1.0 : (double)(p.layers + 1);
+  int cpw = (int)((EXT_MASS_ITEMS + L1 - 1.0) / L1);
   if (cpw < 1) cpw = 1;
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident = 0, sms = 0;  // per process: one GPU model
-  if (resident == 0) {
+  static int resident[2] = {0, 0}, sms = 0;  // per process: one GPU model
+  if (resident[var] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_p1, kWarps * 32, 0);
-    if (resident < 1) resident = 1;
+    if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_mass_p1<true>, kWarps * 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_mass_p1<false>, kWarps * 32, 0);
+    if (resident[var] < 1) resident[var] = 1;
   }
-  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
-  k_mass_p1<<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  if (blocks > (int64_t)resident[var] * sms) blocks = (int64_t)resident[var] * sms;
+  if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ constexpr int kMaxCols = 32;
 struct TPCol {
   double alpha;              // |2A| * (1/2)(1/12 if NH=3)(1/6 if NV=2): c = alpha |h|
   long long rx[3], ry[3];    // level-0 x, y bit patterns
+  int lay;                   // layers of this column
 };
 
 // element vector of a general prism: out[a*NV+b] = sum_q w_q |detJ| f(x_q) H_a V_b
@@ -62,7 +63,8 @@ __device__ void tp_general(const double X[6][3], const double f[NH * NV], double
   }
 }
 
-template <int NH, int NV>
+// VAR: column c has cell_layers[c] layers (lists taken at its bottom layer).
+template <int NH, int NV, bool VAR>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,8 +74,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
   for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
     const int64_t c0 = grp * cpw;
     const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    int my_items = 0;
     if (lane < ncol) {
       const int64_t c = c0 + lane;
+      const int lay = VAR ? __ldg(p.cell_layers + c) : layers;
+      cols[warp][lane].lay = lay;
+      my_items = lay;
       double x[3], y[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -87,8 +93,16 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
       cols[warp][lane].alpha = fabs(det2) * p.scale;
     }
     __syncwarp();
-    const int nitems = ncol * layers;
-    int cl = lane / layers, l = lane - (lane / layers) * layers;
+    const int nitems = VAR ? __reduce_add_sync(0xffffffffu, my_items) : ncol * layers;
+    int cl, l;
+    if (VAR) {
+      cl = 0;
+      l = lane;
+      while (cl < ncol && l >= cols[warp][cl].lay) { l -= cols[warp][cl].lay; ++cl; }
+    } else {
+      cl = lane / layers;
+      l = lane - cl * layers;
+    }
     for (int base = 0; base < nitems; base += 32) {
       if (base + lane < nitems) {
         const int64_t c = c0 + cl;
@@ -143,39 +157,49 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
         for (int i = 0; i < NH * NV; ++i) atomicAdd(p.b + dof[i], b[i]);
       }
       l += 32;
-      while (l >= layers) { l -= layers; ++cl; }
+      if (VAR) {
+        while (cl < ncol && l >= cols[warp][cl].lay) { l -= cols[warp][cl].lay; ++cl; }
+      } else {
+        while (l >= layers) { l -= layers; ++cl; }
+      }
     }
     __syncwarp();
   }
 }
 
-template <int NH, int NV>
+template <int NH, int NV, bool VAR>
 cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
-  int cpw = (EXT_TP_ITEMS + p.layers - 1) / p.layers;
+  const double lay = VAR ? p.mean_layers : (double)p.layers;
+  int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
   if (cpw < 1) cpw = 1;
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[4] = {0, 0, 0, 0}, sms = 0;
-  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0);
+  static int resident[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sms = 0;
+  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0);
   if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV>, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR>, kWarps * 32, 0);
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  k_mass_tp<NH, NV><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_tp<NH, NV, VAR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
+}
+
+template <bool VAR>
+cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2, VAR>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1, VAR>(p, s);
+  return launch_tp<3, 2, VAR>(p, s);
 }
 
 }  // namespace
 
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
-  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1>(p, s);
-  if (p.nh == 1) return launch_tp<1, 2>(p, s);
-  if (p.nv == 1) return launch_tp<3, 1>(p, s);
-  return launch_tp<3, 2>(p, s);
+  return p.cell_layers ? launch_tp_pair<true>(p, s) : launch_tp_pair<false>(p, s);
 }

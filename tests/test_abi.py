@@ -64,6 +64,16 @@ def test_validation_needs_no_gpu(libpath):
         E.ext_mesh_create(3, 3, 1, np.array([[0, 2, 1]], dtype=np.int32), xy, 2)
     with pytest.raises(E.ExtError, match="kind"):
         E.ext_mesh_create(5, 3, 1, cells, xy, 2)
+    # variable layers: every cell spans at least one layer from a level >= 0,
+    # and every vertex belongs to a cell
+    with pytest.raises(E.ExtError, match="layers 0"):
+        E.ext_mesh_create_var(3, 3, 1, cells, xy, np.array([0]), np.array([0]))
+    with pytest.raises(E.ExtError, match="first -1"):
+        E.ext_mesh_create_var(3, 3, 1, cells, xy, np.array([-1]), np.array([2]))
+    with pytest.raises(E.ExtError, match="belongs to no cell"):
+        E.ext_mesh_create_var(3, 4, 1, cells, np.vstack([xy, [[1.0, 1.0]]]), np.array([0]), np.array([2]))
+    with pytest.raises(ValueError):
+        E.ext_mesh_create_var(3, 3, 1, cells, xy, np.array([0, 0]), np.array([1, 1]))
 
 
 def test_cuda_path_shares_no_code_with_oracle():

@@ -65,17 +65,7 @@ def test_golden_variable_layers():
 
 
 def bathymetry(m, maxlevel, seed, gaps=False):
-    """Per-column (first level, layers): a smooth depth field with a flat top
-    (first = maxlevel - layers), or random ranges that may leave gaps."""
-    rng = np.random.default_rng(seed)
-    if gaps:
-        first = rng.integers(0, maxlevel - 1, m.ncells)
-        lay = 1 + rng.integers(0, maxlevel - first)
-        return first.astype(np.int32), lay.astype(np.int32)
-    cxy = m.xy[m.cells].mean(axis=1)
-    depth = 0.55 + 0.4 * np.sin(3.0 * cxy[:, 0] + 1.0) * np.cos(2.0 * cxy[:, 1])
-    lay = np.clip(np.rint(depth * maxlevel), 1, maxlevel).astype(np.int32)
-    return (maxlevel - lay).astype(np.int32), lay
+    return meshgen.column_layers(m, maxlevel, seed, "random" if gaps else "bathymetry")
 
 
 def _mesh(name, n, seed, order="rcm"):
