@@ -9,7 +9,7 @@ f = sin(x) cos(y) z (INC), P1xP1 mass-matrix action y += M x with x ~ U(-1,1)
 entry moved once) / device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2|3|4|5|6]
+                    [--config 2|3|4|5|6|7]
 
 --impl reference times the CPU oracle on a bounded sample of the same
 workload (the reference arm: there is no reference GPU code).  Under torchrun
@@ -786,6 +786,163 @@ def run_cfg6(args, rank, world, local):
                                 "RCM and random base order", "l2": "flushed"},
                    extra, clocks, launches)
 
+# FP64 operations per facet of the straight-column facet kernels: surface mass
+# with three nodes: c = |n|/24, S = sum f (2), c S, three fma = 7; one node:
+# |n|/2 and the product = 2.  Jump with three nodes: three differences, c,
+# S (2), c S, three fma = 10; one node: 3.
+FACET_MASS_OPS = {3: 7, 1: 2}
+FACET_JUMP_OPS = {3: 10, 1: 3}
+FACET_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), 3), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 1),
+                ("DG1xCG1", (0, 0, 0, 0, 3, 0), 3)]
+JUMP_SPACES = [("DG0xDG0", (0, 0, 0, 0, 0, 1), 1), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 3),
+               ("DG0xDG1", (0, 0, 0, 0, 0, 2), 1), ("DG1xDG1", (0, 0, 0, 0, 0, 6), 3),
+               ("CG1xDG1", (0, 2, 0, 0, 0, 0), 3)]
+
+
+def vertex_hulls(m, first, lay):
+    """Level range of every base vertex column: the hull of its cells' ranges."""
+    lo = np.full(m.nverts, 1 << 30, dtype=np.int64)
+    hi = np.full(m.nverts, -1, dtype=np.int64)
+    for a in range(m.cells.shape[1]):
+        np.minimum.at(lo, m.cells[:, a], first)
+        np.maximum.at(hi, m.cells[:, a], first + lay)
+    return lo, hi
+
+
+def run_cfg7(args, rank, world, local):
+    """Variable layers per column and horizontal-facet loops on the 999,698-
+    triangle base.  (a) The default step (RHS, mass action, DG1 interpolation)
+    plus DG0/DG1 copies on a mesh whose columns hang from a flat top at level
+    100 with a smooth bathymetry-like depth (mean about 55 layers), against
+    the same loops on the constant-layer mesh with the rounded mean; (b) the
+    facet loops at 100 layers: surface mass over the 101 horizontal facets of
+    each column (CG1xCG1, DG0xCG1, DG1xCG1) and the interior-facet jump on five
+    vertically discontinuous spaces, and both kinds on the variable mesh.
+    L2 flushed before every timed launch; min over the repetitions."""
+    import torch
+    import paper_1604_05937_gb300 as E
+    init_dist(world, local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = stream.cuda_stream
+    flush = Flusher(dev)
+    rates = E.ext_fp64_rates(s)
+    hbm, hbm_kind, sm_max = peaks()
+    nominal = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max / 1e3
+    reps = max(3, min(args.steps, 20))
+    m = meshgen.tri_mesh(args.n or N_CFG2, seed=SEED + rank, order=args.order)
+    V, C = m.nverts, m.ncells
+    top = args.layers or LAYERS_CFG2
+    first, lay = meshgen.column_layers(m, top, SEED + 70 + rank, "bathymetry")
+    mean_l = float(lay.mean())
+    R, W, I = E.EXT_READ, E.EXT_WRITE, E.EXT_INC
+    launches = 0
+    clk = ClockSampler(local)
+    clk.start()
+
+    def timed(fn, pre=None):
+        nonlocal launches
+        fn()
+        t = time_kernel(fn, reps, stream, flush, pre=pre)[0]
+        launches += reps + 1
+        return t
+
+    def step_loops(gm):
+        """RHS, mass, interpolation and two DG copies on one mesh."""
+        cs = E.Space(gm, P1_DELTA, ncomp=3)
+        p1 = E.Space(gm, P1_DELTA)
+        dg = E.Space(gm, DG1_DELTA)
+        d0 = E.Space(gm, (0, 0, 0, 0, 0, 1))
+        X = E.extrude_coords(gm, cs)
+        x = torch.rand(p1.ndofs, dtype=torch.float64, device=dev)
+        b, out = p1.zeros(), dg.zeros()
+        u0 = torch.rand(d0.ndofs, dtype=torch.float64, device=dev)
+        o0 = d0.zeros()
+        u1 = torch.rand(dg.ndofs, dtype=torch.float64, device=dev)
+        nP1 = p1.ndofs
+        cells_layers = dg.ndofs // 6
+        items = int(cells_layers + C)  # (column, level) items of the P1 kernel: sum (lambda_c + 1)
+        row = {}
+        t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, [(cs.handle, X, R), (p1.handle, x, R),
+                                                                         (p1.handle, b, I)], s), pre=b.zero_)
+        vb = 24 * nP1 + 16 * nP1 + 48 * C
+        row["mass_p1p1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
+                            "fp64_gops_algorithmic": round(MASS_OPS_PER_ITEM * items / t / 1e6, 1),
+                            "fp64_pct_nominal": round(100 * MASS_OPS_PER_ITEM * items / t / 1e6 / nominal, 1)}
+        t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_INTERP_DG1, [(p1.handle, x, R), (dg.handle, out, W)], s))
+        vb = 8 * nP1 + 8 * dg.ndofs + 48 * C
+        row["interp_dg1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1)}
+        for nm, sp, u, o in (("copy_dg0", d0, u0, o0), ("copy_dg1", dg, u1, out)):
+            t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_COPY_DG, [(sp.handle, u, R), (sp.handle, o, W)], s))
+            vb = 16 * sp.ndofs + 4 * C
+            row[nm] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1)}
+        E.ext_sync_check(s)
+        row["cell_layers"] = int(cells_layers)
+        step_b = 2 * (24 * nP1 + 16 * nP1 + 48 * C) + 8 * nP1 + 8 * dg.ndofs + 48 * C
+        row["step_gbs"] = round(step_b / (2 * row["mass_p1p1"]["ms"] + row["interp_dg1"]["ms"]) / 1e6, 1)
+        return row, (cs, X)
+
+    def facet_loops(gm, cs, X, cell_layers, vint_levels):
+        """Facet mass on the (.)xCG1 spaces and the interior jump on five spaces."""
+        row = {}
+        for kind, spaces in (("facet_mass", FACET_SPACES), ("facet_jump", JUMP_SPACES)):
+            for nm, delta, nh in spaces:
+                sp = E.Space(gm, delta)
+                u = torch.rand(sp.ndofs, dtype=torch.float64, device=dev)
+                b = sp.zeros()
+                kid = E.EXT_K_HFACET_MASS if kind == "facet_mass" else E.EXT_K_HFACET_JUMP
+                t = timed(lambda: E.ext_par_loop(gm.handle, kid, [(cs.handle, X, R), (sp.handle, u, R),
+                                                                  (sp.handle, b, I)], s), pre=b.zero_)
+                if kind == "facet_mass":
+                    facets = int(cell_layers + C)
+                    coords = 24 * cs.ndofs
+                    ops = FACET_MASS_OPS[nh]
+                else:
+                    facets = int(cell_layers - C)
+                    coords = 24 * vint_levels
+                    ops = FACET_JUMP_OPS[nh]
+                vb = coords + 16 * sp.ndofs + 24 * C + 4 * sp.k * C
+                row[f"{kind}:{nm}"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
+                                       "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1),
+                                       "facets": facets, "gfacets_per_s": round(facets / t / 1e6, 2),
+                                       "fp64_pct_nominal": round(100 * ops * facets / t / 1e6 / nominal, 1)}
+                del sp, u, b
+        E.ext_sync_check(s)
+        return row
+
+    results = {}
+    # (a)+(b) variable layers
+    gm = E.Mesh(m.cells, m.xy, cell_first=first, cell_layers=lay)
+    vlo, vhi = vertex_hulls(m, first.astype(np.int64), lay.astype(np.int64))
+    row, (cs, X) = step_loops(gm)
+    row.update(facet_loops(gm, cs, X, int(lay.sum()), int(np.maximum(vhi - vlo - 1, 0).sum())))
+    results["variable"] = row
+    del gm, cs, X
+    torch.cuda.empty_cache()
+    # the same loops with constant layers: the rounded mean, and the top level
+    for name, L in (("constant_mean", int(round(mean_l))), ("constant_top", top)):
+        gm = E.Mesh(m.cells, m.xy, L)
+        row, (cs, X) = step_loops(gm)
+        if name == "constant_top":
+            row.update(facet_loops(gm, cs, X, C * L, V * (L - 1)))
+        results[name] = row
+        del gm, cs, X
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    extra = {"results": results, "mean_layers": round(mean_l, 2), "top_level": top,
+             "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
+             "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
+             "timing": "min over reps, L2 flushed before every timed launch"}
+    val = world * results["variable"]["step_gbs"]
+    return _common(args, world, "valuable GB/s of the RHS + mass + DG1 interpolation step on a mesh with variable "
+                   "layers per column (bathymetry, top level 100)", val, "GB/s",
+                   {"workload": f"extruded prisms: {C} base triangles, column c spans levels 100 - l_c .. 100 with "
+                                f"l_c = round(100 d(x_c, y_c)), d a smooth depth in [0.15, 0.95] (mean "
+                                f"{mean_l:.1f} layers); facet loops at 100 layers; {args.order} base order",
+                    "l2": "flushed"}, extra, clocks, launches)
+
 
 def run_reference(args, rank, world):
     if rank != 0:
@@ -823,9 +980,10 @@ def main():
     ap.add_argument("--count", type=int, default=64, help="config 5: number of meshes")
     ap.add_argument("--cmax", type=float, default=5e5, help="config 5: largest base cell count")
     ap.add_argument("--order", choices=["rcm", "random"], default="rcm")
-    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6], default=2,
+    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6, 7], default=2,
                     help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "
-                         "5: 64-mesh batched vs plain; 6: the nine prism spaces at ~15M cells")
+                         "5: 64-mesh batched vs plain; 6: the nine prism spaces at ~15M cells; "
+                         "7: variable layers per column and horizontal-facet loops")
     ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -836,7 +994,7 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build_library_only()
-        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6}[args.config]
+        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6, 7: run_cfg7}[args.config]
         line = runner(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
