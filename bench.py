@@ -42,16 +42,33 @@ FP64_OPS_PER_CLK_PER_SM = 2.0  # 1.25 TFLOP/s nominal = 2 FMA/clk/SM x 152 SMs x
 SM_MAX_MHZ = 2070.0
 P1_DELTA = (1, 0, 0, 0, 0, 0)
 DG1_DELTA = (0, 0, 0, 0, 0, 6)
-# Algorithmic FP64 work of one (column, level) item of the straight-prism
-# P1xP1 kernel, with every sum done in registers: 2 (S) + 1 (h) + 2 (s, 2s) +
-# 1 (sigma) + 3 (K) + 9 (three rows) = 18 operations, 11 of them FMAs: 29
-# flops.  The kernel executes 13 of them on the SM's FP64 pipe (3 DMUL + 6
-# DFMA + 2 DADD + 2 DMUL) and hands the horizontal sum to L2 as 12 FP64 atomic
-# adds per item (value_a = 2 c_a + c_b + c_c).
-MASS_OPS_PER_ITEM = 18
-MASS_FLOPS_PER_ITEM = 29
-MASS_SM_OPS_PER_ITEM = 13
-MASS_L2_ADDS_PER_ITEM = 12
+# FP64 work of one P1xP1 RHS / mass-action par_loop on straight prisms in the
+# split form the library runs: the vertical sums of every vertex level,
+#   w = |h_lo| (f_lo + 2 f) + |h_hi| (2 f + f_hi)       1 DADD, 1 DMUL, 3 DFMA per DoF,
+# and the horizontal combination of every (column, level) item,
+#   value_a = alpha (w_a + w_0 + w_1 + w_2)              1 DMUL, 5 DFMA per item,
+# with 3 FP64 atomic adds per item (executed in L2).  One launch runs three
+# kernels (vertical sums, cell pass, and the pass over deferred non-straight
+# warp steps, which finds none on a straight mesh).  Evaluating each cell's
+# element matrix by itself instead needs 18 FP64 operations per item.
+VSUM_OPS_PER_DOF = 5
+CELL_OPS_PER_ITEM = 6
+CELL_ATOMICS_PER_ITEM = 3
+CELLWISE_OPS_PER_ITEM = 18
+P1_KERNELS_PER_LAUNCH = 3
+
+
+def p1_ops(ndofs: int, items: int) -> int:
+    """FP64 operations of one P1xP1 RHS / mass-action launch (split form)."""
+    return VSUM_OPS_PER_DOF * ndofs + CELL_OPS_PER_ITEM * items
+
+
+def p1_mix_ceiling(ndofs: int, items: int, rates: dict) -> float:
+    """G op/s ceiling of that operation mix at the measured DFMA/DADD/DMUL rates."""
+    dfma = 3 * ndofs + 5 * items
+    dadd = ndofs
+    dmul = ndofs + items
+    return (dfma + dadd + dmul) / (dfma / rates["dfma"] + dadd / rates["dadd"] + dmul / rates["dmul"])
 
 
 def peaks():
@@ -334,14 +351,14 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     V, C = m.nverts, m.ncells
     value = world * vb["total"] / (ms * 1e-3) / 1e9
     items = C * (L + 1)
+    ndofs = V * (L + 1)
     mass_ms = statistics.mean(k_rhs + k_mass)
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
-    achieved_ops = MASS_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
-    traffic = load_traffic("k_mass_p1")
-    sm_ops = MASS_SM_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
-    # ceiling of the executed SM mix (6 DFMA, 2 DADD, 5 DMUL per item) at the measured rates
-    sm_mix_peak = MASS_SM_OPS_PER_ITEM / (6 / rates["dfma"] + 2 / rates["dadd"] + 5 / rates["dmul"])
-    l2_adds = MASS_L2_ADDS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
+    ops = p1_ops(ndofs, items)
+    achieved_ops = ops / (mass_ms * 1e-3) / 1e9
+    traffic = load_traffic("p1_mass_launch")
+    mix_peak = p1_mix_ceiling(ndofs, items, rates)
+    l2_adds = CELL_ATOMICS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -360,25 +377,26 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                         "interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6, 1)},
         "hbm_frac": {"interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6 / hbm, 4),
                      "step": round(value / world / hbm, 4), "peak_gbs": hbm, "peak_kind": hbm_kind},
-        "roofline": {"kernel": "k_mass_p1 (RHS and mass action)", "bound": "alu",
+        "roofline": {"kernel": "P1xP1 RHS / mass-action launch (k_vsum + k_mass_cells + k_mass_general)",
+                     "bound": "alu",
                      "achieved": round(achieved_ops, 2), "peak": round(ops_peak, 2), "unit": "G FP64 ops/s",
                      "frac": round(achieved_ops / ops_peak, 4), "traffic": traffic,
-                     "algorithmic": f"{MASS_OPS_PER_ITEM} FP64 ops ({MASS_FLOPS_PER_ITEM} flops) per "
-                                    f"(column, level) item x {items} items per launch",
-                     "achieved_tflops": round(MASS_FLOPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e12, 4),
+                     "algorithmic": f"{VSUM_OPS_PER_DOF} FP64 ops per DoF x {ndofs} DoFs + {CELL_OPS_PER_ITEM} "
+                                    f"per (column, level) item x {items} items = {ops} per launch",
                      "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-                     "executed": {"sm_fp64_ops_per_item": MASS_SM_OPS_PER_ITEM,
-                                  "l2_fp64_atomic_adds_per_item": MASS_L2_ADDS_PER_ITEM,
-                                  "sm_fp64_gops": round(sm_ops, 1), "l2_atomic_adds_g_per_s": round(l2_adds, 1),
-                                  "sm_fp64_frac_of_mix_ceiling": round(sm_ops / sm_mix_peak, 4),
-                                  "l2_atomic_frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
-                     "frac_note": "above 1 because 12 of the item's additions run in L2 atomic units, "
-                                  "outside the SM FP64 pipe whose nominal rate is the denominator"},
+                     "mix_ceiling_gops": round(mix_peak, 1),
+                     "frac_of_mix_ceiling": round(achieved_ops / mix_peak, 4),
+                     "l2_atomic_adds": {"per_item": CELL_ATOMICS_PER_ITEM, "g_per_s": round(l2_adds, 1),
+                                        "frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
+                     "cellwise_equivalent_gops": round(CELLWISE_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9, 1),
+                     "note": "the split form computes each vertex column's vertical sums once instead of once "
+                             "per cell around the vertex; evaluated cell by cell the same work is 18 FP64 ops "
+                             "per item (cellwise_equivalent_gops)"},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (2 * P1_KERNELS_PER_LAUNCH + 1) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -528,7 +546,7 @@ def run_cfg3(args, rank, world, local):
             t_rhs = time_kernel(rhs, reps, stream, flush, pre=b.zero_)
             t_c0 = time_kernel(c0, reps, stream, flush)
             t_c1 = time_kernel(c1, reps, stream, flush)
-            launches += 3 * (reps + args.warmup)
+            launches += (P1_KERNELS_PER_LAUNCH + 2) * (reps + args.warmup)
             nP1 = V * (L + 1)
             vb_rhs = 40 * nP1 + 48 * C
             vb_c0 = 16 * C * L + 4 * C
@@ -536,7 +554,7 @@ def run_cfg3(args, rank, world, local):
             items = C * (L + 1)
             sweep[order][L] = {
                 "rhs_ms": round(t_rhs[0], 4), "rhs_gbs": round(vb_rhs / t_rhs[0] / 1e6, 1),
-                "rhs_gops": round(MASS_OPS_PER_ITEM * items / t_rhs[0] / 1e6, 1),
+                "rhs_gops": round(p1_ops(nP1, items) / t_rhs[0] / 1e6, 1),
                 "dg0_ms": round(t_c0[0], 4), "dg0_gbs": round(vb_c0 / t_c0[0] / 1e6, 1),
                 "dg1_ms": round(t_c1[0], 4), "dg1_gbs": round(vb_c1 / t_c1[0] / 1e6, 1)}
             E.ext_sync_check(s)
@@ -707,8 +725,8 @@ def run_cfg5(args, rank, world, local):
 
 
 # FP64 ops per unit of the nine-space mass kernels (straight prisms); unit =
-# (column, level) item for CG1xCG1, cell-layer otherwise (see k_tp.cu)
-TP_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), 18), ("CG1xDG0", (0, 1, 0, 0, 0, 0), 8),
+# cell-layer (see k_tp.cu); CG1xCG1 runs the P1xP1 split form (p1_ops)
+TP_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), None), ("CG1xDG0", (0, 1, 0, 0, 0, 0), 8),
              ("CG1xDG1", (0, 2, 0, 0, 0, 0), 23), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 7),
              ("DG0xDG0", (0, 0, 0, 0, 0, 1), 3), ("DG0xDG1", (0, 0, 0, 0, 0, 2), 7),
              ("DG1xCG1", (0, 0, 0, 0, 3, 0), 23), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 8),
@@ -755,11 +773,11 @@ def run_cfg6(args, rank, world, local):
                 fn()
                 reps = max(3, min(args.steps, 10))
                 t = time_kernel(fn, reps, stream, flush, pre=b.zero_)[0]
-                launches += reps + 1
-                units = C * (L + 1) if name == "CG1xCG1" else C * L
+                launches += (reps + 1) * (P1_KERNELS_PER_LAUNCH if ops is None else 1)
+                work = p1_ops(V * (L + 1), C * (L + 1)) if ops is None else ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
                 vb = vb_paper + 24 * C + 4 * sp.k * C
-                gops = ops * units / t / 1e6
+                gops = work / t / 1e6
                 row[name] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
                              "hbm_pct": round(100 * vb / t / 1e6 / hbm, 2),
                              "hbm_pct_paper_bytes": round(100 * vb_paper / t / 1e6 / hbm, 2),
@@ -777,7 +795,8 @@ def run_cfg6(args, rank, world, local):
     tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES)
     extra = {"spaces": results, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
              "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-             "fp64_ops_per_unit": {nm: ops for nm, _, ops in TP_SPACES},
+             "fp64_ops_per_unit": {nm: (ops if ops is not None else f"{VSUM_OPS_PER_DOF} per DoF + "
+                                        f"{CELL_OPS_PER_ITEM} per column level") for nm, _, ops in TP_SPACES},
              "timing": "min over reps, L2 flushed before every timed launch"}
     return _common(args, world, "I_1 = int f v dx on the nine prism spaces at 100 layers (~15M cells, RCM): valuable "
                    "GB/s over the nine launches", world * tot_b / tot_t, "GB/s",
@@ -840,11 +859,11 @@ def run_cfg7(args, rank, world, local):
     clk = ClockSampler(local)
     clk.start()
 
-    def timed(fn, pre=None):
+    def timed(fn, pre=None, kernels=1):
         nonlocal launches
         fn()
         t = time_kernel(fn, reps, stream, flush, pre=pre)[0]
-        launches += reps + 1
+        launches += (reps + 1) * kernels
         return t
 
     def step_loops(gm):
@@ -864,11 +883,12 @@ def run_cfg7(args, rank, world, local):
         items = int(cells_layers + C)  # (column, level) items of the P1 kernel: sum (lambda_c + 1)
         row = {}
         t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, [(cs.handle, X, R), (p1.handle, x, R),
-                                                                         (p1.handle, b, I)], s), pre=b.zero_)
+                                                                         (p1.handle, b, I)], s), pre=b.zero_,
+                  kernels=P1_KERNELS_PER_LAUNCH)
         vb = 24 * nP1 + 16 * nP1 + 48 * C
         row["mass_p1p1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
-                            "fp64_gops_algorithmic": round(MASS_OPS_PER_ITEM * items / t / 1e6, 1),
-                            "fp64_pct_nominal": round(100 * MASS_OPS_PER_ITEM * items / t / 1e6 / nominal, 1)}
+                            "fp64_gops": round(p1_ops(nP1, items) / t / 1e6, 1),
+                            "fp64_pct_nominal": round(100 * p1_ops(nP1, items) / t / 1e6 / nominal, 1)}
         t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_INTERP_DG1, [(p1.handle, x, R), (dg.handle, out, W)], s))
         vb = 8 * nP1 + 8 * dg.ndofs + 48 * C
         row["interp_dg1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1)}

@@ -512,6 +512,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.err = ext_device_error_word();
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
+      p.nf = args[1].space->ndofs;
       e = launch_mass_p1(p, s);
       break;
     }

@@ -141,6 +141,7 @@ struct MassP1Launch {
   unsigned int *err;
   const int32_t *cell_layers = nullptr;  // variable layers
   double mean_layers = 0.0;
+  int64_t nf = 0;  // DoFs of the f space (CG1xCG1 numbering shared with the coordinates)
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 

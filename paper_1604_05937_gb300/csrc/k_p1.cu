@@ -34,6 +34,7 @@
 // evaluates the element integrals with the full 6-point rule and the general
 // Jacobian instead, so any coordinate field is handled.
 #include "ext_internal.cuh"
+#include "fastdiv.cuh"
 
 namespace {
 
@@ -43,6 +44,9 @@ constexpr unsigned kFull = 0xffffffffu;
 
 #ifndef EXT_MASS_MINB
 #define EXT_MASS_MINB 2  // resident CTAs per SM the register budget must allow
+#endif
+#ifndef EXT_CELLS_MINB
+#define EXT_CELLS_MINB 4  // resident CTAs per SM of the split form's cell pass
 #endif
 #ifndef EXT_MASS_ITEMS
 #define EXT_MASS_ITEMS 1616  // target items (column levels) per column group
@@ -321,7 +325,355 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split form.  On a straight column the vertical sums depend only on the
+// vertex column: with h_l the layer heights of that column,
+//   w_m = h_{m-1} (f_{m-1} + 2 f_m) + h_m (2 f_m + f_{m+1})
+// and a straight cell with area factor alpha = |2A| / 144 contributes
+// c_a = alpha w_{a,m} at level m, i.e. value_a = alpha (w_a + w_0 + w_1 + w_2).
+// Each vertex column is shared by about six cells, so the split form computes
+// w once per vertex level (k_vsum, over the flat DoF range of the field: the
+// column of a CG1xCG1 vertex is a contiguous run, so level m's neighbours are
+// DoFs d - 1 and d + 1) and the cell pass (k_mass_cells) only forms the
+// horizontal combination: 6 FP64 operations and 3 atomic adds per item
+// instead of 13 and 12.  The cell pass still checks straightness exactly and
+// takes the 6-point rule for any other prism.  With variable layers a vertex
+// column spans the hull of its cells' ranges, so the w of a cell's bottom and
+// top levels may include a layer outside that cell: the cell pass recomputes
+// those two levels from f.
+
+// w over the DoFs [0, n) of a CG1xCG1 field; `col` = layers + 1 (constant
+// layers: level m = d mod col, ends have one layer) or unused (VAR: the ends
+// of vertex columns are never read).
+template <bool VAR>
+__global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, const double *__restrict__ f,
+                                              double *__restrict__ W, int64_t n, FastDiv col) {
+  // A warp takes VU consecutive 32-DoF chunks per step and issues all their
+  // loads before any arithmetic (the loop is latency-bound otherwise); the
+  // neighbours across chunk edges come from the adjacent chunk's lanes.
+  constexpr int VU = 4;
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 * VU; base < n; base += wstride) {
+    double zc[VU], fc[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      zc[u] = 0.0;
+      fc[u] = 0.0;
+      if (d < n) {
+        zc[u] = __ldg(X + 3 * d + 2);
+        fc[u] = __ldg(f + d);
+      }
+    }
+    // the DoF before the first chunk and after the last one
+    double zb = 0.0, fb = 0.0, za = 0.0, fa = 0.0;
+    if (lane == 0 && base > 0 && base - 1 < n) {
+      zb = __ldg(X + 3 * (base - 1) + 2);
+      fb = __ldg(f + base - 1);
+    }
+    if (lane == 31 && base + 32 * VU < n) {
+      za = __ldg(X + 3 * (base + 32 * VU) + 2);
+      fa = __ldg(f + base + 32 * VU);
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      // left neighbour: previous lane; for lane 0 the previous chunk's lane 31
+      // (u > 0, a compile-time condition, so every lane reaches the shuffle)
+      // or its own load of DoF base - 1
+      double zl = __shfl_up_sync(kFull, zc[u], 1), fl = __shfl_up_sync(kFull, fc[u], 1);
+      double zlp = zb, flp = fb;
+      if (u > 0) {
+        zlp = __shfl_sync(kFull, zc[u > 0 ? u - 1 : 0], 31);
+        flp = __shfl_sync(kFull, fc[u > 0 ? u - 1 : 0], 31);
+      }
+      if (lane == 0) {
+        zl = zlp;
+        fl = flp;
+      }
+      // right neighbour: next lane; for lane 31 the next chunk's lane 0 or its
+      // own load of the DoF after the last chunk
+      double zr = __shfl_down_sync(kFull, zc[u], 1), fr = __shfl_down_sync(kFull, fc[u], 1);
+      double zrn = za, frn = fa;
+      if (u + 1 < VU) {
+        zrn = __shfl_sync(kFull, zc[u + 1 < VU ? u + 1 : u], 0);
+        frn = __shfl_sync(kFull, fc[u + 1 < VU ? u + 1 : u], 0);
+      }
+      if (lane == 31) {
+        zr = zrn;
+        fr = frn;
+      }
+      // signed layer heights; the absolute values are taken as operand
+      // modifiers of the DMUL / DFMA below (a separate fabs costs DADDs)
+      const double hl = zc[u] - zl;
+      double hh = __shfl_down_sync(kFull, hl, 1);
+      if (lane == 31) hh = zr - zc[u];
+      bool lo_end, hi_end;
+      if (VAR) {
+        lo_end = d == 0;
+        hi_end = d + 1 >= n;
+      } else {
+        const uint32_t q = fdiv((uint32_t)d, col);
+        const uint32_t mm = (uint32_t)d - q * col.d;
+        lo_end = mm == 0;
+        hi_end = mm + 1 == col.d;
+      }
+      // w = |hl| (fl + 2 fc) + |hh| (2 fc + fr): one DADD, one DMUL, three
+      // DFMA.  At a column end the missing layer's f factor is cleared
+      // bitwise (an integer AND, off the FP64 pipe); the height read across
+      // the column boundary is then multiplied by zero (coordinates are
+      // finite).
+      const long long kl = lo_end ? 0LL : -1LL, kh = hi_end ? 0LL : -1LL;
+      const double al = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fl)) & kl);
+      const double bh = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fr)) & kh);
+      if (d < n) W[d] = fma(fabs(hl), al, fabs(hh) * bh);
+    }
+  }
+}
+
+// prism_general reading the coordinates and f from memory (L1) at each
+// quadrature point instead of holding them in registers.
+__device__ void prism_general_g(const double *__restrict__ Xg, const double *__restrict__ fg, const int32_t cd[6],
+                                const int32_t fd[6], double out[6]) {
+  const double tp[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+  const double gz[2] = {0.5 - 0.28867513459481288225, 0.5 + 0.28867513459481288225};
+  for (int i = 0; i < 6; ++i) out[i] = 0.0;
+  for (int t = 0; t < 3; ++t) {
+    const double lam[3] = {1.0 - tp[t][0] - tp[t][1], tp[t][0], tp[t][1]};
+    const double dlx[3] = {-1.0, 1.0, 0.0}, dly[3] = {-1.0, 0.0, 1.0};
+    for (int g = 0; g < 2; ++g) {
+      const double psi[2] = {1.0 - gz[g], gz[g]};
+      const double dpsi[2] = {-1.0, 1.0};
+      double J[3][3] = {{0.0}};
+      double fq = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const int i = 2 * a + b;
+          const double gr[3] = {dlx[a] * psi[b], dly[a] * psi[b], lam[a] * dpsi[b]};
+          for (int r = 0; r < 3; ++r) {
+            const double xr = __ldg(Xg + 3 * (int64_t)cd[i] + r);
+            for (int q = 0; q < 3; ++q) J[r][q] += xr * gr[q];
+          }
+          fq += lam[a] * psi[b] * __ldg(fg + fd[i]);
+        }
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      const double wq = (1.0 / 12.0) * fabs(det) * fq;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 2; ++b) out[2 * a + b] += wq * lam[a] * psi[b];
+    }
+  }
+}
+
+// Stencil rows, area factor and level-0 corner bits of column c (Algorithm
+// 3's outer loop: the lists are read once per column).
+template <bool VAR>
+__device__ __forceinline__ int setup_column(const MassP1Launch &p, int64_t c, ColInfo &ci) {
+  const int lay = VAR ? __ldg(p.cell_layers + c) : p.layers;
+  ci.lay = lay;
+  double x[3], y[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int32_t cb = __ldg(p.cmap + c * 6 + 2 * a), ct = __ldg(p.cmap + c * 6 + 2 * a + 1);
+    const int32_t fb = __ldg(p.fmap + c * 6 + 2 * a), ft = __ldg(p.fmap + c * 6 + 2 * a + 1);
+    const int32_t bb = __ldg(p.bmap + c * 6 + 2 * a), bt = __ldg(p.bmap + c * 6 + 2 * a + 1);
+    ci.cbot[a] = cb;
+    ci.ctop[a] = ct + (lay - 1) * p.coff[2 * a + 1];
+    ci.fbot[a] = fb;
+    ci.ftop[a] = ft + (lay - 1) * p.foff[2 * a + 1];
+    ci.bbot[a] = bb;
+    ci.btop[a] = bt + (lay - 1) * p.boff[2 * a + 1];
+    x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
+    y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
+    ci.rx[a] = __double_as_longlong(x[a]);
+    ci.ry[a] = __double_as_longlong(y[a]);
+  }
+  const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+  ci.alpha = fabs(det2) * (1.0 / 144.0);
+  ci.alpha2 = fabs(det2) * (1.0 / 72.0);
+  return lay + 1;
+}
+
+// (column, level) of item `it` of a group: constant layers by division,
+// variable layers by walking the columns' layer counts.
+template <bool VAR>
+__device__ __forceinline__ void item_pos(const ColInfo *cols, int ncol, int L1, int it, int &cl, int &m) {
+  if (VAR) {
+    cl = 0;
+    m = it;
+    while (cl < ncol && m > cols[cl].lay) { m -= cols[cl].lay + 1; ++cl; }
+  } else {
+    cl = it / L1;
+    m = it - cl * L1;
+  }
+}
+
+struct WLevel {
+  double w[3];  // vertical sums of the three vertices
+  int ok;
+};
+
+// A warp step of the cell pass that meets a prism which is not straight is
+// recorded as (group, first item) and evaluated by k_mass_general instead.
+struct Deferred {
+  int2 *list;
+  unsigned int *count;
+  unsigned int cap;
+};
+
+template <bool VAR>
+__global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(const MassP1Launch p,
+                                                                            const double *__restrict__ W,
+                                                                            Deferred dfr, int cpw) {
+  __shared__ ColInfo cols[kWarps][kMaxCols];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    const int layers = p.layers;
+    const int L1 = layers + 1;
+    int my_items = 0;
+    if (lane < ncol) my_items = setup_column<VAR>(p, c0 + lane, cols[warp][lane]);
+    __syncwarp();
+    const int nitems = VAR ? __reduce_add_sync(kFull, my_items) : ncol * L1;
+    int cl, m;
+    item_pos<VAR>(cols[warp], ncol, L1, lane, cl, m);
+
+    auto load_level = [&](int item, int clx, int mx, WLevel &lv) {
+      lv.w[0] = lv.w[1] = lv.w[2] = 0.0;
+      lv.ok = 1;
+      if (item < nitems) {
+        const ColInfo &ci = cols[warp][clx];
+        const int lay = VAR ? ci.lay : layers;
+        double zz[3];
+        int ok = 1;
+  #pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, lay);
+          const double xa = __ldg(p.X + 3 * cd + 0);
+          const double ya = __ldg(p.X + 3 * cd + 1);
+          zz[a] = __ldg(p.X + 3 * cd + 2);
+          ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
+          lv.w[a] = __ldg(W + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+        }
+        ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
+              (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
+        if (VAR && (mx == 0 || mx == lay)) {
+          // bottom or top level of this cell column: only the one layer of the
+          // column touching it counts (the vertex column may extend beyond it)
+          const int mo = mx == 0 ? 1 : mx - 1;
+          const double zo = __ldg(p.X + 3 * (int64_t)dof_at(ci.cbot[0], ci.ctop[0], p.coff[0], mo, lay) + 2);
+          const double h = fabs(zo - zz[0]);
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const double fm = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+            const double fo = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mo, lay));
+            lv.w[a] = h * fma(2.0, fm, fo);
+          }
+        }
+        lv.ok = ok;
+      }
+    };
+
+    WLevel cur, nxt;
+    int item = lane;
+    load_level(item, cl, m, cur);
+    int carry_ok = 1;
+
+    for (int base = 0; base < nitems; base += 32) {
+      int ncl = cl, nm = m + 32;
+      if (VAR) {
+        while (ncl < ncol && nm > cols[warp][ncl].lay) { nm -= cols[warp][ncl].lay + 1; ++ncl; }
+      } else {
+        while (nm >= L1) { nm -= L1; ++ncl; }
+      }
+      const int nitem = item + 32;
+      if (base + 32 < nitems) load_level(nitem, ncl < ncol ? ncl : ncol - 1, nm, nxt);
+      else { nxt.w[0] = nxt.w[1] = nxt.w[2] = 0.0; nxt.ok = 1; }
+
+      const bool valid = item < nitems;
+      const ColInfo &ci = cols[warp][valid ? cl : 0];
+      const int lay = VAR ? ci.lay : layers;
+      const int nxt_ok0 = __shfl_sync(kFull, nxt.ok, 0);
+      const bool step_ok = __all_sync(kFull, cur.ok) && carry_ok && nxt_ok0;
+      if (step_ok) {
+        // value_a = alpha (w_a + w_0 + w_1 + w_2): one DMUL and five DFMA
+        const double aw = fma(ci.alpha, cur.w[0], fma(ci.alpha, cur.w[1], ci.alpha * cur.w[2]));
+        double val[3];
+  #pragma unroll
+        for (int a = 0; a < 3; ++a) val[a] = fma(ci.alpha, cur.w[a], aw);
+        if (valid) {
+  #pragma unroll
+          for (int a = 0; a < 3; ++a)
+            atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, lay), val[a]);
+        }
+      } else if (lane == 0) {
+        const unsigned int slot = atomicAdd(dfr.count, 1u);
+        if (slot < dfr.cap) dfr.list[slot] = make_int2((int)grp, base);
+        else atomicOr(p.err, EXT_DERR_BOUNDS);
+      }
+      carry_ok = __shfl_sync(kFull, cur.ok, 31);
+      cur = nxt;
+      cl = ncl;
+      m = nm;
+      item = nitem;
+    }
+    __syncwarp();
+  }
+}
+
+// The deferred warp steps: every item of the step evaluates the two element
+// integrals touching its level with the 6-point rule and the general Jacobian.
+template <bool VAR>
+__global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch p, Deferred dfr, int cpw) {
+  __shared__ ColInfo cols[kWarps][kMaxCols];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const unsigned int n = min(*dfr.count, dfr.cap);
+  for (unsigned int e = blockIdx.x * kWarps + warp; e < n; e += gridDim.x * kWarps) {
+    const int2 en = dfr.list[e];
+    const int64_t c0 = (int64_t)en.x * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    int my_items = 0;
+    if (lane < ncol) my_items = setup_column<VAR>(p, c0 + lane, cols[warp][lane]);
+    __syncwarp();
+    const int nitems = VAR ? __reduce_add_sync(kFull, my_items) : ncol * (p.layers + 1);
+    const int it = en.y + lane;
+    if (it < nitems) {
+      int cl, m;
+      item_pos<VAR>(cols[warp], ncol, p.layers + 1, it, cl, m);
+      const ColInfo &ci = cols[warp][cl];
+      const int lay = VAR ? ci.lay : p.layers;
+      double val[3] = {0.0, 0.0, 0.0};
+      for (int half = 0; half < 2; ++half) {
+        const int l = half == 0 ? m - 1 : m;
+        if (l < 0 || l >= lay) continue;
+        int32_t cd[6], fd[6];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 2; ++b) {
+            cd[2 * a + b] = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], l + b, lay);
+            fd[2 * a + b] = dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], l + b, lay);
+          }
+        double out[6];
+        prism_general_g(p.X, p.f, cd, fd, out);
+        for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
+      }
+      for (int a = 0; a < 3; ++a) atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, lay), val[a]);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+#ifndef EXT_MASS_SPLIT
+#define EXT_MASS_SPLIT 1  // 1: vertex-column sums then the cell pass; 0: one fused cell pass
+#endif
 
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
@@ -333,17 +685,59 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[2] = {0, 0}, sms = 0;  // per process: one GPU model
-  if (resident[var] == 0) {
+  static int resident[4] = {0, 0, 0, 0}, sms = 0;  // per process: one GPU model
+  const int slot = (var ? 1 : 0) + (EXT_MASS_SPLIT ? 2 : 0);
+  if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_mass_p1<true>, kWarps * 32, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_mass_p1<false>, kWarps * 32, 0);
-    if (resident[var] < 1) resident[var] = 1;
+    if (EXT_MASS_SPLIT) {
+      if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_cells<true>, kWarps * 32, 0);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_cells<false>, kWarps * 32, 0);
+    } else {
+      if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_p1<true>, kWarps * 32, 0);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_p1<false>, kWarps * 32, 0);
+    }
+    if (resident[slot] < 1) resident[slot] = 1;
   }
-  if (blocks > (int64_t)resident[var] * sms) blocks = (int64_t)resident[var] * sms;
-  if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
-  else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
-  return cudaGetLastError();
+  if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
+  if (!EXT_MASS_SPLIT) {
+    if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+    else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+    return cudaGetLastError();
+  }
+  // The vertical sums and the list of deferred warp steps go to
+  // stream-ordered scratch, so launches on different streams never share it.
+  const int64_t n = p.nf;
+  const double items = (var ? p.mean_layers + 1.0 : (double)(p.layers + 1)) * (double)p.ncells;
+  const int64_t cap64 = (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
+  const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
+  const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) + 255) & ~(size_t)255;
+  char *scr = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s);
+  if (e != cudaSuccess) return e;
+  double *W = reinterpret_cast<double *>(scr);
+  Deferred dfr;
+  dfr.count = reinterpret_cast<unsigned int *>(scr + wbytes);
+  dfr.list = reinterpret_cast<int2 *>(scr + wbytes + 256);
+  dfr.cap = cap;
+  e = cudaMemsetAsync(dfr.count, 0, sizeof(unsigned int), s);
+  int64_t vb = (n + 255) / 256;
+  if (vb > (int64_t)sms * 8) vb = (int64_t)sms * 8;
+  if (vb < 1) vb = 1;
+  const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
+  if (e == cudaSuccess) {
+    if (var) {
+      k_vsum<true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col);
+      k_mass_cells<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw);
+      k_mass_general<true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, cpw);
+    } else {
+      k_vsum<false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col);
+      k_mass_cells<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw);
+      k_mass_general<false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, cpw);
+    }
+    e = cudaGetLastError();
+  }
+  const cudaError_t ef = cudaFreeAsync(scr, s);
+  return e != cudaSuccess ? e : ef;
 }
