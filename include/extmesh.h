@@ -74,6 +74,16 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  * EXT_K_RHS_P1P1    [coords READ, f READ, b INC] on prisms, all CG1xCG1:
  *                   b_i += int_cell f_h phi_i dx  (the residual I_1, Sec. 4.1.1).
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
+ *                   Both run as three kernels: vertical sums of the input per
+ *                   vertex level, the cell pass, and a pass over the warp steps
+ *                   that met a prism which is not straight (6-point rule, general
+ *                   Jacobian).  The sums and that list live in scratch taken
+ *                   from the device's default stream-ordered pool
+ *                   (cudaMallocAsync / cudaFreeAsync on `stream`: about 8 bytes
+ *                   per DoF of f plus 1 byte per item), so launches on different
+ *                   streams never share it and the launch can be captured in a
+ *                   CUDA graph; EXT_ECUDA if the pool cannot supply it.
+ *                   Coordinates must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
  *                   interpolation, out at DG1 node (vertex a, level b) = x there.
  * EXT_K_U2V_FWD     [coords READ, u READ, F INC|WRITE]: F_i += int u_h^2 phi_i dx,
