@@ -79,8 +79,9 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   that met a prism which is not straight (6-point rule, general
  *                   Jacobian).  The sums and that list live in scratch taken
  *                   from the device's default stream-ordered pool
- *                   (cudaMallocAsync / cudaFreeAsync on `stream`: about 8 bytes
- *                   per DoF of f plus 1 byte per item), so launches on different
+ *                   (cudaMallocAsync / cudaFreeAsync on `stream`: 8 bytes per
+ *                   DoF of f, 24 on a mesh with variable layers, plus at most 1
+ *                   byte per item), so launches on different
  *                   streams never share it and the launch can be captured in a
  *                   CUDA graph; EXT_ECUDA if the pool cannot supply it.
  *                   Coordinates must be finite.

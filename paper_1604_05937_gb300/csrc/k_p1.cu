@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
 
 // w over the DoFs [0, n) of a CG1xCG1 field; `col` = layers + 1 (constant
 // layers: level m = d mod col, ends have one layer) or unused (VAR: the ends
-// of vertex columns are never read).
+// of vertex columns are never read; W holds 3n values: w, the upper half
+// |h_hi| (2 f + f_hi) and the lower half |h_lo| (f_lo + 2 f)).
 template <bool VAR>
 __global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, const double *__restrict__ f,
                                               double *__restrict__ W, int64_t n, FastDiv col) {
@@ -427,7 +428,19 @@ __global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, cons
       const long long kl = lo_end ? 0LL : -1LL, kh = hi_end ? 0LL : -1LL;
       const double al = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fl)) & kl);
       const double bh = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fr)) & kh);
-      if (d < n) W[d] = fma(fabs(hl), al, fabs(hh) * bh);
+      if (VAR) {
+        // variable layers: also the one-layer halves, which the bottom (upper
+        // half) and top (lower half) levels of a cell column use
+        const double up = fabs(hh) * bh;
+        const double lo = fabs(hl) * al;
+        if (d < n) {
+          W[d] = lo + up;
+          W[n + d] = up;
+          W[2 * n + d] = lo;
+        }
+      } else if (d < n) {
+        W[d] = fma(fabs(hl), al, fabs(hh) * bh);
+      }
     }
   }
 }
@@ -552,6 +565,11 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
         const int lay = VAR ? ci.lay : layers;
         double zz[3];
         int ok = 1;
+        // variable layers: the bottom and top levels of this cell column take
+        // the one-layer half that lies inside the column (the vertex column
+        // may extend beyond it)
+        const double *src = W;
+        if (VAR) src = mx == 0 ? W + p.nf : (mx == lay ? W + 2 * p.nf : W);
   #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, lay);
@@ -559,23 +577,10 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
           const double ya = __ldg(p.X + 3 * cd + 1);
           zz[a] = __ldg(p.X + 3 * cd + 2);
           ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
-          lv.w[a] = __ldg(W + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+          lv.w[a] = __ldg(src + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
         }
         ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
               (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
-        if (VAR && (mx == 0 || mx == lay)) {
-          // bottom or top level of this cell column: only the one layer of the
-          // column touching it counts (the vertex column may extend beyond it)
-          const int mo = mx == 0 ? 1 : mx - 1;
-          const double zo = __ldg(p.X + 3 * (int64_t)dof_at(ci.cbot[0], ci.ctop[0], p.coff[0], mo, lay) + 2);
-          const double h = fabs(zo - zz[0]);
-  #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const double fm = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
-            const double fo = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mo, lay));
-            lv.w[a] = h * fma(2.0, fm, fo);
-          }
-        }
         lv.ok = ok;
       }
     };
@@ -712,7 +717,7 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const double items = (var ? p.mean_layers + 1.0 : (double)(p.layers + 1)) * (double)p.ncells;
   const int64_t cap64 = (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
-  const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) + 255) & ~(size_t)255;
+  const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) * (var ? 3 : 1) + 255) & ~(size_t)255;
   char *scr = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s);
   if (e != cudaSuccess) return e;
