@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_copy_dg_scalar(const CopyDGLaunch 
   }
 }
 
+#if EXT_INTERP_TILE == 0
 // out(DG1xDG1 node 2a+b of cell c, layer l) = x(vertex a, level l+b).  Pair
 // index v covers slots (2a, 2a+1) of one layer: t = 2v = c*6L + 6l + 2a.  The
 // P1xP1 DoFs are x_map[c][2a] + l*offset (bottom) and x_map[c][2a+1] +
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1(const InterpDG1Launch p
     }
   }
 }
+#endif
 
 // Tiled form of k_interp_dg1: a CTA takes EXT_INTERP_TILE consecutive base
 // columns, stages their two stencil rows in shared memory once, then streams
@@ -250,6 +252,8 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1_var(const InterpDG1Laun
   __shared__ uint32_t wsum[TILE / 32];
   __shared__ int32_t xrow[TILE][6];
   __shared__ int32_t obase[TILE];
+  constexpr int kWarps = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t c0 = tile * TILE;
     const int ncol = (int)(p.ncells - c0 < TILE ? p.ncells - c0 : TILE);
@@ -258,14 +262,19 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1_var(const InterpDG1Laun
     for (int i = threadIdx.x; i < ncol; i += kThreads) obase[i] = __ldg(p.omap + (c0 + i) * 6);
     tile_prefix<TILE>(p.cell_layers, c0, ncol, 3u, pre, wsum);  // three pairs per layer
     const uint32_t npairs = pre[ncol];
-    for (uint32_t v = threadIdx.x; v < npairs; v += UNROLL * kThreads) {
+    // each warp streams one contiguous eighth of the tile's pairs, lanes on
+    // consecutive pairs; a lane finds its column once and then walks forward
+    const uint32_t w0 = (uint32_t)(((uint64_t)npairs * warp) / kWarps);
+    const uint32_t w1 = (uint32_t)(((uint64_t)npairs * (warp + 1)) / kWarps);
+    int cl = tile_find<TILE>(pre, ncol, w0 + lane < npairs ? w0 + lane : (npairs ? npairs - 1 : 0));
+    for (uint32_t v = w0 + lane; v < w1; v += UNROLL * 32) {
       double2 val[UNROLL];
       uint32_t dst[UNROLL];
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
-        const uint32_t vv = v + u * kThreads;
-        if (vv < npairs) {
-          const int cl = tile_find<TILE>(pre, ncol, vv);
+        const uint32_t vv = v + u * 32;
+        if (vv < w1) {
+          while (pre[cl + 1] <= vv) ++cl;
           const uint32_t q = vv - pre[cl];  // pair within the column: 3 l + a
           const uint32_t l = fdiv(q, three);
           const uint32_t a = q - 3u * l;
@@ -277,8 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1_var(const InterpDG1Laun
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
-        const uint32_t vv = v + u * kThreads;
-        if (vv < npairs) st_stream2(p.out + dst[u], val[u]);
+        const uint32_t vv = v + u * 32;
+        if (vv < w1) st_stream2(p.out + dst[u], val[u]);
       }
     }
   }
@@ -327,12 +336,12 @@ cudaError_t launch_interp_dg1(const InterpDG1Launch &p, cudaStream_t s) {
   const uint64_t colsize = 6ull * p.layers;
   const uint64_t n = colsize * (uint64_t)p.ncells;
   if (n == 0) return cudaSuccess;
-  const uint32_t npairs = (uint32_t)(n / 2);
 #if EXT_INTERP_TILE > 0
   const int64_t ntiles = (p.ncells + EXT_INTERP_TILE - 1) / EXT_INTERP_TILE;
   const int64_t grid = ntiles < 152 * 8 ? ntiles : 152 * 8;
   k_interp_dg1_tile<EXT_INTERP_TILE, EXT_INTERP_UNROLL><<<(unsigned)grid, kThreads, 0, s>>>(p, make_fastdiv(3u), ntiles);
 #else
+  const uint32_t npairs = (uint32_t)(n / 2);
   k_interp_dg1<<<grid_for(npairs, kUnroll), kThreads, 0, s>>>(p, make_fastdiv((uint32_t)colsize),
                                                               make_fastdiv(6u), npairs);
 #endif
