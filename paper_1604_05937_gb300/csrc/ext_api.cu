@@ -643,6 +643,14 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.nh = h == 1 ? 1 : 3;
       p.jump = jump ? 1 : 0;
       const int nv = v == 1 ? 1 : 2;
+      p.nv = nv;
+      // a vertically continuous space has no jump across horizontal facets;
+      // a space discontinuous in both directions keeps every DoF in one cell
+      // (the cell-owned form measured faster than facet-centric atomics for
+      // DG1xDG1 only: 3.28 vs 4.37 ms at 1M x 100; slower for the others)
+      p.mode = !jump ? 0 : (v == 0 ? 2 : (h == 2 && v == 2 ? 1 : 0));
+      if (p.mode == 1 && ((((uintptr_t)args[1].data) | ((uintptr_t)args[2].data)) & 15) != 0)
+        p.mode = 0;  // the cell-owned form moves DoF pairs with 16-byte accesses
       int32_t slot[6];
       prism_pair_slots(h, v, p.nh, nv, slot);
       for (int a = 0; a < p.nh; ++a) {

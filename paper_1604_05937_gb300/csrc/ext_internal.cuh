@@ -174,6 +174,8 @@ struct FacetLaunch {
   int32_t layers;
   int32_t nh;             // horizontal nodes: 1 (DG0) or 3 (CG1, DG1)
   int32_t jump;           // 0: facet mass, 1: interior-facet jump
+  int32_t nv;             // vertical nodes of the space: 1 (DG0) or 2 (CG1, DG1)
+  int32_t mode;           // jump: 0 facet-centric atomics, 1 cell-owned DoFs (DG x DG), 2 none (CG1 vertical)
   const int32_t *cmap;    // coords map (k = 6)
   int32_t coff[6];
   const int32_t *fmap;    // f/u and b/r share this numbering

@@ -26,6 +26,8 @@ constexpr int kMaxCols = 32;
 struct TPCol {
   double alpha;              // |2A| * (1/2)(1/12 if NH=3)(1/6 if NV=2): c = alpha |h|
   long long rx[3], ry[3];    // level-0 x, y bit patterns
+  int32_t cm[6];             // the column's coordinate stencil row (layer 0)
+  int32_t fm[6];             // its f/b DoFs of node (a, b) at layer 0
   int lay;                   // layers of this column
 };
 
@@ -82,8 +84,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
       my_items = lay;
       double x[3], y[3];
 #pragma unroll
+      for (int i = 0; i < 6; ++i) cols[warp][lane].cm[i] = __ldg(p.cmap + c * 6 + i);
+#pragma unroll
+      for (int i = 0; i < NH * NV; ++i) cols[warp][lane].fm[i] = __ldg(p.fmap + c * p.k + p.slot[i]);
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const int64_t cd = __ldg(p.cmap + c * 6 + 2 * a);
+        const int64_t cd = cols[warp][lane].cm[2 * a];
         x[a] = __ldg(p.X + 3 * cd + 0);
         y[a] = __ldg(p.X + 3 * cd + 1);
         cols[warp][lane].rx[a] = __double_as_longlong(x[a]);
@@ -105,13 +111,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
     }
     for (int base = 0; base < nitems; base += 32) {
       if (base + lane < nitems) {
-        const int64_t c = c0 + cl;
         const TPCol &ci = cols[warp][cl];
         double Xl[6][3];
         int ok = 1;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-          const int64_t cd = (int64_t)__ldg(p.cmap + c * 6 + i) + (int64_t)l * p.coff[i];
+          const int64_t cd = (int64_t)ci.cm[i] + (int64_t)l * p.coff[i];
           Xl[i][0] = __ldg(p.X + 3 * cd + 0);
           Xl[i][1] = __ldg(p.X + 3 * cd + 1);
           Xl[i][2] = __ldg(p.X + 3 * cd + 2);
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
         double f[NH * NV], b[NH * NV];
 #pragma unroll
         for (int i = 0; i < NH * NV; ++i) {
-          dof[i] = __ldg(p.fmap + c * p.k + p.slot[i]) + l * p.off[i];
+          dof[i] = ci.fm[i] + l * p.off[i];
           f[i] = __ldg(p.f + dof[i]);
         }
         if (ok) {
