@@ -33,6 +33,8 @@
 // the three z values of a level); a warp step touching any other prism
 // evaluates the element integrals with the full 6-point rule and the general
 // Jacobian instead, so any coordinate field is handled.
+#include <cstdlib>
+
 #include "ext_internal.cuh"
 #include "fastdiv.cuh"
 
@@ -674,12 +676,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
   }
 }
 
+
+
+// Resident CTAs per SM of a kernel (one GPU model per process).
+template <typename K>
+int resident_ctas(K kernel, int &cache) {
+  if (cache == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache, kernel, kWarps * 32, 0);
+    if (cache < 1) cache = 1;
+  }
+  return cache;
+}
+
 }  // namespace
 
-#ifndef EXT_MASS_SPLIT
-#define EXT_MASS_SPLIT 1  // 1: vertex-column sums then the cell pass; 0: one fused cell pass
-#endif
-
+// The split form runs unless its scratch cannot be allocated, or the
+// environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
+// (each cell evaluates its own vertical sums; no scratch; the same results
+// up to rounding).
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -689,27 +703,17 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw < 1) cpw = 1;
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
-  int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[4] = {0, 0, 0, 0}, sms = 0;  // per process: one GPU model
-  const int slot = (var ? 1 : 0) + (EXT_MASS_SPLIT ? 2 : 0);
-  if (resident[slot] == 0) {
+  const int64_t blocks0 = (warps + kWarps - 1) / kWarps;
+  static int sms = 0, fused_env = -1;
+  static int res_cells[2] = {0, 0}, res_fused[2] = {0, 0};
+  if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (EXT_MASS_SPLIT) {
-      if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_cells<true>, kWarps * 32, 0);
-      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_cells<false>, kWarps * 32, 0);
-    } else {
-      if (var) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_p1<true>, kWarps * 32, 0);
-      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_p1<false>, kWarps * 32, 0);
-    }
-    if (resident[slot] < 1) resident[slot] = 1;
   }
-  if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  if (!EXT_MASS_SPLIT) {
-    if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
-    else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
-    return cudaGetLastError();
+  if (fused_env < 0) {
+    const char *ev = getenv("EXTMESH_MASS_FUSED");
+    fused_env = (ev && ev[0] == '1') ? 1 : 0;
   }
   // The vertical sums and the list of deferred warp steps go to
   // stream-ordered scratch, so launches on different streams never share it.
@@ -719,14 +723,26 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) * (var ? 3 : 1) + 255) & ~(size_t)255;
   char *scr = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s);
-  if (e != cudaSuccess) return e;
+  if (!fused_env &&
+      cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s) != cudaSuccess) {
+    (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
+    scr = nullptr;
+  }
+  if (!scr) {
+    const int res = var ? resident_ctas(k_mass_p1<true>, res_fused[1]) : resident_ctas(k_mass_p1<false>, res_fused[0]);
+    const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
+    if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+    else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+    return cudaGetLastError();
+  }
+  const int res = var ? resident_ctas(k_mass_cells<true>, res_cells[1]) : resident_ctas(k_mass_cells<false>, res_cells[0]);
+  const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
   double *W = reinterpret_cast<double *>(scr);
   Deferred dfr;
   dfr.count = reinterpret_cast<unsigned int *>(scr + wbytes);
   dfr.list = reinterpret_cast<int2 *>(scr + wbytes + 256);
   dfr.cap = cap;
-  e = cudaMemsetAsync(dfr.count, 0, sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(dfr.count, 0, sizeof(unsigned int), s);
   int64_t vb = (n + 255) / 256;
   if (vb > (int64_t)sms * 8) vb = (int64_t)sms * 8;
   if (vb < 1) vb = 1;

@@ -168,6 +168,25 @@ def test_mass_general_geometry_fallback():
     close(got, ref, absr)
 
 
+def test_mass_single_pass_form():
+    """The single-pass kernel (the fallback when the split form's scratch cannot
+    be allocated, forced here by EXTMESH_MASS_FUSED=1 in a child process) passes
+    the same parity tests."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, EXTMESH_MASS_FUSED="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(root, "tests", "test_gpu_parity.py"),
+                        os.path.join(root, "tests", "test_gpu_var_facets.py"), "-k",
+                        "mass_action_parity or rhs_sin_cos or mass_general_geometry or volume_pin or tp_parity "
+                        "or var_mass"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:]
+    assert " passed" in r.stdout
+
+
 def test_mass_volume_pin_on_gpu():
     m = meshgen.tri_mesh(20, seed=42)
     got, ref, absr = _mass_case(m, 13, f_of_X=lambda X: np.ones(X.shape[0]))
