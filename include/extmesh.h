@@ -83,9 +83,10 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   DoF of f, 24 on a mesh with variable layers, plus at most 1
  *                   byte per item), so launches on different
  *                   streams never share it and the launch can be captured in a
- *                   CUDA graph.  If the pool cannot supply it, a single-pass
- *                   kernel that needs no scratch (every cell forms its own
- *                   vertical sums) runs instead; the environment variable
+ *                   CUDA graph.  If the pool cannot supply it, or the columns
+ *                   are one or two layers tall (mean), a single-pass kernel
+ *                   that needs no scratch (every cell forms its own vertical
+ *                   sums) runs instead; the environment variable
  *                   EXTMESH_MASS_FUSED=1, read once per process, selects it
  *                   always.  Coordinates must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal

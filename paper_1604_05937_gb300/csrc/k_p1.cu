@@ -690,10 +690,10 @@ int resident_ctas(K kernel, int &cache) {
 
 }  // namespace
 
-// The split form runs unless its scratch cannot be allocated, or the
-// environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
-// (each cell evaluates its own vertical sums; no scratch; the same results
-// up to rounding).
+// The split form runs unless the columns are one or two layers tall, its
+// scratch cannot be allocated, or the environment variable
+// EXTMESH_MASS_FUSED=1 asks for the single-pass kernel (each cell evaluates
+// its own vertical sums; no scratch; the same results up to rounding).
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -723,7 +723,10 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) * (var ? 3 : 1) + 255) & ~(size_t)255;
   char *scr = nullptr;
-  if (!fused_env &&
+  // with one or two layers per column a vertex column's sums serve only one
+  // or two levels: the extra pass and its scratch cost more than they save
+  const bool short_columns = L1 <= 3.0;
+  if (!fused_env && !short_columns &&
       cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;

@@ -183,3 +183,68 @@ def test_fullsize_batched_64_meshes():
         d = sampled_dofs(osp, sample, L)
         close_at(per[i][3][1].cpu().numpy(), Fr, aF, d)
         close_at(per[i][4][1].cpu().numpy(), Gr, aG, d)
+
+
+def test_fullsize_variable_layers_1M():
+    """The bathymetry workload of the variable-layer benchmark (999,698 columns,
+    top level 100): numbering, coordinates and DG1 interpolation compared in
+    full, the mass action and the DG1xDG1 interior-facet jump on sampled
+    columns."""
+    m = meshgen.tri_mesh(707, seed=1604, order="rcm")
+    first, lay = meshgen.column_layers(m, 100, 1674, "bathymetry")
+    gm = E.Mesh(m.cells, m.xy, cell_first=first, cell_layers=lay)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    p1 = E.Space(gm, "CG1xCG1")
+    dg = E.Space(gm, "DG1xDG1")
+    ocs, X = O.coords_var(m.cells, m.xy, first, lay)
+    op1 = O.number_var(m.cells, m.nverts, first, lay, P1)
+    odg = O.number_var(m.cells, m.nverts, first, lay, O.DELTA["DG1xDG1"])
+    for g, o in ((p1, op1), (dg, odg), (cs, ocs)):
+        gmap, goff = g.stencil_map()
+        assert g.ndofs == o.ndofs
+        np.testing.assert_array_equal(gmap, o.map)
+        np.testing.assert_array_equal(goff, o.offset)
+    Xg = E.extrude_coords(gm, cs)
+    np.testing.assert_array_equal(Xg.cpu().numpy(), X)
+    x = meshgen.uniform_field(op1.ndofs, 1675)
+    xd = torch.from_numpy(x).to(dev)
+    y, out = p1.zeros(), dg.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xg, E.EXT_READ), (p1, xd, E.EXT_READ), (p1, y, E.EXT_INC))
+    E.par_loop(gm, E.EXT_K_INTERP_DG1, (p1, xd, E.EXT_READ), (dg, out, E.EXT_WRITE))
+    u = meshgen.uniform_field(odg.ndofs, 1676)
+    r = dg.zeros()
+    E.par_loop(gm, E.EXT_K_HFACET_JUMP, (cs, Xg, E.EXT_READ), (dg, torch.from_numpy(u).to(dev), E.EXT_READ),
+               (dg, r, E.EXT_INC))
+    E.ext_sync_check()
+    rng = np.random.default_rng(10)
+    sample = np.concatenate([rng.choice(m.ncells, 300, replace=False), [0, m.ncells - 1]])
+    cl = closure(m.cells, sample)
+    cc = np.ascontiguousarray(m.cells[cl])
+
+    def subv(space, idx):
+        return O.Space(delta=space.delta, layers=space.layers, ndofs=space.ndofs, k=space.k,
+                       map=np.ascontiguousarray(space.map[idx]), offset=space.offset)
+
+    def dofs_of(space, idx):
+        out_ = [space.map[c].astype(np.int64)[None, :] + np.arange(lay[c])[:, None] * space.offset[None, :]
+                for c in idx]
+        return np.unique(np.concatenate([o.ravel() for o in out_]))
+
+    ref, absr = np.zeros(op1.ndofs), np.zeros(op1.ndofs)
+    O.par_loop(O.K_MASS, cc, op1.layers, [(subv(ocs, cl), X, 3, O.READ), (subv(op1, cl), x, 1, O.READ),
+                                          (subv(op1, cl), ref, 1, O.INC, absr)],
+               cell_first=first[cl], cell_layers=lay[cl])
+    close_at(y.cpu().numpy(), ref, absr, dofs_of(op1, sample))
+    oref = np.full(odg.ndofs, np.nan)
+    O.par_loop(O.K_INTERP, np.ascontiguousarray(m.cells[sample]), op1.layers,
+               [(subv(op1, sample), x, 1, O.READ), (subv(odg, sample), oref, 1, O.WRITE)],
+               cell_first=first[sample], cell_layers=lay[sample])
+    d = dofs_of(odg, sample)
+    np.testing.assert_array_equal(out.cpu().numpy()[d], oref[d])
+    # the jump couples only the layers of one column: the sample alone is its closure
+    jref, jabs = np.zeros(odg.ndofs), np.zeros(odg.ndofs)
+    O.set_tp_element(O.DG1, O.DG1)
+    O.par_loop(O.K_HFACET_JUMP, np.ascontiguousarray(m.cells[sample]), op1.layers,
+               [(subv(ocs, sample), X, 3, O.READ), (subv(odg, sample), u, 1, O.READ),
+                (subv(odg, sample), jref, 1, O.INC, jabs)], cell_first=first[sample], cell_layers=lay[sample])
+    close_at(r.cpu().numpy(), jref, jabs, d)
