@@ -55,11 +55,17 @@ VSUM_OPS_PER_DOF = 5
 CELL_OPS_PER_ITEM = 6
 CELL_ATOMICS_PER_ITEM = 3
 CELLWISE_OPS_PER_ITEM = 18
+SINGLE_PASS_SM_OPS_PER_ITEM = 13
+P1_SPLIT_MIN_ITEMS = 1_000_000
 P1_KERNELS_PER_LAUNCH = 3
 
 
 def p1_ops(ndofs: int, items: int) -> int:
-    """FP64 operations of one P1xP1 RHS / mass-action launch (split form)."""
+    """FP64 operations of one P1xP1 RHS / mass-action launch: the split form,
+    or below a million items the single-pass kernel the library runs there
+    (13 operations per item on the SM, the horizontal sum in L2 atomics)."""
+    if items < P1_SPLIT_MIN_ITEMS:
+        return SINGLE_PASS_SM_OPS_PER_ITEM * items
     return VSUM_OPS_PER_DOF * ndofs + CELL_OPS_PER_ITEM * items
 
 
@@ -727,10 +733,10 @@ def run_cfg5(args, rank, world, local):
 # FP64 ops per unit of the nine-space mass kernels (straight prisms); unit =
 # cell-layer (see k_tp.cu); CG1xCG1 runs the P1xP1 split form (p1_ops)
 TP_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), None), ("CG1xDG0", (0, 1, 0, 0, 0, 0), 8),
-             ("CG1xDG1", (0, 2, 0, 0, 0, 0), 23), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 7),
+             ("CG1xDG1", (0, 2, 0, 0, 0, 0), 20), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 7),
              ("DG0xDG0", (0, 0, 0, 0, 0, 1), 3), ("DG0xDG1", (0, 0, 0, 0, 0, 2), 7),
-             ("DG1xCG1", (0, 0, 0, 0, 3, 0), 23), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 8),
-             ("DG1xDG1", (0, 0, 0, 0, 0, 6), 23)]
+             ("DG1xCG1", (0, 0, 0, 0, 3, 0), 20), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 8),
+             ("DG1xDG1", (0, 0, 0, 0, 0, 6), 20)]
 
 
 def run_cfg6(args, rank, world, local):
@@ -805,12 +811,12 @@ def run_cfg6(args, rank, world, local):
                                 "RCM and random base order", "l2": "flushed"},
                    extra, clocks, launches)
 
-# FP64 operations per facet of the straight-column facet kernels: surface mass
-# with three nodes: c = |n|/24, S = sum f (2), c S, three fma = 7; one node:
-# |n|/2 and the product = 2.  Jump with three nodes: three differences, c,
-# S (2), c S, three fma = 10; one node: 3.
-FACET_MASS_OPS = {3: 7, 1: 2}
-FACET_JUMP_OPS = {3: 10, 1: 3}
+# FP64 ops per facet of the straight-column facet kernels (the weight factor
+# |2A|/24 or |2A|/2 is hoisted per column): surface mass with three nodes, c g2,
+# two DFMA for c sum g and three DFMA = 6; one node: 1.  Jump: three (or one)
+# differences more: 9 and 2.
+FACET_MASS_OPS = {3: 6, 1: 1}
+FACET_JUMP_OPS = {3: 9, 1: 2}
 FACET_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), 3), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 1),
                 ("DG1xCG1", (0, 0, 0, 0, 3, 0), 3)]
 JUMP_SPACES = [("DG0xDG0", (0, 0, 0, 0, 0, 1), 1), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 3),

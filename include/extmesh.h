@@ -83,12 +83,13 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   DoF of f, 24 on a mesh with variable layers, plus at most 1
  *                   byte per item), so launches on different
  *                   streams never share it and the launch can be captured in a
- *                   CUDA graph.  If the pool cannot supply it, or the columns
- *                   are one or two layers tall (mean), a single-pass kernel
- *                   that needs no scratch (every cell forms its own vertical
- *                   sums) runs instead; the environment variable
- *                   EXTMESH_MASS_FUSED=1, read once per process, selects it
- *                   always.  Coordinates must be finite.
+ *                   CUDA graph.  If the pool cannot supply it, or the launch
+ *                   has fewer than a million (column, level) items, a
+ *                   single-pass kernel that needs no scratch (every cell forms
+ *                   its own vertical sums) runs instead.  The environment
+ *                   variable EXTMESH_MASS_FUSED, read once per process, selects
+ *                   the single pass (1) or the split form (0) at any size.
+ *                   Coordinates must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
  *                   interpolation, out at DG1 node (vertex a, level b) = x there.
  * EXT_K_U2V_FWD     [coords READ, u READ, F INC|WRITE]: F_i += int u_h^2 phi_i dx,

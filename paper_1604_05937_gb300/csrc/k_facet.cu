@@ -32,7 +32,8 @@ constexpr unsigned kFull = 0xffffffffu;
 struct FacetCol {
   int32_t cb[3], ct[3];  // coords DoF of vertex a at the bottom level, at the top level
   int32_t flo[3], fhi[3];
-  double n2;             // |2A| of the base triangle
+  double wf;             // |2A| / 24 (three nodes) or |2A| / 2 (one node): the
+                         // weight factor of a facet of a straight column
   long long rx[3], ry[3];
   int lay;
 };
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_facet(const FacetLaunch p, int 
         ci.flo[a] = __ldg(p.fmap + c * p.k + p.slot_lo[a]);
         ci.fhi[a] = __ldg(p.fmap + c * p.k + p.slot_hi[a]);
       }
-      ci.n2 = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]));
+      ci.wf = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * (NH == 3 ? 1.0 / 24.0 : 0.5);
     }
     __syncwarp();
     const int nitems = __reduce_add_sync(kFull, my_items);
@@ -97,9 +98,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_facet(const FacetLaunch p, int 
         }
         ok &= (__double_as_longlong(X[0][2]) == __double_as_longlong(X[1][2])) &
               (__double_as_longlong(X[0][2]) == __double_as_longlong(X[2][2]));
-        double ds;
+        double cc;  // |n| / 24 (three nodes) or |n| / 2 (one node)
         if (ok) {
-          ds = ci.n2;
+          cc = ci.wf;
         } else {
           double e1[3], e2[3];
 #pragma unroll
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_facet(const FacetLaunch p, int 
           const double n0 = e1[1] * e2[2] - e1[2] * e2[1];
           const double n1 = e1[2] * e2[0] - e1[0] * e2[2];
           const double nz = e1[0] * e2[1] - e1[1] * e2[0];
-          ds = sqrt(n0 * n0 + n1 * n1 + nz * nz);
+          cc = sqrt(n0 * n0 + n1 * n1 + nz * nz) * (NH == 3 ? 1.0 / 24.0 : 0.5);
         }
         int32_t dlo[NH], dhi[NH];
         double g[NH];
@@ -130,12 +131,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_facet(const FacetLaunch p, int 
         }
         double v[NH];
         if (NH == 3) {
-          const double cc = ds * (1.0 / 24.0);
-          const double cs = cc * ((g[0] + g[1]) + g[2]);
+          // c (g_a + sum g): one DMUL and five DFMA
+          const double cs = fma(cc, g[0], fma(cc, g[1], cc * g[2]));
 #pragma unroll
           for (int a = 0; a < NH; ++a) v[a] = fma(cc, g[a], cs);
         } else {
-          v[0] = (0.5 * ds) * g[0];
+          v[0] = cc * g[0];
         }
 #pragma unroll
         for (int a = 0; a < NH; ++a) {
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_jump_dg(const FacetLaunch p, in
         ci.ry[a] = __double_as_longlong(y[a]);
       }
       ci.flo[0] = __ldg(p.fmap + c * K);  // the column's first DoF
-      ci.n2 = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]));
+      ci.wf = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * (NH == 3 ? 1.0 / 24.0 : 0.5);
     }
     __syncwarp();
     const int nitems = __reduce_add_sync(kFull, my_items);
@@ -249,9 +250,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_jump_dg(const FacetLaunch p, in
         }
         ok &= (__double_as_longlong(X[0][2]) == __double_as_longlong(X[1][2])) &
               (__double_as_longlong(X[0][2]) == __double_as_longlong(X[2][2]));
-        double ds;
+        double cc;  // |n| / 24 (three nodes) or |n| / 2 (one node)
         if (ok) {
-          ds = ci.n2;
+          cc = ci.wf;
         } else {
           double e1[3], e2[3];
 #pragma unroll
@@ -262,18 +263,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_jump_dg(const FacetLaunch p, in
           const double n0 = e1[1] * e2[2] - e1[2] * e2[1];
           const double n1 = e1[2] * e2[0] - e1[0] * e2[2];
           const double nz = e1[0] * e2[1] - e1[1] * e2[0];
-          ds = sqrt(n0 * n0 + n1 * n1 + nz * nz);
+          cc = sqrt(n0 * n0 + n1 * n1 + nz * nz) * (NH == 3 ? 1.0 / 24.0 : 0.5);
         }
         double g[NH];
 #pragma unroll
         for (int a = 0; a < NH; ++a) g[a] = below[a] - u[a * NV];
         if (NH == 3) {
-          const double cc = ds * (1.0 / 24.0);
-          const double cs = cc * ((g[0] + g[1]) + g[2]);
+          const double cs = fma(cc, g[0], fma(cc, g[1], cc * g[2]));
 #pragma unroll
           for (int a = 0; a < NH; ++a) vb[a] = fma(cc, g[a], cs);
         } else {
-          vb[0] = (0.5 * ds) * g[0];
+          vb[0] = cc * g[0];
         }
       }
       // the top facet's term, evaluated by the lane of the cell above

@@ -690,10 +690,11 @@ int resident_ctas(K kernel, int &cache) {
 
 }  // namespace
 
-// The split form runs unless the columns are one or two layers tall, its
-// scratch cannot be allocated, or the environment variable
-// EXTMESH_MASS_FUSED=1 asks for the single-pass kernel (each cell evaluates
-// its own vertical sums; no scratch; the same results up to rounding).
+// The split form runs unless the launch is small (under a million
+// (column, level) items), its scratch cannot be allocated, or the
+// environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
+// (each cell evaluates its own vertical sums; no scratch; the same results up
+// to rounding); EXTMESH_MASS_FUSED=0 asks for the split form at any size.
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -711,9 +712,9 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (fused_env < 0) {
+  if (fused_env < 0) {  // 1: always the single pass; 0: always the split form; unset: by size
     const char *ev = getenv("EXTMESH_MASS_FUSED");
-    fused_env = (ev && ev[0] == '1') ? 1 : 0;
+    fused_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
   }
   // The vertical sums and the list of deferred warp steps go to
   // stream-ordered scratch, so launches on different streams never share it.
@@ -723,10 +724,10 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) * (var ? 3 : 1) + 255) & ~(size_t)255;
   char *scr = nullptr;
-  // with one or two layers per column a vertex column's sums serve only one
-  // or two levels: the extra pass and its scratch cost more than they save
-  const bool short_columns = L1 <= 3.0;
-  if (!fused_env && !short_columns &&
+  // on a small launch the split form's extra pass, scratch allocation and
+  // launches (about 25 us together) cost more than they save
+  const bool small = items < 1.0e6 && fused_env == 2;
+  if (fused_env != 1 && !small &&
       cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;

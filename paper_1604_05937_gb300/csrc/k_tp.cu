@@ -145,15 +145,17 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
             const double cS = cc * ((f[0] + f[1]) + f[2]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
-          } else {  // NH == 3, NV == 2: b_{a,beta} = c (2 T_{a,beta} + T_{a,1-beta})
-            const double c2 = cc + cc;
-            const double S0 = (f[0] + f[2]) + f[4], S1 = (f[1] + f[3]) + f[5];
-            const double K0 = cc * fma(2.0, S0, S1), K1 = cc * fma(2.0, S1, S0);
+          } else {  // NH == 3, NV == 2: b_{a,beta} = c (t_{a,beta} + T_beta),
+                    // t_{a,beta} = 2 f_{a,beta} + f_{a,1-beta}, T_beta = sum_a t_{a,beta}
+            double t[6];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              b[2 * a] = fma(c2, f[2 * a], fma(cc, f[2 * a + 1], K0));
-              b[2 * a + 1] = fma(c2, f[2 * a + 1], fma(cc, f[2 * a], K1));
+              t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
+              t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
             }
+            const double K0 = cc * ((t[0] + t[2]) + t[4]), K1 = cc * ((t[1] + t[3]) + t[5]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
           }
         } else {
           tp_general<NH, NV>(Xl, f, b);

@@ -168,15 +168,18 @@ def test_mass_general_geometry_fallback():
     close(got, ref, absr)
 
 
-def test_mass_single_pass_form():
-    """The single-pass kernel (the fallback when the split form's scratch cannot
-    be allocated, forced here by EXTMESH_MASS_FUSED=1 in a child process) passes
-    the same parity tests."""
+@pytest.mark.parametrize("form", ["0", "1"])
+def test_mass_forced_form(form):
+    """Both forms of the P1xP1 launch pass the same parity tests: the split
+    form (vertical sums, then the cell pass; the default for launches of a
+    million items or more) and the single-pass kernel (the default below, and
+    the fallback when the split form's scratch cannot be allocated), each
+    forced by EXTMESH_MASS_FUSED in a child process."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, EXTMESH_MASS_FUSED="1")
+    env = dict(os.environ, EXTMESH_MASS_FUSED=form)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(root, "tests", "test_gpu_parity.py"),
                         os.path.join(root, "tests", "test_gpu_var_facets.py"), "-k",
