@@ -21,7 +21,8 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 READ, WRITE, INC = 0, 1, 2
-K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ, K_MASS_TP, K_HFACET_MASS, K_HFACET_JUMP = range(9)
+(K_EXTRUDE, K_COPY, K_MASS, K_INTERP, K_U2V, K_U2V_ADJ, K_MASS_TP, K_HFACET_MASS, K_HFACET_JUMP,
+ K_MASS_DGP) = range(10)
 CG1, DG0, DG1 = 0, 1, 2
 
 # delta((d1,d2)) flattened as [d(0,0), d(0,1), d(1,0), d(1,1), d(2,0), d(2,1)]
@@ -64,6 +65,7 @@ class _Arg(ctypes.Structure):
         ("data", ctypes.c_void_p),
         ("absdata", ctypes.c_void_p),
         ("access", ctypes.c_int32),
+        ("rowptr", ctypes.c_void_p),
     ]
 
 
@@ -116,6 +118,13 @@ def lib():
                                         ctypes.c_void_p]
         L.oracle_hfacet_alg2.restype = None
         L.oracle_hfacet_alg2.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_alg1_ragged.restype = ctypes.c_int64
+        L.oracle_alg1_ragged.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_ragged_map.restype = ctypes.c_int
+        L.oracle_ragged_map.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_par_loop_var.restype = ctypes.c_int
         L.oracle_par_loop_var.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -152,6 +161,7 @@ class Space:
     hoffset: np.ndarray | None = None  # (hk,) their offsets
     cell_first: np.ndarray | None = None   # variable layers: first level of each column
     cell_layers: np.ndarray | None = None  # variable layers: layers of each column
+    rowptr: np.ndarray | None = None       # ragged lists: cell c's entries are map[rowptr[c]:rowptr[c+1]]
 
     def facet(self) -> "Space":
         """The same numbering seen through the horizontal-facet lists."""
@@ -292,9 +302,10 @@ def par_loop(kernel: int, cells: np.ndarray, layers: int, args, base_xy: np.ndar
         assert data.size == sp.ndofs * ncomp, (data.size, sp.ndofs, ncomp)
         if absd is not None:
             assert absd.dtype == np.float64 and absd.size == data.size and absd.flags.c_contiguous
-        keep += [sp.map, sp.offset]
+        keep += [sp.map, sp.offset, sp.rowptr]
         arr[i].map = sp.map.ctypes.data
         arr[i].offset = sp.offset.ctypes.data
+        arr[i].rowptr = None if sp.rowptr is None else sp.rowptr.ctypes.data
         arr[i].k = sp.k
         arr[i].ncomp = ncomp
         arr[i].data = data.ctypes.data
@@ -353,3 +364,55 @@ def coords_var(cells: np.ndarray, xy: np.ndarray, cell_first, cell_layers) -> tu
     par_loop(K_EXTRUDE, cells, sp.layers, [(sp, X, 3, WRITE)], base_xy=xy,
              cell_first=sp.cell_first, cell_layers=sp.cell_layers)
     return sp, X
+
+
+def number_ragged(cells: np.ndarray, nverts: int, dent, layers: int | None = None, cell_first=None,
+                  cell_layers=None, keep_tables: bool = False) -> Space:
+    """Algorithm 1 with per-entity DoF counts dent ((V + E + C) x 2:
+    horizontal, vertical; entities dimension-major), on constant layers or
+    per-column layer ranges.  The lists are ragged (Space.rowptr)."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    dent = np.ascontiguousarray(dent, dtype=np.int32).reshape(-1)
+    ce, ne = derive_edges(cells, nverts)
+    N = np.array([nverts, ne, cells.shape[0]], dtype=np.int64)
+    nent = int(N.sum())
+    if dent.size != 2 * nent:
+        raise ValueError(f"dent needs {nent} x 2 entries")
+    if cell_layers is None:
+        cf = np.zeros(cells.shape[0], np.int32)
+        cl = np.full(cells.shape[0], int(layers), np.int32)
+    else:
+        cf = np.ascontiguousarray(cell_first, dtype=np.int32)
+        cl = np.ascontiguousarray(cell_layers, dtype=np.int32)
+    lo, hi, _, _ = var_ranges(cells, nverts, cf, cl)
+    maxlevel = int((cf + cl).max())
+    L = lib()
+    tabs, ptrs = [], (ctypes.c_void_p * 6)()
+    for t in range(6):
+        d1, d2 = divmod(t, 2)
+        a = np.full((int(N[d1]), maxlevel + 1 - d2), -1, dtype=np.int64)
+        tabs.append(a)
+        ptrs[t] = a.ctypes.data
+    ndofs = L.oracle_alg1_ragged(_p(N), maxlevel, _p(lo), _p(hi), _p(dent), ptrs)
+    if ndofs >= 2**31:
+        raise OverflowError("DoF count does not fit int32")
+    rowptr = np.zeros(cells.shape[0] + 1, dtype=np.int64)
+    if L.oracle_ragged_map(cells.shape[1], cells.shape[0], _p(cells), _p(ce), maxlevel, _p(cf), _p(N), _p(dent),
+                           ptrs, _p(rowptr), None, None) != 0:
+        raise ValueError("oracle_ragged_map failed")
+    m = np.empty(int(rowptr[-1]), dtype=np.int32)
+    off = np.empty(int(rowptr[-1]), dtype=np.int32)
+    L.oracle_ragged_map(cells.shape[1], cells.shape[0], _p(cells), _p(ce), maxlevel, _p(cf), _p(N), _p(dent),
+                        ptrs, _p(rowptr), _p(m), _p(off))
+    first = {t: tabs[t] for t in range(6)} if keep_tables else {}
+    return Space(delta=None, layers=maxlevel, ndofs=int(ndofs), k=0, map=m, offset=off, first=first,
+                 cell_first=None if cell_layers is None else cf, cell_layers=None if cell_layers is None else cl,
+                 rowptr=rowptr)
+
+
+def dent_of(cells: np.ndarray, nverts: int, delta) -> np.ndarray:
+    """Per-entity counts of a constant-delta space (for comparisons)."""
+    _, ne = derive_edges(cells, nverts)
+    N = [nverts, ne, cells.shape[0]]
+    return np.concatenate([np.tile(np.array([delta[2 * d], delta[2 * d + 1]], np.int32), (N[d], 1))
+                           for d in range(3)])

@@ -286,6 +286,72 @@ void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Per-entity DoF counts (Sec. 5: the numbering needs neither a constant    */
+/* number of layers nor a constant number of DoFs per entity type).  Entity */
+/* g (dimension-major index: vertices, edges, cells) carries dent[2g] DoFs  */
+/* on each of its horizontal copies and dent[2g+1] on each vertical one.     */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_alg1_ragged(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
+                           const int32_t *hi, const int32_t *dent, int64_t *const first[6]) {
+  int64_t c = 0, ent = 0;
+  for (int d1 = 0; d1 <= 2; ++d1) {
+    for (int64_t i = 0; i < N[d1]; ++i, ++ent) {
+      for (int32_t l = lo[ent]; l < hi[ent]; ++l) {
+        for (int d2 = 0; d2 <= 1; ++d2) {
+          int t = 2 * d1 + d2;
+          if (first[t]) first[t][i * (maxlevel + 1 - d2) + l] = c;
+          c += dent[2 * ent + d2];
+        }
+      }
+      if (first[2 * d1]) first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;
+      c += dent[2 * ent];
+    }
+  }
+  return c;
+}
+
+/* Ragged explicit lists at each column's bottom layer (level cell_first[c],
+ * or 0): row c holds, per base entity of the cell (vertices, edges, cell),
+ * the dent[2g] DoFs of its bottom horizontal copy, the dent[2g] of its top
+ * copy and the dent[2g+1] of its vertical copy; the offset of each entry is
+ * its entity's dent[2g] + dent[2g+1] (Algorithm 2's rule).  rowptr (ncells +
+ * 1) is always filled; map and offset (rowptr[ncells] entries) may be NULL. */
+int oracle_ragged_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                      const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                      const int64_t N[3], const int32_t *dent, int64_t *const first[6],
+                      int64_t *rowptr, int32_t *map, int32_t *offset) {
+  rowptr[0] = 0;
+  for (int64_t c = 0; c < ncells; ++c) {
+    const int64_t s = cell_first ? cell_first[c] : 0;
+    int64_t j = rowptr[c];
+    for (int d = 0; d <= 2; ++d) {
+      for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+        int64_t id;
+        if (d == 0) id = cell_verts[c * nvc + e];
+        else if (d == 1) {
+          if (!cell_edges) return -1;
+          id = cell_edges[c * nvc + e];
+        } else id = c;
+        const int64_t g = (d == 0 ? 0 : (d == 1 ? N[0] : N[0] + N[1])) + id;
+        const int32_t a = dent[2 * g], b = dent[2 * g + 1];
+        for (int part = 0; part < 3; ++part) {
+          const int32_t n = part < 2 ? a : b;
+          for (int32_t q = 0; q < n; ++q, ++j) {
+            if (!map) continue;
+            if (part == 0) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s] + q);
+            else if (part == 1) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s + 1] + q);
+            else map[j] = (int32_t)(first[2 * d + 1][id * maxlevel + s] + q);
+            offset[j] = a + b;
+          }
+        }
+      }
+    }
+    rowptr[c + 1] = j;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Reference elements.                                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -607,9 +673,9 @@ static double tp_phi(int hf, int vf, double xi, double eta, double zeta, double 
 
 /* int f phi_i dx on one prism of a tensor-product space; the coordinates are
  * the P1xP1 vector field (stencil DoF 2a+b) and define a general Jacobian. */
-static void k_mass_tp(double *const *vals, double *const *out, double *const *absv) {
+static void k_mass_tp_hv(int h, int v, double *const *vals, double *const *out, double *const *absv) {
   int hfun[27], vfun[27];
-  const int k = tp_layout(g_tp_h, g_tp_v, hfun, vfun);
+  const int k = tp_layout(h, v, hfun, vfun);
   double pts[6][3], wts[6];
   prism_rule(pts, wts);
   const double *X = vals[0], *f = vals[1];
@@ -700,6 +766,24 @@ static void k_hfacet_jump(int k, double *const *vals, double *const *out, double
   }
 }
 
+static void k_mass_tp(double *const *vals, double *const *out, double *const *absv) {
+  k_mass_tp_hv(g_tp_h, g_tp_v, vals, out, absv);
+}
+
+/* p-adaptive DG: every cell carries its own element, one of the spaces
+ * discontinuous in both directions, told apart by the cell's DoF count:
+ * 1 DG0xDG0, 2 DG0xDG1, 3 DG1xDG0, 6 DG1xDG1.  Returns -1 for other counts. */
+static int k_mass_dgp(int k, double *const *vals, double *const *out, double *const *absv) {
+  int h, v;
+  if (k == 1) { h = ORC_DG0; v = ORC_DG0; }
+  else if (k == 2) { h = ORC_DG0; v = ORC_DG1; }
+  else if (k == 3) { h = ORC_DG1; v = ORC_DG0; }
+  else if (k == 6) { h = ORC_DG1; v = ORC_DG1; }
+  else return -1;
+  k_mass_tp_hv(h, v, vals, out, absv);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 3: for every base cell, read its explicit list once; for every */
 /* layer apply the stencil function, then add the vertical offsets.         */
@@ -718,7 +802,8 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
                          const double *base_xy, int32_t nargs, const orc_arg *args) {
   if (nargs < 1 || nargs > ORC_MAXARGS || layers < 1) return -1;
   for (int a = 0; a < nargs; ++a)
-    if (args[a].k < 1 || args[a].k > 27 || args[a].ncomp < 1 || args[a].ncomp > 3) return -2;
+    if ((!args[a].rowptr && (args[a].k < 1 || args[a].k > 27)) || args[a].ncomp < 1 || args[a].ncomp > 3)
+      return -2;
   if (kernel == ORC_K_HFACET_MASS && (g_tp_v != ORC_CG1 || nvc != 3)) return -5;
   if (kernel == ORC_K_HFACET_JUMP && nvc != 3) return -5;
   const int twocell = kernel == ORC_K_HFACET_JUMP;
@@ -729,7 +814,7 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
     u2v_setup(nvc, T);
   }
   int64_t dofs[ORC_MAXARGS][2 * 27], offs[ORC_MAXARGS][2 * 27];
-  int kk[ORC_MAXARGS];
+  int kk[ORC_MAXARGS], kc[ORC_MAXARGS];
   double vbuf[ORC_MAXARGS][ORC_MAXVALS], obuf[ORC_MAXARGS][ORC_MAXVALS], abuf[ORC_MAXARGS][ORC_MAXVALS];
   double *vals[ORC_MAXARGS], *outv[ORC_MAXARGS], *absv[ORC_MAXARGS];
   for (int a = 0; a < ORC_MAXARGS; ++a) {
@@ -737,11 +822,20 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
     outv[a] = obuf[a];
     absv[a] = abuf[a];
   }
-  for (int a = 0; a < nargs; ++a) {
-    kk[a] = twocell ? 2 * args[a].k : args[a].k;
-    for (int j = 0; j < kk[a]; ++j) offs[a][j] = args[a].offset[j % args[a].k];
-  }
+  for (int a = 0; a < nargs; ++a)
+    if (args[a].rowptr && twocell) return -6; /* ragged lists: cell loops only */
   for (int64_t c = 0; c < ncells; ++c) {
+    /* list length and offsets of this cell (ragged lists vary per cell) */
+    const int32_t *lst[ORC_MAXARGS];
+    for (int a = 0; a < nargs; ++a) {
+      const int64_t r0 = args[a].rowptr ? args[a].rowptr[c] : c * (int64_t)args[a].k;
+      kc[a] = args[a].rowptr ? (int)(args[a].rowptr[c + 1] - r0) : args[a].k;
+      if (kc[a] < 1 || kc[a] > 27) return -2;
+      lst[a] = args[a].map + r0;
+      kk[a] = twocell ? 2 * kc[a] : kc[a];
+      for (int j = 0; j < kk[a]; ++j)
+        offs[a][j] = args[a].rowptr ? args[a].offset[r0 + j] : args[a].offset[j % args[a].k];
+    }
     const int32_t s = cell_first ? cell_first[c] : 0;
     const int32_t lam = cell_layers ? cell_layers[c] : layers;
     int32_t l0 = 0, l1 = lam;                       /* cells: d2 = 1        */
@@ -750,7 +844,7 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
     /* (dof_0 .. dof_{k-1}) <- L(v) */
     for (int a = 0; a < nargs; ++a)
       for (int j = 0; j < kk[a]; ++j)
-        dofs[a][j] = args[a].map[c * args[a].k + j % args[a].k] + (j >= args[a].k ? offs[a][j] : 0);
+        dofs[a][j] = lst[a][j % kc[a]] + (j >= kc[a] ? offs[a][j] : 0);
     for (int32_t l = l0; l < l1; ++l) {
       for (int a = 0; a < nargs; ++a) {
         int n = kk[a] * args[a].ncomp;
@@ -773,7 +867,7 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
           break;
         }
         case ORC_K_COPY:
-          for (int j = 0; j < args[1].k; ++j) obuf[1][j] = vbuf[0][j];
+          for (int j = 0; j < kc[1]; ++j) obuf[1][j] = vbuf[0][j];
           break;
         case ORC_K_MASS:
           k_mass_prism(vals, outv, absv);
@@ -794,7 +888,13 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
           k_hfacet_mass(vals, outv, absv);
           break;
         case ORC_K_HFACET_JUMP:
-          k_hfacet_jump(args[1].k, vals, outv, absv);
+          k_hfacet_jump(kc[1], vals, outv, absv);
+          break;
+        case ORC_K_MASS_DGP:
+          if (k_mass_dgp(kc[1], vals, outv, absv) != 0) {
+            free(T);
+            return -7;
+          }
           break;
         default:
           free(T);

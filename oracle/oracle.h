@@ -33,9 +33,12 @@ enum {
   ORC_K_HFACET_MASS = 7, /* horizontal facets, l = 0 .. lambda (d2 = 0), facet lists:
                             coords READ, f READ, b INC: b_i += int_F f phi_i ds;
                             space (h, CG1) chosen by oracle_set_tp_element         */
-  ORC_K_HFACET_JUMP = 8  /* interior horizontal facets, l = 1 .. lambda-1, two-cell
+  ORC_K_HFACET_JUMP = 8, /* interior horizontal facets, l = 1 .. lambda-1, two-cell
                             lists built from the cell lists: coords READ, u READ,
                             r INC: r_i += int_F [u][phi_i] ds                      */
+  ORC_K_MASS_DGP = 9     /* coords READ, f READ, b INC on a p-adaptive DG space
+                            (ragged lists): each cell's element by its DoF count,
+                            1 DG0xDG0, 2 DG0xDG1, 3 DG1xDG0, 6 DG1xDG1            */
 };
 
 /* Horizontal / vertical elements of the prism spaces of Sec. 4.1.2. */
@@ -49,6 +52,8 @@ typedef struct {
   double *data;          /* field values, ndofs x ncomp                          */
   double *absdata;       /* optional: accumulates |contribution| for INC outputs */
   int32_t access;        /* ORC_READ / ORC_WRITE / ORC_INC                        */
+  const int64_t *rowptr; /* ragged lists (NULL: k per cell): cell c's entries are
+                            map[rowptr[c] .. rowptr[c+1]), offsets alongside     */
 } orc_arg;
 
 /* Edges of the base mesh, numbered by first appearance when cells are scanned
@@ -117,6 +122,19 @@ void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset);
 int oracle_par_loop_var(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
                         const int32_t *cell_layers, int32_t maxlevel, const int32_t *cell_verts,
                         const double *base_xy, int32_t nargs, const orc_arg *args);
+
+/* Per-entity DoF counts: entity g (dimension-major) carries dent[2g] DoFs on
+ * each horizontal copy and dent[2g+1] on each vertical copy.  Algorithm 1 over
+ * the level ranges lo..hi (constant layers: lo = 0, hi = layers). */
+int64_t oracle_alg1_ragged(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
+                           const int32_t *hi, const int32_t *dent, int64_t *const first[6]);
+
+/* Ragged explicit lists and their offsets; rowptr has ncells + 1 entries;
+ * map/offset (rowptr[ncells] entries each) may be NULL to size them. */
+int oracle_ragged_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
+                      const int32_t *cell_edges, int32_t maxlevel, const int32_t *cell_first,
+                      const int64_t N[3], const int32_t *dent, int64_t *const first[6],
+                      int64_t *rowptr, int32_t *map, int32_t *offset);
 
 /* n-point Gauss-Legendre rule on [0,1] (Newton iteration on P_n). */
 void oracle_gauss_legendre(int32_t n, double *x, double *w);

@@ -69,8 +69,15 @@ MUTANTS = {
     "jump_trace_of_bottom": ("pb[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 1.0, g);",
                              "pb[j] = tp_phi(hfun[j], vfun[j], tri_pts[q][0], tri_pts[q][1], 0.0, g);"),
     "jump_above_added": ("out[2][k + i] -= tri_w * ds * jump * pa[i];", "out[2][k + i] += tri_w * ds * jump * pa[i];"),
-    "jump_same_cell_twice": ("+ (j >= args[a].k ? offs[a][j] : 0);", "+ 0;"),
+    "jump_same_cell_twice": ("+ (j >= kc[a] ? offs[a][j] : 0);", "+ 0;"),
     "jump_base_face": ("const double ds = tri_area_element(X + 3, 6);", "const double ds = tri_area_element(X, 6);"),
+    # per-entity DoF counts and the p-adaptive DG kernel
+    "ragged_top_counts_vertical": ("first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;\n      c += dent[2 * ent];",
+                                   "first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;\n      c += dent[2 * ent + 1];"),
+    "ragged_offset_horizontal_only": ("            offset[j] = a + b;", "            offset[j] = a;"),
+    "ragged_top_list_at_bottom": ("else if (part == 1) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s + 1] + q);",
+                                  "else if (part == 1) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s] + q);"),
+    "dgp_two_dofs_as_dg0": ("else if (k == 2) { h = ORC_DG0; v = ORC_DG1; }", "else if (k == 2) { h = ORC_DG0; v = ORC_DG0; }"),
 }
 
 
@@ -85,7 +92,8 @@ def _run_pins(source: str, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_numbering.py"),
                         os.path.join(ROOT, "tests", "test_oracle_kernels.py"),
                         os.path.join(ROOT, "tests", "test_oracle_var.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_facets.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_facets.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_ragged.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r
 
