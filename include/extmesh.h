@@ -118,6 +118,13 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   [w] = w(cell below, at the facet) - w(cell above, at the
  *                   facet), on any of the nine spaces of EXT_K_MASS_TP (zero for
  *                   the vertically continuous ones); u and r share one numbering.
+ * EXT_K_MASS_DGP    [coords READ, f READ, b INC] on prisms, f and b on one space
+ *                   from ext_number_dofs_ragged whose DoFs all sit inside the
+ *                   cells: b_i += int f_h phi_i dx where every cell carries its
+ *                   own element, told apart by its DoF count: 1 DG0xDG0, 2
+ *                   DG0xDG1, 3 DG1xDG0, 6 DG1xDG1 (p-adaptive DG).
+ * EXT_K_COPY_DG also takes a space from ext_number_dofs_ragged whose DoFs all
+ * sit inside the cells (any count per cell).
  * Quadrature: prisms use the 6-point rule (3-point degree-2 triangle rule x
  * 2-point Gauss); hexahedra use 4x4x4 Gauss points; facets are flat triangles
  * whose P1 surface integrals are evaluated exactly. */
@@ -132,7 +139,8 @@ typedef enum {
   EXT_K_U2V_FWDADJ = 7,
   EXT_K_MASS_TP = 8,
   EXT_K_HFACET_MASS = 9,
-  EXT_K_HFACET_JUMP = 10
+  EXT_K_HFACET_JUMP = 10,
+  EXT_K_MASS_DGP = 11
 } ext_kernel_id;
 
 typedef struct ext_mesh ext_mesh;
@@ -227,6 +235,36 @@ void ext_mesh_destroy(ext_mesh *mesh);
  * more), EXT_ENOMEM, EXT_ECUDA. */
 ext_status ext_number_dofs(ext_mesh *mesh, const int32_t delta_host[6], int32_t ncomp,
                            void *stream, ext_space **out);
+
+/* Numbers a space whose DoF counts vary per base entity (the paper fixes one
+ * count per entity type for exposition and notes that the numbering does not
+ * need it, Sec. 5): Algorithm 1 with entity g's column holding
+ * lambda_g (dent[2g] + dent[2g+1]) + dent[2g] numbers, on constant or
+ * variable layers.  The column starts and the list lengths are prefix sums on
+ * the device.
+ *   dent_host  (N_0 + N_1 + N_2) x 2 int32 in [0, 4096]: DoFs of entity g on
+ *              each horizontal copy and on each vertical copy; entities
+ *              dimension-major (vertices, edges, cells), index ascending
+ * The lists are ragged: row c (cell c at its bottom layer) holds, per entity
+ * of the cell (vertices, edges, cell), the bottom horizontal DoFs, the top
+ * horizontal DoFs and the vertical DoFs; each entry's vertical offset is its
+ * entity's dent[2g] + dent[2g+1] (Algorithm 2's rule).  ext_space_info
+ * reports k = 0; ext_space_ragged_info / ext_space_copy_ragged_to_host give
+ * the row pointers (ncells + 1 int64), the entries and their offsets.
+ * Synchronous on `stream`.  Errors: EXT_EINVAL (negative or too large count,
+ * no DoFs), EXT_EOVERFLOW, EXT_ENOMEM, EXT_ECUDA. */
+ext_status ext_number_dofs_ragged(ext_mesh *mesh, const int32_t *dent_host, int32_t ncomp, void *stream,
+                                  ext_space **out);
+
+/* Device row pointers (ncells + 1), entries and per-entry offsets of a space
+ * from ext_number_dofs_ragged (EXT_EINVAL for a space with one length k). */
+ext_status ext_space_ragged_info(const ext_space *space, int64_t *nentries, const int64_t **rowptr_dev,
+                                 const int32_t **map_dev, const int32_t **offset_dev);
+
+/* Copies them to host arrays (ncells + 1, nentries, nentries; any may be
+ * NULL).  Synchronous. */
+ext_status ext_space_copy_ragged_to_host(const ext_space *space, int64_t *rowptr_host, int32_t *map_host,
+                                         int32_t *offset_host);
 
 /* DoF count, stencil length k, ncomp and the device stencil data of a space:
  * base_map (ncells x k int32, row-major, global DoFs at layer 0) and offset

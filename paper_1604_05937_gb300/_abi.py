@@ -20,7 +20,7 @@ STATUS_NAMES = ["EXT_OK", "EXT_EINVAL", "EXT_ENOMEM", "EXT_ECUDA", "EXT_EOVERFLO
 EXT_TRI, EXT_QUAD = 3, 4
 EXT_READ, EXT_WRITE, EXT_INC = 0, 1, 2
 (EXT_K_EXTRUDE, EXT_K_COPY_DG, EXT_K_RHS_P1P1, EXT_K_MASS_P1P1, EXT_K_INTERP_DG1, EXT_K_U2V_FWD,
- EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ, EXT_K_MASS_TP, EXT_K_HFACET_MASS, EXT_K_HFACET_JUMP) = range(11)
+ EXT_K_U2V_ADJ, EXT_K_U2V_FWDADJ, EXT_K_MASS_TP, EXT_K_HFACET_MASS, EXT_K_HFACET_JUMP, EXT_K_MASS_DGP) = range(12)
 
 
 class ExtError(RuntimeError):
@@ -55,6 +55,10 @@ def _load():
         "ext_mesh_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "ext_mesh_destroy": (None, [vp]),
         "ext_number_dofs": (ctypes.c_int, [vp, vp, i32, vp, ctypes.POINTER(vp)]),
+        "ext_number_dofs_ragged": (ctypes.c_int, [vp, vp, i32, vp, ctypes.POINTER(vp)]),
+        "ext_space_ragged_info": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                 ctypes.POINTER(vp)]),
+        "ext_space_copy_ragged_to_host": (ctypes.c_int, [vp, vp, vp, vp]),
         "ext_space_info": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                           ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "ext_space_copy_map_to_host": (ctypes.c_int, [vp, vp, vp]),
@@ -181,6 +185,29 @@ def ext_space_copy_map_to_host(space: int, ncells: int):
     o = np.empty(k, dtype=np.int32)
     _check(lib.ext_space_copy_map_to_host(space, _ptr(m) if m.size else None, _ptr(o)))
     return m, o
+
+
+def ext_number_dofs_ragged(mesh: int, dent, ncomp: int = 1, stream=None) -> int:
+    d = np.ascontiguousarray(dent, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib.ext_number_dofs_ragged(mesh, _ptr(d) if d.size else None, ncomp, _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def ext_space_ragged_info(space: int):
+    n = ctypes.c_int64()
+    rp, mp, op = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.ext_space_ragged_info(space, ctypes.byref(n), ctypes.byref(rp), ctypes.byref(mp), ctypes.byref(op)))
+    return n.value, rp.value, mp.value, op.value
+
+
+def ext_space_copy_ragged_to_host(space: int, ncells: int):
+    n, _, _, _ = ext_space_ragged_info(space)
+    rowptr = np.empty(ncells + 1, dtype=np.int64)
+    m = np.empty(n, dtype=np.int32)
+    o = np.empty(n, dtype=np.int32)
+    _check(lib.ext_space_copy_ragged_to_host(space, _ptr(rowptr), _ptr(m) if n else None, _ptr(o) if n else None))
+    return rowptr, m, o
 
 
 def ext_space_destroy(space: int) -> None:

@@ -68,18 +68,28 @@ class Mesh:
 
 
 class Space:
-    """A function space numbered by Algorithm 1 on `mesh`."""
+    """A function space numbered by Algorithm 1 on `mesh`: one delta table
+    for every entity type, or per-entity counts ``dent`` ((V + E + C) x 2,
+    dimension-major; ragged lists)."""
 
-    def __init__(self, mesh: Mesh, delta, ncomp: int = 1, stream=None):
-        if isinstance(delta, str):
-            delta = DELTA[delta]
+    def __init__(self, mesh: Mesh, delta=None, ncomp: int = 1, stream=None, dent=None):
         self.mesh = mesh
-        self.delta = tuple(int(d) for d in delta)
-        self.handle = A.ext_number_dofs(mesh.handle, self.delta, ncomp, stream)
+        if dent is not None:
+            self.delta = None
+            self.handle = A.ext_number_dofs_ragged(mesh.handle, dent, ncomp, stream)
+        else:
+            if isinstance(delta, str):
+                delta = DELTA[delta]
+            self.delta = tuple(int(d) for d in delta)
+            self.handle = A.ext_number_dofs(mesh.handle, self.delta, ncomp, stream)
         self.ndofs, self.k, self.ncomp, _, _ = A.ext_space_info(self.handle)
+        self.ragged = dent is not None
 
     def stencil_map(self):
-        """(C, k) layer-0 stencil lists and (k,) offsets, copied to the host."""
+        """(C, k) layer-0 stencil lists and (k,) offsets, copied to the host;
+        for per-entity counts (rowptr, entries, per-entry offsets)."""
+        if self.ragged:
+            return A.ext_space_copy_ragged_to_host(self.handle, self.mesh.ncells)
         return A.ext_space_copy_map_to_host(self.handle, self.mesh.ncells)
 
     def zeros(self, device="cuda"):

@@ -364,6 +364,8 @@ extern "C" ext_status ext_space_info(const ext_space *space, int64_t *ndofs, int
 
 extern "C" ext_status ext_space_copy_map_to_host(const ext_space *space, int32_t *map_host, int32_t *offset_host) {
   if (!space) return ext_fail(EXT_EINVAL, "ext_space_copy_map_to_host: space is NULL");
+  if (space->ragged)
+    return ext_fail(EXT_EINVAL, "ext_space_copy_map_to_host: ragged lists (use ext_space_copy_ragged_to_host)");
   if (map_host && space->mesh->N[2] > 0)
     EXT_CUDA(cudaMemcpy(map_host, space->d_map, sizeof(int32_t) * space->k * space->mesh->N[2], cudaMemcpyDeviceToHost),
              "ext_space_copy_map_to_host");
@@ -375,7 +377,132 @@ extern "C" void ext_space_destroy(ext_space *space) {
   if (!space) return;
   cudaFree(space->d_map);
   cudaFree(space->d_offset);
+  cudaFree(space->d_rowptr);
+  cudaFree(space->d_roff);
   delete space;
+}
+
+enum : int { ELEM_RAGGED = 16 };
+
+extern "C" ext_status ext_number_dofs_ragged(ext_mesh *mesh, const int32_t *dent_host, int32_t ncomp, void *stream,
+                                             ext_space **out) {
+  if (!out) return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: out is NULL");
+  *out = nullptr;
+  if (!mesh) return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: mesh is NULL");
+  if (ncomp < 1 || ncomp > 3) return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: ncomp must be 1..3");
+  const int64_t nent = mesh->N[0] + mesh->N[1] + mesh->N[2];
+  if (nent > 0 && !dent_host) return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: dent is NULL");
+  bool dg_cells = true, dgp = true;
+  int64_t any = 0;
+  for (int64_t g = 0; g < nent; ++g) {
+    const int32_t a = dent_host[2 * g], b = dent_host[2 * g + 1];
+    if (a < 0 || b < 0 || a > 4096 || b > 4096)
+      return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: entity %lld has counts %d, %d", (long long)g, a, b);
+    any += a + b;
+    const bool cell = g >= mesh->N[0] + mesh->N[1];
+    if ((!cell && (a | b)) || (cell && a)) dg_cells = false;
+    if (cell && !(b == 1 || b == 2 || b == 3 || b == 6)) dgp = false;
+  }
+  if (any == 0) return ext_fail(EXT_EINVAL, "ext_number_dofs_ragged: the space has no DoFs");
+  ext_space *sp = new ext_space();
+  sp->mesh = mesh;
+  memset(sp->delta, 0, sizeof(sp->delta));
+  sp->ncomp = ncomp;
+  sp->k = 0;
+  sp->elem = ELEM_RAGGED;
+  sp->ragged = true;
+  sp->dg_cells = dg_cells;
+  sp->dgp = dg_cells && dgp && mesh->kind == EXT_TRI;
+  sp->stream = (cudaStream_t)stream;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t C = mesh->N[2];
+  int32_t *d_dent = nullptr;
+  int64_t *d_starts = nullptr, *d_scratch = nullptr;
+  int64_t ndofs = 0, nentries = 0;
+  RaggedLaunch rl;
+  memset(&rl, 0, sizeof(rl));
+  for (int d = 0; d < 3; ++d) rl.N[d] = mesh->N[d];
+  rl.ncells = C;
+  rl.nvc = mesh->kind;
+  rl.layers = mesh->layers;
+  rl.cell_verts = mesh->d_cell_verts;
+  rl.cell_edges = mesh->d_cell_edges;
+  if (mesh->var) {
+    rl.ent_lo = mesh->d_ent_lo;
+    rl.ent_hi = mesh->d_ent_hi;
+    rl.cell_first = mesh->d_cell_first;
+  }
+  const int64_t nscr = scan_scratch_elems(nent > C ? nent : C);
+  cudaError_t e = cudaMalloc(&d_dent, sizeof(int32_t) * 2 * (nent > 0 ? nent : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_starts, sizeof(int64_t) * (nent + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_scratch, sizeof(int64_t) * nscr);
+  if (e == cudaSuccess) e = cudaMalloc(&sp->d_rowptr, sizeof(int64_t) * (C + 1));
+  if (e == cudaSuccess && nent > 0)
+    e = cudaMemcpyAsync(d_dent, dent_host, sizeof(int32_t) * 2 * nent, cudaMemcpyHostToDevice, st);
+  rl.dent = d_dent;
+  rl.ent_start = d_starts;
+  rl.rowptr = sp->d_rowptr;
+  // Algorithm 1's counter at each entity column: a prefix sum of the sizes;
+  // each row's start: a prefix sum of the row lengths
+  if (e == cudaSuccess) e = launch_ragged_colsize(rl, d_starts, st);
+  if (e == cudaSuccess) e = launch_scan_i64(d_starts, nent, d_scratch, st);
+  if (e == cudaSuccess) e = launch_ragged_rowlen(rl, st);
+  if (e == cudaSuccess) e = launch_scan_i64(sp->d_rowptr, C, d_scratch, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ndofs, d_starts + nent, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nentries, sp->d_rowptr + C, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ext_status bad = EXT_OK;
+  if (e == cudaSuccess && (ndofs >= INT32_MAX || ndofs * ncomp >= INT32_MAX))
+    bad = ext_fail(EXT_EOVERFLOW, "ext_number_dofs_ragged: %lld DoFs do not fit int32 indices", (long long)ndofs);
+  if (e == cudaSuccess && bad == EXT_OK) {
+    e = cudaMalloc(&sp->d_map, sizeof(int32_t) * (nentries > 0 ? nentries : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&sp->d_roff, sizeof(int32_t) * (nentries > 0 ? nentries : 1));
+    rl.map = sp->d_map;
+    rl.roff = sp->d_roff;
+    if (e == cudaSuccess) e = launch_ragged_map(rl, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(d_dent);
+  cudaFree(d_starts);
+  cudaFree(d_scratch);
+  if (e != cudaSuccess || bad != EXT_OK) {
+    ext_space_destroy(sp);
+    if (bad != EXT_OK) return bad;
+    return ext_fail(e == cudaErrorMemoryAllocation ? EXT_ENOMEM : EXT_ECUDA, "ext_number_dofs_ragged: %s",
+                    cudaGetErrorString(e));
+  }
+  sp->ndofs = ndofs;
+  sp->nentries = nentries;
+  *out = sp;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_space_ragged_info(const ext_space *space, int64_t *nentries, const int64_t **rowptr_dev,
+                                            const int32_t **map_dev, const int32_t **offset_dev) {
+  if (!space) return ext_fail(EXT_EINVAL, "ext_space_ragged_info: space is NULL");
+  if (!space->ragged) return ext_fail(EXT_EINVAL, "ext_space_ragged_info: the space has one list length k");
+  if (nentries) *nentries = space->nentries;
+  if (rowptr_dev) *rowptr_dev = space->d_rowptr;
+  if (map_dev) *map_dev = space->d_map;
+  if (offset_dev) *offset_dev = space->d_roff;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_space_copy_ragged_to_host(const ext_space *space, int64_t *rowptr_host, int32_t *map_host,
+                                                    int32_t *offset_host) {
+  if (!space) return ext_fail(EXT_EINVAL, "ext_space_copy_ragged_to_host: space is NULL");
+  if (!space->ragged) return ext_fail(EXT_EINVAL, "ext_space_copy_ragged_to_host: the space has one list length k");
+  const int64_t C = space->mesh->N[2];
+  if (rowptr_host)
+    EXT_CUDA(cudaMemcpy(rowptr_host, space->d_rowptr, sizeof(int64_t) * (C + 1), cudaMemcpyDeviceToHost),
+             "ext_space_copy_ragged_to_host");
+  if (map_host && space->nentries > 0)
+    EXT_CUDA(cudaMemcpy(map_host, space->d_map, sizeof(int32_t) * space->nentries, cudaMemcpyDeviceToHost),
+             "ext_space_copy_ragged_to_host");
+  if (offset_host && space->nentries > 0)
+    EXT_CUDA(cudaMemcpy(offset_host, space->d_roff, sizeof(int32_t) * space->nentries, cudaMemcpyDeviceToHost),
+             "ext_space_copy_ragged_to_host");
+  return EXT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -432,6 +559,7 @@ static ext_status check_arg(const ext_mesh *mesh, const ext_arg *args, int i, co
 }
 
 static bool same_numbering(const ext_space *a, const ext_space *b) {
+  if (a->ragged || b->ragged) return a == b;  // per-entity counts: the same space object
   return a->mesh == b->mesh && memcmp(a->delta, b->delta, sizeof(a->delta)) == 0;
 }
 
@@ -472,8 +600,11 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
     case EXT_K_COPY_DG: {
       const char *kn = "EXT_K_COPY_DG";
       if (nargs != 2) return ext_fail(EXT_EINVAL, "%s: expects 2 arguments", kn);
-      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_DGCELL, 1, EXT_READ));
-      EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_DGCELL, 1, EXT_WRITE));
+      const bool rg = args[0].space && args[0].space->ragged;
+      if (rg && !args[0].space->dg_cells)
+        return ext_fail(EXT_EINVAL, "%s: the space has DoFs outside the cells", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, rg ? (int)ELEM_RAGGED : (int)ELEM_DGCELL, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, rg ? (int)ELEM_RAGGED : (int)ELEM_DGCELL, 1, EXT_WRITE));
       if (!same_numbering(args[0].space, args[1].space))
         return ext_fail(EXT_EINVAL, "%s: input and output must share one numbering", kn);
       CopyDGLaunch p;
@@ -484,6 +615,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.in = (const double *)args[0].data;
       p.out = (double *)args[1].data;
       p.cell_layers = mesh->d_cell_layers;
+      p.rowptr = rg ? args[0].space->d_rowptr : nullptr;
       e = launch_copy_dg(p, s);
       break;
     }
@@ -618,6 +750,33 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
       e = launch_mass_tp(p, s);
+      break;
+    }
+    case EXT_K_MASS_DGP: {
+      const char *kn = "EXT_K_MASS_DGP";
+      if (mesh->kind != EXT_TRI) return ext_fail(EXT_EINVAL, "%s: needs a triangular base mesh", kn);
+      if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
+      EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_RAGGED, 1, EXT_READ));
+      EXT_CHECK(check_arg(mesh, args, 2, kn, ELEM_RAGGED, 1, EXT_INC));
+      if (!same_numbering(args[1].space, args[2].space))
+        return ext_fail(EXT_EINVAL, "%s: f and b must be on the same space", kn);
+      if (!args[1].space->dgp)
+        return ext_fail(EXT_EINVAL, "%s: every cell needs 1, 2, 3 or 6 DoFs and no DoF may sit outside the cells", kn);
+      MassDGPLaunch p;
+      memset(&p, 0, sizeof(p));
+      p.ncells = C;
+      p.layers = L;
+      p.cmap = args[0].space->d_map;
+      for (int i = 0; i < 6; ++i) p.coff[i] = args[0].space->h_offset[i];
+      p.rowptr = args[1].space->d_rowptr;
+      p.fmap = args[1].space->d_map;
+      p.X = (const double *)args[0].data;
+      p.f = (const double *)args[1].data;
+      p.b = (double *)args[2].data;
+      p.cell_layers = mesh->d_cell_layers;
+      p.mean_layers = mesh->mean_layers;
+      e = launch_mass_dgp(p, s);
       break;
     }
     case EXT_K_HFACET_MASS:

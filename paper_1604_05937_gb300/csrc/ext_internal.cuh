@@ -57,6 +57,13 @@ struct ext_space {
   int32_t h_offset[EXT_MAXK];
   int elem;
   cudaStream_t stream;  // creation stream (map ready after it)
+  // per-entity DoF counts: ragged lists (k = 0; d_map holds nentries values)
+  bool ragged = false;
+  int64_t nentries = 0;
+  int64_t *d_rowptr = nullptr;  // ncells + 1
+  int32_t *d_roff = nullptr;    // nentries: offset of every list entry
+  bool dg_cells = false;        // DoFs only inside cells (copyable column by column)
+  bool dgp = false;             // and every cell is DG0|DG1 x DG0|DG1 (1, 2, 3 or 6 DoFs)
 };
 
 // ---------------------------------------------------------------------------
@@ -95,6 +102,24 @@ cudaError_t launch_var_colsize(const ext_mesh *m, const int32_t delta[6], int64_
 cudaError_t launch_scan_i64(int64_t *data, int64_t n, int64_t *scratch, cudaStream_t s);
 int64_t scan_scratch_elems(int64_t n);
 
+// Per-entity DoF counts (k_number.cu): column sizes from dent (2 per entity,
+// dimension-major) and the entity ranges (variable layers) or `layers`; row
+// lengths of the ragged lists; the lists and their offsets.
+struct RaggedLaunch {
+  int64_t N[3];
+  int64_t ncells;
+  int32_t nvc, layers;
+  const int32_t *dent;                      // (N0+N1+N2) x 2
+  const int32_t *ent_lo = nullptr, *ent_hi = nullptr, *cell_first = nullptr;  // variable layers
+  const int32_t *cell_verts, *cell_edges;
+  const int64_t *ent_start;                 // column starts (exclusive scan of the sizes)
+  int64_t *rowptr;                          // ncells + 1 (row lengths before the scan)
+  int32_t *map, *roff;
+};
+cudaError_t launch_ragged_colsize(const RaggedLaunch &p, int64_t *sizes, cudaStream_t s);
+cudaError_t launch_ragged_rowlen(const RaggedLaunch &p, cudaStream_t s);
+cudaError_t launch_ragged_map(const RaggedLaunch &p, cudaStream_t s);
+
 struct ExtrudeLaunch {
   int64_t ncells;
   int32_t nvc, layers;
@@ -115,6 +140,7 @@ struct CopyDGLaunch {
   const double *in;
   double *out;
   const int32_t *cell_layers = nullptr;  // variable layers
+  const int64_t *rowptr = nullptr;       // ragged lists: k of cell c = rowptr[c+1] - rowptr[c]
 };
 cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s);
 
@@ -163,6 +189,23 @@ struct MassTPLaunch {
   double mean_layers = 0.0;
 };
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
+
+// p-adaptive DG right-hand side (k_tp.cu): every cell's element is DG0|DG1 x
+// DG0|DG1 by its DoF count (1 DG0xDG0, 2 DG0xDG1, 3 DG1xDG0, 6 DG1xDG1); the
+// cell's DoFs are consecutive, layer after layer (Algorithm 1).
+struct MassDGPLaunch {
+  int64_t ncells;
+  int32_t layers;
+  const int32_t *cmap;   // coords map (k = 6)
+  int32_t coff[6];
+  const int64_t *rowptr; // ragged lists of the f/b space
+  const int32_t *fmap;
+  const double *X, *f;
+  double *b;
+  const int32_t *cell_layers = nullptr;  // variable layers
+  double mean_layers = 0.0;
+};
+cudaError_t launch_mass_dgp(const MassDGPLaunch &p, cudaStream_t s);
 
 // Horizontal-facet loops (k_facet.cu).  Facet m of a column (m = 0..lambda)
 // reads the bottom stencil slots at layer m, or the top slots of the last

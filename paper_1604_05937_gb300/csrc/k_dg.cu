@@ -164,14 +164,20 @@ __global__ void __launch_bounds__(kThreads) k_interp_dg1_tile(const InterpDG1Lau
 // in shared memory; a flattened unit index v of the tile then belongs to the
 // column cl with pre[cl] <= v < pre[cl + 1] (binary search).
 
+// Column c's unit count: its layers (lay[c], or `layers`) times its units
+// per layer (rowptr[c+1] - rowptr[c] for ragged lists, or per_layer).
 template <int TILE>
 __device__ void tile_prefix(const int32_t *lay, int64_t c0, int ncol, uint32_t per_layer, uint32_t *pre,
-                            uint32_t *wsum) {
+                            uint32_t *wsum, int layers = 0, const int64_t *rowptr = nullptr) {
   static_assert(TILE % 32 == 0 && TILE <= kThreads, "tile must be whole warps of the CTA");
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   uint32_t x = 0;
   if (t < TILE) {
-    x = t < ncol ? (uint32_t)__ldg(lay + c0 + t) * per_layer : 0u;
+    if (t < ncol) {
+      const uint32_t nl = lay ? (uint32_t)__ldg(lay + c0 + t) : (uint32_t)layers;
+      const uint32_t pl = rowptr ? (uint32_t)(__ldg(rowptr + c0 + t + 1) - __ldg(rowptr + c0 + t)) : per_layer;
+      x = nl * pl;
+    }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
@@ -200,23 +206,35 @@ __device__ __forceinline__ int tile_find(const uint32_t *pre, int ncol, uint32_t
   return lo;
 }
 
+// Variable layers or ragged lists (any number of DoFs per cell).
 template <int TILE, int UNROLL>
 __global__ void __launch_bounds__(kThreads) k_copy_dg_var(const CopyDGLaunch p, int64_t ntiles) {
   __shared__ uint32_t pre[TILE + 1];
   __shared__ uint32_t wsum[TILE / 32];
   __shared__ int32_t base[TILE];
-  __shared__ int contiguous;
+  __shared__ int contiguous, i0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t c0 = tile * TILE;
     const int ncol = (int)(p.ncells - c0 < TILE ? p.ncells - c0 : TILE);
     __syncthreads();  // the previous tile's readers are done
-    if (threadIdx.x == 0) contiguous = 1;
-    for (int i = threadIdx.x; i < ncol; i += kThreads) base[i] = __ldg(p.map + (c0 + i) * p.k);
-    tile_prefix<TILE>(p.cell_layers, c0, ncol, (uint32_t)p.k, pre, wsum);
+    if (threadIdx.x == 0) {
+      contiguous = 1;
+      i0 = TILE;
+    }
+    for (int i = threadIdx.x; i < ncol; i += kThreads) {
+      const int64_t r0 = p.rowptr ? __ldg(p.rowptr + c0 + i) : (c0 + i) * p.k;
+      const bool empty = p.rowptr && __ldg(p.rowptr + c0 + i + 1) == r0;
+      base[i] = empty ? 0 : __ldg(p.map + r0);
+    }
+    tile_prefix<TILE>(p.cell_layers, c0, ncol, (uint32_t)p.k, pre, wsum, p.layers, p.rowptr);
+    for (int i = threadIdx.x; i < ncol; i += kThreads)
+      if (pre[i + 1] > pre[i]) atomicMin(&i0, i);
+    __syncthreads();
     // columns numbered back to back (as Algorithm 1 numbers a cell-interior
     // space) make the tile one range: no search
+    const int f0 = i0 < ncol ? i0 : 0;
     for (int i = threadIdx.x; i < ncol; i += kThreads)
-      if ((uint32_t)(base[i] - base[0]) != pre[i]) contiguous = 0;
+      if (pre[i + 1] > pre[i] && (uint32_t)(base[i] - base[f0]) != pre[i] - pre[f0]) contiguous = 0;
     __syncthreads();
     const uint32_t total = pre[ncol];
     const bool flat = contiguous != 0;
@@ -228,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_copy_dg_var(const CopyDGLaunch p, 
         const uint32_t vv = v + u * kThreads;
         if (vv < total) {
           if (flat) {
-            dst[u] = (uint32_t)base[0] + vv;
+            dst[u] = (uint32_t)base[f0] - pre[f0] + vv;
           } else {
             const int cl = tile_find<TILE>(pre, ncol, vv);
             dst[u] = (uint32_t)base[cl] + (vv - pre[cl]);
@@ -304,7 +322,7 @@ unsigned grid_for(uint64_t work, int per_thread) {
 }  // namespace
 
 cudaError_t launch_copy_dg(const CopyDGLaunch &p, cudaStream_t s) {
-  if (p.cell_layers) {
+  if (p.cell_layers || p.rowptr) {
     if (p.ncells == 0) return cudaSuccess;
     const int64_t ntiles = (p.ncells + 127) / 128;
     const int64_t grid = ntiles < 152 * 8 ? ntiles : 152 * 8;

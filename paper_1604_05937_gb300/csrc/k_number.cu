@@ -181,3 +181,82 @@ cudaError_t launch_extrude(const ExtrudeLaunch &p, cudaStream_t s) {
   k_extrude<<<(unsigned)blocks, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Per-entity DoF counts (ragged lists).  Entity g (dimension-major) carries
+// dent[2g] DoFs on each horizontal copy and dent[2g+1] on each vertical one;
+// its column holds (hi - lo)(dent[2g] + dent[2g+1]) + dent[2g] numbers.
+
+__global__ void __launch_bounds__(256) k_ragged_colsize(const RaggedLaunch p, int64_t nent, int64_t *sizes) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nent; g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = p.dent[2 * g], b = p.dent[2 * g + 1];
+    const int64_t lay = p.ent_lo ? (int64_t)(p.ent_hi[g] - p.ent_lo[g]) : (int64_t)p.layers;
+    sizes[g] = lay * (a + b) + a;
+  }
+}
+
+cudaError_t launch_ragged_colsize(const RaggedLaunch &p, int64_t *sizes, cudaStream_t s) {
+  const int64_t nent = p.N[0] + p.N[1] + p.N[2];
+  if (nent == 0) return cudaSuccess;
+  int64_t blocks = (nent + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_ragged_colsize<<<(unsigned)blocks, 256, 0, s>>>(p, nent, sizes);
+  return cudaGetLastError();
+}
+
+// global entity index of local entity e of dimension d of cell c
+__device__ __forceinline__ int64_t ragged_entity(const RaggedLaunch &p, int64_t c, int d, int e) {
+  if (d == 0) return p.cell_verts[c * p.nvc + e];
+  if (d == 1) return p.N[0] + p.cell_edges[c * p.nvc + e];
+  return p.N[0] + p.N[1] + c;
+}
+
+// row length of cell c: sum over its entities of 2 dent_h + dent_v
+__global__ void __launch_bounds__(256) k_ragged_rowlen(const RaggedLaunch p) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < p.ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t len = 0;
+    for (int d = 0; d <= 2; ++d)
+      for (int e = 0; e < (d == 2 ? 1 : p.nvc); ++e) {
+        const int64_t g = ragged_entity(p, c, d, e);
+        len += 2 * p.dent[2 * g] + p.dent[2 * g + 1];
+      }
+    p.rowptr[c] = len;
+  }
+}
+
+cudaError_t launch_ragged_rowlen(const RaggedLaunch &p, cudaStream_t s) {
+  if (p.ncells == 0) return cudaSuccess;
+  int64_t blocks = (p.ncells + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_ragged_rowlen<<<(unsigned)blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Row c at the cell's bottom layer: per entity the bottom horizontal DoFs,
+// the top horizontal DoFs and the vertical DoFs; each entry's offset is its
+// entity's dent_h + dent_v (Algorithm 2's rule).
+__global__ void __launch_bounds__(256) k_ragged_map(const RaggedLaunch p) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < p.ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = p.rowptr[c];
+    for (int d = 0; d <= 2; ++d)
+      for (int e = 0; e < (d == 2 ? 1 : p.nvc); ++e) {
+        const int64_t g = ragged_entity(p, c, d, e);
+        const int32_t a = p.dent[2 * g], b = p.dent[2 * g + 1];
+        const int64_t lift = p.ent_lo ? (int64_t)(p.cell_first[c] - p.ent_lo[g]) * (a + b) : 0;
+        const int64_t s0 = p.ent_start[g] + lift;
+        for (int32_t q = 0; q < a; ++q, ++j) { p.map[j] = (int32_t)(s0 + q); p.roff[j] = a + b; }
+        for (int32_t q = 0; q < a; ++q, ++j) { p.map[j] = (int32_t)(s0 + a + b + q); p.roff[j] = a + b; }
+        for (int32_t q = 0; q < b; ++q, ++j) { p.map[j] = (int32_t)(s0 + a + q); p.roff[j] = a + b; }
+      }
+  }
+}
+
+cudaError_t launch_ragged_map(const RaggedLaunch &p, cudaStream_t s) {
+  if (p.ncells == 0) return cudaSuccess;
+  int64_t blocks = (p.ncells + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_ragged_map<<<(unsigned)blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
