@@ -817,6 +817,10 @@ def run_cfg6(args, rank, world, local):
 # differences more: 9 and 2.
 FACET_MASS_OPS = {3: 6, 1: 1}
 FACET_JUMP_OPS = {3: 9, 1: 2}
+# FP64 ops per cell-layer of the p-adaptive DG right-hand side on a straight
+# prism, by the cell's DoF count (layer height, node scaling, the element's
+# closed form, and the K additions into the output block).
+DGP_OPS = {1: 4, 2: 10, 3: 12, 6: 27}
 FACET_SPACES = [("CG1xCG1", (1, 0, 0, 0, 0, 0), 3), ("DG0xCG1", (0, 0, 0, 0, 1, 0), 1),
                 ("DG1xCG1", (0, 0, 0, 0, 3, 0), 3)]
 JUMP_SPACES = [("DG0xDG0", (0, 0, 0, 0, 0, 1), 1), ("DG1xDG0", (0, 0, 0, 0, 0, 3), 3),
@@ -936,12 +940,47 @@ def run_cfg7(args, rank, world, local):
         E.ext_sync_check(s)
         return row
 
+    def padaptive(gm, cs, X, cell_layers):
+        """p-adaptive DG (per-entity DoF counts): RHS and copy on a space with
+        DG1xDG1 cells in a disk and DG0xDG0 cells elsewhere."""
+        _, ne, _ = gm.N
+        dent = meshgen.padaptive_dent(m, ne, SEED + 80, "disk")
+        sp = E.Space(gm, dent=dent)
+        f = torch.rand(sp.ndofs, dtype=torch.float64, device=dev)
+        b, o = sp.zeros(), sp.zeros()
+        kc = dent[-C:, 1].astype(np.int64)
+        lay_c = cell_layers.astype(np.int64)
+        ops = int(sum(DGP_OPS[k] * int(lay_c[kc == k].sum()) for k in (1, 2, 3, 6)))
+        entries = int((kc).sum())
+        t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_DGP, [(cs.handle, X, R), (sp.handle, f, R),
+                                                                        (sp.handle, b, I)], s), pre=b.zero_)
+        vb = 24 * cs.ndofs + 16 * sp.ndofs + 24 * C + 8 * (C + 1) + 4 * entries
+        row = {"dg1_cells": int((kc == 6).sum()), "ndofs": int(sp.ndofs),
+               "rhs": {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1),
+                       "fp64_pct_nominal": round(100 * ops / t / 1e6 / nominal, 1)}}
+        t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_COPY_DG, [(sp.handle, f, R), (sp.handle, o, W)], s))
+        vb = 16 * sp.ndofs + 8 * (C + 1) + 4 * entries
+        row["copy"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1)}
+        del b, o, f
+        # the same right-hand side with one element everywhere, for reference
+        for nm, delta in (("uniform_DG0xDG0", (0, 0, 0, 0, 0, 1)), ("uniform_DG1xDG1", (0, 0, 0, 0, 0, 6))):
+            su = E.Space(gm, delta)
+            fu = torch.rand(su.ndofs, dtype=torch.float64, device=dev)
+            bu = su.zeros()
+            t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_TP, [(cs.handle, X, R), (su.handle, fu, R),
+                                                                           (su.handle, bu, I)], s), pre=bu.zero_)
+            row[nm] = {"ms": round(t, 4)}
+            del su, fu, bu
+        E.ext_sync_check(s)
+        return row
+
     results = {}
     # (a)+(b) variable layers
     gm = E.Mesh(m.cells, m.xy, cell_first=first, cell_layers=lay)
     vlo, vhi = vertex_hulls(m, first.astype(np.int64), lay.astype(np.int64))
     row, (cs, X) = step_loops(gm)
     row.update(facet_loops(gm, cs, X, int(lay.sum()), int(np.maximum(vhi - vlo - 1, 0).sum())))
+    row["padaptive_dg"] = padaptive(gm, cs, X, lay)
     results["variable"] = row
     del gm, cs, X
     torch.cuda.empty_cache()
@@ -951,6 +990,7 @@ def run_cfg7(args, rank, world, local):
         row, (cs, X) = step_loops(gm)
         if name == "constant_top":
             row.update(facet_loops(gm, cs, X, C * L, V * (L - 1)))
+            row["padaptive_dg"] = padaptive(gm, cs, X, np.full(C, L))
         results[name] = row
         del gm, cs, X
         torch.cuda.empty_cache()

@@ -220,3 +220,22 @@ def column_layers(m: BaseMesh, maxlevel: int, seed: int, kind: str = "bathymetry
     depth = 0.55 + 0.4 * np.sin(3.0 * cxy[:, 0] + ph[0]) * np.cos(2.0 * cxy[:, 1] + ph[1])
     lay = np.clip(np.rint(depth * maxlevel), 1, maxlevel).astype(np.int32)
     return (maxlevel - lay).astype(np.int32), lay
+
+
+def padaptive_dent(m: BaseMesh, nedges: int, seed: int, kind: str = "disk") -> np.ndarray:
+    """Per-entity DoF counts ((V + E + C) x 2, dimension-major) of a p-adaptive
+    DG space: DoFs only inside the cells, each cell one of DG0xDG0 (1),
+    DG0xDG1 (2), DG1xDG0 (3), DG1xDG1 (6).  ``disk``: DG1xDG1 in the cells
+    whose centroid lies within 0.3 of (0.5, 0.5) (about 28 % of the cells),
+    DG0xDG0 elsewhere; ``mixed``: the four kinds drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    dent = np.zeros((m.nverts + nedges + m.ncells, 2), dtype=np.int32)
+    if kind == "mixed":
+        k = rng.choice(np.array([1, 2, 3, 6], dtype=np.int32), m.ncells)
+    elif kind == "disk":
+        c = m.xy[m.cells].mean(axis=1)
+        k = np.where(((c[:, 0] - 0.5) ** 2 + (c[:, 1] - 0.5) ** 2) < 0.09, 6, 1).astype(np.int32)
+    else:
+        raise ValueError(kind)
+    dent[m.nverts + nedges:, 1] = k
+    return dent

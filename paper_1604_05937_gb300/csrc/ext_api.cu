@@ -379,6 +379,7 @@ extern "C" void ext_space_destroy(ext_space *space) {
   cudaFree(space->d_offset);
   cudaFree(space->d_rowptr);
   cudaFree(space->d_roff);
+  for (int i = 0; i < 4; ++i) cudaFree(space->d_cells_by_k[i]);
   delete space;
 }
 
@@ -465,6 +466,22 @@ extern "C" ext_status ext_number_dofs_ragged(ext_mesh *mesh, const int32_t *dent
   cudaFree(d_dent);
   cudaFree(d_starts);
   cudaFree(d_scratch);
+  if (e == cudaSuccess && bad == EXT_OK && sp->dgp) {
+    // p-adaptive DG: the cells of each element kind, for one launch per kind
+    const int kinds[4] = {1, 2, 3, 6};
+    std::vector<int32_t> lst;
+    const int64_t cbase = mesh->N[0] + mesh->N[1];
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+      lst.clear();
+      for (int64_t c = 0; c < C; ++c)
+        if (dent_host[2 * (cbase + c) + 1] == kinds[t]) lst.push_back((int32_t)c);
+      sp->ncells_by_k[t] = (int64_t)lst.size();
+      if (lst.empty()) continue;
+      e = cudaMalloc(&sp->d_cells_by_k[t], sizeof(int32_t) * lst.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(sp->d_cells_by_k[t], lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice);
+    }
+  }
   if (e != cudaSuccess || bad != EXT_OK) {
     ext_space_destroy(sp);
     if (bad != EXT_OK) return bad;
@@ -765,7 +782,6 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
         return ext_fail(EXT_EINVAL, "%s: every cell needs 1, 2, 3 or 6 DoFs and no DoF may sit outside the cells", kn);
       MassDGPLaunch p;
       memset(&p, 0, sizeof(p));
-      p.ncells = C;
       p.layers = L;
       p.cmap = args[0].space->d_map;
       for (int i = 0; i < 6; ++i) p.coff[i] = args[0].space->h_offset[i];
@@ -776,7 +792,13 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.b = (double *)args[2].data;
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
-      e = launch_mass_dgp(p, s);
+      const int kinds[4] = {1, 2, 3, 6};
+      for (int t = 0; t < 4 && e == cudaSuccess; ++t) {
+        p.ncells = args[1].space->ncells_by_k[t];
+        p.cells = args[1].space->d_cells_by_k[t];
+        p.kind = kinds[t];
+        e = launch_mass_dgp(p, s);
+      }
       break;
     }
     case EXT_K_HFACET_MASS:

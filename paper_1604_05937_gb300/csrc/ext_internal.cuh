@@ -64,6 +64,8 @@ struct ext_space {
   int32_t *d_roff = nullptr;    // nentries: offset of every list entry
   bool dg_cells = false;        // DoFs only inside cells (copyable column by column)
   bool dgp = false;             // and every cell is DG0|DG1 x DG0|DG1 (1, 2, 3 or 6 DoFs)
+  int32_t *d_cells_by_k[4] = {nullptr, nullptr, nullptr, nullptr};  // dgp: cells with 1, 2, 3, 6 DoFs
+  int64_t ncells_by_k[4] = {0, 0, 0, 0};
 };
 
 // ---------------------------------------------------------------------------
@@ -194,7 +196,9 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
 // DG0|DG1 by its DoF count (1 DG0xDG0, 2 DG0xDG1, 3 DG1xDG0, 6 DG1xDG1); the
 // cell's DoFs are consecutive, layer after layer (Algorithm 1).
 struct MassDGPLaunch {
-  int64_t ncells;
+  int64_t ncells;        // cells in `cells` (one element kind per launch)
+  const int32_t *cells;  // base cells of this element kind
+  int32_t kind;          // DoFs per cell-layer: 1, 2, 3 or 6
   int32_t layers;
   const int32_t *cmap;   // coords map (k = 6)
   int32_t coff[6];

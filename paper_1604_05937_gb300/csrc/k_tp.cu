@@ -206,73 +206,45 @@ cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
 
 
 // p-adaptive DG (EXT_K_MASS_DGP): every cell carries its own element, DG0|DG1
-// x DG0|DG1, told apart by its DoF count K (1, 2, 3, 6); node (a, b) is DoF
-// a NV + b of the cell's block, and the blocks of a column follow each other
-// layer by layer (Algorithm 1), so layer l's block starts at row[0] + l K.
-// One lane per (column, layer) item as in k_mass_tp; the element vector is
-// the closed form of that element on a straight prism, tp_general otherwise.
-// Each block belongs to one cell-layer, so the increments are plain stores.
+// x DG0|DG1, told apart by its DoF count K = NH NV (1, 2, 3, 6).  The library
+// keeps the cells of each kind in a list and launches one kernel per kind
+// over its list, so a warp never mixes elements.  Node (a, b) is DoF a NV + b
+// of the cell's block, and the blocks of a column follow each other layer by
+// layer (Algorithm 1), so layer l's block starts at row[0] + l K.  One lane
+// per (column, layer) item as in k_mass_tp; the element vector is the closed
+// form on a straight prism, tp_general otherwise.  Each block belongs to one
+// cell-layer; the increments still go out as reductions (no load of b waits
+// on the lane).
 struct DGPCol {
-  double w;                // |2A| / 2, the horizontal factor before the node scaling
+  double cc0;              // |2A| / 2 x (1/12 if NH = 3) x (1/6 if NV = 2): cc = cc0 |h|
   long long rx[3], ry[3];
   int32_t cm[6];
   int32_t blk;             // first DoF of the column's block at its bottom layer
-  int kk;                  // DoFs per cell-layer (1, 2, 3, 6)
   int lay;
 };
 
-template <int NH, int NV>
-__device__ __forceinline__ void dgp_element(const double Xl[6][3], bool ok, double cc, const double *f, double *b) {
-  if (ok) {
-    if (NH == 1 && NV == 1) {
-      b[0] = cc * f[0];
-    } else if (NH == 1) {
-      const double c2 = cc + cc;
-      b[0] = fma(c2, f[0], cc * f[1]);
-      b[1] = fma(c2, f[1], cc * f[0]);
-    } else if (NV == 1) {
-      const double cS = cc * ((f[0] + f[1]) + f[2]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
-    } else {
-      double t[6];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
-        t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
-      }
-      const double K0 = cc * ((t[0] + t[2]) + t[4]), K1 = cc * ((t[1] + t[3]) + t[5]);
-#pragma unroll
-      for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
-    }
-  } else {
-    tp_general<NH, NV>(Xl, f, b);
-  }
-}
-
-template <bool VAR>
+template <int NH, int NV, bool VAR>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_dgp(const MassDGPLaunch p, int cpw) {
+  constexpr int K = NH * NV;
   __shared__ DGPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int layers = p.layers;
   const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
   const int64_t wstride = (int64_t)gridDim.x * kWarps;
   for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
-    const int64_t c0 = grp * cpw;
-    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    const int64_t i0 = grp * cpw;
+    const int ncol = (int)(p.ncells - i0 < cpw ? p.ncells - i0 : (int64_t)cpw);
     int my_items = 0;
     if (lane < ncol) {
-      const int64_t c = c0 + lane;
+      const int64_t c = __ldg(p.cells + i0 + lane);
       DGPCol &ci = cols[warp][lane];
       const int lay = VAR ? __ldg(p.cell_layers + c) : layers;
       ci.lay = lay;
       my_items = lay;
-      const int64_t r0 = __ldg(p.rowptr + c);
-      ci.kk = (int)(__ldg(p.rowptr + c + 1) - r0);
-      ci.blk = __ldg(p.fmap + r0);
+      ci.blk = __ldg(p.fmap + __ldg(p.rowptr + c));
       double x[3], y[3];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) ci.cm[i] = __ldg(p.cmap + c * 6 + i);
+      for (int q = 0; q < 6; ++q) ci.cm[q] = __ldg(p.cmap + c * 6 + q);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         x[a] = __ldg(p.X + 3 * (int64_t)ci.cm[2 * a] + 0);
@@ -280,7 +252,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_dgp(const MassDGPLaunch
         ci.rx[a] = __double_as_longlong(x[a]);
         ci.ry[a] = __double_as_longlong(y[a]);
       }
-      ci.w = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * 0.5;
+      ci.cc0 = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) *
+               (0.5 * (NH == 3 ? 1.0 / 12.0 : 1.0) * (NV == 2 ? 1.0 / 6.0 : 1.0));
     }
     __syncwarp();
     const int nitems = VAR ? __reduce_add_sync(0xffffffffu, my_items) : ncol * layers;
@@ -299,28 +272,49 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_dgp(const MassDGPLaunch
         double Xl[6][3];
         int ok = 1;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          const int64_t cd = (int64_t)ci.cm[i] + (int64_t)l * p.coff[i];
-          Xl[i][0] = __ldg(p.X + 3 * cd + 0);
-          Xl[i][1] = __ldg(p.X + 3 * cd + 1);
-          Xl[i][2] = __ldg(p.X + 3 * cd + 2);
-          ok &= (__double_as_longlong(Xl[i][0]) == ci.rx[i >> 1]) & (__double_as_longlong(Xl[i][1]) == ci.ry[i >> 1]);
+        for (int q = 0; q < 6; ++q) {
+          const int64_t cd = (int64_t)ci.cm[q] + (int64_t)l * p.coff[q];
+          Xl[q][0] = __ldg(p.X + 3 * cd + 0);
+          Xl[q][1] = __ldg(p.X + 3 * cd + 1);
+          Xl[q][2] = __ldg(p.X + 3 * cd + 2);
+          ok &= (__double_as_longlong(Xl[q][0]) == ci.rx[q >> 1]) & (__double_as_longlong(Xl[q][1]) == ci.ry[q >> 1]);
         }
         ok &= (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[2][2])) &
               (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[4][2])) &
               (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
               (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
-        const int K = ci.kk;
         const int64_t blk = (int64_t)ci.blk + (int64_t)l * K;
-        const double h = fabs(Xl[1][2] - Xl[0][2]);
-        double f[6], b[6];
+        double f[K], b[K];
+#pragma unroll
         for (int j = 0; j < K; ++j) f[j] = __ldg(p.f + blk + j);
-        // |2A|/2 x (1/12 if three horizontal nodes) x (1/6 if two vertical nodes) x |h|
-        if (K == 1) dgp_element<1, 1>(Xl, ok, ci.w * h, f, b);
-        else if (K == 2) dgp_element<1, 2>(Xl, ok, ci.w * (1.0 / 6.0) * h, f, b);
-        else if (K == 3) dgp_element<3, 1>(Xl, ok, ci.w * (1.0 / 12.0) * h, f, b);
-        else dgp_element<3, 2>(Xl, ok, ci.w * (1.0 / 72.0) * h, f, b);
-        for (int j = 0; j < K; ++j) p.b[blk + j] += b[j];
+        const double cc = ci.cc0 * fabs(Xl[1][2] - Xl[0][2]);
+        if (ok) {
+          if (NH == 1 && NV == 1) {
+            b[0] = cc * f[0];
+          } else if (NH == 1) {
+            const double c2 = cc + cc;
+            b[0] = fma(c2, f[0], cc * f[1]);
+            b[K - 1] = fma(c2, f[K - 1], cc * f[0]);
+          } else if (NV == 1) {
+            const double cS = cc * ((f[0] + f[1 % K]) + f[2 % K]);
+#pragma unroll
+            for (int a = 0; a < K; ++a) b[a] = fma(cc, f[a], cS);
+          } else {
+            double t[K];
+#pragma unroll
+            for (int a = 0; a < K / 2; ++a) {
+              t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
+              t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
+            }
+            const double K0 = cc * ((t[0] + t[2 % K]) + t[4 % K]), K1 = cc * ((t[1 % K] + t[3 % K]) + t[5 % K]);
+#pragma unroll
+            for (int q = 0; q < K; ++q) b[q] = fma(cc, t[q], (q & 1) ? K1 : K0);
+          }
+        } else {
+          tp_general<NH, NV>(Xl, f, b);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) atomicAdd(p.b + blk + j, b[j]);
       }
       l += 32;
       if (VAR) {
@@ -333,7 +327,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_dgp(const MassDGPLaunch
   }
 }
 
-template <bool VAR>
+template <int NH, int NV, bool VAR>
 cudaError_t launch_dgp(const MassDGPLaunch &p, cudaStream_t s) {
   const double lay = VAR ? p.mean_layers : (double)p.layers;
   int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
@@ -346,12 +340,23 @@ cudaError_t launch_dgp(const MassDGPLaunch &p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_dgp<VAR>, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_dgp<NH, NV, VAR>, kWarps * 32, 0);
     if (resident < 1) resident = 1;
   }
   if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
-  k_mass_dgp<VAR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_dgp<NH, NV, VAR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
+}
+
+template <bool VAR>
+cudaError_t launch_dgp_kind(const MassDGPLaunch &p, cudaStream_t s) {
+  switch (p.kind) {
+    case 1: return launch_dgp<1, 1, VAR>(p, s);
+    case 2: return launch_dgp<1, 2, VAR>(p, s);
+    case 3: return launch_dgp<3, 1, VAR>(p, s);
+    case 6: return launch_dgp<3, 2, VAR>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -363,5 +368,5 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
 
 cudaError_t launch_mass_dgp(const MassDGPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
-  return p.cell_layers ? launch_dgp<true>(p, s) : launch_dgp<false>(p, s);
+  return p.cell_layers ? launch_dgp_kind<true>(p, s) : launch_dgp_kind<false>(p, s);
 }

@@ -116,6 +116,39 @@ def test_padaptive_rhs_parity(var, perturb):
     close(b.cpu().numpy(), ref, absr)
 
 
+
+@pytest.mark.parametrize("layers", [1, 30])
+@pytest.mark.parametrize("var", [False, True])
+def test_padaptive_rhs_disk_many_warps(layers, var):
+    """Two element kinds only (DG1xDG1 in a disk, DG0xDG0 elsewhere), so two of
+    the four per-kind launches are empty; 7,200 cells span many warps."""
+    m = meshgen.tri_mesh(60, seed=916, order="rcm")
+    _, ne = O.derive_edges(m.cells, m.nverts)
+    dent = meshgen.padaptive_dent(m, ne, 917, "disk")
+    assert set(np.unique(dent[m.nverts + ne:, 1])) == {1, 6}
+    if var:
+        first, lay = meshgen.column_layers(m, layers, 918, "bathymetry")
+        gm = E.Mesh(m.cells, m.xy, cell_first=first, cell_layers=lay)
+        ocs, X = O.coords_var(m.cells, m.xy, first, lay)
+        osp = O.number_ragged(m.cells, m.nverts, dent, cell_first=first, cell_layers=lay)
+        kw = dict(cell_first=first, cell_layers=lay)
+    else:
+        gm = E.Mesh(m.cells, m.xy, layers)
+        ocs, X = O.coords(m.cells, m.xy, layers)
+        osp = O.number_ragged(m.cells, m.nverts, dent, layers=layers)
+        kw = {}
+    f = meshgen.uniform_field(osp.ndofs, 919)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.par_loop(O.K_MASS_DGP, m.cells, ocs.layers, [(ocs, X, 3, O.READ), (osp, f, 1, O.READ),
+                                                   (osp, ref, 1, O.INC, absr)], **kw)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    gs = E.Space(gm, dent=dent)
+    b = gs.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_DGP, (cs, torch.from_numpy(X).to(dev), E.EXT_READ),
+               (gs, torch.from_numpy(f).to(dev), E.EXT_READ), (gs, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(b.cpu().numpy(), ref, absr)
+
 def test_ragged_validation():
     m = meshgen.tri_mesh(4, seed=916)
     gm = E.Mesh(m.cells, m.xy, 3)
