@@ -43,37 +43,69 @@ SM_MAX_MHZ = 2070.0
 P1_DELTA = (1, 0, 0, 0, 0, 0)
 DG1_DELTA = (0, 0, 0, 0, 0, 6)
 # FP64 work of one P1xP1 RHS / mass-action par_loop on straight prisms in the
-# split form the library runs: the vertical sums of every vertex level,
-#   w = |h_lo| (f_lo + 2 f) + |h_hi| (2 f + f_hi)       1 DADD, 1 DMUL, 3 DFMA per DoF,
-# and the horizontal combination of every (column, level) item,
-#   value_a = alpha (w_a + w_0 + w_1 + w_2)              1 DMUL, 5 DFMA per item,
-# with 3 FP64 atomic adds per item (executed in L2).  One launch runs three
-# kernels (vertical sums, cell pass, and the pass over deferred non-straight
-# warp steps, which finds none on a straight mesh).  Evaluating each cell's
-# element matrix by itself instead needs 18 FP64 operations per item.
-VSUM_OPS_PER_DOF = 5
-CELL_OPS_PER_ITEM = 6
+# split form the library runs.  Constant layers, two or more (factored form):
+#   alpha_c = |2A_c| / 144, A_a = sum of alpha_c around a   4 DADD, 2 DMUL, 1 DFMA per cell,
+#   w = |h_lo| (f_lo + 2 f) + |h_hi| (2 f + f_hi),
+#   b += A_a w                                             6 per DoF,
+#   alpha_c (w_0 + w_1 + w_2) to the three vertices        3 per item,
+# four kernels (areas, vertex pass, cell pass, and the pass over deferred
+# non-straight warp steps, which finds none on a straight mesh).  One
+# constant layer: w alone (5 per DoF) and
+#   value_a = alpha (w_a + w_0 + w_1 + w_2)                6 per item,
+# three kernels.  Variable layers: w and its two one-layer halves (6 per DoF)
+# and the same 6 per item, three kernels.  The vertex and cell passes issue
+# their products and sums as DFMA (a b + (-0), a (+-1) + b).  All send 3 FP64
+# atomic adds per item to L2.  Evaluating each cell's element matrix by itself
+# instead needs 18 FP64 operations per item.
+P1_MIX = {  # (dadd, dmul, dfma) per DoF, per item, per cell
+    "factored": ((0, 0, 6), (0, 0, 3), (4, 2, 1)),
+    "plain": ((0, 0, 5), (0, 0, 6), (0, 0, 0)),
+    "var": ((0, 0, 6), (0, 0, 6), (0, 0, 0)),
+}
+P1_KERNELS = {"factored": 4, "plain": 3, "var": 3, "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 CELLWISE_OPS_PER_ITEM = 18
 SINGLE_PASS_SM_OPS_PER_ITEM = 13
 P1_SPLIT_MIN_ITEMS = 1_000_000
-P1_KERNELS_PER_LAUNCH = 3
+P1_FACTORED_MIN_LAYERS = 2
 
 
-def p1_ops(ndofs: int, items: int) -> int:
-    """FP64 operations of one P1xP1 RHS / mass-action launch: the split form,
-    or below a million items the single-pass kernel the library runs there
-    (13 operations per item on the SM, the horizontal sum in L2 atomics)."""
-    if items < P1_SPLIT_MIN_ITEMS:
-        return SINGLE_PASS_SM_OPS_PER_ITEM * items
-    return VSUM_OPS_PER_DOF * ndofs + CELL_OPS_PER_ITEM * items
+def p1_form(items: int, layers: int, var: bool = False) -> str:
+    """The form the library picks for a P1xP1 launch (EXTMESH_MASS_FUSED and
+    EXTMESH_MASS_FACTORED override its choice as they do the library's)."""
+    fused, fac = os.environ.get("EXTMESH_MASS_FUSED", ""), os.environ.get("EXTMESH_MASS_FACTORED", "")
+    if fused == "1" or (fused != "0" and items < P1_SPLIT_MIN_ITEMS):
+        return "single"
+    if var:
+        return "var"
+    if fac in ("0", "1"):
+        return "factored" if fac == "1" else "plain"
+    return "factored" if layers >= P1_FACTORED_MIN_LAYERS else "plain"
 
 
-def p1_mix_ceiling(ndofs: int, items: int, rates: dict) -> float:
+def p1_counts(ndofs: int, items: int, ncells: int, layers: int, var: bool = False) -> tuple:
+    """(DADD, DMUL, DFMA) of one P1xP1 RHS / mass-action launch; the single-pass
+    kernel below a million items executes 13 operations per item on the SM
+    (3 DMUL, 6 DFMA, 4 for the layer factors counted as DFMA; the horizontal
+    sum in L2 atomics)."""
+    form = p1_form(items, layers, var)
+    if form == "single":
+        return (0, 3 * items, 10 * items)
+    per = P1_MIX[form]
+    return tuple(per[0][k] * ndofs + per[1][k] * items + per[2][k] * ncells for k in range(3))
+
+
+def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False) -> int:
+    return sum(p1_counts(ndofs, items, ncells, layers, var))
+
+
+def p1_kernels(items: int, layers: int, var: bool = False) -> int:
+    return P1_KERNELS[p1_form(items, layers, var)]
+
+
+def p1_mix_ceiling(ndofs: int, items: int, ncells: int, layers: int, rates: dict, var: bool = False) -> float:
     """G op/s ceiling of that operation mix at the measured DFMA/DADD/DMUL rates."""
-    dfma = 3 * ndofs + 5 * items
-    dadd = ndofs
-    dmul = ndofs + items
+    dadd, dmul, dfma = p1_counts(ndofs, items, ncells, layers, var)
     return (dfma + dadd + dmul) / (dfma / rates["dfma"] + dadd / rates["dadd"] + dmul / rates["dmul"])
 
 
@@ -360,10 +392,10 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     ndofs = V * (L + 1)
     mass_ms = statistics.mean(k_rhs + k_mass)
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
-    ops = p1_ops(ndofs, items)
+    ops = p1_ops(ndofs, items, C, L)
     achieved_ops = ops / (mass_ms * 1e-3) / 1e9
     traffic = load_traffic("p1_mass_launch")
-    mix_peak = p1_mix_ceiling(ndofs, items, rates)
+    mix_peak = p1_mix_ceiling(ndofs, items, C, L, rates)
     l2_adds = CELL_ATOMICS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
@@ -383,12 +415,13 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                         "interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6, 1)},
         "hbm_frac": {"interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6 / hbm, 4),
                      "step": round(value / world / hbm, 4), "peak_gbs": hbm, "peak_kind": hbm_kind},
-        "roofline": {"kernel": "P1xP1 RHS / mass-action launch (k_vsum + k_mass_cells + k_mass_general)",
+        "roofline": {"kernel": "P1xP1 RHS / mass-action launch (k_area + k_vsum + k_mass_cells + k_mass_general)",
                      "bound": "alu",
                      "achieved": round(achieved_ops, 2), "peak": round(ops_peak, 2), "unit": "G FP64 ops/s",
                      "frac": round(achieved_ops / ops_peak, 4), "traffic": traffic,
-                     "algorithmic": f"{VSUM_OPS_PER_DOF} FP64 ops per DoF x {ndofs} DoFs + {CELL_OPS_PER_ITEM} "
-                                    f"per (column, level) item x {items} items = {ops} per launch",
+                     "algorithmic": f"{sum(P1_MIX['factored'][0])} FP64 ops per DoF x {ndofs} DoFs + "
+                                    f"{sum(P1_MIX['factored'][1])} per (column, level) item x {items} items + "
+                                    f"{sum(P1_MIX['factored'][2])} per cell x {C} cells = {ops} per launch",
                      "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
                      "mix_ceiling_gops": round(mix_peak, 1),
@@ -397,12 +430,13 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                                         "frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
                      "cellwise_equivalent_gops": round(CELLWISE_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9, 1),
                      "note": "the split form computes each vertex column's vertical sums once instead of once "
-                             "per cell around the vertex; evaluated cell by cell the same work is 18 FP64 ops "
-                             "per item (cellwise_equivalent_gops)"},
+                             "per cell around the vertex, and adds the vertex part alpha_c w_a of all cells "
+                             "around a vertex as one product A_a w_a; evaluated cell by cell the same work is "
+                             "18 FP64 ops per item (cellwise_equivalent_gops)"},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-        "gpu_launches": (2 * P1_KERNELS_PER_LAUNCH + 1) * args.steps,
+        "gpu_launches": (2 * p1_kernels(items, L) + 1) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -552,7 +586,7 @@ def run_cfg3(args, rank, world, local):
             t_rhs = time_kernel(rhs, reps, stream, flush, pre=b.zero_)
             t_c0 = time_kernel(c0, reps, stream, flush)
             t_c1 = time_kernel(c1, reps, stream, flush)
-            launches += (P1_KERNELS_PER_LAUNCH + 2) * (reps + args.warmup)
+            launches += (p1_kernels(C * (L + 1), L) + 2) * (reps + args.warmup)
             nP1 = V * (L + 1)
             vb_rhs = 40 * nP1 + 48 * C
             vb_c0 = 16 * C * L + 4 * C
@@ -560,7 +594,7 @@ def run_cfg3(args, rank, world, local):
             items = C * (L + 1)
             sweep[order][L] = {
                 "rhs_ms": round(t_rhs[0], 4), "rhs_gbs": round(vb_rhs / t_rhs[0] / 1e6, 1),
-                "rhs_gops": round(p1_ops(nP1, items) / t_rhs[0] / 1e6, 1),
+                "rhs_gops": round(p1_ops(nP1, items, C, L) / t_rhs[0] / 1e6, 1),
                 "dg0_ms": round(t_c0[0], 4), "dg0_gbs": round(vb_c0 / t_c0[0] / 1e6, 1),
                 "dg1_ms": round(t_c1[0], 4), "dg1_gbs": round(vb_c1 / t_c1[0] / 1e6, 1)}
             E.ext_sync_check(s)
@@ -779,8 +813,8 @@ def run_cfg6(args, rank, world, local):
                 fn()
                 reps = max(3, min(args.steps, 10))
                 t = time_kernel(fn, reps, stream, flush, pre=b.zero_)[0]
-                launches += (reps + 1) * (P1_KERNELS_PER_LAUNCH if ops is None else 1)
-                work = p1_ops(V * (L + 1), C * (L + 1)) if ops is None else ops * C * L
+                launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None else 1)
+                work = p1_ops(V * (L + 1), C * (L + 1), C, L) if ops is None else ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
                 vb = vb_paper + 24 * C + 4 * sp.k * C
                 gops = work / t / 1e6
@@ -801,8 +835,12 @@ def run_cfg6(args, rank, world, local):
     tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES)
     extra = {"spaces": results, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
              "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-             "fp64_ops_per_unit": {nm: (ops if ops is not None else f"{VSUM_OPS_PER_DOF} per DoF + "
-                                        f"{CELL_OPS_PER_ITEM} per column level") for nm, _, ops in TP_SPACES},
+             "fp64_ops_per_unit": {nm: (ops if ops is not None else
+                                        f"{sum(P1_MIX['factored'][0])} per DoF + {sum(P1_MIX['factored'][1])} "
+                                        f"per column level + {sum(P1_MIX['factored'][2])} per column from "
+                                        f"{P1_FACTORED_MIN_LAYERS} layers, {sum(P1_MIX['plain'][0])} per DoF + "
+                                        f"{sum(P1_MIX['plain'][1])} per column level below")
+                                   for nm, _, ops in TP_SPACES},
              "timing": "min over reps, L2 flushed before every timed launch"}
     return _common(args, world, "I_1 = int f v dx on the nine prism spaces at 100 layers (~15M cells, RCM): valuable "
                    "GB/s over the nine launches", world * tot_b / tot_t, "GB/s",
@@ -894,11 +932,12 @@ def run_cfg7(args, rank, world, local):
         row = {}
         t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, [(cs.handle, X, R), (p1.handle, x, R),
                                                                          (p1.handle, b, I)], s), pre=b.zero_,
-                  kernels=P1_KERNELS_PER_LAUNCH)
+                  kernels=p1_kernels(items, gm.layers, gm.variable))
         vb = 24 * nP1 + 16 * nP1 + 48 * C
         row["mass_p1p1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
-                            "fp64_gops": round(p1_ops(nP1, items) / t / 1e6, 1),
-                            "fp64_pct_nominal": round(100 * p1_ops(nP1, items) / t / 1e6 / nominal, 1)}
+                            "fp64_gops": round(p1_ops(nP1, items, C, gm.layers, gm.variable) / t / 1e6, 1),
+                            "fp64_pct_nominal": round(100 * p1_ops(nP1, items, C, gm.layers, gm.variable) / t / 1e6
+                                                      / nominal, 1)}
         t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_INTERP_DG1, [(p1.handle, x, R), (dg.handle, out, W)], s))
         vb = 8 * nP1 + 8 * dg.ndofs + 48 * C
         row["interp_dg1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1), "hbm_pct": round(100 * vb / t / 1e6 / hbm, 1)}

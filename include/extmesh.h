@@ -56,7 +56,9 @@ typedef enum { EXT_TRI = 3, EXT_QUAD = 4 } ext_cell_kind;
 
 /* Access descriptors of a par_loop argument (Sec. 3.3, PyOP2 semantics):
  * READ is never written; WRITE overwrites every DoF the loop reaches; INC
- * adds into the existing values (the caller zeroes them first). */
+ * adds into the existing values (the caller zeroes them first).  A WRITE or
+ * INC argument's data must not overlap any other argument's data
+ * (EXT_EINVAL). */
 typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
 
 /* Local kernels (stencil functions S of Algorithm 3).  Each fixes its
@@ -74,21 +76,28 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  * EXT_K_RHS_P1P1    [coords READ, f READ, b INC] on prisms, all CG1xCG1:
  *                   b_i += int_cell f_h phi_i dx  (the residual I_1, Sec. 4.1.1).
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
- *                   Both run as three kernels: vertical sums of the input per
- *                   vertex level, the cell pass, and a pass over the warp steps
- *                   that met a prism which is not straight (6-point rule, general
- *                   Jacobian).  The sums and that list live in scratch taken
- *                   from the device's default stream-ordered pool
- *                   (cudaMallocAsync / cudaFreeAsync on `stream`: 8 bytes per
- *                   DoF of f, 24 on a mesh with variable layers, plus at most 1
- *                   byte per item), so launches on different
+ *                   Both run as four kernels on two or more constant
+ *                   layers: the area factor of every cell summed per vertex,
+ *                   vertical sums of the input per vertex level (which also
+ *                   add each vertex's share of its own sums), the cell pass,
+ *                   and a pass over the warp steps that met a prism which is
+ *                   not straight (6-point rule, general Jacobian); three with
+ *                   one or variable layers (no area pass; the cell pass adds
+ *                   each vertex's share).  The sums, the area factors and that
+ *                   list live in scratch taken from the device's default
+ *                   stream-ordered pool (cudaMallocAsync / cudaFreeAsync on
+ *                   `stream`: 16 bytes per DoF of f plus 8 per vertex, 24 per
+ *                   DoF on a mesh with variable layers, plus at most 1 byte per
+ *                   item), so launches on different
  *                   streams never share it and the launch can be captured in a
  *                   CUDA graph.  If the pool cannot supply it, or the launch
  *                   has fewer than a million (column, level) items, a
  *                   single-pass kernel that needs no scratch (every cell forms
  *                   its own vertical sums) runs instead.  The environment
- *                   variable EXTMESH_MASS_FUSED, read once per process, selects
- *                   the single pass (1) or the split form (0) at any size.
+ *                   variables EXTMESH_MASS_FUSED and EXTMESH_MASS_FACTORED,
+ *                   read once per process, select the single pass (1) or the
+ *                   split form (0) at any size, and the split form with (1)
+ *                   or without (0) the area pass at any constant layer count.
  *                   Coordinates must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
  *                   interpolation, out at DG1 node (vertex a, level b) = x there.

@@ -594,6 +594,19 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
   const int64_t C = mesh->N[2];
   const int L = mesh->layers;
   cudaError_t e = cudaSuccess;
+  // a WRITE or INC argument may share no byte with another argument
+  for (int i = 0; i < nargs; ++i) {
+    if (args[i].access == EXT_READ || !args[i].space || !args[i].data) continue;
+    const char *lo_i = (const char *)args[i].data;
+    const char *hi_i = lo_i + sizeof(double) * (size_t)args[i].space->ndofs * (size_t)args[i].space->ncomp;
+    for (int j = 0; j < nargs; ++j) {
+      if (j == i || !args[j].space || !args[j].data) continue;
+      const char *lo_j = (const char *)args[j].data;
+      const char *hi_j = lo_j + sizeof(double) * (size_t)args[j].space->ndofs * (size_t)args[j].space->ncomp;
+      if (lo_i < hi_j && lo_j < hi_i)
+        return ext_fail(EXT_EINVAL, "ext_par_loop: argument %d (written) overlaps argument %d", i, j);
+    }
+  }
   switch (kernel_id) {
     case EXT_K_EXTRUDE: {
       const char *kn = "EXT_K_EXTRUDE";
@@ -662,6 +675,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
       p.nf = args[1].space->ndofs;
+      p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
       e = launch_mass_p1(p, s);
       break;
     }

@@ -170,6 +170,7 @@ struct MassP1Launch {
   const int32_t *cell_layers = nullptr;  // variable layers
   double mean_layers = 0.0;
   int64_t nf = 0;  // DoFs of the f space (CG1xCG1 numbering shared with the coordinates)
+  const double *base_xy = nullptr;  // the mesh's base coordinates (nverts x 2), if it has them
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 

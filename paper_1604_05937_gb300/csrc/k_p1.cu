@@ -48,7 +48,13 @@ constexpr unsigned kFull = 0xffffffffu;
 #define EXT_MASS_MINB 2  // resident CTAs per SM the register budget must allow
 #endif
 #ifndef EXT_CELLS_MINB
-#define EXT_CELLS_MINB 4  // resident CTAs per SM of the split form's cell pass
+#define EXT_CELLS_MINB 5  // resident CTAs per SM of the split form's cell pass (constant layers)
+#endif
+#ifndef EXT_CELLS_VAR_MINB
+#define EXT_CELLS_VAR_MINB 4  // the same with variable layers
+#endif
+#ifndef EXT_FACTORED_MIN_LAYERS
+#define EXT_FACTORED_MIN_LAYERS 2  // constant layers: the factored split form from this many layers
 #endif
 #ifndef EXT_MASS_ITEMS
 #define EXT_MASS_ITEMS 1616  // target items (column levels) per column group
@@ -333,40 +339,135 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_MASS_MINB) k_mass_p1(const Ma
 //   w_m = h_{m-1} (f_{m-1} + 2 f_m) + h_m (2 f_m + f_{m+1})
 // and a straight cell with area factor alpha = |2A| / 144 contributes
 // c_a = alpha w_{a,m} at level m, i.e. value_a = alpha (w_a + w_0 + w_1 + w_2).
-// Each vertex column is shared by about six cells, so the split form computes
-// w once per vertex level (k_vsum, over the flat DoF range of the field: the
-// column of a CG1xCG1 vertex is a contiguous run, so level m's neighbours are
-// DoFs d - 1 and d + 1) and the cell pass (k_mass_cells) only forms the
-// horizontal combination: 6 FP64 operations and 3 atomic adds per item
-// instead of 13 and 12.  The cell pass still checks straightness exactly and
-// takes the 6-point rule for any other prism.  With variable layers a vertex
-// column spans the hull of its cells' ranges, so the w of a cell's bottom and
-// top levels may include a layer outside that cell: the cell pass recomputes
-// those two levels from f.
+// Summed over the cells around vertex a this factors into a vertex part and
+// a cell part,
+//   b_{a,m} += A_a w_{a,m} + sum_{c containing a} alpha_c S_{c,m},
+//   A_a = sum_{c containing a} alpha_c,  S_{c,m} = w_0 + w_1 + w_2,
+// so with two or more constant layers the launch runs
+//   k_area        alpha_c per cell (stored) and A_a (alpha_c added to the
+//                 cell's three vertices),
+//   k_vsum        per vertex level: w, and b += A_a w (the vertex part),
+//   k_mass_cells  per (column, level) item: alpha_c S_c added to the three
+//                 vertices (3 FP64 operations and 3 atomic adds per item,
+//                 against 13 and 12 when every cell forms its own sums),
+//   k_mass_general the warp steps that met a prism which is not straight:
+//                 the 6-point rule with the general Jacobian, minus the
+//                 alpha_c w_a that the vertex part already added for them.
+// Straightness is checked exactly: k_vsum compares every DoF's x, y with its
+// column's reference x, y (those alpha was formed from: the mesh's base
+// coordinates, or the field's level 0) and stores z next to w (a NaN pattern
+// when x, y differ; coordinates are finite), and the cell pass compares the
+// three z of each level bitwise.  With one layer the area pass costs more than the
+// vertex part saves (a cell has two items to spread it over), and the cell
+// pass forms alpha (w_a + S) per item instead (6 FP64 operations).  With
+// variable layers a vertex column spans the hull of its cells' ranges, so the
+// w of a cell's bottom and top levels may include a layer outside that cell;
+// that form keeps the per-item combination with the one-layer halves at the
+// cell's ends.
 
-// w over the DoFs [0, n) of a CG1xCG1 field; `col` = layers + 1 (constant
-// layers: level m = d mod col, ends have one layer) or unused (VAR: the ends
-// of vertex columns are never read; W holds 3n values: w, the upper half
-// |h_hi| (2 f + f_hi) and the lower half |h_lo| (f_lo + 2 f)).
-template <bool VAR>
-__global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, const double *__restrict__ f,
-                                              double *__restrict__ W, int64_t n, FastDiv col) {
+// bit pattern stored in place of z when a DoF's x, y differ from its column's
+// level-0 x, y (a NaN, which finite coordinates never produce)
+constexpr long long kNotVertical = 0x7ff4000000000badLL;
+
+// A_a over the vertices (constant layers): cell c adds alpha_c = |2A_c| / 144
+// to the three vertex columns of its level-0 DoFs (column of DoF d: d / col,
+// which is base vertex d / col) and stores alpha_c for the cell and general
+// passes.  The reference x, y are the mesh's base coordinates when it has
+// them (16 bytes per vertex, which stay in L2 however the cells are ordered),
+// else the coordinate field's level 0; the vertex pass checks every level
+// against the same reference.
+__global__ void __launch_bounds__(256) k_area(const MassP1Launch p, double *__restrict__ A,
+                                              double *__restrict__ alpha_out, FastDiv col) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < p.ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double x[3], y[3];
+    uint32_t v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v[a] = fdiv((uint32_t)__ldg(p.fmap + c * 6 + 2 * a), col);
+      if (p.base_xy) {
+        x[a] = __ldg(p.base_xy + 2 * (int64_t)v[a] + 0);
+        y[a] = __ldg(p.base_xy + 2 * (int64_t)v[a] + 1);
+      } else {
+        const int64_t cb = __ldg(p.cmap + c * 6 + 2 * a);
+        x[a] = __ldg(p.X + 3 * cb + 0);
+        y[a] = __ldg(p.X + 3 * cb + 1);
+      }
+    }
+    const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+    const double alpha = fabs(det2) * (1.0 / 144.0);
+    alpha_out[c] = alpha;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) atomicAdd(A + v[a], alpha);
+  }
+}
+
+// FP64 constants the kernels take as arguments: a product and a sum are
+// issued as DFMA, a b + (-0) and a (+-1) + b, which round exactly like DMUL
+// and DADD but issue at the DFMA rate (GB300 issues DADD and DMUL at about
+// 5/6 of it).  Literal constants would let the compiler fold them back.
+struct Fp64Ones {
+  double one, mone, mzero;  // 1, -1, -0
+};
+__device__ __forceinline__ double fmul(double a, double b, const Fp64Ones &k) { return fma(a, b, k.mzero); }
+__device__ __forceinline__ double fsub(double a, double b, const Fp64Ones &k) { return fma(b, k.mone, a); }
+
+// Vertex pass over the DoFs [0, n) of a CG1xCG1 field (the column of a vertex
+// is a contiguous run, so level m's neighbours are DoFs d - 1 and d + 1).
+// Constant layers (`col` = layers + 1, level m = d mod col, the ends have one
+// layer): W holds n pairs (w, z or kNotVertical), and in the factored form
+// (FAC) b[d] += A[d / col] w.  VAR: the ends of vertex columns are
+// never read; W holds 3n values: w, the upper half |h_hi| (2 f + f_hi) and
+// the lower half |h_lo| (f_lo + 2 f); A and b are unused.
+#ifndef EXT_VSUM_MINB
+#define EXT_VSUM_MINB 4  // resident 256-thread CTAs per SM the vertex pass's registers must allow
+#endif
+#ifndef EXT_VSUM_VU
+#define EXT_VSUM_VU 2  // 32-DoF chunks per warp step of the vertex pass
+#endif
+
+template <bool VAR, bool FAC>
+__global__ void __launch_bounds__(256, EXT_VSUM_MINB) k_vsum(const double *__restrict__ X, const double *__restrict__ f,
+                                              double *__restrict__ W, int64_t n, FastDiv col,
+                                              const double *__restrict__ A, double *__restrict__ b, Fp64Ones k1,
+                                              const double *__restrict__ ref_xy) {
   // A warp takes VU consecutive 32-DoF chunks per step and issues all their
   // loads before any arithmetic (the loop is latency-bound otherwise); the
   // neighbours across chunk edges come from the adjacent chunk's lanes.
-  constexpr int VU = 4;
+  constexpr int VU = EXT_VSUM_VU;
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 * VU; base < n; base += wstride) {
     double zc[VU], fc[VU];
+    double bc[VU], Ac[VU];   // constant layers: b and A of the DoF's column
+    int okv[VU];             // constant layers: x, y equal the column's level-0 x, y
+    uint32_t mmv[VU];        // constant layers: level of the DoF
 #pragma unroll
     for (int u = 0; u < VU; ++u) {
       const int64_t d = base + u * 32 + lane;
       zc[u] = 0.0;
       fc[u] = 0.0;
+      bc[u] = 0.0;
+      Ac[u] = 0.0;
+      okv[u] = 1;
+      mmv[u] = 0;
       if (d < n) {
         zc[u] = __ldg(X + 3 * d + 2);
         fc[u] = __ldg(f + d);
+        if (!VAR) {
+          const uint32_t q = fdiv((uint32_t)d, col);
+          const int64_t d0 = (int64_t)q * col.d;
+          mmv[u] = (uint32_t)(d - d0);
+          // reference x, y of the column: the base coordinates (factored
+          // form, when the mesh has them) or the field's level 0
+          const double *r = (FAC && ref_xy) ? ref_xy + 2 * (int64_t)q : X + 3 * d0;
+          okv[u] = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(r + 0))) &
+                   (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(r + 1)));
+          if (FAC) {
+            Ac[u] = __ldg(A + q);
+            bc[u] = b[d];
+          }
+        }
       }
     }
     // the DoF before the first chunk and after the last one
@@ -379,13 +480,15 @@ __global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, cons
       za = __ldg(X + 3 * (base + 32 * VU) + 2);
       fa = __ldg(f + base + 32 * VU);
     }
+    // signed heights of the layer below each DoF, hl = z - z_left (left
+    // neighbour: previous lane; for lane 0 the previous chunk's lane 31 or
+    // its own load of DoF base - 1; u > 0 is a compile-time condition, so
+    // every lane reaches the shuffles), and the left f
+    double hl[VU], fl[VU];
 #pragma unroll
     for (int u = 0; u < VU; ++u) {
-      const int64_t d = base + u * 32 + lane;
-      // left neighbour: previous lane; for lane 0 the previous chunk's lane 31
-      // (u > 0, a compile-time condition, so every lane reaches the shuffle)
-      // or its own load of DoF base - 1
-      double zl = __shfl_up_sync(kFull, zc[u], 1), fl = __shfl_up_sync(kFull, fc[u], 1);
+      double zl = __shfl_up_sync(kFull, zc[u], 1);
+      fl[u] = __shfl_up_sync(kFull, fc[u], 1);
       double zlp = zb, flp = fb;
       if (u > 0) {
         zlp = __shfl_sync(kFull, zc[u > 0 ? u - 1 : 0], 31);
@@ -393,55 +496,59 @@ __global__ void __launch_bounds__(256) k_vsum(const double *__restrict__ X, cons
       }
       if (lane == 0) {
         zl = zlp;
-        fl = flp;
+        fl[u] = flp;
       }
-      // right neighbour: next lane; for lane 31 the next chunk's lane 0 or its
-      // own load of the DoF after the last chunk
-      double zr = __shfl_down_sync(kFull, zc[u], 1), fr = __shfl_down_sync(kFull, fc[u], 1);
-      double zrn = za, frn = fa;
+      hl[u] = fsub(zc[u], zl, k1);
+    }
+    // height of the layer above the last chunk's lane 31 (one DFMA per warp
+    // step; the value is used by lane 31 only)
+    const double ha = fsub(za, zc[VU - 1], k1);
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      // height above and right f: next lane; for lane 31 the next chunk's
+      // lane 0, or the DoF after the last chunk
+      double hh = __shfl_down_sync(kFull, hl[u], 1), fr = __shfl_down_sync(kFull, fc[u], 1);
+      double hhn = ha, frn = fa;
       if (u + 1 < VU) {
-        zrn = __shfl_sync(kFull, zc[u + 1 < VU ? u + 1 : u], 0);
+        hhn = __shfl_sync(kFull, hl[u + 1 < VU ? u + 1 : u], 0);
         frn = __shfl_sync(kFull, fc[u + 1 < VU ? u + 1 : u], 0);
       }
       if (lane == 31) {
-        zr = zrn;
+        hh = hhn;
         fr = frn;
       }
-      // signed layer heights; the absolute values are taken as operand
-      // modifiers of the DMUL / DFMA below (a separate fabs costs DADDs)
-      const double hl = zc[u] - zl;
-      double hh = __shfl_down_sync(kFull, hl, 1);
-      if (lane == 31) hh = zr - zc[u];
       bool lo_end, hi_end;
       if (VAR) {
         lo_end = d == 0;
         hi_end = d + 1 >= n;
       } else {
-        const uint32_t q = fdiv((uint32_t)d, col);
-        const uint32_t mm = (uint32_t)d - q * col.d;
-        lo_end = mm == 0;
-        hi_end = mm + 1 == col.d;
+        lo_end = mmv[u] == 0;
+        hi_end = mmv[u] + 1 == col.d;
       }
-      // w = |hl| (fl + 2 fc) + |hh| (2 fc + fr): one DADD, one DMUL, three
-      // DFMA.  At a column end the missing layer's f factor is cleared
-      // bitwise (an integer AND, off the FP64 pipe); the height read across
-      // the column boundary is then multiplied by zero (coordinates are
-      // finite).
+      // w = |hl| (fl + 2 fc) + |hh| (2 fc + fr): four DFMA (the absolute
+      // values are operand modifiers).  At a column end the missing layer's
+      // f factor is cleared bitwise (an integer AND, off the FP64 pipe); the
+      // height read across the column boundary is then multiplied by zero
+      // (coordinates are finite).
       const long long kl = lo_end ? 0LL : -1LL, kh = hi_end ? 0LL : -1LL;
-      const double al = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fl)) & kl);
+      const double al = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fl[u])) & kl);
       const double bh = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fr)) & kh);
       if (VAR) {
         // variable layers: also the one-layer halves, which the bottom (upper
         // half) and top (lower half) levels of a cell column use
-        const double up = fabs(hh) * bh;
-        const double lo = fabs(hl) * al;
+        const double up = fmul(fabs(hh), bh, k1);
+        const double lo = fmul(fabs(hl[u]), al, k1);
         if (d < n) {
-          W[d] = lo + up;
+          W[d] = fma(fabs(hl[u]), al, up);
           W[n + d] = up;
           W[2 * n + d] = lo;
         }
       } else if (d < n) {
-        W[d] = fma(fabs(hl), al, fabs(hh) * bh);
+        const double w = fma(fabs(hl[u]), al, fmul(fabs(hh), bh, k1));
+        if (FAC) b[d] = fma(w, Ac[u], bc[u]);
+        reinterpret_cast<double2 *>(W)[d] =
+            make_double2(w, okv[u] ? zc[u] : __longlong_as_double(kNotVertical));
       }
     }
   }
@@ -483,9 +590,12 @@ __device__ void prism_general_g(const double *__restrict__ Xg, const double *__r
 }
 
 // Stencil rows, area factor and level-0 corner bits of column c (Algorithm
-// 3's outer loop: the lists are read once per column).
-template <bool VAR>
-__device__ __forceinline__ int setup_column(const MassP1Launch &p, int64_t c, ColInfo &ci) {
+// 3's outer loop: the lists are read once per column).  STORED (the
+// factored form): the area factor is the one the area pass stored in
+// `alpha`, and the corner bits are not needed.
+template <bool VAR, bool STORED = false>
+__device__ __forceinline__ int setup_column(const MassP1Launch &p, int64_t c, ColInfo &ci,
+                                            const double *__restrict__ alpha = nullptr) {
   const int lay = VAR ? __ldg(p.cell_layers + c) : p.layers;
   ci.lay = lay;
   double x[3], y[3];
@@ -500,14 +610,20 @@ __device__ __forceinline__ int setup_column(const MassP1Launch &p, int64_t c, Co
     ci.ftop[a] = ft + (lay - 1) * p.foff[2 * a + 1];
     ci.bbot[a] = bb;
     ci.btop[a] = bt + (lay - 1) * p.boff[2 * a + 1];
-    x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
-    y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
-    ci.rx[a] = __double_as_longlong(x[a]);
-    ci.ry[a] = __double_as_longlong(y[a]);
+    if (!STORED) {
+      x[a] = __ldg(p.X + 3 * (int64_t)cb + 0);
+      y[a] = __ldg(p.X + 3 * (int64_t)cb + 1);
+      ci.rx[a] = __double_as_longlong(x[a]);
+      ci.ry[a] = __double_as_longlong(y[a]);
+    }
   }
-  const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
-  ci.alpha = fabs(det2) * (1.0 / 144.0);
-  ci.alpha2 = fabs(det2) * (1.0 / 72.0);
+  if (STORED) {
+    ci.alpha = __ldg(alpha + c);
+  } else {
+    const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+    ci.alpha = fabs(det2) * (1.0 / 144.0);
+  }
+  ci.alpha2 = 2.0 * ci.alpha;
   return lay + 1;
 }
 
@@ -538,10 +654,11 @@ struct Deferred {
   unsigned int cap;
 };
 
-template <bool VAR>
-__global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(const MassP1Launch p,
+template <bool VAR, bool FAC>
+__global__ void __launch_bounds__(kWarps * 32, VAR ? EXT_CELLS_VAR_MINB : EXT_CELLS_MINB) k_mass_cells(const MassP1Launch p,
                                                                             const double *__restrict__ W,
-                                                                            Deferred dfr, int cpw) {
+                                                                            Deferred dfr, int cpw, Fp64Ones k1,
+                                                                            const double *__restrict__ alpha) {
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -553,7 +670,7 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
     const int layers = p.layers;
     const int L1 = layers + 1;
     int my_items = 0;
-    if (lane < ncol) my_items = setup_column<VAR>(p, c0 + lane, cols[warp][lane]);
+    if (lane < ncol) my_items = setup_column<VAR, FAC>(p, c0 + lane, cols[warp][lane], alpha);
     __syncwarp();
     const int nitems = VAR ? __reduce_add_sync(kFull, my_items) : ncol * L1;
     int cl, m;
@@ -565,25 +682,38 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
       if (item < nitems) {
         const ColInfo &ci = cols[warp][clx];
         const int lay = VAR ? ci.lay : layers;
-        double zz[3];
-        int ok = 1;
-        // variable layers: the bottom and top levels of this cell column take
-        // the one-layer half that lies inside the column (the vertex column
-        // may extend beyond it)
-        const double *src = W;
-        if (VAR) src = mx == 0 ? W + p.nf : (mx == lay ? W + 2 * p.nf : W);
-  #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, lay);
-          const double xa = __ldg(p.X + 3 * cd + 0);
-          const double ya = __ldg(p.X + 3 * cd + 1);
-          zz[a] = __ldg(p.X + 3 * cd + 2);
-          ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
-          lv.w[a] = __ldg(src + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+        if (VAR) {
+          double zz[3];
+          int ok = 1;
+          // variable layers: the bottom and top levels of this cell column
+          // take the one-layer half that lies inside the column (the vertex
+          // column may extend beyond it)
+          const double *src = mx == 0 ? W + p.nf : (mx == lay ? W + 2 * p.nf : W);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], mx, lay);
+            const double xa = __ldg(p.X + 3 * cd + 0);
+            const double ya = __ldg(p.X + 3 * cd + 1);
+            zz[a] = __ldg(p.X + 3 * cd + 2);
+            ok &= same_bits(xa, ci.rx[a]) & same_bits(ya, ci.ry[a]);
+            lv.w[a] = __ldg(src + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+          }
+          ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
+                (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
+          lv.ok = ok;
+        } else {
+          // constant layers: (w, z) pairs; z equal at the three vertices and
+          // none of them marked as off its column's vertical
+          long long zb[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(W) +
+                                    dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], mx, lay));
+            lv.w[a] = v.x;
+            zb[a] = __double_as_longlong(v.y);
+          }
+          lv.ok = (zb[0] == zb[1]) & (zb[1] == zb[2]) & (zb[0] != kNotVertical);
         }
-        ok &= (__double_as_longlong(zz[0]) == __double_as_longlong(zz[1])) &
-              (__double_as_longlong(zz[1]) == __double_as_longlong(zz[2]));
-        lv.ok = ok;
       }
     };
 
@@ -609,13 +739,15 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
       const int nxt_ok0 = __shfl_sync(kFull, nxt.ok, 0);
       const bool step_ok = __all_sync(kFull, cur.ok) && carry_ok && nxt_ok0;
       if (step_ok) {
-        // value_a = alpha (w_a + w_0 + w_1 + w_2): one DMUL and five DFMA
-        const double aw = fma(ci.alpha, cur.w[0], fma(ci.alpha, cur.w[1], ci.alpha * cur.w[2]));
+        // alpha S = alpha (w_0 + w_1 + w_2): three DFMA; unfactored (variable
+        // layers, or few layers) value_a = alpha (w_a + S) (three DFMA more);
+        // factored, the vertex part alpha w_a is in A_a w_a already
+        const double aw = fma(ci.alpha, cur.w[0], fma(ci.alpha, cur.w[1], fmul(ci.alpha, cur.w[2], k1)));
         double val[3];
-  #pragma unroll
-        for (int a = 0; a < 3; ++a) val[a] = fma(ci.alpha, cur.w[a], aw);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) val[a] = FAC ? aw : fma(ci.alpha, cur.w[a], aw);
         if (valid) {
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < 3; ++a)
             atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, lay), val[a]);
         }
@@ -636,8 +768,9 @@ __global__ void __launch_bounds__(kWarps * 32, EXT_CELLS_MINB) k_mass_cells(cons
 
 // The deferred warp steps: every item of the step evaluates the two element
 // integrals touching its level with the 6-point rule and the general Jacobian.
-template <bool VAR>
-__global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch p, Deferred dfr, int cpw) {
+template <bool VAR, bool FAC>
+__global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch p, const double *__restrict__ W,
+                                                              Deferred dfr, int cpw, const double *__restrict__ alpha) {
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -647,7 +780,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
     const int64_t c0 = (int64_t)en.x * cpw;
     const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
     int my_items = 0;
-    if (lane < ncol) my_items = setup_column<VAR>(p, c0 + lane, cols[warp][lane]);
+    if (lane < ncol) my_items = setup_column<VAR, FAC>(p, c0 + lane, cols[warp][lane], alpha);
     __syncwarp();
     const int nitems = VAR ? __reduce_add_sync(kFull, my_items) : ncol * (p.layers + 1);
     const int it = en.y + lane;
@@ -670,6 +803,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
         prism_general_g(p.X, p.f, cd, fd, out);
         for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
       }
+      // factored form: the vertex pass added alpha_c w_a for this item too
+      if (FAC)
+        for (int a = 0; a < 3; ++a)
+          val[a] = fma(-ci.alpha,
+                       __ldg(reinterpret_cast<const double2 *>(W) + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], m, lay)).x,
+                       val[a]);
       for (int a = 0; a < 3; ++a) atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, lay), val[a]);
     }
     __syncwarp();
@@ -695,6 +834,9 @@ int resident_ctas(K kernel, int &cache) {
 // environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
 // (each cell evaluates its own vertical sums; no scratch; the same results up
 // to rounding); EXTMESH_MASS_FUSED=0 asks for the split form at any size.
+// With constant layers the split form is factored (area pass, vertex part in
+// the vertex pass) from EXT_FACTORED_MIN_LAYERS layers on;
+// EXTMESH_MASS_FACTORED=1 / 0 asks for it at any layer count / never.
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -705,8 +847,8 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   const int64_t blocks0 = (warps + kWarps - 1) / kWarps;
-  static int sms = 0, fused_env = -1;
-  static int res_cells[2] = {0, 0}, res_fused[2] = {0, 0};
+  static int sms = 0, fused_env = -1, fac_env = -1;
+  static int res_cells[3] = {0, 0, 0}, res_fused[2] = {0, 0};
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -715,20 +857,30 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (fused_env < 0) {  // 1: always the single pass; 0: always the split form; unset: by size
     const char *ev = getenv("EXTMESH_MASS_FUSED");
     fused_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
+    ev = getenv("EXTMESH_MASS_FACTORED");  // 1 / 0: factored split form always / never; unset: by layers
+    fac_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
   }
-  // The vertical sums and the list of deferred warp steps go to
-  // stream-ordered scratch, so launches on different streams never share it.
+  const bool factored = !var && (fac_env == 1 || (fac_env == 2 && p.layers >= EXT_FACTORED_MIN_LAYERS));
+  // The vertical sums, the vertex area sums A and the list of deferred warp
+  // steps go to stream-ordered scratch, so launches on different streams
+  // never share it.
   const int64_t n = p.nf;
   const double items = (var ? p.mean_layers + 1.0 : (double)(p.layers + 1)) * (double)p.ncells;
   const int64_t cap64 = (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
-  const size_t wbytes = (sizeof(double) * (size_t)(n > 0 ? n : 1) * (var ? 3 : 1) + 255) & ~(size_t)255;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const size_t wbytes = (sizeof(double) * nn * (var ? 3 : 2) + 255) & ~(size_t)255;
+  const size_t nverts = factored ? (size_t)(n / (p.layers + 1)) : 0;
+  // factored: A (per vertex) and alpha (per cell)
+  const size_t abytes = (sizeof(double) * nverts + 255) & ~(size_t)255;
+  const size_t cbytes = factored ? ((sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255) : 0;
   char *scr = nullptr;
-  // on a small launch the split form's extra pass, scratch allocation and
+  // on a small launch the split form's extra passes, scratch allocation and
   // launches (about 25 us together) cost more than they save
   const bool small = items < 1.0e6 && fused_env == 2;
   if (fused_env != 1 && !small &&
-      cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + sizeof(int2) * (size_t)cap, s) != cudaSuccess) {
+      cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + abytes + cbytes + sizeof(int2) * (size_t)cap, s) !=
+          cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;
   }
@@ -739,27 +891,40 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
     return cudaGetLastError();
   }
-  const int res = var ? resident_ctas(k_mass_cells<true>, res_cells[1]) : resident_ctas(k_mass_cells<false>, res_cells[0]);
+  const int res = var ? resident_ctas(k_mass_cells<true, false>, res_cells[1])
+                      : (factored ? resident_ctas(k_mass_cells<false, true>, res_cells[0])
+                                  : resident_ctas(k_mass_cells<false, false>, res_cells[2]));
   const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
   double *W = reinterpret_cast<double *>(scr);
+  double *A = reinterpret_cast<double *>(scr + wbytes + 256);
   Deferred dfr;
   dfr.count = reinterpret_cast<unsigned int *>(scr + wbytes);
-  dfr.list = reinterpret_cast<int2 *>(scr + wbytes + 256);
+  double *alpha = reinterpret_cast<double *>(scr + wbytes + 256 + abytes);
+  dfr.list = reinterpret_cast<int2 *>(scr + wbytes + 256 + abytes + cbytes);
   dfr.cap = cap;
-  cudaError_t e = cudaMemsetAsync(dfr.count, 0, sizeof(unsigned int), s);
+  // one memset clears the deferred-step counter and A
+  cudaError_t e = cudaMemsetAsync(scr + wbytes, 0, 256 + abytes, s);
   int64_t vb = (n + 255) / 256;
   if (vb > (int64_t)sms * 8) vb = (int64_t)sms * 8;
   if (vb < 1) vb = 1;
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
+  const Fp64Ones k1 = {1.0, -1.0, -0.0};
   if (e == cudaSuccess) {
     if (var) {
-      k_vsum<true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col);
-      k_mass_cells<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw);
-      k_mass_general<true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, cpw);
+      k_vsum<true, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, nullptr, k1, nullptr);
+      k_mass_cells<true, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
+      k_mass_general<true, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
+    } else if (factored) {
+      int64_t ab = (p.ncells + 255) / 256;
+      if (ab > (int64_t)sms * 8) ab = (int64_t)sms * 8;
+      k_area<<<(unsigned)ab, 256, 0, s>>>(p, A, alpha, col);
+      k_vsum<false, true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, A, p.b, k1, p.base_xy);
+      k_mass_cells<false, true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, alpha);
+      k_mass_general<false, true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, alpha);
     } else {
-      k_vsum<false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col);
-      k_mass_cells<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw);
-      k_mass_general<false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, cpw);
+      k_vsum<false, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, nullptr, k1, nullptr);
+      k_mass_cells<false, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
+      k_mass_general<false, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
     }
     e = cudaGetLastError();
   }

@@ -168,18 +168,64 @@ def test_mass_general_geometry_fallback():
     close(got, ref, absr)
 
 
-@pytest.mark.parametrize("form", ["0", "1"])
+@pytest.mark.parametrize("layers", [100, 7])
+@pytest.mark.parametrize("with_xy", [True, False])
+def test_mass_general_geometry_partial(layers, with_xy):
+    """Straight prisms except near a few vertex columns: some columns are
+    moved in x, y from a level upwards (from level 0: a vertical column off
+    the mesh's base coordinates), some have one level lifted in z, so warp
+    steps of the cell pass mix straight and general prisms, and deferred steps
+    must take back the vertex part the vertex pass added for them.  The mesh
+    has its base coordinates or not (the factored form then takes its
+    reference x, y from the field's level 0).  Over a million (column, level)
+    items at 100 layers: the factored split form."""
+    n = 72 if layers == 100 else 40
+    m = meshgen.tri_mesh(n, seed=45, order="rcm")
+    gm = E.Mesh(m.cells, m.xy if with_xy else None, layers, nverts=m.nverts)
+    csp, X = O.coords(m.cells, m.xy, layers)
+    osp = O.number(m.cells, m.nverts, layers, P1)
+    Xr = X.reshape(-1, 3).copy()
+    rng = np.random.default_rng(46)
+    L1 = layers + 1
+    lean = rng.choice(m.nverts, m.nverts // 40, replace=False)
+    # the CG1xCG1 column of vertex v is DoFs v * L1 .. v * L1 + layers (Algorithm 1)
+    for v in lean:
+        lv = int(rng.integers(0, layers + 1))
+        Xr[v * L1 + lv:v * L1 + L1, 0] += 0.1 / n
+        Xr[v * L1 + lv:v * L1 + L1, 1] -= 0.05 / n
+    lift = rng.choice(np.setdiff1d(np.arange(m.nverts), lean), m.nverts // 40, replace=False)
+    for v in lift:
+        lv = int(rng.integers(0, L1))
+        Xr[v * L1 + lv, 2] += 0.3 / layers
+    X = Xr.reshape(-1)
+    f = meshgen.uniform_field(osp.ndofs, 47)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.par_loop(O.K_MASS, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    ps = E.Space(gm, "CG1xCG1")
+    b = ps.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, to_dev(X), E.EXT_READ), (ps, to_dev(f), E.EXT_READ), (ps, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(host(b), ref, absr)
+
+
+@pytest.mark.parametrize("form", [{"EXTMESH_MASS_FUSED": "0"}, {"EXTMESH_MASS_FUSED": "1"},
+                                  {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_FACTORED": "0"},
+                                  {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_FACTORED": "1"}],
+                         ids=["split", "single", "split-unfactored", "split-factored"])
 def test_mass_forced_form(form):
-    """Both forms of the P1xP1 launch pass the same parity tests: the split
+    """Every form of the P1xP1 launch passes the same parity tests: the split
     form (vertical sums, then the cell pass; the default for launches of a
-    million items or more) and the single-pass kernel (the default below, and
-    the fallback when the split form's scratch cannot be allocated), each
-    forced by EXTMESH_MASS_FUSED in a child process."""
+    million items or more), factored (vertex part A_a w_a in the vertex pass;
+    the default from two constant layers) or not, and the single-pass kernel
+    (the default below a million items, and the fallback when the split form's
+    scratch cannot be allocated), each forced by EXTMESH_MASS_FUSED and
+    EXTMESH_MASS_FACTORED in a child process."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, EXTMESH_MASS_FUSED=form)
+    env = dict(os.environ, **form)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(root, "tests", "test_gpu_parity.py"),
                         os.path.join(root, "tests", "test_gpu_var_facets.py"), "-k",
@@ -365,6 +411,15 @@ def test_argument_validation():
         E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (dg, dg.zeros(), E.EXT_READ), (ps, b, E.EXT_INC))
     with pytest.raises(E.ExtError, match="unknown kernel"):
         E.ext_par_loop(gm.handle, 99, [])
+    # an INC output may not overlap an input, wholly or in part
+    with pytest.raises(E.ExtError, match="overlaps"):
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (ps, b, E.EXT_READ), (ps, b, E.EXT_INC))
+    buf = torch.zeros(2 * ps.ndofs, dtype=torch.float64, device=dev)
+    with pytest.raises(E.ExtError, match="overlaps"):
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (ps, buf[:ps.ndofs], E.EXT_READ),
+                   (ps, buf[ps.ndofs // 2:ps.ndofs // 2 + ps.ndofs], E.EXT_INC))
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, X, E.EXT_READ), (ps, buf[:ps.ndofs], E.EXT_READ),
+               (ps, buf[ps.ndofs:], E.EXT_INC))  # adjacent, not overlapping
     other = E.Mesh(m.cells, m.xy, 3)
     os_ = E.Space(other, "CG1xCG1")
     with pytest.raises(E.ExtError, match="another mesh"):
