@@ -248,14 +248,13 @@ def run_ours(args, rank, world, local):
     vb_paper = valuable_bytes_cfg2(V, C, L, maps=False)
     READ, WRITE, INC = E.EXT_READ, E.EXT_WRITE, E.EXT_INC
     h = {"gm": gm.handle}
-    a_rhs = [(cs.handle, X, READ), (p1.handle, f, READ), (p1.handle, b, INC)]
-    a_mass = [(cs.handle, X, READ), (p1.handle, x, READ), (p1.handle, y, INC)]
+    # WRITE: the P1xP1 loops overwrite b and y with the assembled results
+    a_rhs = [(cs.handle, X, READ), (p1.handle, f, READ), (p1.handle, b, WRITE)]
+    a_mass = [(cs.handle, X, READ), (p1.handle, x, READ), (p1.handle, y, WRITE)]
     a_int = [(p1.handle, x, READ), (dg.handle, out, WRITE)]
     s = stream.cuda_stream
 
     def step(ev=None):
-        b.zero_()
-        y.zero_()
         if ev is not None:
             ev[0].record(stream)
         E.ext_par_loop(h["gm"], E.EXT_K_RHS_P1P1, a_rhs, s)
@@ -324,8 +323,8 @@ def e2e_time(args, world, dev, gm, cs, p1, dg, X, f, x):
         d = {"X": torch.empty_like(X), "f": torch.empty_like(f), "x": torch.empty_like(x),
              "b": p1.zeros(), "y": p1.zeros(), "out": dg.zeros()}
         R, W, I = E.EXT_READ, E.EXT_WRITE, E.EXT_INC
-        d["rhs"] = [(cs.handle, d["X"], R), (p1.handle, d["f"], R), (p1.handle, d["b"], I)]
-        d["mass"] = [(cs.handle, d["X"], R), (p1.handle, d["x"], R), (p1.handle, d["y"], I)]
+        d["rhs"] = [(cs.handle, d["X"], R), (p1.handle, d["f"], R), (p1.handle, d["b"], W)]
+        d["mass"] = [(cs.handle, d["X"], R), (p1.handle, d["x"], R), (p1.handle, d["y"], W)]
         d["int"] = [(p1.handle, d["x"], R), (dg.handle, d["out"], W)]
         sets.append(d)
     s_in, s_cmp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
@@ -345,8 +344,6 @@ def e2e_time(args, world, dev, gm, cs, p1, dg, X, f, x):
             s_cmp.wait_event(in_done[k])
             s_cmp.wait_event(out_done[k])         # step i-2's outputs have been read back
             with torch.cuda.stream(s_cmp):
-                d["b"].zero_()
-                d["y"].zero_()
                 E.ext_par_loop(gm.handle, E.EXT_K_INTERP_DG1, d["int"], s_cmp.cuda_stream)
                 int_done[k].record(s_cmp)
                 E.ext_par_loop(gm.handle, E.EXT_K_RHS_P1P1, d["rhs"], s_cmp.cuda_stream)

@@ -73,8 +73,10 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   of the unit-height column over every base vertex (Sec. 4.1.1).
  * EXT_K_COPY_DG     [in READ, out WRITE], one space with DoFs only on cells
  *                   (delta(2,1) > 0, all other deltas 0): out = in.
- * EXT_K_RHS_P1P1    [coords READ, f READ, b INC] on prisms, all CG1xCG1:
- *                   b_i += int_cell f_h phi_i dx  (the residual I_1, Sec. 4.1.1).
+ * EXT_K_RHS_P1P1    [coords READ, f READ, b INC|WRITE] on prisms, all CG1xCG1:
+ *                   b_i += int_cell f_h phi_i dx  (the residual I_1, Sec. 4.1.1);
+ *                   with WRITE, b is overwritten with the assembled result
+ *                   (every DoF set, no zeroing needed beforehand).
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
  *                   Both run as four kernels on two or more constant
  *                   layers: the area factor of every cell summed per vertex,

@@ -656,7 +656,8 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
       EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
       EXT_CHECK(check_arg(mesh, args, 1, kn, ELEM_P1P1, 1, EXT_READ));
-      EXT_CHECK(check_arg(mesh, args, 2, kn, ELEM_P1P1, 1, EXT_INC));
+      // INC adds M f into b; WRITE overwrites b with M f
+      EXT_CHECK(check_arg(mesh, args, 2, kn, ELEM_P1P1, 1, args[2].access == EXT_WRITE ? EXT_WRITE : EXT_INC));
       MassP1Launch p;
       p.ncells = C;
       p.layers = L;
@@ -676,6 +677,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.mean_layers = mesh->mean_layers;
       p.nf = args[1].space->ndofs;
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
+      p.overwrite = args[2].access == EXT_WRITE;
       e = launch_mass_p1(p, s);
       break;
     }

@@ -171,6 +171,7 @@ struct MassP1Launch {
   double mean_layers = 0.0;
   int64_t nf = 0;  // DoFs of the f space (CG1xCG1 numbering shared with the coordinates)
   const double *base_xy = nullptr;  // the mesh's base coordinates (nverts x 2), if it has them
+  bool overwrite = false;           // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 

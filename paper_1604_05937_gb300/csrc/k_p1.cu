@@ -416,9 +416,10 @@ __device__ __forceinline__ double fsub(double a, double b, const Fp64Ones &k) { 
 // is a contiguous run, so level m's neighbours are DoFs d - 1 and d + 1).
 // Constant layers (`col` = layers + 1, level m = d mod col, the ends have one
 // layer): W holds n pairs (w, z or kNotVertical), and in the factored form
-// (FAC) b[d] += A[d / col] w.  VAR: the ends of vertex columns are
-// never read; W holds 3n values: w, the upper half |h_hi| (2 f + f_hi) and
-// the lower half |h_lo| (f_lo + 2 f); A and b are unused.
+// (FAC) b[d] += A[d / col] w (b[d] = A[d / col] w with `overwrite`).  VAR:
+// the ends of vertex columns are never read; W holds 3n values: w, the upper
+// half |h_hi| (2 f + f_hi) and the lower half |h_lo| (f_lo + 2 f); A is
+// unused.  Without FAC, `overwrite` clears b for the cell pass.
 #ifndef EXT_VSUM_MINB
 #define EXT_VSUM_MINB 4  // resident 256-thread CTAs per SM the vertex pass's registers must allow
 #endif
@@ -430,7 +431,7 @@ template <bool VAR, bool FAC>
 __global__ void __launch_bounds__(256, EXT_VSUM_MINB) k_vsum(const double *__restrict__ X, const double *__restrict__ f,
                                               double *__restrict__ W, int64_t n, FastDiv col,
                                               const double *__restrict__ A, double *__restrict__ b, Fp64Ones k1,
-                                              const double *__restrict__ ref_xy) {
+                                              const double *__restrict__ ref_xy, bool overwrite) {
   // A warp takes VU consecutive 32-DoF chunks per step and issues all their
   // loads before any arithmetic (the loop is latency-bound otherwise); the
   // neighbours across chunk edges come from the adjacent chunk's lanes.
@@ -465,7 +466,8 @@ __global__ void __launch_bounds__(256, EXT_VSUM_MINB) k_vsum(const double *__res
                    (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(r + 1)));
           if (FAC) {
             Ac[u] = __ldg(A + q);
-            bc[u] = b[d];
+            // b = A w + b, or with overwrite A w + (-0), which is A w exactly
+            bc[u] = overwrite ? -0.0 : b[d];
           }
         }
       }
@@ -534,6 +536,8 @@ __global__ void __launch_bounds__(256, EXT_VSUM_MINB) k_vsum(const double *__res
       const long long kl = lo_end ? 0LL : -1LL, kh = hi_end ? 0LL : -1LL;
       const double al = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fl[u])) & kl);
       const double bh = __longlong_as_double(__double_as_longlong(fma(2.0, fc[u], fr)) & kh);
+      // overwrite without the factored form: clear b before the cell pass adds
+      if (!FAC && overwrite && d < n) b[d] = 0.0;
       if (VAR) {
         // variable layers: also the one-layer halves, which the bottom (upper
         // half) and top (lower half) levels of a cell column use
@@ -887,6 +891,10 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (!scr) {
     const int res = var ? resident_ctas(k_mass_p1<true>, res_fused[1]) : resident_ctas(k_mass_p1<false>, res_fused[0]);
     const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
+    if (p.overwrite) {  // the single pass only adds: clear b first
+      const cudaError_t ez = cudaMemsetAsync(p.b, 0, sizeof(double) * (size_t)(p.nf > 0 ? p.nf : 0), s);
+      if (ez != cudaSuccess) return ez;
+    }
     if (var) k_mass_p1<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
     else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
     return cudaGetLastError();
@@ -911,18 +919,18 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const Fp64Ones k1 = {1.0, -1.0, -0.0};
   if (e == cudaSuccess) {
     if (var) {
-      k_vsum<true, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, nullptr, k1, nullptr);
+      k_vsum<true, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, p.b, k1, nullptr, p.overwrite);
       k_mass_cells<true, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
       k_mass_general<true, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
     } else if (factored) {
       int64_t ab = (p.ncells + 255) / 256;
       if (ab > (int64_t)sms * 8) ab = (int64_t)sms * 8;
       k_area<<<(unsigned)ab, 256, 0, s>>>(p, A, alpha, col);
-      k_vsum<false, true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, A, p.b, k1, p.base_xy);
+      k_vsum<false, true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, A, p.b, k1, p.base_xy, p.overwrite);
       k_mass_cells<false, true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, alpha);
       k_mass_general<false, true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, alpha);
     } else {
-      k_vsum<false, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, nullptr, k1, nullptr);
+      k_vsum<false, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, p.b, k1, nullptr, p.overwrite);
       k_mass_cells<false, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
       k_mass_general<false, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
     }

@@ -153,6 +153,43 @@ def test_mass_action_parity(n, layers, order):
     close(got, ref, absr)
 
 
+@pytest.mark.parametrize("n,layers,var", [(9, 3, False), (12, 1, False), (23, 32, False), (72, 100, False),
+                                          (11, 9, True), (72, 100, True)])
+def test_mass_action_parity_write(n, layers, var):
+    """WRITE access overwrites the output with the assembled result: the
+    output starts as NaN, every DoF must come out equal to the oracle's sum
+    (constant and variable layers; the last cases are over a million items,
+    so the split forms run)."""
+    m = meshgen.tri_mesh(n, seed=310 + n, order="rcm")
+    if var:
+        first, lay = meshgen.column_layers(m, layers, 311, "bathymetry")
+        gm = E.Mesh(m.cells, m.xy, cell_first=first, cell_layers=lay)
+        csp, X = O.coords_var(m.cells, m.xy, first, lay)
+        osp = O.number_var(m.cells, m.nverts, first, lay, P1)
+        kw = dict(cell_first=first, cell_layers=lay)
+    else:
+        gm = E.Mesh(m.cells, m.xy, layers)
+        csp, X = O.coords(m.cells, m.xy, layers)
+        osp = O.number(m.cells, m.nverts, layers, P1)
+        kw = {}
+    f = meshgen.uniform_field(osp.ndofs, 312)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.par_loop(O.K_MASS, m.cells, csp.layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ),
+                                               (osp, ref, 1, O.INC, absr)], **kw)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    ps = E.Space(gm, "CG1xCG1")
+    b = torch.full((ps.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, to_dev(X), E.EXT_READ), (ps, to_dev(f), E.EXT_READ), (ps, b, E.EXT_WRITE))
+    E.ext_sync_check()
+    got = host(b)
+    assert np.isfinite(got).all()
+    close(got, ref, absr)
+    # a second WRITE gives the same values, a following INC doubles them
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, to_dev(X), E.EXT_READ), (ps, to_dev(f), E.EXT_READ), (ps, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(host(b), 2 * ref, 2 * absr)
+
+
 def test_rhs_sin_cos_z_parity():
     m = meshgen.tri_mesh(30, seed=1604, order="rcm")  # the 1,800-triangle, 10-layer case
     f = lambda X: np.sin(X[:, 0]) * np.cos(X[:, 1]) * X[:, 2]
