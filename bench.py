@@ -57,12 +57,19 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 # their products and sums as DFMA (a b + (-0), a (+-1) + b).  All send 3 FP64
 # atomic adds per item to L2.  Evaluating each cell's element matrix by itself
 # instead needs 18 FP64 operations per item.
+# Gather form (constant layers, mesh with base coordinates; the default):
+#   w = |h_lo| f_lo + 2 (|h_lo| + |h_hi|) f + |h_hi| f_hi   3 DFMA per DoF,
+#   b_{a,m} = sum over the vertex row of a of weight x w   1 DFMA per row entry and level,
+# with V + 2E row entries (each vertex and each of its neighbours), four
+# kernels (level table, vertex pass, gather, the pass over recorded DoFs,
+# which finds none on a straight mesh), no atomics.
+GATHER_OPS_PER_DOF = 3
 P1_MIX = {  # (dadd, dmul, dfma) per DoF, per item, per cell
     "factored": ((0, 0, 6), (0, 0, 3), (4, 2, 1)),
     "plain": ((0, 0, 5), (0, 0, 6), (0, 0, 0)),
     "var": ((0, 0, 6), (0, 0, 6), (0, 0, 0)),
 }
-P1_KERNELS = {"factored": 4, "plain": 3, "var": 3, "single": 1}
+P1_KERNELS = {"gather": 4, "factored": 4, "plain": 3, "var": 3, "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 CELLWISE_OPS_PER_ITEM = 18
 SINGLE_PASS_SM_OPS_PER_ITEM = 13
@@ -71,41 +78,64 @@ P1_FACTORED_MIN_LAYERS = 2
 
 
 def p1_form(items: int, layers: int, var: bool = False) -> str:
-    """The form the library picks for a P1xP1 launch (EXTMESH_MASS_FUSED and
+    """The form the library picks for a P1xP1 launch on a mesh with base
+    coordinates (EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and
     EXTMESH_MASS_FACTORED override its choice as they do the library's)."""
     fused, fac = os.environ.get("EXTMESH_MASS_FUSED", ""), os.environ.get("EXTMESH_MASS_FACTORED", "")
     if fused == "1" or (fused != "0" and items < P1_SPLIT_MIN_ITEMS):
         return "single"
     if var:
         return "var"
+    if os.environ.get("EXTMESH_MASS_GATHER", "") != "0":
+        return "gather"
     if fac in ("0", "1"):
         return "factored" if fac == "1" else "plain"
     return "factored" if layers >= P1_FACTORED_MIN_LAYERS else "plain"
 
 
-def p1_counts(ndofs: int, items: int, ncells: int, layers: int, var: bool = False) -> tuple:
+def euler_edges(nverts: int, ncells: int) -> int:
+    """Edges of a triangulated disc (Euler: V - E + F = 1), as the unit-square
+    meshes here are."""
+    return nverts + ncells - 1
+
+
+def p1_counts(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None) -> tuple:
     """(DADD, DMUL, DFMA) of one P1xP1 RHS / mass-action launch; the single-pass
     kernel below a million items executes 13 operations per item on the SM
     (3 DMUL, 6 DFMA, 4 for the layer factors counted as DFMA; the horizontal
-    sum in L2 atomics)."""
+    sum in L2 atomics).  The gather form needs the base edge count (default:
+    Euler's formula)."""
     form = p1_form(items, layers, var)
     if form == "single":
         return (0, 3 * items, 10 * items)
+    if form == "gather":
+        nv = ndofs // (layers + 1)
+        ne = euler_edges(nv, ncells) if nedges is None else nedges
+        return (0, 0, GATHER_OPS_PER_DOF * ndofs + (nv + 2 * ne) * (layers + 1))
     per = P1_MIX[form]
     return tuple(per[0][k] * ndofs + per[1][k] * items + per[2][k] * ncells for k in range(3))
 
 
-def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False) -> int:
-    return sum(p1_counts(ndofs, items, ncells, layers, var))
+def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None) -> int:
+    return sum(p1_counts(ndofs, items, ncells, layers, var, nedges))
+
+
+def base_edges(cells) -> int:
+    """Distinct edges of a base triangulation (C x 3 vertex ids)."""
+    c = np.asarray(cells, dtype=np.int64)
+    e = np.concatenate([c[:, [0, 1]], c[:, [1, 2]], c[:, [2, 0]]])
+    e.sort(axis=1)
+    return int(np.unique(e[:, 0] * (int(c.max()) + 1) + e[:, 1]).size) if c.size else 0
 
 
 def p1_kernels(items: int, layers: int, var: bool = False) -> int:
     return P1_KERNELS[p1_form(items, layers, var)]
 
 
-def p1_mix_ceiling(ndofs: int, items: int, ncells: int, layers: int, rates: dict, var: bool = False) -> float:
+def p1_mix_ceiling(ndofs: int, items: int, ncells: int, layers: int, rates: dict, var: bool = False,
+                   nedges: int | None = None) -> float:
     """G op/s ceiling of that operation mix at the measured DFMA/DADD/DMUL rates."""
-    dadd, dmul, dfma = p1_counts(ndofs, items, ncells, layers, var)
+    dadd, dmul, dfma = p1_counts(ndofs, items, ncells, layers, var, nedges)
     return (dfma + dadd + dmul) / (dfma / rates["dfma"] + dadd / rates["dadd"] + dmul / rates["dmul"])
 
 
@@ -389,11 +419,30 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     ndofs = V * (L + 1)
     mass_ms = statistics.mean(k_rhs + k_mass)
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
-    ops = p1_ops(ndofs, items, C, L)
+    E_ = base_edges(m.cells)
+    form = p1_form(items, L)
+    ops = p1_ops(ndofs, items, C, L, nedges=E_)
     achieved_ops = ops / (mass_ms * 1e-3) / 1e9
     traffic = load_traffic("p1_mass_launch")
-    mix_peak = p1_mix_ceiling(ndofs, items, C, L, rates)
-    l2_adds = CELL_ATOMICS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9
+    mix_peak = p1_mix_ceiling(ndofs, items, C, L, rates, nedges=E_)
+    l2_adds = (CELL_ATOMICS_PER_ITEM if form != "gather" else 0) * items / (mass_ms * 1e-3) / 1e9
+    if form == "gather":
+        algorithmic = (f"{GATHER_OPS_PER_DOF} FP64 ops per DoF x {ndofs} DoFs (column mass matrix) + 1 per "
+                       f"vertex-row entry and level x {V + 2 * E_} entries x {L + 1} levels (base mass matrix) "
+                       f"= {ops} per launch")
+        kname = "P1xP1 RHS / mass-action launch (k_levels + k_vsum_tab + k_vgather + k_vgather_general)"
+        note = ("on straight prisms with flat levels M = Mh (x) Mv: the column mass matrix Mv is applied once "
+                "per vertex level (3 FP64 ops), then the base mass matrix Mh row by row per level (one FP64 op "
+                "per row entry, no atomics); evaluated cell by cell the same work is 18 FP64 ops per "
+                "(column, level) item (cellwise_equivalent_gops)")
+    else:
+        per = P1_MIX[form]
+        algorithmic = (f"{sum(per[0])} FP64 ops per DoF x {ndofs} DoFs + {sum(per[1])} per (column, level) item "
+                       f"x {items} items + {sum(per[2])} per cell x {C} cells = {ops} per launch")
+        kname = "P1xP1 RHS / mass-action launch (k_area + k_vsum + k_mass_cells + k_mass_general)"
+        note = ("the split form computes each vertex column's vertical sums once instead of once per cell around "
+                "the vertex, and adds the vertex part alpha_c w_a of all cells around a vertex as one product "
+                "A_a w_a; evaluated cell by cell the same work is 18 FP64 ops per item (cellwise_equivalent_gops)")
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -412,24 +461,20 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                         "interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6, 1)},
         "hbm_frac": {"interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6 / hbm, 4),
                      "step": round(value / world / hbm, 4), "peak_gbs": hbm, "peak_kind": hbm_kind},
-        "roofline": {"kernel": "P1xP1 RHS / mass-action launch (k_area + k_vsum + k_mass_cells + k_mass_general)",
+        "roofline": {"kernel": kname, "form": form,
                      "bound": "alu",
                      "achieved": round(achieved_ops, 2), "peak": round(ops_peak, 2), "unit": "G FP64 ops/s",
                      "frac": round(achieved_ops / ops_peak, 4), "traffic": traffic,
-                     "algorithmic": f"{sum(P1_MIX['factored'][0])} FP64 ops per DoF x {ndofs} DoFs + "
-                                    f"{sum(P1_MIX['factored'][1])} per (column, level) item x {items} items + "
-                                    f"{sum(P1_MIX['factored'][2])} per cell x {C} cells = {ops} per launch",
+                     "algorithmic": algorithmic,
                      "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
                      "mix_ceiling_gops": round(mix_peak, 1),
                      "frac_of_mix_ceiling": round(achieved_ops / mix_peak, 4),
-                     "l2_atomic_adds": {"per_item": CELL_ATOMICS_PER_ITEM, "g_per_s": round(l2_adds, 1),
+                     "l2_atomic_adds": {"per_item": CELL_ATOMICS_PER_ITEM if form != "gather" else 0,
+                                        "g_per_s": round(l2_adds, 1),
                                         "frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
                      "cellwise_equivalent_gops": round(CELLWISE_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9, 1),
-                     "note": "the split form computes each vertex column's vertical sums once instead of once "
-                             "per cell around the vertex, and adds the vertex part alpha_c w_a of all cells "
-                             "around a vertex as one product A_a w_a; evaluated cell by cell the same work is "
-                             "18 FP64 ops per item (cellwise_equivalent_gops)"},
+                     "note": note},
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},

@@ -78,29 +78,43 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   with WRITE, b is overwritten with the assembled result
  *                   (every DoF set, no zeroing needed beforehand).
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
- *                   Both run as four kernels on two or more constant
- *                   layers: the area factor of every cell summed per vertex,
- *                   vertical sums of the input per vertex level (which also
- *                   add each vertex's share of its own sums), the cell pass,
- *                   and a pass over the warp steps that met a prism which is
- *                   not straight (6-point rule, general Jacobian); three with
- *                   one or variable layers (no area pass; the cell pass adds
- *                   each vertex's share).  The sums, the area factors and that
- *                   list live in scratch taken from the device's default
- *                   stream-ordered pool (cudaMallocAsync / cudaFreeAsync on
- *                   `stream`: 16 bytes per DoF of f plus 8 per vertex, 24 per
- *                   DoF on a mesh with variable layers, plus at most 1 byte per
- *                   item), so launches on different
- *                   streams never share it and the launch can be captured in a
- *                   CUDA graph.  If the pool cannot supply it, or the launch
- *                   has fewer than a million (column, level) items, a
- *                   single-pass kernel that needs no scratch (every cell forms
- *                   its own vertical sums) runs instead.  The environment
- *                   variables EXTMESH_MASS_FUSED and EXTMESH_MASS_FACTORED,
- *                   read once per process, select the single pass (1) or the
- *                   split form (0) at any size, and the split form with (1)
- *                   or without (0) the area pass at any constant layer count.
- *                   Coordinates must be finite.
+ *                   On a mesh with base coordinates and constant layers both
+ *                   run in the gather form, four kernels: a table of the
+ *                   level heights (from the column of vertex 0), the column
+ *                   mass matrix applied per vertex level (w = Mv f), the base
+ *                   triangulation's P1 mass matrix applied per level as vertex
+ *                   rows built by ext_mesh_create (b = Mh w; every DoF of b is
+ *                   written by one thread, in a fixed order, so the result is
+ *                   the same bit for bit from launch to launch), and a pass
+ *                   over the DoFs whose stencil holds a prism that is not
+ *                   straight with flat levels, or a NaN (6-point rule, general
+ *                   Jacobian, both layers of every cell around the vertex).
+ *                   Otherwise (no base coordinates, or variable layers): four
+ *                   kernels on two or more constant layers (the area factor
+ *                   of every cell summed per vertex, vertical sums of the
+ *                   input per vertex level which also add each vertex's share
+ *                   of its own sums, the cell pass with FP64 atomic adds, and
+ *                   a pass over the warp steps that met a prism which is not
+ *                   straight), three with one or variable layers (no area
+ *                   pass; the cell pass adds each vertex's share).  The
+ *                   vertical sums, the level table, the area factors and the
+ *                   list of recorded steps live in scratch taken from the
+ *                   device's default stream-ordered pool (cudaMallocAsync /
+ *                   cudaFreeAsync on `stream`: 8 bytes per DoF of f in the
+ *                   gather form, 16 per DoF plus 8 per vertex in the factored
+ *                   one, 24 per DoF on a mesh with variable layers, plus at
+ *                   most 1 byte per item), so launches on different streams
+ *                   never share it and the launch can be captured in a CUDA
+ *                   graph.  If the pool cannot supply it, or the launch has
+ *                   fewer than a million (column, level) items, a single-pass
+ *                   kernel that needs no scratch (every cell forms its own
+ *                   vertical sums) runs instead.  The environment variables
+ *                   EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and
+ *                   EXTMESH_MASS_FACTORED, read once per process, select the
+ *                   single pass (1) or the split forms (0) at any size, turn
+ *                   the gather form off (0), and select the factored split
+ *                   form with (1) or without (0) the area pass at any
+ *                   constant layer count.  Coordinates must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
  *                   interpolation, out at DG1 node (vertex a, level b) = x there.
  * EXT_K_U2V_FWD     [coords READ, u READ, F INC|WRITE]: F_i += int u_h^2 phi_i dx,
@@ -193,7 +207,12 @@ const char *ext_last_error(void);
  *                   EXT_K_EXTRUDE is unavailable and orientation is unchecked)
  * Edges are numbered by first appearance when scanning cells in order with
  * local edge k = (vertex k, vertex k+1 mod kind).  The topology is copied to
- * the device (synchronously).  Errors: EXT_EINVAL (ids out of range, repeated
+ * the device (synchronously).  A triangle mesh with base coordinates also
+ * gets, on the device, the rows of its base P1 mass matrix per vertex (the
+ * vertex itself and its neighbours, weighted by |2A|/144 of the cells on each
+ * edge, 16 bytes per entry, about 7 entries per vertex) and the cells around
+ * every vertex, which the P1xP1 loops' gather form reads.  Errors: EXT_EINVAL
+ * (ids out of range, repeated
  * vertex in a cell, clockwise or degenerate cell, layers < 1), EXT_EOVERFLOW,
  * EXT_ENOMEM, EXT_ECUDA. */
 ext_status ext_mesh_create(int32_t kind, int64_t nverts, int64_t ncells,

@@ -2,6 +2,7 @@
 // base-mesh entity derivation, space numbering set-up, par_loop dispatch and
 // the batched plan (autotuning, colouring, CUDA-graph capture).
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -87,6 +88,70 @@ static int64_t derive_edges(int kind, int64_t ncells, const int32_t *cv, std::ve
   return (int64_t)first.size();
 }
 
+// Vertex rows of the P1 mass matrix of a triangulation (for the P1xP1
+// gather form): with alpha_c = |2 A_c| / 144, the weight of neighbour j in
+// row a is the sum of alpha_c over the cells holding edge (a, j), and the
+// diagonal weight is the sum of the row's neighbour weights (twice the sum
+// of alpha_c around a).  Rows list a itself first, then its neighbours in
+// ascending order; neighbour weights are summed in ascending cell order.
+// Also the cells around every vertex, ascending.  Returns false (rows not
+// built) when the entry count does not fit int32.
+static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const double *xy,
+                              std::vector<int32_t> &vrow, std::vector<double2> &vent,
+                              std::vector<int32_t> &vcrow, std::vector<int32_t> &vcells) {
+  std::vector<double> alpha((size_t)nc);
+  vcrow.assign((size_t)nv + 1, 0);
+  for (int64_t c = 0; c < nc; ++c) {
+    const int32_t *t = cv + 3 * c;
+    const double x0 = xy[2 * (int64_t)t[0]], y0 = xy[2 * (int64_t)t[0] + 1];
+    const double x1 = xy[2 * (int64_t)t[1]], y1 = xy[2 * (int64_t)t[1] + 1];
+    const double x2 = xy[2 * (int64_t)t[2]], y2 = xy[2 * (int64_t)t[2] + 1];
+    alpha[(size_t)c] = std::fabs((x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0)) * (1.0 / 144.0);
+    for (int a = 0; a < 3; ++a) ++vcrow[(size_t)t[a] + 1];
+  }
+  for (int64_t v = 0; v < nv; ++v) vcrow[(size_t)v + 1] += vcrow[(size_t)v];
+  vcells.assign((size_t)(3 * nc), 0);
+  {
+    std::vector<int32_t> cur(vcrow.begin(), vcrow.end() - 1);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int a = 0; a < 3; ++a) vcells[(size_t)cur[(size_t)cv[3 * c + a]]++] = (int32_t)c;
+  }
+  vrow.assign((size_t)nv + 1, 0);
+  vent.clear();
+  vent.reserve((size_t)(nv + 6 * nc));
+  std::vector<std::pair<int32_t, double>> nb;
+  auto entry = [](double w, int32_t j) {
+    double2 en;
+    en.x = w;
+    const long long bits = (long long)(uint32_t)j;
+    std::memcpy(&en.y, &bits, sizeof bits);
+    return en;
+  };
+  for (int64_t a = 0; a < nv; ++a) {
+    nb.clear();
+    for (int32_t t = vcrow[(size_t)a]; t < vcrow[(size_t)a + 1]; ++t) {
+      const int64_t c = vcells[(size_t)t];
+      for (int k = 0; k < 3; ++k)
+        if (cv[3 * c + k] != a) nb.push_back({cv[3 * c + k], alpha[(size_t)c]});
+    }
+    std::stable_sort(nb.begin(), nb.end(),
+                     [](const std::pair<int32_t, double> &l, const std::pair<int32_t, double> &r) { return l.first < r.first; });
+    size_t w = 0;
+    for (size_t i = 0; i < nb.size(); ++i) {
+      if (w > 0 && nb[w - 1].first == nb[i].first) nb[w - 1].second += nb[i].second;
+      else nb[w++] = nb[i];
+    }
+    nb.resize(w);
+    double diag = 0.0;
+    for (const auto &q : nb) diag += q.second;
+    vent.push_back(entry(diag, (int32_t)a));
+    for (const auto &q : nb) vent.push_back(entry(q.second, q.first));
+    if (vent.size() >= (size_t)INT32_MAX) return false;
+    vrow[(size_t)a + 1] = (int32_t)vent.size();
+  }
+  return true;
+}
+
 static void free_mesh(ext_mesh *m) {
   if (!m) return;
   cudaFree(m->d_cell_verts);
@@ -96,6 +161,10 @@ static void free_mesh(ext_mesh *m) {
   cudaFree(m->d_cell_layers);
   cudaFree(m->d_ent_lo);
   cudaFree(m->d_ent_hi);
+  cudaFree(m->d_vrow);
+  cudaFree(m->d_vent);
+  cudaFree(m->d_vcrow);
+  cudaFree(m->d_vcells);
   delete reinterpret_cast<ext_mesh_host *>(m->host);
   delete m;
 }
@@ -182,6 +251,20 @@ static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, cons
       e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->has_xy = base_xy_host != nullptr;
+  if (e == cudaSuccess && kind == EXT_TRI && base_xy_host && !var && nverts > 0 && ncells > 0) {
+    std::vector<int32_t> vrow, vcrow, vcells;
+    std::vector<double2> vent;
+    if (build_vertex_rows(nverts, ncells, cell_verts_host, base_xy_host, vrow, vent, vcrow, vcells)) {
+      const size_t rb = sizeof(int32_t) * vrow.size(), eb = sizeof(double2) * vent.size();
+      const size_t cb = sizeof(int32_t) * vcells.size();
+      if ((e = cudaMalloc(&m->d_vrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vent, eb)) == cudaSuccess &&
+          (e = cudaMalloc(&m->d_vcrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vcells, cb)) == cudaSuccess &&
+          (e = cudaMemcpy(m->d_vrow, vrow.data(), rb, cudaMemcpyHostToDevice)) == cudaSuccess &&
+          (e = cudaMemcpy(m->d_vent, vent.data(), eb, cudaMemcpyHostToDevice)) == cudaSuccess &&
+          (e = cudaMemcpy(m->d_vcrow, vcrow.data(), rb, cudaMemcpyHostToDevice)) == cudaSuccess)
+        e = cudaMemcpy(m->d_vcells, vcells.data(), cb, cudaMemcpyHostToDevice);
+    }
+  }
   if (e == cudaSuccess && var) {
     m->var = true;
     m->mean_layers = mean;
@@ -678,6 +761,10 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.nf = args[1].space->ndofs;
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
       p.overwrite = args[2].access == EXT_WRITE;
+      p.vrow = mesh->d_vrow;
+      p.vent = mesh->d_vent;
+      p.vcrow = mesh->d_vcrow;
+      p.vcells = mesh->d_vcells;
       e = launch_mass_p1(p, s);
       break;
     }

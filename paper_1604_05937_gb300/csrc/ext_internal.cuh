@@ -44,6 +44,15 @@ struct ext_mesh {
   int32_t *d_ent_hi = nullptr;       // dimension-major (vertices, edges, cells)
   double mean_layers = 0.0;
   void *host = nullptr;             // host-side copies (ext_api.cu)
+  // triangle meshes with base coordinates and constant layers: the P1 mass
+  // matrix of the base triangulation as vertex rows (row a: a itself, then
+  // its neighbours in ascending order; entry (weight, vertex) with the
+  // vertex in the low 32 bits of the second double) and the cells around
+  // every vertex in ascending order (the P1xP1 gather form)
+  int32_t *d_vrow = nullptr;    // nverts + 1
+  double2 *d_vent = nullptr;    // d_vrow[nverts] entries
+  int32_t *d_vcrow = nullptr;   // nverts + 1
+  int32_t *d_vcells = nullptr;  // 3 ncells
 };
 
 struct ext_space {
@@ -172,6 +181,10 @@ struct MassP1Launch {
   int64_t nf = 0;  // DoFs of the f space (CG1xCG1 numbering shared with the coordinates)
   const double *base_xy = nullptr;  // the mesh's base coordinates (nverts x 2), if it has them
   bool overwrite = false;           // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
+  // the mesh's vertex rows (ext_mesh::d_vrow ...), null when it has none
+  const int32_t *vrow = nullptr;
+  const double2 *vent = nullptr;
+  const int32_t *vcrow = nullptr, *vcells = nullptr;
 };
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 

@@ -820,6 +820,272 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
 }
 
 
+// ---------------------------------------------------------------------------
+// Gather form (constant layers, a mesh with base coordinates).  A straight
+// extrusion with flat levels (every DoF at its vertex's base x, y, level m at
+// one height z_m in every column) is a tensor product, and the P1xP1 mass
+// matrix factors as M = Mh (x) Mv: Mh the P1 mass matrix of the base
+// triangulation, held by the mesh as vertex rows (the weight of neighbour j
+// of vertex a is the sum of alpha_c = |2 A_c| / 144 over the cells holding
+// edge (a, j), the diagonal weight is the sum of the row), and Mv the P1
+// mass matrix of the column,
+//   w_m = (Mv f)_m = |h_{m-1}| f_{m-1} + 2 (|h_{m-1}| + |h_m|) f_m + |h_m| f_{m+1}
+// (the factor 1/6 of Mv is in alpha).  b = Mh (x) Mv f is then, per level,
+// the row sums b_{a,m} = sum_j Mh_{aj} w_{j,m}: 3 FP64 operations per DoF
+// for Mv and one per row entry (about 7 per DoF) for Mh, against 6 per DoF
+// and 3 per (cell, level) item plus 3 atomic adds in the factored form.  The
+// launch runs
+//   k_levels            the level table (z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|),
+//                       |h_m|) from the column of vertex 0 (DoFs 0 .. layers),
+//   k_vsum_tab          w per DoF, stored; a NaN pattern instead where the DoF
+//                       or a vertical neighbour of it is off its column's base
+//                       x, y or its level's height,
+//   k_vgather           b per DoF: one thread forms the row sum over the
+//                       vertex row (no atomics) and overwrites b (WRITE) or
+//                       adds to it (INC); a 32-DoF chunk whose sums came out
+//                       NaN is recorded with the mask of those DoFs and left
+//                       untouched,
+//   k_vgather_general   the recorded DoFs: the 6-point rule with the general
+//                       Jacobian over both layers of every cell around the
+//                       vertex.
+// A NaN input or a non-straight prism anywhere in a DoF's stencil makes its
+// row sum NaN (NaN survives every product and sum), so every DoF is either
+// formed by the gather on a verified tensor-product stencil or recomputed in
+// full.  Every DoF of b is written by one thread, in a fixed order of
+// operations: the result does not depend on scheduling.
+
+struct LevelCoef {
+  double z, lo, mid, hi;  // z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|), |h_m| (0 beyond the column)
+};
+
+__global__ void __launch_bounds__(256) k_levels(const double *__restrict__ X, int layers, LevelCoef *__restrict__ tab) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > layers) return;
+  const double z = X[3 * (int64_t)m + 2];
+  const double hl = m > 0 ? fabs(z - X[3 * (int64_t)(m - 1) + 2]) : 0.0;
+  const double hh = m < layers ? fabs(X[3 * (int64_t)(m + 1) + 2] - z) : 0.0;
+  LevelCoef c;
+  c.z = z;
+  c.lo = hl;
+  c.mid = 2.0 * (hl + hh);
+  c.hi = hh;
+  tab[m] = c;
+}
+
+#ifndef EXT_VTAB_MINB
+#define EXT_VTAB_MINB 4  // resident 256-thread CTAs per SM of the table vertex pass
+#endif
+#ifndef EXT_VGATHER_MINB
+#define EXT_VGATHER_MINB 4  // resident 256-thread CTAs per SM of the gather pass
+#endif
+#ifndef EXT_VT_VU
+#define EXT_VT_VU 2  // 32-DoF chunks per warp step of the table vertex pass
+#endif
+#ifndef EXT_VG_VU
+#define EXT_VG_VU 1  // 32-DoF chunks per warp step of the gather
+#endif
+#ifndef EXT_VG_UNROLL
+#define EXT_VG_UNROLL 4  // unrolling of the gather's row loop
+#endif
+constexpr int kVGUnroll = EXT_VG_UNROLL;
+
+// DoF d is at its vertex's base x, y and at its level's height (bitwise)
+__device__ __forceinline__ int dof_straight(const double *__restrict__ X, const double *__restrict__ xy,
+                                            const LevelCoef *__restrict__ tab, int64_t d, FastDiv col) {
+  const uint32_t q = fdiv((uint32_t)d, col);
+  const uint32_t m = (uint32_t)d - q * col.d;
+  return (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 0))) &
+         (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 1))) &
+         (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(__ldg(&tab[m].z)));
+}
+
+__global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *__restrict__ X, const double *__restrict__ f,
+                                                                const double *__restrict__ xy,
+                                                                const LevelCoef *__restrict__ tab,
+                                                                double *__restrict__ W, int64_t n, FastDiv col,
+                                                                Fp64Ones k1) {
+  constexpr int VU = EXT_VT_VU;
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 * VU; base < n; base += wstride) {
+    double fc[VU], clo[VU], cmid[VU], chi[VU];
+    int ok[VU];
+    uint32_t mm[VU];
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      fc[u] = 0.0;
+      clo[u] = cmid[u] = chi[u] = 0.0;
+      ok[u] = 1;
+      mm[u] = 0;
+      if (d < n) {
+        const uint32_t q = fdiv((uint32_t)d, col);
+        mm[u] = (uint32_t)d - q * col.d;
+        const double2 t0 = __ldg(reinterpret_cast<const double2 *>(tab + mm[u]));
+        const double2 t1 = __ldg(reinterpret_cast<const double2 *>(tab + mm[u]) + 1);
+        clo[u] = t0.y;
+        cmid[u] = t1.x;
+        chi[u] = t1.y;
+        ok[u] = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 0))) &
+                (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 1))) &
+                (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(t0.x));
+        fc[u] = __ldg(f + d);
+      }
+    }
+    // the DoF before the first chunk and after the last one
+    double fb = 0.0, fa = 0.0;
+    int okb = 1, oka = 1;
+    if (lane == 0 && base > 0 && base - 1 < n) {
+      fb = __ldg(f + base - 1);
+      okb = dof_straight(X, xy, tab, base - 1, col);
+    }
+    if (lane == 31 && base + 32 * VU < n) {
+      fa = __ldg(f + base + 32 * VU);
+      oka = dof_straight(X, xy, tab, base + 32 * VU, col);
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      // left neighbour: previous lane (lane 0: the previous chunk's lane 31,
+      // or the DoF before the first chunk); right neighbour likewise
+      double fl = __shfl_up_sync(kFull, fc[u], 1), fr = __shfl_down_sync(kFull, fc[u], 1);
+      int okl = __shfl_up_sync(kFull, ok[u], 1), okr = __shfl_down_sync(kFull, ok[u], 1);
+      double flp = fb, frn = fa;
+      int oklp = okb, okrn = oka;
+      if (u > 0) {
+        flp = __shfl_sync(kFull, fc[u > 0 ? u - 1 : 0], 31);
+        oklp = __shfl_sync(kFull, ok[u > 0 ? u - 1 : 0], 31);
+      }
+      if (u + 1 < VU) {
+        frn = __shfl_sync(kFull, fc[u + 1 < VU ? u + 1 : u], 0);
+        okrn = __shfl_sync(kFull, ok[u + 1 < VU ? u + 1 : u], 0);
+      }
+      if (lane == 0) {
+        fl = flp;
+        okl = oklp;
+      }
+      if (lane == 31) {
+        fr = frn;
+        okr = okrn;
+      }
+      const bool lo_end = mm[u] == 0, hi_end = mm[u] + 1 == col.d;
+      // the neighbour across a column end is cleared bitwise (an integer AND)
+      fl = __longlong_as_double(__double_as_longlong(fl) & (lo_end ? 0LL : -1LL));
+      fr = __longlong_as_double(__double_as_longlong(fr) & (hi_end ? 0LL : -1LL));
+      const int good = ok[u] & (lo_end | okl) & (hi_end | okr);
+      const double w = fma(clo[u], fl, fma(cmid[u], fc[u], fmul(chi[u], fr, k1)));
+      if (d < n) W[d] = good ? w : __longlong_as_double(kNotVertical);
+    }
+  }
+}
+
+template <bool INC>
+__global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double *__restrict__ W,
+                                                                   const int32_t *__restrict__ vrow,
+                                                                   const double2 *__restrict__ vent,
+                                                                   double *__restrict__ b, int64_t n, FastDiv col,
+                                                                   Deferred dfr, unsigned int *err, Fp64Ones k1) {
+  constexpr int VU = EXT_VG_VU;
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 * VU; base < n; base += wstride) {
+    int r0[VU], deg[VU];
+    uint32_t mm[VU];
+    double acc[VU];
+    int dmx = 0;
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      r0[u] = 0;
+      deg[u] = 0;
+      mm[u] = 0;
+      acc[u] = k1.mzero;  // WRITE: the first product is added to -0, which leaves it exact
+      if (d < n) {
+        const uint32_t q = fdiv((uint32_t)d, col);
+        mm[u] = (uint32_t)d - q * col.d;
+        r0[u] = __ldg(vrow + q);
+        deg[u] = __ldg(vrow + q + 1) - r0[u];
+        if (INC) acc[u] = b[d];
+      }
+      const int dm = __reduce_max_sync(kFull, deg[u]);
+      dmx = dm > dmx ? dm : dmx;
+    }
+    // one product per row entry up to the warp's longest row; past its own
+    // row a lane multiplies zeros.  The trip count is the loop bound (no
+    // guarded products, which the compiler turns into a product and a select)
+#pragma unroll kVGUnroll
+    for (int t = 0; t < dmx; ++t) {
+      double ev[VU], wv[VU];
+#pragma unroll
+      for (int u = 0; u < VU; ++u) {
+        ev[u] = 0.0;
+        wv[u] = 0.0;
+        if (t < deg[u]) {
+          const double2 en = __ldg(vent + r0[u] + t);
+          ev[u] = en.x;
+          wv[u] = __ldg(W + (int64_t)(uint32_t)__double_as_longlong(en.y) * col.d + mm[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VU; ++u) acc[u] = fma(ev[u], wv[u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < VU; ++u) {
+      const int64_t d = base + u * 32 + lane;
+      // NaN test on the bit pattern (integer ALU)
+      const bool bad = d < n && (__double_as_longlong(acc[u]) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+      if (d < n && !bad) b[d] = acc[u];
+      const unsigned int mask = __ballot_sync(kFull, bad);
+      if (mask != 0u && lane == 0) {
+        const unsigned int slot = atomicAdd(dfr.count, 1u);
+        if (slot < dfr.cap) dfr.list[slot] = make_int2((int)(base + u * 32), (int)mask);
+        else atomicOr(err, EXT_DERR_BOUNDS);
+      }
+    }
+  }
+}
+
+// The recorded DoFs of the gather: b_{a,m} (+)= the bottom-row entries of the
+// prisms (c, m) and the top-row entries of the prisms (c, m - 1) for every
+// cell c around vertex a, each from the 6-point rule with the general
+// Jacobian, summed in ascending cell order.
+template <bool INC>
+__global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Launch p, Deferred dfr, FastDiv col) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const unsigned int n = min(*dfr.count, dfr.cap);
+  for (unsigned int e = blockIdx.x * kWarps + warp; e < n; e += gridDim.x * kWarps) {
+    const int2 en = dfr.list[e];
+    if ((((unsigned int)en.y) >> lane & 1u) == 0u) continue;
+    const int64_t d = (int64_t)en.x + lane;
+    const uint32_t q = fdiv((uint32_t)d, col);
+    const int m = (int)((uint32_t)d - q * col.d);
+    const int32_t v0 = (int32_t)(q * col.d);  // DoF of vertex q at level 0
+    double acc = INC ? p.b[d] : 0.0;
+    for (int32_t t = __ldg(p.vcrow + q); t < __ldg(p.vcrow + q + 1); ++t) {
+      const int64_t c = __ldg(p.vcells + t);
+      int a = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (__ldg(p.fmap + c * 6 + 2 * k) == v0) a = k;
+      for (int half = 0; half < 2; ++half) {
+        const int l = half == 0 ? m - 1 : m;
+        if (l < 0 || l >= p.layers) continue;
+        int32_t cd[6], fd[6];
+        for (int i = 0; i < 6; ++i) {
+          cd[i] = __ldg(p.cmap + c * 6 + i) + l * p.coff[i];
+          fd[i] = __ldg(p.fmap + c * 6 + i) + l * p.foff[i];
+        }
+        double out[6];
+        prism_general_g(p.X, p.f, cd, fd, out);
+        acc += out[2 * a + (half == 0 ? 1 : 0)];
+      }
+    }
+    p.b[d] = acc;
+  }
+}
+
+
 
 // Resident CTAs per SM of a kernel (one GPU model per process).
 template <typename K>
@@ -838,9 +1104,11 @@ int resident_ctas(K kernel, int &cache) {
 // environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
 // (each cell evaluates its own vertical sums; no scratch; the same results up
 // to rounding); EXTMESH_MASS_FUSED=0 asks for the split form at any size.
-// With constant layers the split form is factored (area pass, vertex part in
-// the vertex pass) from EXT_FACTORED_MIN_LAYERS layers on;
-// EXTMESH_MASS_FACTORED=1 / 0 asks for it at any layer count / never.
+// With constant layers on a mesh that has base coordinates the split form is
+// the gather form (EXTMESH_MASS_GATHER=0 turns it off); otherwise, with
+// constant layers, it is factored (area pass, vertex part in the vertex pass)
+// from EXT_FACTORED_MIN_LAYERS layers on; EXTMESH_MASS_FACTORED=1 / 0 asks
+// for that at any layer count / never.
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -851,7 +1119,7 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   const int64_t blocks0 = (warps + kWarps - 1) / kWarps;
-  static int sms = 0, fused_env = -1, fac_env = -1;
+  static int sms = 0, fused_env = -1, fac_env = -1, gather_env = -1;
   static int res_cells[3] = {0, 0, 0}, res_fused[2] = {0, 0};
   if (sms == 0) {
     int dev = 0;
@@ -863,21 +1131,28 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     fused_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
     ev = getenv("EXTMESH_MASS_FACTORED");  // 1 / 0: factored split form always / never; unset: by layers
     fac_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
+    ev = getenv("EXTMESH_MASS_GATHER");  // 0: never the gather form; unset: whenever the mesh has vertex rows
+    gather_env = (ev && ev[0] == '0') ? 0 : 1;
   }
-  const bool factored = !var && (fac_env == 1 || (fac_env == 2 && p.layers >= EXT_FACTORED_MIN_LAYERS));
+  const bool gather = !var && p.vrow && p.vent && p.vcrow && p.vcells && gather_env == 1;
+  const bool factored = !var && !gather && (fac_env == 1 || (fac_env == 2 && p.layers >= EXT_FACTORED_MIN_LAYERS));
   // The vertical sums, the vertex area sums A and the list of deferred warp
   // steps go to stream-ordered scratch, so launches on different streams
   // never share it.
   const int64_t n = p.nf;
   const double items = (var ? p.mean_layers + 1.0 : (double)(p.layers + 1)) * (double)p.ncells;
-  const int64_t cap64 = (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
+  // deferred warp steps: one per warp step of the cell pass at most, or
+  // one per 32-DoF chunk of the gather
+  const int64_t cap64 = gather ? (n + 31) / 32 + 1
+                               : (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t nn = (size_t)(n > 0 ? n : 1);
-  const size_t wbytes = (sizeof(double) * nn * (var ? 3 : 2) + 255) & ~(size_t)255;
+  const size_t wbytes = (sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)) + 255) & ~(size_t)255;
   const size_t nverts = factored ? (size_t)(n / (p.layers + 1)) : 0;
   // factored: A (per vertex) and alpha (per cell)
   const size_t abytes = (sizeof(double) * nverts + 255) & ~(size_t)255;
-  const size_t cbytes = factored ? ((sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255) : 0;
+  const size_t cbytes = factored ? ((sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255)
+                                  : (gather ? ((sizeof(LevelCoef) * (size_t)(p.layers + 1) + 255) & ~(size_t)255) : 0);
   char *scr = nullptr;
   // on a small launch the split form's extra passes, scratch allocation and
   // launches (about 25 us together) cost more than they save
@@ -917,7 +1192,28 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (vb < 1) vb = 1;
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
   const Fp64Ones k1 = {1.0, -1.0, -0.0};
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && gather) {
+    LevelCoef *tab = reinterpret_cast<LevelCoef *>(alpha);  // the table takes the place of alpha
+    static int res_vtab = 0, res_vg[2] = {0, 0};
+    const int rv = resident_ctas(k_vsum_tab, res_vtab);
+    const int rg = p.overwrite ? resident_ctas(k_vgather<false>, res_vg[0]) : resident_ctas(k_vgather<true>, res_vg[1]);
+    int64_t gv = ((n + 32 * EXT_VT_VU - 1) / (32 * EXT_VT_VU) + 7) / 8;  // CTAs of 8 warps, one warp step each
+    int64_t gg = ((n + 32 * EXT_VG_VU - 1) / (32 * EXT_VG_VU) + 7) / 8;
+    if (gv > (int64_t)rv * sms) gv = (int64_t)rv * sms;
+    if (gg > (int64_t)rg * sms) gg = (int64_t)rg * sms;
+    if (gv < 1) gv = 1;
+    if (gg < 1) gg = 1;
+    k_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab);
+    k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1);
+    if (p.overwrite) {
+      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vent, p.b, n, col, dfr, p.err, k1);
+      k_vgather_general<false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, col);
+    } else {
+      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vent, p.b, n, col, dfr, p.err, k1);
+      k_vgather_general<true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, col);
+    }
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
     if (var) {
       k_vsum<true, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, p.b, k1, nullptr, p.overwrite);
       k_mass_cells<true, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
