@@ -116,6 +116,11 @@ def p1_counts(ndofs: int, items: int, ncells: int, layers: int, var: bool = Fals
     return tuple(per[0][k] * ndofs + per[1][k] * items + per[2][k] * ncells for k in range(3))
 
 
+P1_OPS_NOTE = (f"gather form from {P1_SPLIT_MIN_ITEMS} (column, level) items: {GATHER_OPS_PER_DOF} per DoF "
+               "(column mass matrix) + 1 per vertex-row entry and level (V + 2E entries: base mass matrix); "
+               "single pass below: 13 per column level")
+
+
 def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None) -> int:
     return sum(p1_counts(ndofs, items, ncells, layers, var, nedges))
 
@@ -877,12 +882,7 @@ def run_cfg6(args, rank, world, local):
     tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES)
     extra = {"spaces": results, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
              "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-             "fp64_ops_per_unit": {nm: (ops if ops is not None else
-                                        f"{sum(P1_MIX['factored'][0])} per DoF + {sum(P1_MIX['factored'][1])} "
-                                        f"per column level + {sum(P1_MIX['factored'][2])} per column from "
-                                        f"{P1_FACTORED_MIN_LAYERS} layers, {sum(P1_MIX['plain'][0])} per DoF + "
-                                        f"{sum(P1_MIX['plain'][1])} per column level below")
-                                   for nm, _, ops in TP_SPACES},
+             "fp64_ops_per_unit": {nm: (ops if ops is not None else P1_OPS_NOTE) for nm, _, ops in TP_SPACES},
              "timing": "min over reps, L2 flushed before every timed launch"}
     return _common(args, world, "I_1 = int f v dx on the nine prism spaces at 100 layers (~15M cells, RCM): valuable "
                    "GB/s over the nine launches", world * tot_b / tot_t, "GB/s",
