@@ -435,7 +435,7 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
         algorithmic = (f"{GATHER_OPS_PER_DOF} FP64 ops per DoF x {ndofs} DoFs (column mass matrix) + 1 per "
                        f"vertex-row entry and level x {V + 2 * E_} entries x {L + 1} levels (base mass matrix) "
                        f"= {ops} per launch")
-        kname = "P1xP1 RHS / mass-action launch (k_levels + k_vsum_tab + k_vgather + k_vgather_general)"
+        kname = "P1xP1 RHS / mass-action launch (k_levels + k_vsum_bulk + k_vgather + k_vgather_general)"
         note = ("on straight prisms with flat levels M = Mh (x) Mv: the column mass matrix Mv is applied once "
                 "per vertex level (3 FP64 ops), then the base mass matrix Mh row by row per level (one FP64 op "
                 "per row entry, no atomics); evaluated cell by cell the same work is 18 FP64 ops per "

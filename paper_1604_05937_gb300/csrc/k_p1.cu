@@ -881,6 +881,9 @@ __global__ void __launch_bounds__(256) k_levels(const double *__restrict__ X, in
 #ifndef EXT_VT_VU
 #define EXT_VT_VU 2  // 32-DoF chunks per warp step of the table vertex pass
 #endif
+#ifndef EXT_VSUM_BULK
+#define EXT_VSUM_BULK 1  // 1: the table vertex pass with bulk copies (k_vsum_bulk); 0: plain loads (k_vsum_tab)
+#endif
 #ifndef EXT_VG_VU
 #define EXT_VG_VU 1  // 32-DoF chunks per warp step of the gather
 #endif
@@ -974,6 +977,184 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
       fr = __longlong_as_double(__double_as_longlong(fr) & (hi_end ? 0LL : -1LL));
       const int good = ok[u] & (lo_end | okl) & (hi_end | okr);
       const double w = fma(clo[u], fl, fma(cmid[u], fc[u], fmul(chi[u], fr, k1)));
+      if (d < n) W[d] = good ? w : __longlong_as_double(kNotVertical);
+    }
+  }
+}
+
+// The same vertex pass with bulk copies.  A warp step covers 64 DoFs
+// [base, base + 64); the coordinates (24 bytes per DoF) and f (8 bytes) of
+// the DoFs base - 2 .. base + 65 are copied into one of the warp's two
+// shared-memory stages by the bulk-copy engine (cp.async.bulk, completion
+// counted in bytes on an mbarrier), the next step's copy in flight while the
+// current step is computed.  A step starts at an even DoF, so with 16-byte
+// aligned X and f every copy starts on a 16-byte boundary and has a length
+// that is a multiple of 16; a step whose clamped range is odd (the last one,
+// when n is odd) is filled by the lanes with plain loads.  Every wait is
+// bounded: when it runs out the kernel sets EXT_DERR_TIMEOUT, waits (bounded
+// again) for its other copy in flight and returns.
+constexpr int kBulkDofs = 64;              // DoFs per warp step
+constexpr int kBulkSpan = kBulkDofs + 4;   // with two DoFs before and two after
+constexpr unsigned kBulkWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
+
+struct __align__(16) BulkStage {
+  double X[3 * kBulkSpan];
+  double f[kBulkSpan];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+  for (unsigned i = 0; i < kBulkWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// DoF range [lo, hi) of the step at `base`, clamped to [0, n), and whether
+// bulk copies can fetch it (even length; the start is even by construction)
+__device__ __forceinline__ void bulk_range(int64_t base, int64_t n, int64_t &lo, int64_t &hi, bool &bulk, bool aligned) {
+  lo = base - 2 > 0 ? base - 2 : 0;
+  hi = base + kBulkDofs + 2 < n ? base + kBulkDofs + 2 : n;
+  bulk = aligned && ((hi - lo) & 1) == 0;
+}
+
+__global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *__restrict__ X, const double *__restrict__ f,
+                                                                 const double *__restrict__ xy,
+                                                                 const LevelCoef *__restrict__ tab,
+                                                                 double *__restrict__ W, int64_t n, FastDiv col,
+                                                                 Fp64Ones k1, unsigned int *err) {
+  __shared__ BulkStage stage[8][2];
+  __shared__ __align__(8) uint64_t bar[8][2];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const bool aligned = ((((uintptr_t)X) | ((uintptr_t)f)) & 15) == 0;
+  if (lane == 0) {
+    for (int q = 0; q < 2; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[warp][q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int64_t nsteps = (n + kBulkDofs - 1) / kBulkDofs;
+  const int64_t wstride = (int64_t)gridDim.x * 8;
+  // lane 0 starts the copies of a step into stage q
+  auto issue = [&](int64_t stp, int q) {
+    int64_t lo, hi;
+    bool bulk;
+    bulk_range(stp * kBulkDofs, n, lo, hi, bulk, aligned);
+    if (bulk && lane == 0) {
+      const int64_t off = lo - (stp * kBulkDofs - 2);  // 0, or 2 for the first step
+      const unsigned bx = (unsigned)(24 * (hi - lo)), bf = (unsigned)(8 * (hi - lo));
+      const uint32_t b = smem_addr(&bar[warp][q]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bx + bf) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_addr(&stage[warp][q].X[3 * off])),
+                   "l"(X + 3 * lo), "r"(bx), "r"(b)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_addr(&stage[warp][q].f[off])),
+                   "l"(f + lo), "r"(bf), "r"(b)
+                   : "memory");
+    }
+  };
+  int64_t stp = (int64_t)blockIdx.x * 8 + warp;
+  if (stp < nsteps) issue(stp, 0);
+  unsigned use0 = 0u, use1 = 0u;  // completed uses of each stage's barrier (their parity is the phase to wait for)
+  for (int it = 0; stp < nsteps; stp += wstride, ++it) {
+    const int q = it & 1;
+    const int64_t nxt = stp + wstride;
+    __syncwarp();  // every lane is done with stage q ^ 1 (the previous step)
+    if (nxt < nsteps) issue(nxt, q ^ 1);
+    const int64_t base = stp * kBulkDofs;
+    int64_t lo, hi;
+    bool bulk;
+    bulk_range(base, n, lo, hi, bulk, aligned);
+    BulkStage &sg = stage[warp][q];
+    if (bulk) {
+      if (!mbar_wait_bounded(&bar[warp][q], (q ? use1 : use0) & 1u)) {
+        if (lane == 0) atomicOr(err, EXT_DERR_TIMEOUT);
+        // the other stage may hold a copy in flight: wait for it (bounded) before leaving
+        int64_t lo2, hi2;
+        bool bulk2;
+        if (nxt < nsteps) {
+          bulk_range(nxt * kBulkDofs, n, lo2, hi2, bulk2, aligned);
+          if (bulk2) (void)mbar_wait_bounded(&bar[warp][q ^ 1], (q ? use0 : use1) & 1u);
+        }
+        (void)mbar_wait_bounded(&bar[warp][q], (q ? use1 : use0) & 1u);
+        return;
+      }
+      if (q) ++use1;
+      else ++use0;
+    } else {
+      for (int64_t d = lo + lane; d < hi; d += 32) {
+        const int64_t r = d - (base - 2);
+        sg.X[3 * r + 0] = __ldg(X + 3 * d + 0);
+        sg.X[3 * r + 1] = __ldg(X + 3 * d + 1);
+        sg.X[3 * r + 2] = __ldg(X + 3 * d + 2);
+        sg.f[r] = __ldg(f + d);
+      }
+      __syncwarp();
+    }
+    // stage row r holds DoF base - 2 + r
+    auto ok_row = [&](int r, int64_t d) {
+      const uint32_t qv = fdiv((uint32_t)d, col);
+      const uint32_t m = (uint32_t)d - qv * col.d;
+      return (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 0))) &
+             (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 1))) &
+             (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(__ldg(&tab[m].z)));
+    };
+    int ok[2];
+    uint32_t mm[2];
+    double clo[2], cmid[2], chi[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t d = base + 32 * u + lane;
+      ok[u] = 1;
+      mm[u] = 0;
+      clo[u] = cmid[u] = chi[u] = 0.0;
+      if (d < n) {
+        const uint32_t qv = fdiv((uint32_t)d, col);
+        mm[u] = (uint32_t)d - qv * col.d;
+        const double2 t0 = __ldg(reinterpret_cast<const double2 *>(tab + mm[u]));
+        const double2 t1 = __ldg(reinterpret_cast<const double2 *>(tab + mm[u]) + 1);
+        clo[u] = t0.y;
+        cmid[u] = t1.x;
+        chi[u] = t1.y;
+        const int r = 32 * u + lane + 2;
+        ok[u] = (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 0))) &
+                (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 1))) &
+                (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(t0.x));
+      }
+    }
+    // straightness of the DoFs just outside the step
+    int okb = 1, oka = 1;
+    if (lane == 0 && base > 0) okb = ok_row(1, base - 1);
+    if (lane == 31 && base + kBulkDofs < n) oka = ok_row(kBulkDofs + 2, base + kBulkDofs);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t d = base + 32 * u + lane;
+      const int r = 32 * u + lane + 2;
+      int okl = __shfl_up_sync(kFull, ok[u], 1), okr = __shfl_down_sync(kFull, ok[u], 1);
+      const int oklp = u > 0 ? __shfl_sync(kFull, ok[0], 31) : okb;
+      const int okrn = u == 0 ? __shfl_sync(kFull, ok[1], 0) : oka;
+      if (lane == 0) okl = oklp;
+      if (lane == 31) okr = okrn;
+      const bool lo_end = mm[u] == 0, hi_end = mm[u] + 1 == col.d;
+      // neighbours across a column end (or outside the array) are cleared bitwise
+      const double fl = __longlong_as_double(__double_as_longlong(sg.f[r - 1]) & (lo_end ? 0LL : -1LL));
+      const double fr = __longlong_as_double(__double_as_longlong(sg.f[r + 1]) & (hi_end ? 0LL : -1LL));
+      const int good = ok[u] & (lo_end | okl) & (hi_end | okr);
+      const double w = fma(clo[u], fl, fma(cmid[u], sg.f[r], fmul(chi[u], fr, k1)));
       if (d < n) W[d] = good ? w : __longlong_as_double(kNotVertical);
     }
   }
@@ -1204,7 +1385,16 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     if (gv < 1) gv = 1;
     if (gg < 1) gg = 1;
     k_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab);
-    k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1);
+    if (EXT_VSUM_BULK) {
+      static int res_vb = 0;
+      const int rb = resident_ctas(k_vsum_bulk, res_vb);
+      int64_t gb = ((n + kBulkDofs - 1) / kBulkDofs + 7) / 8;  // CTAs of 8 warps, one warp step each
+      if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
+      if (gb < 1) gb = 1;
+      k_vsum_bulk<<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1, p.err);
+    } else {
+      k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1);
+    }
     if (p.overwrite) {
       k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vent, p.b, n, col, dfr, p.err, k1);
       k_vgather_general<false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, col);
