@@ -667,8 +667,12 @@ def run_cfg3(args, rank, world, local):
 # residual, plus 1 (h) + 18 (differences) + 27 (scaling); the adjoint
 # evaluates two fields and forms 2 P w; the fused pass shares P.
 HEX_OPS = {1: 1 + 18 + 4 * 234 + 27, 2: 1 + 36 + 4 * 338 + 27, 3: 1 + 36 + 4 * 468 + 54}
-# per prism cell-layer of the fused P1xP1 u^2 v residual + adjoint (straight)
-PRISM_U2V_OPS = {1: 59, 2: 81, 3: 117}
+# per prism cell-layer of the P1xP1 u^2 v residual / adjoint / both (straight
+# prism, all issued as DFMA): 2 for the weight |2A| |h| / 12, 21 per field
+# evaluated at the six points, 2 for the projection constants (weight / 6,
+# weight / 2; 1 more for the adjoint's doubled ones), 6 point products and
+# 24 for the projection per output
+PRISM_U2V_OPS = {1: 55, 2: 77, 3: 107}
 
 
 def run_cfg4(args, rank, world, local):

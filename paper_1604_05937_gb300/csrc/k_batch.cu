@@ -45,7 +45,7 @@ __device__ __forceinline__ int find_mesh(const BatchDesc *d, int nmesh, int64_t 
 
 template <int MODE, bool COLOUR>
 __global__ void __launch_bounds__(256) k_batch(const BatchDesc *descs, int nmesh, int64_t nitems, int cpi, int lt,
-                        unsigned long long *counter) {
+                        unsigned long long *counter, Fp64Ones k1) {
   __shared__ prism_u2v::ColGeom geo[8][32];  // per warp (<= 8 warps), per column of the tile
   __shared__ int64_t cid[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchDesc *descs, int nmesh
             urow[i] = __ldg(d.umap + c * 6 + i);
           }
           prism_u2v::cell_layer<MODE>(crow, urow, d.coff, d.uoff, l0 + l, geo[warp][cl], d.X, d.u, d.w,
-                                      d.F, d.G);
+                                      d.F, d.G, k1);
         }
         l += 32;
         while (l >= nl) { l -= nl; ++cl; }
@@ -128,11 +128,12 @@ __global__ void __launch_bounds__(256) k_batch(const BatchDesc *descs, int nmesh
               (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
         double Fo[6], Go[6];
         if (ok) {
-          prism_u2v::local_straight<MODE>(uu, ww, cg.wdet * fabs(Xl[1][2] - Xl[0][2]), Fo, Go);
+          prism_u2v::local_straight<MODE>(uu, ww, fmul(cg.wdet, fabs(fsub(Xl[1][2], Xl[0][2], k1)), k1), Fo, Go,
+                                          k1);
         } else {
           double W[6];
           prism_u2v::general_weights(Xl, W);
-          prism_u2v::local<MODE>(uu, ww, W, Fo, Go);
+          prism_u2v::local<MODE>(uu, ww, W, Fo, Go, k1);
         }
         for (int a = 0; a < 3; ++a) {
           const int ib = 2 * a, itp = 2 * a + 1;
@@ -197,7 +198,7 @@ cudaError_t launch_batch_phase(const void *d_descs, int nmesh, int64_t nitems, i
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const BatchDesc *dd = reinterpret_cast<const BatchDesc *>(d_descs);
-#define EXT_LAUNCH_BATCH(M, C) k_batch<M, C><<<grid, threads, 0, s>>>(dd, nmesh, nitems, cpi, lt, counter)
+#define EXT_LAUNCH_BATCH(M, C) k_batch<M, C><<<grid, threads, 0, s>>>(dd, nmesh, nitems, cpi, lt, counter, fp64_ones())
   if (colour) {
     if (mode == 1) EXT_LAUNCH_BATCH(1, true);
     else if (mode == 2) EXT_LAUNCH_BATCH(2, true);

@@ -402,16 +402,6 @@ __global__ void __launch_bounds__(256) k_area(const MassP1Launch p, double *__re
   }
 }
 
-// FP64 constants the kernels take as arguments: a product and a sum are
-// issued as DFMA, a b + (-0) and a (+-1) + b, which round exactly like DMUL
-// and DADD but issue at the DFMA rate (GB300 issues DADD and DMUL at about
-// 5/6 of it).  Literal constants would let the compiler fold them back.
-struct Fp64Ones {
-  double one, mone, mzero;  // 1, -1, -0
-};
-__device__ __forceinline__ double fmul(double a, double b, const Fp64Ones &k) { return fma(a, b, k.mzero); }
-__device__ __forceinline__ double fsub(double a, double b, const Fp64Ones &k) { return fma(b, k.mone, a); }
-
 // Vertex pass over the DoFs [0, n) of a CG1xCG1 field (the column of a vertex
 // is a contiguous run, so level m's neighbours are DoFs d - 1 and d + 1).
 // Constant layers (`col` = layers + 1, level m = d mod col, the ends have one

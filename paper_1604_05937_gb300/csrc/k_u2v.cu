@@ -6,7 +6,9 @@
 // Every kernel is bound by the FP64 pipe, so the local kernels are written
 // to minimise FP64 operations: sum factorisation, per-column hoisting of the
 // horizontal Jacobian on straight columns, and increments handed to L2 as
-// FP64 atomic adds instead of being merged in registers.
+// FP64 atomic adds instead of being merged in registers; products and sums
+// are issued as DFMA with run-time constants (Fp64Ones), which round like
+// DMUL and DADD but issue at the higher DFMA rate.
 #include "ext_internal.cuh"
 #include "prism_u2v.cuh"
 
@@ -78,8 +80,8 @@ __device__ void hex_general_weights(const double X[8][3], int g3, double W[16]) 
 
 // Values at the 4 Gauss points of a 1-D P2 function with nodal values
 // (v0, v1, v2), using l2 = 1 - l0 - l1.
-__device__ __forceinline__ void interp4(double v0, double v1, double v2, double out[4]) {
-  const double d0 = v0 - v2, d1 = v1 - v2;
+__device__ __forceinline__ void interp4(double v0, double v1, double v2, double out[4], const Fp64Ones &k) {
+  const double d0 = fsub(v0, v2, k), d1 = fsub(v1, v2, k);
 #pragma unroll
   for (int g = 0; g < 4; ++g) out[g] = fma(d1, kB1[g], fma(d0, kB0[g], v2));
 }
@@ -87,7 +89,7 @@ __device__ __forceinline__ void interp4(double v0, double v1, double v2, double 
 // For vertical point g3: field values D[g1][g2] at the 16 points from the
 // nodal values (diff form: U2[ix][iy] and d0, d1 = U0 - U2, U1 - U2).
 __device__ __forceinline__ void hex_eval_slice(const double U2[3][3], const double d0[3][3],
-                                               const double d1[3][3], int g3, double D[4][4]) {
+                                               const double d1[3][3], int g3, double D[4][4], const Fp64Ones &k) {
   double A[3][3];
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix)
@@ -95,11 +97,11 @@ __device__ __forceinline__ void hex_eval_slice(const double U2[3][3], const doub
     for (int iy = 0; iy < 3; ++iy) A[ix][iy] = fma(d1[ix][iy], kB1[g3], fma(d0[ix][iy], kB0[g3], U2[ix][iy]));
   double C[3][4];
 #pragma unroll
-  for (int ix = 0; ix < 3; ++ix) interp4(A[ix][0], A[ix][1], A[ix][2], C[ix]);
+  for (int ix = 0; ix < 3; ++ix) interp4(A[ix][0], A[ix][1], A[ix][2], C[ix], k);
 #pragma unroll
   for (int g2 = 0; g2 < 4; ++g2) {
     double t[4];
-    interp4(C[0][g2], C[1][g2], C[2][g2], t);
+    interp4(C[0][g2], C[1][g2], C[2][g2], t, k);
 #pragma unroll
     for (int g1 = 0; g1 < 4; ++g1) D[g1][g2] = t[g1];
   }
@@ -107,27 +109,29 @@ __device__ __forceinline__ void hex_eval_slice(const double U2[3][3], const doub
 
 // Projects point values r[g1][g2] of vertical point g3 back onto the 27
 // basis functions, accumulating Facc[ix][iy][v] += sum r B_ix B_iy B_v w_g3.
-__device__ __forceinline__ void hex_project_slice(const double r[4][4], int g3, double Facc[3][3][3]) {
+__device__ __forceinline__ void hex_project_slice(const double r[4][4], int g3, double Facc[3][3][3],
+                                                  const Fp64Ones &k) {
   double E1[3][4];
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
     for (int g2 = 0; g2 < 4; ++g2)
-      E1[ix][g2] = fma(r[3][g2], B(ix, 3), fma(r[2][g2], B(ix, 2), fma(r[1][g2], B(ix, 1), r[0][g2] * B(ix, 0))));
+      E1[ix][g2] = fma(r[3][g2], B(ix, 3), fma(r[2][g2], B(ix, 2), fma(r[1][g2], B(ix, 1), fmul(r[0][g2], B(ix, 0), k))));
   const double wz = kW[g3];
-  const double bw[3] = {kB0[g3] * wz, kB1[g3] * wz, kB2[g3] * wz};
+  const double bw[3] = {fmul(kB0[g3], wz, k), fmul(kB1[g3], wz, k), fmul(kB2[g3], wz, k)};
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
     for (int iy = 0; iy < 3; ++iy) {
-      const double e2 = fma(E1[ix][3], B(iy, 3), fma(E1[ix][2], B(iy, 2), fma(E1[ix][1], B(iy, 1), E1[ix][0] * B(iy, 0))));
+      const double e2 =
+          fma(E1[ix][3], B(iy, 3), fma(E1[ix][2], B(iy, 2), fma(E1[ix][1], B(iy, 1), fmul(E1[ix][0], B(iy, 0), k))));
 #pragma unroll
       for (int v = 0; v < 3; ++v) Facc[ix][iy][v] = fma(e2, bw[v], Facc[ix][iy][v]);
     }
 }
 
 template <int MODE, bool DG>
-__global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
+__global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw, Fp64Ones k1) {
   constexpr int kWarps = 4;
   __shared__ HexCol cols[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -186,12 +190,12 @@ __global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
           if (MODE & 2) wv[v] = __ldg(p.w + ud[i]);
         }
         U2[kIX[e]][kIY[e]] = uv[2];
-        d0[kIX[e]][kIY[e]] = uv[0] - uv[2];
-        d1[kIX[e]][kIY[e]] = uv[1] - uv[2];
+        d0[kIX[e]][kIY[e]] = fsub(uv[0], uv[2], k1);
+        d1[kIX[e]][kIY[e]] = fsub(uv[1], uv[2], k1);
         if (MODE & 2) {
           W2[kIX[e]][kIY[e]] = wv[2];
-          e0[kIX[e]][kIY[e]] = wv[0] - wv[2];
-          e1[kIX[e]][kIY[e]] = wv[1] - wv[2];
+          e0[kIX[e]][kIY[e]] = fsub(wv[0], wv[2], k1);
+          e1[kIX[e]][kIY[e]] = fsub(wv[1], wv[2], k1);
         }
       }
       double Facc[3][3][3], Gacc[3][3][3];
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
         for (int iy = 0; iy < 3; ++iy)
 #pragma unroll
           for (int v = 0; v < 3; ++v) Facc[ix][iy][v] = Gacc[ix][iy][v] = 0.0;
-      const double hscale = ok ? fabs(X[1][2] - X[0][2]) : 1.0;
+      const double hscale = ok ? fabs(fsub(X[1][2], X[0][2], k1)) : 1.0;
 #pragma unroll 1
       for (int g3 = 0; g3 < 4; ++g3) {
         double Wh[16];
@@ -212,29 +216,29 @@ __global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
           hex_general_weights(X, g3, Wh);
         }
         double Du[4][4];
-        hex_eval_slice(U2, d0, d1, g3, Du);
+        hex_eval_slice(U2, d0, d1, g3, Du, k1);
         double P[4][4];
 #pragma unroll
         for (int g1 = 0; g1 < 4; ++g1)
 #pragma unroll
-          for (int g2 = 0; g2 < 4; ++g2) P[g1][g2] = Wh[g1 * 4 + g2] * Du[g1][g2];
+          for (int g2 = 0; g2 < 4; ++g2) P[g1][g2] = fmul(Wh[g1 * 4 + g2], Du[g1][g2], k1);
         if (MODE & 1) {
           double r[4][4];
 #pragma unroll
           for (int g1 = 0; g1 < 4; ++g1)
 #pragma unroll
-            for (int g2 = 0; g2 < 4; ++g2) r[g1][g2] = P[g1][g2] * Du[g1][g2];
-          hex_project_slice(r, g3, Facc);
+            for (int g2 = 0; g2 < 4; ++g2) r[g1][g2] = fmul(P[g1][g2], Du[g1][g2], k1);
+          hex_project_slice(r, g3, Facc, k1);
         }
         if (MODE & 2) {
           double Dw[4][4];
-          hex_eval_slice(W2, e0, e1, g3, Dw);
+          hex_eval_slice(W2, e0, e1, g3, Dw, k1);
           double r[4][4];
 #pragma unroll
           for (int g1 = 0; g1 < 4; ++g1)
 #pragma unroll
-            for (int g2 = 0; g2 < 4; ++g2) r[g1][g2] = (P[g1][g2] + P[g1][g2]) * Dw[g1][g2];
-          hex_project_slice(r, g3, Gacc);
+            for (int g2 = 0; g2 < 4; ++g2) r[g1][g2] = fmul(fadd(P[g1][g2], P[g1][g2], k1), Dw[g1][g2], k1);
+          hex_project_slice(r, g3, Gacc, k1);
         }
       }
       // scatter: INC (continuous) via L2 atomics, WRITE (DG2) via stores
@@ -244,12 +248,12 @@ __global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
         for (int v = 0; v < 3; ++v) {
           const int i = 3 * e + v;
           if (MODE & 1) {
-            const double val = Facc[kIX[e]][kIY[e]][v] * hscale;
+            const double val = fmul(Facc[kIX[e]][kIY[e]][v], hscale, k1);
             if (DG) p.F[ud[i]] = val;
             else atomicAdd(p.F + ud[i], val);
           }
           if (MODE & 2) {
-            const double val = Gacc[kIX[e]][kIY[e]][v] * hscale;
+            const double val = fmul(Gacc[kIX[e]][kIY[e]][v], hscale, k1);
             if (DG) p.g[ud[i]] = val;
             else atomicAdd(p.g + ud[i], val);
           }
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(128) k_u2v_hex(const U2VLaunch p, int cpw) {
 
 // Prism (P1xP1) u^2 v: lanes along (column, layer) items of the warp's columns.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_u2v_prism(const U2VLaunch p, int cpw) {
+__global__ void __launch_bounds__(256) k_u2v_prism(const U2VLaunch p, int cpw, Fp64Ones k1) {
   constexpr int kWarps = 8;
   __shared__ prism_u2v::ColGeom cols[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(256) k_u2v_prism(const U2VLaunch p, int cpw) {
         crow[i] = __ldg(p.cmap + c * 6 + i);
         urow[i] = __ldg(p.umap + c * 6 + i);
       }
-      prism_u2v::cell_layer<MODE>(crow, urow, coff, uoff, l, cols[warp][cl], p.X, p.u, p.w, p.F, p.g);
+      prism_u2v::cell_layer<MODE>(crow, urow, coff, uoff, l, cols[warp][cl], p.X, p.u, p.w, p.F, p.g, k1);
     }
     l += 32;
     while (l >= layers) { l -= layers; ++cl; }
@@ -319,9 +323,9 @@ cudaError_t launch_u2v(const U2VLaunch &p, cudaStream_t s) {
     const int64_t warps = (p.ncells + cpw - 1) / cpw;
     const unsigned blocks = (unsigned)((warps + 7) / 8);
     switch (p.mode) {
-      case 1: k_u2v_prism<1><<<blocks, 256, 0, s>>>(p, cpw); break;
-      case 2: k_u2v_prism<2><<<blocks, 256, 0, s>>>(p, cpw); break;
-      default: k_u2v_prism<3><<<blocks, 256, 0, s>>>(p, cpw); break;
+      case 1: k_u2v_prism<1><<<blocks, 256, 0, s>>>(p, cpw, fp64_ones()); break;
+      case 2: k_u2v_prism<2><<<blocks, 256, 0, s>>>(p, cpw, fp64_ones()); break;
+      default: k_u2v_prism<3><<<blocks, 256, 0, s>>>(p, cpw, fp64_ones()); break;
     }
   } else {
     const int cpw = 32;  // lane j sets up column j; items per warp = 32 * layers
@@ -329,15 +333,15 @@ cudaError_t launch_u2v(const U2VLaunch &p, cudaStream_t s) {
     const unsigned blocks = (unsigned)((warps + 3) / 4);
     if (p.dg) {
       switch (p.mode) {
-        case 1: k_u2v_hex<1, true><<<blocks, 128, 0, s>>>(p, cpw); break;
-        case 2: k_u2v_hex<2, true><<<blocks, 128, 0, s>>>(p, cpw); break;
-        default: k_u2v_hex<3, true><<<blocks, 128, 0, s>>>(p, cpw); break;
+        case 1: k_u2v_hex<1, true><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
+        case 2: k_u2v_hex<2, true><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
+        default: k_u2v_hex<3, true><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
       }
     } else {
       switch (p.mode) {
-        case 1: k_u2v_hex<1, false><<<blocks, 128, 0, s>>>(p, cpw); break;
-        case 2: k_u2v_hex<2, false><<<blocks, 128, 0, s>>>(p, cpw); break;
-        default: k_u2v_hex<3, false><<<blocks, 128, 0, s>>>(p, cpw); break;
+        case 1: k_u2v_hex<1, false><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
+        case 2: k_u2v_hex<2, false><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
+        default: k_u2v_hex<3, false><<<blocks, 128, 0, s>>>(p, cpw, fp64_ones()); break;
       }
     }
   }

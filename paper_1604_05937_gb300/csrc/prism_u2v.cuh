@@ -8,7 +8,8 @@
 // points is evaluated in factorised form: vertical interpolation per vertex,
 // then u_t = S/6 + ubar_t/2; the projection back onto phi_i is the
 // transpose.  On a straight prism |det J| = |2A| |h| at every point; other
-// prisms use the full Jacobian per point.
+// prisms use the full Jacobian per point.  Products and sums are issued as
+// DFMA (see Fp64Ones): GB300 runs DADD and DMUL at about 5/6 of the DFMA rate.
 #pragma once
 #include "ext_internal.cuh"
 
@@ -58,77 +59,85 @@ __device__ inline void general_weights(const double X[6][3], double W[6]) {
 }
 
 // Values at the six points (t, g) of a P1xP1 field with nodal values v[2a+b].
-__device__ __forceinline__ void eval6(const double v[6], double q[6]) {
+// Every product and sum here is a DFMA (k: run-time 1, -1, -0).
+__device__ __forceinline__ void eval6(const double v[6], double q[6], const Fp64Ones &k) {
   double ub[2][3];
   for (int a = 0; a < 3; ++a) {
-    const double d = v[2 * a + 1] - v[2 * a];
+    const double d = fsub(v[2 * a + 1], v[2 * a], k);
     ub[0][a] = fma(kZ0, d, v[2 * a]);
     ub[1][a] = fma(kZ1, d, v[2 * a]);
   }
   for (int g = 0; g < 2; ++g) {
-    const double s6 = ((ub[g][0] + ub[g][1]) + ub[g][2]) * (1.0 / 6.0);
+    const double s6 = fma(ub[g][0], 1.0 / 6.0, fma(ub[g][1], 1.0 / 6.0, fmul(ub[g][2], 1.0 / 6.0, k)));
     for (int t = 0; t < 3; ++t) q[2 * t + g] = fma(0.5, ub[g][t], s6);
   }
 }
 
-// out[2a+b] = sum_{t,g} r[(t,g)] lambda_a(t) psi_b(g)   (transpose of eval6)
-__device__ __forceinline__ void project6(const double r[6], double out[6]) {
+// out[2a+b] = W sum_{t,g} r[(t,g)] lambda_a(t) psi_b(g), the transpose of
+// eval6 times a weight W common to the six points, with c6 = W / 6 and
+// c2 = W / 2 (lambda_a(t) = 1/6 + [a = t]/2).
+__device__ __forceinline__ void project6_scaled(const double r[6], double c6, double c2, double out[6],
+                                                const Fp64Ones &k) {
   double rho[2][3];
   for (int g = 0; g < 2; ++g) {
-    const double r6 = ((r[g] + r[2 + g]) + r[4 + g]) * (1.0 / 6.0);
-    for (int a = 0; a < 3; ++a) rho[g][a] = fma(0.5, r[2 * a + g], r6);
+    const double r6 = fma(r[g], c6, fma(r[2 + g], c6, fmul(r[4 + g], c6, k)));
+    for (int a = 0; a < 3; ++a) rho[g][a] = fma(c2, r[2 * a + g], r6);
   }
   for (int a = 0; a < 3; ++a) {
     // psi_0(z0) = z1, psi_0(z1) = z0 (symmetric points)
-    out[2 * a] = fma(kZ1, rho[0][a], kZ0 * rho[1][a]);
-    out[2 * a + 1] = fma(kZ0, rho[0][a], kZ1 * rho[1][a]);
+    out[2 * a] = fma(kZ1, rho[0][a], fmul(kZ0, rho[1][a], k));
+    out[2 * a + 1] = fma(kZ0, rho[0][a], fmul(kZ1, rho[1][a], k));
   }
 }
 
-// Local kernel on one prism.  W[6] = w_q |det J_q| (straight: all equal).
+// out[2a+b] = sum_{t,g} r[(t,g)] lambda_a(t) psi_b(g)   (transpose of eval6)
+__device__ __forceinline__ void project6(const double r[6], double out[6], const Fp64Ones &k) {
+  project6_scaled(r, 1.0 / 6.0, 0.5, out, k);
+}
+
+// Local kernel on one prism.  W[6] = w_q |det J_q| (general prisms).
 // mode bit 0: F contributions, bit 1: adjoint contributions.
 template <int MODE>
 __device__ __forceinline__ void local(const double u[6], const double w[6], const double W[6],
-                                      double Fo[6], double Go[6]) {
+                                      double Fo[6], double Go[6], const Fp64Ones &k) {
   double uq[6];
-  eval6(u, uq);
+  eval6(u, uq, k);
   double P[6];
-  for (int q = 0; q < 6; ++q) P[q] = W[q] * uq[q];
+  for (int q = 0; q < 6; ++q) P[q] = fmul(W[q], uq[q], k);
   if (MODE & 1) {
     double r[6];
-    for (int q = 0; q < 6; ++q) r[q] = P[q] * uq[q];
-    project6(r, Fo);
+    for (int q = 0; q < 6; ++q) r[q] = fmul(P[q], uq[q], k);
+    project6(r, Fo, k);
   }
   if (MODE & 2) {
     double wq[6];
-    eval6(w, wq);
+    eval6(w, wq, k);
     double r[6];
-    for (int q = 0; q < 6; ++q) r[q] = (P[q] + P[q]) * wq[q];
-    project6(r, Go);
+    for (int q = 0; q < 6; ++q) r[q] = fmul(fadd(P[q], P[q], k), wq[q], k);
+    project6(r, Go, k);
   }
 }
 
-// Straight-prism variant: one weight for all points, applied after projection
-// would change nothing in cost, so it is applied to the point values.
+// Straight prism: one weight Wc = |2A| |h| / 12 for all six points, folded
+// into the projection's constants (Wc / 6, Wc / 2; twice those for the
+// adjoint's factor 2), so the point values need no weighting.
 template <int MODE>
 __device__ __forceinline__ void local_straight(const double u[6], const double w[6], double Wc,
-                                               double Fo[6], double Go[6]) {
+                                               double Fo[6], double Go[6], const Fp64Ones &k) {
   double uq[6];
-  eval6(u, uq);
-  double P[6];
-  for (int q = 0; q < 6; ++q) P[q] = Wc * uq[q];
+  eval6(u, uq, k);
+  const double c6 = fmul(Wc, 1.0 / 6.0, k), c2 = fmul(Wc, 0.5, k);
   if (MODE & 1) {
     double r[6];
-    for (int q = 0; q < 6; ++q) r[q] = P[q] * uq[q];
-    project6(r, Fo);
+    for (int q = 0; q < 6; ++q) r[q] = fmul(uq[q], uq[q], k);
+    project6_scaled(r, c6, c2, Fo, k);
   }
   if (MODE & 2) {
     double wq[6];
-    eval6(w, wq);
+    eval6(w, wq, k);
     double r[6];
-    const double W2 = Wc + Wc;
-    for (int q = 0; q < 6; ++q) r[q] = (W2 * uq[q]) * wq[q];
-    project6(r, Go);
+    for (int q = 0; q < 6; ++q) r[q] = fmul(uq[q], wq[q], k);
+    project6_scaled(r, fadd(c6, c6, k), Wc, Go, k);
   }
 }
 
@@ -138,7 +147,7 @@ template <int MODE>
 __device__ __forceinline__ void cell_layer(const int32_t *cmap_row, const int32_t *umap_row,
                                            const int32_t coff[6], const int32_t uoff[6], int l,
                                            const ColGeom &cg, const double *X, const double *u,
-                                           const double *w, double *F, double *G) {
+                                           const double *w, double *F, double *G, const Fp64Ones &k) {
   double uu[6], ww[6], Xl[6][3];
   int32_t ud[6];
   int ok = 1;
@@ -158,12 +167,12 @@ __device__ __forceinline__ void cell_layer(const int32_t *cmap_row, const int32_
         (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
   double Fo[6], Go[6];
   if (ok) {
-    const double Wc = cg.wdet * fabs(Xl[1][2] - Xl[0][2]);
-    local_straight<MODE>(uu, ww, Wc, Fo, Go);
+    const double Wc = fmul(cg.wdet, fabs(fsub(Xl[1][2], Xl[0][2], k)), k);
+    local_straight<MODE>(uu, ww, Wc, Fo, Go, k);
   } else {
     double W[6];
     general_weights(Xl, W);
-    local<MODE>(uu, ww, W, Fo, Go);
+    local<MODE>(uu, ww, W, Fo, Go, k);
   }
   for (int i = 0; i < 6; ++i) {
     if (MODE & 1) atomicAdd(F + ud[i], Fo[i]);
