@@ -869,6 +869,8 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.b = (double *)args[2].data;
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
+      p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
+      p.ncoord = args[0].space->ndofs;
       e = launch_mass_tp(p, s);
       break;
     }

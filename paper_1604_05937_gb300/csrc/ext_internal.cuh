@@ -218,6 +218,11 @@ struct MassTPLaunch {
   double *b;
   const int32_t *cell_layers = nullptr;  // variable layers
   double mean_layers = 0.0;
+  const double *base_xy = nullptr;       // the mesh's base coordinates, if it has them
+  int64_t ncoord = 0;                    // DoFs of the coordinate space (V (layers + 1))
+  // filled by launch_mass_tp when it runs the flagged form
+  const uint32_t *vflags = nullptr;      // bit d: coordinate DoF d verified straight
+  const double *hlay = nullptr;          // |z_{l+1} - z_l| of the reference column
 };
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
 

@@ -13,7 +13,10 @@
 // out column groups round-robin so resident warps sweep the mesh together.
 // Straightness is checked exactly as in the P1xP1 kernel; other prisms use the
 // 6-point rule with the general Jacobian.
+#include <cstdlib>
+
 #include "ext_internal.cuh"
+#include "fastdiv.cuh"
 
 namespace {
 
@@ -65,8 +68,50 @@ __device__ void tp_general(const double X[6][3], const double f[NH * NV], double
   }
 }
 
+// Flagged form (constant layers, mesh with base coordinates, a million
+// (column, layer) items or more): one pass reads the coordinate field once
+// and sets bit d of `flags` when coordinate DoF d sits at its vertex's base
+// x, y and at the height of its level in the column of vertex 0 (bitwise);
+// hlay[l] = |z_{l+1} - z_l| of that column.  A prism whose six vertex levels
+// are all flagged is straight with flat faces, so the cell kernel takes its
+// element matrix from the column's area and hlay[l] without loading its 18
+// coordinates; other prisms load them and take the general 6-point rule.
+__global__ void __launch_bounds__(256) k_tp_levels(const double *__restrict__ X, int layers,
+                                                   double *__restrict__ ztab, double *__restrict__ hlay) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > layers) return;
+  const double z = X[3 * (int64_t)m + 2];
+  ztab[m] = z;
+  if (m < layers) hlay[m] = fabs(X[3 * (int64_t)(m + 1) + 2] - z);
+}
+
+__global__ void __launch_bounds__(256) k_tp_vflags(const double *__restrict__ X, const double *__restrict__ xy,
+                                                   const double *__restrict__ ztab, int64_t n, FastDiv col,
+                                                   uint32_t *__restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwords = (n + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); w < nwords; w += (int64_t)gridDim.x * kWarps) {
+    const int64_t d = w * 32 + lane;
+    int ok = 0;
+    if (d < n) {
+      const uint32_t q = fdiv((uint32_t)d, col);
+      const uint32_t m = (uint32_t)d - q * col.d;
+      ok = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 0))) &
+           (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 1))) &
+           (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(__ldg(ztab + m)));
+    }
+    const unsigned int word = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) flags[w] = word;
+  }
+}
+
+__device__ __forceinline__ int vflag(const uint32_t *__restrict__ flags, int64_t d) {
+  return (int)((__ldg(flags + (d >> 5)) >> (uint32_t)(d & 31)) & 1u);
+}
+
 // VAR: column c has cell_layers[c] layers (lists taken at its bottom layer).
-template <int NH, int NV, bool VAR>
+// FLAGS: the flagged form (constant layers only).
+template <int NH, int NV, bool VAR, bool FLAGS>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -90,8 +135,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int64_t cd = cols[warp][lane].cm[2 * a];
-        x[a] = __ldg(p.X + 3 * cd + 0);
-        y[a] = __ldg(p.X + 3 * cd + 1);
+        if (FLAGS) {  // the base coordinates the flags were checked against (vertex = level-0 DoF / (layers + 1))
+          const int64_t v = cd / (layers + 1);
+          x[a] = __ldg(p.base_xy + 2 * v + 0);
+          y[a] = __ldg(p.base_xy + 2 * v + 1);
+        } else {
+          x[a] = __ldg(p.X + 3 * cd + 0);
+          y[a] = __ldg(p.X + 3 * cd + 1);
+        }
         cols[warp][lane].rx[a] = __double_as_longlong(x[a]);
         cols[warp][lane].ry[a] = __double_as_longlong(y[a]);
       }
@@ -114,18 +165,28 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
         const TPCol &ci = cols[warp][cl];
         double Xl[6][3];
         int ok = 1;
+        auto load_coords = [&]() {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          const int64_t cd = (int64_t)ci.cm[i] + (int64_t)l * p.coff[i];
-          Xl[i][0] = __ldg(p.X + 3 * cd + 0);
-          Xl[i][1] = __ldg(p.X + 3 * cd + 1);
-          Xl[i][2] = __ldg(p.X + 3 * cd + 2);
-          ok &= (__double_as_longlong(Xl[i][0]) == ci.rx[i >> 1]) & (__double_as_longlong(Xl[i][1]) == ci.ry[i >> 1]);
+          for (int i = 0; i < 6; ++i) {
+            const int64_t cd = (int64_t)ci.cm[i] + (int64_t)l * p.coff[i];
+            Xl[i][0] = __ldg(p.X + 3 * cd + 0);
+            Xl[i][1] = __ldg(p.X + 3 * cd + 1);
+            Xl[i][2] = __ldg(p.X + 3 * cd + 2);
+          }
+        };
+        if (FLAGS) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) ok &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+        } else {
+          load_coords();
+#pragma unroll
+          for (int i = 0; i < 6; ++i)
+            ok &= (__double_as_longlong(Xl[i][0]) == ci.rx[i >> 1]) & (__double_as_longlong(Xl[i][1]) == ci.ry[i >> 1]);
+          ok &= (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[2][2])) &
+                (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[4][2])) &
+                (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
+                (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
         }
-        ok &= (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[2][2])) &
-              (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[4][2])) &
-              (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
-              (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
         int32_t dof[NH * NV];
         double f[NH * NV], b[NH * NV];
 #pragma unroll
@@ -134,7 +195,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
           f[i] = __ldg(p.f + dof[i]);
         }
         if (ok) {
-          const double cc = ci.alpha * fabs(Xl[1][2] - Xl[0][2]);
+          const double cc = ci.alpha * (FLAGS ? __ldg(p.hlay + l) : fabs(Xl[1][2] - Xl[0][2]));
           if (NH == 1 && NV == 1) {
             b[0] = cc * f[0];
           } else if (NH == 1) {  // NV == 2
@@ -158,6 +219,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
             for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
           }
         } else {
+          if (FLAGS) load_coords();
           tp_general<NH, NV>(Xl, f, b);
         }
 #pragma unroll
@@ -174,7 +236,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
   }
 }
 
-template <int NH, int NV, bool VAR>
+template <int NH, int NV, bool VAR, bool FLAGS>
 cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   const double lay = VAR ? p.mean_layers : (double)p.layers;
   int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
@@ -182,28 +244,27 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sms = 0;
-  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0);
+  static int resident[12] = {0}, sms = 0;
+  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0);
   if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR>, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS>, kWarps * 32, 0);
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  k_mass_tp<NH, NV, VAR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_tp<NH, NV, VAR, FLAGS><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
 
-template <bool VAR>
+template <bool VAR, bool FLAGS>
 cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
-  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR>(p, s);
-  if (p.nh == 1) return launch_tp<1, 2, VAR>(p, s);
-  if (p.nv == 1) return launch_tp<3, 1, VAR>(p, s);
-  return launch_tp<3, 2, VAR>(p, s);
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS>(p, s);
+  return launch_tp<3, 2, VAR, FLAGS>(p, s);
 }
-
 
 // p-adaptive DG (EXT_K_MASS_DGP): every cell carries its own element, DG0|DG1
 // x DG0|DG1, told apart by its DoF count K = NH NV (1, 2, 3, 6).  The library
@@ -361,9 +422,52 @@ cudaError_t launch_dgp_kind(const MassDGPLaunch &p, cudaStream_t s) {
 
 }  // namespace
 
+// The flagged form runs on constant layers when the mesh has base
+// coordinates and the launch has a million (column, layer) items or more
+// (EXTMESH_TP_FLAGS=1 / 0, read once per process: at any size / never), and
+// its scratch (one bit per coordinate DoF and two level tables) can be taken
+// from the stream-ordered pool; otherwise every lane loads its coordinates.
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
-  return p.cell_layers ? launch_tp_pair<true>(p, s) : launch_tp_pair<false>(p, s);
+  if (p.cell_layers) return launch_tp_pair<true, false>(p, s);
+  static int flags_env = -1;
+  if (flags_env < 0) {
+    const char *ev = getenv("EXTMESH_TP_FLAGS");
+    flags_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
+  }
+  const double items = (double)p.ncells * (double)p.layers;
+  const bool want = p.base_xy && p.ncoord > 0 && flags_env != 0 && (flags_env == 1 || items >= 1.0e6);
+  char *scr = nullptr;
+  const size_t fbytes = (sizeof(uint32_t) * (size_t)((p.ncoord + 31) / 32) + 255) & ~(size_t)255;
+  const size_t zbytes = (sizeof(double) * (size_t)(p.layers + 1) + 255) & ~(size_t)255;
+  if (want && cudaMallocAsync(reinterpret_cast<void **>(&scr), fbytes + 2 * zbytes, s) != cudaSuccess) {
+    (void)cudaGetLastError();  // not sticky: the plain form needs no scratch
+    scr = nullptr;
+  }
+  if (!scr) return launch_tp_pair<false, false>(p, s);
+  MassTPLaunch q = p;
+  uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
+  double *ztab = reinterpret_cast<double *>(scr + fbytes);
+  double *hlay = reinterpret_cast<double *>(scr + fbytes + zbytes);
+  q.vflags = flags;
+  q.hlay = hlay;
+  static int sms = 0, res_vf = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res_vf, k_tp_vflags, 256, 0);
+    if (res_vf < 1) res_vf = 1;
+  }
+  int64_t gv = ((p.ncoord + 31) / 32 + kWarps - 1) / kWarps;
+  if (gv > (int64_t)res_vf * sms) gv = (int64_t)res_vf * sms;
+  if (gv < 1) gv = 1;
+  k_tp_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, ztab, hlay);
+  k_tp_vflags<<<(unsigned)gv, 256, 0, s>>>(p.X, p.base_xy, ztab, p.ncoord, make_fastdiv((uint32_t)(p.layers + 1)), flags);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_tp_pair<false, true>(q, s);
+  const cudaError_t ef = cudaFreeAsync(scr, s);
+  return e != cudaSuccess ? e : ef;
 }
 
 cudaError_t launch_mass_dgp(const MassDGPLaunch &p, cudaStream_t s) {

@@ -251,8 +251,9 @@ def test_mass_general_geometry_partial(layers, with_xy):
                                   {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_GATHER": "0",
                                    "EXTMESH_MASS_FACTORED": "0"},
                                   {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_GATHER": "0",
-                                   "EXTMESH_MASS_FACTORED": "1"}],
-                         ids=["split", "single", "split-nogather", "split-unfactored", "split-factored"])
+                                   "EXTMESH_MASS_FACTORED": "1"},
+                                  {"EXTMESH_TP_FLAGS": "1"}],
+                         ids=["split", "single", "split-nogather", "split-unfactored", "split-factored", "tp-flags"])
 def test_mass_forced_form(form):
     """Every form of the P1xP1 launch passes the same parity tests: the split
     forms (the default for launches of a million items or more) -- the gather
@@ -263,7 +264,9 @@ def test_mass_forced_form(form):
     single-pass kernel (the default below a million items, and the fallback
     when the split form's scratch cannot be allocated), each forced by
     EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and EXTMESH_MASS_FACTORED in a
-    child process."""
+    child process; and the nine-space kernels' flagged form (straightness
+    bits per coordinate DoF, the default from a million items) forced at every
+    size by EXTMESH_TP_FLAGS."""
     import os
     import subprocess
     import sys
@@ -534,6 +537,43 @@ def test_mass_tp_parity(name, h, v, n, layers, order, perturb):
     f = meshgen.uniform_field(osp.ndofs, 602)
     ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
     O.set_tp_element(h, v)
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    sp = E.Space(gm, O.DELTA[name])
+    b = sp.zeros()
+    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, to_dev(X), E.EXT_READ), (sp, to_dev(f), E.EXT_READ), (sp, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(host(b), ref, absr)
+
+
+@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1"])
+def test_mass_tp_flags_partial(name):
+    """Over a million (column, layer) items the nine-space kernels take their
+    flagged form (one straightness bit per coordinate DoF against the base
+    coordinates and the level heights); columns moved in x, y from some level
+    up, single lifted levels and a level-0 vertex moved off its base position
+    must send exactly the prisms that touch them to the general 6-point rule."""
+    n, layers = 72, 100
+    m = meshgen.tri_mesh(n, seed=650, order="rcm")
+    gm = E.Mesh(m.cells, m.xy, layers)
+    csp, X = O.coords(m.cells, m.xy, layers)
+    Xr = X.reshape(-1, 3).copy()
+    rng = np.random.default_rng(651)
+    L1 = layers + 1
+    lean = rng.choice(m.nverts, m.nverts // 40, replace=False)
+    for v in lean:
+        lv = int(rng.integers(0, L1))
+        Xr[v * L1 + lv:v * L1 + L1, 0] += 0.1 / n
+        Xr[v * L1 + lv:v * L1 + L1, 1] -= 0.05 / n
+    lift = rng.choice(np.setdiff1d(np.arange(m.nverts), lean), m.nverts // 40, replace=False)
+    for v in lift:
+        Xr[v * L1 + int(rng.integers(0, L1)), 2] += 0.3 / layers
+    X = Xr.reshape(-1)
+    h = {"CG1": O.CG1, "DG0": O.DG0, "DG1": O.DG1}
+    osp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    f = meshgen.uniform_field(osp.ndofs, 652)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.set_tp_element(h[name[:3]], h[name[4:]])
     O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
     cs = E.Space(gm, "CG1xCG1", ncomp=3)
     sp = E.Space(gm, O.DELTA[name])
