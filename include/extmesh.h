@@ -130,7 +130,14 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   Sec. 4.1.2 (delta: CG1xCG1 {1,0,0,0,0,0}, CG1xDG0 {0,1,..},
  *                   CG1xDG1 {0,2,..}, DG0xCG1 {..,1,0}, DG0xDG0 {..,0,1},
  *                   DG0xDG1 {..,0,2}, DG1xCG1 {..,3,0}, DG1xDG0 {..,0,3},
- *                   DG1xDG1 {..,0,6}); f and b share one numbering.
+ *                   DG1xDG1 {..,0,6}); f and b share one numbering.  From a
+ *                   million (column, layer) items on a mesh with base
+ *                   coordinates and constant layers, a first kernel sets one
+ *                   straightness bit per coordinate DoF (scratch from the
+ *                   stream-ordered pool: 1 bit per coordinate DoF and two
+ *                   level tables), and the cell kernel tests those bits
+ *                   instead of comparing each prism's coordinates; without
+ *                   the scratch, or with EXTMESH_TP_FLAGS=0, it compares them.
  * EXT_K_HFACET_MASS [coords READ, f READ, b INC] on prisms, over the horizontal
  *                   facets ((2,0),(c,m)), m = 0..lambda, of every column
  *                   (Algorithm 3 with d2 = 0): b_i += int_F f_h phi_i ds on the
