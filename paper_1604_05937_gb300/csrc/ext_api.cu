@@ -94,9 +94,11 @@ static int64_t derive_edges(int kind, int64_t ncells, const int32_t *cv, std::ve
 // diagonal weight is the sum of the row's neighbour weights (twice the sum
 // of alpha_c around a).  Rows list a itself first, then its neighbours in
 // ascending order; neighbour weights are summed in ascending cell order.
+// An entry carries, instead of the vertex j, the first DoF j col of j's
+// CG1xCG1 column (col = layers + 1 levels; the DoF of level m is j col + m).
 // Also the cells around every vertex, ascending.  Returns false (rows not
 // built) when the entry count does not fit int32.
-static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const double *xy,
+static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const double *xy, int64_t col,
                               std::vector<int32_t> &vrow, std::vector<double2> &vent,
                               std::vector<int32_t> &vcrow, std::vector<int32_t> &vcells) {
   std::vector<double> alpha((size_t)nc);
@@ -144,8 +146,8 @@ static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const d
     nb.resize(w);
     double diag = 0.0;
     for (const auto &q : nb) diag += q.second;
-    vent.push_back(entry(diag, (int32_t)a));
-    for (const auto &q : nb) vent.push_back(entry(q.second, q.first));
+    vent.push_back(entry(diag, (int32_t)(a * col)));
+    for (const auto &q : nb) vent.push_back(entry(q.second, (int32_t)(q.first * col)));
     if (vent.size() >= (size_t)INT32_MAX) return false;
     vrow[(size_t)a + 1] = (int32_t)vent.size();
   }
@@ -254,7 +256,8 @@ static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, cons
   if (e == cudaSuccess && kind == EXT_TRI && base_xy_host && !var && nverts > 0 && ncells > 0) {
     std::vector<int32_t> vrow, vcrow, vcells;
     std::vector<double2> vent;
-    if (build_vertex_rows(nverts, ncells, cell_verts_host, base_xy_host, vrow, vent, vcrow, vcells)) {
+    if (build_vertex_rows(nverts, ncells, cell_verts_host, base_xy_host, (int64_t)layers + 1, vrow, vent, vcrow,
+                          vcells)) {
       const size_t rb = sizeof(int32_t) * vrow.size(), eb = sizeof(double2) * vent.size();
       const size_t cb = sizeof(int32_t) * vcells.size();
       if ((e = cudaMalloc(&m->d_vrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vent, eb)) == cudaSuccess &&

@@ -60,9 +60,10 @@ struct ext_mesh {
   void *host = nullptr;             // host-side copies (ext_api.cu)
   // triangle meshes with base coordinates and constant layers: the P1 mass
   // matrix of the base triangulation as vertex rows (row a: a itself, then
-  // its neighbours in ascending order; entry (weight, vertex) with the
-  // vertex in the low 32 bits of the second double) and the cells around
-  // every vertex in ascending order (the P1xP1 gather form)
+  // its neighbours in ascending order; entry (weight, first DoF j (layers+1)
+  // of vertex j's CG1xCG1 column, in the low 32 bits of the second double))
+  // and the cells around every vertex in ascending order (the P1xP1 gather
+  // form)
   int32_t *d_vrow = nullptr;    // nverts + 1
   double2 *d_vent = nullptr;    // d_vrow[nverts] entries
   int32_t *d_vcrow = nullptr;   // nverts + 1

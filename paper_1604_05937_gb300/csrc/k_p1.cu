@@ -1194,7 +1194,7 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
         if (t < deg[u]) {
           const double2 en = __ldg(vent + r0[u] + t);
           ev[u] = en.x;
-          wv[u] = __ldg(W + (int64_t)(uint32_t)__double_as_longlong(en.y) * col.d + mm[u]);
+          wv[u] = __ldg(W + (int64_t)(int32_t)__double_as_longlong(en.y) + mm[u]);
         }
       }
 #pragma unroll

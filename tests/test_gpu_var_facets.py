@@ -154,6 +154,45 @@ def test_var_mass_parity(kernel, n, maxlevel, kind, perturb):
     close(host(b), ref, absr)
 
 
+@pytest.mark.parametrize("n,maxlevel,kind", [(30, 20, "random"), (100, 100, "bathymetry")])
+def test_var_mass_partial(n, maxlevel, kind):
+    """Variable layers with some vertex columns moved in x, y from a level up
+    and some single levels lifted: the prisms touching them take the general
+    6-point rule, the rest the straight forms (on the larger case, over a
+    million items, the gather form with its regular levels and the per-cell
+    pass at the column ends; the random ranges of the smaller case leave gaps)."""
+    m = meshgen.tri_mesh(n, seed=760 + n, order="rcm")
+    gm, first, lay = var_mesh(m, maxlevel, 761, kind)
+    ocs = O.number_var(m.cells, m.nverts, first, lay, O.DELTA["CG1xCG1"])
+    _, X = O.coords_var(m.cells, m.xy, first, lay)
+    Xr = X.reshape(-1, 3).copy()
+    # vertex v's column: DoFs start[v] .. start[v] + (hi - lo); the numbering
+    # puts the vertex columns first, in vertex order
+    lo = np.full(m.nverts, 1 << 30)
+    hi = np.full(m.nverts, -1)
+    for a in range(3):
+        np.minimum.at(lo, m.cells[:, a], first)
+        np.maximum.at(hi, m.cells[:, a], first + lay)
+    start = np.concatenate([[0], np.cumsum(hi - lo + 1)])
+    rng = np.random.default_rng(762)
+    for v in rng.choice(m.nverts, m.nverts // 30, replace=False):
+        k = int(rng.integers(0, hi[v] - lo[v] + 1))
+        Xr[start[v] + k:start[v + 1], 0] += 0.1 / n
+    for v in rng.choice(m.nverts, m.nverts // 30, replace=False):
+        Xr[start[v] + int(rng.integers(0, hi[v] - lo[v] + 1)), 2] += 0.2 / maxlevel
+    X = Xr.reshape(-1)
+    f = meshgen.uniform_field(ocs.ndofs, 763)
+    ref, absr = np.zeros(ocs.ndofs), np.zeros(ocs.ndofs)
+    O.par_loop(O.K_MASS, m.cells, ocs.layers, [(ocs, X, 3, O.READ), (ocs, f, 1, O.READ), (ocs, ref, 1, O.INC, absr)],
+               cell_first=first, cell_layers=lay)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    ps = E.Space(gm, "CG1xCG1")
+    b = torch.full((ps.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, to_dev(X), E.EXT_READ), (ps, to_dev(f), E.EXT_READ), (ps, b, E.EXT_WRITE))
+    E.ext_sync_check()
+    close(host(b), ref, absr)
+
+
 @pytest.mark.parametrize("name,h,v", O.TP_PAIRS)
 @pytest.mark.parametrize("n,maxlevel,kind,perturb", [(5, 4, "bathymetry", 0.0), (13, 30, "random", 0.0),
                                                       (7, 6, "random", 0.05)])
