@@ -508,9 +508,10 @@ def load_traffic(kernel: str):
 
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
-def cpu_baseline(m, L, seconds: float, steps: int = 1):
+def cpu_baseline(m, L, seconds: float, steps: int = 1, warmup: int = 0):
     """The oracle (serial C, one core) on the first S base columns of the same
-    workload, all layers; S grows until one pass takes about `seconds`/steps."""
+    workload, all layers; S grows until one pass takes about `seconds`/steps;
+    `warmup` untimed passes, then `steps` timed ones (the minimum is kept)."""
     import oracle as O
     X_sp, X = O.coords(m.cells, m.xy, L)
     p1 = O.number(m.cells, m.nverts, L, P1_DELTA)
@@ -536,6 +537,8 @@ def cpu_baseline(m, L, seconds: float, steps: int = 1):
         S = min(m.ncells, S * 4)
         dt = one(S)
     S = min(m.ncells, max(1, int(S * target / max(dt, 1e-9))))
+    for _ in range(warmup):
+        one(S)
     times = [one(S) for _ in range(steps)]
     t = min(times)
     # valuable bytes of the sample: the touched vertex columns, the S cell
@@ -1100,8 +1103,10 @@ def run_reference(args, rank, world):
         return None
     m = meshgen.tri_mesh(N_CFG2, seed=SEED, order="rcm")
     L = LAYERS_CFG2
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    cb = cpu_baseline(m, L, per_step * args.steps, steps=args.steps)
+    # the whole arm stays near a minute and a half whatever K and W are: each
+    # step is a sample of that share (at most 2 s, at least 0.05 s)
+    per_step = min(2.0, max(0.05, 90.0 / max(1, args.steps + args.warmup)))
+    cb = cpu_baseline(m, L, per_step * args.steps, steps=args.steps, warmup=args.warmup)
     C = m.ncells
     line = {
         "impl": "reference",
