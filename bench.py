@@ -491,17 +491,30 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     return line
 
 
+def code_hash(path: str) -> str:
+    """SHA-256 of a source file's code: // comments, trailing blanks and blank
+    lines removed, so that editing a comment keeps a kernel's counters valid
+    and any change to its code voids them."""
+    import hashlib
+    import re
+    lines = []
+    with open(path) as f:
+        for line in f:
+            line = re.sub(r"//.*$", "", line).rstrip()
+            if line:
+                lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def load_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel's source has changed since the counters were taken."""
-    import hashlib
+    when the kernel's code has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)[kernel]
-        with open(os.path.join(ROOT, t["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
-                return None
+        if code_hash(os.path.join(ROOT, t["source"])) != t["code_sha256"]:
+            return None
         return t["bytes_per_launch"]
     except Exception:
         return None

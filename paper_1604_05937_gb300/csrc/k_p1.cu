@@ -827,9 +827,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
 // launch runs
 //   k_levels            the level table (z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|),
 //                       |h_m|) from the column of vertex 0 (DoFs 0 .. layers),
-//   k_vsum_tab          w per DoF, stored; a NaN pattern instead where the DoF
+//   k_vsum_bulk         w per DoF, stored; a NaN pattern instead where the DoF
 //                       or a vertical neighbour of it is off its column's base
-//                       x, y or its level's height,
+//                       x, y or its level's height (coordinates and f staged in
+//                       shared memory by bulk copies; k_vsum_tab is the same pass
+//                       with plain loads, for X or f not 16-byte aligned),
 //   k_vgather           b per DoF: one thread forms the row sum over the
 //                       vertex row (no atomics) and overwrites b (WRITE) or
 //                       adds to it (INC); a 32-DoF chunk whose sums came out
