@@ -105,13 +105,47 @@ __global__ void __launch_bounds__(256) k_tp_vflags(const double *__restrict__ X,
   }
 }
 
+// Element vector of a straight prism with c = alpha |h|: Mh (x) Mv f in closed
+// form for NH horizontal and NV vertical nodes.
+template <int NH, int NV>
+__device__ __forceinline__ void tp_closed(double cc, const double f[NH * NV], double b[NH * NV]) {
+  if (NH == 1 && NV == 1) {
+    b[0] = cc * f[0];
+  } else if (NH == 1) {  // NV == 2
+    const double c2 = cc + cc;
+    b[0] = fma(c2, f[0], cc * f[1]);
+    b[1] = fma(c2, f[1], cc * f[0]);
+  } else if (NV == 1) {  // NH == 3
+    const double cS = cc * ((f[0] + f[1]) + f[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
+  } else {  // NH == 3, NV == 2: b_{a,beta} = c (t_{a,beta} + T_beta),
+            // t_{a,beta} = 2 f_{a,beta} + f_{a,1-beta}, T_beta = sum_a t_{a,beta}
+    double t[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
+      t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
+    }
+    const double K0 = cc * ((t[0] + t[2]) + t[4]), K1 = cc * ((t[1] + t[3]) + t[5]);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
+  }
+}
+
+#ifndef EXT_TP_UNROLL
+#define EXT_TP_UNROLL 4  // (column, layer) items per lane per step of the flagged form
+#endif
+
 __device__ __forceinline__ int vflag(const uint32_t *__restrict__ flags, int64_t d) {
   return (int)((__ldg(flags + (d >> 5)) >> (uint32_t)(d & 31)) & 1u);
 }
 
 // VAR: column c has cell_layers[c] layers (lists taken at its bottom layer).
-// FLAGS: the flagged form (constant layers only).
-template <int NH, int NV, bool VAR, bool FLAGS>
+// FLAGS: the flagged form (constant layers only); MULTI (with FLAGS): several
+// items per lane per step, a separate instantiation so that its registers do
+// not lower the occupancy of the one-item loop.
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -160,6 +194,61 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
       cl = lane / layers;
       l = lane - cl * layers;
     }
+    if (FLAGS && !VAR && MULTI) {
+      // U items per lane per step, all their loads (straightness bits, layer
+      // heights, f) issued before any arithmetic or increment
+      constexpr int U = EXT_TP_UNROLL;
+      for (int base = 0; base < nitems; base += 32 * U) {
+        int32_t dof[U][NH * NV];
+        double f[U][NH * NV], hl[U];
+        int ok[U], cls[U], ls[U];
+        bool valid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          valid[u] = base + u * 32 + lane < nitems;
+          cls[u] = cl;
+          ls[u] = l;
+          ok[u] = 1;
+          hl[u] = 0.0;
+          if (valid[u]) {
+            const TPCol &ci = cols[warp][cl];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+            hl[u] = __ldg(p.hlay + l);
+#pragma unroll
+            for (int i = 0; i < NH * NV; ++i) {
+              dof[u][i] = ci.fm[i] + l * p.off[i];
+              f[u][i] = __ldg(p.f + dof[u][i]);
+            }
+          }
+          l += 32;
+          while (l >= layers) { l -= layers; ++cl; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!valid[u]) continue;
+          const TPCol &ci = cols[warp][cls[u]];
+          double b[NH * NV];
+          if (ok[u]) {
+            tp_closed<NH, NV>(ci.alpha * hl[u], f[u], b);
+          } else {
+            double Xl[6][3];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              const int64_t cd = (int64_t)ci.cm[i] + (int64_t)ls[u] * p.coff[i];
+              Xl[i][0] = __ldg(p.X + 3 * cd + 0);
+              Xl[i][1] = __ldg(p.X + 3 * cd + 1);
+              Xl[i][2] = __ldg(p.X + 3 * cd + 2);
+            }
+            tp_general<NH, NV>(Xl, f[u], b);
+          }
+#pragma unroll
+          for (int i = 0; i < NH * NV; ++i) atomicAdd(p.b + dof[u][i], b[i]);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     for (int base = 0; base < nitems; base += 32) {
       if (base + lane < nitems) {
         const TPCol &ci = cols[warp][cl];
@@ -195,29 +284,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
           f[i] = __ldg(p.f + dof[i]);
         }
         if (ok) {
-          const double cc = ci.alpha * (FLAGS ? __ldg(p.hlay + l) : fabs(Xl[1][2] - Xl[0][2]));
-          if (NH == 1 && NV == 1) {
-            b[0] = cc * f[0];
-          } else if (NH == 1) {  // NV == 2
-            const double c2 = cc + cc;
-            b[0] = fma(c2, f[0], cc * f[1]);
-            b[1] = fma(c2, f[1], cc * f[0]);
-          } else if (NV == 1) {  // NH == 3
-            const double cS = cc * ((f[0] + f[1]) + f[2]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
-          } else {  // NH == 3, NV == 2: b_{a,beta} = c (t_{a,beta} + T_beta),
-                    // t_{a,beta} = 2 f_{a,beta} + f_{a,1-beta}, T_beta = sum_a t_{a,beta}
-            double t[6];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
-              t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
-            }
-            const double K0 = cc * ((t[0] + t[2]) + t[4]), K1 = cc * ((t[1] + t[3]) + t[5]);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
-          }
+          tp_closed<NH, NV>(ci.alpha * (FLAGS ? __ldg(p.hlay + l) : fabs(Xl[1][2] - Xl[0][2])), f, b);
         } else {
           if (FLAGS) load_coords();
           tp_general<NH, NV>(Xl, f, b);
@@ -236,7 +303,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
   }
 }
 
-template <int NH, int NV, bool VAR, bool FLAGS>
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI>
 cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   const double lay = VAR ? p.mean_layers : (double)p.layers;
   int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
@@ -244,26 +311,37 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[12] = {0}, sms = 0;
-  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0);
+  static int resident[16] = {0}, sms = 0;
+  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0) + (MULTI ? 4 : 0);
   if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS>, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS, MULTI>, kWarps * 32,
+                                                  0);
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  k_mass_tp<NH, NV, VAR, FLAGS><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_tp<NH, NV, VAR, FLAGS, MULTI><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
 
+// the flagged form takes several items per lane from EXT_TP_MULTI_LAYERS
+// layers on (a warp's group of up to 32 columns then fills the lanes' slots)
+#ifndef EXT_TP_MULTI_LAYERS
+#define EXT_TP_MULTI_LAYERS 8
+#endif
+template <bool VAR, bool FLAGS, bool MULTI>
+cudaError_t launch_tp_kind(const MassTPLaunch &p, cudaStream_t s) {
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS, MULTI>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS, MULTI>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS, MULTI>(p, s);
+  return launch_tp<3, 2, VAR, FLAGS, MULTI>(p, s);
+}
 template <bool VAR, bool FLAGS>
 cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
-  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS>(p, s);
-  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS>(p, s);
-  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS>(p, s);
-  return launch_tp<3, 2, VAR, FLAGS>(p, s);
+  if (FLAGS && !VAR && p.layers >= EXT_TP_MULTI_LAYERS) return launch_tp_kind<VAR, FLAGS, true>(p, s);
+  return launch_tp_kind<VAR, FLAGS, false>(p, s);
 }
 
 // p-adaptive DG (EXT_K_MASS_DGP): every cell carries its own element, DG0|DG1
