@@ -121,6 +121,50 @@ def test_tilted_prism_volume_and_symmetry():
     assert abs(M[2, 2] - M[0, 0]) > 1e-2 * M[0, 0]
 
 
+@pytest.mark.parametrize("n,layers,order", [(6, 4, "rcm"), (9, 7, "random")])
+def test_mass_is_kronecker_product_on_straight_extrusions(n, layers, order):
+    """On a straight extrusion with flat levels the P1xP1 mass matrix is
+    Mh (x) Mv: Mh the base triangulation's P1 mass matrix as vertex rows (the
+    weight of neighbour j is the sum of |2A_c|/144 over the cells holding edge
+    (a, j), the diagonal weight the row's sum) and Mv the column's
+    |h_{m-1}| f_{m-1} + 2 (|h_{m-1}| + |h_m|) f_m + |h_m| f_{m+1} -- the
+    factorisation the library's gather form evaluates.  Built here with numpy
+    from the base mesh alone, it equals the oracle's cell-by-cell assembly
+    (6-point rule, full Jacobian) within the parity tolerance; non-uniform
+    layer heights make Mv level dependent."""
+    m = meshgen.tri_mesh(n, seed=170 + n, order=order)
+    sp, csp, X = _mesh_space(m, layers, P1)
+    # non-uniform flat levels: move every level to z_m = (m / L)^1.5
+    Xr = X.reshape(-1, 3).copy()
+    lev = np.tile(np.arange(layers + 1), m.nverts)  # level of CG1xCG1 DoF v (L+1) + m
+    Xr[:, 2] = (lev / layers) ** 1.5
+    X = Xr.reshape(-1)
+    f = meshgen.uniform_field(sp.ndofs, 171)
+    absr = np.zeros(sp.ndofs)
+    ref = _mass(m.cells, layers, csp, X, sp, f, absr)
+    # Mh as vertex rows
+    V = m.nverts
+    xy = m.xy
+    c = m.cells
+    alpha = np.abs((xy[c[:, 1], 0] - xy[c[:, 0], 0]) * (xy[c[:, 2], 1] - xy[c[:, 0], 1])
+                   - (xy[c[:, 2], 0] - xy[c[:, 0], 0]) * (xy[c[:, 1], 1] - xy[c[:, 0], 1])) / 144.0
+    Mh = np.zeros((V, V))
+    for k in range(3):
+        a, b = c[:, k], c[:, (k + 1) % 3]
+        np.add.at(Mh, (a, b), alpha)
+        np.add.at(Mh, (b, a), alpha)
+    Mh[np.arange(V), np.arange(V)] = Mh.sum(axis=1)
+    # Mv from the level heights
+    z = (np.arange(layers + 1) / layers) ** 1.5
+    h = np.abs(np.diff(z))
+    Mv = np.zeros((layers + 1, layers + 1))
+    for l in range(layers):
+        Mv[l:l + 2, l:l + 2] += h[l] * np.array([[2.0, 1.0], [1.0, 2.0]])
+    F = f.reshape(V, layers + 1)  # vertex columns are contiguous (Algorithm 1)
+    got = (Mh @ F @ Mv.T).reshape(-1)
+    assert np.all(np.abs(got - ref) <= 1e-12 * absr + 1e-300)
+
+
 def test_mass_action_symmetric_and_bounded():
     layers = 6
     m = meshgen.tri_mesh(6, seed=12, order="random")
