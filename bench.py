@@ -125,6 +125,15 @@ def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, 
     return sum(p1_counts(ndofs, items, ncells, layers, var, nedges))
 
 
+def tp_kernels(items: int) -> int:
+    """Kernels of one EXT_K_MASS_TP launch on constant layers over a mesh with
+    base coordinates: the level table, the straightness flags and the cell
+    kernel from a million (column, layer) items (EXTMESH_TP_FLAGS=1 / 0: at any
+    size / never), the cell kernel alone otherwise."""
+    env = os.environ.get("EXTMESH_TP_FLAGS", "")
+    return 3 if env == "1" or (env != "0" and items >= 1_000_000) else 1
+
+
 def base_edges(cells) -> int:
     """Distinct edges of a base triangulation (C x 3 vertex ids)."""
     c = np.asarray(cells, dtype=np.int64)
@@ -880,7 +889,7 @@ def run_cfg6(args, rank, world, local):
                 fn()
                 reps = max(3, min(args.steps, 10))
                 t = time_kernel(fn, reps, stream, flush, pre=b.zero_)[0]
-                launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None else 1)
+                launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None else tp_kernels(C * L))
                 work = p1_ops(V * (L + 1), C * (L + 1), C, L) if ops is None else ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
                 vb = vb_paper + 24 * C + 4 * sp.k * C
