@@ -78,27 +78,41 @@ int64_t oracle_derive_edges(int32_t nvc, int64_t ncells, const int32_t *cell_ver
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1: number every extruded entity, vertical innermost.           */
+/* The numbering of Sec. 3.2 (Algorithm 1), written from the property it    */
+/* establishes rather than as the algorithm's loop.  Base entity g (index   */
+/* dimension-major: vertices, edges, cells, each ascending) owns one column */
+/* of extruded entities.  Along that column every extruded entity has a     */
+/* height rank s counted from the bottom: the horizontal copy at level l    */
+/* has s = 2l, the vertical entity spanning layer l has s = 2l + 1, so a    */
+/* column with levels lo..hi has ranks 2 lo .. 2 hi.  The numbers are       */
+/* handed out in increasing (g, s), each extruded entity taking as many     */
+/* consecutive numbers as it carries DoFs.  A column is then one contiguous */
+/* range, ordered from its bottom to its top (vertical innermost).          */
+/* lo/hi NULL: every column spans 0..layers; dent NULL: an extruded entity  */
+/* of type t = 2 d1 + d2 carries delta[t] DoFs, else entity g carries        */
+/* dent[2g + d2].                                                           */
 /* ------------------------------------------------------------------------ */
-int64_t oracle_alg1(const int64_t N[3], int32_t layers, const int32_t delta[6],
-                    int64_t *const first[6]) {
-  int64_t c = 0;
-  for (int d1 = 0; d1 <= 2; ++d1) {           /* base entities, dimension-major */
-    for (int64_t i = 0; i < N[d1]; ++i) {     /* ... index ascending            */
-      for (int32_t l = 0; l < layers; ++l) {  /* layers                          */
-        for (int d2 = 0; d2 <= 1; ++d2) {     /* horizontal entity, then vertical */
-          int t = 2 * d1 + d2;
-          if (first[t]) first[t][i * (layers + 1 - d2) + l] = c;
-          c += delta[t];
-        }
+static int64_t number_by_rank(const int64_t N[3], int32_t maxlevel, const int32_t *lo, const int32_t *hi,
+                              const int32_t *delta, const int32_t *dent, int64_t *const first[6]) {
+  int64_t next = 0, g = 0;
+  for (int d1 = 0; d1 <= 2; ++d1) {
+    for (int64_t i = 0; i < N[d1]; ++i, ++g) {
+      const int64_t s_lo = 2 * (int64_t)(lo ? lo[g] : 0), s_hi = 2 * (int64_t)(hi ? hi[g] : maxlevel);
+      for (int64_t s = s_lo; s <= s_hi; ++s) {
+        const int d2 = (int)(s % 2);    /* odd rank: a vertical entity */
+        const int64_t level = s / 2;    /* its level (horizontal) or layer (vertical) */
+        const int t = 2 * d1 + d2;
+        if (first[t]) first[t][i * (maxlevel + 1 - d2) + level] = next;
+        next += dent ? dent[2 * g + d2] : delta[t];
       }
-      /* the top horizontal entity of the column */
-      int t = 2 * d1;
-      if (first[t]) first[t][i * (layers + 1) + layers] = c;
-      c += delta[t];
     }
   }
-  return c;
+  return next;
+}
+
+int64_t oracle_alg1(const int64_t N[3], int32_t layers, const int32_t delta[6],
+                    int64_t *const first[6]) {
+  return number_by_rank(N, layers, NULL, NULL, delta, NULL, first);
 }
 
 static int32_t nentities(int32_t nvc, int d) { return d == 2 ? 1 : nvc; }
@@ -138,15 +152,36 @@ int oracle_base_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
   return 0;
 }
 
-/* Algorithm 2: offset of stencil DoF i = delta((d,0)) + delta((d,1)) where d
- * is the base entity dimension E_S(i) of that DoF. */
+/* Offsets (Sec. 3.3, Algorithm 2), from what they are for: the explicit
+ * list of a cell at layer l + 1 is its list at layer l plus the offsets.
+ * One base cell with its own nvc vertices and nvc edges is numbered over two
+ * layers, its explicit lists at layers 0 and 1 are read off the tables, and
+ * the offsets are their differences. */
+static void list_at_layer(int32_t nvc, int32_t layers, const int32_t delta[6], int64_t *const first[6],
+                          int32_t l, int64_t *list) {
+  int32_t j = 0;
+  for (int d = 0; d <= 2; ++d)
+    for (int32_t e = 0; e < nentities(nvc, d); ++e) {
+      for (int32_t q = 0; q < delta[2 * d]; ++q) list[j++] = first[2 * d][e * (layers + 1) + l] + q;
+      for (int32_t q = 0; q < delta[2 * d]; ++q) list[j++] = first[2 * d][e * (layers + 1) + l + 1] + q;
+      for (int32_t q = 0; q < delta[2 * d + 1]; ++q) list[j++] = first[2 * d + 1][e * layers + l] + q;
+    }
+}
+
 void oracle_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
-  int32_t i = 0;
-  for (int d = 0; d <= 2; ++d) {
-    int32_t per = 2 * delta[2 * d] + delta[2 * d + 1];
-    for (int32_t e = 0; e < nentities(nvc, d); ++e)
-      for (int32_t q = 0; q < per; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];
-  }
+  const int64_t N[3] = {nvc, nvc, 1};
+  int64_t tab[6][2 * 3 * 4];  /* at most 4 entities per dimension, 3 levels */
+  int64_t *first[6];
+  for (int t = 0; t < 6; ++t) first[t] = tab[t];
+  number_by_rank(N, 2, NULL, NULL, delta, NULL, first);
+  const int32_t k = oracle_stencil_size(nvc, delta);
+  int64_t *l0 = (int64_t *)malloc(sizeof(int64_t) * (k > 0 ? k : 1));
+  int64_t *l1 = (int64_t *)malloc(sizeof(int64_t) * (k > 0 ? k : 1));
+  list_at_layer(nvc, 2, delta, first, 0, l0);
+  list_at_layer(nvc, 2, delta, first, 1, l1);
+  for (int32_t i = 0; i < k; ++i) offset[i] = (int32_t)(l1[i] - l0[i]);
+  free(l0);
+  free(l1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -189,28 +224,12 @@ int oracle_var_ranges(int32_t nvc, const int64_t N[3], const int32_t *cell_verts
   return 0;
 }
 
-/* Algorithm 1 with per-entity level ranges: the column of entity (d1, i)
- * holds, for every layer l of its range, the DoFs of ((d1,0),(i,l)) then of
- * ((d1,1),(i,l)), and last those of the top horizontal entity.  first[t] is
- * indexed by absolute level: i * (maxlevel + 1 - d2) + l. */
+/* The numbering over per-entity level ranges: the same order of height
+ * ranks, each column running from its own lowest level to its highest.
+ * first[t] is indexed by absolute level: i * (maxlevel + 1 - d2) + l. */
 int64_t oracle_alg1_var(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
                         const int32_t *hi, const int32_t delta[6], int64_t *const first[6]) {
-  int64_t c = 0, ent = 0;
-  for (int d1 = 0; d1 <= 2; ++d1) {
-    for (int64_t i = 0; i < N[d1]; ++i, ++ent) {
-      for (int32_t l = lo[ent]; l < hi[ent]; ++l) {
-        for (int d2 = 0; d2 <= 1; ++d2) {
-          int t = 2 * d1 + d2;
-          if (first[t]) first[t][i * (maxlevel + 1 - d2) + l] = c;
-          c += delta[t];
-        }
-      }
-      int t = 2 * d1;
-      if (first[t]) first[t][i * (maxlevel + 1) + hi[ent]] = c;
-      c += delta[t];
-    }
-  }
-  return c;
+  return number_by_rank(N, maxlevel, lo, hi, delta, NULL, first);
 }
 
 /* Explicit lists L(c) at the bottom layer of each column (level
@@ -278,11 +297,19 @@ int oracle_hfacet_map(int32_t nvc, int64_t ncells, const int32_t *cell_verts,
   return 0;
 }
 
+/* Facet offsets, like the cell offsets, as the difference between the
+ * facet's lists at levels 1 and 0 of one base cell numbered over two layers. */
 void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
+  const int64_t N[3] = {nvc, nvc, 1};
+  int64_t tab[6][2 * 3 * 4];
+  int64_t *first[6];
+  for (int t = 0; t < 6; ++t) first[t] = tab[t];
+  number_by_rank(N, 2, NULL, NULL, delta, NULL, first);
   int32_t i = 0;
   for (int d = 0; d <= 2; ++d)
     for (int32_t e = 0; e < nentities(nvc, d); ++e)
-      for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];
+      for (int32_t q = 0; q < delta[2 * d]; ++q, ++i)
+        offset[i] = (int32_t)(first[2 * d][e * 3 + 1] - first[2 * d][e * 3 + 0]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -293,21 +320,7 @@ void oracle_hfacet_alg2(int32_t nvc, const int32_t delta[6], int32_t *offset) {
 /* ------------------------------------------------------------------------ */
 int64_t oracle_alg1_ragged(const int64_t N[3], int32_t maxlevel, const int32_t *lo,
                            const int32_t *hi, const int32_t *dent, int64_t *const first[6]) {
-  int64_t c = 0, ent = 0;
-  for (int d1 = 0; d1 <= 2; ++d1) {
-    for (int64_t i = 0; i < N[d1]; ++i, ++ent) {
-      for (int32_t l = lo[ent]; l < hi[ent]; ++l) {
-        for (int d2 = 0; d2 <= 1; ++d2) {
-          int t = 2 * d1 + d2;
-          if (first[t]) first[t][i * (maxlevel + 1 - d2) + l] = c;
-          c += dent[2 * ent + d2];
-        }
-      }
-      if (first[2 * d1]) first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;
-      c += dent[2 * ent];
-    }
-  }
-  return c;
+  return number_by_rank(N, maxlevel, lo, hi, NULL, dent, first);
 }
 
 /* Ragged explicit lists at each column's bottom layer (level cell_first[c],

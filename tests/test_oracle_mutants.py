@@ -14,13 +14,16 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 MUTANTS = {
     # Algorithm 1
-    "top_entity_numbered_late": ("first[t][i * (layers + 1) + layers] = c;",
-                                 "first[t][i * (layers + 1) + layers] = c + 1;"),
-    "vertical_before_horizontal": ("for (int d2 = 0; d2 <= 1; ++d2) {", "for (int d2 = 1; d2 >= 0; --d2) {"),
-    "top_not_counted": ("      c += delta[t];\n    }\n  }\n  return c;", "    }\n  }\n  return c;"),
+    "top_copy_not_numbered": ("for (int64_t s = s_lo; s <= s_hi; ++s) {", "for (int64_t s = s_lo; s < s_hi; ++s) {"),
+    "bottom_copy_not_numbered": ("const int64_t s_lo = 2 * (int64_t)(lo ? lo[g] : 0),",
+                                 "const int64_t s_lo = 2 * (int64_t)(lo ? lo[g] : 0) + 1,"),
+    "vertical_counted_as_horizontal": ("next += dent ? dent[2 * g + d2] : delta[t];",
+                                       "next += dent ? dent[2 * g + d2] : delta[2 * d1];"),
+    "number_taken_after_counting": ("if (first[t]) first[t][i * (maxlevel + 1 - d2) + level] = next;",
+                                    "if (first[t]) first[t][i * (maxlevel + 1 - d2) + level] = next + (d2 ? 0 : delta[t]);"),
     # explicit lists and Algorithm 2
     "top_slot_reads_bottom": ("first[2 * d][id * (layers + 1) + 1] + q", "first[2 * d][id * (layers + 1) + 0] + q"),
-    "offset_drops_horizontal": ("offset[i++] = delta[2 * d] + delta[2 * d + 1];", "offset[i++] = delta[2 * d + 1];"),
+    "offset_from_same_layer": ("list_at_layer(nvc, 2, delta, first, 1, l1);", "list_at_layer(nvc, 2, delta, first, 0, l1);"),
     "edge_wrong_neighbour": ("cell_verts[c * nvc + (k + 1) % nvc]", "cell_verts[c * nvc + (k + nvc - 1) % nvc]"),
     # quadrature and elements
     "prism_weight": ("wts[q] = (1.0 / 6.0) * gw[g];", "wts[q] = (1.0 / 3.0) * gw[g];"),
@@ -49,8 +52,8 @@ MUTANTS = {
     # variable layers per column
     "var_hull_max_bottom": ("if (lo[id] < 0 || bottom < lo[id]) lo[id] = bottom;",
                             "if (lo[id] < 0 || bottom > lo[id]) lo[id] = bottom;"),
-    "var_top_at_last_layer": ("first[t][i * (maxlevel + 1) + hi[ent]] = c;",
-                              "first[t][i * (maxlevel + 1) + hi[ent] - 1] = c;"),
+    "var_column_stops_a_layer_early": ("s_hi = 2 * (int64_t)(hi ? hi[g] : maxlevel);",
+                                       "s_hi = 2 * (int64_t)(hi ? hi[g] - 1 : maxlevel);"),
     "var_list_at_level_0": ("map[c * k + j++] = (int32_t)(first[2 * d + 1][id * maxlevel + s] + q);",
                             "map[c * k + j++] = (int32_t)(first[2 * d + 1][id * maxlevel + 0] + q);"),
     "var_uniform_trip_count": ("const int32_t lam = cell_layers ? cell_layers[c] : layers;",
@@ -58,8 +61,8 @@ MUTANTS = {
     "extrude_ignores_first": ("(double)(s + l + b) / (double)layers;", "(double)(l + b) / (double)layers;"),
     # horizontal facets
     "facet_loop_skips_top": ("if (kernel == ORC_K_HFACET_MASS) l1 = lam + 1;", "if (kernel == ORC_K_HFACET_MASS) l1 = lam;"),
-    "facet_offset_horizontal_only": ("for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d] + delta[2 * d + 1];",
-                                     "for (int32_t q = 0; q < delta[2 * d]; ++q) offset[i++] = delta[2 * d];"),
+    "facet_offset_horizontal_only": ("offset[i] = (int32_t)(first[2 * d][e * 3 + 1] - first[2 * d][e * 3 + 0]);",
+                                     "offset[i] = (int32_t)(first[2 * d][e * 3 + 1] - first[2 * d][e * 3 + 0] - delta[2 * d + 1]);"),
     "facet_normal_sign": ("const double n1 = e1[2] * e2[0] - e1[0] * e2[2];",
                           "const double n1 = e1[2] * e2[0] + e1[0] * e2[2];"),
     "facet_weight": ("static const double tri_w = 1.0 / 6.0;", "static const double tri_w = 1.0 / 3.0;"),
@@ -72,8 +75,8 @@ MUTANTS = {
     "jump_same_cell_twice": ("+ (j >= kc[a] ? offs[a][j] : 0);", "+ 0;"),
     "jump_base_face": ("const double ds = tri_area_element(X + 3, 6);", "const double ds = tri_area_element(X, 6);"),
     # per-entity DoF counts and the p-adaptive DG kernel
-    "ragged_top_counts_vertical": ("first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;\n      c += dent[2 * ent];",
-                                   "first[2 * d1][i * (maxlevel + 1) + hi[ent]] = c;\n      c += dent[2 * ent + 1];"),
+    "ragged_counts_swapped": ("next += dent ? dent[2 * g + d2] : delta[t];",
+                              "next += dent ? dent[2 * g + 1 - d2] : delta[t];"),
     "ragged_offset_horizontal_only": ("            offset[j] = a + b;", "            offset[j] = a;"),
     "ragged_top_list_at_bottom": ("else if (part == 1) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s + 1] + q);",
                                   "else if (part == 1) map[j] = (int32_t)(first[2 * d][id * (maxlevel + 1) + s] + q);"),
