@@ -78,43 +78,46 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   with WRITE, b is overwritten with the assembled result
  *                   (every DoF set, no zeroing needed beforehand).
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
- *                   On a mesh with base coordinates and constant layers both
- *                   run in the gather form, four kernels: a table of the
- *                   level heights (from the column of vertex 0), the column
- *                   mass matrix applied per vertex level (w = Mv f), the base
- *                   triangulation's P1 mass matrix applied per level as vertex
- *                   rows built by ext_mesh_create (b = Mh w; every DoF of b is
- *                   written by one thread, in a fixed order, so the result is
- *                   the same bit for bit from launch to launch), and a pass
- *                   over the DoFs whose stencil holds a prism that is not
- *                   straight with flat levels, or a NaN (6-point rule, general
- *                   Jacobian, both layers of every cell around the vertex).
- *                   Otherwise (no base coordinates, or variable layers): four
- *                   kernels on two or more constant layers (the area factor
- *                   of every cell summed per vertex, vertical sums of the
- *                   input per vertex level which also add each vertex's share
- *                   of its own sums, the cell pass with FP64 atomic adds, and
- *                   a pass over the warp steps that met a prism which is not
- *                   straight), three with one or variable layers (no area
- *                   pass; the cell pass adds each vertex's share).  The
- *                   vertical sums, the level table, the area factors and the
- *                   list of recorded steps live in scratch taken from the
- *                   device's default stream-ordered pool (cudaMallocAsync /
- *                   cudaFreeAsync on `stream`: 8 bytes per DoF of f in the
- *                   gather form, 16 per DoF plus 8 per vertex in the factored
- *                   one, 24 per DoF on a mesh with variable layers, plus at
- *                   most 1 byte per item), so launches on different streams
- *                   never share it and the launch can be captured in a CUDA
- *                   graph.  If the pool cannot supply it, or the launch has
- *                   fewer than a million (column, level) items, a single-pass
- *                   kernel that needs no scratch (every cell forms its own
- *                   vertical sums) runs instead.  The environment variables
- *                   EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and
- *                   EXTMESH_MASS_FACTORED, read once per process, select the
- *                   single pass (1) or the split forms (0) at any size, turn
- *                   the gather form off (0), and select the factored split
- *                   form with (1) or without (0) the area pass at any
- *                   constant layer count.  Coordinates must be finite.
+ *                   Forms (ext_set_option(EXT_OPT_P1_FORM); the default picks
+ *                   by size and geometry; all agree within rounding):
+ *                   - gather form (constant layers on a triangle mesh; chosen
+ *                     when a probe of the coordinates of about 4,096 sampled
+ *                     vertex columns, every level, finds a straight extrusion
+ *                     with flat levels): per launch, a table of the level
+ *                     heights (column of vertex 0), the area of every
+ *                     level-0 triangle and from them the weights of the base
+ *                     triangulation's P1 mass matrix Mh on the mesh's vertex
+ *                     rows; the column mass matrix applied per vertex level
+ *                     (w = Mv f); b = Mh w per level, every DoF written by
+ *                     one thread in a fixed order (the same bits from launch
+ *                     to launch); and a pass over the DoFs whose stencil
+ *                     holds a prism that is not straight with flat levels,
+ *                     or a NaN (the 6-point rule on both layers of every
+ *                     cell around the vertex);
+ *                   - cell loop (any other coordinate field, e.g.
+ *                     terrain-following levels or leaning columns):
+ *                     Algorithm 3 over the cell columns, one element vector
+ *                     per prism with the 6-point rule (a closed form of the
+ *                     rule for prisms with vertical edges, the general
+ *                     Jacobian otherwise), FP64 atomic adds;
+ *                   - factored / unfactored cell pass over vertical sums
+ *                     (vertex area sums, vertical sums per vertex level, the
+ *                     cell pass with FP64 atomic adds, and a pass over the
+ *                     warp steps that met a prism which is not straight);
+ *                     variable layers always take this form;
+ *                   - single pass (under a million (column, level) items, or
+ *                     when the scratch cannot be allocated): every cell forms
+ *                     its own vertical sums.
+ *                   Scratch (vertical sums, level table, areas, row weights,
+ *                   recorded steps: 8 bytes per DoF of f plus 8 per cell and
+ *                   8 per row entry in the gather form, 16 per DoF plus 8
+ *                   per vertex in the factored one, 24 per DoF on variable
+ *                   layers, none in the cell loop, plus at most 1 byte per
+ *                   item) comes from the device's default stream-ordered pool
+ *                   (cudaMallocAsync / cudaFreeAsync on `stream`), so
+ *                   launches on different streams never share it and the
+ *                   launch can be captured in a CUDA graph.  Coordinates
+ *                   must be finite.
  * EXT_K_INTERP_DG1  [x READ (CG1xCG1), out WRITE (DG1xDG1)] on prisms: nodal
  *                   interpolation, out at DG1 node (vertex a, level b) = x there.
  * EXT_K_U2V_FWD     [coords READ, u READ, F INC|WRITE]: F_i += int u_h^2 phi_i dx,
@@ -386,6 +389,37 @@ ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, i
  * assembly kernels; the paper has no counterpart.  Synchronous on `stream`;
  * allocates and frees scratch buffers. */
 ext_status ext_fp64_rates(double gops_host[4], void *stream);
+
+/* Process-wide options.  EXT_OPT_P1_FORM selects the form of the
+ * EXT_K_RHS_P1P1 / EXT_K_MASS_P1P1 launch (all forms give the same result
+ * within the rounding of their summation orders):
+ *   EXT_P1_AUTO (default)  the single-pass kernel under a million
+ *                          (column, level) items, else EXT_P1_SPLIT;
+ *   EXT_P1_SPLIT           a probe of the coordinate field picks the gather
+ *                          form on a straight extrusion with flat levels and
+ *                          the cell loop on any other geometry;
+ *   EXT_P1_GATHER          the gather form without the probe;
+ *   EXT_P1_FACTORED        the cell pass over vertical sums with the area
+ *                          pass; EXT_P1_UNFACTORED without it;
+ *   EXT_P1_CELLS           the cell loop (Algorithm 3, one element vector
+ *                          per prism);
+ *   EXT_P1_SINGLE          the single-pass kernel.
+ * The initial value comes from the environment variable EXTMESH_P1_FORM
+ * (auto, split, gather, factored, unfactored, cells, single), read at the
+ * first query.  ext_set_option returns EXT_EINVAL for an unknown option or
+ * value; it affects launches issued after it returns. */
+typedef enum { EXT_OPT_P1_FORM = 1 } ext_option;
+typedef enum {
+  EXT_P1_AUTO = 0,
+  EXT_P1_SPLIT = 1,
+  EXT_P1_GATHER = 2,
+  EXT_P1_FACTORED = 3,
+  EXT_P1_UNFACTORED = 4,
+  EXT_P1_CELLS = 5,
+  EXT_P1_SINGLE = 6
+} ext_p1_form;
+ext_status ext_set_option(int32_t option, int32_t value);
+ext_status ext_get_option(int32_t option, int32_t *value);
 
 /* Waits for `stream`, then reads and clears the device error word:
  * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device

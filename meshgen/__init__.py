@@ -222,6 +222,36 @@ def column_layers(m: BaseMesh, maxlevel: int, seed: int, kind: str = "bathymetry
     return (maxlevel - lay).astype(np.int32), lay
 
 
+def level_coords(m: BaseMesh, layers: int, seed: int, kind: str = "terrain") -> np.ndarray:
+    """Coordinates of every (base vertex, level) pair, float64, shape
+    (nverts, layers + 1, 3), for geometries other than the flat unit-height
+    extrusion.
+
+    ``terrain``: terrain-following levels over a smooth depth field
+    d(x, y) = 0.55 + 0.4 sin(3x + p1) cos(2y + p2) in [0.15, 0.95]: the vertex
+    at level l sits at (x, y, (l / layers) d(x, y)), so every column is
+    vertical and no two vertices of a prism's top face (away from symmetric
+    points) share a height.  ``tilted``: the same levels with x and y sheared
+    with height, x + 0.05 z sin(2 pi y) and y + 0.05 z cos(2 pi x), so the
+    columns lean as well.  The phases come from ``seed``."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0.0, 2.0 * np.pi, 2)
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    depth = 0.55 + 0.4 * np.sin(3.0 * x + ph[0]) * np.cos(2.0 * y + ph[1])
+    lev = np.arange(layers + 1, dtype=np.float64) / float(layers)
+    out = np.empty((m.nverts, layers + 1, 3))
+    out[:, :, 0] = x[:, None]
+    out[:, :, 1] = y[:, None]
+    out[:, :, 2] = lev[None, :] * depth[:, None]
+    if kind == "tilted":
+        z = out[:, :, 2]
+        out[:, :, 0] = x[:, None] + 0.05 * z * np.sin(2.0 * np.pi * y)[:, None]
+        out[:, :, 1] = y[:, None] + 0.05 * z * np.cos(2.0 * np.pi * x)[:, None]
+    elif kind != "terrain":
+        raise ValueError(kind)
+    return out
+
+
 def padaptive_dent(m: BaseMesh, nedges: int, seed: int, kind: str = "disk") -> np.ndarray:
     """Per-entity DoF counts ((V + E + C) x 2, dimension-major) of a p-adaptive
     DG space: DoFs only inside the cells, each cell one of DG0xDG0 (1),

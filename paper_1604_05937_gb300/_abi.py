@@ -295,3 +295,25 @@ def ext_fp64_rates(stream=None) -> dict:
     out = np.zeros(4)
     _check(lib.ext_fp64_rates(_ptr(out), _stream(stream)))
     return {"dfma": float(out[0]), "dadd": float(out[1]), "dmul": float(out[2]), "l2_atomic_add": float(out[3])}
+
+
+# ---- process-wide options (ext_set_option / ext_get_option)
+EXT_OPT_P1_FORM = 1
+(EXT_P1_AUTO, EXT_P1_SPLIT, EXT_P1_GATHER, EXT_P1_FACTORED, EXT_P1_UNFACTORED, EXT_P1_CELLS,
+ EXT_P1_SINGLE) = range(7)
+P1_FORMS = {"auto": EXT_P1_AUTO, "split": EXT_P1_SPLIT, "gather": EXT_P1_GATHER, "factored": EXT_P1_FACTORED,
+            "unfactored": EXT_P1_UNFACTORED, "cells": EXT_P1_CELLS, "single": EXT_P1_SINGLE}
+lib.ext_set_option.restype = ctypes.c_int
+lib.ext_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
+lib.ext_get_option.restype = ctypes.c_int
+lib.ext_get_option.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+
+
+def ext_set_option(option: int, value: int) -> None:
+    _check(lib.ext_set_option(option, value))
+
+
+def ext_get_option(option: int) -> int:
+    v = ctypes.c_int32(0)
+    _check(lib.ext_get_option(option, ctypes.byref(v)))
+    return int(v.value)

@@ -2,6 +2,8 @@
 // base-mesh entity derivation, space numbering set-up, par_loop dispatch and
 // the batched plan (autotuning, colouring, CUDA-graph capture).
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,6 +37,40 @@ ext_status ext_fail(ext_status st, const char *fmt, ...) {
 
 extern "C" const char *ext_last_error(void) { return g_last_error.c_str(); }
 extern "C" int32_t ext_abi_version(void) { return EXT_ABI_VERSION; }
+
+// ---------------------------------------------------------------------------
+// options
+static std::atomic<int> g_p1_form{-1};
+
+int p1_form() {
+  int v = g_p1_form.load();
+  if (v < 0) {
+    static const char *names[] = {"auto", "split", "gather", "factored", "unfactored", "cells", "single"};
+    const char *ev = getenv("EXTMESH_P1_FORM");
+    int init = EXT_P1_AUTO;
+    for (int i = 0; ev && i < 7; ++i)
+      if (strcmp(ev, names[i]) == 0) init = i;
+    int expect = -1;
+    g_p1_form.compare_exchange_strong(expect, init);
+    v = g_p1_form.load();
+  }
+  return v;
+}
+
+extern "C" ext_status ext_set_option(int32_t option, int32_t value) {
+  if (option != EXT_OPT_P1_FORM) return ext_fail(EXT_EINVAL, "ext_set_option: unknown option %d", option);
+  if (value < EXT_P1_AUTO || value > EXT_P1_SINGLE)
+    return ext_fail(EXT_EINVAL, "ext_set_option: EXT_OPT_P1_FORM value %d out of range", value);
+  g_p1_form.store(value);
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_get_option(int32_t option, int32_t *value) {
+  if (!value) return ext_fail(EXT_EINVAL, "ext_get_option: value is NULL");
+  if (option != EXT_OPT_P1_FORM) return ext_fail(EXT_EINVAL, "ext_get_option: unknown option %d", option);
+  *value = p1_form();
+  return EXT_OK;
+}
 
 static std::mutex g_word_mu;
 static unsigned int *g_word[128];
@@ -88,29 +124,22 @@ static int64_t derive_edges(int kind, int64_t ncells, const int32_t *cv, std::ve
   return (int64_t)first.size();
 }
 
-// Vertex rows of the P1 mass matrix of a triangulation (for the P1xP1
-// gather form): with alpha_c = |2 A_c| / 144, the weight of neighbour j in
-// row a is the sum of alpha_c over the cells holding edge (a, j), and the
-// diagonal weight is the sum of the row's neighbour weights (twice the sum
-// of alpha_c around a).  Rows list a itself first, then its neighbours in
-// ascending order; neighbour weights are summed in ascending cell order.
-// An entry carries, instead of the vertex j, the first DoF j col of j's
-// CG1xCG1 column (col = layers + 1 levels; the DoF of level m is j col + m).
-// Also the cells around every vertex, ascending.  Returns false (rows not
-// built) when the entry count does not fit int32.
-static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const double *xy, int64_t col,
-                              std::vector<int32_t> &vrow, std::vector<double2> &vent,
-                              std::vector<int32_t> &vcrow, std::vector<int32_t> &vcells) {
-  std::vector<double> alpha((size_t)nc);
+// Vertex rows of the P1 mass matrix of a triangulation, topology only (for
+// the P1xP1 gather form, which computes the weights from each launch's
+// coordinate field): row a lists a itself, then its neighbours j in
+// ascending order.  An entry carries, instead of the vertex j, the first DoF
+// j col of j's CG1xCG1 column (col = layers + 1 levels; the DoF of level m
+// is j col + m), and the cells on edge (a, j) in ascending order (-1 where
+// the edge has one cell; both -1 on the diagonal).  Also the cells around
+// every vertex, ascending.  Returns false (rows not built) when an edge has
+// more than two cells or the entry count does not fit int32.
+static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, int64_t col, std::vector<int32_t> &vrow,
+                              std::vector<int32_t> &vnbr, std::vector<int2> &vedge, std::vector<int32_t> &vcrow,
+                              std::vector<int32_t> &vcells) {
+  if ((nv - 1) * col + col > (int64_t)INT32_MAX) return false;
   vcrow.assign((size_t)nv + 1, 0);
-  for (int64_t c = 0; c < nc; ++c) {
-    const int32_t *t = cv + 3 * c;
-    const double x0 = xy[2 * (int64_t)t[0]], y0 = xy[2 * (int64_t)t[0] + 1];
-    const double x1 = xy[2 * (int64_t)t[1]], y1 = xy[2 * (int64_t)t[1] + 1];
-    const double x2 = xy[2 * (int64_t)t[2]], y2 = xy[2 * (int64_t)t[2] + 1];
-    alpha[(size_t)c] = std::fabs((x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0)) * (1.0 / 144.0);
-    for (int a = 0; a < 3; ++a) ++vcrow[(size_t)t[a] + 1];
-  }
+  for (int64_t c = 0; c < nc; ++c)
+    for (int a = 0; a < 3; ++a) ++vcrow[(size_t)cv[3 * c + a] + 1];
   for (int64_t v = 0; v < nv; ++v) vcrow[(size_t)v + 1] += vcrow[(size_t)v];
   vcells.assign((size_t)(3 * nc), 0);
   {
@@ -119,37 +148,31 @@ static bool build_vertex_rows(int64_t nv, int64_t nc, const int32_t *cv, const d
       for (int a = 0; a < 3; ++a) vcells[(size_t)cur[(size_t)cv[3 * c + a]]++] = (int32_t)c;
   }
   vrow.assign((size_t)nv + 1, 0);
-  vent.clear();
-  vent.reserve((size_t)(nv + 6 * nc));
-  std::vector<std::pair<int32_t, double>> nb;
-  auto entry = [](double w, int32_t j) {
-    double2 en;
-    en.x = w;
-    const long long bits = (long long)(uint32_t)j;
-    std::memcpy(&en.y, &bits, sizeof bits);
-    return en;
-  };
+  vnbr.clear();
+  vedge.clear();
+  vnbr.reserve((size_t)(nv + 6 * nc));
+  vedge.reserve((size_t)(nv + 6 * nc));
+  std::vector<std::pair<int32_t, int32_t>> nb;  // (neighbour, cell)
   for (int64_t a = 0; a < nv; ++a) {
     nb.clear();
     for (int32_t t = vcrow[(size_t)a]; t < vcrow[(size_t)a + 1]; ++t) {
-      const int64_t c = vcells[(size_t)t];
+      const int32_t c = vcells[(size_t)t];
       for (int k = 0; k < 3; ++k)
-        if (cv[3 * c + k] != a) nb.push_back({cv[3 * c + k], alpha[(size_t)c]});
+        if (cv[3 * (int64_t)c + k] != a) nb.push_back({cv[3 * (int64_t)c + k], c});
     }
-    std::stable_sort(nb.begin(), nb.end(),
-                     [](const std::pair<int32_t, double> &l, const std::pair<int32_t, double> &r) { return l.first < r.first; });
-    size_t w = 0;
-    for (size_t i = 0; i < nb.size(); ++i) {
-      if (w > 0 && nb[w - 1].first == nb[i].first) nb[w - 1].second += nb[i].second;
-      else nb[w++] = nb[i];
+    std::sort(nb.begin(), nb.end());
+    vnbr.push_back((int32_t)(a * col));
+    vedge.push_back(make_int2(-1, -1));
+    for (size_t i = 0; i < nb.size();) {
+      size_t e = i + 1;
+      while (e < nb.size() && nb[e].first == nb[i].first) ++e;
+      if (e - i > 2) return false;
+      vnbr.push_back((int32_t)(nb[i].first * col));
+      vedge.push_back(make_int2(nb[i].second, e - i == 2 ? nb[i + 1].second : -1));
+      i = e;
     }
-    nb.resize(w);
-    double diag = 0.0;
-    for (const auto &q : nb) diag += q.second;
-    vent.push_back(entry(diag, (int32_t)(a * col)));
-    for (const auto &q : nb) vent.push_back(entry(q.second, (int32_t)(q.first * col)));
-    if (vent.size() >= (size_t)INT32_MAX) return false;
-    vrow[(size_t)a + 1] = (int32_t)vent.size();
+    if (vnbr.size() >= (size_t)INT32_MAX) return false;
+    vrow[(size_t)a + 1] = (int32_t)vnbr.size();
   }
   return true;
 }
@@ -164,7 +187,8 @@ static void free_mesh(ext_mesh *m) {
   cudaFree(m->d_ent_lo);
   cudaFree(m->d_ent_hi);
   cudaFree(m->d_vrow);
-  cudaFree(m->d_vent);
+  cudaFree(m->d_vnbr);
+  cudaFree(m->d_vedge);
   cudaFree(m->d_vcrow);
   cudaFree(m->d_vcells);
   delete reinterpret_cast<ext_mesh_host *>(m->host);
@@ -253,19 +277,21 @@ static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, cons
       e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->has_xy = base_xy_host != nullptr;
-  if (e == cudaSuccess && kind == EXT_TRI && base_xy_host && !var && nverts > 0 && ncells > 0) {
-    std::vector<int32_t> vrow, vcrow, vcells;
-    std::vector<double2> vent;
-    if (build_vertex_rows(nverts, ncells, cell_verts_host, base_xy_host, (int64_t)layers + 1, vrow, vent, vcrow,
-                          vcells)) {
-      const size_t rb = sizeof(int32_t) * vrow.size(), eb = sizeof(double2) * vent.size();
-      const size_t cb = sizeof(int32_t) * vcells.size();
-      if ((e = cudaMalloc(&m->d_vrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vent, eb)) == cudaSuccess &&
-          (e = cudaMalloc(&m->d_vcrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vcells, cb)) == cudaSuccess &&
+  if (e == cudaSuccess && kind == EXT_TRI && !var && nverts > 0 && ncells > 0) {
+    std::vector<int32_t> vrow, vnbr, vcrow, vcells;
+    std::vector<int2> vedge;
+    if (build_vertex_rows(nverts, ncells, cell_verts_host, (int64_t)layers + 1, vrow, vnbr, vedge, vcrow, vcells)) {
+      const size_t rb = sizeof(int32_t) * vrow.size(), nb4 = sizeof(int32_t) * vnbr.size();
+      const size_t eb = sizeof(int2) * vedge.size(), cb = sizeof(int32_t) * vcells.size();
+      if ((e = cudaMalloc(&m->d_vrow, rb)) == cudaSuccess && (e = cudaMalloc(&m->d_vnbr, nb4)) == cudaSuccess &&
+          (e = cudaMalloc(&m->d_vedge, eb)) == cudaSuccess && (e = cudaMalloc(&m->d_vcrow, rb)) == cudaSuccess &&
+          (e = cudaMalloc(&m->d_vcells, cb)) == cudaSuccess &&
           (e = cudaMemcpy(m->d_vrow, vrow.data(), rb, cudaMemcpyHostToDevice)) == cudaSuccess &&
-          (e = cudaMemcpy(m->d_vent, vent.data(), eb, cudaMemcpyHostToDevice)) == cudaSuccess &&
+          (e = cudaMemcpy(m->d_vnbr, vnbr.data(), nb4, cudaMemcpyHostToDevice)) == cudaSuccess &&
+          (e = cudaMemcpy(m->d_vedge, vedge.data(), eb, cudaMemcpyHostToDevice)) == cudaSuccess &&
           (e = cudaMemcpy(m->d_vcrow, vcrow.data(), rb, cudaMemcpyHostToDevice)) == cudaSuccess)
         e = cudaMemcpy(m->d_vcells, vcells.data(), cb, cudaMemcpyHostToDevice);
+      m->n_vent = (int64_t)vnbr.size();
     }
   }
   if (e == cudaSuccess && var) {
@@ -765,7 +791,10 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
       p.overwrite = args[2].access == EXT_WRITE;
       p.vrow = mesh->d_vrow;
-      p.vent = mesh->d_vent;
+      p.vnbr = mesh->d_vnbr;
+      p.vedge = mesh->d_vedge;
+      p.nverts = (int32_t)mesh->N[0];
+      p.nvent = mesh->n_vent;
       p.vcrow = mesh->d_vcrow;
       p.vcells = mesh->d_vcells;
       e = launch_mass_p1(p, s);

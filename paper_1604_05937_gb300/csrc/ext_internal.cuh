@@ -58,16 +58,20 @@ struct ext_mesh {
   int32_t *d_ent_hi = nullptr;       // dimension-major (vertices, edges, cells)
   double mean_layers = 0.0;
   void *host = nullptr;             // host-side copies (ext_api.cu)
-  // triangle meshes with base coordinates and constant layers: the P1 mass
-  // matrix of the base triangulation as vertex rows (row a: a itself, then
-  // its neighbours in ascending order; entry (weight, first DoF j (layers+1)
-  // of vertex j's CG1xCG1 column, in the low 32 bits of the second double))
-  // and the cells around every vertex in ascending order (the P1xP1 gather
-  // form)
+  // triangle meshes with constant layers: the sparsity pattern of the P1
+  // mass matrix of the base triangulation as vertex rows (row a: a itself,
+  // then its neighbours in ascending order), each entry holding the first
+  // DoF j (layers + 1) of vertex j's CG1xCG1 column and the one or two cells
+  // on edge (a, j) (ascending; -1 where absent, both -1 on the diagonal), and
+  // the cells around every vertex in ascending order.  Topology only: the
+  // P1xP1 gather form computes the weights from the coordinate field of each
+  // launch.
   int32_t *d_vrow = nullptr;    // nverts + 1
-  double2 *d_vent = nullptr;    // d_vrow[nverts] entries
+  int32_t *d_vnbr = nullptr;    // d_vrow[nverts] entries
+  int2 *d_vedge = nullptr;      // d_vrow[nverts] entries
   int32_t *d_vcrow = nullptr;   // nverts + 1
   int32_t *d_vcells = nullptr;  // 3 ncells
+  int64_t n_vent = 0;           // d_vrow[nverts]
 };
 
 struct ext_space {
@@ -197,10 +201,15 @@ struct MassP1Launch {
   const double *base_xy = nullptr;  // the mesh's base coordinates (nverts x 2), if it has them
   bool overwrite = false;           // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
   // the mesh's vertex rows (ext_mesh::d_vrow ...), null when it has none
-  const int32_t *vrow = nullptr;
-  const double2 *vent = nullptr;
+  const int32_t *vrow = nullptr, *vnbr = nullptr;
+  const int2 *vedge = nullptr;
   const int32_t *vcrow = nullptr, *vcells = nullptr;
+  int32_t nverts = 0;
+  int64_t nvent = 0;  // entries of the vertex rows
 };
+
+// Form of the P1xP1 launch (ext_set_option(EXT_OPT_P1_FORM, ...)).
+int p1_form();
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 
 // Mass action on the nine prism tensor-product spaces (k_tp.cu).

@@ -128,6 +128,106 @@ __device__ void prism_general(const double X[6][3], const double f[6], double ou
 
 __device__ __forceinline__ bool same_bits(double a, long long b) { return __double_as_longlong(a) == b; }
 
+// P1xP1 element vector of one prism with the 6-point rule (3-point triangle
+// rule x 2-point Gauss rule, weight 1/12 per point), stencil order
+// i = 2a + b (vertex a, bottom/top b):
+//   out_i = sum_q (1/12) |det J_q| f_h(x_q) phi_i(x_q).
+// Nodes X[i] (x, y, z) and values f[i]; rx, ry: bit patterns of the level-0
+// x, y of the cell's three vertex columns; k2 = |2A| / 864 and
+// k6 = |2A| / 2592 with A the area of the level-0 triangle.
+//
+// Vertical form: when all six nodes lie on the vertical lines through the
+// level-0 vertices (x, y equal to rx, ry bitwise), J has the columns
+// (e1, e2, (0, 0, h(t))) with h(t) = sum_a lambda_a(t) h_a the interpolated
+// height of the vertical edges h_a = z_a1 - z_a0, so det J = 2A h(t) does not
+// depend on the Gauss point.  With lambda_a(t) = 1/6 + [a = t]/2 at the
+// triangle points and sum_g psi_b psi_b' = (1 + [b = b']) / 3 over the two
+// Gauss points, the rule sums to
+//   out_ab = D_a (G_b + 3 g_ab) + G_b (D_0 + D_1 + D_2) / 3 + sum_t D_t g_tb,
+//   D_t = |k2 h_t + k6 (h_0 + h_1 + h_2)|,  g_ab = 2 f_ab + f_a(1-b),
+//   G_b = g_0b + g_1b + g_2b:
+// 42 FP64 operations, all issued as DFMA.
+//
+// General form (any other prism): per Gauss point height z the horizontal
+// tangents e1 = P_1 - P_0, e2 = P_2 - P_0 of the points P_a = (1 - z) X_a0 +
+// z X_a1 on the vertical edges, n = e1 x e2, and with the edge vectors
+// H_a = X_a1 - X_a0 the determinant at triangle point t is
+// det = sum_a lambda_a(t) (H_a . n) (about 130 FP64 operations).
+__device__ __forceinline__ void p1_prism(const double X[6][3], const double f[6], const long long rx[3],
+                                         const long long ry[3], double k2, double k6, const Fp64Ones &k1,
+                                         double out[6]) {
+  bool vert = true;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) vert &= same_bits(X[i][0], rx[i >> 1]) & same_bits(X[i][1], ry[i >> 1]);
+  if (vert) {
+    double h[3], D[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h[a] = fsub(X[2 * a + 1][2], X[2 * a][2], k1);
+    const double ks = fmul(k6, fadd(h[0], fadd(h[1], h[2], k1), k1), k1);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) D[t] = fabs(fma(k2, h[t], ks));
+    const double Ds = fmul(fadd(D[0], fadd(D[1], D[2], k1), k1), 1.0 / 3.0, k1);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      double g[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) g[a] = fma(2.0, f[2 * a + b], f[2 * a + 1 - b]);
+      const double G = fadd(g[0], fadd(g[1], g[2], k1), k1);
+      const double Q = fma(D[0], g[0], fma(D[1], g[1], fmul(D[2], g[2], k1)));
+      const double C = fma(G, Ds, Q);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) out[2 * a + b] = fma(D[a], fma(3.0, g[a], G), C);
+    }
+    return;
+  }
+  const double zg[2] = {0.5 - 0.28867513459481288225, 0.5 + 0.28867513459481288225};
+  double H[3][3], E10[3], E20[3], dE1[3], dE2[3], df[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) H[a][r] = fsub(X[2 * a + 1][r], X[2 * a][r], k1);
+    E10[r] = fsub(X[2][r], X[0][r], k1);
+    E20[r] = fsub(X[4][r], X[0][r], k1);
+    dE1[r] = fsub(fsub(X[3][r], X[1][r], k1), E10[r], k1);
+    dE2[r] = fsub(fsub(X[5][r], X[1][r], k1), E20[r], k1);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    df[a] = fsub(f[2 * a + 1], f[2 * a], k1);
+    out[2 * a] = 0.0;
+    out[2 * a + 1] = 0.0;
+  }
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const double z = zg[g];
+    double e1[3], e2[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      e1[r] = fma(z, dE1[r], E10[r]);
+      e2[r] = fma(z, dE2[r], E20[r]);
+    }
+    const double n[3] = {fma(e1[1], e2[2], -e1[2] * e2[1]), fma(e1[2], e2[0], -e1[0] * e2[2]),
+                         fma(e1[0], e2[1], -e1[1] * e2[0])};
+    double pa[3], F[3], w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      pa[a] = fma(H[a][0], n[0], fma(H[a][1], n[1], fmul(H[a][2], n[2], k1)));
+      F[a] = fma(z, df[a], f[2 * a]);
+    }
+    const double sp = fmul(fadd(pa[0], fadd(pa[1], pa[2], k1), k1), 1.0 / 72.0, k1);
+    const double sf = fmul(fadd(F[0], fadd(F[1], F[2], k1), k1), 1.0 / 6.0, k1);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) w[t] = fmul(fabs(fma(1.0 / 24.0, pa[t], sp)), fma(0.5, F[t], sf), k1);
+    const double sw = fmul(fadd(w[0], fadd(w[1], w[2], k1), k1), 1.0 / 6.0, k1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double R = fma(0.5, w[a], sw);
+      out[2 * a] = fma(1.0 - z, R, out[2 * a]);
+      out[2 * a + 1] = fma(z, R, out[2 * a + 1]);
+    }
+  }
+}
+
 // VAR: column c has cell_layers[c] layers (its stencil lists are taken at its
 // own bottom layer), so a group's item count and the (column, level) walk
 // read each column's layer count from shared memory.
@@ -548,41 +648,6 @@ __global__ void __launch_bounds__(256, EXT_VSUM_MINB) k_vsum(const double *__res
   }
 }
 
-// prism_general reading the coordinates and f from memory (L1) at each
-// quadrature point instead of holding them in registers.
-__device__ void prism_general_g(const double *__restrict__ Xg, const double *__restrict__ fg, const int32_t cd[6],
-                                const int32_t fd[6], double out[6]) {
-  const double tp[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
-  const double gz[2] = {0.5 - 0.28867513459481288225, 0.5 + 0.28867513459481288225};
-  for (int i = 0; i < 6; ++i) out[i] = 0.0;
-  for (int t = 0; t < 3; ++t) {
-    const double lam[3] = {1.0 - tp[t][0] - tp[t][1], tp[t][0], tp[t][1]};
-    const double dlx[3] = {-1.0, 1.0, 0.0}, dly[3] = {-1.0, 0.0, 1.0};
-    for (int g = 0; g < 2; ++g) {
-      const double psi[2] = {1.0 - gz[g], gz[g]};
-      const double dpsi[2] = {-1.0, 1.0};
-      double J[3][3] = {{0.0}};
-      double fq = 0.0;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 2; ++b) {
-          const int i = 2 * a + b;
-          const double gr[3] = {dlx[a] * psi[b], dly[a] * psi[b], lam[a] * dpsi[b]};
-          for (int r = 0; r < 3; ++r) {
-            const double xr = __ldg(Xg + 3 * (int64_t)cd[i] + r);
-            for (int q = 0; q < 3; ++q) J[r][q] += xr * gr[q];
-          }
-          fq += lam[a] * psi[b] * __ldg(fg + fd[i]);
-        }
-      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-      const double wq = (1.0 / 12.0) * fabs(det) * fq;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 2; ++b) out[2 * a + b] += wq * lam[a] * psi[b];
-    }
-  }
-}
-
 // Stencil rows, area factor and level-0 corner bits of column c (Algorithm
 // 3's outer loop: the lists are read once per column).  STORED (the
 // factored form): the area factor is the one the area pass stored in
@@ -760,11 +825,45 @@ __global__ void __launch_bounds__(kWarps * 32, VAR ? EXT_CELLS_VAR_MINB : EXT_CE
   }
 }
 
+// Reference x, y bit patterns of a cell column (its bottom coordinate DoFs)
+// and the area constants k2 = |2A| / 864, k6 = |2A| / 2592 of p1_prism.
+__device__ __forceinline__ void column_ref(const double *__restrict__ X, const int32_t cb[3], long long rx[3],
+                                          long long ry[3], double &k2, double &k6) {
+  double x[3], y[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = __ldg(X + 3 * (int64_t)cb[a] + 0);
+    y[a] = __ldg(X + 3 * (int64_t)cb[a] + 1);
+    rx[a] = __double_as_longlong(x[a]);
+    ry[a] = __double_as_longlong(y[a]);
+  }
+  const double det2 = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]));
+  k2 = det2 * (1.0 / 864.0);
+  k6 = det2 * (1.0 / 2592.0);
+}
+
+// Nodes and values of prism (c, l) of a column set up in `ci` (layers lay).
+__device__ __forceinline__ void load_prism(const MassP1Launch &p, const ColInfo &ci, int l, int lay, double X[6][3],
+                                           double f[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int64_t cd = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], l + b, lay);
+      X[2 * a + b][0] = __ldg(p.X + 3 * cd + 0);
+      X[2 * a + b][1] = __ldg(p.X + 3 * cd + 1);
+      X[2 * a + b][2] = __ldg(p.X + 3 * cd + 2);
+      f[2 * a + b] = __ldg(p.f + dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], l + b, lay));
+    }
+}
+
 // The deferred warp steps: every item of the step evaluates the two element
-// integrals touching its level with the 6-point rule and the general Jacobian.
+// vectors touching its level (p1_prism: the 6-point rule, vertical or
+// general form).
 template <bool VAR, bool FAC>
 __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch p, const double *__restrict__ W,
-                                                              Deferred dfr, int cpw, const double *__restrict__ alpha) {
+                                                              Deferred dfr, int cpw, const double *__restrict__ alpha,
+                                                              Fp64Ones k1) {
   __shared__ ColInfo cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -783,18 +882,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
       item_pos<VAR>(cols[warp], ncol, p.layers + 1, it, cl, m);
       const ColInfo &ci = cols[warp][cl];
       const int lay = VAR ? ci.lay : p.layers;
+      long long rx[3], ry[3];
+      double k2, k6;
+      column_ref(p.X, ci.cbot, rx, ry, k2, k6);
       double val[3] = {0.0, 0.0, 0.0};
       for (int half = 0; half < 2; ++half) {
         const int l = half == 0 ? m - 1 : m;
         if (l < 0 || l >= lay) continue;
-        int32_t cd[6], fd[6];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 2; ++b) {
-            cd[2 * a + b] = dof_at(ci.cbot[a], ci.ctop[a], p.coff[2 * a], l + b, lay);
-            fd[2 * a + b] = dof_at(ci.fbot[a], ci.ftop[a], p.foff[2 * a], l + b, lay);
-          }
-        double out[6];
-        prism_general_g(p.X, p.f, cd, fd, out);
+        double Xp[6][3], fp[6], out[6];
+        load_prism(p, ci, l, lay, Xp, fp);
+        p1_prism(Xp, fp, rx, ry, k2, k6, k1, out);
         for (int a = 0; a < 3; ++a) val[a] += out[2 * a + (half == 0 ? 1 : 0)];
       }
       // factored form: the vertex pass added alpha_c w_a for this item too
@@ -809,59 +906,114 @@ __global__ void __launch_bounds__(kWarps * 32) k_mass_general(const MassP1Launch
   }
 }
 
-
 // ---------------------------------------------------------------------------
-// Gather form (constant layers, a mesh with base coordinates).  A straight
-// extrusion with flat levels (every DoF at its vertex's base x, y, level m at
-// one height z_m in every column) is a tensor product, and the P1xP1 mass
-// matrix factors as M = Mh (x) Mv: Mh the P1 mass matrix of the base
-// triangulation, held by the mesh as vertex rows (the weight of neighbour j
-// of vertex a is the sum of alpha_c = |2 A_c| / 144 over the cells holding
-// edge (a, j), the diagonal weight is the sum of the row), and Mv the P1
-// mass matrix of the column,
+// Gather form (constant layers, triangle meshes).  A straight extrusion with
+// flat levels (every DoF at the x, y of its column's level 0, level m at one
+// height z_m in every column) is a tensor product, and the P1xP1 mass matrix
+// factors as M = Mh (x) Mv: Mh the P1 mass matrix of the level-0
+// triangulation, applied through the mesh's vertex rows (the weight of
+// neighbour j of vertex a is the sum of alpha_c = |2 A_c| / 144 over the
+// cells holding edge (a, j), the diagonal weight is the sum of the row), and
+// Mv the P1 mass matrix of the column,
 //   w_m = (Mv f)_m = |h_{m-1}| f_{m-1} + 2 (|h_{m-1}| + |h_m|) f_m + |h_m| f_{m+1}
 // (the factor 1/6 of Mv is in alpha).  b = Mh (x) Mv f is then, per level,
 // the row sums b_{a,m} = sum_j Mh_{aj} w_{j,m}: 3 FP64 operations per DoF
-// for Mv and one per row entry (about 7 per DoF) for Mh, against 6 per DoF
-// and 3 per (cell, level) item plus 3 atomic adds in the factored form.  The
-// launch runs
-//   k_levels            the level table (z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|),
-//                       |h_m|) from the column of vertex 0 (DoFs 0 .. layers),
+// for Mv and one per row entry (about 7 per DoF) for Mh.  Every geometric
+// quantity comes from the coordinate field of the launch.  The launch runs
+//   k_p1_prep           the level table (z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|),
+//                       |h_m|) from the column of vertex 0, alpha_c of every
+//                       cell from its level-0 nodes, and (automatic form) a
+//                       probe of the coordinates of a sample of vertex
+//                       columns: any sampled DoF off its column's vertical or
+//                       its level's height sets the mode word, and the launch
+//                       then runs as the cell loop k_p1_cells instead,
+//   k_p1_rowweights     the row weights from alpha,
 //   k_vsum_bulk         w per DoF, stored; a NaN pattern instead where the DoF
-//                       or a vertical neighbour of it is off its column's base
-//                       x, y or its level's height (coordinates and f staged in
-//                       shared memory by bulk copies; k_vsum_tab is the same pass
-//                       with plain loads, for X or f not 16-byte aligned),
+//                       or a vertical neighbour of it is off its column's
+//                       level-0 x, y or its level's height (coordinates and f
+//                       staged in shared memory by bulk copies; k_vsum_tab is
+//                       the same pass with plain loads, for X or f not 16-byte
+//                       aligned),
 //   k_vgather           b per DoF: one thread forms the row sum over the
 //                       vertex row (no atomics) and overwrites b (WRITE) or
 //                       adds to it (INC); a 32-DoF chunk whose sums came out
 //                       NaN is recorded with the mask of those DoFs and left
 //                       untouched,
-//   k_vgather_general   the recorded DoFs: the 6-point rule with the general
-//                       Jacobian over both layers of every cell around the
-//                       vertex.
+//   k_vgather_general   the recorded DoFs: p1_prism over both layers of every
+//                       cell around the vertex,
+//   k_p1_cells          (cell-loop mode only) Algorithm 3 over the cell
+//                       columns with p1_prism per prism.
 // A NaN input or a non-straight prism anywhere in a DoF's stencil makes its
 // row sum NaN (NaN survives every product and sum), so every DoF is either
 // formed by the gather on a verified tensor-product stencil or recomputed in
-// full.  Every DoF of b is written by one thread, in a fixed order of
-// operations: the result does not depend on scheduling.
+// full.  In the gather mode every DoF of b is written by one thread, in a
+// fixed order of operations: the result does not depend on scheduling.
 
 struct LevelCoef {
   double z, lo, mid, hi;  // z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|), |h_m| (0 beyond the column)
 };
 
-__global__ void __launch_bounds__(256) k_levels(const double *__restrict__ X, int layers, LevelCoef *__restrict__ tab) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m > layers) return;
-  const double z = X[3 * (int64_t)m + 2];
-  const double hl = m > 0 ? fabs(z - X[3 * (int64_t)(m - 1) + 2]) : 0.0;
-  const double hh = m < layers ? fabs(X[3 * (int64_t)(m + 1) + 2] - z) : 0.0;
-  LevelCoef c;
-  c.z = z;
-  c.lo = hl;
-  c.mid = 2.0 * (hl + hh);
-  c.hi = hh;
-  tab[m] = c;
+// Level table (threads 0..layers), alpha_c per cell, and the sampled probe:
+// the DoFs of vertex columns q = s * stride, s < nsamp (all levels), must sit
+// at their column's level-0 x, y and at the height of column 0's level.
+__global__ void __launch_bounds__(256) k_p1_prep(const double *__restrict__ X, int layers, const int32_t *__restrict__ cmap,
+                                                 int64_t ncells, int64_t nsamp, int64_t stride,
+                                                 LevelCoef *__restrict__ tab, double *__restrict__ alpha,
+                                                 unsigned int *__restrict__ mode) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t col = (int64_t)layers + 1;
+  if (gid <= layers) {
+    const int m = (int)gid;
+    const double z = X[3 * (int64_t)m + 2];
+    const double hl = m > 0 ? fabs(z - X[3 * (int64_t)(m - 1) + 2]) : 0.0;
+    const double hh = m < layers ? fabs(X[3 * (int64_t)(m + 1) + 2] - z) : 0.0;
+    LevelCoef c;
+    c.z = z;
+    c.lo = hl;
+    c.mid = 2.0 * (hl + hh);
+    c.hi = hh;
+    tab[m] = c;
+  }
+  for (int64_t c = gid; c < ncells; c += gstride) {
+    double x[3], y[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int64_t cb = __ldg(cmap + c * 6 + 2 * a);
+      x[a] = __ldg(X + 3 * cb + 0);
+      y[a] = __ldg(X + 3 * cb + 1);
+    }
+    alpha[c] = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * (1.0 / 144.0);
+  }
+  int bad = 0;
+  for (int64_t i = gid; i < nsamp * col; i += gstride) {
+    const int64_t s = i / col, m = i - s * col;
+    const int64_t d0 = s * stride * col, d = d0 + m;
+    bad |= (__double_as_longlong(__ldg(X + 3 * d + 0)) != __double_as_longlong(__ldg(X + 3 * d0 + 0))) |
+           (__double_as_longlong(__ldg(X + 3 * d + 1)) != __double_as_longlong(__ldg(X + 3 * d0 + 1))) |
+           (__double_as_longlong(__ldg(X + 3 * d + 2)) != __double_as_longlong(__ldg(X + 3 * m + 2)));
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(mode, 1u);
+}
+
+// Row weights of Mh from alpha (gather mode only): entry (a, j) = the sum of
+// alpha over the one or two cells on edge (a, j), ascending; the diagonal is
+// the sum of the row's neighbour weights in row order.
+__global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict__ vrow, const int2 *__restrict__ vedge,
+                                                       const double *__restrict__ alpha, double *__restrict__ wts,
+                                                       int32_t nv, const unsigned int *__restrict__ mode) {
+  if (*mode) return;
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nv; a += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
+    double diag = 0.0;
+    for (int32_t t = t0 + 1; t < t1; ++t) {
+      const int2 e = __ldg(vedge + t);
+      const double w = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
+      wts[t] = w;
+      diag += w;
+    }
+    wts[t0] = diag;
+  }
 }
 
 #ifndef EXT_VTAB_MINB
@@ -884,21 +1036,22 @@ __global__ void __launch_bounds__(256) k_levels(const double *__restrict__ X, in
 #endif
 constexpr int kVGUnroll = EXT_VG_UNROLL;
 
-// DoF d is at its vertex's base x, y and at its level's height (bitwise)
-__device__ __forceinline__ int dof_straight(const double *__restrict__ X, const double *__restrict__ xy,
-                                            const LevelCoef *__restrict__ tab, int64_t d, FastDiv col) {
+// DoF d is at its column's level-0 x, y and at its level's height (bitwise)
+__device__ __forceinline__ int dof_straight(const double *__restrict__ X, const LevelCoef *__restrict__ tab, int64_t d,
+                                            FastDiv col) {
   const uint32_t q = fdiv((uint32_t)d, col);
   const uint32_t m = (uint32_t)d - q * col.d;
-  return (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 0))) &
-         (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 1))) &
+  const int64_t d0 = (int64_t)q * col.d;
+  return (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
+         (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
          (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(__ldg(&tab[m].z)));
 }
 
 __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *__restrict__ X, const double *__restrict__ f,
-                                                                const double *__restrict__ xy,
                                                                 const LevelCoef *__restrict__ tab,
                                                                 double *__restrict__ W, int64_t n, FastDiv col,
-                                                                Fp64Ones k1) {
+                                                                Fp64Ones k1, const unsigned int *__restrict__ mode) {
+  if (*mode) return;  // cell-loop mode: k_p1_cells forms b
   constexpr int VU = EXT_VT_VU;
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
@@ -921,8 +1074,9 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
         clo[u] = t0.y;
         cmid[u] = t1.x;
         chi[u] = t1.y;
-        ok[u] = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 0))) &
-                (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(xy + 2 * (int64_t)q + 1))) &
+        const int64_t d0 = (int64_t)q * col.d;
+        ok[u] = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
+                (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
                 (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(t0.x));
         fc[u] = __ldg(f + d);
       }
@@ -932,11 +1086,11 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
     int okb = 1, oka = 1;
     if (lane == 0 && base > 0 && base - 1 < n) {
       fb = __ldg(f + base - 1);
-      okb = dof_straight(X, xy, tab, base - 1, col);
+      okb = dof_straight(X, tab, base - 1, col);
     }
     if (lane == 31 && base + 32 * VU < n) {
       fa = __ldg(f + base + 32 * VU);
-      oka = dof_straight(X, xy, tab, base + 32 * VU, col);
+      oka = dof_straight(X, tab, base + 32 * VU, col);
     }
 #pragma unroll
     for (int u = 0; u < VU; ++u) {
@@ -982,9 +1136,14 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
 // current step is computed.  A step starts at an even DoF, so with 16-byte
 // aligned X and f every copy starts on a 16-byte boundary and has a length
 // that is a multiple of 16; a step whose clamped range is odd (the last one,
-// when n is odd) is filled by the lanes with plain loads.  Every wait is
-// bounded: when it runs out the kernel sets EXT_DERR_TIMEOUT, waits (bounded
-// again) for its other copy in flight and returns.
+// when n is odd) is filled by the lanes with plain loads.  A warp issues the
+// next step's copy only after the wait for the current one has succeeded, so
+// at most one of its copies is unconfirmed at any time.  Every wait is
+// bounded: when it runs out the warp sets EXT_DERR_TIMEOUT, waits once more
+// (bounded) for that copy and returns.  Test hook: skip_step >= 0 makes lane
+// 0 of the warp that owns that step leave its copy out (no arrival on the
+// barrier either), so the wait runs out with no copy in flight; wait_limit
+// is then small.
 constexpr int kBulkDofs = 64;              // DoFs per warp step
 constexpr int kBulkSpan = kBulkDofs + 4;   // with two DoFs before and two after
 constexpr unsigned kBulkWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
@@ -1006,8 +1165,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
-  for (unsigned i = 0; i < kBulkWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit) {
+  for (unsigned i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1021,10 +1180,12 @@ __device__ __forceinline__ void bulk_range(int64_t base, int64_t n, int64_t &lo,
 }
 
 __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *__restrict__ X, const double *__restrict__ f,
-                                                                 const double *__restrict__ xy,
                                                                  const LevelCoef *__restrict__ tab,
                                                                  double *__restrict__ W, int64_t n, FastDiv col,
-                                                                 Fp64Ones k1, unsigned int *err) {
+                                                                 Fp64Ones k1, unsigned int *err,
+                                                                 const unsigned int *__restrict__ mode, int64_t skip_step,
+                                                                 unsigned wait_limit) {
+  if (*mode) return;  // cell-loop mode: k_p1_cells forms b
   __shared__ BulkStage stage[8][2];
   __shared__ __align__(8) uint64_t bar[8][2];
   const int lane = threadIdx.x & 31;
@@ -1043,7 +1204,7 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
     int64_t lo, hi;
     bool bulk;
     bulk_range(stp * kBulkDofs, n, lo, hi, bulk, aligned);
-    if (bulk && lane == 0) {
+    if (bulk && lane == 0 && stp != skip_step) {
       const int64_t off = lo - (stp * kBulkDofs - 2);  // 0, or 2 for the first step
       const unsigned bx = (unsigned)(24 * (hi - lo)), bf = (unsigned)(8 * (hi - lo));
       const uint32_t b = smem_addr(&bar[warp][q]);
@@ -1065,29 +1226,25 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
   for (int it = 0; stp < nsteps; stp += wstride, ++it) {
     const int q = it & 1;
     const int64_t nxt = stp + wstride;
-    __syncwarp();  // every lane is done with stage q ^ 1 (the previous step)
-    if (nxt < nsteps) issue(nxt, q ^ 1);
     const int64_t base = stp * kBulkDofs;
     int64_t lo, hi;
     bool bulk;
     bulk_range(base, n, lo, hi, bulk, aligned);
     BulkStage &sg = stage[warp][q];
     if (bulk) {
-      if (!mbar_wait_bounded(&bar[warp][q], (q ? use1 : use0) & 1u)) {
+      const unsigned par = (q ? use1 : use0) & 1u;
+      if (!mbar_wait_bounded(&bar[warp][q], par, wait_limit)) {
+        // the only unconfirmed copy of this warp is this stage's
         if (lane == 0) atomicOr(err, EXT_DERR_TIMEOUT);
-        // the other stage may hold a copy in flight: wait for it (bounded) before leaving
-        int64_t lo2, hi2;
-        bool bulk2;
-        if (nxt < nsteps) {
-          bulk_range(nxt * kBulkDofs, n, lo2, hi2, bulk2, aligned);
-          if (bulk2) (void)mbar_wait_bounded(&bar[warp][q ^ 1], (q ? use0 : use1) & 1u);
-        }
-        (void)mbar_wait_bounded(&bar[warp][q], (q ? use1 : use0) & 1u);
+        (void)mbar_wait_bounded(&bar[warp][q], par, wait_limit);
         return;
       }
       if (q) ++use1;
       else ++use0;
-    } else {
+    }
+    __syncwarp();  // every lane is done with stage q ^ 1 (the previous step)
+    if (nxt < nsteps) issue(nxt, q ^ 1);
+    if (!bulk) {
       for (int64_t d = lo + lane; d < hi; d += 32) {
         const int64_t r = d - (base - 2);
         sg.X[3 * r + 0] = __ldg(X + 3 * d + 0);
@@ -1101,8 +1258,9 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
     auto ok_row = [&](int r, int64_t d) {
       const uint32_t qv = fdiv((uint32_t)d, col);
       const uint32_t m = (uint32_t)d - qv * col.d;
-      return (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 0))) &
-             (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 1))) &
+      const int64_t d0 = (int64_t)qv * col.d;
+      return (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
+             (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
              (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(__ldg(&tab[m].z)));
     };
     int ok[2];
@@ -1123,8 +1281,9 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
         cmid[u] = t1.x;
         chi[u] = t1.y;
         const int r = 32 * u + lane + 2;
-        ok[u] = (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 0))) &
-                (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(xy + 2 * (int64_t)qv + 1))) &
+        const int64_t d0 = (int64_t)qv * col.d;
+        ok[u] = (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
+                (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
                 (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(t0.x));
       }
     }
@@ -1152,14 +1311,24 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
   }
 }
 
+
 template <bool INC>
 __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double *__restrict__ W,
                                                                    const int32_t *__restrict__ vrow,
-                                                                   const double2 *__restrict__ vent,
+                                                                   const int32_t *__restrict__ vnbr,
+                                                                   const double *__restrict__ wts,
                                                                    double *__restrict__ b, int64_t n, FastDiv col,
-                                                                   Deferred dfr, unsigned int *err, Fp64Ones k1) {
+                                                                   Deferred dfr, unsigned int *err, Fp64Ones k1,
+                                                                   const unsigned int *__restrict__ mode) {
   constexpr int VU = EXT_VG_VU;
   const int lane = threadIdx.x & 31;
+  if (*mode) {
+    // cell-loop mode: k_p1_cells adds every contribution; WRITE clears b first
+    if (!INC)
+      for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x)
+        b[d] = 0.0;
+    return;
+  }
   const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 * VU; base < n; base += wstride) {
     int r0[VU], deg[VU];
@@ -1194,9 +1363,8 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
         ev[u] = 0.0;
         wv[u] = 0.0;
         if (t < deg[u]) {
-          const double2 en = __ldg(vent + r0[u] + t);
-          ev[u] = en.x;
-          wv[u] = __ldg(W + (int64_t)(int32_t)__double_as_longlong(en.y) + mm[u]);
+          ev[u] = __ldg(wts + r0[u] + t);
+          wv[u] = __ldg(W + (int64_t)__ldg(vnbr + r0[u] + t) + mm[u]);
         }
       }
 #pragma unroll
@@ -1220,10 +1388,11 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
 
 // The recorded DoFs of the gather: b_{a,m} (+)= the bottom-row entries of the
 // prisms (c, m) and the top-row entries of the prisms (c, m - 1) for every
-// cell c around vertex a, each from the 6-point rule with the general
-// Jacobian, summed in ascending cell order.
+// cell c around vertex a (p1_prism), summed in ascending cell order.  One
+// warp per record, one lane per DoF of its 32-DoF chunk.
 template <bool INC>
-__global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Launch p, Deferred dfr, FastDiv col) {
+__global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Launch p, Deferred dfr, FastDiv col,
+                                                                 Fp64Ones k1) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const unsigned int n = min(*dfr.count, dfr.cap);
@@ -1238,19 +1407,28 @@ __global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Lau
     for (int32_t t = __ldg(p.vcrow + q); t < __ldg(p.vcrow + q + 1); ++t) {
       const int64_t c = __ldg(p.vcells + t);
       int a = 0;
+      int32_t cb[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < 3; ++k) {
         if (__ldg(p.fmap + c * 6 + 2 * k) == v0) a = k;
+        cb[k] = __ldg(p.cmap + c * 6 + 2 * k);
+      }
+      long long rx[3], ry[3];
+      double k2, k6;
+      column_ref(p.X, cb, rx, ry, k2, k6);
       for (int half = 0; half < 2; ++half) {
         const int l = half == 0 ? m - 1 : m;
         if (l < 0 || l >= p.layers) continue;
-        int32_t cd[6], fd[6];
+        double Xp[6][3], fp[6], out[6];
+#pragma unroll
         for (int i = 0; i < 6; ++i) {
-          cd[i] = __ldg(p.cmap + c * 6 + i) + l * p.coff[i];
-          fd[i] = __ldg(p.fmap + c * 6 + i) + l * p.foff[i];
+          const int64_t cd = __ldg(p.cmap + c * 6 + i) + (int64_t)l * p.coff[i];
+          Xp[i][0] = __ldg(p.X + 3 * cd + 0);
+          Xp[i][1] = __ldg(p.X + 3 * cd + 1);
+          Xp[i][2] = __ldg(p.X + 3 * cd + 2);
+          fp[i] = __ldg(p.f + __ldg(p.fmap + c * 6 + i) + (int64_t)l * p.foff[i]);
         }
-        double out[6];
-        prism_general_g(p.X, p.f, cd, fd, out);
+        p1_prism(Xp, fp, rx, ry, k2, k6, k1, out);
         acc += out[2 * a + (half == 0 ? 1 : 0)];
       }
     }
@@ -1258,6 +1436,80 @@ __global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Lau
   }
 }
 
+#ifndef EXT_P1C_MINB
+#define EXT_P1C_MINB 2  // resident CTAs per SM the cell loop's registers must allow
+#endif
+
+// Cell-loop mode (Algorithm 3 on any coordinate field): a warp owns a group
+// of cpw whole cell columns and walks its flattened items (column, level m),
+// 32 consecutive items per step, lanes along a column's levels.  The lane of
+// item (c, m), m < layers, evaluates prism (c, m) once with p1_prism (the
+// vertical form on columns with vertical edges, e.g. terrain-following
+// levels; the general Jacobian otherwise); its bottom row belongs to level m
+// and stays with the lane, its top row belongs to level m + 1 and moves one
+// lane up (warp shuffle; the step's last lane hands it to the next step).
+// Each item then adds its three values to the vertex DoFs with FP64 atomic
+// adds.  mode (if given) is the word the probe sets: a zero word (a flat,
+// straight extrusion, which the gather form handles) makes the kernel exit.
+__global__ void __launch_bounds__(kWarps * 32, EXT_P1C_MINB) k_p1_cells(const MassP1Launch p, int cpw, Fp64Ones k1,
+                                                                       const unsigned int *__restrict__ mode) {
+  if (mode && *mode == 0u) return;
+  __shared__ ColInfo cols[kWarps][kMaxCols];
+  __shared__ double kk[kWarps][kMaxCols][2];  // k2, k6 of each column
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  const int layers = p.layers, L1 = layers + 1;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    if (lane < ncol) {
+      ColInfo &ci = cols[warp][lane];
+      setup_column<false>(p, c0 + lane, ci);
+      const double det2 = ci.alpha * 144.0;  // |2A| of the level-0 triangle
+      kk[warp][lane][0] = det2 * (1.0 / 864.0);
+      kk[warp][lane][1] = det2 * (1.0 / 2592.0);
+    }
+    __syncwarp();
+    const int nitems = ncol * L1;
+    double carry[3] = {0.0, 0.0, 0.0};
+    for (int base = 0; base < nitems; base += 32) {
+      const int it = base + lane;
+      const bool valid = it < nitems;
+      const int cl = valid ? it / L1 : 0;
+      const int m = valid ? it - cl * L1 : L1;
+      const ColInfo &ci = cols[warp][cl];
+      double r0[3] = {0.0, 0.0, 0.0}, r1[3] = {0.0, 0.0, 0.0};
+      if (m < layers) {
+        double Xp[6][3], fp[6], out[6];
+        load_prism(p, ci, m, layers, Xp, fp);
+        p1_prism(Xp, fp, ci.rx, ci.ry, kk[warp][cl][0], kk[warp][cl][1], k1, out);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          r0[a] = out[2 * a];
+          r1[a] = out[2 * a + 1];
+        }
+      }
+      // top rows one lane up: item (c, m) receives prism (c, m - 1)'s top row;
+      // at m = 0 the lane below holds the previous column's top level, which
+      // has no prism above it and passes zeros
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double up = __shfl_up_sync(kFull, r1[a], 1);
+        const double last = __shfl_sync(kFull, r1[a], 31);
+        if (lane == 0) up = carry[a];
+        carry[a] = last;
+        r0[a] = fadd(r0[a], up, k1);
+      }
+      if (valid) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) atomicAdd(p.b + dof_at(ci.bbot[a], ci.btop[a], p.boff[2 * a], m, layers), r0[a]);
+      }
+    }
+    __syncwarp();
+  }
+}
 
 
 // Resident CTAs per SM of a kernel (one GPU model per process).
@@ -1272,16 +1524,24 @@ int resident_ctas(K kernel, int &cache) {
 
 }  // namespace
 
-// The split form runs unless the launch is small (under a million
-// (column, level) items), its scratch cannot be allocated, or the
-// environment variable EXTMESH_MASS_FUSED=1 asks for the single-pass kernel
-// (each cell evaluates its own vertical sums; no scratch; the same results up
-// to rounding); EXTMESH_MASS_FUSED=0 asks for the split form at any size.
-// With constant layers on a mesh that has base coordinates the split form is
-// the gather form (EXTMESH_MASS_GATHER=0 turns it off); otherwise, with
-// constant layers, it is factored (area pass, vertex part in the vertex pass)
-// from EXT_FACTORED_MIN_LAYERS layers on; EXTMESH_MASS_FACTORED=1 / 0 asks
-// for that at any layer count / never.
+// Forms of the launch (ext_set_option(EXT_OPT_P1_FORM, ...)):
+//   EXT_P1_AUTO   under a million (column, level) items the single-pass
+//                 kernel; otherwise as EXT_P1_SPLIT;
+//   EXT_P1_SPLIT  constant layers on a mesh with vertex rows: the probe
+//                 decides between the gather form (a flat, straight
+//                 extrusion) and the cell loop (any other coordinate field);
+//                 variable layers: the variable-layer split form; no vertex
+//                 rows: the factored form from EXT_FACTORED_MIN_LAYERS layers,
+//                 else the unfactored one;
+//   EXT_P1_GATHER the gather form without the probe (DoFs next to a prism
+//                 that is not straight are recomputed one by one);
+//   EXT_P1_FACTORED / EXT_P1_UNFACTORED  the split form with / without the
+//                 area pass (Algorithm 3 over cells on vertical sums);
+//   EXT_P1_CELLS  the cell loop k_p1_cells;
+//   EXT_P1_SINGLE the single-pass kernel.
+// Variable layers take the variable-layer split form under every form but
+// EXT_P1_SINGLE.  When the scratch cannot be allocated the single-pass
+// kernel runs.
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   const bool var = p.cell_layers != nullptr;
@@ -1292,46 +1552,47 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   const int64_t blocks0 = (warps + kWarps - 1) / kWarps;
-  static int sms = 0, fused_env = -1, fac_env = -1, gather_env = -1;
-  static int res_cells[3] = {0, 0, 0}, res_fused[2] = {0, 0};
+  static int sms = 0;
+  static int res_cells[3] = {0, 0, 0}, res_fused[2] = {0, 0}, res_p1c = 0, res_vgg[2] = {0, 0};
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (fused_env < 0) {  // 1: always the single pass; 0: always the split form; unset: by size
-    const char *ev = getenv("EXTMESH_MASS_FUSED");
-    fused_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
-    ev = getenv("EXTMESH_MASS_FACTORED");  // 1 / 0: factored split form always / never; unset: by layers
-    fac_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
-    ev = getenv("EXTMESH_MASS_GATHER");  // 0: never the gather form; unset: whenever the mesh has vertex rows
-    gather_env = (ev && ev[0] == '0') ? 0 : 1;
-  }
-  const bool gather = !var && p.vrow && p.vent && p.vcrow && p.vcells && gather_env == 1;
-  const bool factored = !var && !gather && (fac_env == 1 || (fac_env == 2 && p.layers >= EXT_FACTORED_MIN_LAYERS));
-  // The vertical sums, the vertex area sums A and the list of deferred warp
-  // steps go to stream-ordered scratch, so launches on different streams
-  // never share it.
+  int form = p1_form();
+  const double items = L1 * (double)p.ncells;
+  // on a small launch the split form's extra passes, scratch allocation and
+  // launches (about 25 us together) cost more than they save
+  if (form == EXT_P1_AUTO) form = items < 1.0e6 ? EXT_P1_SINGLE : EXT_P1_SPLIT;
+  const bool rows = !var && p.vrow && p.vnbr && p.vedge && p.vcrow && p.vcells && p.nvent > 0;
+  if (!var && !rows && (form == EXT_P1_GATHER || form == EXT_P1_SPLIT))
+    form = p.layers >= EXT_FACTORED_MIN_LAYERS ? EXT_P1_FACTORED : EXT_P1_UNFACTORED;
+  const bool gather = !var && (form == EXT_P1_SPLIT || form == EXT_P1_GATHER);
+  const bool probe = !var && form == EXT_P1_SPLIT;
+  const bool cells = !var && form == EXT_P1_CELLS;
+  const bool factored = !var && form == EXT_P1_FACTORED;
+  const Fp64Ones k1 = {1.0, -1.0, -0.0};
   const int64_t n = p.nf;
-  const double items = (var ? p.mean_layers + 1.0 : (double)(p.layers + 1)) * (double)p.ncells;
-  // deferred warp steps: one per warp step of the cell pass at most, or
-  // one per 32-DoF chunk of the gather
+  // Scratch from the stream-ordered pool, so launches on different streams
+  // never share it: a 256-byte block (the recorded-step counter, then the
+  // mode word), the vertical sums W, the vertex area sums A (factored), the
+  // level table, alpha per cell and the row weights (gather), alpha per cell
+  // (factored), and the list of recorded steps: one per warp step of the
+  // cell pass at most, or one per 32-DoF chunk of the gather.
+  char *scr = nullptr;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nn = (size_t)(n > 0 ? n : 1);
   const int64_t cap64 = gather ? (n + 31) / 32 + 1
                                : (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
-  const size_t nn = (size_t)(n > 0 ? n : 1);
-  const size_t wbytes = (sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)) + 255) & ~(size_t)255;
-  const size_t nverts = factored ? (size_t)(n / (p.layers + 1)) : 0;
-  // factored: A (per vertex) and alpha (per cell)
-  const size_t abytes = (sizeof(double) * nverts + 255) & ~(size_t)255;
-  const size_t cbytes = factored ? ((sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255)
-                                  : (gather ? ((sizeof(LevelCoef) * (size_t)(p.layers + 1) + 255) & ~(size_t)255) : 0);
-  char *scr = nullptr;
-  // on a small launch the split form's extra passes, scratch allocation and
-  // launches (about 25 us together) cost more than they save
-  const bool small = items < 1.0e6 && fused_env == 2;
-  if (fused_env != 1 && !small &&
-      cudaMallocAsync(reinterpret_cast<void **>(&scr), wbytes + 256 + abytes + cbytes + sizeof(int2) * (size_t)cap, s) !=
+  const size_t wbytes = cells ? 0 : al(sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)));
+  const size_t abytes = factored ? al(sizeof(double) * (size_t)(n / (p.layers + 1))) : 0;
+  const size_t tbytes = gather ? al(sizeof(LevelCoef) * (size_t)(p.layers + 1)) : 0;
+  const size_t cbytes = (gather || factored) ? al(sizeof(double) * (size_t)p.ncells) : 0;
+  const size_t ebytes = gather ? al(sizeof(double) * (size_t)p.nvent) : 0;
+  const size_t lbytes = cells ? 0 : sizeof(int2) * (size_t)cap;
+  if (form != EXT_P1_SINGLE &&
+      cudaMallocAsync(reinterpret_cast<void **>(&scr), 256 + wbytes + abytes + tbytes + cbytes + ebytes + lbytes, s) !=
           cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;
@@ -1347,27 +1608,41 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     else k_mass_p1<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
     return cudaGetLastError();
   }
-  const int res = var ? resident_ctas(k_mass_cells<true, false>, res_cells[1])
-                      : (factored ? resident_ctas(k_mass_cells<false, true>, res_cells[0])
-                                  : resident_ctas(k_mass_cells<false, false>, res_cells[2]));
-  const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
-  double *W = reinterpret_cast<double *>(scr);
-  double *A = reinterpret_cast<double *>(scr + wbytes + 256);
+  unsigned int *count = reinterpret_cast<unsigned int *>(scr);
+  unsigned int *mode = count + 1;
+  double *W = reinterpret_cast<double *>(scr + 256);
+  double *A = reinterpret_cast<double *>(scr + 256 + wbytes);
+  LevelCoef *tab = reinterpret_cast<LevelCoef *>(scr + 256 + wbytes + abytes);
+  double *alpha = reinterpret_cast<double *>(scr + 256 + wbytes + abytes + tbytes);
+  double *wts = reinterpret_cast<double *>(scr + 256 + wbytes + abytes + tbytes + cbytes);
   Deferred dfr;
-  dfr.count = reinterpret_cast<unsigned int *>(scr + wbytes);
-  double *alpha = reinterpret_cast<double *>(scr + wbytes + 256 + abytes);
-  dfr.list = reinterpret_cast<int2 *>(scr + wbytes + 256 + abytes + cbytes);
+  dfr.count = count;
+  dfr.list = reinterpret_cast<int2 *>(scr + 256 + wbytes + abytes + tbytes + cbytes + ebytes);
   dfr.cap = cap;
-  // one memset clears the deferred-step counter and A
-  cudaError_t e = cudaMemsetAsync(scr + wbytes, 0, 256 + abytes, s);
-  int64_t vb = (n + 255) / 256;
-  if (vb > (int64_t)sms * 8) vb = (int64_t)sms * 8;
-  if (vb < 1) vb = 1;
+  // one memset clears the counter, the mode word and A
+  cudaError_t e = cudaMemsetAsync(scr, 0, 256, s);
+  if (e == cudaSuccess && factored && abytes) e = cudaMemsetAsync(A, 0, abytes, s);
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
-  const Fp64Ones k1 = {1.0, -1.0, -0.0};
-  if (e == cudaSuccess && gather) {
-    LevelCoef *tab = reinterpret_cast<LevelCoef *>(alpha);  // the table takes the place of alpha
-    static int res_vtab = 0, res_vg[2] = {0, 0};
+  const int rc = resident_ctas(k_p1_cells, res_p1c);
+  const int64_t gc = blocks0 < (int64_t)rc * sms ? blocks0 : (int64_t)rc * sms;
+  if (e == cudaSuccess && cells) {
+    if (p.overwrite) e = cudaMemsetAsync(p.b, 0, sizeof(double) * (size_t)n, s);
+    if (e == cudaSuccess) {
+      k_p1_cells<<<(unsigned)gc, kWarps * 32, 0, s>>>(p, cpw, k1, nullptr);
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess && gather) {
+    static int res_vtab = 0, res_vg[2] = {0, 0}, res_vb = 0;
+    static int64_t skip_step = -2;
+    if (skip_step == -2) {
+      // test hook, read once per process: the first bulk-copy vertex pass
+      // leaves out the copy of this step (its wait then runs out)
+      const char *ev = getenv("EXTMESH_TEST_BULK_SKIP");
+      skip_step = ev ? atoll(ev) : -1;
+    }
+    const int64_t skip = skip_step;
+    skip_step = -1;
+    const unsigned wait_limit = skip >= 0 ? (1u << 12) : kBulkWaitLimit;
     const int rv = resident_ctas(k_vsum_tab, res_vtab);
     const int rg = p.overwrite ? resident_ctas(k_vgather<false>, res_vg[0]) : resident_ctas(k_vgather<true>, res_vg[1]);
     int64_t gv = ((n + 32 * EXT_VT_VU - 1) / (32 * EXT_VT_VU) + 7) / 8;  // CTAs of 8 warps, one warp step each
@@ -1376,41 +1651,60 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     if (gg > (int64_t)rg * sms) gg = (int64_t)rg * sms;
     if (gv < 1) gv = 1;
     if (gg < 1) gg = 1;
-    k_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab);
+    // probe: about 4096 vertex columns, every level
+    const int64_t nv = p.nverts;
+    const int64_t stride = nv > 4096 ? (nv + 4095) / 4096 : 1;
+    const int64_t nsamp = probe ? (nv + stride - 1) / stride : 0;
+    int64_t gp = ((int64_t)p.ncells > nsamp * (p.layers + 1) ? (int64_t)p.ncells : nsamp * (p.layers + 1)) / 256 + 1;
+    if (gp > (int64_t)sms * 8) gp = (int64_t)sms * 8;
+    if (gp * 256 < (int64_t)p.layers + 1) gp = ((int64_t)p.layers + 1 + 255) / 256;
+    k_p1_prep<<<(unsigned)gp, 256, 0, s>>>(p.X, p.layers, p.cmap, p.ncells, nsamp, stride, tab, alpha, mode);
+    int64_t gw = (nv + 255) / 256;
+    if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
+    k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vedge, alpha, wts, (int32_t)nv, mode);
     if (EXT_VSUM_BULK) {
-      static int res_vb = 0;
       const int rb = resident_ctas(k_vsum_bulk, res_vb);
       int64_t gb = ((n + kBulkDofs - 1) / kBulkDofs + 7) / 8;  // CTAs of 8 warps, one warp step each
       if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
       if (gb < 1) gb = 1;
-      k_vsum_bulk<<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1, p.err);
+      k_vsum_bulk<<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, skip, wait_limit);
     } else {
-      k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, p.base_xy, tab, W, n, col, k1);
+      k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode);
     }
     if (p.overwrite) {
-      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vent, p.b, n, col, dfr, p.err, k1);
-      k_vgather_general<false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, col);
+      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode);
+      const int r = resident_ctas(k_vgather_general<false>, res_vgg[0]);
+      k_vgather_general<false><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
     } else {
-      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vent, p.b, n, col, dfr, p.err, k1);
-      k_vgather_general<true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, dfr, col);
+      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode);
+      const int r = resident_ctas(k_vgather_general<true>, res_vgg[1]);
+      k_vgather_general<true><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
     }
+    if (probe) k_p1_cells<<<(unsigned)gc, kWarps * 32, 0, s>>>(p, cpw, k1, mode);
     e = cudaGetLastError();
   } else if (e == cudaSuccess) {
+    const int res = var ? resident_ctas(k_mass_cells<true, false>, res_cells[1])
+                        : (factored ? resident_ctas(k_mass_cells<false, true>, res_cells[0])
+                                    : resident_ctas(k_mass_cells<false, false>, res_cells[2]));
+    const int64_t blocks = blocks0 < (int64_t)res * sms ? blocks0 : (int64_t)res * sms;
+    int64_t vb = (n + 255) / 256;
+    if (vb > (int64_t)sms * 8) vb = (int64_t)sms * 8;
+    if (vb < 1) vb = 1;
     if (var) {
       k_vsum<true, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, p.b, k1, nullptr, p.overwrite);
       k_mass_cells<true, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
-      k_mass_general<true, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
+      k_mass_general<true, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr, k1);
     } else if (factored) {
       int64_t ab = (p.ncells + 255) / 256;
       if (ab > (int64_t)sms * 8) ab = (int64_t)sms * 8;
       k_area<<<(unsigned)ab, 256, 0, s>>>(p, A, alpha, col);
       k_vsum<false, true><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, A, p.b, k1, p.base_xy, p.overwrite);
       k_mass_cells<false, true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, alpha);
-      k_mass_general<false, true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, alpha);
+      k_mass_general<false, true><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, alpha, k1);
     } else {
       k_vsum<false, false><<<(unsigned)vb, 256, 0, s>>>(p.X, p.f, W, n, col, nullptr, p.b, k1, nullptr, p.overwrite);
       k_mass_cells<false, false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, W, dfr, cpw, k1, nullptr);
-      k_mass_general<false, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr);
+      k_mass_general<false, false><<<(unsigned)sms * 2, kWarps * 32, 0, s>>>(p, W, dfr, cpw, nullptr, k1);
     }
     e = cudaGetLastError();
   }

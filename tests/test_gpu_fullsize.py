@@ -93,6 +93,36 @@ def test_fullsize_prisms_1M_by_100():
     assert not torch.isnan(out).any()
 
 
+@pytest.mark.parametrize("kind", ["terrain", "tilted"])
+def test_fullsize_non_flat_prisms_1M_by_100(kind):
+    """The benchmark mesh (999,698 triangles x 100 layers) with
+    terrain-following levels (every prism's top face tilted) or, in addition,
+    leaning columns: the default launch (the probe picks the cell loop) and
+    the mass action with WRITE access, on sampled cells."""
+    m = meshgen.tri_mesh(707, seed=1604, order="rcm")
+    L = 100
+    gm = E.Mesh(m.cells, m.xy, L)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    p1 = E.Space(gm, "CG1xCG1")
+    ocs, _ = O.coords(m.cells, m.xy, L)
+    op1 = O.number(m.cells, m.nverts, L, P1)
+    X = meshgen.level_coords(m, L, seed=1615, kind=kind).reshape(-1)
+    x = meshgen.uniform_field(op1.ndofs, 1616)
+    y = torch.full((p1.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, torch.from_numpy(X).to(dev), E.EXT_READ),
+               (p1, torch.from_numpy(x).to(dev), E.EXT_READ), (p1, y, E.EXT_WRITE))
+    E.ext_sync_check()
+    got = y.cpu().numpy()
+    assert not np.isnan(got).any()
+    rng = np.random.default_rng(8)
+    sample = np.concatenate([rng.choice(m.ncells, 300, replace=False), [0, m.ncells - 1]])
+    cl = closure(m.cells, sample)
+    ref, absr = np.zeros(op1.ndofs), np.zeros(op1.ndofs)
+    O.par_loop(O.K_MASS, np.ascontiguousarray(m.cells[cl]), L,
+               [(sub(ocs, cl), X, 3, O.READ), (sub(op1, cl), x, 1, O.READ), (sub(op1, cl), ref, 1, O.INC, absr)])
+    close_at(got, ref, absr, sampled_dofs(op1, sample, L))
+
+
 @pytest.mark.parametrize("name", ["Q2xP2", "DG2hex"])
 def test_fullsize_hexes_500k_by_64(name):
     q = meshgen.quad_mesh(707, seed=1608, order="rcm")

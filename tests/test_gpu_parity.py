@@ -246,26 +246,23 @@ def test_mass_general_geometry_partial(layers, with_xy):
     close(host(b), ref, absr)
 
 
-@pytest.mark.parametrize("form", [{"EXTMESH_MASS_FUSED": "0"}, {"EXTMESH_MASS_FUSED": "1"},
-                                  {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_GATHER": "0"},
-                                  {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_GATHER": "0",
-                                   "EXTMESH_MASS_FACTORED": "0"},
-                                  {"EXTMESH_MASS_FUSED": "0", "EXTMESH_MASS_GATHER": "0",
-                                   "EXTMESH_MASS_FACTORED": "1"},
+@pytest.mark.parametrize("form", [{"EXTMESH_P1_FORM": "split"}, {"EXTMESH_P1_FORM": "single"},
+                                  {"EXTMESH_P1_FORM": "gather"}, {"EXTMESH_P1_FORM": "unfactored"},
+                                  {"EXTMESH_P1_FORM": "factored"}, {"EXTMESH_P1_FORM": "cells"},
                                   {"EXTMESH_TP_FLAGS": "1"}],
-                         ids=["split", "single", "split-nogather", "split-unfactored", "split-factored", "tp-flags"])
+                         ids=["split", "single", "gather", "split-unfactored", "split-factored", "cells", "tp-flags"])
 def test_mass_forced_form(form):
-    """Every form of the P1xP1 launch passes the same parity tests: the split
-    forms (the default for launches of a million items or more) -- the gather
-    form (Mv per vertex column, then the base mass matrix's vertex rows per
-    level; constant layers on a mesh with base coordinates), the factored
-    form (vertex part A_a w_a in the vertex pass, then the cell pass; constant
-    layers otherwise, from two layers) and the unfactored one -- and the
-    single-pass kernel (the default below a million items, and the fallback
-    when the split form's scratch cannot be allocated), each forced by
-    EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and EXTMESH_MASS_FACTORED in a
-    child process; and the nine-space kernels' flagged form (straightness
-    bits per coordinate DoF, the default from a million items) forced at every
+    """Every form of the P1xP1 launch passes the same parity tests, each
+    forced at every size by EXTMESH_P1_FORM (read once per process, so in a
+    child process): the split form (a probe of the coordinates picks the
+    gather form on a flat, straight extrusion -- Mv per vertex column, then
+    the base mass matrix's vertex rows per level -- and the cell loop
+    otherwise), the gather form without the probe, the factored and
+    unfactored cell passes over vertical sums, the cell loop (one element
+    vector per prism), and the single-pass kernel (the default below a
+    million items, and the fallback when the split forms' scratch cannot be
+    allocated); and the nine-space kernels' flagged form (straightness bits
+    per coordinate DoF, the default from a million items) forced at every
     size by EXTMESH_TP_FLAGS."""
     import os
     import subprocess
