@@ -3,16 +3,16 @@
 
 Default workload (one step = the three FP64 loops of the ~1M-triangle,
 100-layer prism mesh, RCM-ordered): P1xP1 RHS assembly of int f v dx with
-f = sin(x) cos(y) z (INC), P1xP1 mass-matrix action y += M x with x ~ U(-1,1)
-(INC, outputs zeroed every step), and DG1xDG1 nodal interpolation of x
-(WRITE).  Valuable bytes (each coordinate, input, output DoF and stencil-map
-entry moved once) / device time.
+f = sin(x) cos(y) z, P1xP1 mass-matrix action y = M x with x ~ U(-1,1) (both
+with WRITE access), and DG1xDG1 nodal interpolation of x (WRITE).  Valuable
+bytes (each coordinate, input, output DoF and stencil-map entry moved once) /
+device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2|3|4|5|6|7]
+                    [--config 2|3|4|5|6|7|8] [--geometry flat|terrain|tilted]
 
---impl reference times the CPU oracle on a bounded sample of the same
-workload (the reference arm: there is no reference GPU code).  Under torchrun
+--impl reference times the CPU oracle (all host cores) on a bounded sample of
+the same workload (the reference arm: there is no reference GPU code).  Under torchrun
 every rank runs its own independent copy of the workload (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
@@ -57,40 +57,59 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 # their products and sums as DFMA (a b + (-0), a (+-1) + b).  All send 3 FP64
 # atomic adds per item to L2.  Evaluating each cell's element matrix by itself
 # instead needs 18 FP64 operations per item.
-# Gather form (constant layers, mesh with base coordinates; the default):
-#   w = |h_lo| f_lo + 2 (|h_lo| + |h_hi|) f + |h_hi| f_hi   3 DFMA per DoF,
-#   b_{a,m} = sum over the vertex row of a of weight x w   1 DFMA per row entry and level,
-# with V + 2E row entries (each vertex and each of its neighbours), four
-# kernels (level table, vertex pass, gather, the pass over recorded DoFs,
-# which finds none on a straight mesh), no atomics.
-GATHER_OPS_PER_DOF = 3
-P1_MIX = {  # (dadd, dmul, dfma) per DoF, per item, per cell
-    "factored": ((0, 0, 6), (0, 0, 3), (4, 2, 1)),
-    "plain": ((0, 0, 5), (0, 0, 6), (0, 0, 0)),
-    "var": ((0, 0, 6), (0, 0, 6), (0, 0, 0)),
-}
-P1_KERNELS = {"gather": 4, "factored": 4, "plain": 3, "var": 3, "single": 1}
+# FP64 operations of one P1xP1 RHS / mass-action launch, per form (as the
+# kernels issue them; products and sums all go to the DFMA pipe):
+#   gather   3 per DoF (column mass matrix Mv) + 1 per vertex-row entry and
+#            level (V + 2E entries: base mass matrix Mh) + the per-launch
+#            geometry (7 per cell for the level-0 areas, 4 per edge for the
+#            row weights); no atomics;
+#   factored 6 per DoF + 3 per (column, level) item + 7 per cell, 3 L2 atomic
+#            adds per item;
+#   cells    42 per prism with vertical edges (closed form of the 6-point
+#            rule), 132 per prism otherwise (general Jacobian), + 3 per item,
+#            3 L2 atomic adds per item;
+#   single   13 per item (below a million items).
+P1_PRISM_OPS = {"vertical": 42, "general": 132}
+P1_KERNELS = {"gather": 6, "cells": 6, "cells-forced": 1, "factored": 4, "plain": 3, "var": 3, "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
-CELLWISE_OPS_PER_ITEM = 18
-SINGLE_PASS_SM_OPS_PER_ITEM = 13
 P1_SPLIT_MIN_ITEMS = 1_000_000
 P1_FACTORED_MIN_LAYERS = 2
 
 
-def p1_form(items: int, layers: int, var: bool = False) -> str:
-    """The form the library picks for a P1xP1 launch on a mesh with base
-    coordinates (EXTMESH_MASS_FUSED, EXTMESH_MASS_GATHER and
-    EXTMESH_MASS_FACTORED override its choice as they do the library's)."""
-    fused, fac = os.environ.get("EXTMESH_MASS_FUSED", ""), os.environ.get("EXTMESH_MASS_FACTORED", "")
-    if fused == "1" or (fused != "0" and items < P1_SPLIT_MIN_ITEMS):
+def p1_form(items: int, layers: int, var: bool = False, geometry: str = "flat") -> str:
+    """The form the library's default picks for a P1xP1 launch on a triangle
+    mesh: the single pass below a million items, the variable-layer split form
+    on variable layers, else the probe's choice (gather on a flat straight
+    extrusion, the cell loop on any other geometry)."""
+    if items < P1_SPLIT_MIN_ITEMS:
         return "single"
     if var:
         return "var"
-    if os.environ.get("EXTMESH_MASS_GATHER", "") != "0":
-        return "gather"
-    if fac in ("0", "1"):
-        return "factored" if fac == "1" else "plain"
-    return "factored" if layers >= P1_FACTORED_MIN_LAYERS else "plain"
+    return "gather" if geometry == "flat" else "cells"
+
+
+def p1_ops_form(form: str, ndofs: int, items: int, ncells: int, layers: int, nedges: int,
+                geometry: str = "flat") -> int:
+    nv = ndofs // (layers + 1)
+    if form == "gather":
+        return 3 * ndofs + (nv + 2 * nedges) * (layers + 1) + 7 * ncells + 4 * nedges
+    if form == "factored":
+        return 6 * ndofs + 3 * items + 7 * ncells
+    if form in ("cells", "cells-forced"):
+        per = P1_PRISM_OPS["general" if geometry == "tilted" else "vertical"]
+        return per * ncells * layers + 3 * items
+    if form == "var":
+        return 6 * ndofs + 6 * items
+    if form == "plain":
+        return 5 * ndofs + 6 * items
+    return 13 * items
+
+
+def p1_bytes_8d(nverts: int, ncells: int, layers: int) -> int:
+    """Algorithmic bytes of one P1xP1 RHS / mass-action launch: coordinates
+    (24 per vertex level), input and output (8 + 8), one int32 map row of 6
+    entries per base cell, each moved once."""
+    return 40 * nverts * (layers + 1) + 24 * ncells
 
 
 def euler_edges(nverts: int, ncells: int) -> int:
@@ -99,30 +118,17 @@ def euler_edges(nverts: int, ncells: int) -> int:
     return nverts + ncells - 1
 
 
-def p1_counts(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None) -> tuple:
-    """(DADD, DMUL, DFMA) of one P1xP1 RHS / mass-action launch; the single-pass
-    kernel below a million items executes 13 operations per item on the SM
-    (3 DMUL, 6 DFMA, 4 for the layer factors counted as DFMA; the horizontal
-    sum in L2 atomics).  The gather form needs the base edge count (default:
-    Euler's formula)."""
-    form = p1_form(items, layers, var)
-    if form == "single":
-        return (0, 3 * items, 10 * items)
-    if form == "gather":
-        nv = ndofs // (layers + 1)
-        ne = euler_edges(nv, ncells) if nedges is None else nedges
-        return (0, 0, GATHER_OPS_PER_DOF * ndofs + (nv + 2 * ne) * (layers + 1))
-    per = P1_MIX[form]
-    return tuple(per[0][k] * ndofs + per[1][k] * items + per[2][k] * ncells for k in range(3))
+def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None,
+           geometry: str = "flat") -> int:
+    """FP64 operations of the default form (nedges: Euler's formula unless given)."""
+    nv = ndofs // (layers + 1)
+    ne = euler_edges(nv, ncells) if nedges is None else nedges
+    return p1_ops_form(p1_form(items, layers, var, geometry), ndofs, items, ncells, layers, ne, geometry)
 
 
-P1_OPS_NOTE = (f"gather form from {P1_SPLIT_MIN_ITEMS} (column, level) items: {GATHER_OPS_PER_DOF} per DoF "
-               "(column mass matrix) + 1 per vertex-row entry and level (V + 2E entries: base mass matrix); "
-               "single pass below: 13 per column level")
-
-
-def p1_ops(ndofs: int, items: int, ncells: int, layers: int, var: bool = False, nedges: int | None = None) -> int:
-    return sum(p1_counts(ndofs, items, ncells, layers, var, nedges))
+P1_OPS_NOTE = ("default form from a million (column, level) items: gather on a flat straight extrusion "
+               "(3 per DoF + 1 per vertex-row entry and level + 7 per cell + 4 per edge), cell loop otherwise "
+               "(42 per prism with vertical edges + 3 per item); single pass below: 13 per item")
 
 
 def tp_kernels(items: int) -> int:
@@ -142,15 +148,8 @@ def base_edges(cells) -> int:
     return int(np.unique(e[:, 0] * (int(c.max()) + 1) + e[:, 1]).size) if c.size else 0
 
 
-def p1_kernels(items: int, layers: int, var: bool = False) -> int:
-    return P1_KERNELS[p1_form(items, layers, var)]
-
-
-def p1_mix_ceiling(ndofs: int, items: int, ncells: int, layers: int, rates: dict, var: bool = False,
-                   nedges: int | None = None) -> float:
-    """G op/s ceiling of that operation mix at the measured DFMA/DADD/DMUL rates."""
-    dadd, dmul, dfma = p1_counts(ndofs, items, ncells, layers, var, nedges)
-    return (dfma + dadd + dmul) / (dfma / rates["dfma"] + dadd / rates["dadd"] + dmul / rates["dmul"])
+def p1_kernels(items: int, layers: int, var: bool = False, geometry: str = "flat") -> int:
+    return P1_KERNELS[p1_form(items, layers, var, geometry)]
 
 
 def peaks():
@@ -269,6 +268,52 @@ def valuable_bytes_cfg2(V, C, L, maps=True):
     return {"rhs": k1, "mass": k1, "interp": k5, "total": 2 * k1 + k5}
 
 
+def geometry_coords(m, L, geometry, dev):
+    """Coordinate field of the benchmark mesh: the flat unit-height extrusion
+    comes from EXT_K_EXTRUDE; terrain-following levels and leaning columns
+    (meshgen.level_coords) are uploaded."""
+    import torch
+    return torch.from_numpy(meshgen.level_coords(m, L, seed=SEED + 20, kind=geometry).reshape(-1)).to(dev)
+
+
+def time_p1_forms(E, gm, cs, p1, X, x, y, stream, forms, reps):
+    """Mean device time (ms) of one mass-action launch (WRITE) in each form,
+    forced with ext_set_option; reps back to back after one warm-up launch
+    (inputs larger than L2)."""
+    import torch
+    old = E.ext_get_option(E.EXT_OPT_P1_FORM)
+    out = {}
+    args = [(cs.handle, X, E.EXT_READ), (p1.handle, x, E.EXT_READ), (p1.handle, y, E.EXT_WRITE)]
+    try:
+        for name in forms:
+            E.ext_set_option(E.EXT_OPT_P1_FORM, E.P1_FORMS[name])
+            E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, args, stream.cuda_stream)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, args, stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            E.ext_sync_check(stream.cuda_stream)
+            out[name] = a.elapsed_time(b) / reps
+    finally:
+        E.ext_set_option(E.EXT_OPT_P1_FORM, old)
+    return out
+
+
+def form_entry(form, ms, V, C, L, E_, geometry, ops_peak, hbm, launches=None):
+    ndofs, items = V * (L + 1), C * (L + 1)
+    ops = p1_ops_form(form, ndofs, items, C, L, E_, geometry)
+    nbytes = p1_bytes_8d(V, C, L)
+    gops = ops / (ms * 1e-3) / 1e9
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"ms": round(ms, 4), "fp64_ops": ops, "fp64_gops": round(gops, 1),
+            "fp64_frac": round(gops / ops_peak, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+            "l2_atomic_adds_per_item": 0 if form == "gather" else CELL_ATOMICS_PER_ITEM,
+            "kernels": P1_KERNELS[form] if launches is None else launches}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_1604_05937_gb300 as E
@@ -276,13 +321,20 @@ def run_ours(args, rank, world, local):
     init_dist(world, local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    geometry = args.geometry
     m = meshgen.tri_mesh(args.n or N_CFG2, seed=SEED + rank, order=args.order)
     L = args.layers or LAYERS_CFG2
-    gm = E.Mesh(m.cells, m.xy, L)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    gm = E.Mesh(m.cells, m.xy, L)  # ext_mesh_create: device topology, vertex rows
+    t_mesh = time.perf_counter() - t
+    t = time.perf_counter()
     cs = E.Space(gm, P1_DELTA, ncomp=3)
     p1 = E.Space(gm, P1_DELTA)
     dg = E.Space(gm, DG1_DELTA)
-    X = E.extrude_coords(gm, cs)
+    torch.cuda.synchronize()
+    t_spaces = time.perf_counter() - t
+    X = E.extrude_coords(gm, cs) if geometry == "flat" else geometry_coords(m, L, geometry, dev)
     Xr = X.view(-1, 3)
     f = (torch.sin(Xr[:, 0]) * torch.cos(Xr[:, 1]) * Xr[:, 2]).contiguous()  # synthetic input data
     x = torch.from_numpy(meshgen.uniform_field(p1.ndofs, SEED + 10 + rank)).to(dev)
@@ -290,7 +342,7 @@ def run_ours(args, rank, world, local):
     V, C = m.nverts, m.ncells
     vb = valuable_bytes_cfg2(V, C, L)
     vb_paper = valuable_bytes_cfg2(V, C, L, maps=False)
-    READ, WRITE, INC = E.EXT_READ, E.EXT_WRITE, E.EXT_INC
+    READ, WRITE = E.EXT_READ, E.EXT_WRITE
     h = {"gm": gm.handle}
     # WRITE: the P1xP1 loops overwrite b and y with the assembled results
     a_rhs = [(cs.handle, X, READ), (p1.handle, f, READ), (p1.handle, b, WRITE)]
@@ -335,7 +387,17 @@ def run_ours(args, rank, world, local):
     k_rhs = [e[0].elapsed_time(e[1]) for e in evs]
     k_mass = [e[1].elapsed_time(e[2]) for e in evs]
     k_int = [e[2].elapsed_time(e[3]) for e in evs]
-
+    extra = {"setup_s": {"mesh_create": round(t_mesh, 3), "spaces": round(t_spaces, 3),
+                         "note": "host wall time of ext_mesh_create (topology upload, edges, vertex rows) and "
+                                 "ext_number_dofs for the three spaces; outside the timed step"}}
+    reps = 20
+    if geometry == "flat" and not args.no_forms:
+        extra["forms_ms"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split", "factored", "cells"], reps)
+        for kind in ("terrain", "tilted"):
+            Xk = geometry_coords(m, L, kind, dev)
+            extra["forms_ms"][kind] = time_p1_forms(E, gm, cs, p1, Xk, x, y, stream, ["split"], reps)["split"]
+            del Xk
+        torch.cuda.empty_cache()
     if args.no_e2e:
         e2e_ms = None
     else:
@@ -344,7 +406,8 @@ def run_ours(args, rank, world, local):
     d2h = (b.numel() + y.numel() + out.numel()) * 8
     if rank != 0:
         return None
-    return report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates)
+    return report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates,
+                  extra)
 
 
 def e2e_time(args, world, dev, gm, cs, p1, dg, X, f, x):
@@ -425,46 +488,46 @@ def e2e_time(args, world, dev, gm, cs, p1, dg, X, f, x):
     return ms
 
 
-def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates):
+def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2e_ms, h2d, d2h, rates, extra):
     hbm, hbm_kind, sm_max = peaks()
     V, C = m.nverts, m.ncells
+    geometry = args.geometry
     value = world * vb["total"] / (ms * 1e-3) / 1e9
     items = C * (L + 1)
-    ndofs = V * (L + 1)
     mass_ms = statistics.mean(k_rhs + k_mass)
     ops_peak = FP64_OPS_PER_CLK_PER_SM * SMS * sm_max * 1e6 / 1e9  # G FP64 ops/s
     E_ = base_edges(m.cells)
-    form = p1_form(items, L)
-    ops = p1_ops(ndofs, items, C, L, nedges=E_)
-    achieved_ops = ops / (mass_ms * 1e-3) / 1e9
-    traffic = load_traffic("p1_mass_launch")
-    mix_peak = p1_mix_ceiling(ndofs, items, C, L, rates, nedges=E_)
-    l2_adds = (CELL_ATOMICS_PER_ITEM if form != "gather" else 0) * items / (mass_ms * 1e-3) / 1e9
+    form = p1_form(items, L, geometry=geometry)
+    main = form_entry(form, mass_ms, V, C, L, E_, geometry, ops_peak, hbm)
+    traffic = load_traffic("p1_mass_launch" if form == "gather" else "p1_cells_launch")
+    nbytes = p1_bytes_8d(V, C, L)
     if form == "gather":
-        algorithmic = (f"{GATHER_OPS_PER_DOF} FP64 ops per DoF x {ndofs} DoFs (column mass matrix) + 1 per "
-                       f"vertex-row entry and level x {V + 2 * E_} entries x {L + 1} levels (base mass matrix) "
-                       f"= {ops} per launch")
-        kname = "P1xP1 RHS / mass-action launch (k_levels + k_vsum_bulk + k_vgather + k_vgather_general)"
-        note = ("on straight prisms with flat levels M = Mh (x) Mv: the column mass matrix Mv is applied once "
-                "per vertex level (3 FP64 ops), then the base mass matrix Mh row by row per level (one FP64 op "
-                "per row entry, no atomics); evaluated cell by cell the same work is 18 FP64 ops per "
-                "(column, level) item (cellwise_equivalent_gops)")
+        label = ("gather (flat-level special case): the probe found a straight extrusion with flat levels, so "
+                 "M = Mh (x) Mv; Mv applied per vertex level, Mh per level through the vertex rows, whose weights "
+                 "and the level table are computed from the coordinate field in every launch")
+        algorithmic = (f"3 FP64 ops per DoF x {V * (L + 1)} DoFs + 1 per vertex-row entry and level x {V + 2 * E_} "
+                       f"entries x {L + 1} levels + 7 per cell x {C} + 4 per edge x {E_} = {main['fp64_ops']} per "
+                       f"launch")
+        kname = ("P1xP1 RHS / mass-action launch (k_p1_prep + k_p1_rowweights + k_vsum_bulk + k_vgather + "
+                 "k_vgather_general + k_p1_cells, the last two finding no work)")
     else:
-        per = P1_MIX[form]
-        algorithmic = (f"{sum(per[0])} FP64 ops per DoF x {ndofs} DoFs + {sum(per[1])} per (column, level) item "
-                       f"x {items} items + {sum(per[2])} per cell x {C} cells = {ops} per launch")
-        kname = "P1xP1 RHS / mass-action launch (k_area + k_vsum + k_mass_cells + k_mass_general)"
-        note = ("the split form computes each vertex column's vertical sums once instead of once per cell around "
-                "the vertex, and adds the vertex part alpha_c w_a of all cells around a vertex as one product "
-                "A_a w_a; evaluated cell by cell the same work is 18 FP64 ops per item (cellwise_equivalent_gops)")
+        per = P1_PRISM_OPS["general" if geometry == "tilted" else "vertical"]
+        label = (f"cell loop (Algorithm 3 over cells, one element vector per prism, {geometry} geometry): the probe "
+                 "found no flat straight extrusion")
+        algorithmic = (f"{per} FP64 ops per prism x {C * L} prisms + 3 per (column, level) item x {items} = "
+                       f"{main['fp64_ops']} per launch")
+        kname = ("P1xP1 RHS / mass-action launch (k_p1_prep probe + k_vgather clearing b + k_p1_cells; the "
+                 "gather-form kernels exit)")
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded perturbed structured triangulation, RCM; f = sin x cos y z; x ~ U(-1,1))",
+        "dtype": "f64",
+        "data": f"synthetic (seeded perturbed structured triangulation, RCM; {geometry} levels; f = sin x cos y z; "
+                "x ~ U(-1,1))",
         "config": {"workload": f"extruded prisms: {C} base triangles x {L} layers, {args.order} base order, "
-                               "P1xP1 RHS + P1xP1 mass action + DG1xDG1 interpolation",
-                   "base_cells": C, "base_vertices": V, "layers": L, "global_batch": world,
+                               f"{geometry} geometry, P1xP1 RHS + P1xP1 mass action + DG1xDG1 interpolation",
+                   "base_cells": C, "base_vertices": V, "layers": L, "geometry": geometry, "global_batch": world,
                    "l2": "inputs larger than L2 (7.5 GB working set per step, L2 129 MB)",
                    "valuable_bytes_per_step": vb["total"], "valuable_bytes_paper_definition": vb_paper["total"],
                    "parallelism": f"replicas x{world}"},
@@ -474,29 +537,41 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                         "mass_p1p1": round(vb["mass"] / statistics.mean(k_mass) / 1e6, 1),
                         "interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6, 1)},
         "hbm_frac": {"interp_dg1": round(vb["interp"] / statistics.mean(k_int) / 1e6 / hbm, 4),
-                     "step": round(value / world / hbm, 4), "peak_gbs": hbm, "peak_kind": hbm_kind},
-        "roofline": {"kernel": kname, "form": form,
-                     "bound": "alu",
-                     "achieved": round(achieved_ops, 2), "peak": round(ops_peak, 2), "unit": "G FP64 ops/s",
-                     "frac": round(achieved_ops / ops_peak, 4), "traffic": traffic,
-                     "algorithmic": algorithmic,
-                     "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
+                     "p1p1": main["hbm_frac"], "step": round(value / world / hbm, 4), "peak_gbs": hbm,
+                     "peak_kind": hbm_kind},
+        "roofline": {"kernel": kname, "form": label, "bound": "alu",
+                     "achieved": main["fp64_gops"], "peak": round(ops_peak, 2), "unit": "G FP64 ops/s",
+                     "frac": main["fp64_frac"], "traffic": traffic, "algorithmic": algorithmic,
+                     "peak_note": "2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s); "
+                                  "all products and sums issued as DFMA",
+                     "hbm": {"algorithmic_bytes": nbytes,
+                             "bytes_note": "24 per vertex level (coordinates) + 16 (input, output) + 24 per base "
+                                           "cell (one map row), each moved once",
+                             "achieved_gbs": main["gbs"], "peak_gbs": hbm, "frac": main["hbm_frac"]},
                      "measured_fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
-                     "mix_ceiling_gops": round(mix_peak, 1),
-                     "frac_of_mix_ceiling": round(achieved_ops / mix_peak, 4),
-                     "l2_atomic_adds": {"per_item": CELL_ATOMICS_PER_ITEM if form != "gather" else 0,
-                                        "g_per_s": round(l2_adds, 1),
-                                        "frac_of_measured": round(l2_adds / rates["l2_atomic_add"], 4)},
-                     "cellwise_equivalent_gops": round(CELLWISE_OPS_PER_ITEM * items / (mass_ms * 1e-3) / 1e9, 1),
-                     "note": note},
+                     "frac_of_measured_dfma": round(main["fp64_gops"] / rates["dfma"], 4)},
+        "setup_s": extra["setup_s"],
         "e2e": None if e2e_ms is None else {
             "value": round(world * vb["total"] / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-        "gpu_launches": (2 * p1_kernels(items, L) + 1) * args.steps,
+        "gpu_launches": (2 * P1_KERNELS[form] + 1) * args.steps,
         "clocks": clocks,
     }
+    if "forms_ms" in extra:
+        fm = extra["forms_ms"]
+        line["p1_forms"] = {
+            "note": "one mass-action launch (WRITE) on this mesh in each form, forced with ext_set_option, mean of "
+                    "20 back-to-back launches; terrain and tilted: the same mesh with terrain-following levels "
+                    "(every prism's top face tilted) and with leaning columns as well, default form (the probe "
+                    "picks the cell loop)",
+            "gather": form_entry("gather", fm["split"], V, C, L, E_, "flat", ops_peak, hbm),
+            "factored_cell_pass": form_entry("factored", fm["factored"], V, C, L, E_, "flat", ops_peak, hbm),
+            "cell_loop": form_entry("cells-forced", fm["cells"], V, C, L, E_, "flat", ops_peak, hbm),
+            "terrain_cell_loop": form_entry("cells", fm["terrain"], V, C, L, E_, "terrain", ops_peak, hbm),
+            "tilted_cell_loop": form_entry("cells", fm["tilted"], V, C, L, E_, "tilted", ops_peak, hbm),
+        }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m, L, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(m, L, args.cpu_runs, geometry)
     return line
 
 
@@ -530,46 +605,86 @@ def load_traffic(kernel: str):
 
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
-def cpu_baseline(m, L, seconds: float, steps: int = 1, warmup: int = 0):
-    """The oracle (serial C, one core) on the first S base columns of the same
-    workload, all layers; S grows until one pass takes about `seconds`/steps;
-    `warmup` untimed passes, then `steps` timed ones (the minimum is kept)."""
-    import oracle as O
-    X_sp, X = O.coords(m.cells, m.xy, L)
-    p1 = O.number(m.cells, m.nverts, L, P1_DELTA)
-    dg = O.number(m.cells, m.nverts, L, DG1_DELTA)
-    Xr = X.reshape(-1, 3)
-    f = np.sin(Xr[:, 0]) * np.cos(Xr[:, 1]) * Xr[:, 2]
-    x = meshgen.uniform_field(p1.ndofs, SEED + 10)
-    b = np.zeros(p1.ndofs)
-    y = np.zeros(p1.ndofs)
-    out = np.zeros(dg.ndofs)
+CPU_SAMPLE_COLUMNS = 2048  # base columns of the CPU sample (all layers, all three loops)
 
-    def one(S):
+
+def host_cpu() -> str:
+    """Host CPU model as the kernel reports it."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model", "Hardware", "CPU part"):
+            for line in txt.splitlines():
+                if line.lower().startswith(key.lower()) and ":" in line:
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class CpuSample:
+    """The benchmark step of the oracle on the first S base columns (all
+    layers): RHS, mass action and DG1 interpolation, serial (one core) or
+    over base-cell colours on every host core (OpenMP).  Valuable bytes of
+    the sample: the touched vertex columns (coordinates, input, output), the
+    DG1 output of the S cell columns and S map rows per map, each once."""
+
+    def __init__(self, m, L, S=CPU_SAMPLE_COLUMNS, geometry="flat"):
+        import oracle as O
+        self.O = O
+        self.L, self.S = L, min(S, m.ncells)
+        self.cells = np.ascontiguousarray(m.cells[:self.S])
+        self.X_sp, self.X = O.coords(m.cells, m.xy, L)
+        if geometry != "flat":
+            self.X = meshgen.level_coords(m, L, seed=SEED + 20, kind=geometry).reshape(-1)
+        self.p1 = O.number(m.cells, m.nverts, L, P1_DELTA)
+        self.dg = O.number(m.cells, m.nverts, L, DG1_DELTA)
+        Xr = self.X.reshape(-1, 3)
+        self.f = np.sin(Xr[:, 0]) * np.cos(Xr[:, 1]) * Xr[:, 2]
+        self.x = meshgen.uniform_field(self.p1.ndofs, SEED + 10)
+        self.b = np.zeros(self.p1.ndofs)
+        self.y = np.zeros(self.p1.ndofs)
+        self.out = np.zeros(self.dg.ndofs)
+        sub = lambda sp: O.Space(delta=sp.delta, layers=sp.layers, ndofs=sp.ndofs, k=sp.k,
+                                 map=np.ascontiguousarray(sp.map[:self.S]), offset=sp.offset)
+        self.sX, self.sp1, self.sdg = sub(self.X_sp), sub(self.p1), sub(self.dg)
+        self.ptr, self.ids = O.color_cells(self.cells, m.nverts)
+        self.threads = O.max_threads()
+        Vs = np.unique(self.cells).size
+        self.bytes = 2 * (40 * Vs * (L + 1) + 48 * self.S) + (8 * Vs * (L + 1) + 48 * self.S * L + 48 * self.S)
+
+    def run(self, parallel: bool) -> float:
+        O, L = self.O, self.L
+        loops = ((O.K_MASS, [(self.sX, self.X, 3, O.READ), (self.sp1, self.f, 1, O.READ), (self.sp1, self.b, 1, O.INC)]),
+                 (O.K_MASS, [(self.sX, self.X, 3, O.READ), (self.sp1, self.x, 1, O.READ), (self.sp1, self.y, 1, O.INC)]),
+                 (O.K_INTERP, [(self.sp1, self.x, 1, O.READ), (self.sdg, self.out, 1, O.WRITE)]))
         t = time.perf_counter()
-        O.par_loop(O.K_MASS, m.cells, L, [(X_sp, X, 3, O.READ), (p1, f, 1, O.READ), (p1, b, 1, O.INC)], ncells=S)
-        O.par_loop(O.K_MASS, m.cells, L, [(X_sp, X, 3, O.READ), (p1, x, 1, O.READ), (p1, y, 1, O.INC)], ncells=S)
-        O.par_loop(O.K_INTERP, m.cells, L, [(p1, x, 1, O.READ), (dg, out, 1, O.WRITE)], ncells=S)
+        for k, a in loops:
+            if parallel:
+                O.par_loop_colored(k, self.cells, L, a, self.ptr, self.ids, self.threads)
+            else:
+                O.par_loop(k, self.cells, L, a)
         return time.perf_counter() - t
 
-    S = 256
-    dt = one(S)
-    target = seconds / max(1, steps)
-    while dt < 0.25 * target and S < m.ncells:
-        S = min(m.ncells, S * 4)
-        dt = one(S)
-    S = min(m.ncells, max(1, int(S * target / max(dt, 1e-9))))
-    for _ in range(warmup):
-        one(S)
-    times = [one(S) for _ in range(steps)]
-    t = min(times)
-    # valuable bytes of the sample: the touched vertex columns, the S cell
-    # columns of DG1 output, S map rows per map (each counted once)
-    Vs = np.unique(m.cells[:S]).size
-    vb = 2 * (40 * Vs * (L + 1) + 48 * S) + (8 * Vs * (L + 1) + 48 * S * L + 48 * S)
-    return {"value": round(vb / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {S} of {m.ncells} base columns x {L} layers, all three loops, "
-                      f"min of {steps} run(s), {t:.2f} s"}
+    def describe(self, m) -> str:
+        return (f"first {self.S} of {m.ncells} base columns x {self.L} layers, RHS + mass action + DG1 "
+                f"interpolation")
+
+
+def cpu_baseline(m, L, runs: int = 10, geometry: str = "flat"):
+    """The oracle on the CPU sample: the all-core variant (base-cell colours
+    in sequence, cells of a colour over every host core) and the serial one,
+    each the minimum of `runs` runs (the paper's timing rule)."""
+    cs = CpuSample(m, L, geometry=geometry)
+    cs.run(True)  # first touch of the sample's pages
+    tp = min(cs.run(True) for _ in range(runs))
+    ts = min(cs.run(False) for _ in range(runs))
+    return {"value": round(cs.bytes / tp / 1e9, 4), "unit": "GB/s", "cores": cs.threads, "kind": "oracle",
+            "sample": f"{cs.describe(m)}; min of {runs} runs each",
+            "variant": f"OpenMP over {cs.ptr.size - 1} vertex-disjoint base-cell colours, {cs.threads} threads",
+            "serial": {"value": round(cs.bytes / ts / 1e9, 4), "unit": "GB/s", "cores": 1, "s_per_run": round(ts, 3)},
+            "s_per_run": round(tp, 3), "nproc": os.cpu_count(), "host_cpu": host_cpu()}
 
 
 # ----------------------------------------------------------------------------- other workloads
@@ -1121,25 +1236,33 @@ def run_cfg7(args, rank, world, local):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, all host cores (the
+    coloured variant of its Algorithm 3), one pass over the CPU sample per
+    step; W untimed passes, then K timed ones."""
     if rank != 0:
         return None
     m = meshgen.tri_mesh(N_CFG2, seed=SEED, order="rcm")
     L = LAYERS_CFG2
-    # the whole arm stays near a minute and a half whatever K and W are: each
-    # step is a sample of that share (at most 2 s, at least 0.05 s)
-    per_step = min(2.0, max(0.05, 90.0 / max(1, args.steps + args.warmup)))
-    cb = cpu_baseline(m, L, per_step * args.steps, steps=args.steps, warmup=args.warmup)
+    cs = CpuSample(m, L)
+    for _ in range(max(args.warmup, 1)):
+        cs.run(True)
+    ts = [cs.run(True) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    value = cs.bytes / t / 1e9
     C = m.ncells
     line = {
         "impl": "reference",
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
-        "value": cb["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded perturbed structured triangulation, RCM)",
         "config": {"workload": f"extruded prisms: {C} base triangles x {L} layers, {args.order} base order, "
                                "P1xP1 RHS + P1xP1 mass action + DG1xDG1 interpolation (bounded sample)"},
-        "cpu_baseline": cb,
-        "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cs.threads, "kind": "oracle",
+                         "sample": f"{cs.describe(m)}; mean of {args.steps} timed passes",
+                         "nproc": os.cpu_count(), "host_cpu": host_cpu()},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return line
 
@@ -1150,7 +1273,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-runs", type=int, default=10, help="runs of each CPU-baseline variant (minimum kept)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="base grid size (config 2: 707, config 4: 707)")
@@ -1158,21 +1281,28 @@ def main():
     ap.add_argument("--count", type=int, default=64, help="config 5: number of meshes")
     ap.add_argument("--cmax", type=float, default=5e5, help="config 5: largest base cell count")
     ap.add_argument("--order", choices=["rcm", "random"], default="rcm")
-    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6, 7], default=2,
+    ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6, 7, 8], default=2,
                     help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "
                          "5: 64-mesh batched vs plain; 6: the nine prism spaces at ~15M cells; "
-                         "7: variable layers per column and horizontal-facet loops")
+                         "7: variable layers per column and horizontal-facet loops; 8: config 2 with "
+                         "terrain-following levels (--geometry tilted: leaning columns as well)")
+    ap.add_argument("--geometry", choices=["flat", "terrain", "tilted"], default=None,
+                    help="levels of the config 2 step (config 8: terrain by default)")
+    ap.add_argument("--no-forms", action="store_true", help="config 2: skip the per-form P1xP1 timings")
     ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.geometry is None:
+        args.geometry = "terrain" if args.config == 8 else "flat"
     rank, world, local = dist_env()
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
         import __graft_entry__
         __graft_entry__.build_library_only()
-        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6, 7: run_cfg7}[args.config]
+        runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6, 7: run_cfg7,
+                  8: run_ours}[args.config]
         line = runner(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)

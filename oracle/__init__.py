@@ -47,8 +47,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                           "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    # OpenMP only spreads the coloured CPU-baseline loop over cores; without
+    # it that loop runs on one thread and everything else is unchanged
+    if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,6 +94,15 @@ def lib():
                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_alg2.restype = None
         L.oracle_alg2.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_color_cells.restype = ctypes.c_int32
+        L.oracle_color_cells.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p]
+        L.oracle_max_threads.restype = ctypes.c_int32
+        L.oracle_max_threads.argtypes = []
+        L.oracle_par_loop_colored.restype = ctypes.c_int
+        L.oracle_par_loop_colored.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         L.oracle_par_loop.restype = ctypes.c_int
         L.oracle_par_loop.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
@@ -321,6 +333,59 @@ def par_loop(kernel: int, cells: np.ndarray, layers: int, args, base_xy: np.ndar
                                        len(args), arr)
     if rc != 0:
         raise RuntimeError(f"oracle_par_loop failed: {rc}")
+
+
+def _args_array(args):
+    arr = (_Arg * len(args))()
+    keep = []
+    for i, a in enumerate(args):
+        sp, data, ncomp, acc = a[:4]
+        absd = a[4] if len(a) > 4 else None
+        assert data.dtype == np.float64 and data.flags.c_contiguous
+        assert data.size == sp.ndofs * ncomp, (data.size, sp.ndofs, ncomp)
+        keep += [sp.map, sp.offset]
+        arr[i].map = sp.map.ctypes.data
+        arr[i].offset = sp.offset.ctypes.data
+        arr[i].rowptr = None
+        arr[i].k = sp.k
+        arr[i].ncomp = ncomp
+        arr[i].data = data.ctypes.data
+        arr[i].absdata = None if absd is None else absd.ctypes.data
+        arr[i].access = acc
+    return arr, keep
+
+
+def color_cells(cells: np.ndarray, nverts: int) -> tuple[np.ndarray, np.ndarray]:
+    """Greedy vertex-disjoint colouring of base cells (in cell order):
+    (color_ptr of ncolors + 1 offsets, cells grouped by colour, ascending)."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    col = np.empty(cells.shape[0], dtype=np.int32)
+    nc = lib().oracle_color_cells(cells.shape[1], cells.shape[0], _p(cells), nverts, _p(col))
+    if nc < 0:
+        raise RuntimeError(f"oracle_color_cells failed: {nc}")
+    order = np.argsort(col, kind="stable").astype(np.int64)
+    ptr = np.zeros(nc + 1, dtype=np.int64)
+    np.cumsum(np.bincount(col, minlength=nc), out=ptr[1:])
+    return ptr, np.ascontiguousarray(order)
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+def par_loop_colored(kernel: int, cells: np.ndarray, layers: int, args, color_ptr, color_cells_,
+                     nthreads: int | None = None) -> None:
+    """Algorithm 3 over the listed cells on several host cores: colours in
+    sequence, the cells of one colour (no shared vertex) split over threads.
+    A CPU baseline; the checks use the serial par_loop."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    arr, keep = _args_array(args)
+    ptr = np.ascontiguousarray(color_ptr, dtype=np.int64)
+    ids = np.ascontiguousarray(color_cells_, dtype=np.int64)
+    rc = lib().oracle_par_loop_colored(kernel, cells.shape[1], layers, _p(cells), None, len(args), arr,
+                                       ptr.size - 1, _p(ptr), _p(ids), nthreads or max_threads())
+    if rc != 0:
+        raise RuntimeError(f"oracle_par_loop_colored failed: {rc}")
 
 
 def gauss_legendre(n: int) -> tuple[np.ndarray, np.ndarray]:

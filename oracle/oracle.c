@@ -32,6 +32,9 @@
 #include "oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -810,9 +813,10 @@ static int k_mass_dgp(int k, double *const *vals, double *const *out, double *co
  * advances by (offset, offset).  lambda_c = cell_layers[c] (or `layers`), and
  * level s + l of a column has z = (s + l) / layers with s = cell_first[c]
  * (or 0). */
-static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
-                         const int32_t *cell_layers, int32_t layers, const int32_t *cell_verts,
-                         const double *base_xy, int32_t nargs, const orc_arg *args) {
+static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int64_t *cell_ids,
+                         const int32_t *cell_first, const int32_t *cell_layers, int32_t layers,
+                         const int32_t *cell_verts, const double *base_xy, int32_t nargs,
+                         const orc_arg *args) {
   if (nargs < 1 || nargs > ORC_MAXARGS || layers < 1) return -1;
   for (int a = 0; a < nargs; ++a)
     if ((!args[a].rowptr && (args[a].k < 1 || args[a].k > 27)) || args[a].ncomp < 1 || args[a].ncomp > 3)
@@ -837,7 +841,8 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
   }
   for (int a = 0; a < nargs; ++a)
     if (args[a].rowptr && twocell) return -6; /* ragged lists: cell loops only */
-  for (int64_t c = 0; c < ncells; ++c) {
+  for (int64_t ci = 0; ci < ncells; ++ci) {
+    const int64_t c = cell_ids ? cell_ids[ci] : ci; /* the cells visited: all, or a given list */
     /* list length and offsets of this cell (ragged lists vary per cell) */
     const int32_t *lst[ORC_MAXARGS];
     for (int a = 0; a < nargs; ++a) {
@@ -940,7 +945,7 @@ static int par_loop_impl(int32_t kernel, int32_t nvc, int64_t ncells, const int3
 int oracle_par_loop(int32_t kernel, int32_t nvc, int64_t ncells, int32_t layers,
                     const int32_t *cell_verts, const double *base_xy, int32_t nargs,
                     const orc_arg *args) {
-  return par_loop_impl(kernel, nvc, ncells, NULL, NULL, layers, cell_verts, base_xy, nargs, args);
+  return par_loop_impl(kernel, nvc, ncells, NULL, NULL, NULL, layers, cell_verts, base_xy, nargs, args);
 }
 
 int oracle_par_loop_var(int32_t kernel, int32_t nvc, int64_t ncells, const int32_t *cell_first,
@@ -949,6 +954,68 @@ int oracle_par_loop_var(int32_t kernel, int32_t nvc, int64_t ncells, const int32
   if (!cell_first || !cell_layers) return -1;
   for (int64_t c = 0; c < ncells; ++c)
     if (cell_first[c] < 0 || cell_layers[c] < 1 || cell_first[c] + cell_layers[c] > maxlevel) return -1;
-  return par_loop_impl(kernel, nvc, ncells, cell_first, cell_layers, maxlevel, cell_verts, base_xy, nargs,
+  return par_loop_impl(kernel, nvc, ncells, NULL, cell_first, cell_layers, maxlevel, cell_verts, base_xy, nargs,
                        args);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 on several host cores (a CPU baseline, not a check): the     */
+/* base cells are grouped in colours such that no two cells of a colour     */
+/* share a vertex (greedy, in cell order), so the cells of one colour write */
+/* disjoint DoFs of every space whose DoFs sit on vertices or cells; the    */
+/* colours run one after another, the cells of a colour split evenly over   */
+/* the threads.  Each thread runs the serial loop above on its share.       */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_color_cells(int32_t nvc, int64_t ncells, const int32_t *cell_verts, int64_t nverts,
+                           int32_t *color) {
+  uint64_t *used = (uint64_t *)calloc((size_t)(nverts > 0 ? nverts : 1), sizeof(uint64_t));
+  if (!used) return -1;
+  int32_t ncolors = 0;
+  for (int64_t c = 0; c < ncells; ++c) {
+    uint64_t taken = 0;
+    for (int32_t a = 0; a < nvc; ++a) taken |= used[cell_verts[c * nvc + a]];
+    int32_t k = 0;
+    while (k < 64 && (taken >> k & 1u)) ++k;
+    if (k == 64) {
+      free(used);
+      return -2;
+    }
+    color[c] = k;
+    for (int32_t a = 0; a < nvc; ++a) used[cell_verts[c * nvc + a]] |= (uint64_t)1 << k;
+    if (k + 1 > ncolors) ncolors = k + 1;
+  }
+  free(used);
+  return ncolors;
+}
+
+int32_t oracle_max_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int oracle_par_loop_colored(int32_t kernel, int32_t nvc, int32_t layers, const int32_t *cell_verts,
+                            const double *base_xy, int32_t nargs, const orc_arg *args, int32_t ncolors,
+                            const int64_t *color_ptr, const int64_t *color_cells, int32_t nthreads) {
+  int err = 0;
+  for (int32_t k = 0; k < ncolors; ++k) {
+    const int64_t n = color_ptr[k + 1] - color_ptr[k];
+    const int64_t *ids = color_cells + color_ptr[k];
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads) reduction(| : err)
+    {
+      const int64_t t = omp_get_thread_num(), T = omp_get_num_threads();
+      const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+      if (hi > lo)
+        err |= par_loop_impl(kernel, nvc, hi - lo, ids + lo, NULL, NULL, layers, cell_verts, base_xy, nargs,
+                             args) != 0;
+    }
+#else
+    (void)nthreads;
+    err |= par_loop_impl(kernel, nvc, n, ids, NULL, NULL, layers, cell_verts, base_xy, nargs, args) != 0;
+#endif
+  }
+  return err ? -1 : 0;
 }

@@ -146,6 +146,18 @@ void oracle_set_hex_rule(int32_t n);
  * vertical element v on the interval, each ORC_CG1, ORC_DG0 or ORC_DG1. */
 void oracle_set_tp_element(int32_t h, int32_t v);
 
+/* CPU baseline on several cores: greedy vertex-disjoint colouring of the
+ * base cells (returns the colour count, or a negative error), the number of
+ * threads OpenMP would use (1 without OpenMP), and Algorithm 3 over the
+ * cells listed per colour (color_ptr: ncolors + 1 offsets into color_cells),
+ * colours in sequence, the cells of a colour split over nthreads threads. */
+int32_t oracle_color_cells(int32_t nvc, int64_t ncells, const int32_t *cell_verts, int64_t nverts,
+                           int32_t *color);
+int32_t oracle_max_threads(void);
+int oracle_par_loop_colored(int32_t kernel, int32_t nvc, int32_t layers, const int32_t *cell_verts,
+                            const double *base_xy, int32_t nargs, const orc_arg *args, int32_t ncolors,
+                            const int64_t *color_ptr, const int64_t *color_cells, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif
