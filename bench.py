@@ -63,6 +63,9 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 #            level (V + 2E entries: base mass matrix Mh) + the per-launch
 #            geometry (7 per cell for the level-0 areas, 4 per edge for the
 #            row weights); no atomics;
+#   gather-sigma (terrain-following levels) the same + 2 per DoF (the check
+#            against the terrain-following model) + 14 per edge, 11 per cell
+#            and 5 per vertex for the depth-weighted rows;
 #   factored 6 per DoF + 3 per (column, level) item + 7 per cell, 3 L2 atomic
 #            adds per item;
 #   cells    42 per prism with vertical edges (closed form of the 6-point
@@ -70,7 +73,8 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 #            3 L2 atomic adds per item;
 #   single   13 per item (below a million items).
 P1_PRISM_OPS = {"vertical": 42, "general": 132}
-P1_KERNELS = {"gather": 6, "cells": 6, "cells-forced": 1, "factored": 4, "plain": 3, "var": 3, "single": 1}
+P1_KERNELS = {"gather": 9, "gather-sigma": 9, "cells": 9, "cells-forced": 1, "factored": 4, "plain": 3, "var": 3,
+              "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 P1_SPLIT_MIN_ITEMS = 1_000_000
 P1_FACTORED_MIN_LAYERS = 2
@@ -85,7 +89,7 @@ def p1_form(items: int, layers: int, var: bool = False, geometry: str = "flat") 
         return "single"
     if var:
         return "var"
-    return "gather" if geometry == "flat" else "cells"
+    return {"flat": "gather", "terrain": "gather-sigma"}.get(geometry, "cells")
 
 
 def p1_ops_form(form: str, ndofs: int, items: int, ncells: int, layers: int, nedges: int,
@@ -93,6 +97,8 @@ def p1_ops_form(form: str, ndofs: int, items: int, ncells: int, layers: int, ned
     nv = ndofs // (layers + 1)
     if form == "gather":
         return 3 * ndofs + (nv + 2 * nedges) * (layers + 1) + 7 * ncells + 4 * nedges
+    if form == "gather-sigma":
+        return 5 * ndofs + (nv + 2 * nedges) * (layers + 1) + 18 * ncells + 14 * nedges + 5 * nv
     if form == "factored":
         return 6 * ndofs + 3 * items + 7 * ncells
     if form in ("cells", "cells-forced"):
@@ -310,7 +316,7 @@ def form_entry(form, ms, V, C, L, E_, geometry, ops_peak, hbm, launches=None):
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"ms": round(ms, 4), "fp64_ops": ops, "fp64_gops": round(gops, 1),
             "fp64_frac": round(gops / ops_peak, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-            "l2_atomic_adds_per_item": 0 if form == "gather" else CELL_ATOMICS_PER_ITEM,
+            "l2_atomic_adds_per_item": 0 if form.startswith("gather") else CELL_ATOMICS_PER_ITEM,
             "kernels": P1_KERNELS[form] if launches is None else launches}
 
 
@@ -393,7 +399,7 @@ def run_ours(args, rank, world, local):
     reps = 20
     if geometry == "flat" and not args.no_forms:
         extra["forms_ms"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split", "factored", "cells"], reps)
-        for kind in ("terrain", "tilted"):
+        for kind in ("terrain", "wavy", "tilted"):
             Xk = geometry_coords(m, L, kind, dev)
             extra["forms_ms"][kind] = time_p1_forms(E, gm, cs, p1, Xk, x, y, stream, ["split"], reps)["split"]
             del Xk
@@ -499,25 +505,34 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     E_ = base_edges(m.cells)
     form = p1_form(items, L, geometry=geometry)
     main = form_entry(form, mass_ms, V, C, L, E_, geometry, ops_peak, hbm)
-    traffic = load_traffic("p1_mass_launch" if form == "gather" else "p1_cells_launch")
+    traffic = load_traffic({"gather": "p1_mass_launch", "gather-sigma": "p1_sigma_launch"}.get(form, "p1_cells_launch"))
     nbytes = p1_bytes_8d(V, C, L)
-    if form == "gather":
-        label = ("gather (flat-level special case): the probe found a straight extrusion with flat levels, so "
-                 "M = Mh (x) Mv; Mv applied per vertex level, Mh per level through the vertex rows, whose weights "
-                 "and the level table are computed from the coordinate field in every launch")
-        algorithmic = (f"3 FP64 ops per DoF x {V * (L + 1)} DoFs + 1 per vertex-row entry and level x {V + 2 * E_} "
-                       f"entries x {L + 1} levels + 7 per cell x {C} + 4 per edge x {E_} = {main['fp64_ops']} per "
-                       f"launch")
-        kname = ("P1xP1 RHS / mass-action launch (k_p1_prep + k_p1_rowweights + k_vsum_bulk + k_vgather + "
-                 "k_vgather_general + k_p1_cells, the last two finding no work)")
+    if form in ("gather", "gather-sigma"):
+        if form == "gather":
+            label = ("gather (flat-level special case): the probe found a straight extrusion with flat levels, so "
+                     "M = Mh (x) Mv; Mv applied per vertex level, Mh per level through the vertex rows, whose "
+                     "weights and the level table are computed from the coordinate field in every launch")
+            algorithmic = (f"3 FP64 ops per DoF x {V * (L + 1)} DoFs + 1 per vertex-row entry and level x "
+                           f"{V + 2 * E_} entries x {L + 1} levels + 7 per cell x {C} + 4 per edge x {E_} = "
+                           f"{main['fp64_ops']} per launch")
+        else:
+            label = ("terrain-following gather: the probe found vertical columns with z = z0 + sigma_l D(x, y), so "
+                     "M = Hd (x) Mv(sigma) with Hd the depth-weighted P1 mass matrix of the base; every DoF checked "
+                     "against that model within 2^-42 D min(sigma spacing)")
+            algorithmic = (f"5 FP64 ops per DoF x {V * (L + 1)} DoFs (Mv and the model check) + 1 per vertex-row "
+                           f"entry and level x {V + 2 * E_} x {L + 1} + 18 per cell + 14 per edge + 5 per vertex = "
+                           f"{main['fp64_ops']} per launch")
+        kname = ("P1xP1 RHS / mass-action launch (k_p1_levels + k_p1_prep + k_p1_sigma_prep + k_p1_rowweights + "
+                 "k_vsum_bulk<flat> + k_vsum_bulk<terrain> + k_vgather + k_vgather_general + k_p1_cells; the kernels "
+                 "of the other modes exit at once)")
     else:
         per = P1_PRISM_OPS["general" if geometry == "tilted" else "vertical"]
         label = (f"cell loop (Algorithm 3 over cells, one element vector per prism, {geometry} geometry): the probe "
                  "found no flat straight extrusion")
         algorithmic = (f"{per} FP64 ops per prism x {C * L} prisms + 3 per (column, level) item x {items} = "
                        f"{main['fp64_ops']} per launch")
-        kname = ("P1xP1 RHS / mass-action launch (k_p1_prep probe + k_vgather clearing b + k_p1_cells; the "
-                 "gather-form kernels exit)")
+        kname = ("P1xP1 RHS / mass-action launch (k_p1_levels + k_p1_prep probe + k_vgather clearing b + "
+                 "k_p1_cells; the gather-form kernels exit at once)")
     line = {
         "metric": "par_loop valuable HBM GB/s (P1xP1 RHS + mass action + DG1 interpolation, 100 layers, RCM)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -561,13 +576,15 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
         fm = extra["forms_ms"]
         line["p1_forms"] = {
             "note": "one mass-action launch (WRITE) on this mesh in each form, forced with ext_set_option, mean of "
-                    "20 back-to-back launches; terrain and tilted: the same mesh with terrain-following levels "
-                    "(every prism's top face tilted) and with leaning columns as well, default form (the probe "
-                    "picks the cell loop)",
+                    "20 back-to-back launches; terrain, wavy, tilted: the same mesh with terrain-following levels "
+                    "(every prism's top face tilted; the probe picks the terrain-following gather), with bent "
+                    "levels (no common profile; the cell loop) and with leaning columns (the cell loop), default "
+                    "form",
             "gather": form_entry("gather", fm["split"], V, C, L, E_, "flat", ops_peak, hbm),
             "factored_cell_pass": form_entry("factored", fm["factored"], V, C, L, E_, "flat", ops_peak, hbm),
             "cell_loop": form_entry("cells-forced", fm["cells"], V, C, L, E_, "flat", ops_peak, hbm),
-            "terrain_cell_loop": form_entry("cells", fm["terrain"], V, C, L, E_, "terrain", ops_peak, hbm),
+            "terrain_gather": form_entry("gather-sigma", fm["terrain"], V, C, L, E_, "terrain", ops_peak, hbm),
+            "wavy_cell_loop": form_entry("cells", fm["wavy"], V, C, L, E_, "wavy", ops_peak, hbm),
             "tilted_cell_loop": form_entry("cells", fm["tilted"], V, C, L, E_, "tilted", ops_peak, hbm),
         }
     if not args.no_cpu_baseline:
@@ -1285,8 +1302,8 @@ def main():
                     help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "
                          "5: 64-mesh batched vs plain; 6: the nine prism spaces at ~15M cells; "
                          "7: variable layers per column and horizontal-facet loops; 8: config 2 with "
-                         "terrain-following levels (--geometry tilted: leaning columns as well)")
-    ap.add_argument("--geometry", choices=["flat", "terrain", "tilted"], default=None,
+                         "terrain-following levels (--geometry wavy: bent levels; tilted: leaning columns)")
+    ap.add_argument("--geometry", choices=["flat", "terrain", "wavy", "tilted"], default=None,
                     help="levels of the config 2 step (config 8: terrain by default)")
     ap.add_argument("--no-forms", action="store_true", help="config 2: skip the per-form P1xP1 timings")
     ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")

@@ -231,9 +231,12 @@ def level_coords(m: BaseMesh, layers: int, seed: int, kind: str = "terrain") -> 
     d(x, y) = 0.55 + 0.4 sin(3x + p1) cos(2y + p2) in [0.15, 0.95]: the vertex
     at level l sits at (x, y, (l / layers) d(x, y)), so every column is
     vertical and no two vertices of a prism's top face (away from symmetric
-    points) share a height.  ``tilted``: the same levels with x and y sheared
-    with height, x + 0.05 z sin(2 pi y) and y + 0.05 z cos(2 pi x), so the
-    columns lean as well.  The phases come from ``seed``."""
+    points) share a height.  ``wavy``: the same with the levels bent by
+    0.3 / layers sin(7x + 5y) sin(pi l / layers), so that the heights are no
+    longer a fixed profile scaled per column.  ``tilted``: the terrain levels
+    with x and y sheared with height, x + 0.05 z sin(2 pi y) and
+    y + 0.05 z cos(2 pi x), so the columns lean as well.  The phases come
+    from ``seed``."""
     rng = np.random.default_rng(seed)
     ph = rng.uniform(0.0, 2.0 * np.pi, 2)
     x, y = m.xy[:, 0], m.xy[:, 1]
@@ -243,7 +246,9 @@ def level_coords(m: BaseMesh, layers: int, seed: int, kind: str = "terrain") -> 
     out[:, :, 0] = x[:, None]
     out[:, :, 1] = y[:, None]
     out[:, :, 2] = lev[None, :] * depth[:, None]
-    if kind == "tilted":
+    if kind == "wavy":
+        out[:, :, 2] += (0.3 / layers) * np.sin(7.0 * x + 5.0 * y)[:, None] * np.sin(np.pi * lev)[None, :]
+    elif kind == "tilted":
         z = out[:, :, 2]
         out[:, :, 0] = x[:, None] + 0.05 * z * np.sin(2.0 * np.pi * y)[:, None]
         out[:, :, 1] = y[:, None] + 0.05 * z * np.cos(2.0 * np.pi * x)[:, None]

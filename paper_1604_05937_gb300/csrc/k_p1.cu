@@ -953,28 +953,74 @@ struct LevelCoef {
   double z, lo, mid, hi;  // z_m, |h_{m-1}|, 2 (|h_{m-1}| + |h_m|), |h_m| (0 beyond the column)
 };
 
-// Level table (threads 0..layers), alpha_c per cell, and the sampled probe:
-// the DoFs of vertex columns q = s * stride, s < nsamp (all levels), must sit
-// at their column's level-0 x, y and at the height of column 0's level.
+// Mode word of the gather form (set by the probe): bit 0 = not a flat
+// extrusion, bit 1 = not terrain-following either.  0: flat gather, 1:
+// terrain-following gather, 3: cell loop.
+constexpr unsigned kNotFlat = 1u, kNotSigma = 2u;
+__device__ __forceinline__ bool mode_cells(unsigned m) { return (m & 3u) == 3u; }
+
+// Terrain-following (sigma) levels: z_{q,m} = z_{q,0} + sigma_m D_q in every
+// vertex column q, with sigma_m = (z_{0,m} - z_{0,0}) / D_0 from the column
+// of vertex 0, D_q = z_{q,layers} - z_{q,0} > 0 and sigma increasing.  A
+// DoF's z is accepted when it lies within kSigmaTol D_q min_l (sigma_{l+1} -
+// sigma_l) of that model (the probe: within kSigmaTol D_q times the smaller
+// of its two adjacent layer spacings): every layer height then differs from
+// sigma's by a relative 2 kSigmaTol = 4.5e-13 at most, which bounds the
+// relative change of every element contribution.
+constexpr double kSigmaTol = 0x1p-42;
+
+__device__ __forceinline__ double sigma_at(const double *__restrict__ X, int layers, int m) {
+  return (X[3 * (int64_t)m + 2] - X[2]) / (X[3 * (int64_t)layers + 2] - X[2]);
+}
+
+// Level tables (one thread per level, before the probe): tab[m] from the
+// heights of column 0, tab[layers + 1 + m] from its sigma; the smallest sigma
+// spacing (bit pattern of a positive double, atomic min, in *minds); bit 1 of
+// *mode when sigma does not increase (or D_0 is not positive).
+__global__ void __launch_bounds__(256) k_p1_levels(const double *__restrict__ X, int layers,
+                                                   LevelCoef *__restrict__ tab, unsigned int *__restrict__ mode,
+                                                   unsigned long long *__restrict__ minds) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > layers) return;
+  const int64_t col = (int64_t)layers + 1;
+  const double z = X[3 * (int64_t)m + 2];
+  const double hl = m > 0 ? fabs(z - X[3 * (int64_t)(m - 1) + 2]) : 0.0;
+  const double hh = m < layers ? fabs(X[3 * (int64_t)(m + 1) + 2] - z) : 0.0;
+  LevelCoef c;
+  c.z = z;
+  c.lo = hl;
+  c.mid = 2.0 * (hl + hh);
+  c.hi = hh;
+  tab[m] = c;
+  const double sg = sigma_at(X, layers, m);
+  const double sl = m > 0 ? sg - sigma_at(X, layers, m - 1) : 0.0;
+  const double sh = m < layers ? sigma_at(X, layers, m + 1) - sg : 0.0;
+  LevelCoef cs;
+  cs.z = sg;
+  cs.lo = sl;
+  cs.mid = 2.0 * (sl + sh);
+  cs.hi = sh;
+  tab[col + m] = cs;
+  if (m < layers) {
+    if (!(sh > 0.0)) atomicOr(mode, kNotSigma);  // also catches NaN (D_0 = 0)
+    else atomicMin(minds, (unsigned long long)__double_as_longlong(sh));
+  }
+}
+
+// alpha_c per cell, and the sampled probe over the DoFs of vertex columns
+// q = s * stride, s < nsamp (all levels): bit 0 of *mode when a DoF is off
+// its column's level-0 x, y or off its level's height in column 0, bit 1 when
+// it is off its column's vertical or off the terrain-following model by more
+// than kSigmaTol D_q times the smaller of its two adjacent sigma spacings (or
+// D_q <= 0).  Reads the level tables of k_p1_levels.
 __global__ void __launch_bounds__(256) k_p1_prep(const double *__restrict__ X, int layers, const int32_t *__restrict__ cmap,
                                                  int64_t ncells, int64_t nsamp, int64_t stride,
-                                                 LevelCoef *__restrict__ tab, double *__restrict__ alpha,
+                                                 const LevelCoef *__restrict__ tab, double *__restrict__ alpha,
                                                  unsigned int *__restrict__ mode) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t col = (int64_t)layers + 1;
-  if (gid <= layers) {
-    const int m = (int)gid;
-    const double z = X[3 * (int64_t)m + 2];
-    const double hl = m > 0 ? fabs(z - X[3 * (int64_t)(m - 1) + 2]) : 0.0;
-    const double hh = m < layers ? fabs(X[3 * (int64_t)(m + 1) + 2] - z) : 0.0;
-    LevelCoef c;
-    c.z = z;
-    c.lo = hl;
-    c.mid = 2.0 * (hl + hh);
-    c.hi = hh;
-    tab[m] = c;
-  }
+  unsigned bad = 0u;
   for (int64_t c = gid; c < ncells; c += gstride) {
     double x[3], y[3];
 #pragma unroll
@@ -985,32 +1031,102 @@ __global__ void __launch_bounds__(256) k_p1_prep(const double *__restrict__ X, i
     }
     alpha[c] = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * (1.0 / 144.0);
   }
-  int bad = 0;
   for (int64_t i = gid; i < nsamp * col; i += gstride) {
     const int64_t s = i / col, m = i - s * col;
     const int64_t d0 = s * stride * col, d = d0 + m;
-    bad |= (__double_as_longlong(__ldg(X + 3 * d + 0)) != __double_as_longlong(__ldg(X + 3 * d0 + 0))) |
-           (__double_as_longlong(__ldg(X + 3 * d + 1)) != __double_as_longlong(__ldg(X + 3 * d0 + 1))) |
-           (__double_as_longlong(__ldg(X + 3 * d + 2)) != __double_as_longlong(__ldg(X + 3 * m + 2)));
+    const bool vert = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
+                      (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1)));
+    const double z = __ldg(X + 3 * d + 2);
+    if (!vert || __double_as_longlong(z) != __double_as_longlong(__ldg(&tab[m].z))) bad |= kNotFlat;
+    const double z0 = __ldg(X + 3 * d0 + 2), D = __ldg(X + 3 * (d0 + layers) + 2) - z0;
+    const LevelCoef ts = tab[col + m];
+    const double gap = m == 0 ? ts.hi : (m == layers ? ts.lo : fmin(ts.lo, ts.hi));
+    if (!vert || !(D > 0.0) || !(fabs(z - fma(ts.z, D, z0)) <= kSigmaTol * D * gap)) bad |= kNotSigma;
   }
-  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(mode, 1u);
+  const unsigned wbad = __reduce_or_sync(kFull, bad);
+  if (wbad && (threadIdx.x & 31) == 0) atomicOr(mode, wbad);
 }
 
-// Row weights of Mh from alpha (gather mode only): entry (a, j) = the sum of
-// alpha over the one or two cells on edge (a, j), ascending; the diagonal is
-// the sum of the row's neighbour weights in row order.
-__global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict__ vrow, const int2 *__restrict__ vedge,
-                                                       const double *__restrict__ alpha, double *__restrict__ wts,
-                                                       int32_t nv, const unsigned int *__restrict__ mode) {
-  if (*mode) return;
+// Terrain-following gather only (mode 1): per vertex column q its D_q, z_q0
+// and the acceptance bound B_q = kSigmaTol D_q min(sigma spacing) (-1 when
+// D_q <= 0, so that no DoF of the column passes); per cell S_c = the sum of
+// D over its three vertex columns.
+__global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict__ X, int layers,
+                                                       const int32_t *__restrict__ cmap, int64_t ncells, int64_t nv,
+                                                       const unsigned int *__restrict__ mode,
+                                                       const unsigned long long *__restrict__ minds,
+                                                       double *__restrict__ Dv, double *__restrict__ Z0,
+                                                       double *__restrict__ Bv, double *__restrict__ S) {
+  if (*mode != kNotFlat) return;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t col = (int64_t)layers + 1;
+  const double gap = __longlong_as_double((long long)*minds);
+  for (int64_t v = gid; v < nv; v += gstride) {
+    const double z0 = __ldg(X + 3 * v * col + 2);
+    const double D = __ldg(X + 3 * (v * col + layers) + 2) - z0;
+    Dv[v] = D;
+    Z0[v] = z0;
+    Bv[v] = D > 0.0 ? kSigmaTol * D * gap : -1.0;
+  }
+  for (int64_t c = gid; c < ncells; c += gstride) {
+    double sum = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int64_t cb = __ldg(cmap + c * 6 + 2 * a);
+      sum += __ldg(X + 3 * (cb + layers) + 2) - __ldg(X + 3 * cb + 2);
+    }
+    S[c] = sum;
+  }
+}
+
+// Row weights (gather modes only).  Flat extrusion, Mh: entry (a, j) = the
+// sum of alpha over the one or two cells on edge (a, j), ascending; the
+// diagonal is the sum of the row's neighbour weights in row order.
+// Terrain-following levels, Hd: a prism's heights are h_k = (sigma_{l+1} -
+// sigma_l) D_k, so its element matrix under the 6-point rule is the column
+// factor times (alpha_c / 54) sum_k D_k T_{aa'k}, with T = 54 sum_t lambda_a
+// lambda_a' lambda_k over the three triangle points = 66 (a = a' = k), 21 (two
+// equal), 12 (all different): entry (a, j) = sum_c alpha_c (9 (D_a + D_j) +
+// 12 S_c) / 54 over the cells on the edge, diagonal = sum over the cells
+// around a of alpha_c (45 D_a + 21 S_c) / 54, S_c the sum of the cell's D.
+// (D = 1 gives Mh.)
+__global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict__ vrow, const int32_t *__restrict__ vnbr,
+                                                       const int2 *__restrict__ vedge, const int32_t *__restrict__ vcrow,
+                                                       const int32_t *__restrict__ vcells,
+                                                       const double *__restrict__ alpha, const double *__restrict__ Dv,
+                                                       const double *__restrict__ S, double *__restrict__ wts,
+                                                       int32_t nv, FastDiv col, const unsigned int *__restrict__ mode) {
+  const unsigned md = *mode;
+  if (mode_cells(md)) return;
+  const bool sig = (md & kNotFlat) != 0u;
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nv; a += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
     double diag = 0.0;
-    for (int32_t t = t0 + 1; t < t1; ++t) {
-      const int2 e = __ldg(vedge + t);
-      const double w = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
-      wts[t] = w;
-      diag += w;
+    if (!sig) {
+#pragma unroll 4
+      for (int32_t t = t0 + 1; t < t1; ++t) {
+        const int2 e = __ldg(vedge + t);
+        const double w = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
+        wts[t] = w;
+        diag += w;
+      }
+    } else {
+      const double Da = __ldg(Dv + a);
+#pragma unroll 4
+      for (int32_t t = t0 + 1; t < t1; ++t) {
+        const int2 e = __ldg(vedge + t);
+        const double Dj = __ldg(Dv + fdiv((uint32_t)__ldg(vnbr + t), col));
+        const double dd = 9.0 * (Da + Dj);
+        double w = __ldg(alpha + e.x) * fma(12.0, __ldg(S + e.x), dd);
+        if (e.y >= 0) w = fma(__ldg(alpha + e.y), fma(12.0, __ldg(S + e.y), dd), w);
+        wts[t] = w * (1.0 / 54.0);
+      }
+      for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) {
+        const int32_t c = __ldg(vcells + t);
+        diag = fma(__ldg(alpha + c), fma(21.0, __ldg(S + c), 45.0 * Da), diag);
+      }
+      diag *= 1.0 / 54.0;
     }
     wts[t0] = diag;
   }
@@ -1036,22 +1152,44 @@ __global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict
 #endif
 constexpr int kVGUnroll = EXT_VG_UNROLL;
 
-// DoF d is at its column's level-0 x, y and at its level's height (bitwise)
+// Per vertex column arrays of the terrain-following gather (k_p1_sigma_prep).
+struct SigmaCols {
+  const double *Dv, *Z0, *Bv;
+};
+
+// z of a DoF of vertex column q at a level whose table entry holds zt (the
+// height in column 0, or sigma): flat mode, bitwise equal; terrain-following
+// mode, within B_q of z_q0 + sigma D_q (two FP64 operations; the comparison
+// on the bit patterns of the absolute difference and the non-negative bound,
+// or a negative bound that nothing passes).
+__device__ __forceinline__ int z_ok(double z, double zt, bool sig, const SigmaCols &sc, uint32_t q, const Fp64Ones &k1) {
+  if (!sig) return __double_as_longlong(z) == __double_as_longlong(zt);
+  const double model = fma(zt, __ldg(sc.Dv + q), __ldg(sc.Z0 + q));
+  const long long dev = __double_as_longlong(fsub(z, model, k1)) & 0x7fffffffffffffffLL;
+  return dev <= __double_as_longlong(__ldg(sc.Bv + q));
+}
+
+// DoF d is on its column's vertical (x, y of its level 0, bitwise) and at its
+// level (z_ok)
 __device__ __forceinline__ int dof_straight(const double *__restrict__ X, const LevelCoef *__restrict__ tab, int64_t d,
-                                            FastDiv col) {
+                                            FastDiv col, bool sig, const SigmaCols &sc, const Fp64Ones &k1) {
   const uint32_t q = fdiv((uint32_t)d, col);
   const uint32_t m = (uint32_t)d - q * col.d;
   const int64_t d0 = (int64_t)q * col.d;
   return (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
          (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
-         (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(__ldg(&tab[m].z)));
+         z_ok(__ldg(X + 3 * d + 2), __ldg(&tab[m].z), sig, sc, q, k1);
 }
 
+template <bool SIG>
 __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *__restrict__ X, const double *__restrict__ f,
-                                                                const LevelCoef *__restrict__ tab,
+                                                                const LevelCoef *__restrict__ tab0,
                                                                 double *__restrict__ W, int64_t n, FastDiv col,
-                                                                Fp64Ones k1, const unsigned int *__restrict__ mode) {
-  if (*mode) return;  // cell-loop mode: k_p1_cells forms b
+                                                                Fp64Ones k1, const unsigned int *__restrict__ mode,
+                                                                SigmaCols sc) {
+  const unsigned md = *mode;
+  if (mode_cells(md) || ((md & kNotFlat) != 0u) != SIG) return;
+  const LevelCoef *__restrict__ tab = SIG ? tab0 + col.d : tab0;
   constexpr int VU = EXT_VT_VU;
   const int lane = threadIdx.x & 31;
   const int64_t wstride = (int64_t)gridDim.x * 8 * 32 * VU;
@@ -1077,7 +1215,7 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
         const int64_t d0 = (int64_t)q * col.d;
         ok[u] = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
                 (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
-                (__double_as_longlong(__ldg(X + 3 * d + 2)) == __double_as_longlong(t0.x));
+                z_ok(__ldg(X + 3 * d + 2), t0.x, SIG, sc, q, k1);
         fc[u] = __ldg(f + d);
       }
     }
@@ -1086,11 +1224,11 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_tab(const double *_
     int okb = 1, oka = 1;
     if (lane == 0 && base > 0 && base - 1 < n) {
       fb = __ldg(f + base - 1);
-      okb = dof_straight(X, tab, base - 1, col);
+      okb = dof_straight(X, tab, base - 1, col, SIG, sc, k1);
     }
     if (lane == 31 && base + 32 * VU < n) {
       fa = __ldg(f + base + 32 * VU);
-      oka = dof_straight(X, tab, base + 32 * VU, col);
+      oka = dof_straight(X, tab, base + 32 * VU, col, SIG, sc, k1);
     }
 #pragma unroll
     for (int u = 0; u < VU; ++u) {
@@ -1179,13 +1317,18 @@ __device__ __forceinline__ void bulk_range(int64_t base, int64_t n, int64_t &lo,
   bulk = aligned && ((hi - lo) & 1) == 0;
 }
 
+template <bool SIG>
 __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *__restrict__ X, const double *__restrict__ f,
-                                                                 const LevelCoef *__restrict__ tab,
+                                                                 const LevelCoef *__restrict__ tab0,
                                                                  double *__restrict__ W, int64_t n, FastDiv col,
                                                                  Fp64Ones k1, unsigned int *err,
-                                                                 const unsigned int *__restrict__ mode, int64_t skip_step,
-                                                                 unsigned wait_limit) {
-  if (*mode) return;  // cell-loop mode: k_p1_cells forms b
+                                                                 const unsigned int *__restrict__ mode, SigmaCols sc,
+                                                                 int64_t skip_step, unsigned wait_limit) {
+  // one instantiation per gather mode (flat: SIG = false); the other exits,
+  // as both do in cell-loop mode
+  const unsigned md = *mode;
+  if (mode_cells(md) || ((md & kNotFlat) != 0u) != SIG) return;
+  const LevelCoef *__restrict__ tab = SIG ? tab0 + col.d : tab0;
   __shared__ BulkStage stage[8][2];
   __shared__ __align__(8) uint64_t bar[8][2];
   const int lane = threadIdx.x & 31;
@@ -1261,7 +1404,7 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
       const int64_t d0 = (int64_t)qv * col.d;
       return (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
              (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
-             (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(__ldg(&tab[m].z)));
+             z_ok(sg.X[3 * r + 2], __ldg(&tab[m].z), SIG, sc, qv, k1);
     };
     int ok[2];
     uint32_t mm[2];
@@ -1284,7 +1427,7 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
         const int64_t d0 = (int64_t)qv * col.d;
         ok[u] = (__double_as_longlong(sg.X[3 * r + 0]) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
                 (__double_as_longlong(sg.X[3 * r + 1]) == __double_as_longlong(__ldg(X + 3 * d0 + 1))) &
-                (__double_as_longlong(sg.X[3 * r + 2]) == __double_as_longlong(t0.x));
+                z_ok(sg.X[3 * r + 2], t0.x, SIG, sc, qv, k1);
       }
     }
     // straightness of the DoFs just outside the step
@@ -1322,7 +1465,7 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
                                                                    const unsigned int *__restrict__ mode) {
   constexpr int VU = EXT_VG_VU;
   const int lane = threadIdx.x & 31;
-  if (*mode) {
+  if (mode_cells(*mode)) {
     // cell-loop mode: k_p1_cells adds every contribution; WRITE clears b first
     if (!INC)
       for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x)
@@ -1453,7 +1596,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Lau
 // straight extrusion, which the gather form handles) makes the kernel exit.
 __global__ void __launch_bounds__(kWarps * 32, EXT_P1C_MINB) k_p1_cells(const MassP1Launch p, int cpw, Fp64Ones k1,
                                                                        const unsigned int *__restrict__ mode) {
-  if (mode && *mode == 0u) return;
+  if (mode && !mode_cells(*mode)) return;  // a gather mode formed b
   __shared__ ColInfo cols[kWarps][kMaxCols];
   __shared__ double kk[kWarps][kMaxCols][2];  // k2, k6 of each column
   const int lane = threadIdx.x & 31;
@@ -1587,13 +1730,16 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = cells ? 0 : al(sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)));
   const size_t abytes = factored ? al(sizeof(double) * (size_t)(n / (p.layers + 1))) : 0;
-  const size_t tbytes = gather ? al(sizeof(LevelCoef) * (size_t)(p.layers + 1)) : 0;
+  const size_t tbytes = gather ? al(sizeof(LevelCoef) * 2 * (size_t)(p.layers + 1)) : 0;
   const size_t cbytes = (gather || factored) ? al(sizeof(double) * (size_t)p.ncells) : 0;
   const size_t ebytes = gather ? al(sizeof(double) * (size_t)p.nvent) : 0;
+  // terrain-following gather: D, z_0 and the bound per vertex column, S per cell
+  const size_t vbytes = gather ? al(sizeof(double) * (size_t)p.nverts) : 0;
+  const size_t sbytes = gather ? 3 * vbytes + cbytes : 0;
   const size_t lbytes = cells ? 0 : sizeof(int2) * (size_t)cap;
   if (form != EXT_P1_SINGLE &&
-      cudaMallocAsync(reinterpret_cast<void **>(&scr), 256 + wbytes + abytes + tbytes + cbytes + ebytes + lbytes, s) !=
-          cudaSuccess) {
+      cudaMallocAsync(reinterpret_cast<void **>(&scr),
+                      256 + wbytes + abytes + tbytes + cbytes + ebytes + sbytes + lbytes, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;
   }
@@ -1610,17 +1756,26 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   }
   unsigned int *count = reinterpret_cast<unsigned int *>(scr);
   unsigned int *mode = count + 1;
+  unsigned long long *minds = reinterpret_cast<unsigned long long *>(scr + 8);
   double *W = reinterpret_cast<double *>(scr + 256);
   double *A = reinterpret_cast<double *>(scr + 256 + wbytes);
   LevelCoef *tab = reinterpret_cast<LevelCoef *>(scr + 256 + wbytes + abytes);
   double *alpha = reinterpret_cast<double *>(scr + 256 + wbytes + abytes + tbytes);
   double *wts = reinterpret_cast<double *>(scr + 256 + wbytes + abytes + tbytes + cbytes);
+  char *sg0 = scr + 256 + wbytes + abytes + tbytes + cbytes + ebytes;
+  SigmaCols sc;
+  sc.Dv = reinterpret_cast<double *>(sg0);
+  sc.Z0 = reinterpret_cast<double *>(sg0 + vbytes);
+  sc.Bv = reinterpret_cast<double *>(sg0 + 2 * vbytes);
+  double *Sc = reinterpret_cast<double *>(sg0 + 3 * vbytes);
   Deferred dfr;
   dfr.count = count;
-  dfr.list = reinterpret_cast<int2 *>(scr + 256 + wbytes + abytes + tbytes + cbytes + ebytes);
+  dfr.list = reinterpret_cast<int2 *>(sg0 + sbytes);
   dfr.cap = cap;
-  // one memset clears the counter, the mode word and A
+  // the counter and the mode word start at zero, the smallest sigma spacing
+  // at a large positive double (bytes 0x7f)
   cudaError_t e = cudaMemsetAsync(scr, 0, 256, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scr + 8, 0x7f, 8, s);
   if (e == cudaSuccess && factored && abytes) e = cudaMemsetAsync(A, 0, abytes, s);
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
   const int rc = resident_ctas(k_p1_cells, res_p1c);
@@ -1643,7 +1798,7 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     const int64_t skip = skip_step;
     skip_step = -1;
     const unsigned wait_limit = skip >= 0 ? (1u << 12) : kBulkWaitLimit;
-    const int rv = resident_ctas(k_vsum_tab, res_vtab);
+    const int rv = resident_ctas(k_vsum_tab<false>, res_vtab);
     const int rg = p.overwrite ? resident_ctas(k_vgather<false>, res_vg[0]) : resident_ctas(k_vgather<true>, res_vg[1]);
     int64_t gv = ((n + 32 * EXT_VT_VU - 1) / (32 * EXT_VT_VU) + 7) / 8;  // CTAs of 8 warps, one warp step each
     int64_t gg = ((n + 32 * EXT_VG_VU - 1) / (32 * EXT_VG_VU) + 7) / 8;
@@ -1658,18 +1813,28 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     int64_t gp = ((int64_t)p.ncells > nsamp * (p.layers + 1) ? (int64_t)p.ncells : nsamp * (p.layers + 1)) / 256 + 1;
     if (gp > (int64_t)sms * 8) gp = (int64_t)sms * 8;
     if (gp * 256 < (int64_t)p.layers + 1) gp = ((int64_t)p.layers + 1 + 255) / 256;
+    k_p1_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab, mode, minds);
     k_p1_prep<<<(unsigned)gp, 256, 0, s>>>(p.X, p.layers, p.cmap, p.ncells, nsamp, stride, tab, alpha, mode);
+    int64_t gs = ((nv > (int64_t)p.ncells ? nv : (int64_t)p.ncells) + 255) / 256;
+    if (gs > (int64_t)sms * 8) gs = (int64_t)sms * 8;
+    k_p1_sigma_prep<<<(unsigned)(gs > 0 ? gs : 1), 256, 0, s>>>(p.X, p.layers, p.cmap, p.ncells, nv, mode, minds,
+                                                                 const_cast<double *>(sc.Dv),
+                                                                 const_cast<double *>(sc.Z0),
+                                                                 const_cast<double *>(sc.Bv), Sc);
     int64_t gw = (nv + 255) / 256;
     if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
-    k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vedge, alpha, wts, (int32_t)nv, mode);
+    k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vnbr, p.vedge, p.vcrow, p.vcells, alpha,
+                                                                 sc.Dv, Sc, wts, (int32_t)nv, col, mode);
     if (EXT_VSUM_BULK) {
-      const int rb = resident_ctas(k_vsum_bulk, res_vb);
+      const int rb = resident_ctas(k_vsum_bulk<false>, res_vb);
       int64_t gb = ((n + kBulkDofs - 1) / kBulkDofs + 7) / 8;  // CTAs of 8 warps, one warp step each
       if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
       if (gb < 1) gb = 1;
-      k_vsum_bulk<<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, skip, wait_limit);
+      k_vsum_bulk<false><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
+      k_vsum_bulk<true><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
     } else {
-      k_vsum_tab<<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode);
+      k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
+      k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
     }
     if (p.overwrite) {
       k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode);

@@ -93,12 +93,13 @@ def test_fullsize_prisms_1M_by_100():
     assert not torch.isnan(out).any()
 
 
-@pytest.mark.parametrize("kind", ["terrain", "tilted"])
+@pytest.mark.parametrize("kind", ["terrain", "wavy", "tilted"])
 def test_fullsize_non_flat_prisms_1M_by_100(kind):
     """The benchmark mesh (999,698 triangles x 100 layers) with
-    terrain-following levels (every prism's top face tilted) or, in addition,
-    leaning columns: the default launch (the probe picks the cell loop) and
-    the mass action with WRITE access, on sampled cells."""
+    terrain-following levels (every prism's top face tilted: the
+    terrain-following gather), bent levels or leaning columns (the cell
+    loop): the default launch of the mass action with WRITE access, on
+    sampled cells."""
     m = meshgen.tri_mesh(707, seed=1604, order="rcm")
     L = 100
     gm = E.Mesh(m.cells, m.xy, L)

@@ -1,13 +1,14 @@
 """P1xP1 right-hand side / mass action on coordinate fields that are not a
 flat, straight extrusion: terrain-following levels (vertical columns, every
-prism's top and bottom faces tilted) and sheared columns (tilted vertical
-edges), over a million (column, level) items so that the split forms run.
-Every form of the launch (ext_set_option(EXT_OPT_P1_FORM, ...)) must match
-the oracle within 1e-12 of its absolute contribution sums, with WRITE and
-INC access; the probe of the automatic form must pick the cell loop on such
-fields and the gather form on a flat extrusion, including when the probe's
-sample misses a perturbed column (whose DoFs the gather form then
-recomputes one by one)."""
+prism's top and bottom faces tilted; the heights a fixed profile scaled per
+column), bent levels (vertical columns, no such profile) and sheared columns
+(tilted vertical edges), over a million (column, level) items so that the
+split forms run.  Every form of the launch (ext_set_option(EXT_OPT_P1_FORM,
+...)) must match the oracle within 1e-12 of its absolute contribution sums,
+with WRITE and INC access.  The probe of the automatic form picks the flat
+gather on a flat extrusion, the terrain-following gather on terrain levels
+and the cell loop otherwise; when its sample misses a perturbed column, the
+gather form recomputes the DoFs next to it one by one."""
 import numpy as np
 import pytest
 
@@ -79,7 +80,7 @@ def run(gm, cs, ps, Xd, fd, access, init=None):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("kind", ["terrain", "tilted"])
+@pytest.mark.parametrize("kind", ["terrain", "wavy", "tilted"])
 def test_every_form_on_non_flat_geometry(kind, form):
     m, gm, cs, ps, Xd, fd, ref, absr = case(kind)
     assert m.ncells * 101 >= 1_000_000
@@ -98,17 +99,21 @@ def test_every_prism_of_the_terrain_is_non_straight():
     assert np.all((zt[:, 0] != zt[:, 1]) | (zt[:, 1] != zt[:, 2]))
 
 
+@pytest.mark.parametrize("base", ["flat", "terrain"])
 @pytest.mark.parametrize("column,mode", [(1, "gather"), (2, "cells")])
-def test_probe_sample_and_recorded_dofs(column, mode):
-    """A flat extrusion with one perturbed vertex column.  The probe samples
-    every second column on this mesh (5,184 vertex columns, about 4,096
-    sampled): column 1 escapes it and the gather form recomputes the DoFs
-    next to that column one by one; column 2 is sampled and the whole launch
-    runs as the cell loop.  Both match the oracle."""
+def test_probe_sample_and_recorded_dofs(base, column, mode):
+    """A flat or terrain-following extrusion with one perturbed vertex
+    column.  The probe samples every second column on this mesh (5,184
+    vertex columns, about 4,096 sampled): column 1 escapes it and the gather
+    form (flat or terrain-following) recomputes the DoFs next to that column
+    one by one; column 2 is sampled and the whole launch runs as the cell
+    loop.  Both match the oracle."""
     n, layers = 71, 100
     m = meshgen.tri_mesh(n, seed=880 + n, order="rcm")
     assert m.nverts == 5184
     csp, X = O.coords(m.cells, m.xy, layers)
+    if base == "terrain":
+        X = meshgen.level_coords(m, layers, seed=884, kind="terrain").reshape(-1)
     Xr = X.reshape(m.nverts, layers + 1, 3).copy()
     Xr[column, 3:60, 2] += 0.2 / layers        # levels off their heights
     Xr[column, 70:, 0] += 0.3 / n              # and a leaning top part
@@ -130,6 +135,19 @@ def test_probe_sample_and_recorded_dofs(column, mode):
     # launches agree bit for bit; the cell loop adds with atomics
     if mode == "gather":
         assert np.array_equal(a.view(np.int64), b.view(np.int64))
+
+
+def test_terrain_takes_the_terrain_following_gather():
+    """On terrain-following levels the automatic split form is the gather
+    form (bitwise reproducible from launch to launch), and it differs from the
+    flat-gather-without-probe result only by rounding (that form recomputes
+    every DoF with the element rule)."""
+    m, gm, cs, ps, Xd, fd, ref, absr = case("terrain")
+    E.ext_set_option(E.EXT_OPT_P1_FORM, E.EXT_P1_SPLIT)
+    a = run(gm, cs, ps, Xd, fd, E.EXT_WRITE)
+    b = run(gm, cs, ps, Xd, fd, E.EXT_WRITE)
+    close(a, ref, absr)
+    assert np.array_equal(a.view(np.int64), b.view(np.int64))
 
 
 def test_flat_extrusion_takes_the_gather_form():
