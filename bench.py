@@ -1016,11 +1016,12 @@ def run_cfg6(args, rank, world, local):
                 sp = E.Space(gm, delta)
                 f = torch.rand(sp.ndofs, dtype=torch.float64, device=dev)
                 b = sp.zeros()
+                # WRITE: b = M f (spaces with horizontal CG1 clear b inside the launch)
                 fn = lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_TP, [(cs.handle, X, E.EXT_READ),
-                                            (sp.handle, f, E.EXT_READ), (sp.handle, b, E.EXT_INC)], s)
+                                            (sp.handle, f, E.EXT_READ), (sp.handle, b, E.EXT_WRITE)], s)
                 fn()
                 reps = max(3, min(args.steps, 10))
-                t = time_kernel(fn, reps, stream, flush, pre=b.zero_)[0]
+                t = time_kernel(fn, reps, stream, flush)[0]
                 launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None else tp_kernels(C * L))
                 work = p1_ops(V * (L + 1), C * (L + 1), C, L) if ops is None else ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs

@@ -128,7 +128,7 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   scatter-adds; F's INC output becomes the READ cotangent w).
  * EXT_K_U2V_FWDADJ  [coords READ, u READ, w READ, F INC|WRITE, g INC|WRITE]:
  *                   both of the above in one pass.
- * EXT_K_MASS_TP     [coords READ, f READ, b INC] on prisms: b_i += int f_h phi_i dx
+ * EXT_K_MASS_TP     [coords READ, f READ, b INC|WRITE] on prisms: b_i += int f_h phi_i dx
  *                   on any of the nine spaces h x v, h, v in {CG1, DG0, DG1}, of
  *                   Sec. 4.1.2 (delta: CG1xCG1 {1,0,0,0,0,0}, CG1xDG0 {0,1,..},
  *                   CG1xDG1 {0,2,..}, DG0xCG1 {..,1,0}, DG0xDG0 {..,0,1},
@@ -141,6 +141,13 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                   level tables), and the cell kernel tests those bits
  *                   instead of comparing each prism's coordinates; without
  *                   the scratch, or with EXTMESH_TP_FLAGS=0, it compares them.
+ *                   WRITE overwrites b with the result.  Where every DoF
+ *                   belongs to one cell-layer (DG x DG) each is stored once;
+ *                   the other spaces add with FP64 atomics, b cleared first
+ *                   for WRITE (EXTMESH_TP_LEVELS=1, read once per process:
+ *                   DG0 x CG1 and DG1 x CG1 on constant layers instead walk a
+ *                   column's levels and form each DoF from the two layers
+ *                   that share it in registers).
  * EXT_K_HFACET_MASS [coords READ, f READ, b INC] on prisms, over the horizontal
  *                   facets ((2,0),(c,m)), m = 0..lambda, of every column
  *                   (Algorithm 3 with d2 = 0): b_i += int_F f_h phi_i ds on the

@@ -876,7 +876,8 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       if (nargs != 3) return ext_fail(EXT_EINVAL, "%s: expects 3 arguments", kn);
       EXT_CHECK(check_arg(mesh, args, 0, kn, ELEM_P1P1, 3, EXT_READ));
       EXT_CHECK(check_arg(mesh, args, 1, kn, -1, 1, EXT_READ));
-      EXT_CHECK(check_arg(mesh, args, 2, kn, -1, 1, EXT_INC));
+      // INC adds M f into b; WRITE overwrites b with M f
+      EXT_CHECK(check_arg(mesh, args, 2, kn, -1, 1, args[2].access == EXT_WRITE ? EXT_WRITE : EXT_INC));
       if (!same_numbering(args[1].space, args[2].space))
         return ext_fail(EXT_EINVAL, "%s: f and b must share one numbering", kn);
       int h = 0, v = 0;
@@ -903,6 +904,10 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.mean_layers = mesh->mean_layers;
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
       p.ncoord = args[0].space->ndofs;
+      p.overwrite = args[2].access == EXT_WRITE;
+      p.hown = h != 0;
+      p.vcont = v == 0;
+      p.nf = args[1].space->ndofs;
       e = launch_mass_tp(p, s);
       break;
     }

@@ -230,9 +230,13 @@ struct MassTPLaunch {
   double mean_layers = 0.0;
   const double *base_xy = nullptr;       // the mesh's base coordinates, if it has them
   int64_t ncoord = 0;                    // DoFs of the coordinate space (V (layers + 1))
+  int64_t nf = 0;                        // DoFs of the f / b space
   // filled by launch_mass_tp when it runs the flagged form
   const uint32_t *vflags = nullptr;      // bit d: coordinate DoF d verified straight
   const double *hlay = nullptr;          // |z_{l+1} - z_l| of the reference column
+  bool overwrite = false;                // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
+  bool hown = false;                     // horizontal DG0/DG1: every DoF belongs to one cell column
+  bool vcont = false;                    // vertical CG1: layers l and l + 1 share their facet DoFs
 };
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
 

@@ -962,7 +962,7 @@ __device__ __forceinline__ bool mode_cells(unsigned m) { return (m & 3u) == 3u; 
 // Terrain-following (sigma) levels: z_{q,m} = z_{q,0} + sigma_m D_q in every
 // vertex column q, with sigma_m = (z_{0,m} - z_{0,0}) / D_0 from the column
 // of vertex 0, D_q = z_{q,layers} - z_{q,0} > 0 and sigma increasing.  A
-// DoF's z is accepted when it lies within kSigmaTol D_q min_l (sigma_{l+1} -
+// DoF's z is accepted only where it provably lies within kSigmaTol D_q min_l (sigma_{l+1} -
 // sigma_l) of that model (the probe: within kSigmaTol D_q times the smaller
 // of its two adjacent layer spacings): every layer height then differs from
 // sigma's by a relative 2 kSigmaTol = 4.5e-13 at most, which bounds the
@@ -1064,10 +1064,18 @@ __global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict_
   const double gap = __longlong_as_double((long long)*minds);
   for (int64_t v = gid; v < nv; v += gstride) {
     const double z0 = __ldg(X + 3 * v * col + 2);
-    const double D = __ldg(X + 3 * (v * col + layers) + 2) - z0;
+    const double zl = __ldg(X + 3 * (v * col + layers) + 2);
+    const double D = zl - z0;
     Dv[v] = D;
     Z0[v] = z0;
-    Bv[v] = D > 0.0 ? kSigmaTol * D * gap : -1.0;
+    // the bound in units in the last place of the column's largest |z| (a
+    // column is monotonic, so its end levels hold that value): any z of the
+    // column within kb units of its model, with the same sign, is within
+    // kSigmaTol D gap of it
+    const double zmax = fmax(fabs(z0), fabs(zl));
+    const double ulp = __longlong_as_double(__double_as_longlong(zmax) + 1) - zmax;  // zmax >= 0
+    const double kb = D > 0.0 && ulp > 0.0 ? floor(kSigmaTol * D * gap / ulp) : -1.0;
+    Bv[v] = __longlong_as_double(kb < 0.0 ? -1LL : (kb > 4.0e18 ? (long long)4e18 : (long long)kb));
   }
   for (int64_t c = gid; c < ncells; c += gstride) {
     double sum = 0.0;
@@ -1159,14 +1167,16 @@ struct SigmaCols {
 
 // z of a DoF of vertex column q at a level whose table entry holds zt (the
 // height in column 0, or sigma): flat mode, bitwise equal; terrain-following
-// mode, within B_q of z_q0 + sigma D_q (two FP64 operations; the comparison
-// on the bit patterns of the absolute difference and the non-negative bound,
-// or a negative bound that nothing passes).
+// mode, z and the model z_q0 + sigma D_q (one DFMA) of one sign and at most
+// K_q apart as ordered bit patterns (integer ALU; K_q in units in the last
+// place of the column's largest |z|, negative when nothing may pass).
 __device__ __forceinline__ int z_ok(double z, double zt, bool sig, const SigmaCols &sc, uint32_t q, const Fp64Ones &k1) {
+  (void)k1;
   if (!sig) return __double_as_longlong(z) == __double_as_longlong(zt);
-  const double model = fma(zt, __ldg(sc.Dv + q), __ldg(sc.Z0 + q));
-  const long long dev = __double_as_longlong(fsub(z, model, k1)) & 0x7fffffffffffffffLL;
-  return dev <= __double_as_longlong(__ldg(sc.Bv + q));
+  const long long bm = __double_as_longlong(fma(zt, __ldg(sc.Dv + q), __ldg(sc.Z0 + q)));
+  const long long bz = __double_as_longlong(z);
+  const long long dd = bz > bm ? bz - bm : bm - bz;
+  return ((bz ^ bm) >= 0) & (dd <= __double_as_longlong(__ldg(sc.Bv + q)));
 }
 
 // DoF d is on its column's vertical (x, y of its level 0, bitwise) and at its
@@ -1430,10 +1440,14 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
                 z_ok(sg.X[3 * r + 2], t0.x, SIG, sc, qv, k1);
       }
     }
-    // straightness of the DoFs just outside the step
-    int okb = 1, oka = 1;
-    if (lane == 0 && base > 0) okb = ok_row(1, base - 1);
-    if (lane == 31 && base + kBulkDofs < n) oka = ok_row(kBulkDofs + 2, base + kBulkDofs);
+    // straightness of the DoFs just outside the step (lanes 0 and 31 in one pass)
+    int okx = 1;
+    if ((lane == 0 && base > 0) || (lane == 31 && base + kBulkDofs < n)) {
+      const int rx = lane == 0 ? 1 : kBulkDofs + 2;
+      const int64_t dx = lane == 0 ? base - 1 : base + kBulkDofs;
+      okx = ok_row(rx, dx);
+    }
+    const int okb = okx, oka = okx;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int64_t d = base + 32 * u + lane;

@@ -145,7 +145,9 @@ __device__ __forceinline__ int vflag(const uint32_t *__restrict__ flags, int64_t
 // FLAGS: the flagged form (constant layers only); MULTI (with FLAGS): several
 // items per lane per step, a separate instantiation so that its registers do
 // not lower the occupancy of the one-item loop.
-template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false>
+// WR: each DoF belongs to one cell-layer (DG x DG) and b is overwritten:
+// plain stores instead of atomic adds.
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = false>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -243,7 +245,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
             tp_general<NH, NV>(Xl, f[u], b);
           }
 #pragma unroll
-          for (int i = 0; i < NH * NV; ++i) atomicAdd(p.b + dof[u][i], b[i]);
+          for (int i = 0; i < NH * NV; ++i) {
+            if (WR) p.b[dof[u][i]] = b[i];
+            else atomicAdd(p.b + dof[u][i], b[i]);
+          }
         }
       }
       __syncwarp();
@@ -290,7 +295,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
           tp_general<NH, NV>(Xl, f, b);
         }
 #pragma unroll
-        for (int i = 0; i < NH * NV; ++i) atomicAdd(p.b + dof[i], b[i]);
+        for (int i = 0; i < NH * NV; ++i) {
+          if (WR) p.b[dof[i]] = b[i];
+          else atomicAdd(p.b + dof[i], b[i]);
+        }
       }
       l += 32;
       if (VAR) {
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
   }
 }
 
-template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI>
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI, bool WR = false>
 cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   const double lay = VAR ? p.mean_layers : (double)p.layers;
   int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
@@ -311,18 +319,19 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[16] = {0}, sms = 0;
-  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0) + (MULTI ? 4 : 0);
+  static int resident[32] = {0}, sms = 0;
+  const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0) + (MULTI ? 4 : 0) +
+                   (WR ? 16 : 0);
   if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS, MULTI>, kWarps * 32,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR>,
+                                                  kWarps * 32, 0);
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  k_mass_tp<NH, NV, VAR, FLAGS, MULTI><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
 
@@ -331,18 +340,195 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
 #ifndef EXT_TP_MULTI_LAYERS
 #define EXT_TP_MULTI_LAYERS 8
 #endif
-template <bool VAR, bool FLAGS, bool MULTI>
+template <bool VAR, bool FLAGS, bool MULTI, bool WR = false>
 cudaError_t launch_tp_kind(const MassTPLaunch &p, cudaStream_t s) {
-  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS, MULTI>(p, s);
-  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS, MULTI>(p, s);
-  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS, MULTI>(p, s);
-  return launch_tp<3, 2, VAR, FLAGS, MULTI>(p, s);
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS, MULTI, WR>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS, MULTI, WR>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS, MULTI, WR>(p, s);
+  return launch_tp<3, 2, VAR, FLAGS, MULTI, WR>(p, s);
 }
-template <bool VAR, bool FLAGS>
+template <bool VAR, bool FLAGS, bool WR = false>
 cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
-  if (FLAGS && !VAR && p.layers >= EXT_TP_MULTI_LAYERS) return launch_tp_kind<VAR, FLAGS, true>(p, s);
-  return launch_tp_kind<VAR, FLAGS, false>(p, s);
+  if (FLAGS && !VAR && p.layers >= EXT_TP_MULTI_LAYERS) return launch_tp_kind<VAR, FLAGS, true, WR>(p, s);
+  return launch_tp_kind<VAR, FLAGS, false, WR>(p, s);
 }
+
+// DG0 x CG1 and DG1 x CG1 on constant layers: the DoFs of a cell column are
+// its own (horizontal DG), and layers l and l + 1 share the DoFs of the
+// facet between them (vertical CG1).  A warp walks its group's flattened
+// items (column, level m), m = 0..layers, lanes along the levels; the lane of
+// level m < layers evaluates prism (c, m) once (closed form when its six
+// coordinate flags are set, tp_general otherwise), keeps the bottom row
+// (level m) and hands the top row (level m + 1) one lane up by a warp
+// shuffle (the step's last lane to the next step).  Every DoF is then formed
+// in registers by one lane and written once: stored (WR) or added with one
+// fire-and-forget reduction.
+template <int NH, bool FLAGS, bool WR>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPLaunch p, int cpw) {
+  __shared__ TPCol cols[kWarps][kMaxCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int layers = p.layers, L1 = layers + 1;
+  const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  for (int64_t grp = (int64_t)blockIdx.x * kWarps + warp; grp < ngroups; grp += wstride) {
+    const int64_t c0 = grp * cpw;
+    const int ncol = (int)(p.ncells - c0 < cpw ? p.ncells - c0 : (int64_t)cpw);
+    if (lane < ncol) {
+      const int64_t c = c0 + lane;
+      TPCol &ci = cols[warp][lane];
+      ci.lay = layers;
+      double x[3], y[3];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) ci.cm[i] = __ldg(p.cmap + c * 6 + i);
+#pragma unroll
+      for (int i = 0; i < NH * 2; ++i) ci.fm[i] = __ldg(p.fmap + c * p.k + p.slot[i]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t cd = ci.cm[2 * a];
+        if (FLAGS) {
+          const int64_t v = cd / L1;
+          x[a] = __ldg(p.base_xy + 2 * v + 0);
+          y[a] = __ldg(p.base_xy + 2 * v + 1);
+        } else {
+          x[a] = __ldg(p.X + 3 * cd + 0);
+          y[a] = __ldg(p.X + 3 * cd + 1);
+        }
+        ci.rx[a] = __double_as_longlong(x[a]);
+        ci.ry[a] = __double_as_longlong(y[a]);
+      }
+      ci.alpha = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * p.scale;
+    }
+    __syncwarp();
+    const int nitems = ncol * L1;
+    double carry[NH];
+#pragma unroll
+    for (int a = 0; a < NH; ++a) carry[a] = 0.0;
+    // U steps of 32 items per pass: every load of the pass (flags, layer
+    // heights, f at both levels of each prism) is issued before any
+    // arithmetic, then the steps are finished in order (the carry runs from
+    // one step's last lane to the next step's first)
+    constexpr int U = EXT_TP_UNROLL;
+    for (int base = 0; base < nitems; base += 32 * U) {
+      double f[U][NH * 2], hl[U];
+      int ok[U], ms[U], cls[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it = base + u * 32 + lane;
+        const bool valid = it < nitems;
+        cls[u] = valid ? it / L1 : 0;
+        ms[u] = valid ? it - cls[u] * L1 : L1;
+        ok[u] = 1;
+        hl[u] = 0.0;
+        const TPCol &ci = cols[warp][cls[u]];
+        if (ms[u] < layers) {
+#pragma unroll
+          for (int i = 0; i < NH * 2; ++i) f[u][i] = __ldg(p.f + ci.fm[i] + ms[u] * p.off[i]);
+          if (FLAGS) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)ms[u] * p.coff[i]);
+            hl[u] = __ldg(p.hlay + ms[u]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < NH * 2; ++i) f[u][i] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int m = ms[u];
+        const TPCol &ci = cols[warp][cls[u]];
+        double bot[NH], top[NH];
+#pragma unroll
+        for (int a = 0; a < NH; ++a) bot[a] = top[a] = 0.0;
+        if (m < layers) {
+          double b[NH * 2];
+          int okp = ok[u];
+          double Xl[6][3];
+          if (!FLAGS || !okp) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              const int64_t cd = (int64_t)ci.cm[i] + (int64_t)m * p.coff[i];
+              Xl[i][0] = __ldg(p.X + 3 * cd + 0);
+              Xl[i][1] = __ldg(p.X + 3 * cd + 1);
+              Xl[i][2] = __ldg(p.X + 3 * cd + 2);
+            }
+            if (!FLAGS) {
+#pragma unroll
+              for (int i = 0; i < 6; ++i)
+                okp &= (__double_as_longlong(Xl[i][0]) == ci.rx[i >> 1]) &
+                       (__double_as_longlong(Xl[i][1]) == ci.ry[i >> 1]);
+              okp &= (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[2][2])) &
+                     (__double_as_longlong(Xl[0][2]) == __double_as_longlong(Xl[4][2])) &
+                     (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
+                     (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
+            }
+          }
+          if (okp) tp_closed<NH, 2>(ci.alpha * (FLAGS ? hl[u] : fabs(Xl[1][2] - Xl[0][2])), f[u], b);
+          else tp_general<NH, 2>(Xl, f[u], b);
+#pragma unroll
+          for (int a = 0; a < NH; ++a) {
+            bot[a] = b[2 * a];
+            top[a] = b[2 * a + 1];
+          }
+        }
+        // the top row of the prism below (lane - 1, or the previous step's
+        // last lane); at m = 0 the lane below holds the previous column's top
+        // level, which has no prism above it and passes zeros
+#pragma unroll
+        for (int a = 0; a < NH; ++a) {
+          double up = __shfl_up_sync(0xffffffffu, top[a], 1);
+          const double last = __shfl_sync(0xffffffffu, top[a], 31);
+          if (lane == 0) up = carry[a];
+          carry[a] = last;
+          bot[a] += up;
+        }
+        if (base + u * 32 + lane < nitems) {
+#pragma unroll
+          for (int a = 0; a < NH; ++a) {
+            const int64_t d = m < layers ? (int64_t)ci.fm[2 * a] + (int64_t)m * p.off[2 * a]
+                                         : (int64_t)ci.fm[2 * a + 1] + (int64_t)(layers - 1) * p.off[2 * a + 1];
+            if (WR) p.b[d] = bot[a];
+            else atomicAdd(p.b + d, bot[a]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int NH, bool FLAGS, bool WR>
+cudaError_t launch_tp_levels(const MassTPLaunch &p, cudaStream_t s) {
+  const double L1 = (double)p.layers + 1.0;
+  int cpw = (int)((EXT_TP_ITEMS + L1 - 1.0) / L1);
+  if (cpw < 1) cpw = 1;
+  if (cpw > kMaxCols) cpw = kMaxCols;
+  const int64_t warps = (p.ncells + cpw - 1) / cpw;
+  int64_t blocks = (warps + kWarps - 1) / kWarps;
+  static int resident = 0, sms = 0;
+  if (resident == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_tp_levels<NH, FLAGS, WR>, kWarps * 32, 0);
+    if (resident < 1) resident = 1;
+  }
+  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
+  k_mass_tp_levels<NH, FLAGS, WR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  return cudaGetLastError();
+}
+
+template <bool FLAGS>
+cudaError_t launch_tp_owned(const MassTPLaunch &p, cudaStream_t s) {
+  if (p.vcont) {  // DG x CG1: the level kernel
+    if (p.nh == 1) return p.overwrite ? launch_tp_levels<1, FLAGS, true>(p, s) : launch_tp_levels<1, FLAGS, false>(p, s);
+    return p.overwrite ? launch_tp_levels<3, FLAGS, true>(p, s) : launch_tp_levels<3, FLAGS, false>(p, s);
+  }
+  // DG x DG: every DoF in one cell-layer
+  return p.overwrite ? launch_tp_pair<false, FLAGS, true>(p, s) : launch_tp_pair<false, FLAGS, false>(p, s);
+}
+
+
 
 // p-adaptive DG (EXT_K_MASS_DGP): every cell carries its own element, DG0|DG1
 // x DG0|DG1, told apart by its DoF count K = NH NV (1, 2, 3, 6).  The library
@@ -507,6 +693,23 @@ cudaError_t launch_dgp_kind(const MassDGPLaunch &p, cudaStream_t s) {
 // from the stream-ordered pool; otherwise every lane loads its coordinates.
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
+  // DG x CG1 takes the atomic form (FP64 reductions into the shared facet
+  // DoFs, b cleared first for WRITE), which measured 5-10 % faster at 10 and
+  // 100 layers than the level kernel that merges the shared DoFs in
+  // registers; EXTMESH_TP_LEVELS=1 (read once per process) selects the level
+  // kernel on constant layers
+  static int levels_env = -1;
+  if (levels_env < 0) {
+    const char *ev = getenv("EXTMESH_TP_LEVELS");
+    levels_env = (ev && ev[0] == '1') ? 1 : 0;
+  }
+  // the forms that add into shared DoFs with atomics (horizontal CG1, variable
+  // layers) clear b first for WRITE
+  const bool owned = p.hown && !p.cell_layers && (!p.vcont || levels_env == 1);
+  if (p.overwrite && !owned) {
+    const cudaError_t ez = cudaMemsetAsync(p.b, 0, sizeof(double) * (size_t)p.nf, s);
+    if (ez != cudaSuccess) return ez;
+  }
   if (p.cell_layers) return launch_tp_pair<true, false>(p, s);
   static int flags_env = -1;
   if (flags_env < 0) {
@@ -522,7 +725,7 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
     (void)cudaGetLastError();  // not sticky: the plain form needs no scratch
     scr = nullptr;
   }
-  if (!scr) return launch_tp_pair<false, false>(p, s);
+  if (!scr) return owned ? launch_tp_owned<false>(p, s) : launch_tp_pair<false, false>(p, s);
   MassTPLaunch q = p;
   uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
   double *ztab = reinterpret_cast<double *>(scr + fbytes);
@@ -543,7 +746,7 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   k_tp_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, ztab, hlay);
   k_tp_vflags<<<(unsigned)gv, 256, 0, s>>>(p.X, p.base_xy, ztab, p.ncoord, make_fastdiv((uint32_t)(p.layers + 1)), flags);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_tp_pair<false, true>(q, s);
+  if (e == cudaSuccess) e = owned ? launch_tp_owned<true>(q, s) : launch_tp_pair<false, true>(q, s);
   const cudaError_t ef = cudaFreeAsync(scr, s);
   return e != cudaSuccess ? e : ef;
 }

@@ -249,8 +249,10 @@ def test_mass_general_geometry_partial(layers, with_xy):
 @pytest.mark.parametrize("form", [{"EXTMESH_P1_FORM": "split"}, {"EXTMESH_P1_FORM": "single"},
                                   {"EXTMESH_P1_FORM": "gather"}, {"EXTMESH_P1_FORM": "unfactored"},
                                   {"EXTMESH_P1_FORM": "factored"}, {"EXTMESH_P1_FORM": "cells"},
-                                  {"EXTMESH_TP_FLAGS": "1"}],
-                         ids=["split", "single", "gather", "split-unfactored", "split-factored", "cells", "tp-flags"])
+                                  {"EXTMESH_TP_FLAGS": "1"}, {"EXTMESH_TP_FLAGS": "1", "EXTMESH_TP_LEVELS": "1"},
+                                  {"EXTMESH_TP_FLAGS": "0", "EXTMESH_TP_LEVELS": "1"}],
+                         ids=["split", "single", "gather", "split-unfactored", "split-factored", "cells", "tp-flags",
+                              "tp-levels-flags", "tp-levels"])
 def test_mass_forced_form(form):
     """Every form of the P1xP1 launch passes the same parity tests, each
     forced at every size by EXTMESH_P1_FORM (read once per process, so in a
@@ -263,7 +265,9 @@ def test_mass_forced_form(form):
     million items, and the fallback when the split forms' scratch cannot be
     allocated); and the nine-space kernels' flagged form (straightness bits
     per coordinate DoF, the default from a million items) forced at every
-    size by EXTMESH_TP_FLAGS."""
+    size by EXTMESH_TP_FLAGS, with and without the level kernel for DG x CG1
+    (EXTMESH_TP_LEVELS=1: the DoFs shared by consecutive layers merged in
+    registers)."""
     import os
     import subprocess
     import sys
@@ -537,13 +541,23 @@ def test_mass_tp_parity(name, h, v, n, layers, order, perturb):
     O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
     cs = E.Space(gm, "CG1xCG1", ncomp=3)
     sp = E.Space(gm, O.DELTA[name])
-    b = sp.zeros()
-    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, to_dev(X), E.EXT_READ), (sp, to_dev(f), E.EXT_READ), (sp, b, E.EXT_INC))
+    check_tp_access(gm, cs, sp, X, f, ref, absr)
+
+
+def check_tp_access(gm, cs, sp, X, f, ref, absr):
+    """INC onto 0.25 everywhere, and WRITE onto NaN (every DoF overwritten)."""
+    Xd, fd = to_dev(X), to_dev(f)
+    b = torch.full((sp.ndofs,), 0.25, dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, Xd, E.EXT_READ), (sp, fd, E.EXT_READ), (sp, b, E.EXT_INC))
+    E.ext_sync_check()
+    close(host(b), ref + 0.25, absr + 0.25)
+    b = torch.full((sp.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, Xd, E.EXT_READ), (sp, fd, E.EXT_READ), (sp, b, E.EXT_WRITE))
     E.ext_sync_check()
     close(host(b), ref, absr)
 
 
-@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1"])
+@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1", "DG0xCG1", "DG1xDG1"])
 def test_mass_tp_flags_partial(name):
     """Over a million (column, layer) items the nine-space kernels take their
     flagged form (one straightness bit per coordinate DoF against the base
@@ -574,7 +588,4 @@ def test_mass_tp_flags_partial(name):
     O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
     cs = E.Space(gm, "CG1xCG1", ncomp=3)
     sp = E.Space(gm, O.DELTA[name])
-    b = sp.zeros()
-    E.par_loop(gm, E.EXT_K_MASS_TP, (cs, to_dev(X), E.EXT_READ), (sp, to_dev(f), E.EXT_READ), (sp, b, E.EXT_INC))
-    E.ext_sync_check()
-    close(host(b), ref, absr)
+    check_tp_access(gm, cs, sp, X, f, ref, absr)
