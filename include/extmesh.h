@@ -359,6 +359,21 @@ ext_status ext_batch_launch_params(ext_batch *batch, const ext_tune_params *para
 /* Parameters in use by the batch (chosen or autotuned). */
 ext_status ext_batch_params(const ext_batch *batch, ext_tune_params *out);
 
+/* Where the batch's parameters came from (*source: 0 given by the caller,
+ * 1 autotuned by ext_batch_create, 2 read from the tuning cache) and the host
+ * time ext_batch_create took, in seconds; either pointer may be NULL.
+ * Tuning cache: with params NULL, ext_batch_create first looks up the
+ * parameters tuned earlier for the same GPU (name, SM count), kernel and
+ * power-of-two buckets of the prism count, mean layer count and mesh count,
+ * in memory and in a file of JSON lines (EXTMESH_TUNE_CACHE, else
+ * $XDG_CACHE_HOME/extmesh/batch_tune.jsonl or $HOME/.cache/extmesh/
+ * batch_tune.jsonl); it autotunes and records the result only on a miss.
+ * EXTMESH_TUNE=force re-tunes and replaces the entry, EXTMESH_TUNE=off
+ * neither reads nor writes the cache.  The environment is read at every
+ * ext_batch_create.  (The autotuner and its cache are this library's; the
+ * paper has no counterpart.) */
+ext_status ext_batch_plan_info(const ext_batch *batch, int32_t *source, double *setup_seconds);
+
 void ext_batch_destroy(ext_batch *batch);
 
 /* Batched launch for callers that cannot allocate device memory (the paper
@@ -381,7 +396,11 @@ void ext_batch_destroy(ext_batch *batch);
  * device current; make that first call before any stream capture.  Every call
  * on a device shares the array and it keeps the last call's contents, so calls
  * whose launches overlap on the GPU race: order them (e.g. one stream).
- * Asynchronous on `stream`; errors as ext_batch_create. */
+ * The per-mesh descriptors travel to the array as kernel parameters (16 per
+ * small staging launch), so the call reads no host memory after it returns
+ * and does not wait for `stream`.  Every mesh must live on the current device,
+ * and no written argument may overlap another argument of its mesh
+ * (EXT_EINVAL).  Asynchronous on `stream`; errors as ext_batch_create. */
 #define EXT_NOALLOC_MAX_MESHES 256
 #define EXT_NOALLOC_SCRATCH_BYTES 65536
 ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id,

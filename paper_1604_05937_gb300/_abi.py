@@ -260,6 +260,18 @@ def ext_batch_params(batch: int) -> dict:
     return {f: getattr(p, f) for f, _ in ext_tune_params._fields_}
 
 
+lib.ext_batch_plan_info.restype = ctypes.c_int
+lib.ext_batch_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+TUNE_SOURCES = {0: "given", 1: "autotuned", 2: "cache"}
+
+
+def ext_batch_plan_info(batch: int) -> dict:
+    """Origin of the batch's parameters and the host time of its creation."""
+    src, sec = ctypes.c_int32(0), ctypes.c_double(0.0)
+    _check(lib.ext_batch_plan_info(batch, ctypes.byref(src), ctypes.byref(sec)))
+    return {"source": TUNE_SOURCES.get(int(src.value), str(src.value)), "setup_seconds": float(sec.value)}
+
+
 def ext_batch_destroy(batch: int) -> None:
     lib.ext_batch_destroy(batch)
 

@@ -152,6 +152,11 @@ class Batch:
     def params(self) -> dict:
         return A.ext_batch_params(self.handle)
 
+    @property
+    def plan_info(self) -> dict:
+        """{"source": "given" | "autotuned" | "cache", "setup_seconds": host time of the creation}."""
+        return A.ext_batch_plan_info(self.handle)
+
     def launch(self, stream=None) -> None:
         A.ext_batch_launch(self.handle, stream)
 

@@ -2,6 +2,11 @@
 // base-mesh entity derivation, space numbering set-up, par_loop dispatch and
 // the batched plan (autotuning, colouring, CUDA-graph capture).
 #include <algorithm>
+#include <unistd.h>
+#include <sys/stat.h>
+#include <chrono>
+#include <string>
+#include <map>
 #include <atomic>
 #include <cstdlib>
 #include <cmath>
@@ -698,15 +703,9 @@ static bool same_numbering(const ext_space *a, const ext_space *b) {
     if (st_ != EXT_OK) return st_;     \
   } while (0)
 
-extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int32_t nargs, const ext_arg *args,
-                                   void *stream) {
-  if (!mesh) return ext_fail(EXT_EINVAL, "ext_par_loop: mesh is NULL");
-  if (nargs > 0 && !args) return ext_fail(EXT_EINVAL, "ext_par_loop: args is NULL");
-  cudaStream_t s = (cudaStream_t)stream;
-  const int64_t C = mesh->N[2];
-  const int L = mesh->layers;
-  cudaError_t e = cudaSuccess;
-  // a WRITE or INC argument may share no byte with another argument
+// A WRITE or INC argument may share no byte with another argument of the
+// same launch (checked from the arguments' base pointers and sizes).
+static ext_status check_no_overlap(int32_t nargs, const ext_arg *args, const char *who) {
   for (int i = 0; i < nargs; ++i) {
     if (args[i].access == EXT_READ || !args[i].space || !args[i].data) continue;
     const char *lo_i = (const char *)args[i].data;
@@ -716,9 +715,21 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       const char *lo_j = (const char *)args[j].data;
       const char *hi_j = lo_j + sizeof(double) * (size_t)args[j].space->ndofs * (size_t)args[j].space->ncomp;
       if (lo_i < hi_j && lo_j < hi_i)
-        return ext_fail(EXT_EINVAL, "ext_par_loop: argument %d (written) overlaps argument %d", i, j);
+        return ext_fail(EXT_EINVAL, "%s: argument %d (written) overlaps argument %d", who, i, j);
     }
   }
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int32_t nargs, const ext_arg *args,
+                                   void *stream) {
+  if (!mesh) return ext_fail(EXT_EINVAL, "ext_par_loop: mesh is NULL");
+  if (nargs > 0 && !args) return ext_fail(EXT_EINVAL, "ext_par_loop: args is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t C = mesh->N[2];
+  const int L = mesh->layers;
+  cudaError_t e = cudaSuccess;
+  EXT_CHECK(check_no_overlap(nargs, args, "ext_par_loop"));
   switch (kernel_id) {
     case EXT_K_EXTRUDE: {
       const char *kn = "EXT_K_EXTRUDE";
@@ -1039,6 +1050,9 @@ struct ext_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int sms = 152;
+  bool coloured = false;
+  int32_t source = 0;        // 0 parameters given, 1 autotuned, 2 from the tuning cache
+  double setup_seconds = 0;  // host time of ext_batch_create
 };
 
 static void free_phases(std::vector<BatchPhaseDev> &ph) {
@@ -1150,6 +1164,158 @@ static void destroy_batch(ext_batch *b) {
   delete b;
 }
 
+// Colour classes of every mesh of the batch (the colour form's phases), built
+// on first use.
+static ext_status ensure_colours(ext_batch *b) {
+  if (b->coloured) return EXT_OK;
+  b->d_cells.assign((size_t)b->nmesh, nullptr);
+  b->colour_off.resize((size_t)b->nmesh);
+  for (int mi = 0; mi < b->nmesh; ++mi) {
+    std::vector<int32_t> order;
+    const int nc = colour_cells(b->meshes[(size_t)mi], order, b->colour_off[(size_t)mi]);
+    if (nc < 0) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d needs more than 64 colours", mi);
+    b->ncolours = std::max(b->ncolours, nc);
+    if (!order.empty()) {
+      cudaError_t e = cudaMalloc(&b->d_cells[(size_t)mi], order.size() * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_cells[(size_t)mi], order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return ext_fail(EXT_ENOMEM, "batched launch: %s", cudaGetErrorString(e));
+    }
+  }
+  b->coloured = true;
+  return EXT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning cache of the batched launch.  Key: GPU name and SM count, kernel
+// (forward, adjoint or both), and power-of-two buckets of the prism count,
+// the mean layer count and the mesh count; value: the autotuned parameters
+// and their time.  Kept in memory for the process and, unless EXTMESH_TUNE=off,
+// in a file of JSON lines (EXTMESH_TUNE_CACHE, else
+// $XDG_CACHE_HOME/extmesh/batch_tune.jsonl or $HOME/.cache/extmesh/...),
+// rewritten through a temporary file and a rename.  EXTMESH_TUNE=force times
+// the candidates again and replaces the entry.
+static std::mutex g_tune_mu;
+static std::map<std::string, ext_tune_params> g_tune_mem;
+
+static int tune_env() {
+  const char *ev = getenv("EXTMESH_TUNE");
+  if (ev && strcmp(ev, "force") == 0) return 1;
+  if (ev && strcmp(ev, "off") == 0) return 2;
+  return 0;
+}
+
+static std::string tune_path() {
+  const char *ev = getenv("EXTMESH_TUNE_CACHE");
+  if (ev && ev[0]) return ev;
+  const char *xdg = getenv("XDG_CACHE_HOME");
+  if (xdg && xdg[0]) return std::string(xdg) + "/extmesh/batch_tune.jsonl";
+  const char *home = getenv("HOME");
+  if (home && home[0]) return std::string(home) + "/.cache/extmesh/batch_tune.jsonl";
+  return std::string();
+}
+
+static int log2_bucket(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
+
+static std::string tune_key(const ext_batch *b) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char &c : name)
+    if (c == '"' || c == '\\' || c == '|') c = '_';
+  double prisms = 0.0, layers = 0.0;
+  for (const ext_mesh *m : b->meshes) {
+    prisms += (double)m->N[2] * (double)m->layers;
+    layers += (double)m->layers;
+  }
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|sm%d|mode%d|prisms2^%d|layers2^%d|meshes2^%d", name.c_str(), b->sms, b->mode,
+           log2_bucket(prisms), log2_bucket(layers / (double)b->nmesh), log2_bucket((double)b->nmesh));
+  return buf;
+}
+
+// one line: {"key": "...", "params": [cols_per_item, layer_tile, use_atomics, threads, ctas_per_sm], "ms": t}
+static bool tune_parse(const std::string &line, std::string &key, ext_tune_params &tp) {
+  const size_t k0 = line.find("\"key\": \"");
+  if (k0 == std::string::npos) return false;
+  const size_t ks = k0 + 8, ke = line.find('"', ks);
+  if (ke == std::string::npos) return false;
+  key = line.substr(ks, ke - ks);
+  const size_t p0 = line.find("\"params\": [", ke);
+  if (p0 == std::string::npos) return false;
+  int v[5];
+  if (sscanf(line.c_str() + p0 + 11, "%d, %d, %d, %d, %d", &v[0], &v[1], &v[2], &v[3], &v[4]) != 5) return false;
+  tp.cols_per_item = v[0];
+  tp.layer_tile = v[1];
+  tp.use_atomics = v[2];
+  tp.threads = v[3];
+  tp.ctas_per_sm = v[4];
+  return true;
+}
+
+static bool tune_lookup(const std::string &key, ext_tune_params &out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_mem.find(key);
+  if (it != g_tune_mem.end()) {
+    out = it->second;
+    return true;
+  }
+  const std::string path = tune_path();
+  if (path.empty()) return false;
+  FILE *f = fopen(path.c_str(), "r");
+  if (!f) return false;
+  bool found = false;
+  char buf[1024];
+  while (fgets(buf, sizeof buf, f)) {
+    std::string k;
+    ext_tune_params tp;
+    if (tune_parse(buf, k, tp) && check_params(tp) == EXT_OK) {
+      g_tune_mem[k] = tp;
+      if (k == key) {
+        out = tp;
+        found = true;
+      }
+    }
+  }
+  fclose(f);
+  (void)cudaGetLastError();
+  return found;
+}
+
+static void tune_store(const std::string &key, const ext_tune_params &tp, float ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_mem[key] = tp;
+  const std::string path = tune_path();
+  if (path.empty()) return;
+  // keep the other entries of the file, replace this key's
+  std::vector<std::string> keep;
+  if (FILE *f = fopen(path.c_str(), "r")) {
+    char buf[1024];
+    while (fgets(buf, sizeof buf, f)) {
+      std::string k;
+      ext_tune_params t;
+      if (tune_parse(buf, k, t) && k != key) keep.push_back(buf);
+    }
+    fclose(f);
+  }
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {  // create the directory chain
+    for (size_t q = 1; q <= slash; ++q)
+      if (path[q] == '/' || q == slash) mkdir(path.substr(0, q == slash ? slash : q).c_str(), 0755);
+  }
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (const auto &l : keep) fputs(l.c_str(), f);
+  fprintf(f, "{\"key\": \"%s\", \"params\": [%d, %d, %d, %d, %d], \"ms\": %.4f}\n", key.c_str(), tp.cols_per_item,
+          tp.layer_tile, tp.use_atomics, tp.threads, tp.ctas_per_sm, (double)ms);
+  const bool ok = fclose(f) == 0;
+  if (ok) rename(tmp.c_str(), path.c_str());
+  else remove(tmp.c_str());
+}
+
 static ext_status capture(ext_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -1172,27 +1338,13 @@ static ext_status capture(ext_batch *b) {
 extern "C" ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *meshes, int32_t kernel_id, int32_t nargs,
                                        const ext_arg *args, const ext_tune_params *params, void *stream,
                                        ext_batch **out) {
+  const auto t_start = std::chrono::steady_clock::now();
   if (!out) return ext_fail(EXT_EINVAL, "ext_batch_create: out is NULL");
   *out = nullptr;
-  if (nmesh < 1 || !meshes || !args) return ext_fail(EXT_EINVAL, "ext_batch_create: no meshes");
-  int mode;
-  if (kernel_id == EXT_K_U2V_FWD) mode = 1;
-  else if (kernel_id == EXT_K_U2V_ADJ) mode = 2;
-  else if (kernel_id == EXT_K_U2V_FWDADJ) mode = 3;
-  else return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: kernel %d is not batched", kernel_id);
-  const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
-  if (nargs != want) return ext_fail(EXT_EINVAL, "ext_batch_create: expects %d arguments per mesh", want);
-  for (int mi = 0; mi < nmesh; ++mi) {
-    const ext_mesh *m = meshes[mi];
-    const ext_arg *a = args + (size_t)mi * nargs;
-    if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d: prisms only", mi);
-    if (m->var) return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d has variable layers", mi);
-    EXT_CHECK(check_arg(m, a, 0, "ext_batch_create", ELEM_P1P1, 3, EXT_READ));
-    for (int j = 1; j < nargs; ++j) {
-      const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);
-      EXT_CHECK(check_arg(m, a, j, "ext_batch_create", ELEM_P1P1, 1, is_out ? EXT_INC : EXT_READ));
-    }
-  }
+  // the same checks as every batched launch: kernel, argument lists,
+  // current device, no written argument overlapping another
+  int mode = 0;
+  EXT_CHECK(ext_batch_validate(nmesh, meshes, kernel_id, nargs, args, &mode));
   if (params) EXT_CHECK(check_params(*params));
   ext_batch *b = new ext_batch();
   b->nmesh = nmesh;
@@ -1208,31 +1360,22 @@ extern "C" ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *mes
     destroy_batch(b);
     return ext_fail(EXT_ENOMEM, "ext_batch_create: %s", cudaGetErrorString(e));
   }
-  // colour classes of every mesh (used when a candidate asks for them)
-  b->d_cells.assign((size_t)nmesh, nullptr);
-  b->colour_off.resize((size_t)nmesh);
-  for (int mi = 0; mi < nmesh; ++mi) {
-    std::vector<int32_t> order;
-    const int nc = colour_cells(meshes[mi], order, b->colour_off[(size_t)mi]);
-    if (nc < 0) {
-      destroy_batch(b);
-      return ext_fail(EXT_EUNSUPPORTED, "ext_batch_create: mesh %d needs more than 64 colours", mi);
-    }
-    b->ncolours = std::max(b->ncolours, nc);
-    if (!order.empty()) {
-      e = cudaMalloc(&b->d_cells[(size_t)mi], order.size() * sizeof(int32_t));
-      if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_cells[(size_t)mi], order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) {
-        destroy_batch(b);
-        return ext_fail(EXT_ENOMEM, "ext_batch_create: %s", cudaGetErrorString(e));
-      }
-    }
-  }
   cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = tune_key(b);
+  const int tune_mode = tune_env();  // 0 use the cache, 1 re-tune and store, 2 no cache
+  ext_tune_params cached;
   if (params) {
     b->params = *params;
+  } else if (tune_mode == 0 && tune_lookup(key, cached)) {
+    b->params = cached;
+    b->source = 2;
   } else {
+    b->source = 1;
+    const ext_status cs = ensure_colours(b);
+    if (cs != EXT_OK) {
+      destroy_batch(b);
+      return cs;
+    }
     // autotune: time each candidate once after one warm-up launch
     std::vector<ext_tune_params> cand;
     const int cpis[] = {1, 2, 4, 8};
@@ -1277,14 +1420,24 @@ extern "C" ext_status ext_batch_create(int32_t nmesh, const ext_mesh *const *mes
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (tune_mode != 2) tune_store(key, b->params, best);
   }
-  ext_status st = build_phases(b, b->params, b->phases);
+  ext_status st = b->params.use_atomics ? EXT_OK : ensure_colours(b);
+  if (st == EXT_OK) st = build_phases(b, b->params, b->phases);
   if (st == EXT_OK) st = capture(b);
   if (st != EXT_OK) {
     destroy_batch(b);
     return st;
   }
+  b->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   *out = b;
+  return EXT_OK;
+}
+
+extern "C" ext_status ext_batch_plan_info(const ext_batch *batch, int32_t *source, double *setup_seconds) {
+  if (!batch) return ext_fail(EXT_EINVAL, "ext_batch_plan_info: batch is NULL");
+  if (source) *source = batch->source;
+  if (setup_seconds) *setup_seconds = batch->setup_seconds;
   return EXT_OK;
 }
 
@@ -1297,6 +1450,7 @@ extern "C" ext_status ext_batch_launch(ext_batch *batch, void *stream) {
 extern "C" ext_status ext_batch_launch_params(ext_batch *batch, const ext_tune_params *params, void *stream) {
   if (!batch || !params) return ext_fail(EXT_EINVAL, "ext_batch_launch_params: invalid arguments");
   EXT_CHECK(check_params(*params));
+  if (!params->use_atomics) EXT_CHECK(ensure_colours(batch));
   std::vector<BatchPhaseDev> ph;
   EXT_CHECK(build_phases(batch, *params, ph));
   cudaError_t e = run_phases(batch, ph, *params, (cudaStream_t)stream);
@@ -1326,11 +1480,18 @@ ext_status ext_batch_validate(int32_t nmesh, const ext_mesh *const *meshes, int3
   else return ext_fail(EXT_EUNSUPPORTED, "batched launch: kernel %d is not batched", kernel_id);
   const int want = mode == 1 ? 3 : (mode == 2 ? 4 : 5);
   if (nargs != want) return ext_fail(EXT_EINVAL, "batched launch: expects %d arguments per mesh", want);
+  int cur = 0;
+  const cudaError_t ed = cudaGetDevice(&cur);
+  if (ed != cudaSuccess) return ext_fail(EXT_ECUDA, "batched launch: %s", cudaGetErrorString(ed));
   for (int mi = 0; mi < nmesh; ++mi) {
     const ext_mesh *m = meshes[mi];
     const ext_arg *a = args + (size_t)mi * nargs;
     if (!m || m->kind != EXT_TRI) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d: prisms only", mi);
     if (m->var) return ext_fail(EXT_EUNSUPPORTED, "batched launch: mesh %d has variable layers", mi);
+    if (m->device != cur)
+      return ext_fail(EXT_EINVAL, "batched launch: mesh %d lives on device %d, the current device is %d", mi,
+                      m->device, cur);
+    EXT_CHECK(check_no_overlap(nargs, a, "batched launch"));
     EXT_CHECK(check_arg(m, a, 0, "batched launch", ELEM_P1P1, 3, EXT_READ));
     for (int j = 1; j < nargs; ++j) {
       const bool is_out = (mode == 1 && j == 2) || (mode == 2 && j == 3) || (mode == 3 && j >= 3);

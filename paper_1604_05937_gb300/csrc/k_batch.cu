@@ -229,6 +229,7 @@ cudaError_t launch_batch_phase(const void *d_descs, int nmesh, int64_t nitems, i
 // launches overlap on the GPU race on it, so issue them in one stream or
 // otherwise order them.
 
+#include <cstring>
 #include <mutex>
 
 #define EXT_NOALLOC_COUNTER_BYTES 256
@@ -236,6 +237,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[EXT_NOALLOC_SCR
 
 static_assert(EXT_NOALLOC_COUNTER_BYTES + EXT_NOALLOC_MAX_MESHES * sizeof(BatchDesc) <= EXT_NOALLOC_SCRATCH_BYTES,
               "scratch array too small for the descriptor table");
+
+// The descriptors reach the array as kernel parameters, kNoallocChunk per
+// launch of k_noalloc_stage: no host buffer is read after the entry point
+// returns, and the host never waits for the stream.
+constexpr int kNoallocChunk = 16;
+struct NoallocChunk {
+  BatchDesc d[kNoallocChunk];
+};
+
+__global__ void k_noalloc_stage(const NoallocChunk chunk, BatchDesc *__restrict__ dst, int count) {
+  const int i = threadIdx.x;
+  if (i < count) dst[i] = chunk.d[i];
+}
 
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_dev[128];  // device address of the array, per device
@@ -288,8 +302,9 @@ extern "C" ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const
   st = noalloc_scratch(&scratch);
   if (st != EXT_OK) return st;
 
-  // descriptors staged in a per-thread host buffer, then copied into the array
-  static thread_local BatchDesc stage[EXT_NOALLOC_MAX_MESHES];
+  // descriptors built on the host, then written into the array by
+  // k_noalloc_stage, kNoallocChunk at a time, as kernel parameters
+  BatchDesc stage[EXT_NOALLOC_MAX_MESHES];
   int64_t item = 0;
   for (int mi = 0; mi < nmesh; ++mi) {
     const ext_arg *a = args + (size_t)mi * nargs;
@@ -309,8 +324,15 @@ extern "C" ext_status ext_batch_run_noalloc(int32_t nmesh, const ext_mesh *const
     item += (int64_t)ncol_items * nlay_items;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(scratch + EXT_NOALLOC_COUNTER_BYTES, stage, sizeof(BatchDesc) * (size_t)nmesh,
-                                  cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
+  BatchDesc *table = reinterpret_cast<BatchDesc *>(scratch + EXT_NOALLOC_COUNTER_BYTES);
+  for (int first = 0; first < nmesh && e == cudaSuccess; first += kNoallocChunk) {
+    NoallocChunk chunk;
+    const int count = nmesh - first < kNoallocChunk ? nmesh - first : kNoallocChunk;
+    memcpy(chunk.d, stage + first, sizeof(BatchDesc) * (size_t)count);
+    k_noalloc_stage<<<1, kNoallocChunk, 0, s>>>(chunk, table + first, count);
+    e = cudaGetLastError();
+  }
   int dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

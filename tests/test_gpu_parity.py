@@ -473,6 +473,26 @@ def test_batched_parity_autotuned_and_replayed():
     assert p["cols_per_item"] >= 1 and p["threads"] in (64, 128, 256)
 
 
+def test_batched_tuning_cache(tmp_path, monkeypatch):
+    """The second plan of the same workload reads its parameters from the
+    tuning cache (file of JSON lines) instead of timing the candidates again,
+    and EXTMESH_TUNE=force re-tunes."""
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("EXTMESH_TUNE_CACHE", str(path))
+    monkeypatch.setenv("EXTMESH_TUNE", "force")
+    a = _batch_case(None)
+    assert a.plan_info["source"] == "autotuned"
+    assert path.exists() and '"params": [' in path.read_text()
+    monkeypatch.delenv("EXTMESH_TUNE")
+    b = _batch_case(None)
+    assert b.plan_info["source"] == "cache"
+    assert b.params == a.params
+    assert b.plan_info["setup_seconds"] < a.plan_info["setup_seconds"]
+    monkeypatch.setenv("EXTMESH_TUNE", "off")
+    c = _batch_case(dict(cols_per_item=2, layer_tile=0, use_atomics=1, threads=256, ctas_per_sm=4))
+    assert c.plan_info["source"] == "given"
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_mesh_and_single_cell():
     cells = np.zeros((0, 3), dtype=np.int32)

@@ -90,3 +90,27 @@ def test_noalloc_rejects_oversized_batch_and_colours():
         E.ext_batch_run_noalloc([gm.handle], E.EXT_K_U2V_FWD, 3, args,
                                 params=dict(cols_per_item=32, layer_tile=0, use_atomics=0, threads=256,
                                             ctas_per_sm=2))
+
+
+def test_noalloc_and_plan_reject_overlapping_outputs():
+    """The batched entry points check, per mesh, that no written argument
+    overlaps another one: with the forward and adjoint outputs in one buffer
+    both the plan and the allocation-free launch fail with EXT_EINVAL before
+    launching anything."""
+    m = meshgen.tri_mesh(6, seed=2500, order="rcm")
+    gm = E.Mesh(m.cells, m.xy, 3)
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    sp = E.Space(gm, "CG1xCG1")
+    X = E.extrude_coords(gm, cs)
+    u = torch.from_numpy(meshgen.uniform_field(sp.ndofs, 2501)).to(dev)
+    w = torch.from_numpy(meshgen.uniform_field(sp.ndofs, 2502)).to(dev)
+    F = sp.zeros()
+    args = [(cs.handle, X, E.EXT_READ), (sp.handle, u, E.EXT_READ), (sp.handle, w, E.EXT_READ),
+            (sp.handle, F, E.EXT_INC), (sp.handle, F, E.EXT_INC)]
+    with pytest.raises(E.ExtError, match="overlaps"):
+        E.ext_batch_run_noalloc([gm.handle], E.EXT_K_U2V_FWDADJ, 5, args)
+    with pytest.raises(E.ExtError, match="overlaps"):
+        E.ext_batch_create([gm.handle], E.EXT_K_U2V_FWDADJ, 5, args, params=None)
+    args[4] = (sp.handle, u, E.EXT_INC)  # the adjoint output aliasing the input u
+    with pytest.raises(E.ExtError, match="overlaps"):
+        E.ext_batch_run_noalloc([gm.handle], E.EXT_K_U2V_FWDADJ, 5, args)
