@@ -1300,6 +1300,115 @@ def run_reference(args, rank, world):
     return line
 
 
+def _node_cpus():
+    """{NUMA node: CPUs of that node this process may run on}, nodes with CPUs only."""
+    out = {}
+    allowed = os.sched_getaffinity(0)
+    base = "/sys/devices/system/node"
+    for d in sorted(os.listdir(base)) if os.path.isdir(base) else []:
+        if not d.startswith("node") or not d[4:].isdigit():
+            continue
+        try:
+            with open(os.path.join(base, d, "cpulist")) as f:
+                spec = f.read().strip()
+        except OSError:
+            continue
+        cpus = set()
+        for part in spec.split(","):
+            if not part:
+                continue
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= allowed
+        if cpus:
+            out[int(d[4:])] = sorted(cpus)
+    return out
+
+
+def run_hostlink(args, rank, world, local):
+    """Host link rates of the end-to-end step's copies: pinned host buffers of
+    1 GiB first touched from the CPUs of each NUMA node this process may use
+    (so that their pages sit on that node), H2D and D2H alone and both
+    directions at once, copy engines driven by cudaMemcpyAsync, best of 5."""
+    import torch
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prop = torch.cuda.get_device_properties(dev)
+    bus = None
+    for attr in ("pci_domain_id", "pci_bus_id", "pci_device_id"):
+        if not hasattr(prop, attr):
+            break
+    else:
+        bus = "%04x:%02x:%02x.0" % (prop.pci_domain_id, prop.pci_bus_id, prop.pci_device_id)
+    gpu_node = None
+    if bus:
+        try:
+            with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+                gpu_node = int(f.read().strip())
+        except (OSError, ValueError):
+            gpu_node = None
+    nbytes = 1 << 30
+    n = nbytes // 8
+    d_a = torch.empty(n, dtype=torch.float64, device=dev)
+    d_b = torch.empty(n, dtype=torch.float64, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    old = os.sched_getaffinity(0)
+    rows = {}
+
+    def rate(fn, streams, moved):
+        best = 0.0
+        for _ in range(5):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(streams[0])
+            for st in streams[1:]:
+                st.wait_event(a)
+            fn()
+            for st in streams[1:]:
+                streams[0].wait_stream(st)
+            b.record(streams[0])
+            b.synchronize()
+            best = max(best, moved / (a.elapsed_time(b) * 1e-3) / 1e9)
+        return round(best, 1)
+
+    nodes = _node_cpus()
+    for node, cpus in (nodes.items() if nodes else [(-1, sorted(old))]):
+        os.sched_setaffinity(0, cpus)
+        h_a = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_b = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_a.fill_(1.0)  # first touch from this node's CPUs
+        h_b.fill_(2.0)
+
+        def h2d():
+            with torch.cuda.stream(s1):
+                d_a.copy_(h_a, non_blocking=True)
+
+        def d2h():
+            with torch.cuda.stream(s1):
+                h_b.copy_(d_b, non_blocking=True)
+
+        def both():
+            with torch.cuda.stream(s1):
+                d_a.copy_(h_a, non_blocking=True)
+            with torch.cuda.stream(s2):
+                h_b.copy_(d_b, non_blocking=True)
+
+        rows[str(node)] = {"cpus": len(cpus), "h2d_gbs": rate(h2d, [s1], nbytes),
+                           "d2h_gbs": rate(d2h, [s1], nbytes), "both_gbs": rate(both, [s1, s2], 2 * nbytes)}
+        del h_a, h_b
+    os.sched_setaffinity(0, old)
+    if rank != 0:
+        return None
+    best = max(rows.values(), key=lambda r: r["h2d_gbs"] + r["d2h_gbs"])
+    return {"metric": "host link: pinned host <-> GB300 copy rates per NUMA node of the host buffers",
+            "value": best["both_gbs"], "unit": "GB/s", "n_gpus": world, "steps": 5, "warmup": 0,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic (1 GiB buffers)",
+            "config": {"workload": "1 GiB H2D, D2H and both at once, copy engines, best of 5",
+                       "gpu_pci": bus, "gpu_numa_node": gpu_node, "gpu": prop.name},
+            "per_node": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1322,6 +1431,8 @@ def main():
     ap.add_argument("--geometry", choices=["flat", "terrain", "wavy", "tilted"], default=None,
                     help="levels of the config 2 step (config 8: terrain by default)")
     ap.add_argument("--no-forms", action="store_true", help="config 2: skip the per-form P1xP1 timings")
+    ap.add_argument("--hostlink", action="store_true",
+                    help="measure the host link (pinned buffers on each NUMA node) instead of a workload")
     ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1336,6 +1447,8 @@ def main():
         __graft_entry__.build_library_only()
         runner = {2: run_ours, 3: run_cfg3, 4: run_cfg4, 5: run_cfg5, 6: run_cfg6, 7: run_cfg7,
                   8: run_ours}[args.config]
+        if args.hostlink:
+            runner = run_hostlink
         line = runner(args, rank, world, local)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)

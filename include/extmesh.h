@@ -447,6 +447,17 @@ typedef enum {
 ext_status ext_set_option(int32_t option, int32_t value);
 ext_status ext_get_option(int32_t option, int32_t *value);
 
+/* Range check of a space's stencil lists on the device: every index that
+ * Algorithm 3 forms from them (base_map[c][i] + l * offset[i] for every layer
+ * l of column c; for a CG1xCG1 space also the gather form's vertex rows) must
+ * lie in [0, ndofs).  Synchronous on `stream`; EXT_OK, or EXT_EDEVICE when an
+ * index is out of range (the error word is cleared again) or when the device
+ * error word was already set.  The checked build of the library
+ * (libextmesh_checked.so, compiled with EXT_CHECKED) runs the same checks on
+ * every argument of ext_par_loop before launching and launches nothing when
+ * one fails.  A debugging aid of this library; the paper has no counterpart. */
+ext_status ext_space_check(const ext_space *space, void *stream);
+
 /* Waits for `stream`, then reads and clears the device error word:
  * EXT_OK, EXT_ETIMEOUT (a bounded wait expired), EXT_EDEVICE (another device
  * condition; see ext_last_error), or EXT_ECUDA (an asynchronous CUDA error). */

@@ -12,7 +12,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libextmesh.so")
+# EXTMESH_CHECKED=1 loads the checked build (stencil indices range-checked on
+# the device before every launch)
+LIB_PATH = os.path.join(_HERE, "libextmesh_checked.so" if os.environ.get("EXTMESH_CHECKED") == "1"
+                        else "libextmesh.so")
 
 EXT_OK, EXT_EINVAL, EXT_ENOMEM, EXT_ECUDA, EXT_EOVERFLOW, EXT_ETIMEOUT, EXT_EDEVICE, EXT_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["EXT_OK", "EXT_EINVAL", "EXT_ENOMEM", "EXT_ECUDA", "EXT_EOVERFLOW", "EXT_ETIMEOUT",
@@ -329,3 +332,12 @@ def ext_get_option(option: int) -> int:
     v = ctypes.c_int32(0)
     _check(lib.ext_get_option(option, ctypes.byref(v)))
     return int(v.value)
+
+
+# ---- range check of a space's stencil lists (ext_space_check)
+lib.ext_space_check.restype = ctypes.c_int
+lib.ext_space_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+
+
+def ext_space_check(space: int, stream=None) -> None:
+    _check(lib.ext_space_check(space, _stream(stream)))

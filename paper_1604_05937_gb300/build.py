@@ -18,6 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libextmesh.so")
+# the checked build: ext_api.cu with EXT_CHECKED (every stencil index range-
+# checked on the device before a launch), the other units shared
+LIB_CHECKED = os.path.join(HERE, "libextmesh_checked.so")
 ROOT = os.path.dirname(HERE)
 HEADER = os.path.join(ROOT, "include", "extmesh.h")
 
@@ -37,9 +40,9 @@ def _deps() -> list[str]:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_CHECKED):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECKED))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -52,9 +55,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra or [])
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    def compile_one(job) -> str:
+        src, checked = job
+        obj = os.path.join(BUILD, os.path.basename(src) + (".checked.o" if checked else ".o"))
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, *(["-DEXT_CHECKED"] if checked else []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -62,15 +66,19 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    api = os.path.join(CSRC, "ext_api.cu")
+    jobs = [(src, False) for src in srcs] + [(api, True)]
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    plain, checked = objs[:-1], [o for o in objs[:-1] if not o.endswith("ext_api.cu.o")] + [objs[-1]]
+    for lib, parts in ((LIB, plain), (LIB_CHECKED, checked)):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *parts,
+               "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

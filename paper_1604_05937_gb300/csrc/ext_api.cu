@@ -721,6 +721,28 @@ static ext_status check_no_overlap(int32_t nargs, const ext_arg *args, const cha
   return EXT_OK;
 }
 
+extern "C" ext_status ext_space_check(const ext_space *space, void *stream) {
+  if (!space || !space->mesh) return ext_fail(EXT_EINVAL, "ext_space_check: space is NULL");
+  const ext_mesh *mesh = space->mesh;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int *w = ext_device_error_word();
+  if (!w) return ext_fail(EXT_ECUDA, "ext_space_check: no device error word");
+  unsigned int v = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) return ext_fail(EXT_EDEVICE, "ext_space_check: the device error word is already set (0x%x)", v);
+  if (e == cudaSuccess && space->d_map) e = launch_check_map(space, mesh->d_cell_layers, mesh->layers, w, s);
+  if (e == cudaSuccess && space->elem == ELEM_P1P1 && space->ncomp == 1) e = launch_check_rows(mesh, space->ndofs, w, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_space_check: %s", cudaGetErrorString(e));
+  if (v & EXT_DERR_BOUNDS) {
+    cudaMemset(w, 0, sizeof(v));
+    return ext_fail(EXT_EDEVICE, "ext_space_check: a stencil index of the space is out of range");
+  }
+  return EXT_OK;
+}
+
 extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int32_t nargs, const ext_arg *args,
                                    void *stream) {
   if (!mesh) return ext_fail(EXT_EINVAL, "ext_par_loop: mesh is NULL");
@@ -730,6 +752,29 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
   const int L = mesh->layers;
   cudaError_t e = cudaSuccess;
   EXT_CHECK(check_no_overlap(nargs, args, "ext_par_loop"));
+#ifdef EXT_CHECKED
+  // checked build: every index the launch will form from the stencil maps
+  // (and the gather form's vertex rows) is range-checked on the device first;
+  // on a failure nothing is launched
+  {
+    unsigned int *w = ext_device_error_word();
+    if (!w) return ext_fail(EXT_ECUDA, "ext_par_loop: no device error word");
+    for (int i = 0; i < nargs && e == cudaSuccess; ++i)
+      if (args[i].space && args[i].space->d_map && args[i].space->mesh == mesh)
+        e = launch_check_map(args[i].space, mesh->d_cell_layers, L, w, s);
+    if (e == cudaSuccess && (kernel_id == EXT_K_RHS_P1P1 || kernel_id == EXT_K_MASS_P1P1) && nargs > 1 &&
+        args[1].space)
+      e = launch_check_rows(mesh, args[1].space->ndofs, w, s);
+    unsigned int v = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ext_fail(EXT_ECUDA, "ext_par_loop: checked build: %s", cudaGetErrorString(e));
+    if (v & EXT_DERR_BOUNDS) {
+      cudaMemset(w, 0, sizeof(v));
+      return ext_fail(EXT_EDEVICE, "ext_par_loop: checked build: a stencil index is out of range; nothing launched");
+    }
+  }
+#endif
   switch (kernel_id) {
     case EXT_K_EXTRUDE: {
       const char *kn = "EXT_K_EXTRUDE";

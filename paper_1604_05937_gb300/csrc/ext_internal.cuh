@@ -324,3 +324,9 @@ const int32_t *ext_space_map_dev(const ext_space *s);
 const int32_t *ext_space_offsets_host(const ext_space *s);
 int64_t ext_mesh_ncells(const ext_mesh *m);
 int32_t ext_mesh_layers(const ext_mesh *m);
+
+// Range checks of the checked build (k_number.cu): stencil maps of a space
+// over its mesh's layers, and the vertex rows of the gather form.
+cudaError_t launch_check_map(const ext_space *sp, const int32_t *cell_layers, int32_t layers, unsigned int *err,
+                             cudaStream_t s);
+cudaError_t launch_check_rows(const ext_mesh *m, int64_t ndofs, unsigned int *err, cudaStream_t s);

@@ -260,3 +260,77 @@ cudaError_t launch_ragged_map(const RaggedLaunch &p, cudaStream_t s) {
   k_ragged_map<<<(unsigned)blocks, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Range check of a stencil map (the checked build, EXT_CHECKED, runs it for
+// every argument before a launch): every index Algorithm 3 forms,
+// map[c][i] + l offset[i] for l = 0 .. lambda_c - 1, must lie in [0, ndofs).
+// The map is linear in l, so checking l = 0 and l = lambda_c - 1 covers all
+// layers.  A failure sets EXT_DERR_BOUNDS in the error word; the kernel reads
+// only the map, the offsets and the layer counts, all in range.
+__global__ void __launch_bounds__(256) k_check_map(const int32_t *__restrict__ map, const int64_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ roff, int32_t k,
+                                                   const int32_t *__restrict__ offset, int64_t ncells, int32_t layers,
+                                                   const int32_t *__restrict__ cell_layers, int64_t ndofs,
+                                                   unsigned int *err) {
+  const int64_t n = rowptr ? rowptr[ncells] : ncells * (int64_t)k;
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c;
+    int32_t off;
+    if (rowptr) {  // ragged lists: find the cell of entry e (binary search on the row pointer)
+      int64_t lo = 0, hi = ncells - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (rowptr[mid] <= e) lo = mid;
+        else hi = mid - 1;
+      }
+      c = lo;
+      off = roff[e];
+    } else {
+      c = e / k;
+      off = offset[e - c * k];
+    }
+    const int64_t lay = cell_layers ? cell_layers[c] : layers;
+    const int64_t lo_i = map[e], hi_i = lo_i + (lay - 1) * (int64_t)off;
+    bad |= (lo_i < 0) | (lo_i >= ndofs) | (hi_i < 0) | (hi_i >= ndofs) | (lay < 1);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, EXT_DERR_BOUNDS);
+}
+
+// The vertex rows of the gather form: every entry's column start j (layers +
+// 1) plus a level up to `layers` must be a DoF of the CG1xCG1 space, and every
+// cell of a row's edge a cell of the mesh.
+__global__ void __launch_bounds__(256) k_check_rows(const int32_t *__restrict__ vnbr, const int2 *__restrict__ vedge,
+                                                    int64_t nent, int32_t layers, int64_t ndofs, int64_t ncells,
+                                                    unsigned int *err) {
+  int bad = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nent; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j0 = vnbr[t];
+    const int2 e = vedge[t];
+    bad |= (j0 < 0) | (j0 + layers >= ndofs) | (e.x >= ncells) | (e.y >= ncells) | (e.x < -1) | (e.y < -1);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, EXT_DERR_BOUNDS);
+}
+
+cudaError_t launch_check_map(const ext_space *sp, const int32_t *cell_layers, int32_t layers, unsigned int *err,
+                             cudaStream_t s) {
+  const int64_t C = sp->mesh->N[2];
+  if (C == 0) return cudaSuccess;
+  const int64_t n = sp->ragged ? sp->nentries : C * (int64_t)sp->k;
+  int64_t g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  k_check_map<<<(unsigned)g, 256, 0, s>>>(sp->d_map, sp->ragged ? sp->d_rowptr : nullptr,
+                                          sp->ragged ? sp->d_roff : nullptr, sp->k, sp->d_offset, C, layers,
+                                          cell_layers, sp->ndofs, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_rows(const ext_mesh *m, int64_t ndofs, unsigned int *err, cudaStream_t s) {
+  if (!m->d_vnbr || m->n_vent == 0) return cudaSuccess;
+  int64_t g = (m->n_vent + 255) / 256;
+  if (g > 4096) g = 4096;
+  k_check_rows<<<(unsigned)g, 256, 0, s>>>(m->d_vnbr, m->d_vedge, m->n_vent, m->layers, ndofs, m->N[2], err);
+  return cudaGetLastError();
+}
