@@ -399,6 +399,10 @@ def run_ours(args, rank, world, local):
     reps = 20
     if geometry == "flat" and not args.no_forms:
         extra["forms_ms"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split", "factored", "cells"], reps)
+        old_flat = E.ext_get_option(E.EXT_OPT_P1_FLAT)
+        E.ext_set_option(E.EXT_OPT_P1_FLAT, E.EXT_P1_FLAT_FUSED)
+        extra["forms_ms"]["gather_fused"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split"], reps)["split"]
+        E.ext_set_option(E.EXT_OPT_P1_FLAT, old_flat)
         for kind in ("terrain", "wavy", "tilted"):
             Xk = geometry_coords(m, L, kind, dev)
             extra["forms_ms"][kind] = time_p1_forms(E, gm, cs, p1, Xk, x, y, stream, ["split"], reps)["split"]
@@ -581,6 +585,7 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                     "levels (no common profile; the cell loop) and with leaning columns (the cell loop), default "
                     "form",
             "gather": form_entry("gather", fm["split"], V, C, L, E_, "flat", ops_peak, hbm),
+            "gather_fused": form_entry("gather", fm["gather_fused"], V, C, L, E_, "flat", ops_peak, hbm),
             "factored_cell_pass": form_entry("factored", fm["factored"], V, C, L, E_, "flat", ops_peak, hbm),
             "cell_loop": form_entry("cells-forced", fm["cells"], V, C, L, E_, "flat", ops_peak, hbm),
             "terrain_gather": form_entry("gather-sigma", fm["terrain"], V, C, L, E_, "terrain", ops_peak, hbm),

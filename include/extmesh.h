@@ -434,7 +434,15 @@ ext_status ext_fp64_rates(double gops_host[4], void *stream);
  * (auto, split, gather, factored, unfactored, cells, single), read at the
  * first query.  ext_set_option returns EXT_EINVAL for an unknown option or
  * value; it affects launches issued after it returns. */
-typedef enum { EXT_OPT_P1_FORM = 1 } ext_option;
+typedef enum { EXT_OPT_P1_FORM = 1, EXT_OPT_P1_FLAT = 2 } ext_option;
+/* EXT_OPT_P1_FLAT: how the flat gather runs: EXT_P1_FLAT_SPLIT (default) the
+ * vertex pass w = Mv f stored, then b = Mh w; EXT_P1_FLAT_FUSED one pass,
+ * b_{a,m} = Mv applied to g = Mh f per level, lanes along a column's levels,
+ * straightness checked while walking the rows (no w round trip: DRAM traffic
+ * 1.07 x the algorithmic bytes instead of 1.33 x, but more FP64 work per DoF,
+ * so it is not faster on GB300).  Initial value from EXTMESH_P1_FLAT (split,
+ * fused). */
+typedef enum { EXT_P1_FLAT_FUSED = 0, EXT_P1_FLAT_SPLIT = 1 } ext_p1_flat;
 typedef enum {
   EXT_P1_AUTO = 0,
   EXT_P1_SPLIT = 1,

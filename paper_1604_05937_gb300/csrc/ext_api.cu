@@ -62,18 +62,41 @@ int p1_form() {
   return v;
 }
 
+static std::atomic<int> g_p1_flat{-1};
+
+int p1_flat() {
+  int v = g_p1_flat.load();
+  if (v < 0) {
+    const char *ev = getenv("EXTMESH_P1_FLAT");
+    int expect = -1;
+    g_p1_flat.compare_exchange_strong(expect, (ev && strcmp(ev, "fused") == 0) ? EXT_P1_FLAT_FUSED
+                                                                                : EXT_P1_FLAT_SPLIT);
+    v = g_p1_flat.load();
+  }
+  return v;
+}
+
 extern "C" ext_status ext_set_option(int32_t option, int32_t value) {
-  if (option != EXT_OPT_P1_FORM) return ext_fail(EXT_EINVAL, "ext_set_option: unknown option %d", option);
-  if (value < EXT_P1_AUTO || value > EXT_P1_SINGLE)
-    return ext_fail(EXT_EINVAL, "ext_set_option: EXT_OPT_P1_FORM value %d out of range", value);
-  g_p1_form.store(value);
-  return EXT_OK;
+  if (option == EXT_OPT_P1_FORM) {
+    if (value < EXT_P1_AUTO || value > EXT_P1_SINGLE)
+      return ext_fail(EXT_EINVAL, "ext_set_option: EXT_OPT_P1_FORM value %d out of range", value);
+    g_p1_form.store(value);
+    return EXT_OK;
+  }
+  if (option == EXT_OPT_P1_FLAT) {
+    if (value != EXT_P1_FLAT_FUSED && value != EXT_P1_FLAT_SPLIT)
+      return ext_fail(EXT_EINVAL, "ext_set_option: EXT_OPT_P1_FLAT value %d out of range", value);
+    g_p1_flat.store(value);
+    return EXT_OK;
+  }
+  return ext_fail(EXT_EINVAL, "ext_set_option: unknown option %d", option);
 }
 
 extern "C" ext_status ext_get_option(int32_t option, int32_t *value) {
   if (!value) return ext_fail(EXT_EINVAL, "ext_get_option: value is NULL");
-  if (option != EXT_OPT_P1_FORM) return ext_fail(EXT_EINVAL, "ext_get_option: unknown option %d", option);
-  *value = p1_form();
+  if (option == EXT_OPT_P1_FORM) *value = p1_form();
+  else if (option == EXT_OPT_P1_FLAT) *value = p1_flat();
+  else return ext_fail(EXT_EINVAL, "ext_get_option: unknown option %d", option);
   return EXT_OK;
 }
 
@@ -762,8 +785,10 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
     for (int i = 0; i < nargs && e == cudaSuccess; ++i)
       if (args[i].space && args[i].space->d_map && args[i].space->mesh == mesh)
         e = launch_check_map(args[i].space, mesh->d_cell_layers, L, w, s);
+    // the vertex rows address the CG1xCG1 space (an argument of another space
+    // is refused by the kernel's own validation below)
     if (e == cudaSuccess && (kernel_id == EXT_K_RHS_P1P1 || kernel_id == EXT_K_MASS_P1P1) && nargs > 1 &&
-        args[1].space)
+        args[1].space && args[1].space->mesh == mesh && args[1].space->elem == ELEM_P1P1 && args[1].space->ncomp == 1)
       e = launch_check_rows(mesh, args[1].space->ndofs, w, s);
     unsigned int v = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -208,8 +208,10 @@ struct MassP1Launch {
   int64_t nvent = 0;  // entries of the vertex rows
 };
 
-// Form of the P1xP1 launch (ext_set_option(EXT_OPT_P1_FORM, ...)).
+// Form of the P1xP1 launch (ext_set_option(EXT_OPT_P1_FORM, ...)) and of its
+// flat gather (EXT_OPT_P1_FLAT).
 int p1_form();
+int p1_flat();
 cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s);
 
 // Mass action on the nine prism tensor-product spaces (k_tp.cu).

@@ -34,6 +34,7 @@
 // evaluates the element integrals with the full 6-point rule and the general
 // Jacobian instead, so any coordinate field is handled.
 #include <cstdlib>
+#include <cstring>
 
 #include "ext_internal.cuh"
 #include "fastdiv.cuh"
@@ -1476,9 +1477,11 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
                                                                    const double *__restrict__ wts,
                                                                    double *__restrict__ b, int64_t n, FastDiv col,
                                                                    Deferred dfr, unsigned int *err, Fp64Ones k1,
-                                                                   const unsigned int *__restrict__ mode) {
+                                                                   const unsigned int *__restrict__ mode,
+                                                                   bool flat_fused) {
   constexpr int VU = EXT_VG_VU;
   const int lane = threadIdx.x & 31;
+  if (*mode == 0u && flat_fused) return;  // k_vfused formed b
   if (mode_cells(*mode)) {
     // cell-loop mode: k_p1_cells adds every contribution; WRITE clears b first
     if (!INC)
@@ -1539,6 +1542,88 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
         if (slot < dfr.cap) dfr.list[slot] = make_int2((int)(base + u * 32), (int)mask);
         else atomicOr(err, EXT_DERR_BOUNDS);
       }
+    }
+  }
+}
+
+// Flat gather in one pass (flat mode only): b = Mh (x) Mv f evaluated as
+// b_{a,m} = lo_m g_{a,m-1} + mid_m g_{a,m} + hi_m g_{a,m+1} with g_{a,m} =
+// sum over the vertex row of a of weight x f_{j,m}, so no vertical sums are
+// stored and read back.  A warp step covers 32 consecutive DoFs, d = start - 1
+// .. start + 30: every lane forms g of its own DoF (one DFMA per row entry),
+// and lanes 1..30 take their lower and upper neighbours' g by shuffles and
+// write b of DoFs start .. start + 29 (lanes 0 and 31 only supply the halo).
+// While it walks the row, each lane checks bitwise that every f_{j,m} it uses
+// sits on a straight flat DoF (x, y of column j's level 0, z of level m in
+// column 0); a DoF whose own check or a vertical neighbour's fails, or whose
+// sum comes out NaN, is recorded for k_vgather_general instead of written.
+template <bool INC>
+__global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vfused(const double *__restrict__ X,
+                                                                  const double *__restrict__ f,
+                                                                  const int32_t *__restrict__ vrow,
+                                                                  const int32_t *__restrict__ vnbr,
+                                                                  const double *__restrict__ wts,
+                                                                  const LevelCoef *__restrict__ tab,
+                                                                  double *__restrict__ b, int64_t n, FastDiv col,
+                                                                  Deferred dfr, unsigned int *err, Fp64Ones k1,
+                                                                  const unsigned int *__restrict__ mode) {
+  if (*mode != 0u) return;  // terrain-following or cell-loop mode
+  const int lane = threadIdx.x & 31;
+  constexpr int kOut = 30;
+  const int64_t nsteps = (n + kOut - 1) / kOut;
+  const int64_t wstride = (int64_t)gridDim.x * 8;
+  for (int64_t stp = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); stp < nsteps; stp += wstride) {
+    const int64_t start = stp * kOut;
+    const int64_t d = start - 1 + lane;
+    const bool in = d >= 0 && d < n;
+    int r0 = 0, deg = 0;
+    uint32_t m = 0;
+    double acc = k1.mzero, zl = 0.0;
+    double2 c01 = make_double2(0.0, 0.0), c23 = make_double2(0.0, 0.0);
+    if (in) {
+      const uint32_t q = fdiv((uint32_t)d, col);
+      m = (uint32_t)d - q * col.d;
+      r0 = __ldg(vrow + q);
+      deg = __ldg(vrow + q + 1) - r0;
+      c01 = __ldg(reinterpret_cast<const double2 *>(tab + m));      // z_m, |h_{m-1}|
+      c23 = __ldg(reinterpret_cast<const double2 *>(tab + m) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
+      zl = c01.x;
+    }
+    const long long zbits = __double_as_longlong(zl);
+    int ok = 1;
+    const int dmx = __reduce_max_sync(kFull, deg);
+#pragma unroll 4
+    for (int t = 0; t < dmx; ++t) {
+      double ev = 0.0, fv = 0.0;
+      if (t < deg) {
+        const int64_t j0 = __ldg(vnbr + r0 + t);  // first DoF of column j
+        const int64_t dj = j0 + m;
+        ev = __ldg(wts + r0 + t);
+        fv = __ldg(f + dj);
+        ok &= (__double_as_longlong(__ldg(X + 3 * dj + 0)) == __double_as_longlong(__ldg(X + 3 * j0 + 0))) &
+              (__double_as_longlong(__ldg(X + 3 * dj + 1)) == __double_as_longlong(__ldg(X + 3 * j0 + 1))) &
+              (__double_as_longlong(__ldg(X + 3 * dj + 2)) == zbits);
+      }
+      acc = fma(ev, fv, acc);
+    }
+    // vertical neighbours (lanes -1 and +1, the same column unless at its end)
+    const bool lo_end = m == 0, hi_end = m + 1 == col.d;
+    const double gl = __shfl_up_sync(kFull, acc, 1), gr = __shfl_down_sync(kFull, acc, 1);
+    const int okl = __shfl_up_sync(kFull, ok, 1), okr = __shfl_down_sync(kFull, ok, 1);
+    const double glm = __longlong_as_double(__double_as_longlong(gl) & (lo_end ? 0LL : -1LL));
+    const double grm = __longlong_as_double(__double_as_longlong(gr) & (hi_end ? 0LL : -1LL));
+    double res = fma(c01.y, glm, fma(c23.x, acc, fmul(c23.y, grm, k1)));
+    const bool out = lane >= 1 && lane <= kOut && in;
+    const int good = ok & (lo_end | okl) & (hi_end | okr);
+    if (INC && out) res = fadd(res, b[d], k1);
+    const bool nan = (__double_as_longlong(res) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    const bool bad = out && (!good || nan);
+    if (out && !bad) b[d] = res;
+    const unsigned int mask = __ballot_sync(kFull, bad) >> 1;  // bit i: DoF start + i
+    if (mask != 0u && lane == 0) {
+      const unsigned int slot = atomicAdd(dfr.count, 1u);
+      if (slot < dfr.cap) dfr.list[slot] = make_int2((int)start, (int)mask);
+      else atomicOr(err, EXT_DERR_BOUNDS);
     }
   }
 }
@@ -1739,7 +1824,7 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   char *scr = nullptr;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nn = (size_t)(n > 0 ? n : 1);
-  const int64_t cap64 = gather ? (n + 31) / 32 + 1
+  const int64_t cap64 = gather ? (n + 29) / 30 + 2
                                : (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = cells ? 0 : al(sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)));
@@ -1839,23 +1924,36 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
     k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vnbr, p.vedge, p.vcrow, p.vcells, alpha,
                                                                  sc.Dv, Sc, wts, (int32_t)nv, col, mode);
+    const bool fused = p1_flat() == EXT_P1_FLAT_FUSED;
+    if (fused) {
+      static int res_vf[2] = {0, 0};
+      const int rf = p.overwrite ? resident_ctas(k_vfused<false>, res_vf[0]) : resident_ctas(k_vfused<true>, res_vf[1]);
+      int64_t gf = ((n + 29) / 30 + 7) / 8;
+      if (gf > (int64_t)rf * sms) gf = (int64_t)rf * sms;
+      if (gf < 1) gf = 1;
+      if (p.overwrite)
+        k_vfused<false><<<(unsigned)gf, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, n, col, dfr, p.err, k1, mode);
+      else
+        k_vfused<true><<<(unsigned)gf, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, n, col, dfr, p.err, k1, mode);
+    }
     if (EXT_VSUM_BULK) {
       const int rb = resident_ctas(k_vsum_bulk<false>, res_vb);
       int64_t gb = ((n + kBulkDofs - 1) / kBulkDofs + 7) / 8;  // CTAs of 8 warps, one warp step each
       if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
       if (gb < 1) gb = 1;
-      k_vsum_bulk<false><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
+      if (!fused)
+        k_vsum_bulk<false><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
       k_vsum_bulk<true><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
     } else {
-      k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
+      if (!fused) k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
       k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
     }
     if (p.overwrite) {
-      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode);
+      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode, fused);
       const int r = resident_ctas(k_vgather_general<false>, res_vgg[0]);
       k_vgather_general<false><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
     } else {
-      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode);
+      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode, fused);
       const int r = resident_ctas(k_vgather_general<true>, res_vgg[1]);
       k_vgather_general<true><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
     }

@@ -62,7 +62,8 @@ print("RECOVERED", ok)
 @pytest.mark.parametrize("step", [0, 5])
 def test_bulk_wait_runs_out_and_library_recovers(step):
     import paper_1604_05937_gb300 as E
-    env = dict(os.environ, EXTMESH_TEST_BULK_SKIP=str(step))
+    # the two-pass flat gather runs the bulk-copy vertex pass
+    env = dict(os.environ, EXTMESH_TEST_BULK_SKIP=str(step), EXTMESH_P1_FLAT="split")
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     assert f"STATUS {E.EXT_ETIMEOUT}" in r.stdout, r.stdout

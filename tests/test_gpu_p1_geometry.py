@@ -39,11 +39,16 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.fixture(autouse=True)
-def _restore_form():
+@pytest.fixture(autouse=True, params=["fused", "split"])
+def flat(request):
+    """Every test runs with the flat gather in one pass and as vertex pass +
+    gather (EXT_OPT_P1_FLAT)."""
     old = E.ext_get_option(E.EXT_OPT_P1_FORM)
-    yield
+    oldf = E.ext_get_option(E.EXT_OPT_P1_FLAT)
+    E.ext_set_option(E.EXT_OPT_P1_FLAT, E.EXT_P1_FLAT_FUSED if request.param == "fused" else E.EXT_P1_FLAT_SPLIT)
+    yield request.param
     E.ext_set_option(E.EXT_OPT_P1_FORM, old)
+    E.ext_set_option(E.EXT_OPT_P1_FLAT, oldf)
 
 
 _cache = {}

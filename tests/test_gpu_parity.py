@@ -246,12 +246,14 @@ def test_mass_general_geometry_partial(layers, with_xy):
     close(host(b), ref, absr)
 
 
-@pytest.mark.parametrize("form", [{"EXTMESH_P1_FORM": "split"}, {"EXTMESH_P1_FORM": "single"},
+@pytest.mark.parametrize("form", [{"EXTMESH_P1_FORM": "split"}, {"EXTMESH_P1_FORM": "split", "EXTMESH_P1_FLAT": "fused"},
+                                  {"EXTMESH_P1_FORM": "single"},
                                   {"EXTMESH_P1_FORM": "gather"}, {"EXTMESH_P1_FORM": "unfactored"},
                                   {"EXTMESH_P1_FORM": "factored"}, {"EXTMESH_P1_FORM": "cells"},
                                   {"EXTMESH_TP_FLAGS": "1"}, {"EXTMESH_TP_FLAGS": "1", "EXTMESH_TP_LEVELS": "1"},
                                   {"EXTMESH_TP_FLAGS": "0", "EXTMESH_TP_LEVELS": "1"}],
-                         ids=["split", "single", "gather", "split-unfactored", "split-factored", "cells", "tp-flags",
+                         ids=["split", "split-flat-fused", "single", "gather", "split-unfactored", "split-factored",
+                              "cells", "tp-flags",
                               "tp-levels-flags", "tp-levels"])
 def test_mass_forced_form(form):
     """Every form of the P1xP1 launch passes the same parity tests, each
