@@ -1090,8 +1090,9 @@ __global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict_
 }
 
 // Row weights (gather modes only).  Flat extrusion, Mh: entry (a, j) = the
-// sum of alpha over the one or two cells on edge (a, j), ascending; the
-// diagonal is the sum of the row's neighbour weights in row order.
+// sum of alpha over the one or two cells on edge (a, j), ascending (one
+// thread per entry); the diagonal is the sum of 2 alpha over the cells
+// around a (one thread per vertex).
 // Terrain-following levels, Hd: a prism's heights are h_k = (sigma_{l+1} -
 // sigma_l) D_k, so its element matrix under the 6-point rule is the column
 // factor times (alpha_c / 54) sum_k D_k T_{aa'k}, with T = 54 sum_t lambda_a
@@ -1105,39 +1106,46 @@ __global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict
                                                        const int32_t *__restrict__ vcells,
                                                        const double *__restrict__ alpha, const double *__restrict__ Dv,
                                                        const double *__restrict__ S, double *__restrict__ wts,
-                                                       int32_t nv, FastDiv col, const unsigned int *__restrict__ mode) {
+                                                       int32_t nv, int64_t nent, FastDiv col,
+                                                       const unsigned int *__restrict__ mode) {
   const unsigned md = *mode;
   if (mode_cells(md)) return;
   const bool sig = (md & kNotFlat) != 0u;
-  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nv; a += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
-    double diag = 0.0;
-    if (!sig) {
-#pragma unroll 4
-      for (int32_t t = t0 + 1; t < t1; ++t) {
-        const int2 e = __ldg(vedge + t);
-        const double w = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
-        wts[t] = w;
-        diag += w;
-      }
+  // one thread per row entry (off-diagonal weights) and one per vertex (the
+  // diagonal), all independent
+  const int64_t total = nent + nv;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nent) {
+      // flat: an off-diagonal entry on its own (terrain-following: the vertex
+      // thread forms its row, which needs the row's D_a)
+      if (sig) continue;
+      const int2 e = __ldg(vedge + i);
+      if (e.x < 0) continue;  // a diagonal entry
+      wts[i] = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
     } else {
-      const double Da = __ldg(Dv + a);
-#pragma unroll 4
-      for (int32_t t = t0 + 1; t < t1; ++t) {
-        const int2 e = __ldg(vedge + t);
-        const double Dj = __ldg(Dv + fdiv((uint32_t)__ldg(vnbr + t), col));
-        const double dd = 9.0 * (Da + Dj);
-        double w = __ldg(alpha + e.x) * fma(12.0, __ldg(S + e.x), dd);
-        if (e.y >= 0) w = fma(__ldg(alpha + e.y), fma(12.0, __ldg(S + e.y), dd), w);
-        wts[t] = w * (1.0 / 54.0);
+      const int64_t a = i - nent;
+      const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
+      double diag = 0.0;
+      if (!sig) {
+        for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) diag += 2.0 * __ldg(alpha + __ldg(vcells + t));
+      } else {
+        const double Da = __ldg(Dv + a);
+        for (int32_t t = t0 + 1; t < t1; ++t) {
+          const int2 e = __ldg(vedge + t);
+          const double Dj = __ldg(Dv + fdiv((uint32_t)__ldg(vnbr + t), col));
+          const double dd = 9.0 * (Da + Dj);
+          double w = __ldg(alpha + e.x) * fma(12.0, __ldg(S + e.x), dd);
+          if (e.y >= 0) w = fma(__ldg(alpha + e.y), fma(12.0, __ldg(S + e.y), dd), w);
+          wts[t] = w * (1.0 / 54.0);
+        }
+        for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) {
+          const int32_t c = __ldg(vcells + t);
+          diag = fma(__ldg(alpha + c), fma(21.0, __ldg(S + c), 45.0 * Da), diag);
+        }
+        diag *= 1.0 / 54.0;
       }
-      for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) {
-        const int32_t c = __ldg(vcells + t);
-        diag = fma(__ldg(alpha + c), fma(21.0, __ldg(S + c), 45.0 * Da), diag);
-      }
-      diag *= 1.0 / 54.0;
+      wts[t0] = diag;
     }
-    wts[t0] = diag;
   }
 }
 
@@ -1920,10 +1928,10 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
                                                                  const_cast<double *>(sc.Dv),
                                                                  const_cast<double *>(sc.Z0),
                                                                  const_cast<double *>(sc.Bv), Sc);
-    int64_t gw = (nv + 255) / 256;
-    if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
+    int64_t gw = (nv + p.nvent + 255) / 256;
+    if (gw > (int64_t)sms * 16) gw = (int64_t)sms * 16;
     k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vnbr, p.vedge, p.vcrow, p.vcells, alpha,
-                                                                 sc.Dv, Sc, wts, (int32_t)nv, col, mode);
+                                                                 sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode);
     const bool fused = p1_flat() == EXT_P1_FLAT_FUSED;
     if (fused) {
       static int res_vf[2] = {0, 0};
