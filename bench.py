@@ -631,15 +631,21 @@ CPU_SAMPLE_COLUMNS = 2048  # base columns of the CPU sample (all layers, all thr
 
 
 def host_cpu() -> str:
-    """Host CPU model as the kernel reports it."""
+    """Host CPU model: /proc/cpuinfo's model name, else lscpu's (Arm kernels
+    list only part numbers in /proc/cpuinfo)."""
     try:
         with open("/proc/cpuinfo") as f:
-            txt = f.read()
-        for key in ("model name", "Model", "Hardware", "CPU part"):
-            for line in txt.splitlines():
-                if line.lower().startswith(key.lower()) and ":" in line:
+            for line in f:
+                if line.lower().startswith("model name") and ":" in line:
                     return line.split(":", 1)[1].strip()
     except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name") and ":" in line:
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
         pass
     import platform
     return platform.processor() or platform.machine()

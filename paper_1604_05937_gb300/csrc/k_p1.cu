@@ -1038,7 +1038,10 @@ __global__ void __launch_bounds__(256) k_p1_prep(const double *__restrict__ X, i
     const bool vert = (__double_as_longlong(__ldg(X + 3 * d + 0)) == __double_as_longlong(__ldg(X + 3 * d0 + 0))) &
                       (__double_as_longlong(__ldg(X + 3 * d + 1)) == __double_as_longlong(__ldg(X + 3 * d0 + 1)));
     const double z = __ldg(X + 3 * d + 2);
-    if (!vert || __double_as_longlong(z) != __double_as_longlong(__ldg(&tab[m].z))) bad |= kNotFlat;
+    if (vert && __double_as_longlong(z) == __double_as_longlong(__ldg(&tab[m].z))) continue;
+    // not flat; a flat DoF also fits the terrain-following model (its column
+    // has column 0's z_0 and D), so only the others need that test
+    bad |= kNotFlat;
     const double z0 = __ldg(X + 3 * d0 + 2), D = __ldg(X + 3 * (d0 + layers) + 2) - z0;
     const LevelCoef ts = tab[col + m];
     const double gap = m == 0 ? ts.hi : (m == layers ? ts.lo : fmin(ts.lo, ts.hi));
