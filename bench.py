@@ -77,7 +77,8 @@ P1_KERNELS = {"gather": 9, "gather-sigma": 9, "cells": 9, "cells-forced": 1, "fa
               "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 P1_SPLIT_MIN_ITEMS = 1_000_000
-P1_FACTORED_MIN_LAYERS = 2
+P1_FACTORED_MIN_LAYERS = 3
+P1_GATHER_MIN_LAYERS = 32
 
 
 def p1_form(items: int, layers: int, var: bool = False, geometry: str = "flat") -> str:
@@ -89,6 +90,8 @@ def p1_form(items: int, layers: int, var: bool = False, geometry: str = "flat") 
         return "single"
     if var:
         return "var"
+    if layers < P1_GATHER_MIN_LAYERS:
+        return "factored" if layers >= P1_FACTORED_MIN_LAYERS else "plain"
     return {"flat": "gather", "terrain": "gather-sigma"}.get(geometry, "cells")
 
 

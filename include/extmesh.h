@@ -80,10 +80,12 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  * EXT_K_MASS_P1P1   same arguments and operator: y += M x (mass-matrix action).
  *                   Forms (ext_set_option(EXT_OPT_P1_FORM); the default picks
  *                   by size and geometry; all agree within rounding):
- *                   - gather form (constant layers on a triangle mesh; chosen
- *                     when a probe of the coordinates of about 4,096 sampled
- *                     vertex columns, every level, finds a straight extrusion
- *                     with flat levels): per launch, a table of the level
+ *                   - gather form (constant layers on a triangle mesh, from
+ *                     32 layers; chosen when a probe of the coordinates of
+ *                     about 4,096 sampled vertex columns, every level, finds a
+ *                     straight extrusion with flat levels, or, with a
+ *                     depth-weighted base matrix, terrain-following levels
+ *                     z = z0 + sigma_l D(x, y)): per launch, a table of the level
  *                     heights (column of vertex 0), the area of every
  *                     level-0 triangle and from them the weights of the base
  *                     triangulation's P1 mass matrix Mh on the mesh's vertex
@@ -100,7 +102,8 @@ typedef enum { EXT_READ = 0, EXT_WRITE = 1, EXT_INC = 2 } ext_access;
  *                     per prism with the 6-point rule (a closed form of the
  *                     rule for prisms with vertical edges, the general
  *                     Jacobian otherwise), FP64 atomic adds;
- *                   - factored / unfactored cell pass over vertical sums
+ *                   - factored / unfactored cell pass over vertical sums (the
+ *                     default below 32 layers: from 3 / at 1 or 2 layers)
  *                     (vertex area sums, vertical sums per vertex level, the
  *                     cell pass with FP64 atomic adds, and a pass over the
  *                     warp steps that met a prism which is not straight);

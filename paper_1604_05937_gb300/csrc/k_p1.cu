@@ -55,7 +55,10 @@ constexpr unsigned kFull = 0xffffffffu;
 #define EXT_CELLS_VAR_MINB 4  // the same with variable layers
 #endif
 #ifndef EXT_FACTORED_MIN_LAYERS
-#define EXT_FACTORED_MIN_LAYERS 2  // constant layers: the factored split form from this many layers
+#define EXT_FACTORED_MIN_LAYERS 3  // constant layers: the factored split form from this many layers
+#endif
+#ifndef EXT_GATHER_MIN_LAYERS
+#define EXT_GATHER_MIN_LAYERS 32  // constant layers: the probe and the gather forms from this many layers
 #endif
 #ifndef EXT_MASS_ITEMS
 #define EXT_MASS_ITEMS 1616  // target items (column levels) per column group
@@ -1780,12 +1783,12 @@ int resident_ctas(K kernel, int &cache) {
 // Forms of the launch (ext_set_option(EXT_OPT_P1_FORM, ...)):
 //   EXT_P1_AUTO   under a million (column, level) items the single-pass
 //                 kernel; otherwise as EXT_P1_SPLIT;
-//   EXT_P1_SPLIT  constant layers on a mesh with vertex rows: the probe
-//                 decides between the gather form (a flat, straight
-//                 extrusion) and the cell loop (any other coordinate field);
-//                 variable layers: the variable-layer split form; no vertex
-//                 rows: the factored form from EXT_FACTORED_MIN_LAYERS layers,
-//                 else the unfactored one;
+//   EXT_P1_SPLIT  constant layers on a mesh with vertex rows, from
+//                 EXT_GATHER_MIN_LAYERS layers: the probe decides between the
+//                 flat gather, the terrain-following gather and the cell
+//                 loop; fewer layers, or no vertex rows: the factored form
+//                 from EXT_FACTORED_MIN_LAYERS layers, else the unfactored
+//                 one; variable layers: the variable-layer split form;
 //   EXT_P1_GATHER the gather form without the probe (DoFs next to a prism
 //                 that is not straight are recomputed one by one);
 //   EXT_P1_FACTORED / EXT_P1_UNFACTORED  the split form with / without the
@@ -1818,6 +1821,13 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   // launches (about 25 us together) cost more than they save
   if (form == EXT_P1_AUTO) form = items < 1.0e6 ? EXT_P1_SINGLE : EXT_P1_SPLIT;
   const bool rows = !var && p.vrow && p.vnbr && p.vedge && p.vcrow && p.vcells && p.nvent > 0;
+  // below EXT_GATHER_MIN_LAYERS layers the per-launch geometry of the gather
+  // forms (areas, one weight per vertex-row entry) costs about as much as the
+  // vertical work it serves; the cell pass over vertical sums is faster there
+  // on a well-ordered base (15M cells, RCM: 0.85 against 1.08 ms at one layer,
+  // 0.25 against 0.27 ms at 20)
+  if (!var && form == EXT_P1_SPLIT && p.layers < EXT_GATHER_MIN_LAYERS)
+    form = p.layers >= EXT_FACTORED_MIN_LAYERS ? EXT_P1_FACTORED : EXT_P1_UNFACTORED;
   if (!var && !rows && (form == EXT_P1_GATHER || form == EXT_P1_SPLIT))
     form = p.layers >= EXT_FACTORED_MIN_LAYERS ? EXT_P1_FACTORED : EXT_P1_UNFACTORED;
   const bool gather = !var && (form == EXT_P1_SPLIT || form == EXT_P1_GATHER);

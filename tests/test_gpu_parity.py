@@ -292,44 +292,49 @@ def test_mass_gather_form_deterministic(layers):
     oracle; and a NaN in f reaches exactly the DoFs whose stencil holds it
     (they are recomputed by the general path, which yields NaN as well),
     leaving every other DoF equal to the oracle's."""
-    n = {1: 710, 2: 420, 100: 72}[layers]  # over a million (column, level) items: the split form runs
+    n = {1: 710, 2: 420, 100: 72}[layers]  # over a million (column, level) items
     m = meshgen.tri_mesh(n, seed=320 + layers, order="rcm")
-    gm, csp, X = mesh_pair(m, layers)
-    osp = O.number(m.cells, m.nverts, layers, P1)
-    f = meshgen.uniform_field(osp.ndofs, 321)
-    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
-    O.par_loop(O.K_MASS, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
-    cs = E.Space(gm, "CG1xCG1", ncomp=3)
-    ps = E.Space(gm, "CG1xCG1")
-    Xd, fd = to_dev(X), to_dev(f)
-    outs = []
-    for _ in range(2):
-        b = torch.full((ps.ndofs,), float("nan"), dtype=torch.float64, device=dev)
-        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, fd, E.EXT_READ), (ps, b, E.EXT_WRITE))
+    old_form = E.ext_get_option(E.EXT_OPT_P1_FORM)
+    E.ext_set_option(E.EXT_OPT_P1_FORM, E.EXT_P1_SPLIT if layers >= 32 else E.EXT_P1_GATHER)
+    try:
+        gm, csp, X = mesh_pair(m, layers)
+        osp = O.number(m.cells, m.nverts, layers, P1)
+        f = meshgen.uniform_field(osp.ndofs, 321)
+        ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+        O.par_loop(O.K_MASS, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+        cs = E.Space(gm, "CG1xCG1", ncomp=3)
+        ps = E.Space(gm, "CG1xCG1")
+        Xd, fd = to_dev(X), to_dev(f)
+        outs = []
+        for _ in range(2):
+            b = torch.full((ps.ndofs,), float("nan"), dtype=torch.float64, device=dev)
+            E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, fd, E.EXT_READ), (ps, b, E.EXT_WRITE))
+            E.ext_sync_check()
+            outs.append(host(b))
+        assert np.array_equal(outs[0].view(np.int64), outs[1].view(np.int64))
+        close(outs[0], ref, absr)
+        b = to_dev(np.full(osp.ndofs, 0.25))
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, fd, E.EXT_READ), (ps, b, E.EXT_INC))
         E.ext_sync_check()
-        outs.append(host(b))
-    assert np.array_equal(outs[0].view(np.int64), outs[1].view(np.int64))
-    close(outs[0], ref, absr)
-    b = to_dev(np.full(osp.ndofs, 0.25))
-    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, fd, E.EXT_READ), (ps, b, E.EXT_INC))
-    E.ext_sync_check()
-    close(host(b), ref + 0.25, absr + 0.25)
-    # one NaN in f at vertex v0, level 0: the DoFs of v0 and its neighbours at
-    # levels 0 and 1 become NaN, all others keep the oracle's value
-    L1 = layers + 1
-    v0 = m.nverts // 2
-    fn = f.copy()
-    fn[v0 * L1] = np.nan
-    b = ps.zeros()
-    E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, to_dev(fn), E.EXT_READ), (ps, b, E.EXT_WRITE))
-    E.ext_sync_check()
-    got = host(b)
-    nb = np.unique(m.cells[np.any(m.cells == v0, axis=1)].reshape(-1))
-    hit = np.zeros(osp.ndofs, dtype=bool)
-    for v in nb:
-        hit[v * L1:v * L1 + 2] = True
-    assert np.isnan(got[hit]).all()
-    close(got[~hit], ref[~hit], absr[~hit])
+        close(host(b), ref + 0.25, absr + 0.25)
+        # one NaN in f at vertex v0, level 0: the DoFs of v0 and its neighbours at
+        # levels 0 and 1 become NaN, all others keep the oracle's value
+        L1 = layers + 1
+        v0 = m.nverts // 2
+        fn = f.copy()
+        fn[v0 * L1] = np.nan
+        b = ps.zeros()
+        E.par_loop(gm, E.EXT_K_MASS_P1P1, (cs, Xd, E.EXT_READ), (ps, to_dev(fn), E.EXT_READ), (ps, b, E.EXT_WRITE))
+        E.ext_sync_check()
+        got = host(b)
+        nb = np.unique(m.cells[np.any(m.cells == v0, axis=1)].reshape(-1))
+        hit = np.zeros(osp.ndofs, dtype=bool)
+        for v in nb:
+            hit[v * L1:v * L1 + 2] = True
+        assert np.isnan(got[hit]).all()
+        close(got[~hit], ref[~hit], absr[~hit])
+    finally:
+        E.ext_set_option(E.EXT_OPT_P1_FORM, old_form)
 
 
 def test_mass_volume_pin_on_gpu():
