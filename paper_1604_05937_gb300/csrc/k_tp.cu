@@ -32,6 +32,7 @@ struct TPCol {
   int32_t cm[6];             // the column's coordinate stencil row (layer 0)
   int32_t fm[6];             // its f/b DoFs of node (a, b) at layer 0
   int lay;                   // layers of this column
+  int allok;                 // flagged form: every level of the three vertex columns is straight
 };
 
 // element vector of a general prism: out[a*NV+b] = sum_q w_q |detJ| f(x_q) H_a V_b
@@ -141,6 +142,18 @@ __device__ __forceinline__ int vflag(const uint32_t *__restrict__ flags, int64_t
   return (int)((__ldg(flags + (d >> 5)) >> (uint32_t)(d & 31)) & 1u);
 }
 
+// bits lo .. lo + n - 1 of the flags all set (a whole vertex column straight)
+__device__ __forceinline__ int vflags_all(const uint32_t *__restrict__ flags, int64_t lo, int64_t n) {
+  const int64_t hi = lo + n;
+  for (int64_t w = lo >> 5; w <= (hi - 1) >> 5; ++w) {
+    uint32_t need = 0xffffffffu;
+    if (w == (lo >> 5)) need &= 0xffffffffu << (uint32_t)(lo & 31);
+    if (w == ((hi - 1) >> 5)) need &= 0xffffffffu >> (uint32_t)(31 - ((hi - 1) & 31));
+    if ((__ldg(flags + w) & need) != need) return 0;
+  }
+  return 1;
+}
+
 // VAR: column c has cell_layers[c] layers (lists taken at its bottom layer).
 // FLAGS: the flagged form (constant layers only); MULTI (with FLAGS): several
 // items per lane per step, a separate instantiation so that its registers do
@@ -184,6 +197,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
       }
       const double det2 = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
       cols[warp][lane].alpha = fabs(det2) * p.scale;
+      // flagged form: a column whose three vertex columns are straight at
+      // every level needs no per-item flag test (Algorithm 3's outer loop
+      // does the test once per column)
+      int allok = 0;
+      if (FLAGS)
+        allok = vflags_all(p.vflags, cols[warp][lane].cm[0], layers + 1) &
+                vflags_all(p.vflags, cols[warp][lane].cm[2], layers + 1) &
+                vflags_all(p.vflags, cols[warp][lane].cm[4], layers + 1);
+      cols[warp][lane].allok = allok;
     }
     __syncwarp();
     const int nitems = VAR ? __reduce_add_sync(0xffffffffu, my_items) : ncol * layers;
@@ -214,8 +236,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
           hl[u] = 0.0;
           if (valid[u]) {
             const TPCol &ci = cols[warp][cl];
+            if (!ci.allok) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+              for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+            }
             hl[u] = __ldg(p.hlay + l);
 #pragma unroll
             for (int i = 0; i < NH * NV; ++i) {
@@ -269,8 +293,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p
           }
         };
         if (FLAGS) {
+          if (!ci.allok) {
 #pragma unroll
-          for (int i = 0; i < 6; ++i) ok &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+            for (int i = 0; i < 6; ++i) ok &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
+          }
         } else {
           load_coords();
 #pragma unroll
