@@ -161,7 +161,10 @@ __device__ __forceinline__ int vflags_all(const uint32_t *__restrict__ flags, in
 // WR: each DoF belongs to one cell-layer (DG x DG) and b is overwritten:
 // plain stores instead of atomic adds.
 template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = false>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp(const MassTPLaunch p, int cpw) {
+#ifndef EXT_TP_SMALL_MINB
+#define EXT_TP_SMALL_MINB 3  // resident CTAs per SM for one-node elements (DG0xDG0: registers for occupancy)
+#endif
+__global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB : 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int layers = p.layers;
