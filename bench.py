@@ -62,7 +62,9 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 #   gather   3 per DoF (column mass matrix Mv) + 1 per vertex-row entry and
 #            level (V + 2E entries: base mass matrix Mh) + the per-launch
 #            geometry (7 per cell for the level-0 areas, 4 per edge for the
-#            row weights); no atomics;
+#            row weights); no atomics (the optimistic one-pass form issues the
+#            Mh and Mv work of 32 DoFs for every 30 it writes: the two halo
+#            lanes of each window are not counted);
 #   gather-sigma (terrain-following levels) the same + 2 per DoF (the check
 #            against the terrain-following model) + 14 per edge, 11 per cell
 #            and 5 per vertex for the depth-weighted rows;
@@ -73,8 +75,10 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 #            3 L2 atomic adds per item;
 #   single   13 per item (below a million items).
 P1_PRISM_OPS = {"vertical": 42, "general": 132}
-P1_KERNELS = {"gather": 9, "gather-sigma": 9, "cells": 9, "cells-forced": 1, "factored": 4, "plain": 3, "var": 3,
-              "single": 1}
+# kernels of one launch (WRITE access: the flat gather runs optimistic, one
+# pass and a fix-up launch; the split and one-pass-checked flat forms launch 9)
+P1_KERNELS = {"gather": 10, "gather-split": 9, "gather-sigma": 10, "cells": 10, "cells-forced": 1, "factored": 4,
+              "plain": 3, "var": 3, "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 P1_SPLIT_MIN_ITEMS = 1_000_000
 P1_FACTORED_MIN_LAYERS = 3
@@ -140,13 +144,19 @@ P1_OPS_NOTE = ("default form from a million (column, level) items: gather on a f
                "(42 per prism with vertical edges + 3 per item); single pass below: 13 per item")
 
 
-def tp_kernels(items: int) -> int:
+def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False) -> int:
     """Kernels of one EXT_K_MASS_TP launch on constant layers over a mesh with
     base coordinates: the level table, the straightness flags and the cell
     kernel from a million (column, layer) items (EXTMESH_TP_FLAGS=1 / 0: at any
-    size / never), the cell kernel alone otherwise."""
+    size / never), the cell kernel alone otherwise; with WRITE on a DG x DG
+    space from 8 to 2048 layers the optimistic form (flags and element vectors
+    in one launch, then the fix-up launch)."""
     env = os.environ.get("EXTMESH_TP_FLAGS", "")
-    return 3 if env == "1" or (env != "0" and items >= 1_000_000) else 1
+    flagged = env == "1" or (env != "0" and items >= 1_000_000)
+    dgdg = name[:2] == "DG" and name[4:6] == "DG"
+    if flagged and write and dgdg and 8 <= layers <= 2048 and os.environ.get("EXTMESH_TP_OPTIMISTIC", "") != "0":
+        return 2
+    return 3 if flagged else 1
 
 
 def base_edges(cells) -> int:
@@ -157,8 +167,13 @@ def base_edges(cells) -> int:
     return int(np.unique(e[:, 0] * (int(c.max()) + 1) + e[:, 1]).size) if c.size else 0
 
 
-def p1_kernels(items: int, layers: int, var: bool = False, geometry: str = "flat") -> int:
-    return P1_KERNELS[p1_form(items, layers, var, geometry)]
+def p1_kernels(items: int, layers: int, var: bool = False, geometry: str = "flat", write: bool = True) -> int:
+    """Kernels of one launch in the default form (INC access: the gather
+    forms launch the split flat pass instead of the optimistic pair)."""
+    form = p1_form(items, layers, var, geometry)
+    if not write and form in ("gather", "gather-sigma", "cells"):
+        return P1_KERNELS["gather-split"]
+    return P1_KERNELS[form]
 
 
 def peaks():
@@ -405,6 +420,8 @@ def run_ours(args, rank, world, local):
         old_flat = E.ext_get_option(E.EXT_OPT_P1_FLAT)
         E.ext_set_option(E.EXT_OPT_P1_FLAT, E.EXT_P1_FLAT_FUSED)
         extra["forms_ms"]["gather_fused"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split"], reps)["split"]
+        E.ext_set_option(E.EXT_OPT_P1_FLAT, E.EXT_P1_FLAT_SPLIT)
+        extra["forms_ms"]["gather_split"] = time_p1_forms(E, gm, cs, p1, X, x, y, stream, ["split"], reps)["split"]
         E.ext_set_option(E.EXT_OPT_P1_FLAT, old_flat)
         for kind in ("terrain", "wavy", "tilted"):
             Xk = geometry_coords(m, L, kind, dev)
@@ -517,8 +534,10 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
     if form in ("gather", "gather-sigma"):
         if form == "gather":
             label = ("gather (flat-level special case): the probe found a straight extrusion with flat levels, so "
-                     "M = Mh (x) Mv; Mv applied per vertex level, Mh per level through the vertex rows, whose "
-                     "weights and the level table are computed from the coordinate field in every launch")
+                     "M = Mh (x) Mv, formed in one optimistic pass (g = Mh f per level through the vertex rows, then "
+                     "Mv by warp shuffles along each column) beside one straightness bit per coordinate DoF, and a "
+                     "fix-up launch that sends the DoFs next to a DoF that is not straight to the general rule; "
+                     "the row weights and the level table are computed from the coordinate field in every launch")
             algorithmic = (f"3 FP64 ops per DoF x {V * (L + 1)} DoFs + 1 per vertex-row entry and level x "
                            f"{V + 2 * E_} entries x {L + 1} levels + 7 per cell x {C} + 4 per edge x {E_} = "
                            f"{main['fp64_ops']} per launch")
@@ -530,8 +549,8 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                            f"entry and level x {V + 2 * E_} x {L + 1} + 18 per cell + 14 per edge + 5 per vertex = "
                            f"{main['fp64_ops']} per launch")
         kname = ("P1xP1 RHS / mass-action launch (k_p1_levels + k_p1_prep + k_p1_sigma_prep + k_p1_rowweights + "
-                 "k_vsum_bulk<flat> + k_vsum_bulk<terrain> + k_vgather + k_vgather_general + k_p1_cells; the kernels "
-                 "of the other modes exit at once)")
+                 "k_p1_opt + k_p1_fix + k_vsum_bulk<terrain> + k_vgather + k_vgather_general + k_p1_cells; the "
+                 "kernels of the other modes exit at once)")
     else:
         per = P1_PRISM_OPS["general" if geometry == "tilted" else "vertical"]
         label = (f"cell loop (Algorithm 3 over cells, one element vector per prism, {geometry} geometry): the probe "
@@ -588,7 +607,10 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                     "levels (no common profile; the cell loop) and with leaning columns (the cell loop), default "
                     "form",
             "gather": form_entry("gather", fm["split"], V, C, L, E_, "flat", ops_peak, hbm),
-            "gather_fused": form_entry("gather", fm["gather_fused"], V, C, L, E_, "flat", ops_peak, hbm),
+            "gather_split": form_entry("gather", fm["gather_split"], V, C, L, E_, "flat", ops_peak, hbm,
+                                       launches=P1_KERNELS["gather-split"]),
+            "gather_fused": form_entry("gather", fm["gather_fused"], V, C, L, E_, "flat", ops_peak, hbm,
+                                       launches=P1_KERNELS["gather-split"]),
             "factored_cell_pass": form_entry("factored", fm["factored"], V, C, L, E_, "flat", ops_peak, hbm),
             "cell_loop": form_entry("cells-forced", fm["cells"], V, C, L, E_, "flat", ops_peak, hbm),
             "terrain_gather": form_entry("gather-sigma", fm["terrain"], V, C, L, E_, "terrain", ops_peak, hbm),
@@ -804,7 +826,7 @@ def run_cfg3(args, rank, world, local):
             t_rhs = time_kernel(rhs, reps, stream, flush, pre=b.zero_)
             t_c0 = time_kernel(c0, reps, stream, flush)
             t_c1 = time_kernel(c1, reps, stream, flush)
-            launches += (p1_kernels(C * (L + 1), L) + 2) * (reps + args.warmup)
+            launches += (p1_kernels(C * (L + 1), L, write=False) + 2) * (reps + args.warmup)
             nP1 = V * (L + 1)
             vb_rhs = 40 * nP1 + 48 * C
             vb_c0 = 16 * C * L + 4 * C
@@ -1051,7 +1073,8 @@ def run_cfg6(args, rank, world, local):
                 fn()
                 reps = max(3, min(args.steps, 10))
                 t = time_kernel(fn, reps, stream, flush)[0]
-                launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None else tp_kernels(C * L))
+                launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None
+                                          else tp_kernels(C * L, L, name, write=True))
                 work = p1_ops(V * (L + 1), C * (L + 1), C, L) if ops is None else ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
                 vb = vb_paper + 24 * C + 4 * sp.k * C
@@ -1165,7 +1188,7 @@ def run_cfg7(args, rank, world, local):
         row = {}
         t = timed(lambda: E.ext_par_loop(gm.handle, E.EXT_K_MASS_P1P1, [(cs.handle, X, R), (p1.handle, x, R),
                                                                          (p1.handle, b, I)], s), pre=b.zero_,
-                  kernels=p1_kernels(items, gm.layers, gm.variable))
+                  kernels=p1_kernels(items, gm.layers, gm.variable, write=False))
         vb = 24 * nP1 + 16 * nP1 + 48 * C
         row["mass_p1p1"] = {"ms": round(t, 4), "gbs": round(vb / t / 1e6, 1),
                             "fp64_gops": round(p1_ops(nP1, items, C, gm.layers, gm.variable) / t / 1e6, 1),

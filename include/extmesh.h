@@ -438,14 +438,19 @@ ext_status ext_fp64_rates(double gops_host[4], void *stream);
  * first query.  ext_set_option returns EXT_EINVAL for an unknown option or
  * value; it affects launches issued after it returns. */
 typedef enum { EXT_OPT_P1_FORM = 1, EXT_OPT_P1_FLAT = 2 } ext_option;
-/* EXT_OPT_P1_FLAT: how the flat gather runs: EXT_P1_FLAT_SPLIT (default) the
- * vertex pass w = Mv f stored, then b = Mh w; EXT_P1_FLAT_FUSED one pass,
- * b_{a,m} = Mv applied to g = Mh f per level, lanes along a column's levels,
- * straightness checked while walking the rows (no w round trip: DRAM traffic
- * 1.07 x the algorithmic bytes instead of 1.33 x, but more FP64 work per DoF,
- * so it is not faster on GB300).  Initial value from EXTMESH_P1_FLAT (split,
- * fused). */
-typedef enum { EXT_P1_FLAT_FUSED = 0, EXT_P1_FLAT_SPLIT = 1 } ext_p1_flat;
+/* EXT_OPT_P1_FLAT: how the flat gather runs.  EXT_P1_FLAT_OPTIMISTIC
+ * (default): with WRITE access one pass forms b_{a,m} = Mv applied to
+ * g = Mh f per level (lanes along a column's levels) for every DoF as if the
+ * mesh were a straight flat extrusion, while the same launch sets one
+ * straightness bit per coordinate DoF; a second launch sends every DoF whose
+ * stencil holds a DoF that is not straight to the general path (and exits at
+ * once when there is none), so the coordinate field, f and b each cross HBM
+ * once; with INC access the split form runs.  EXT_P1_FLAT_SPLIT: the vertex
+ * pass w = Mv f stored, then b = Mh w (w written and read back).
+ * EXT_P1_FLAT_FUSED: one pass with the straightness of every row entry
+ * checked while walking the rows (three coordinate loads per entry).
+ * Initial value from EXTMESH_P1_FLAT (optimistic, split, fused). */
+typedef enum { EXT_P1_FLAT_FUSED = 0, EXT_P1_FLAT_SPLIT = 1, EXT_P1_FLAT_OPTIMISTIC = 2 } ext_p1_flat;
 typedef enum {
   EXT_P1_AUTO = 0,
   EXT_P1_SPLIT = 1,

@@ -315,7 +315,7 @@ def ext_fp64_rates(stream=None) -> dict:
 # ---- process-wide options (ext_set_option / ext_get_option)
 EXT_OPT_P1_FORM = 1
 EXT_OPT_P1_FLAT = 2
-EXT_P1_FLAT_FUSED, EXT_P1_FLAT_SPLIT = 0, 1
+EXT_P1_FLAT_FUSED, EXT_P1_FLAT_SPLIT, EXT_P1_FLAT_OPTIMISTIC = 0, 1, 2
 (EXT_P1_AUTO, EXT_P1_SPLIT, EXT_P1_GATHER, EXT_P1_FACTORED, EXT_P1_UNFACTORED, EXT_P1_CELLS,
  EXT_P1_SINGLE) = range(7)
 P1_FORMS = {"auto": EXT_P1_AUTO, "split": EXT_P1_SPLIT, "gather": EXT_P1_GATHER, "factored": EXT_P1_FACTORED,

@@ -69,8 +69,11 @@ int p1_flat() {
   if (v < 0) {
     const char *ev = getenv("EXTMESH_P1_FLAT");
     int expect = -1;
-    g_p1_flat.compare_exchange_strong(expect, (ev && strcmp(ev, "fused") == 0) ? EXT_P1_FLAT_FUSED
-                                                                                : EXT_P1_FLAT_SPLIT);
+    const int init = !ev ? EXT_P1_FLAT_OPTIMISTIC
+                         : (strcmp(ev, "fused") == 0 ? EXT_P1_FLAT_FUSED
+                                                     : (strcmp(ev, "split") == 0 ? EXT_P1_FLAT_SPLIT
+                                                                                 : EXT_P1_FLAT_OPTIMISTIC));
+    g_p1_flat.compare_exchange_strong(expect, init);
     v = g_p1_flat.load();
   }
   return v;
@@ -84,7 +87,7 @@ extern "C" ext_status ext_set_option(int32_t option, int32_t value) {
     return EXT_OK;
   }
   if (option == EXT_OPT_P1_FLAT) {
-    if (value != EXT_P1_FLAT_FUSED && value != EXT_P1_FLAT_SPLIT)
+    if (value != EXT_P1_FLAT_FUSED && value != EXT_P1_FLAT_SPLIT && value != EXT_P1_FLAT_OPTIMISTIC)
       return ext_fail(EXT_EINVAL, "ext_set_option: EXT_OPT_P1_FLAT value %d out of range", value);
     g_p1_flat.store(value);
     return EXT_OK;
@@ -210,6 +213,7 @@ static void free_mesh(ext_mesh *m) {
   cudaFree(m->d_cell_verts);
   cudaFree(m->d_cell_edges);
   cudaFree(m->d_base_xy);
+  cudaFree(m->d_area2);
   cudaFree(m->d_cell_first);
   cudaFree(m->d_cell_layers);
   cudaFree(m->d_ent_lo);
@@ -305,6 +309,20 @@ static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, cons
       e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->has_xy = base_xy_host != nullptr;
+  if (e == cudaSuccess && base_xy_host && kind == EXT_TRI && ncells > 0) {
+    // |2A| of every base triangle, as fma(dx1, dy2, -(dx2 dy1)) so that the
+    // host compilers of both architectures round it alike
+    std::vector<double> a2((size_t)ncells);
+    for (int64_t c = 0; c < ncells; ++c) {
+      const int32_t *cv = cell_verts_host + 3 * c;
+      const double x0 = base_xy_host[2 * cv[0]], y0 = base_xy_host[2 * cv[0] + 1];
+      const double dx1 = base_xy_host[2 * cv[1]] - x0, dy1 = base_xy_host[2 * cv[1] + 1] - y0;
+      const double dx2 = base_xy_host[2 * cv[2]] - x0, dy2 = base_xy_host[2 * cv[2] + 1] - y0;
+      a2[(size_t)c] = std::fabs(std::fma(dx1, dy2, -(dx2 * dy1)));
+    }
+    if ((e = cudaMalloc(&m->d_area2, (size_t)ncells * sizeof(double))) == cudaSuccess)
+      e = cudaMemcpy(m->d_area2, a2.data(), (size_t)ncells * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && kind == EXT_TRI && !var && nverts > 0 && ncells > 0) {
     std::vector<int32_t> vrow, vnbr, vcrow, vcells;
     std::vector<int2> vedge;
@@ -984,6 +1002,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
+      p.area2 = mesh->d_area2;
       p.ncoord = args[0].space->ndofs;
       p.overwrite = args[2].access == EXT_WRITE;
       p.hown = h != 0;

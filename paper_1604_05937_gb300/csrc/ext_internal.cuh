@@ -50,6 +50,7 @@ struct ext_mesh {
   int32_t *d_cell_edges = nullptr;  // ncells x kind
   double *d_base_xy = nullptr;      // nverts x 2 (may be null)
   bool has_xy = false;              // base coordinates were given
+  double *d_area2 = nullptr;        // triangles with base coordinates: |2A| of every base cell
   // variable layers per column: cell c spans levels first[c] .. first[c] + layers[c]
   bool var = false;
   int32_t *d_cell_first = nullptr;   // ncells
@@ -236,6 +237,10 @@ struct MassTPLaunch {
   // filled by launch_mass_tp when it runs the flagged form
   const uint32_t *vflags = nullptr;      // bit d: coordinate DoF d verified straight
   const double *hlay = nullptr;          // |z_{l+1} - z_l| of the reference column
+  const double *area2 = nullptr;         // |2A| of every base cell from the base coordinates, if known
+  const int32_t *badv = nullptr;         // optimistic form: per CTA of its first launch, a DoF not verified straight
+  int32_t nbadv = 0;
+  Fp64Ones k1 = {1.0, -1.0, -0.0};       // products and sums of the closed forms issued as DFMA
   bool overwrite = false;                // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
   bool hown = false;                     // horizontal DG0/DG1: every DoF belongs to one cell column
   bool vcont = false;                    // vertical CG1: layers l and l + 1 share their facet DoFs

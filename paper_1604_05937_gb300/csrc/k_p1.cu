@@ -1642,6 +1642,190 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vfused(const double *
   }
 }
 
+#ifndef EXT_P1OPT_MINB
+#define EXT_P1OPT_MINB 4  // resident 256-thread CTAs per SM of the optimistic flat gather
+#endif
+#ifndef EXT_P1OPT_UF
+#define EXT_P1OPT_UF 2  // flag words per lane per flag chunk
+#endif
+
+// Optimistic flat gather (flat mode, WRITE access).  The one-pass flat
+// gather of k_vfused checks, for every row entry it reads, that the DoF sits
+// on a straight flat extrusion; here nothing is checked in the gather:
+// b = Mh (x) Mv f is formed for every DoF as if the whole mesh were straight
+// and flat (g_{a,m} = the row of a against f at level m, then
+// b_{a,m} = lo_m g_{a,m-1} + mid_m g_{a,m} + hi_m g_{a,m+1} by warp shuffles,
+// 30 DoFs per 32-lane window), while the same launch sets one straightness
+// bit per coordinate DoF (x, y of its column's level 0 and z of its level in
+// column 0, bitwise), one bit per vertex column holding a DoF that fails, and
+// one word per CTA saying whether it saw such a DoF.  The warps take flag
+// chunks and gather windows interleaved in proportion to their counts, so
+// the HBM-bound flag work runs beside the FP64-bound gather on every SM, and
+// the coordinate field is read once.  k_p1_fix then records, for the general
+// path, every DoF whose stencil (the vertex row's columns at levels m - 1 ..
+// m + 1) holds a DoF that is not straight; it exits at once when no CTA saw
+// one.  So each DoF keeps the Kronecker value exactly when its stencil is
+// verified straight and flat, as in the split form.  A NaN in f reaches
+// exactly the DoFs whose stencil holds it, as it would through the general
+// path.
+__global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
+    k_p1_opt(const double *__restrict__ X, const double *__restrict__ f, const int32_t *__restrict__ vrow,
+             const int32_t *__restrict__ vnbr, const double *__restrict__ wts, const LevelCoef *__restrict__ tab,
+             double *__restrict__ b, uint32_t n, FastDiv col, uint32_t *__restrict__ flags,
+             uint32_t *__restrict__ vbad, int32_t *__restrict__ badv, Fp64Ones k1,
+             const unsigned int *__restrict__ mode, int64_t nfc, int64_t ngc) {
+  constexpr int UF = EXT_P1OPT_UF, kOut = 30;
+  __shared__ int cta_bad;
+  if (*mode != 0u) return;  // terrain-following or cell-loop mode (k_p1_fix exits too)
+  if (threadIdx.x == 0) cta_bad = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nwords = (n + 31) / 32;
+  const int64_t nch = nfc + ngc;
+  const int64_t wstride = (int64_t)gridDim.x * 8;
+  bool bad = false;
+  // Bresenham's interleave of the nfc flag chunks among the nch chunks, as in
+  // the nine-space optimistic form (no division in the loop)
+  const int64_t j0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  int64_t fb = j0 * nfc / nch, r = j0 * nfc - fb * nch;
+  const int64_t qw = wstride * nfc / nch, rw = wstride * nfc - qw * nch;
+  for (int64_t j = j0; j < nch; j += wstride) {
+    const bool flag_chunk = r + nfc >= nch;
+    const int64_t fcur = fb;
+    fb += qw;
+    r += rw;
+    if (r >= nch) {
+      r -= nch;
+      ++fb;
+    }
+    if (flag_chunk) {
+      const uint32_t dbase = (uint32_t)fcur * (uint32_t)(UF * 32) + (uint32_t)lane;
+      long long x[UF], y[UF], z[UF], x0[UF], y0[UF], zt[UF];
+      uint32_t qv[UF];
+      bool v[UF];
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t d = dbase + (uint32_t)(u * 32);
+        v[u] = d < n;
+        x[u] = y[u] = z[u] = x0[u] = y0[u] = zt[u] = 0;
+        qv[u] = 0;
+        if (v[u]) {
+          const uint32_t q = fdiv(d, col);
+          const uint32_t m = d - q * col.d;
+          const double *xp = X + 3 * (size_t)d;
+          const double *x0p = X + 3 * (size_t)(q * col.d);
+          qv[u] = q;
+          x[u] = __double_as_longlong(__ldg(xp + 0));
+          y[u] = __double_as_longlong(__ldg(xp + 1));
+          z[u] = __double_as_longlong(__ldg(xp + 2));
+          x0[u] = __double_as_longlong(__ldg(x0p + 0));
+          y0[u] = __double_as_longlong(__ldg(x0p + 1));
+          zt[u] = __double_as_longlong(__ldg(&tab[m].z));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t w = (uint32_t)fcur * (uint32_t)UF + (uint32_t)u;
+        const bool ok = v[u] && x[u] == x0[u] && y[u] == y0[u] && z[u] == zt[u];
+        const unsigned int word = __ballot_sync(kFull, ok);
+        const unsigned int want = __ballot_sync(kFull, v[u]);
+        if (w < nwords) {
+          if (lane == 0) flags[w] = word;
+          bad |= word != want;
+        }
+        if (v[u] && !ok) atomicOr(vbad + (qv[u] >> 5), 1u << (qv[u] & 31u));
+      }
+    } else {
+      // window (j - fcur): lanes hold DoFs start - 1 .. start + 30, lanes 1..30 write
+      const int64_t start = (j - fcur) * kOut;
+      const int64_t d = start - 1 + lane;
+      const bool in = d >= 0 && d < (int64_t)n;
+      int r0 = 0, deg = 0;
+      uint32_t m = 0;
+      double acc = k1.mzero;
+      double2 c01 = make_double2(0.0, 0.0), c23 = make_double2(0.0, 0.0);
+      if (in) {
+        const uint32_t q = fdiv((uint32_t)d, col);
+        m = (uint32_t)d - q * col.d;
+        r0 = __ldg(vrow + q);
+        deg = __ldg(vrow + q + 1) - r0;
+        c01 = __ldg(reinterpret_cast<const double2 *>(tab + m));      // z_m, |h_{m-1}|
+        c23 = __ldg(reinterpret_cast<const double2 *>(tab + m) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
+      }
+      const int dmx = __reduce_max_sync(kFull, deg);
+#pragma unroll 4
+      for (int t = 0; t < dmx; ++t) {
+        double ev = 0.0, fv = 0.0;
+        if (t < deg) {
+          ev = __ldg(wts + r0 + t);
+          fv = __ldg(f + (uint32_t)__ldg(vnbr + r0 + t) + m);
+        }
+        acc = fma(ev, fv, acc);
+      }
+      // vertical neighbours (lanes -1 and +1, the same column unless at its end)
+      const bool lo_end = m == 0, hi_end = m + 1 == col.d;
+      const double gl = __shfl_up_sync(kFull, acc, 1), gr = __shfl_down_sync(kFull, acc, 1);
+      const double glm = __longlong_as_double(__double_as_longlong(gl) & (lo_end ? 0LL : -1LL));
+      const double grm = __longlong_as_double(__double_as_longlong(gr) & (hi_end ? 0LL : -1LL));
+      const double res = fma(c01.y, glm, fma(c23.x, acc, fmul(c23.y, grm, k1)));
+      if (lane >= 1 && lane <= kOut && in) b[d] = res;
+    }
+  }
+  if (bad && lane == 0) cta_bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) badv[blockIdx.x] = cta_bad;
+}
+
+// bits pos .. pos + 31 of a bitmap (which holds a zero word past its end)
+__device__ __forceinline__ uint32_t bits32(const uint32_t *__restrict__ bm, uint32_t pos) {
+  const uint32_t w = pos >> 5, s = pos & 31u;
+  const uint32_t lo = __ldg(bm + w) >> s;
+  return s ? lo | (__ldg(bm + w + 1) << (32u - s)) : lo;
+}
+
+// Fix-up of the optimistic flat gather: returns at once unless a CTA of
+// k_p1_opt saw a coordinate DoF that is not straight.  Then one thread per
+// vertex column a whose row (a and its neighbours) holds a column with such a
+// DoF records, 32 levels at a time, the DoFs b_{a,m} whose stencil (row
+// columns at levels m - 1, m, m + 1) holds one, for k_vgather_general.
+__global__ void __launch_bounds__(256) k_p1_fix(const int32_t *__restrict__ vrow, const int32_t *__restrict__ vnbr,
+                                                const uint32_t *__restrict__ flags, const uint32_t *__restrict__ vbad,
+                                                const int32_t *__restrict__ badv, int32_t nbadv, uint32_t nverts,
+                                                FastDiv col, Deferred dfr, unsigned int *err,
+                                                const unsigned int *__restrict__ mode) {
+  if (*mode != 0u) return;
+  int any = 0;
+  for (int i = threadIdx.x; i < nbadv; i += blockDim.x) any |= __ldg(badv + i);
+  if (!__syncthreads_or(any)) return;
+  const uint32_t L1 = col.d;
+  for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nverts; a += gridDim.x * blockDim.x) {
+    const int32_t r0 = __ldg(vrow + a), r1 = __ldg(vrow + a + 1);
+    bool hit = false;
+    for (int32_t t = r0; t < r1 && !hit; ++t) {
+      const uint32_t jv = fdiv((uint32_t)__ldg(vnbr + t), col);
+      hit = (__ldg(vbad + (jv >> 5)) >> (jv & 31u)) & 1u;
+    }
+    if (!hit) continue;
+    for (uint32_t lo = 0; lo < L1; lo += 32) {
+      const uint32_t nl = L1 - lo < 32 ? L1 - lo : 32;  // levels lo .. lo + nl - 1 of this word
+      const uint32_t valid = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
+      uint32_t B = 0, below = 0, above = 0;  // not straight: at lo + i, at lo - 1, at lo + 32
+      for (int32_t t = r0; t < r1; ++t) {
+        const uint32_t j0 = (uint32_t)__ldg(vnbr + t);
+        B |= ~bits32(flags, j0 + lo) & valid;
+        if (lo > 0) below |= ~bits32(flags, j0 + lo - 1) & 1u;
+        if (lo + 32 < L1) above |= ~bits32(flags, j0 + lo + 32) & 1u;
+      }
+      const uint32_t need = (B | (B << 1) | (B >> 1) | below | (above << 31)) & valid;
+      if (need) {
+        const unsigned int slot = atomicAdd(dfr.count, 1u);
+        if (slot < dfr.cap) dfr.list[slot] = make_int2((int)(a * L1 + lo), (int)need);
+        else atomicOr(err, EXT_DERR_BOUNDS);
+      }
+    }
+  }
+}
+
 // The recorded DoFs of the gather: b_{a,m} (+)= the bottom-row entries of the
 // prisms (c, m) and the top-row entries of the prisms (c, m - 1) for every
 // cell c around vertex a (p1_prism), summed in ascending cell order.  One
@@ -1845,8 +2029,17 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   char *scr = nullptr;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nn = (size_t)(n > 0 ? n : 1);
-  const int64_t cap64 = gather ? (n + 29) / 30 + 2
-                               : (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
+  // the optimistic flat gather (WRITE): one straightness bit per coordinate
+  // DoF (and a zero word past the end), one per vertex column, one word per
+  // CTA of k_p1_opt; its fix-up records up to one 32-level word per vertex
+  // column and word of levels
+  const bool opt = gather && p.overwrite && p1_flat() == EXT_P1_FLAT_OPTIMISTIC;
+  static int res_opt = 0;
+  const int64_t go = opt ? (int64_t)resident_ctas(k_p1_opt, res_opt) * sms : 0;
+  const int64_t fix_recs = opt ? (int64_t)p.nverts * ((p.layers + 1 + 31) / 32) + 2 : 0;
+  int64_t cap64 = gather ? (n + 29) / 30 + 2
+                         : (int64_t)(items / 32.0) + (p.ncells + cpw - 1) / cpw + 64 + (var ? p.ncells / 8 : 0);
+  if (cap64 < fix_recs) cap64 = fix_recs;
   const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
   const size_t wbytes = cells ? 0 : al(sizeof(double) * nn * (var ? 3 : (gather ? 1 : 2)));
   const size_t abytes = factored ? al(sizeof(double) * (size_t)(n / (p.layers + 1))) : 0;
@@ -1857,9 +2050,13 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   const size_t vbytes = gather ? al(sizeof(double) * (size_t)p.nverts) : 0;
   const size_t sbytes = gather ? 3 * vbytes + cbytes : 0;
   const size_t lbytes = cells ? 0 : sizeof(int2) * (size_t)cap;
+  const size_t vbbytes = opt ? al(sizeof(uint32_t) * (size_t)((p.nverts + 31) / 32)) : 0;
+  const size_t fbytes = opt ? al(sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1)) : 0;
+  const size_t bvbytes = opt ? al(sizeof(int32_t) * (size_t)go) : 0;
   if (form != EXT_P1_SINGLE &&
-      cudaMallocAsync(reinterpret_cast<void **>(&scr),
-                      256 + wbytes + abytes + tbytes + cbytes + ebytes + sbytes + lbytes, s) != cudaSuccess) {
+      cudaMallocAsync(reinterpret_cast<void **>(&scr), 256 + vbbytes + wbytes + abytes + tbytes + cbytes + ebytes +
+                                                           sbytes + lbytes + fbytes + bvbytes,
+                      s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: run the single-pass kernel instead
     scr = nullptr;
   }
@@ -1877,6 +2074,9 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   unsigned int *count = reinterpret_cast<unsigned int *>(scr);
   unsigned int *mode = count + 1;
   unsigned long long *minds = reinterpret_cast<unsigned long long *>(scr + 8);
+  uint32_t *vbad = reinterpret_cast<uint32_t *>(scr + 256);  // cleared with the 256-byte block
+  scr += vbbytes;  // the rest of the layout follows the vertex-column bits
+  char *const scr0 = scr - vbbytes;
   double *W = reinterpret_cast<double *>(scr + 256);
   double *A = reinterpret_cast<double *>(scr + 256 + wbytes);
   LevelCoef *tab = reinterpret_cast<LevelCoef *>(scr + 256 + wbytes + abytes);
@@ -1892,10 +2092,14 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   dfr.count = count;
   dfr.list = reinterpret_cast<int2 *>(sg0 + sbytes);
   dfr.cap = cap;
-  // the counter and the mode word start at zero, the smallest sigma spacing
-  // at a large positive double (bytes 0x7f)
-  cudaError_t e = cudaMemsetAsync(scr, 0, 256, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(scr + 8, 0x7f, 8, s);
+  uint32_t *oflags = reinterpret_cast<uint32_t *>(sg0 + sbytes + lbytes);
+  int32_t *badv = reinterpret_cast<int32_t *>(sg0 + sbytes + lbytes + fbytes);
+  // the counter and the mode word start at zero (and the vertex-column bits
+  // of the optimistic gather), the smallest sigma spacing at a large positive
+  // double (bytes 0x7f)
+  cudaError_t e = cudaMemsetAsync(scr0, 0, 256 + vbbytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scr0 + 8, 0x7f, 8, s);
+  if (e == cudaSuccess && opt) e = cudaMemsetAsync(oflags + (n + 31) / 32, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess && factored && abytes) e = cudaMemsetAsync(A, 0, abytes, s);
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
   const int rc = resident_ctas(k_p1_cells, res_p1c);
@@ -1946,7 +2150,19 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vnbr, p.vedge, p.vcrow, p.vcells, alpha,
                                                                  sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode);
     const bool fused = p1_flat() == EXT_P1_FLAT_FUSED;
-    if (fused) {
+    if (opt) {
+      const int64_t nfc = ((n + 31) / 32 + EXT_P1OPT_UF - 1) / EXT_P1OPT_UF;
+      const int64_t ngc = (n + 29) / 30;
+      int64_t g = (nfc + ngc + 7) / 8;
+      if (g > go) g = go;
+      if (g < 1) g = 1;
+      k_p1_opt<<<(unsigned)g, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, (uint32_t)n, col, oflags, vbad,
+                                           badv, k1, mode, nfc, ngc);
+      int64_t gx = (nv + 255) / 256;
+      if (gx > (int64_t)sms * 8) gx = (int64_t)sms * 8;
+      k_p1_fix<<<(unsigned)(gx > 0 ? gx : 1), 256, 0, s>>>(p.vrow, p.vnbr, oflags, vbad, badv, (int32_t)g,
+                                                             (uint32_t)nv, col, dfr, p.err, mode);
+    } else if (fused) {
       static int res_vf[2] = {0, 0};
       const int rf = p.overwrite ? resident_ctas(k_vfused<false>, res_vf[0]) : resident_ctas(k_vfused<true>, res_vf[1]);
       int64_t gf = ((n + 29) / 30 + 7) / 8;
@@ -1962,15 +2178,16 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       int64_t gb = ((n + kBulkDofs - 1) / kBulkDofs + 7) / 8;  // CTAs of 8 warps, one warp step each
       if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
       if (gb < 1) gb = 1;
-      if (!fused)
+      if (!fused && !opt)
         k_vsum_bulk<false><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
       k_vsum_bulk<true><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
     } else {
-      if (!fused) k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
+      if (!fused && !opt) k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
       k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
     }
     if (p.overwrite) {
-      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode, fused);
+      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode,
+                                                    fused || opt);
       const int r = resident_ctas(k_vgather_general<false>, res_vgg[0]);
       k_vgather_general<false><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
     } else {
@@ -2006,6 +2223,6 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     }
     e = cudaGetLastError();
   }
-  const cudaError_t ef = cudaFreeAsync(scr, s);
+  const cudaError_t ef = cudaFreeAsync(scr0, s);
   return e != cudaSuccess ? e : ef;
 }

@@ -107,17 +107,18 @@ __global__ void __launch_bounds__(256) k_tp_vflags(const double *__restrict__ X,
 }
 
 // Element vector of a straight prism with c = alpha |h|: Mh (x) Mv f in closed
-// form for NH horizontal and NV vertical nodes.
+// form for NH horizontal and NV vertical nodes; products and sums go out as
+// DFMA (k1), which GB300 issues faster than DMUL and DADD.
 template <int NH, int NV>
-__device__ __forceinline__ void tp_closed(double cc, const double f[NH * NV], double b[NH * NV]) {
+__device__ __forceinline__ void tp_closed(double cc, const double f[NH * NV], double b[NH * NV], const Fp64Ones &k1) {
   if (NH == 1 && NV == 1) {
-    b[0] = cc * f[0];
+    b[0] = fmul(cc, f[0], k1);
   } else if (NH == 1) {  // NV == 2
-    const double c2 = cc + cc;
-    b[0] = fma(c2, f[0], cc * f[1]);
-    b[1] = fma(c2, f[1], cc * f[0]);
+    const double c2 = fadd(cc, cc, k1);
+    b[0] = fma(c2, f[0], fmul(cc, f[1], k1));
+    b[1] = fma(c2, f[1], fmul(cc, f[0], k1));
   } else if (NV == 1) {  // NH == 3
-    const double cS = cc * ((f[0] + f[1]) + f[2]);
+    const double cS = fmul(cc, fadd(fadd(f[0], f[1], k1), f[2], k1), k1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) b[a] = fma(cc, f[a], cS);
   } else {  // NH == 3, NV == 2: b_{a,beta} = c (t_{a,beta} + T_beta),
@@ -128,7 +129,8 @@ __device__ __forceinline__ void tp_closed(double cc, const double f[NH * NV], do
       t[2 * a] = fma(2.0, f[2 * a], f[2 * a + 1]);
       t[2 * a + 1] = fma(2.0, f[2 * a + 1], f[2 * a]);
     }
-    const double K0 = cc * ((t[0] + t[2]) + t[4]), K1 = cc * ((t[1] + t[3]) + t[5]);
+    const double K0 = fmul(cc, fadd(fadd(t[0], t[2], k1), t[4], k1), k1);
+    const double K1 = fmul(cc, fadd(fadd(t[1], t[3], k1), t[5], k1), k1);
 #pragma unroll
     for (int i = 0; i < 6; ++i) b[i] = fma(cc, t[i], (i & 1) ? K1 : K0);
   }
@@ -159,13 +161,20 @@ __device__ __forceinline__ int vflags_all(const uint32_t *__restrict__ flags, in
 // items per lane per step, a separate instantiation so that its registers do
 // not lower the occupancy of the one-item loop.
 // WR: each DoF belongs to one cell-layer (DG x DG) and b is overwritten:
-// plain stores instead of atomic adds.
-template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = false>
+// plain stores instead of atomic adds.  FIX (with FLAGS and WR): the fix-up
+// launch of the optimistic form, which writes only the prisms whose flags are
+// not all set (and returns at once when the flag pass found none).
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = false, bool FIX = false>
 #ifndef EXT_TP_SMALL_MINB
 #define EXT_TP_SMALL_MINB 3  // resident CTAs per SM for one-node elements (DG0xDG0: registers for occupancy)
 #endif
 __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB : 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
+  if (FIX) {  // no CTA of the optimistic launch saw a coordinate DoF that is not straight
+    int any = 0;
+    for (int i = threadIdx.x; i < p.nbadv; i += blockDim.x) any |= __ldg(p.badv + i);
+    if (!__syncthreads_or(any)) return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int layers = p.layers;
   const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
@@ -243,7 +252,11 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
 #pragma unroll
               for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)l * p.coff[i]);
             }
-            hl[u] = __ldg(p.hlay + l);
+            if (FIX && ok[u]) valid[u] = false;  // written by the optimistic launch
+          }
+          if (valid[u]) {
+            const TPCol &ci = cols[warp][cl];
+            if (!FIX) hl[u] = __ldg(p.hlay + l);
 #pragma unroll
             for (int i = 0; i < NH * NV; ++i) {
               dof[u][i] = ci.fm[i] + l * p.off[i];
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
           const TPCol &ci = cols[warp][cls[u]];
           double b[NH * NV];
           if (ok[u]) {
-            tp_closed<NH, NV>(ci.alpha * hl[u], f[u], b);
+            tp_closed<NH, NV>(fmul(ci.alpha, hl[u], p.k1), f[u], b, p.k1);
           } else {
             double Xl[6][3];
 #pragma unroll
@@ -310,23 +323,25 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
                 (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[3][2])) &
                 (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
         }
-        int32_t dof[NH * NV];
-        double f[NH * NV], b[NH * NV];
+        if (!(FIX && ok)) {  // FIX: straight prisms were written by the optimistic launch
+          int32_t dof[NH * NV];
+          double f[NH * NV], b[NH * NV];
 #pragma unroll
-        for (int i = 0; i < NH * NV; ++i) {
-          dof[i] = ci.fm[i] + l * p.off[i];
-          f[i] = __ldg(p.f + dof[i]);
-        }
-        if (ok) {
-          tp_closed<NH, NV>(ci.alpha * (FLAGS ? __ldg(p.hlay + l) : fabs(Xl[1][2] - Xl[0][2])), f, b);
-        } else {
-          if (FLAGS) load_coords();
-          tp_general<NH, NV>(Xl, f, b);
-        }
+          for (int i = 0; i < NH * NV; ++i) {
+            dof[i] = ci.fm[i] + l * p.off[i];
+            f[i] = __ldg(p.f + dof[i]);
+          }
+          if (ok) {
+            tp_closed<NH, NV>(fmul(ci.alpha, FLAGS ? __ldg(p.hlay + l) : fabs(Xl[1][2] - Xl[0][2]), p.k1), f, b, p.k1);
+          } else {
+            if (FLAGS) load_coords();
+            tp_general<NH, NV>(Xl, f, b);
+          }
 #pragma unroll
-        for (int i = 0; i < NH * NV; ++i) {
-          if (WR) p.b[dof[i]] = b[i];
-          else atomicAdd(p.b + dof[i], b[i]);
+          for (int i = 0; i < NH * NV; ++i) {
+            if (WR) p.b[dof[i]] = b[i];
+            else atomicAdd(p.b + dof[i], b[i]);
+          }
         }
       }
       l += 32;
@@ -340,7 +355,181 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
   }
 }
 
-template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI, bool WR = false>
+#ifndef EXT_TP_DGDG_UI1
+#define EXT_TP_DGDG_UI1 4  // DG0 x DG0: items per lane per element chunk
+#endif
+#ifndef EXT_TP_DGDG_UF1
+#define EXT_TP_DGDG_UF1 2  // DG0 x DG0: flag words per lane per flag chunk
+#endif
+#ifndef EXT_TP_DGDG_MINB
+#define EXT_TP_DGDG_MINB 4  // DG0 x DG0: resident CTAs per SM
+#endif
+#ifndef EXT_TP_DGDG_MAX_LAYERS
+#define EXT_TP_DGDG_MAX_LAYERS 2048  // the level tables of the optimistic form live in shared memory
+#endif
+// Optimistic WRITE form for DG x DG on constant layers (every DoF of b
+// belongs to one cell-layer).  The flagged form's two passes (straightness
+// flags over the coordinate field, then the element vectors) have no data
+// dependence when the element vector is taken in closed form for every prism
+// on the assumption that it is straight: the column's |2A| comes from the
+// mesh's base coordinates and the layer's height from the reference column
+// (vertex 0's, coordinate DoFs 0 .. layers).  So one launch does both, the
+// same warps taking flag chunks and element chunks interleaved in proportion
+// to their counts, and the HBM-bound flag work runs beside the FP64-bound
+// element work on every SM.  A fix-up launch (k_mass_tp with FIX) then
+// rewrites the DoFs of every prism whose six flags are not all set with the
+// general rule, and returns at once when no CTA of this launch found such a
+// coordinate DoF.  The result is the flagged form's: each DoF is written by
+// the closed form exactly when its prism is verified straight.
+// flag words per lane per flag chunk, items per lane per element chunk (for
+// DG0 x DG0 sized so that 4 CTAs of 256 threads stay resident per SM; 2 CTAs
+// for the element vectors of 2, 3 and 6 DoFs)
+__host__ __device__ constexpr int dgdg_uf(int k) { return k == 1 ? EXT_TP_DGDG_UF1 : 4; }
+__host__ __device__ constexpr int dgdg_ui(int k) { return k == 1 ? EXT_TP_DGDG_UI1 : 4; }
+
+template <int NH, int NV>
+__global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB : 2)
+    k_tp_dgdg(const MassTPLaunch p, uint32_t *__restrict__ flags, int32_t *__restrict__ badv, FastDiv colv,
+              FastDiv lay, int64_t nfc, int64_t nic) {
+  constexpr int UF = dgdg_uf(NH * NV), UI = dgdg_ui(NH * NV), K = NH * NV;
+  // level tables of the reference column: z at every level, scaled heights
+  // hs[l] = |z_{l+1} - z_l| x (the element's constant)
+  extern __shared__ double lvl[];
+  double *ztab = lvl, *hs = lvl + p.layers + 1;
+  __shared__ int cta_bad;
+  for (int m = threadIdx.x; m <= p.layers; m += blockDim.x) ztab[m] = __ldg(p.X + 3 * (int64_t)m + 2);
+  if (threadIdx.x == 0) cta_bad = 0;
+  __syncthreads();
+  for (int m = threadIdx.x; m < p.layers; m += blockDim.x) hs[m] = fabs(ztab[m + 1] - ztab[m]) * p.scale;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t ncoord = (uint32_t)p.ncoord, nwords = (uint32_t)((p.ncoord + 31) / 32);
+  const uint32_t nitems = (uint32_t)(p.ncells * (int64_t)p.layers);
+  const int64_t nch = nfc + nic;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  bool bad = false;
+  // chunk j is flag chunk fb = floor(j nfc / nch) when floor((j + 1) nfc / nch)
+  // > fb, i.e. when r + nfc >= nch with r = j nfc - fb nch, else element
+  // chunk j - fb (the flag chunks before it are fb); fb and r advance by the
+  // quotient and remainder of wstride nfc / nch from one chunk of the warp to
+  // the next (Bresenham's interleave, no division in the loop)
+  const int64_t j0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  int64_t fb = j0 * nfc / nch, r = j0 * nfc - fb * nch;
+  const int64_t qw = wstride * nfc / nch, rw = wstride * nfc - qw * nch;
+  for (int64_t j = j0; j < nch; j += wstride) {
+    const bool flag_chunk = r + nfc >= nch;
+    const int64_t fcur = fb;
+    fb += qw;
+    r += rw;
+    if (r >= nch) {
+      r -= nch;
+      ++fb;
+    }
+    if (flag_chunk) {
+      // 32-bit indices: the launcher keeps the coordinate DoFs and the items below 2^31
+      const uint32_t d0 = (uint32_t)fcur * (uint32_t)(UF * 32) + (uint32_t)lane;
+      long long x[UF], y[UF], z[UF], rx[UF], ry[UF], rz[UF];
+      bool v[UF];
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t d = d0 + (uint32_t)(u * 32);
+        v[u] = d < ncoord;
+        x[u] = y[u] = z[u] = rx[u] = ry[u] = rz[u] = 0;
+        if (v[u]) {
+          const uint32_t q = fdiv(d, colv);
+          const uint32_t m = d - q * colv.d;
+          const double *xp = p.X + 3 * (size_t)d;
+          const double *bp = p.base_xy + 2 * (size_t)q;
+          x[u] = __double_as_longlong(__ldg(xp + 0));
+          y[u] = __double_as_longlong(__ldg(xp + 1));
+          z[u] = __double_as_longlong(__ldg(xp + 2));
+          rx[u] = __double_as_longlong(__ldg(bp + 0));
+          ry[u] = __double_as_longlong(__ldg(bp + 1));
+          rz[u] = __double_as_longlong(ztab[m]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t w = (uint32_t)fcur * (uint32_t)UF + (uint32_t)u;
+        const unsigned int word = __ballot_sync(0xffffffffu, v[u] && x[u] == rx[u] && y[u] == ry[u] && z[u] == rz[u]);
+        const unsigned int want = __ballot_sync(0xffffffffu, v[u]);
+        if (w < nwords) {
+          if (lane == 0) flags[w] = word;
+          bad |= word != want;
+        }
+      }
+    } else {
+      const uint32_t i0 = (uint32_t)(j - fcur) * (uint32_t)(32 * UI) + (uint32_t)lane;
+      int32_t dof[UI][K];
+      double a2[UI], h[UI], f[UI][K];
+      bool v[UI];
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+        const uint32_t it = i0 + (uint32_t)(u * 32);
+        v[u] = it < nitems;
+        a2[u] = h[u] = 0.0;
+        if (v[u]) {
+          const uint32_t c = fdiv(it, lay);
+          const int l = (int)(it - c * lay.d);
+          a2[u] = __ldg(p.area2 + c);
+          h[u] = hs[l];
+          const int32_t *row = p.fmap + (size_t)c * (uint32_t)p.k;
+#pragma unroll
+          for (int i = 0; i < K; ++i) dof[u][i] = __ldg(row + p.slot[i]) + l * p.off[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) f[u][i] = v[u] ? __ldg(p.f + (uint32_t)dof[u][i]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+        if (!v[u]) continue;
+        double b[K];
+        tp_closed<NH, NV>(fmul(a2[u], h[u], p.k1), f[u], b, p.k1);
+#pragma unroll
+        for (int i = 0; i < K; ++i) p.b[(uint32_t)dof[u][i]] = b[i];
+      }
+    }
+  }
+  // one word per CTA (every CTA writes its own, so nothing needs clearing first)
+  if (bad && lane == 0) cta_bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) badv[blockIdx.x] = cta_bad;
+}
+
+// grid of the optimistic launch: resident CTAs per SM x SMs, at most the chunk count
+template <int NH, int NV>
+int64_t dgdg_grid(const MassTPLaunch &p, size_t smem) {
+  static int resident = 0, sms = 0;
+  static size_t at = 0;
+  if (resident == 0 || at != smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_tp_dgdg<NH, NV>, kWarps * 32, smem);
+    if (resident < 1) resident = 1;
+    at = smem;
+  }
+  const int64_t nfc = ((p.ncoord + 31) / 32 + dgdg_uf(NH * NV) - 1) / dgdg_uf(NH * NV);
+  const int64_t nic = (p.ncells * (int64_t)p.layers + 32 * dgdg_ui(NH * NV) - 1) / (32 * dgdg_ui(NH * NV));
+  int64_t blocks = (nfc + nic + kWarps - 1) / kWarps;
+  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
+  return blocks < 1 ? 1 : blocks;
+}
+
+template <int NH, int NV>
+cudaError_t launch_tp_dgdg(const MassTPLaunch &p, uint32_t *flags, int32_t *badv, int64_t blocks, size_t smem,
+                           cudaStream_t s) {
+  const int64_t nfc = ((p.ncoord + 31) / 32 + dgdg_uf(NH * NV) - 1) / dgdg_uf(NH * NV);
+  const int64_t nic = (p.ncells * (int64_t)p.layers + 32 * dgdg_ui(NH * NV) - 1) / (32 * dgdg_ui(NH * NV));
+  k_tp_dgdg<NH, NV><<<(unsigned)blocks, kWarps * 32, smem, s>>>(p, flags, badv, make_fastdiv((uint32_t)(p.layers + 1)),
+                                                                make_fastdiv((uint32_t)p.layers), nfc, nic);
+  return cudaGetLastError();
+}
+
+template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI, bool WR = false, bool FIX = false>
 cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   const double lay = VAR ? p.mean_layers : (double)p.layers;
   int cpw = (int)((EXT_TP_ITEMS + lay - 1.0) / lay);
@@ -348,19 +537,19 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (cpw > kMaxCols) cpw = kMaxCols;
   const int64_t warps = (p.ncells + cpw - 1) / cpw;
   int64_t blocks = (warps + kWarps - 1) / kWarps;
-  static int resident[32] = {0}, sms = 0;
+  static int resident[64] = {0}, sms = 0;
   const int slot = (NH == 3 ? 2 : 0) + (NV == 2 ? 1 : 0) + (VAR ? 4 : 0) + (FLAGS ? 8 : 0) + (MULTI ? 4 : 0) +
-                   (WR ? 16 : 0);
+                   (WR ? 16 : 0) + (FIX ? 32 : 0);
   if (resident[slot] == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[slot], k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR, FIX>,
                                                   kWarps * 32, 0);
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
-  k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR, FIX><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
 
@@ -369,12 +558,12 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
 #ifndef EXT_TP_MULTI_LAYERS
 #define EXT_TP_MULTI_LAYERS 8
 #endif
-template <bool VAR, bool FLAGS, bool MULTI, bool WR = false>
+template <bool VAR, bool FLAGS, bool MULTI, bool WR = false, bool FIX = false>
 cudaError_t launch_tp_kind(const MassTPLaunch &p, cudaStream_t s) {
-  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS, MULTI, WR>(p, s);
-  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS, MULTI, WR>(p, s);
-  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS, MULTI, WR>(p, s);
-  return launch_tp<3, 2, VAR, FLAGS, MULTI, WR>(p, s);
+  if (p.nh == 1 && p.nv == 1) return launch_tp<1, 1, VAR, FLAGS, MULTI, WR, FIX>(p, s);
+  if (p.nh == 1) return launch_tp<1, 2, VAR, FLAGS, MULTI, WR, FIX>(p, s);
+  if (p.nv == 1) return launch_tp<3, 1, VAR, FLAGS, MULTI, WR, FIX>(p, s);
+  return launch_tp<3, 2, VAR, FLAGS, MULTI, WR, FIX>(p, s);
 }
 template <bool VAR, bool FLAGS, bool WR = false>
 cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
@@ -492,7 +681,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPL
                      (__double_as_longlong(Xl[1][2]) == __double_as_longlong(Xl[5][2]));
             }
           }
-          if (okp) tp_closed<NH, 2>(ci.alpha * (FLAGS ? hl[u] : fabs(Xl[1][2] - Xl[0][2])), f[u], b);
+          if (okp) tp_closed<NH, 2>(fmul(ci.alpha, FLAGS ? hl[u] : fabs(Xl[1][2] - Xl[0][2]), p.k1), f[u], b, p.k1);
           else tp_general<NH, 2>(Xl, f[u], b);
 #pragma unroll
           for (int a = 0; a < NH; ++a) {
@@ -747,19 +936,53 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   }
   const double items = (double)p.ncells * (double)p.layers;
   const bool want = p.base_xy && p.ncoord > 0 && flags_env != 0 && (flags_env == 1 || items >= 1.0e6);
+  // the optimistic form (WRITE, DG x DG, constant layers from
+  // EXT_TP_MULTI_LAYERS to EXT_TP_DGDG_MAX_LAYERS, a mesh with |2A| per base
+  // cell; EXTMESH_TP_OPTIMISTIC=0, read once per process, turns it off):
+  // 32-bit item and DoF indices
+  static int opt_env = -1;
+  if (opt_env < 0) {
+    const char *ev = getenv("EXTMESH_TP_OPTIMISTIC");
+    opt_env = (ev && ev[0] == '0') ? 0 : 1;
+  }
+  const bool optimistic = want && opt_env == 1 && p.area2 && owned && !p.vcont && p.overwrite &&
+                          p.layers >= EXT_TP_MULTI_LAYERS && p.layers <= EXT_TP_DGDG_MAX_LAYERS &&
+                          items < 2147483647.0 && (double)p.ncoord < 2147483647.0;
   char *scr = nullptr;
   const size_t fbytes = (sizeof(uint32_t) * (size_t)((p.ncoord + 31) / 32) + 255) & ~(size_t)255;
   const size_t zbytes = (sizeof(double) * (size_t)(p.layers + 1) + 255) & ~(size_t)255;
-  if (want && cudaMallocAsync(reinterpret_cast<void **>(&scr), fbytes + 2 * zbytes, s) != cudaSuccess) {
+  const size_t smem = sizeof(double) * (size_t)(2 * p.layers + 1);
+  int64_t oblocks = 0;
+  if (optimistic) {
+    if (p.nh == 1 && p.nv == 1) oblocks = dgdg_grid<1, 1>(p, smem);
+    else if (p.nh == 1) oblocks = dgdg_grid<1, 2>(p, smem);
+    else if (p.nv == 1) oblocks = dgdg_grid<3, 1>(p, smem);
+    else oblocks = dgdg_grid<3, 2>(p, smem);
+  }
+  const size_t sbytes = optimistic ? (sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255 : 2 * zbytes;
+  if (want && cudaMallocAsync(reinterpret_cast<void **>(&scr), fbytes + sbytes, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: the plain form needs no scratch
     scr = nullptr;
   }
   if (!scr) return owned ? launch_tp_owned<false>(p, s) : launch_tp_pair<false, false>(p, s);
   MassTPLaunch q = p;
   uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
+  q.vflags = flags;
+  if (optimistic) {
+    int32_t *badv = reinterpret_cast<int32_t *>(scr + fbytes);
+    cudaError_t e;
+    if (p.nh == 1 && p.nv == 1) e = launch_tp_dgdg<1, 1>(q, flags, badv, oblocks, smem, s);
+    else if (p.nh == 1) e = launch_tp_dgdg<1, 2>(q, flags, badv, oblocks, smem, s);
+    else if (p.nv == 1) e = launch_tp_dgdg<3, 1>(q, flags, badv, oblocks, smem, s);
+    else e = launch_tp_dgdg<3, 2>(q, flags, badv, oblocks, smem, s);
+    q.badv = badv;
+    q.nbadv = (int32_t)oblocks;
+    if (e == cudaSuccess) e = launch_tp_kind<false, true, true, true, true>(q, s);
+    const cudaError_t ef = cudaFreeAsync(scr, s);
+    return e != cudaSuccess ? e : ef;
+  }
   double *ztab = reinterpret_cast<double *>(scr + fbytes);
   double *hlay = reinterpret_cast<double *>(scr + fbytes + zbytes);
-  q.vflags = flags;
   q.hlay = hlay;
   static int sms = 0, res_vf = 0;
   if (sms == 0) {

@@ -39,13 +39,19 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.fixture(autouse=True, params=["fused", "split"])
+FLAT = {"optimistic": E.EXT_P1_FLAT_OPTIMISTIC, "fused": E.EXT_P1_FLAT_FUSED, "split": E.EXT_P1_FLAT_SPLIT}
+
+
+@pytest.fixture(autouse=True, params=list(FLAT))
 def flat(request):
-    """Every test runs with the flat gather in one pass and as vertex pass +
-    gather (EXT_OPT_P1_FLAT)."""
+    """Every test runs with each form of the flat gather (EXT_OPT_P1_FLAT):
+    optimistic (one pass with the straightness bits set beside it, then a
+    fix-up of the DoFs next to a DoF that is not straight; WRITE only, INC
+    takes the split form), one pass with every row entry checked, and vertex
+    pass + gather."""
     old = E.ext_get_option(E.EXT_OPT_P1_FORM)
     oldf = E.ext_get_option(E.EXT_OPT_P1_FLAT)
-    E.ext_set_option(E.EXT_OPT_P1_FLAT, E.EXT_P1_FLAT_FUSED if request.param == "fused" else E.EXT_P1_FLAT_SPLIT)
+    E.ext_set_option(E.EXT_OPT_P1_FLAT, FLAT[request.param])
     yield request.param
     E.ext_set_option(E.EXT_OPT_P1_FORM, old)
     E.ext_set_option(E.EXT_OPT_P1_FLAT, oldf)

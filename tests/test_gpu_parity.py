@@ -251,10 +251,11 @@ def test_mass_general_geometry_partial(layers, with_xy):
                                   {"EXTMESH_P1_FORM": "gather"}, {"EXTMESH_P1_FORM": "unfactored"},
                                   {"EXTMESH_P1_FORM": "factored"}, {"EXTMESH_P1_FORM": "cells"},
                                   {"EXTMESH_TP_FLAGS": "1"}, {"EXTMESH_TP_FLAGS": "1", "EXTMESH_TP_LEVELS": "1"},
-                                  {"EXTMESH_TP_FLAGS": "0", "EXTMESH_TP_LEVELS": "1"}],
+                                  {"EXTMESH_TP_FLAGS": "0", "EXTMESH_TP_LEVELS": "1"},
+                                  {"EXTMESH_TP_FLAGS": "1", "EXTMESH_TP_OPTIMISTIC": "0"}],
                          ids=["split", "split-flat-fused", "single", "gather", "split-unfactored", "split-factored",
                               "cells", "tp-flags",
-                              "tp-levels-flags", "tp-levels"])
+                              "tp-levels-flags", "tp-levels", "tp-flags-not-optimistic"])
 def test_mass_forced_form(form):
     """Every form of the P1xP1 launch passes the same parity tests, each
     forced at every size by EXTMESH_P1_FORM (read once per process, so in a
@@ -269,17 +270,20 @@ def test_mass_forced_form(form):
     per coordinate DoF, the default from a million items) forced at every
     size by EXTMESH_TP_FLAGS, with and without the level kernel for DG x CG1
     (EXTMESH_TP_LEVELS=1: the DoFs shared by consecutive layers merged in
-    registers)."""
+    registers), and with the optimistic WRITE form of the DG x DG spaces
+    turned off (EXTMESH_TP_OPTIMISTIC=0: flags first, then the element
+    vectors)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, **form)
+    sel = "mass_action_parity or rhs_sin_cos or mass_general_geometry or volume_pin or tp_parity or var_mass"
+    if "EXTMESH_TP_OPTIMISTIC" in form:
+        sel += " or tp_flags_partial"
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(root, "tests", "test_gpu_parity.py"),
-                        os.path.join(root, "tests", "test_gpu_var_facets.py"), "-k",
-                        "mass_action_parity or rhs_sin_cos or mass_general_geometry or volume_pin or tp_parity "
-                        "or var_mass"],
+                        os.path.join(root, "tests", "test_gpu_var_facets.py"), "-k", sel],
                        cwd=root, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-3000:]
     assert " passed" in r.stdout
@@ -584,13 +588,17 @@ def check_tp_access(gm, cs, sp, X, f, ref, absr):
     close(host(b), ref, absr)
 
 
-@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1", "DG0xCG1", "DG1xDG1"])
+@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1", "DG0xCG1", "DG1xDG1", "DG1xDG0"])
 def test_mass_tp_flags_partial(name):
     """Over a million (column, layer) items the nine-space kernels take their
     flagged form (one straightness bit per coordinate DoF against the base
     coordinates and the level heights); columns moved in x, y from some level
     up, single lifted levels and a level-0 vertex moved off its base position
-    must send exactly the prisms that touch them to the general 6-point rule."""
+    must send exactly the prisms that touch them to the general 6-point rule.
+    With WRITE the DG x DG spaces take the optimistic form (closed form for
+    every prism beside the flag pass, then a fix-up launch over the prisms
+    whose flags are not all set), so the NaN that WRITE starts from must be
+    overwritten everywhere and the moved prisms must come out of the fix-up."""
     n, layers = 72, 100
     m = meshgen.tri_mesh(n, seed=650, order="rcm")
     gm = E.Mesh(m.cells, m.xy, layers)
