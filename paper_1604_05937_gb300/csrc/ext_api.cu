@@ -213,7 +213,6 @@ static void free_mesh(ext_mesh *m) {
   cudaFree(m->d_cell_verts);
   cudaFree(m->d_cell_edges);
   cudaFree(m->d_base_xy);
-  cudaFree(m->d_area2);
   cudaFree(m->d_cell_first);
   cudaFree(m->d_cell_layers);
   cudaFree(m->d_ent_lo);
@@ -309,20 +308,6 @@ static ext_status create_mesh(int32_t kind, int64_t nverts, int64_t ncells, cons
       e = cudaMemcpy(m->d_base_xy, base_xy_host, (size_t)nverts * 2 * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->has_xy = base_xy_host != nullptr;
-  if (e == cudaSuccess && base_xy_host && kind == EXT_TRI && ncells > 0) {
-    // |2A| of every base triangle, as fma(dx1, dy2, -(dx2 dy1)) so that the
-    // host compilers of both architectures round it alike
-    std::vector<double> a2((size_t)ncells);
-    for (int64_t c = 0; c < ncells; ++c) {
-      const int32_t *cv = cell_verts_host + 3 * c;
-      const double x0 = base_xy_host[2 * cv[0]], y0 = base_xy_host[2 * cv[0] + 1];
-      const double dx1 = base_xy_host[2 * cv[1]] - x0, dy1 = base_xy_host[2 * cv[1] + 1] - y0;
-      const double dx2 = base_xy_host[2 * cv[2]] - x0, dy2 = base_xy_host[2 * cv[2] + 1] - y0;
-      a2[(size_t)c] = std::fabs(std::fma(dx1, dy2, -(dx2 * dy1)));
-    }
-    if ((e = cudaMalloc(&m->d_area2, (size_t)ncells * sizeof(double))) == cudaSuccess)
-      e = cudaMemcpy(m->d_area2, a2.data(), (size_t)ncells * sizeof(double), cudaMemcpyHostToDevice);
-  }
   if (e == cudaSuccess && kind == EXT_TRI && !var && nverts > 0 && ncells > 0) {
     std::vector<int32_t> vrow, vnbr, vcrow, vcells;
     std::vector<int2> vedge;
@@ -985,6 +970,7 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       if (h == 0 && v == 0) return ext_par_loop(mesh, EXT_K_MASS_P1P1, nargs, args, stream);
       MassTPLaunch p;
       memset(&p, 0, sizeof(p));
+      p.k1 = fp64_ones();
       p.ncells = C;
       p.layers = L;
       p.nh = h == 1 ? 1 : 3;
@@ -1002,7 +988,6 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.cell_layers = mesh->d_cell_layers;
       p.mean_layers = mesh->mean_layers;
       p.base_xy = mesh->has_xy ? mesh->d_base_xy : nullptr;
-      p.area2 = mesh->d_area2;
       p.ncoord = args[0].space->ndofs;
       p.overwrite = args[2].access == EXT_WRITE;
       p.hown = h != 0;

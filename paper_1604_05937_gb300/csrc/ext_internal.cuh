@@ -31,6 +31,31 @@ inline Fp64Ones fp64_ones() { return Fp64Ones{1.0, -1.0, -0.0}; }
 __device__ __forceinline__ double fmul(double a, double b, const Fp64Ones &k) { return fma(a, b, k.mzero); }
 __device__ __forceinline__ double fadd(double a, double b, const Fp64Ones &k) { return fma(a, k.one, b); }
 __device__ __forceinline__ double fsub(double a, double b, const Fp64Ones &k) { return fma(b, k.mone, a); }
+
+// Programmatic dependent launch: a kernel started by launch_dependent may
+// begin (its launch and block dispatch overlapping the tail of the kernel
+// before it in the stream) before that kernel has finished; it must wait here
+// before it reads anything the earlier kernel writes.  Returns at once when
+// the kernel was launched the ordinary way.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kernel` on stream s as a programmatic dependent of the kernel
+// before it (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 #endif
 
 // Element recognised from a space's delta table.
@@ -50,7 +75,6 @@ struct ext_mesh {
   int32_t *d_cell_edges = nullptr;  // ncells x kind
   double *d_base_xy = nullptr;      // nverts x 2 (may be null)
   bool has_xy = false;              // base coordinates were given
-  double *d_area2 = nullptr;        // triangles with base coordinates: |2A| of every base cell
   // variable layers per column: cell c spans levels first[c] .. first[c] + layers[c]
   bool var = false;
   int32_t *d_cell_first = nullptr;   // ncells
@@ -237,10 +261,9 @@ struct MassTPLaunch {
   // filled by launch_mass_tp when it runs the flagged form
   const uint32_t *vflags = nullptr;      // bit d: coordinate DoF d verified straight
   const double *hlay = nullptr;          // |z_{l+1} - z_l| of the reference column
-  const double *area2 = nullptr;         // |2A| of every base cell from the base coordinates, if known
   const int32_t *badv = nullptr;         // optimistic form: per CTA of its first launch, a DoF not verified straight
   int32_t nbadv = 0;
-  Fp64Ones k1 = {1.0, -1.0, -0.0};       // products and sums of the closed forms issued as DFMA
+  Fp64Ones k1;                           // fp64_ones(): products and sums of the closed forms issued as DFMA
   bool overwrite = false;                // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
   bool hown = false;                     // horizontal DG0/DG1: every DoF belongs to one cell column
   bool vcont = false;                    // vertical CG1: layers l and l + 1 share their facet DoFs

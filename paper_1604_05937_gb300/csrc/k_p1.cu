@@ -1021,6 +1021,7 @@ __global__ void __launch_bounds__(256) k_p1_prep(const double *__restrict__ X, i
                                                  int64_t ncells, int64_t nsamp, int64_t stride,
                                                  const LevelCoef *__restrict__ tab, double *__restrict__ alpha,
                                                  unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t col = (int64_t)layers + 1;
@@ -1064,6 +1065,7 @@ __global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict_
                                                        const unsigned long long *__restrict__ minds,
                                                        double *__restrict__ Dv, double *__restrict__ Z0,
                                                        double *__restrict__ Bv, double *__restrict__ S) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   if (*mode != kNotFlat) return;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
@@ -1114,6 +1116,7 @@ __global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict
                                                        const double *__restrict__ S, double *__restrict__ wts,
                                                        int32_t nv, int64_t nent, FastDiv col,
                                                        const unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   const unsigned md = *mode;
   if (mode_cells(md)) return;
   const bool sig = (md & kNotFlat) != 0u;
@@ -1349,6 +1352,7 @@ __global__ void __launch_bounds__(256, EXT_VTAB_MINB) k_vsum_bulk(const double *
                                                                  Fp64Ones k1, unsigned int *err,
                                                                  const unsigned int *__restrict__ mode, SigmaCols sc,
                                                                  int64_t skip_step, unsigned wait_limit) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   // one instantiation per gather mode (flat: SIG = false); the other exits,
   // as both do in cell-loop mode
   const unsigned md = *mode;
@@ -1493,6 +1497,7 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
                                                                    Deferred dfr, unsigned int *err, Fp64Ones k1,
                                                                    const unsigned int *__restrict__ mode,
                                                                    bool flat_fused) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   constexpr int VU = EXT_VG_VU;
   const int lane = threadIdx.x & 31;
   if (*mode == 0u && flat_fused) return;  // k_vfused formed b
@@ -1581,6 +1586,7 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vfused(const double *
                                                                   double *__restrict__ b, int64_t n, FastDiv col,
                                                                   Deferred dfr, unsigned int *err, Fp64Ones k1,
                                                                   const unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   if (*mode != 0u) return;  // terrain-following or cell-loop mode
   const int lane = threadIdx.x & 31;
   constexpr int kOut = 30;
@@ -1648,6 +1654,9 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vfused(const double *
 #ifndef EXT_P1OPT_UF
 #define EXT_P1OPT_UF 2  // flag words per lane per flag chunk
 #endif
+#ifndef EXT_P1OPT_R
+#define EXT_P1OPT_R 2  // 32-DoF blocks per gather chunk (it writes 32 R - 2 DoFs; 1M x 100: R = 1, 2, 4, 8 took 1.07, 1.04, 1.21, 1.15 ms)
+#endif
 
 // Optimistic flat gather (flat mode, WRITE access).  The one-pass flat
 // gather of k_vfused checks, for every row entry it reads, that the DoF sits
@@ -1655,11 +1664,12 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vfused(const double *
 // b = Mh (x) Mv f is formed for every DoF as if the whole mesh were straight
 // and flat (g_{a,m} = the row of a against f at level m, then
 // b_{a,m} = lo_m g_{a,m-1} + mid_m g_{a,m} + hi_m g_{a,m+1} by warp shuffles,
-// 30 DoFs per 32-lane window), while the same launch sets one straightness
-// bit per coordinate DoF (x, y of its column's level 0 and z of its level in
-// column 0, bitwise), one bit per vertex column holding a DoF that fails, and
-// one word per CTA saying whether it saw such a DoF.  The warps take flag
-// chunks and gather windows interleaved in proportion to their counts, so
+// each g formed once within a chunk of 32 R DoFs), while the same launch
+// sets one straightness bit per coordinate DoF (x, y of its column's level 0
+// and z of its level in column 0, bitwise), one bit per vertex column holding
+// a DoF that fails, and one word per CTA saying whether it saw such a DoF.
+// The warps take flag chunks and gather chunks interleaved in proportion to
+// their counts, so
 // the HBM-bound flag work runs beside the FP64-bound gather on every SM, and
 // the coordinate field is read once.  k_p1_fix then records, for the general
 // path, every DoF whose stencil (the vertex row's columns at levels m - 1 ..
@@ -1674,7 +1684,8 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
              double *__restrict__ b, uint32_t n, FastDiv col, uint32_t *__restrict__ flags,
              uint32_t *__restrict__ vbad, int32_t *__restrict__ badv, Fp64Ones k1,
              const unsigned int *__restrict__ mode, int64_t nfc, int64_t ngc) {
-  constexpr int UF = EXT_P1OPT_UF, kOut = 30;
+  grid_dep_wait();  // a programmatic dependent of the launch before it
+  constexpr int UF = EXT_P1OPT_UF, R = EXT_P1OPT_R;
   __shared__ int cta_bad;
   if (*mode != 0u) return;  // terrain-following or cell-loop mode (k_p1_fix exits too)
   if (threadIdx.x == 0) cta_bad = 0;
@@ -1736,39 +1747,53 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
         if (v[u] && !ok) atomicOr(vbad + (qv[u] >> 5), 1u << (qv[u] & 31u));
       }
     } else {
-      // window (j - fcur): lanes hold DoFs start - 1 .. start + 30, lanes 1..30 write
-      const int64_t start = (j - fcur) * kOut;
-      const int64_t d = start - 1 + lane;
-      const bool in = d >= 0 && d < (int64_t)n;
-      int r0 = 0, deg = 0;
-      uint32_t m = 0;
-      double acc = k1.mzero;
-      double2 c01 = make_double2(0.0, 0.0), c23 = make_double2(0.0, 0.0);
-      if (in) {
-        const uint32_t q = fdiv((uint32_t)d, col);
-        m = (uint32_t)d - q * col.d;
-        r0 = __ldg(vrow + q);
-        deg = __ldg(vrow + q + 1) - r0;
-        c01 = __ldg(reinterpret_cast<const double2 *>(tab + m));      // z_m, |h_{m-1}|
-        c23 = __ldg(reinterpret_cast<const double2 *>(tab + m) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
-      }
-      const int dmx = __reduce_max_sync(kFull, deg);
-#pragma unroll 4
-      for (int t = 0; t < dmx; ++t) {
-        double ev = 0.0, fv = 0.0;
-        if (t < deg) {
-          ev = __ldg(wts + r0 + t);
-          fv = __ldg(f + (uint32_t)__ldg(vnbr + r0 + t) + m);
+      // gather chunk (j - fcur): R blocks of 32 consecutive DoFs d = cs - 1 +
+      // 32 t + lane; g of block t and of block t - 1 (kept in gprev) give the
+      // output DoF e = d - 1 of every lane: g(e - 1), g(e), g(e + 1) from
+      // lanes - 2, - 1 and 0 (the previous block's lanes 30 and 31 below lane
+      // 2).  The chunk writes DoFs cs .. cs + 32 R - 3 and forms g of each
+      // once, except for the two DoFs it shares with the next chunk.
+      const int64_t cs = (j - fcur) * (int64_t)(32 * R - 2);
+      double gprev = 0.0;
+#pragma unroll 1
+      for (int t = 0; t < R; ++t) {
+        const int64_t d = cs - 1 + 32 * t + lane;
+        int r0 = 0, deg = 0;
+        uint32_t m = 0;
+        double acc = k1.mzero;
+        if (d >= 0 && d < (int64_t)n) {
+          const uint32_t q = fdiv((uint32_t)d, col);
+          m = (uint32_t)d - q * col.d;
+          r0 = __ldg(vrow + q);
+          deg = __ldg(vrow + q + 1) - r0;
         }
-        acc = fma(ev, fv, acc);
+        const int dmx = __reduce_max_sync(kFull, deg);
+#pragma unroll 4
+        for (int u = 0; u < dmx; ++u) {
+          double ev = 0.0, fv = 0.0;
+          if (u < deg) {
+            ev = __ldg(wts + r0 + u);
+            fv = __ldg(f + (uint32_t)__ldg(vnbr + r0 + u) + m);
+          }
+          acc = fma(ev, fv, acc);
+        }
+        const double g1 = __shfl_up_sync(kFull, acc, 1), g2 = __shfl_up_sync(kFull, acc, 2);
+        const double p30 = __shfl_sync(kFull, gprev, 30), p31 = __shfl_sync(kFull, gprev, 31);
+        gprev = acc;
+        const int64_t e = d - 1;
+        if (e >= cs && e < (int64_t)n) {
+          const uint32_t qe = fdiv((uint32_t)e, col);
+          const uint32_t me = (uint32_t)e - qe * col.d;
+          const double2 c01 = __ldg(reinterpret_cast<const double2 *>(tab + me));      // z_m, |h_{m-1}|
+          const double2 c23 = __ldg(reinterpret_cast<const double2 *>(tab + me) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
+          const double gm = lane >= 2 ? g2 : (lane == 1 ? p31 : p30);  // g(e - 1)
+          const double g0 = lane >= 1 ? g1 : p31;                      // g(e)
+          // vertical neighbours beyond the column's ends are cleared bitwise
+          const double gmm = __longlong_as_double(__double_as_longlong(gm) & (me == 0 ? 0LL : -1LL));
+          const double gpm = __longlong_as_double(__double_as_longlong(acc) & (me + 1 == col.d ? 0LL : -1LL));
+          b[e] = fma(c01.y, gmm, fma(c23.x, g0, fmul(c23.y, gpm, k1)));
+        }
       }
-      // vertical neighbours (lanes -1 and +1, the same column unless at its end)
-      const bool lo_end = m == 0, hi_end = m + 1 == col.d;
-      const double gl = __shfl_up_sync(kFull, acc, 1), gr = __shfl_down_sync(kFull, acc, 1);
-      const double glm = __longlong_as_double(__double_as_longlong(gl) & (lo_end ? 0LL : -1LL));
-      const double grm = __longlong_as_double(__double_as_longlong(gr) & (hi_end ? 0LL : -1LL));
-      const double res = fma(c01.y, glm, fma(c23.x, acc, fmul(c23.y, grm, k1)));
-      if (lane >= 1 && lane <= kOut && in) b[d] = res;
     }
   }
   if (bad && lane == 0) cta_bad = 1;
@@ -1793,6 +1818,7 @@ __global__ void __launch_bounds__(256) k_p1_fix(const int32_t *__restrict__ vrow
                                                 const int32_t *__restrict__ badv, int32_t nbadv, uint32_t nverts,
                                                 FastDiv col, Deferred dfr, unsigned int *err,
                                                 const unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   if (*mode != 0u) return;
   int any = 0;
   for (int i = threadIdx.x; i < nbadv; i += blockDim.x) any |= __ldg(badv + i);
@@ -1833,6 +1859,7 @@ __global__ void __launch_bounds__(256) k_p1_fix(const int32_t *__restrict__ vrow
 template <bool INC>
 __global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Launch p, Deferred dfr, FastDiv col,
                                                                  Fp64Ones k1) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const unsigned int n = min(*dfr.count, dfr.cap);
@@ -1893,6 +1920,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_vgather_general(const MassP1Lau
 // straight extrusion, which the gather form handles) makes the kernel exit.
 __global__ void __launch_bounds__(kWarps * 32, EXT_P1C_MINB) k_p1_cells(const MassP1Launch p, int cpw, Fp64Ones k1,
                                                                        const unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
   if (mode && !mode_cells(*mode)) return;  // a gather mode formed b
   __shared__ ColInfo cols[kWarps][kMaxCols];
   __shared__ double kk[kWarps][kMaxCols][2];  // k2, k6 of each column
@@ -2111,6 +2139,10 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       e = cudaGetLastError();
     }
   } else if (e == cudaSuccess && gather) {
+    // every kernel after the first is a programmatic dependent of the one before it
+    auto dep = [&e](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+    };
     static int res_vtab = 0, res_vg[2] = {0, 0}, res_vb = 0;
     static int64_t skip_step = -2;
     if (skip_step == -2) {
@@ -2138,30 +2170,30 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     if (gp > (int64_t)sms * 8) gp = (int64_t)sms * 8;
     if (gp * 256 < (int64_t)p.layers + 1) gp = ((int64_t)p.layers + 1 + 255) / 256;
     k_p1_levels<<<(unsigned)((p.layers + 1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab, mode, minds);
-    k_p1_prep<<<(unsigned)gp, 256, 0, s>>>(p.X, p.layers, p.cmap, p.ncells, nsamp, stride, tab, alpha, mode);
+    dep(launch_dependent(k_p1_prep, dim3((unsigned)gp), dim3(256), 0, s, p.X, p.layers, p.cmap, p.ncells, nsamp,
+                         stride, tab, alpha, mode));
     int64_t gs = ((nv > (int64_t)p.ncells ? nv : (int64_t)p.ncells) + 255) / 256;
     if (gs > (int64_t)sms * 8) gs = (int64_t)sms * 8;
-    k_p1_sigma_prep<<<(unsigned)(gs > 0 ? gs : 1), 256, 0, s>>>(p.X, p.layers, p.cmap, p.ncells, nv, mode, minds,
-                                                                 const_cast<double *>(sc.Dv),
-                                                                 const_cast<double *>(sc.Z0),
-                                                                 const_cast<double *>(sc.Bv), Sc);
+    dep(launch_dependent(k_p1_sigma_prep, dim3((unsigned)(gs > 0 ? gs : 1)), dim3(256), 0, s, p.X, p.layers, p.cmap,
+                         p.ncells, nv, mode, minds, const_cast<double *>(sc.Dv), const_cast<double *>(sc.Z0),
+                         const_cast<double *>(sc.Bv), Sc));
     int64_t gw = (nv + p.nvent + 255) / 256;
     if (gw > (int64_t)sms * 16) gw = (int64_t)sms * 16;
-    k_p1_rowweights<<<(unsigned)(gw > 0 ? gw : 1), 256, 0, s>>>(p.vrow, p.vnbr, p.vedge, p.vcrow, p.vcells, alpha,
-                                                                 sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode);
+    dep(launch_dependent(k_p1_rowweights, dim3((unsigned)(gw > 0 ? gw : 1)), dim3(256), 0, s, p.vrow, p.vnbr,
+                         p.vedge, p.vcrow, p.vcells, alpha, sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode));
     const bool fused = p1_flat() == EXT_P1_FLAT_FUSED;
     if (opt) {
       const int64_t nfc = ((n + 31) / 32 + EXT_P1OPT_UF - 1) / EXT_P1OPT_UF;
-      const int64_t ngc = (n + 29) / 30;
+      const int64_t ngc = (n + 32 * EXT_P1OPT_R - 3) / (32 * EXT_P1OPT_R - 2);
       int64_t g = (nfc + ngc + 7) / 8;
       if (g > go) g = go;
       if (g < 1) g = 1;
-      k_p1_opt<<<(unsigned)g, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, (uint32_t)n, col, oflags, vbad,
-                                           badv, k1, mode, nfc, ngc);
+      dep(launch_dependent(k_p1_opt, dim3((unsigned)g), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b,
+                           (uint32_t)n, col, oflags, vbad, badv, k1, mode, nfc, ngc));
       int64_t gx = (nv + 255) / 256;
       if (gx > (int64_t)sms * 8) gx = (int64_t)sms * 8;
-      k_p1_fix<<<(unsigned)(gx > 0 ? gx : 1), 256, 0, s>>>(p.vrow, p.vnbr, oflags, vbad, badv, (int32_t)g,
-                                                             (uint32_t)nv, col, dfr, p.err, mode);
+      dep(launch_dependent(k_p1_fix, dim3((unsigned)(gx > 0 ? gx : 1)), dim3(256), 0, s, p.vrow, p.vnbr, oflags, vbad,
+                           badv, (int32_t)g, (uint32_t)nv, col, dfr, p.err, mode));
     } else if (fused) {
       static int res_vf[2] = {0, 0};
       const int rf = p.overwrite ? resident_ctas(k_vfused<false>, res_vf[0]) : resident_ctas(k_vfused<true>, res_vf[1]);
@@ -2169,9 +2201,11 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       if (gf > (int64_t)rf * sms) gf = (int64_t)rf * sms;
       if (gf < 1) gf = 1;
       if (p.overwrite)
-        k_vfused<false><<<(unsigned)gf, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, n, col, dfr, p.err, k1, mode);
+        dep(launch_dependent(k_vfused<false>, dim3((unsigned)gf), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab,
+                             p.b, n, col, dfr, p.err, k1, mode));
       else
-        k_vfused<true><<<(unsigned)gf, 256, 0, s>>>(p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b, n, col, dfr, p.err, k1, mode);
+        dep(launch_dependent(k_vfused<true>, dim3((unsigned)gf), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab,
+                             p.b, n, col, dfr, p.err, k1, mode));
     }
     if (EXT_VSUM_BULK) {
       const int rb = resident_ctas(k_vsum_bulk<false>, res_vb);
@@ -2179,24 +2213,29 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       if (gb > (int64_t)rb * sms) gb = (int64_t)rb * sms;
       if (gb < 1) gb = 1;
       if (!fused && !opt)
-        k_vsum_bulk<false><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
-      k_vsum_bulk<true><<<(unsigned)gb, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, p.err, mode, sc, skip, wait_limit);
+        dep(launch_dependent(k_vsum_bulk<false>, dim3((unsigned)gb), dim3(256), 0, s, p.X, p.f, tab, W, n, col, k1,
+                             p.err, mode, sc, skip, wait_limit));
+      dep(launch_dependent(k_vsum_bulk<true>, dim3((unsigned)gb), dim3(256), 0, s, p.X, p.f, tab, W, n, col, k1, p.err,
+                           mode, sc, skip, wait_limit));
     } else {
       if (!fused && !opt) k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
       k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
     }
     if (p.overwrite) {
-      k_vgather<false><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode,
-                                                    fused || opt);
+      dep(launch_dependent(k_vgather<false>, dim3((unsigned)gg), dim3(256), 0, s, W, p.vrow, p.vnbr, wts, p.b, n, col,
+                           dfr, p.err, k1, mode, fused || opt));
       const int r = resident_ctas(k_vgather_general<false>, res_vgg[0]);
-      k_vgather_general<false><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
+      dep(launch_dependent(k_vgather_general<false>, dim3((unsigned)(sms * r)), dim3(kWarps * 32), 0, s, p, dfr, col,
+                           k1));
     } else {
-      k_vgather<true><<<(unsigned)gg, 256, 0, s>>>(W, p.vrow, p.vnbr, wts, p.b, n, col, dfr, p.err, k1, mode, fused);
+      dep(launch_dependent(k_vgather<true>, dim3((unsigned)gg), dim3(256), 0, s, W, p.vrow, p.vnbr, wts, p.b, n, col,
+                           dfr, p.err, k1, mode, fused));
       const int r = resident_ctas(k_vgather_general<true>, res_vgg[1]);
-      k_vgather_general<true><<<(unsigned)(sms * r), kWarps * 32, 0, s>>>(p, dfr, col, k1);
+      dep(launch_dependent(k_vgather_general<true>, dim3((unsigned)(sms * r)), dim3(kWarps * 32), 0, s, p, dfr, col,
+                           k1));
     }
-    if (probe) k_p1_cells<<<(unsigned)gc, kWarps * 32, 0, s>>>(p, cpw, k1, mode);
-    e = cudaGetLastError();
+    if (probe) dep(launch_dependent(k_p1_cells, dim3((unsigned)gc), dim3(kWarps * 32), 0, s, p, cpw, k1, mode));
+    dep(cudaGetLastError());
   } else if (e == cudaSuccess) {
     const int res = var ? resident_ctas(k_mass_cells<true, false>, res_cells[1])
                         : (factored ? resident_ctas(k_mass_cells<false, true>, res_cells[0])

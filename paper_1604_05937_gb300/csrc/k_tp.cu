@@ -171,6 +171,7 @@ template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = fa
 __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB : 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
   if (FIX) {  // no CTA of the optimistic launch saw a coordinate DoF that is not straight
+    grid_dep_wait();  // launched as a dependent of that launch
     int any = 0;
     for (int i = threadIdx.x; i < p.nbadv; i += blockDim.x) any |= __ldg(p.badv + i);
     if (!__syncthreads_or(any)) return;
@@ -372,8 +373,9 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
 // flags over the coordinate field, then the element vectors) have no data
 // dependence when the element vector is taken in closed form for every prism
 // on the assumption that it is straight: the column's |2A| comes from the
-// mesh's base coordinates and the layer's height from the reference column
-// (vertex 0's, coordinate DoFs 0 .. layers).  So one launch does both, the
+// base coordinates (k_tp_area2, in every launch) and the layer's height from
+// the reference column (vertex 0's, coordinate DoFs 0 .. layers).  So one
+// launch does both, the
 // same warps taking flag chunks and element chunks interleaved in proportion
 // to their counts, and the HBM-bound flag work runs beside the FP64-bound
 // element work on every SM.  A fix-up launch (k_mass_tp with FIX) then
@@ -381,6 +383,25 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
 // general rule, and returns at once when no CTA of this launch found such a
 // coordinate DoF.  The result is the flagged form's: each DoF is written by
 // the closed form exactly when its prism is verified straight.
+//
+// |2A| of every base cell, formed in every launch from the base coordinates
+// the straightness flags are checked against (the vertex of a level-0
+// coordinate DoF d is d / (layers + 1)): a prism whose six flags are set has
+// exactly these x, y at both of its levels.
+__global__ void __launch_bounds__(256) k_tp_area2(const int32_t *__restrict__ cmap, const double *__restrict__ xy,
+                                                  FastDiv colv, int64_t ncells, double *__restrict__ area2) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+    double x[3], y[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double *bp = xy + 2 * (size_t)fdiv((uint32_t)__ldg(cmap + 6 * c + 2 * a), colv);
+      x[a] = __ldg(bp + 0);
+      y[a] = __ldg(bp + 1);
+    }
+    area2[c] = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]));
+  }
+}
+
 // flag words per lane per flag chunk, items per lane per element chunk (for
 // DG0 x DG0 sized so that 4 CTAs of 256 threads stay resident per SM; 2 CTAs
 // for the element vectors of 2, 3 and 6 DoFs)
@@ -389,8 +410,8 @@ __host__ __device__ constexpr int dgdg_ui(int k) { return k == 1 ? EXT_TP_DGDG_U
 
 template <int NH, int NV>
 __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB : 2)
-    k_tp_dgdg(const MassTPLaunch p, uint32_t *__restrict__ flags, int32_t *__restrict__ badv, FastDiv colv,
-              FastDiv lay, int64_t nfc, int64_t nic) {
+    k_tp_dgdg(const MassTPLaunch p, const double *__restrict__ area2, uint32_t *__restrict__ flags,
+              int32_t *__restrict__ badv, FastDiv colv, FastDiv lay, int64_t nfc, int64_t nic) {
   constexpr int UF = dgdg_uf(NH * NV), UI = dgdg_ui(NH * NV), K = NH * NV;
   // level tables of the reference column: z at every level, scaled heights
   // hs[l] = |z_{l+1} - z_l| x (the element's constant)
@@ -407,7 +428,7 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB :
   const uint32_t nitems = (uint32_t)(p.ncells * (int64_t)p.layers);
   const int64_t nch = nfc + nic;
   const int64_t wstride = (int64_t)gridDim.x * kWarps;
-  bool bad = false;
+  bool bad = false, waited = false;
   // chunk j is flag chunk fb = floor(j nfc / nch) when floor((j + 1) nfc / nch)
   // > fb, i.e. when r + nfc >= nch with r = j nfc - fb nch, else element
   // chunk j - fb (the flag chunks before it are fb); fb and r advance by the
@@ -459,6 +480,10 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB :
         }
       }
     } else {
+      if (!waited) {  // launched as a dependent of k_tp_area2: its |2A| must be complete
+        grid_dep_wait();
+        waited = true;
+      }
       const uint32_t i0 = (uint32_t)(j - fcur) * (uint32_t)(32 * UI) + (uint32_t)lane;
       int32_t dof[UI][K];
       double a2[UI], h[UI], f[UI][K];
@@ -471,7 +496,7 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB :
         if (v[u]) {
           const uint32_t c = fdiv(it, lay);
           const int l = (int)(it - c * lay.d);
-          a2[u] = __ldg(p.area2 + c);
+          a2[u] = __ldg(area2 + c);
           h[u] = hs[l];
           const int32_t *row = p.fmap + (size_t)c * (uint32_t)p.k;
 #pragma unroll
@@ -520,13 +545,12 @@ int64_t dgdg_grid(const MassTPLaunch &p, size_t smem) {
 }
 
 template <int NH, int NV>
-cudaError_t launch_tp_dgdg(const MassTPLaunch &p, uint32_t *flags, int32_t *badv, int64_t blocks, size_t smem,
-                           cudaStream_t s) {
+cudaError_t launch_tp_dgdg(const MassTPLaunch &p, const double *area2, uint32_t *flags, int32_t *badv, int64_t blocks,
+                           size_t smem, cudaStream_t s) {
   const int64_t nfc = ((p.ncoord + 31) / 32 + dgdg_uf(NH * NV) - 1) / dgdg_uf(NH * NV);
   const int64_t nic = (p.ncells * (int64_t)p.layers + 32 * dgdg_ui(NH * NV) - 1) / (32 * dgdg_ui(NH * NV));
-  k_tp_dgdg<NH, NV><<<(unsigned)blocks, kWarps * 32, smem, s>>>(p, flags, badv, make_fastdiv((uint32_t)(p.layers + 1)),
-                                                                make_fastdiv((uint32_t)p.layers), nfc, nic);
-  return cudaGetLastError();
+  return launch_dependent(k_tp_dgdg<NH, NV>, dim3((unsigned)blocks), dim3(kWarps * 32), smem, s, p, area2, flags,
+                          badv, make_fastdiv((uint32_t)(p.layers + 1)), make_fastdiv((uint32_t)p.layers), nfc, nic);
 }
 
 template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI, bool WR = false, bool FIX = false>
@@ -549,6 +573,8 @@ cudaError_t launch_tp(const MassTPLaunch &p, cudaStream_t s) {
     if (resident[slot] < 1) resident[slot] = 1;
   }
   if (blocks > (int64_t)resident[slot] * sms) blocks = (int64_t)resident[slot] * sms;
+  if (FIX) return launch_dependent(k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR, FIX>, dim3((unsigned)blocks),
+                                   dim3(kWarps * 32), 0, s, p, cpw);
   k_mass_tp<NH, NV, VAR, FLAGS, MULTI, WR, FIX><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
@@ -945,7 +971,7 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
     const char *ev = getenv("EXTMESH_TP_OPTIMISTIC");
     opt_env = (ev && ev[0] == '0') ? 0 : 1;
   }
-  const bool optimistic = want && opt_env == 1 && p.area2 && owned && !p.vcont && p.overwrite &&
+  const bool optimistic = want && opt_env == 1 && owned && !p.vcont && p.overwrite &&
                           p.layers >= EXT_TP_MULTI_LAYERS && p.layers <= EXT_TP_DGDG_MAX_LAYERS &&
                           items < 2147483647.0 && (double)p.ncoord < 2147483647.0;
   char *scr = nullptr;
@@ -959,7 +985,8 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
     else if (p.nv == 1) oblocks = dgdg_grid<3, 1>(p, smem);
     else oblocks = dgdg_grid<3, 2>(p, smem);
   }
-  const size_t sbytes = optimistic ? (sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255 : 2 * zbytes;
+  const size_t abytes = (sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255;
+  const size_t sbytes = optimistic ? ((sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255) + abytes : 2 * zbytes;
   if (want && cudaMallocAsync(reinterpret_cast<void **>(&scr), fbytes + sbytes, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: the plain form needs no scratch
     scr = nullptr;
@@ -969,12 +996,24 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
   q.vflags = flags;
   if (optimistic) {
-    int32_t *badv = reinterpret_cast<int32_t *>(scr + fbytes);
-    cudaError_t e;
-    if (p.nh == 1 && p.nv == 1) e = launch_tp_dgdg<1, 1>(q, flags, badv, oblocks, smem, s);
-    else if (p.nh == 1) e = launch_tp_dgdg<1, 2>(q, flags, badv, oblocks, smem, s);
-    else if (p.nv == 1) e = launch_tp_dgdg<3, 1>(q, flags, badv, oblocks, smem, s);
-    else e = launch_tp_dgdg<3, 2>(q, flags, badv, oblocks, smem, s);
+    double *area2 = reinterpret_cast<double *>(scr + fbytes);
+    int32_t *badv = reinterpret_cast<int32_t *>(scr + fbytes + abytes);
+    static int sms_a = 0;
+    if (sms_a == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms_a, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int64_t ga = (p.ncells + 255) / 256;
+    if (ga > (int64_t)sms_a * 8) ga = (int64_t)sms_a * 8;
+    k_tp_area2<<<(unsigned)ga, 256, 0, s>>>(p.cmap, p.base_xy, make_fastdiv((uint32_t)(p.layers + 1)), p.ncells, area2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      if (p.nh == 1 && p.nv == 1) e = launch_tp_dgdg<1, 1>(q, area2, flags, badv, oblocks, smem, s);
+      else if (p.nh == 1) e = launch_tp_dgdg<1, 2>(q, area2, flags, badv, oblocks, smem, s);
+      else if (p.nv == 1) e = launch_tp_dgdg<3, 1>(q, area2, flags, badv, oblocks, smem, s);
+      else e = launch_tp_dgdg<3, 2>(q, area2, flags, badv, oblocks, smem, s);
+    }
     q.badv = badv;
     q.nbadv = (int32_t)oblocks;
     if (e == cudaSuccess) e = launch_tp_kind<false, true, true, true, true>(q, s);
