@@ -979,7 +979,8 @@ __device__ __forceinline__ double sigma_at(const double *__restrict__ X, int lay
 
 // Level tables (one thread per level, before the probe): tab[m] from the
 // heights of column 0, tab[layers + 1 + m] from its sigma; the smallest sigma
-// spacing (bit pattern of a positive double, atomic min, in *minds); bit 1 of
+// spacing (the complement of the bit pattern of a positive double, atomic max
+// from the cleared word, in *minds); bit 1 of
 // *mode when sigma does not increase (or D_0 is not positive).
 __global__ void __launch_bounds__(256) k_p1_levels(const double *__restrict__ X, int layers,
                                                    LevelCoef *__restrict__ tab, unsigned int *__restrict__ mode,
@@ -1007,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_p1_levels(const double *__restrict__ X,
   tab[col + m] = cs;
   if (m < layers) {
     if (!(sh > 0.0)) atomicOr(mode, kNotSigma);  // also catches NaN (D_0 = 0)
-    else atomicMin(minds, (unsigned long long)__double_as_longlong(sh));
+    else atomicMax(minds, ~(unsigned long long)__double_as_longlong(sh));
   }
 }
 
@@ -1070,7 +1071,7 @@ __global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict_
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t col = (int64_t)layers + 1;
-  const double gap = __longlong_as_double((long long)*minds);
+  const double gap = __longlong_as_double((long long)~*minds);
   for (int64_t v = gid; v < nv; v += gstride) {
     const double z0 = __ldg(X + 3 * v * col + 2);
     const double zl = __ldg(X + 3 * (v * col + layers) + 2);
@@ -1097,10 +1098,10 @@ __global__ void __launch_bounds__(256) k_p1_sigma_prep(const double *__restrict_
   }
 }
 
-// Row weights (gather modes only).  Flat extrusion, Mh: entry (a, j) = the
-// sum of alpha over the one or two cells on edge (a, j), ascending (one
-// thread per entry); the diagonal is the sum of 2 alpha over the cells
-// around a (one thread per vertex).
+// Row weights (gather modes only), one thread per vertex row.  Flat
+// extrusion, Mh: entry (a, j) = the sum of alpha over the one or two cells on
+// edge (a, j), ascending; the diagonal, the sum of 2 alpha over the cells
+// around a, is formed as the sum of the row's off-diagonal entries.
 // Terrain-following levels, Hd: a prism's heights are h_k = (sigma_{l+1} -
 // sigma_l) D_k, so its element matrix under the 6-point rule is the column
 // factor times (alpha_c / 54) sum_k D_k T_{aa'k}, with T = 54 sum_t lambda_a
@@ -1120,41 +1121,37 @@ __global__ void __launch_bounds__(256) k_p1_rowweights(const int32_t *__restrict
   const unsigned md = *mode;
   if (mode_cells(md)) return;
   const bool sig = (md & kNotFlat) != 0u;
-  // one thread per row entry (off-diagonal weights) and one per vertex (the
-  // diagonal), all independent
-  const int64_t total = nent + nv;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < nent) {
-      // flat: an off-diagonal entry on its own (terrain-following: the vertex
-      // thread forms its row, which needs the row's D_a)
-      if (sig) continue;
-      const int2 e = __ldg(vedge + i);
-      if (e.x < 0) continue;  // a diagonal entry
-      wts[i] = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
-    } else {
-      const int64_t a = i - nent;
-      const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
-      double diag = 0.0;
-      if (!sig) {
-        for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) diag += 2.0 * __ldg(alpha + __ldg(vcells + t));
-      } else {
-        const double Da = __ldg(Dv + a);
-        for (int32_t t = t0 + 1; t < t1; ++t) {
-          const int2 e = __ldg(vedge + t);
-          const double Dj = __ldg(Dv + fdiv((uint32_t)__ldg(vnbr + t), col));
-          const double dd = 9.0 * (Da + Dj);
-          double w = __ldg(alpha + e.x) * fma(12.0, __ldg(S + e.x), dd);
-          if (e.y >= 0) w = fma(__ldg(alpha + e.y), fma(12.0, __ldg(S + e.y), dd), w);
-          wts[t] = w * (1.0 / 54.0);
-        }
-        for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) {
-          const int32_t c = __ldg(vcells + t);
-          diag = fma(__ldg(alpha + c), fma(21.0, __ldg(S + c), 45.0 * Da), diag);
-        }
-        diag *= 1.0 / 54.0;
+  // one thread per vertex row; flat: the diagonal is the sum of the row's
+  // off-diagonal weights (each cell around a lies on two of a's edges, so
+  // that sum is sum_c 2 alpha_c), the row's loads all independent
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nv; a += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t0 = __ldg(vrow + a), t1 = __ldg(vrow + a + 1);
+    double diag = 0.0;
+    if (!sig) {
+#pragma unroll 4
+      for (int32_t t = t0 + 1; t < t1; ++t) {
+        const int2 e = __ldg(vedge + t);
+        const double w = e.y >= 0 ? __ldg(alpha + e.x) + __ldg(alpha + e.y) : __ldg(alpha + e.x);
+        wts[t] = w;
+        diag += w;
       }
-      wts[t0] = diag;
+    } else {
+      const double Da = __ldg(Dv + a);
+      for (int32_t t = t0 + 1; t < t1; ++t) {
+        const int2 e = __ldg(vedge + t);
+        const double Dj = __ldg(Dv + fdiv((uint32_t)__ldg(vnbr + t), col));
+        const double dd = 9.0 * (Da + Dj);
+        double w = __ldg(alpha + e.x) * fma(12.0, __ldg(S + e.x), dd);
+        if (e.y >= 0) w = fma(__ldg(alpha + e.y), fma(12.0, __ldg(S + e.y), dd), w);
+        wts[t] = w * (1.0 / 54.0);
+      }
+      for (int32_t t = __ldg(vcrow + a); t < __ldg(vcrow + a + 1); ++t) {
+        const int32_t c = __ldg(vcells + t);
+        diag = fma(__ldg(alpha + c), fma(21.0, __ldg(S + c), 45.0 * Da), diag);
+      }
+      diag *= 1.0 / 54.0;
     }
+    wts[t0] = diag;
   }
 }
 
@@ -1688,6 +1685,7 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
   constexpr int UF = EXT_P1OPT_UF, R = EXT_P1OPT_R;
   __shared__ int cta_bad;
   if (*mode != 0u) return;  // terrain-following or cell-loop mode (k_p1_fix exits too)
+  if (blockIdx.x == 0 && threadIdx.x == 0) flags[(n + 31) / 32] = 0u;  // the zero word past the end
   if (threadIdx.x == 0) cta_bad = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -2122,12 +2120,9 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
   dfr.cap = cap;
   uint32_t *oflags = reinterpret_cast<uint32_t *>(sg0 + sbytes + lbytes);
   int32_t *badv = reinterpret_cast<int32_t *>(sg0 + sbytes + lbytes + fbytes);
-  // the counter and the mode word start at zero (and the vertex-column bits
-  // of the optimistic gather), the smallest sigma spacing at a large positive
-  // double (bytes 0x7f)
+  // the counter, the mode word and the smallest sigma spacing start at zero,
+  // and so do the vertex-column bits of the optimistic gather
   cudaError_t e = cudaMemsetAsync(scr0, 0, 256 + vbbytes, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(scr0 + 8, 0x7f, 8, s);
-  if (e == cudaSuccess && opt) e = cudaMemsetAsync(oflags + (n + 31) / 32, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess && factored && abytes) e = cudaMemsetAsync(A, 0, abytes, s);
   const FastDiv col = make_fastdiv((uint32_t)(var ? 1 : p.layers + 1));
   const int rc = resident_ctas(k_p1_cells, res_p1c);
@@ -2177,8 +2172,8 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     dep(launch_dependent(k_p1_sigma_prep, dim3((unsigned)(gs > 0 ? gs : 1)), dim3(256), 0, s, p.X, p.layers, p.cmap,
                          p.ncells, nv, mode, minds, const_cast<double *>(sc.Dv), const_cast<double *>(sc.Z0),
                          const_cast<double *>(sc.Bv), Sc));
-    int64_t gw = (nv + p.nvent + 255) / 256;
-    if (gw > (int64_t)sms * 16) gw = (int64_t)sms * 16;
+    int64_t gw = (nv + 255) / 256;
+    if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
     dep(launch_dependent(k_p1_rowweights, dim3((unsigned)(gw > 0 ? gw : 1)), dim3(256), 0, s, p.vrow, p.vnbr,
                          p.vedge, p.vcrow, p.vcells, alpha, sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode));
     const bool fused = p1_flat() == EXT_P1_FLAT_FUSED;
