@@ -1053,7 +1053,9 @@ def run_cfg6(args, rank, world, local):
     launches = 0
     clk = ClockSampler(local)
     clk.start()
-    for order in ("rcm", "random"):
+    orders = args.orders.split(",") if args.orders else ["rcm", "random"]
+    only = set(args.spaces.split(",")) if args.spaces else None
+    for order in orders:
         results[order] = {}
         for L in layer_set:
             n = max(2, int(round(math.sqrt(15e6 / (2 * L)))))
@@ -1064,6 +1066,8 @@ def run_cfg6(args, rank, world, local):
             X = E.extrude_coords(gm, cs)
             row = {"base_cells": C, "cells": C * L}
             for name, delta, ops in TP_SPACES:
+                if only is not None and name not in only:
+                    continue
                 sp = E.Space(gm, delta)
                 f = torch.rand(sp.ndofs, dtype=torch.float64, device=dev)
                 b = sp.zeros()
@@ -1091,9 +1095,10 @@ def run_cfg6(args, rank, world, local):
     clocks = clk.stop()
     if rank != 0:
         return None
-    top = results["rcm"][100] if 100 in results["rcm"] else results["rcm"][layer_set[-1]]
-    tot_b = sum(top[nm]["gbs"] * top[nm]["ms"] for nm, _, _ in TP_SPACES)
-    tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES)
+    first = results[orders[0]]
+    top = first[100] if 100 in first else first[layer_set[-1]]
+    tot_b = sum(top[nm]["gbs"] * top[nm]["ms"] for nm, _, _ in TP_SPACES if nm in top)
+    tot_t = sum(top[nm]["ms"] for nm, _, _ in TP_SPACES if nm in top)
     extra = {"spaces": results, "hbm_peak_gbs": hbm, "peak_kind": hbm_kind, "fp64_nominal_gops": round(nominal, 1),
              "fp64_rates_gops": {k: round(v, 1) for k, v in rates.items()},
              "fp64_ops_per_unit": {nm: (ops if ops is not None else P1_OPS_NOTE) for nm, _, ops in TP_SPACES},
@@ -1471,6 +1476,8 @@ def main():
     ap.add_argument("--hostlink", action="store_true",
                     help="measure the host link (pinned buffers on each NUMA node) instead of a workload")
     ap.add_argument("--sweep", default=None, help="config 6: comma-separated layer counts")
+    ap.add_argument("--spaces", default=None, help="config 6: comma-separated spaces (e.g. DG0xDG0); default all nine")
+    ap.add_argument("--orders", default=None, help="config 6: comma-separated base orders (rcm, random); default both")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
