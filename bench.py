@@ -75,9 +75,10 @@ DG1_DELTA = (0, 0, 0, 0, 0, 6)
 #            3 L2 atomic adds per item;
 #   single   13 per item (below a million items).
 P1_PRISM_OPS = {"vertical": 42, "general": 132}
-# kernels of one launch (WRITE access: the flat gather runs optimistic, one
-# pass and a fix-up launch; the split and one-pass-checked flat forms launch 9)
-P1_KERNELS = {"gather": 10, "gather-split": 9, "gather-sigma": 10, "cells": 10, "cells-forced": 1, "factored": 4,
+# kernels of one launch: the gather modes' launch runs 9 (WRITE access: the
+# optimistic one pass and its fix-up in place of the vertex passes of the
+# split form that INC access runs; the one-pass checked form also 9)
+P1_KERNELS = {"gather": 9, "gather-split": 9, "gather-sigma": 9, "cells": 9, "cells-forced": 1, "factored": 4,
               "plain": 3, "var": 3, "single": 1}
 CELL_ATOMICS_PER_ITEM = 3
 P1_SPLIT_MIN_ITEMS = 1_000_000
@@ -543,14 +544,15 @@ def report(args, world, m, L, vb, vb_paper, ms, k_rhs, k_mass, k_int, clocks, e2
                            f"{main['fp64_ops']} per launch")
         else:
             label = ("terrain-following gather: the probe found vertical columns with z = z0 + sigma_l D(x, y), so "
-                     "M = Hd (x) Mv(sigma) with Hd the depth-weighted P1 mass matrix of the base; every DoF checked "
-                     "against that model within 2^-42 D min(sigma spacing)")
+                     "M = Hd (x) Mv(sigma) with Hd the depth-weighted P1 mass matrix of the base, formed in one "
+                     "optimistic pass beside the check of every DoF against that model within 2^-42 D min(sigma "
+                     "spacing); DoFs next to a DoF that fails go to the general rule")
             algorithmic = (f"5 FP64 ops per DoF x {V * (L + 1)} DoFs (Mv and the model check) + 1 per vertex-row "
                            f"entry and level x {V + 2 * E_} x {L + 1} + 18 per cell + 14 per edge + 5 per vertex = "
                            f"{main['fp64_ops']} per launch")
         kname = ("P1xP1 RHS / mass-action launch (k_p1_levels + k_p1_prep + k_p1_sigma_prep + k_p1_rowweights + "
-                 "k_p1_opt + k_p1_fix + k_vsum_bulk<terrain> + k_vgather + k_vgather_general + k_p1_cells; the "
-                 "kernels of the other modes exit at once)")
+                 "k_p1_opt + k_p1_fix + k_vgather + k_vgather_general + k_p1_cells; the kernels of the other modes "
+                 "exit at once)")
     else:
         per = P1_PRISM_OPS["general" if geometry == "tilted" else "vertical"]
         label = (f"cell loop (Algorithm 3 over cells, one element vector per prism, {geometry} geometry): the probe "

@@ -1493,11 +1493,13 @@ __global__ void __launch_bounds__(256, EXT_VGATHER_MINB) k_vgather(const double 
                                                                    double *__restrict__ b, int64_t n, FastDiv col,
                                                                    Deferred dfr, unsigned int *err, Fp64Ones k1,
                                                                    const unsigned int *__restrict__ mode,
-                                                                   bool flat_fused) {
+                                                                   unsigned skip_modes) {
   grid_dep_wait();  // a programmatic dependent of the launch before it
   constexpr int VU = EXT_VG_VU;
   const int lane = threadIdx.x & 31;
-  if (*mode == 0u && flat_fused) return;  // k_vfused formed b
+  // bit m of skip_modes: in gather mode m (0 flat, 1 terrain-following) a
+  // one-pass kernel (k_vfused, k_p1_opt) formed b
+  if (!mode_cells(*mode) && ((skip_modes >> *mode) & 1u)) return;
   if (mode_cells(*mode)) {
     // cell-loop mode: k_p1_cells adds every contribution; WRITE clears b first
     if (!INC)
@@ -1680,11 +1682,16 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
              const int32_t *__restrict__ vnbr, const double *__restrict__ wts, const LevelCoef *__restrict__ tab,
              double *__restrict__ b, uint32_t n, FastDiv col, uint32_t *__restrict__ flags,
              uint32_t *__restrict__ vbad, int32_t *__restrict__ badv, Fp64Ones k1,
-             const unsigned int *__restrict__ mode, int64_t nfc, int64_t ngc) {
+             const unsigned int *__restrict__ mode, SigmaCols sc, int64_t nfc, int64_t ngc) {
   grid_dep_wait();  // a programmatic dependent of the launch before it
   constexpr int UF = EXT_P1OPT_UF, R = EXT_P1OPT_R;
   __shared__ int cta_bad;
-  if (*mode != 0u) return;  // terrain-following or cell-loop mode (k_p1_fix exits too)
+  const unsigned md = *mode;
+  if (mode_cells(md)) return;  // cell-loop mode (k_p1_fix exits too)
+  // terrain-following mode: the depth-weighted rows, the sigma table and the
+  // model check of z (z_ok) in place of the flat ones
+  const bool sig = (md & kNotFlat) != 0u;
+  const LevelCoef *__restrict__ ct = sig ? tab + col.d : tab;
   if (blockIdx.x == 0 && threadIdx.x == 0) flags[(n + 31) / 32] = 0u;  // the zero word past the end
   if (threadIdx.x == 0) cta_bad = 0;
   __syncthreads();
@@ -1709,14 +1716,16 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
     }
     if (flag_chunk) {
       const uint32_t dbase = (uint32_t)fcur * (uint32_t)(UF * 32) + (uint32_t)lane;
-      long long x[UF], y[UF], z[UF], x0[UF], y0[UF], zt[UF];
+      long long x[UF], y[UF], x0[UF], y0[UF];
+      double z[UF], zt[UF];
       uint32_t qv[UF];
       bool v[UF];
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
         const uint32_t d = dbase + (uint32_t)(u * 32);
         v[u] = d < n;
-        x[u] = y[u] = z[u] = x0[u] = y0[u] = zt[u] = 0;
+        x[u] = y[u] = x0[u] = y0[u] = 0;
+        z[u] = zt[u] = 0.0;
         qv[u] = 0;
         if (v[u]) {
           const uint32_t q = fdiv(d, col);
@@ -1726,16 +1735,16 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
           qv[u] = q;
           x[u] = __double_as_longlong(__ldg(xp + 0));
           y[u] = __double_as_longlong(__ldg(xp + 1));
-          z[u] = __double_as_longlong(__ldg(xp + 2));
+          z[u] = __ldg(xp + 2);
           x0[u] = __double_as_longlong(__ldg(x0p + 0));
           y0[u] = __double_as_longlong(__ldg(x0p + 1));
-          zt[u] = __double_as_longlong(__ldg(&tab[m].z));
+          zt[u] = __ldg(&ct[m].z);
         }
       }
 #pragma unroll
       for (int u = 0; u < UF; ++u) {
         const uint32_t w = (uint32_t)fcur * (uint32_t)UF + (uint32_t)u;
-        const bool ok = v[u] && x[u] == x0[u] && y[u] == y0[u] && z[u] == zt[u];
+        const bool ok = v[u] && x[u] == x0[u] && y[u] == y0[u] && z_ok(z[u], zt[u], sig, sc, qv[u], k1);
         const unsigned int word = __ballot_sync(kFull, ok);
         const unsigned int want = __ballot_sync(kFull, v[u]);
         if (w < nwords) {
@@ -1782,8 +1791,8 @@ __global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
         if (e >= cs && e < (int64_t)n) {
           const uint32_t qe = fdiv((uint32_t)e, col);
           const uint32_t me = (uint32_t)e - qe * col.d;
-          const double2 c01 = __ldg(reinterpret_cast<const double2 *>(tab + me));      // z_m, |h_{m-1}|
-          const double2 c23 = __ldg(reinterpret_cast<const double2 *>(tab + me) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
+          const double2 c01 = __ldg(reinterpret_cast<const double2 *>(ct + me));      // z_m, |h_{m-1}|
+          const double2 c23 = __ldg(reinterpret_cast<const double2 *>(ct + me) + 1);  // 2 (|h_{m-1}| + |h_m|), |h_m|
           const double gm = lane >= 2 ? g2 : (lane == 1 ? p31 : p30);  // g(e - 1)
           const double g0 = lane >= 1 ? g1 : p31;                      // g(e)
           // vertical neighbours beyond the column's ends are cleared bitwise
@@ -1817,7 +1826,7 @@ __global__ void __launch_bounds__(256) k_p1_fix(const int32_t *__restrict__ vrow
                                                 FastDiv col, Deferred dfr, unsigned int *err,
                                                 const unsigned int *__restrict__ mode) {
   grid_dep_wait();  // a programmatic dependent of the launch before it
-  if (*mode != 0u) return;
+  if (mode_cells(*mode)) return;
   int any = 0;
   for (int i = threadIdx.x; i < nbadv; i += blockDim.x) any |= __ldg(badv + i);
   if (!__syncthreads_or(any)) return;
@@ -2184,7 +2193,7 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       if (g > go) g = go;
       if (g < 1) g = 1;
       dep(launch_dependent(k_p1_opt, dim3((unsigned)g), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab, p.b,
-                           (uint32_t)n, col, oflags, vbad, badv, k1, mode, nfc, ngc));
+                           (uint32_t)n, col, oflags, vbad, badv, k1, mode, sc, nfc, ngc));
       int64_t gx = (nv + 255) / 256;
       if (gx > (int64_t)sms * 8) gx = (int64_t)sms * 8;
       dep(launch_dependent(k_p1_fix, dim3((unsigned)(gx > 0 ? gx : 1)), dim3(256), 0, s, p.vrow, p.vnbr, oflags, vbad,
@@ -2210,21 +2219,22 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
       if (!fused && !opt)
         dep(launch_dependent(k_vsum_bulk<false>, dim3((unsigned)gb), dim3(256), 0, s, p.X, p.f, tab, W, n, col, k1,
                              p.err, mode, sc, skip, wait_limit));
-      dep(launch_dependent(k_vsum_bulk<true>, dim3((unsigned)gb), dim3(256), 0, s, p.X, p.f, tab, W, n, col, k1, p.err,
-                           mode, sc, skip, wait_limit));
+      if (!opt)
+        dep(launch_dependent(k_vsum_bulk<true>, dim3((unsigned)gb), dim3(256), 0, s, p.X, p.f, tab, W, n, col, k1,
+                             p.err, mode, sc, skip, wait_limit));
     } else {
       if (!fused && !opt) k_vsum_tab<false><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
-      k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
+      if (!opt) k_vsum_tab<true><<<(unsigned)gv, 256, 0, s>>>(p.X, p.f, tab, W, n, col, k1, mode, sc);
     }
     if (p.overwrite) {
       dep(launch_dependent(k_vgather<false>, dim3((unsigned)gg), dim3(256), 0, s, W, p.vrow, p.vnbr, wts, p.b, n, col,
-                           dfr, p.err, k1, mode, fused || opt));
+                           dfr, p.err, k1, mode, opt ? 3u : (fused ? 1u : 0u)));
       const int r = resident_ctas(k_vgather_general<false>, res_vgg[0]);
       dep(launch_dependent(k_vgather_general<false>, dim3((unsigned)(sms * r)), dim3(kWarps * 32), 0, s, p, dfr, col,
                            k1));
     } else {
       dep(launch_dependent(k_vgather<true>, dim3((unsigned)gg), dim3(256), 0, s, W, p.vrow, p.vnbr, wts, p.b, n, col,
-                           dfr, p.err, k1, mode, fused));
+                           dfr, p.err, k1, mode, fused ? 1u : 0u));
       const int r = resident_ctas(k_vgather_general<true>, res_vgg[1]);
       dep(launch_dependent(k_vgather_general<true>, dim3((unsigned)(sms * r)), dim3(kWarps * 32), 0, s, p, dfr, col,
                            k1));
