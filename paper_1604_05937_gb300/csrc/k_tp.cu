@@ -641,6 +641,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPL
         ci.ry[a] = __double_as_longlong(y[a]);
       }
       ci.alpha = fabs((x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0])) * p.scale;
+      // all three vertex columns straight at every level: no per-item test
+      ci.allok = FLAGS ? vflags_all(p.vflags, ci.cm[0], L1) & vflags_all(p.vflags, ci.cm[2], L1) &
+                             vflags_all(p.vflags, ci.cm[4], L1)
+                       : 0;
     }
     __syncwarp();
     const int nitems = ncol * L1;
@@ -668,8 +672,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPL
 #pragma unroll
           for (int i = 0; i < NH * 2; ++i) f[u][i] = __ldg(p.f + ci.fm[i] + ms[u] * p.off[i]);
           if (FLAGS) {
+            if (!ci.allok) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)ms[u] * p.coff[i]);
+              for (int i = 0; i < 6; ++i) ok[u] &= vflag(p.vflags, (int64_t)ci.cm[i] + (int64_t)ms[u] * p.coff[i]);
+            }
             hl[u] = __ldg(p.hlay + ms[u]);
           }
         } else {
