@@ -947,7 +947,8 @@ def run_cfg5(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     s = stream.cuda_stream
-    bp = meshgen.batched_params(count=args.count, seed=SEED + 5 + 1000 * rank, cmax=args.cmax)
+    bp = meshgen.batched_params(count=args.count, seed=SEED + 5 + 1000 * rank, cmin=args.cmin, cmax=args.cmax,
+                                lmax=args.lmax)
     meshes, per, keep = [], [], []
     vb, ops, cells_total = 0, 0, 0
     for i, (n, L) in enumerate(zip(bp.n, bp.layers)):
@@ -1017,7 +1018,8 @@ def run_cfg5(args, rank, world, local):
              "autotuned_params": batch.params, "autotune_seconds": round(tune_s, 2),
              "plans": dict(plans, tuned_launch_ms=round(tt[0], 3), cached_launch_ms=round(tb[0], 3)),
              "fp64_gops": round(ops / tb[0] / 1e6, 1), "cells": cells_total,
-             "meshes": {"count": args.count, "base_cells": [2 * n * n for n in bp.n], "layers": bp.layers}}
+             "meshes": {"count": args.count, "base_cells": [2 * n * n for n in bp.n], "layers": bp.layers,
+                        "base_cells_range": [args.cmin, args.cmax], "layers_range": [8, args.lmax]}}
     return _common(args, world, f"batched u^2 v residual + adjoint over {args.count} prism meshes: valuable GB/s "
                    "(one captured persistent launch)", world * vb / tb[0] / 1e6, "GB/s",
                    {"workload": f"{args.count} extruded prism meshes, {cells_total} prisms, P1xP1 u^2 v forward + adjoint",
@@ -1466,6 +1468,8 @@ def main():
     ap.add_argument("--layers", type=int, default=None, help="layers (config 2: 100, config 4: 64)")
     ap.add_argument("--count", type=int, default=64, help="config 5: number of meshes")
     ap.add_argument("--cmax", type=float, default=5e5, help="config 5: largest base cell count")
+    ap.add_argument("--cmin", type=float, default=1e4, help="config 5: smallest base cell count")
+    ap.add_argument("--lmax", type=int, default=256, help="config 5: largest layer count (smallest: 8)")
     ap.add_argument("--order", choices=["rcm", "random"], default="rcm")
     ap.add_argument("--config", type=int, choices=[2, 3, 4, 5, 6, 7, 8], default=2,
                     help="2: 1M triangles x 100 layers (default); 3: layer sweep; 4: Q2/DG2 hexahedra; "

@@ -319,7 +319,23 @@ int cols_per_warp(int layers, int target) {
 cudaError_t launch_u2v(const U2VLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   if (p.nvc == 3) {
-    const int cpw = cols_per_warp(p.layers, 512);
+    int cpw = cols_per_warp(p.layers, 512);
+    // a small mesh takes fewer columns per warp, down to a warp's 32 items,
+    // until it has 16 warps per SM (64 meshes of 100-2,000 cells x 8-16
+    // layers: 5.9 ms for their 64 launches with 512 items per warp, most SMs
+    // idle)
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms < 1) sms = 1;
+    }
+    const int cpw_min = (32 + p.layers - 1) / p.layers;
+    while (cpw > cpw_min && (p.ncells + cpw - 1) / cpw < (int64_t)sms * 16) {
+      cpw = (cpw + 1) / 2;
+      if (cpw < cpw_min) cpw = cpw_min;
+    }
     const int64_t warps = (p.ncells + cpw - 1) / cpw;
     const unsigned blocks = (unsigned)((warps + 7) / 8);
     switch (p.mode) {
