@@ -145,6 +145,20 @@ P1_OPS_NOTE = ("default form from a million (column, level) items: gather on a f
                "(42 per prism with vertical edges + 3 per item); single pass below: 13 per item")
 
 
+def cgdg_gather(name: str, layers: int, write: bool = True) -> bool:
+    """CG1 x DG0 / CG1 x DG1 with WRITE from 32 layers run the gather path of
+    the P1xP1 launch (EXTMESH_TP_CGDG=0 keeps the cell kernel)."""
+    return (write and name in ("CG1xDG0", "CG1xDG1") and layers >= P1_GATHER_MIN_LAYERS
+            and os.environ.get("EXTMESH_TP_CGDG", "") != "0")
+
+
+def cgdg_ops(nverts: int, nedges: int, ncells: int, layers: int, nv: int) -> int:
+    """FP64 operations of the CG1 x DG gather path: one per vertex-row entry
+    and DoF layer (V + 2E entries, nv DoFs per layer), two per DoF for the
+    layer's DG mass, and the per-launch geometry (7 per cell, 4 per edge)."""
+    return (nverts + 2 * nedges) * nv * layers + 2 * nverts * nv * layers + 7 * ncells + 4 * nedges
+
+
 def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False) -> int:
     """Kernels of one EXT_K_MASS_TP launch on constant layers over a mesh with
     base coordinates: the level table, the straightness flags and the cell
@@ -152,6 +166,8 @@ def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False)
     size / never), the cell kernel alone otherwise; with WRITE on a DG x DG
     space from 8 to 2048 layers the optimistic form (flags and element vectors
     in one launch, then the fix-up launch)."""
+    if cgdg_gather(name, layers, write):
+        return 9  # the gather path: levels, probe, sigma, rows, gather, fix-up, general, clear, cell kernel
     env = os.environ.get("EXTMESH_TP_FLAGS", "")
     flagged = env == "1" or (env != "0" and items >= 1_000_000)
     dgdg = name[:2] == "DG" and name[4:6] == "DG"
@@ -1083,7 +1099,12 @@ def run_cfg6(args, rank, world, local):
                 t = time_kernel(fn, reps, stream, flush)[0]
                 launches += (reps + 1) * (p1_kernels(C * (L + 1), L) if ops is None
                                           else tp_kernels(C * L, L, name, write=True))
-                work = p1_ops(V * (L + 1), C * (L + 1), C, L) if ops is None else ops * C * L
+                if ops is None:
+                    work = p1_ops(V * (L + 1), C * (L + 1), C, L)
+                elif cgdg_gather(name, L):
+                    work = cgdg_ops(V, euler_edges(V, C), C, L, 2 if name == "CG1xDG1" else 1)
+                else:
+                    work = ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs
                 vb = vb_paper + 24 * C + 4 * sp.k * C
                 gops = work / t / 1e6

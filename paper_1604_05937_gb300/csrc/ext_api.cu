@@ -993,6 +993,14 @@ extern "C" ext_status ext_par_loop(const ext_mesh *mesh, int32_t kernel_id, int3
       p.hown = h != 0;
       p.vcont = v == 0;
       p.nf = args[1].space->ndofs;
+      p.vrow = mesh->d_vrow;
+      p.vnbr = mesh->d_vnbr;
+      p.vedge = mesh->d_vedge;
+      p.vcrow = mesh->d_vcrow;
+      p.vcells = mesh->d_vcells;
+      p.nverts = (int32_t)mesh->N[0];
+      p.nvent = mesh->n_vent;
+      p.err = ext_device_error_word();
       e = launch_mass_tp(p, s);
       break;
     }

@@ -11,6 +11,9 @@
 #include "../../include/extmesh.h"
 
 #define EXT_MAXK 64  // longest stencil handled (Q2/DG2 hexahedra use 27)
+#ifndef EXT_GATHER_MIN_LAYERS
+#define EXT_GATHER_MIN_LAYERS 32  // constant layers: the probe and the gather forms from this many layers
+#endif
 
 // Bits of the device error word (ext_sync_check maps them to statuses).
 enum : unsigned int {
@@ -264,11 +267,26 @@ struct MassTPLaunch {
   const int32_t *badv = nullptr;         // optimistic form: per CTA of its first launch, a DoF not verified straight
   int32_t nbadv = 0;
   Fp64Ones k1;                           // fp64_ones(): products and sums of the closed forms issued as DFMA
+  // CG1 x DG on the gather path (launch_mass_cgdg): the mesh's vertex rows
+  const int32_t *vrow = nullptr, *vnbr = nullptr;
+  const int2 *vedge = nullptr;
+  const int32_t *vcrow = nullptr, *vcells = nullptr;
+  int32_t nverts = 0;
+  int64_t nvent = 0;
+  unsigned int *err = nullptr;           // the device error word
+  const unsigned int *mode = nullptr;    // cell kernel: run only when this probe word is in cell-loop mode
   bool overwrite = false;                // b = M f (EXT_WRITE) instead of b += M f (EXT_INC)
   bool hown = false;                     // horizontal DG0/DG1: every DoF belongs to one cell column
   bool vcont = false;                    // vertical CG1: layers l and l + 1 share their facet DoFs
 };
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s);
+// CG1 x DG0 / CG1 x DG1 with WRITE through the P1xP1 gather machinery
+// (k_p1.cu), and its two nine-space kernels (k_tp.cu): the general rule on the
+// recorded DoFs, and the cell kernel gated on the probe's cell-loop mode.
+cudaError_t launch_mass_cgdg(const MassTPLaunch &p, cudaStream_t s);
+cudaError_t launch_cgdg_general(const MassTPLaunch &p, const int2 *list, const unsigned int *count, unsigned int cap,
+                                cudaStream_t s);
+cudaError_t launch_tp_cells_gated(const MassTPLaunch &p, const unsigned int *mode, cudaStream_t s);
 
 // p-adaptive DG right-hand side (k_tp.cu): every cell's element is DG0|DG1 x
 // DG0|DG1 by its DoF count (1 DG0xDG0, 2 DG0xDG1, 3 DG1xDG0, 6 DG1xDG1); the

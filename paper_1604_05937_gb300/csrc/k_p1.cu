@@ -57,9 +57,7 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef EXT_FACTORED_MIN_LAYERS
 #define EXT_FACTORED_MIN_LAYERS 3  // constant layers: the factored split form from this many layers
 #endif
-#ifndef EXT_GATHER_MIN_LAYERS
-#define EXT_GATHER_MIN_LAYERS 32  // constant layers: the probe and the gather forms from this many layers
-#endif
+
 #ifndef EXT_MASS_ITEMS
 #define EXT_MASS_ITEMS 1616  // target items (column levels) per column group
 #endif
@@ -1859,6 +1857,188 @@ __global__ void __launch_bounds__(256) k_p1_fix(const int32_t *__restrict__ vrow
   }
 }
 
+// CG1 x DG0 and CG1 x DG1 (horizontal CG1, vertical DG; WRITE access,
+// constant layers, the gather modes of the probe).  On a straight extrusion
+// with flat (or terrain-following) levels the element matrix of prism (c, l)
+// is the base triangle's row block times the vertical DG mass of layer l, so
+// M = Hd (x) Mv_DG with Mv_DG block diagonal over the layers: DG0, Delta_l;
+// DG1, (Delta_l / 6) [[2, 1], [1, 2]] (Delta_l = |h_l|, or the sigma spacing
+// with Hd depth-weighted), and Hd = 6 x the row weights of the P1xP1 gather.
+// The DoF of vertex a, layer l, node beta is a NV lambda + NV l + beta
+// (Algorithm 1: vertex columns first, NV DoFs per layer), so every neighbour
+// column j of a's row is read at the same offset r = NV l + beta:
+// g = sum_t w_t f[j_t NV lambda + r]; then b = 6 Delta_l g (DG0) or
+// Delta_l (2 g_beta + g_{1-beta}) (DG1: the pair beta, 1 - beta sits in lanes
+// d and d ^ 1, one shuffle).  No atomics: every DoF is written once.  The
+// straightness flags of the coordinate DoFs are set beside it, in the same
+// chunks as k_p1_opt; k_cgdg_fix records the DoFs whose layer's prisms touch
+// a coordinate DoF that is not straight, for the general rule.
+template <int NV>
+__global__ void __launch_bounds__(256, EXT_P1OPT_MINB)
+    k_cgdg_opt(const double *__restrict__ X, const double *__restrict__ f, const int32_t *__restrict__ vrow,
+               const int32_t *__restrict__ vnbr, const double *__restrict__ wts, const LevelCoef *__restrict__ tab,
+               double *__restrict__ b, uint32_t ncoord, uint32_t nf, FastDiv col, FastDiv dcol,
+               uint32_t *__restrict__ flags, uint32_t *__restrict__ vbad, int32_t *__restrict__ badv, Fp64Ones k1,
+               const unsigned int *__restrict__ mode, SigmaCols sc, int64_t nfc, int64_t ngc) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
+  constexpr int UF = EXT_P1OPT_UF, R = EXT_P1OPT_R;
+  __shared__ int cta_bad;
+  const unsigned md = *mode;
+  if (mode_cells(md)) return;  // cell-loop mode: the nine-space cell kernel runs instead
+  const bool sig = (md & kNotFlat) != 0u;
+  const LevelCoef *__restrict__ ct = sig ? tab + col.d : tab;
+  if (blockIdx.x == 0 && threadIdx.x == 0) flags[(ncoord + 31) / 32] = 0u;  // the zero word past the end
+  if (threadIdx.x == 0) cta_bad = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nwords = (ncoord + 31) / 32;
+  const int64_t nch = nfc + ngc;
+  const int64_t wstride = (int64_t)gridDim.x * 8;
+  bool bad = false;
+  const int64_t j0 = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  int64_t fb = j0 * nfc / nch, r = j0 * nfc - fb * nch;
+  const int64_t qw = wstride * nfc / nch, rw = wstride * nfc - qw * nch;
+  for (int64_t j = j0; j < nch; j += wstride) {
+    const bool flag_chunk = r + nfc >= nch;
+    const int64_t fcur = fb;
+    fb += qw;
+    r += rw;
+    if (r >= nch) {
+      r -= nch;
+      ++fb;
+    }
+    if (flag_chunk) {
+      const uint32_t dbase = (uint32_t)fcur * (uint32_t)(UF * 32) + (uint32_t)lane;
+      long long x[UF], y[UF], x0[UF], y0[UF];
+      double z[UF], zt[UF];
+      uint32_t qv[UF];
+      bool v[UF];
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t d = dbase + (uint32_t)(u * 32);
+        v[u] = d < ncoord;
+        x[u] = y[u] = x0[u] = y0[u] = 0;
+        z[u] = zt[u] = 0.0;
+        qv[u] = 0;
+        if (v[u]) {
+          const uint32_t q = fdiv(d, col);
+          const uint32_t m = d - q * col.d;
+          const double *xp = X + 3 * (size_t)d;
+          const double *x0p = X + 3 * (size_t)(q * col.d);
+          qv[u] = q;
+          x[u] = __double_as_longlong(__ldg(xp + 0));
+          y[u] = __double_as_longlong(__ldg(xp + 1));
+          z[u] = __ldg(xp + 2);
+          x0[u] = __double_as_longlong(__ldg(x0p + 0));
+          y0[u] = __double_as_longlong(__ldg(x0p + 1));
+          zt[u] = __ldg(&ct[m].z);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t w = (uint32_t)fcur * (uint32_t)UF + (uint32_t)u;
+        const bool ok = v[u] && x[u] == x0[u] && y[u] == y0[u] && z_ok(z[u], zt[u], sig, sc, qv[u], k1);
+        const unsigned int word = __ballot_sync(kFull, ok);
+        const unsigned int want = __ballot_sync(kFull, v[u]);
+        if (w < nwords) {
+          if (lane == 0) flags[w] = word;
+          bad |= word != want;
+        }
+        if (v[u] && !ok) atomicOr(vbad + (qv[u] >> 5), 1u << (qv[u] & 31u));
+      }
+    } else {
+      const int64_t cs = (j - fcur) * (int64_t)(32 * R);
+#pragma unroll 1
+      for (int t = 0; t < R; ++t) {
+        const int64_t d = cs + 32 * t + lane;
+        int r0 = 0, deg = 0;
+        uint32_t rr = 0;
+        if (d < (int64_t)nf) {
+          const uint32_t q = fdiv((uint32_t)d, dcol);
+          rr = (uint32_t)d - q * dcol.d;
+          r0 = __ldg(vrow + q);
+          deg = __ldg(vrow + q + 1) - r0;
+        }
+        double acc = k1.mzero;
+        const int dmx = __reduce_max_sync(kFull, deg);
+#pragma unroll 4
+        for (int u = 0; u < dmx; ++u) {
+          double ev = 0.0, fv = 0.0;
+          if (u < deg) {
+            ev = __ldg(wts + r0 + u);
+            fv = __ldg(f + (size_t)fdiv((uint32_t)__ldg(vnbr + r0 + u), col) * dcol.d + rr);
+          }
+          acc = fma(ev, fv, acc);
+        }
+        const double other = NV == 2 ? __shfl_xor_sync(kFull, acc, 1) : 0.0;
+        if (d < (int64_t)nf) {
+          const double hi = __ldg(&ct[NV == 2 ? rr >> 1 : rr].hi);  // Delta_l of layer l
+          b[d] = NV == 2 ? fmul(hi, fma(2.0, acc, other), k1) : fmul(fmul(6.0, hi, k1), acc, k1);
+        }
+      }
+    }
+  }
+  if (bad && lane == 0) cta_bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) badv[blockIdx.x] = cta_bad;
+}
+
+// bits 0..15 of m spread to bit pairs (bit i -> bits 2i and 2i + 1)
+__device__ __forceinline__ uint32_t spread_pairs(uint32_t m) {
+  uint32_t x = m & 0xffffu;
+  x = (x | (x << 8)) & 0x00ff00ffu;
+  x = (x | (x << 4)) & 0x0f0f0f0fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x | (x << 1);
+}
+
+// Fix-up of k_cgdg_opt (the counterpart of k_p1_fix): one thread per vertex
+// column a whose row holds a column with a failing coordinate DoF records,
+// 32 / NV layers at a time, the DoFs of the layers l whose levels l or l + 1
+// hold a failing DoF in a row column.
+template <int NV>
+__global__ void __launch_bounds__(256) k_cgdg_fix(const int32_t *__restrict__ vrow, const int32_t *__restrict__ vnbr,
+                                                  const uint32_t *__restrict__ flags,
+                                                  const uint32_t *__restrict__ vbad, const int32_t *__restrict__ badv,
+                                                  int32_t nbadv, uint32_t nverts, FastDiv col, int32_t layers,
+                                                  Deferred dfr, unsigned int *err,
+                                                  const unsigned int *__restrict__ mode) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
+  if (mode_cells(*mode)) return;
+  int any = 0;
+  for (int i = threadIdx.x; i < nbadv; i += blockDim.x) any |= __ldg(badv + i);
+  if (!__syncthreads_or(any)) return;
+  constexpr uint32_t LW = 32 / NV;  // layers per 32-DoF word
+  for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nverts; a += gridDim.x * blockDim.x) {
+    const int32_t r0 = __ldg(vrow + a), r1 = __ldg(vrow + a + 1);
+    bool hit = false;
+    for (int32_t t = r0; t < r1 && !hit; ++t) {
+      const uint32_t jv = fdiv((uint32_t)__ldg(vnbr + t), col);
+      hit = (__ldg(vbad + (jv >> 5)) >> (jv & 31u)) & 1u;
+    }
+    if (!hit) continue;
+    for (uint32_t lo = 0; lo < (uint32_t)layers; lo += LW) {
+      const uint32_t nl = (uint32_t)layers - lo < LW ? (uint32_t)layers - lo : LW;  // layers lo .. lo + nl - 1
+      const uint32_t valid = nl == 32 ? 0xffffffffu : (1u << nl) - 1u;
+      uint32_t B = 0, top = 0;  // not straight: level lo + i (i < nl), level lo + nl
+      for (int32_t t = r0; t < r1; ++t) {
+        const uint32_t j0 = (uint32_t)__ldg(vnbr + t);
+        B |= ~bits32(flags, j0 + lo) & valid;
+        top |= ~(__ldg(flags + ((j0 + lo + nl) >> 5)) >> ((j0 + lo + nl) & 31u)) & 1u;
+      }
+      // layer lo + i needs levels lo + i and lo + i + 1
+      const uint32_t need = (B | (B >> 1) | (top << (nl - 1))) & valid;
+      if (!need) continue;
+      // one 32-DoF record: NV DoFs per layer
+      const uint32_t start = a * (uint32_t)(NV * layers) + (uint32_t)NV * lo;
+      const unsigned int slot = atomicAdd(dfr.count, 1u);
+      if (slot < dfr.cap) dfr.list[slot] = make_int2((int)start, (int)(NV == 1 ? need : spread_pairs(need)));
+      else atomicOr(err, EXT_DERR_BOUNDS);
+    }
+  }
+}
+
 // The recorded DoFs of the gather: b_{a,m} (+)= the bottom-row entries of the
 // prisms (c, m) and the top-row entries of the prisms (c, m - 1) for every
 // cell c around vertex a (p1_prism), summed in ascending cell order.  One
@@ -2268,5 +2448,119 @@ cudaError_t launch_mass_p1(const MassP1Launch &p, cudaStream_t s) {
     e = cudaGetLastError();
   }
   const cudaError_t ef = cudaFreeAsync(scr0, s);
+  return e != cudaSuccess ? e : ef;
+}
+
+// CG1 x DG0 / CG1 x DG1 with WRITE on constant layers (k_tp.cu hands the
+// launch over when the mesh has vertex rows and the layers reach
+// EXT_GATHER_MIN_LAYERS): the level tables, probe, areas and row weights of
+// the P1xP1 gather, then k_cgdg_opt (the gather beside the straightness
+// flags) and k_cgdg_fix; the recorded DoFs are recomputed with the general
+// element rule (launch_cgdg_general), and in cell-loop mode the nine-space
+// cell kernel runs instead (launch_tp_cells_gated: b cleared, FP64 reductions).
+cudaError_t launch_mass_cgdg(const MassTPLaunch &p, cudaStream_t s) {
+  static int sms = 0, res_o[2] = {0, 0};
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int NV = p.nv;
+  const int64_t L1 = (int64_t)p.layers + 1, nv = p.nverts, n = p.nf, nc = p.ncoord;
+  const int64_t go = (int64_t)(NV == 2 ? resident_ctas(k_cgdg_opt<2>, res_o[1]) : resident_ctas(k_cgdg_opt<1>, res_o[0])) *
+                     sms;
+  const int64_t nfc = ((nc + 31) / 32 + EXT_P1OPT_UF - 1) / EXT_P1OPT_UF;
+  const int64_t ngc = (n + 32 * EXT_P1OPT_R - 1) / (32 * EXT_P1OPT_R);
+  int64_t g = (nfc + ngc + 7) / 8;
+  if (g > go) g = go;
+  if (g < 1) g = 1;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const int64_t cap64 = nv * ((p.layers * NV + 31) / 32) + 2;
+  const unsigned int cap = (unsigned int)(cap64 < 0x7fffffff ? cap64 : 0x7fffffff);
+  const size_t vbbytes = al(sizeof(uint32_t) * (size_t)((nv + 31) / 32));
+  const size_t tbytes = al(sizeof(LevelCoef) * 2 * (size_t)L1);
+  const size_t cbytes = al(sizeof(double) * (size_t)p.ncells);
+  const size_t ebytes = al(sizeof(double) * (size_t)p.nvent);
+  const size_t vbytes = al(sizeof(double) * (size_t)nv);
+  const size_t lbytes = al(sizeof(int2) * (size_t)cap);
+  const size_t fbytes = al(sizeof(uint32_t) * (size_t)((nc + 31) / 32 + 1));
+  const size_t bvbytes = al(sizeof(int32_t) * (size_t)g);
+  char *scr = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), 256 + vbbytes + tbytes + 2 * cbytes + ebytes +
+                                                                       3 * vbytes + lbytes + fbytes + bvbytes,
+                                  s);
+  if (e != cudaSuccess) return e;
+  unsigned int *count = reinterpret_cast<unsigned int *>(scr);
+  unsigned int *mode = count + 1;
+  unsigned long long *minds = reinterpret_cast<unsigned long long *>(scr + 8);
+  char *q = scr + 256;
+  uint32_t *vbad = reinterpret_cast<uint32_t *>(q);
+  q += vbbytes;
+  LevelCoef *tab = reinterpret_cast<LevelCoef *>(q);
+  q += tbytes;
+  double *alpha = reinterpret_cast<double *>(q);
+  q += cbytes;
+  double *Sc = reinterpret_cast<double *>(q);
+  q += cbytes;
+  double *wts = reinterpret_cast<double *>(q);
+  q += ebytes;
+  SigmaCols sc;
+  sc.Dv = reinterpret_cast<double *>(q);
+  sc.Z0 = reinterpret_cast<double *>(q + vbytes);
+  sc.Bv = reinterpret_cast<double *>(q + 2 * vbytes);
+  q += 3 * vbytes;
+  Deferred dfr;
+  dfr.count = count;
+  dfr.list = reinterpret_cast<int2 *>(q);
+  dfr.cap = cap;
+  q += lbytes;
+  uint32_t *flags = reinterpret_cast<uint32_t *>(q);
+  q += fbytes;
+  int32_t *badv = reinterpret_cast<int32_t *>(q);
+  // the counter, the mode word, the smallest sigma spacing and the vertex-column bits start at zero
+  e = cudaMemsetAsync(scr, 0, 256 + vbbytes, s);
+  auto dep = [&e](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const FastDiv col = make_fastdiv((uint32_t)L1);
+  const Fp64Ones k1 = {1.0, -1.0, -0.0};
+  if (e == cudaSuccess) {
+    const int64_t stride = nv > 4096 ? (nv + 4095) / 4096 : 1;
+    const int64_t nsamp = (nv + stride - 1) / stride;
+    int64_t gp = ((int64_t)p.ncells > nsamp * L1 ? (int64_t)p.ncells : nsamp * L1) / 256 + 1;
+    if (gp > (int64_t)sms * 8) gp = (int64_t)sms * 8;
+    if (gp * 256 < L1) gp = (L1 + 255) / 256;
+    k_p1_levels<<<(unsigned)((L1 + 255) / 256), 256, 0, s>>>(p.X, p.layers, tab, mode, minds);
+    dep(cudaGetLastError());
+    dep(launch_dependent(k_p1_prep, dim3((unsigned)gp), dim3(256), 0, s, p.X, p.layers, p.cmap, p.ncells, nsamp,
+                         stride, tab, alpha, mode));
+    int64_t gs = ((nv > (int64_t)p.ncells ? nv : (int64_t)p.ncells) + 255) / 256;
+    if (gs > (int64_t)sms * 8) gs = (int64_t)sms * 8;
+    dep(launch_dependent(k_p1_sigma_prep, dim3((unsigned)(gs > 0 ? gs : 1)), dim3(256), 0, s, p.X, p.layers, p.cmap,
+                         p.ncells, nv, mode, minds, const_cast<double *>(sc.Dv), const_cast<double *>(sc.Z0),
+                         const_cast<double *>(sc.Bv), Sc));
+    int64_t gw = (nv + 255) / 256;
+    if (gw > (int64_t)sms * 8) gw = (int64_t)sms * 8;
+    dep(launch_dependent(k_p1_rowweights, dim3((unsigned)(gw > 0 ? gw : 1)), dim3(256), 0, s, p.vrow, p.vnbr,
+                         p.vedge, p.vcrow, p.vcells, alpha, sc.Dv, Sc, wts, (int32_t)nv, p.nvent, col, mode));
+    const FastDiv dcol = make_fastdiv((uint32_t)(NV * p.layers));
+    if (NV == 2)
+      dep(launch_dependent(k_cgdg_opt<2>, dim3((unsigned)g), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab,
+                           p.b, (uint32_t)nc, (uint32_t)n, col, dcol, flags, vbad, badv, k1, mode, sc, nfc, ngc));
+    else
+      dep(launch_dependent(k_cgdg_opt<1>, dim3((unsigned)g), dim3(256), 0, s, p.X, p.f, p.vrow, p.vnbr, wts, tab,
+                           p.b, (uint32_t)nc, (uint32_t)n, col, dcol, flags, vbad, badv, k1, mode, sc, nfc, ngc));
+    int64_t gx = (nv + 255) / 256;
+    if (gx > (int64_t)sms * 8) gx = (int64_t)sms * 8;
+    if (NV == 2)
+      dep(launch_dependent(k_cgdg_fix<2>, dim3((unsigned)(gx > 0 ? gx : 1)), dim3(256), 0, s, p.vrow, p.vnbr, flags,
+                           vbad, badv, (int32_t)g, (uint32_t)nv, col, p.layers, dfr, p.err, mode));
+    else
+      dep(launch_dependent(k_cgdg_fix<1>, dim3((unsigned)(gx > 0 ? gx : 1)), dim3(256), 0, s, p.vrow, p.vnbr, flags,
+                           vbad, badv, (int32_t)g, (uint32_t)nv, col, p.layers, dfr, p.err, mode));
+    if (e == cudaSuccess) e = launch_cgdg_general(p, dfr.list, dfr.count, dfr.cap, s);
+    if (e == cudaSuccess) e = launch_tp_cells_gated(p, mode, s);
+  }
+  const cudaError_t ef = cudaFreeAsync(scr, s);
   return e != cudaSuccess ? e : ef;
 }

@@ -170,6 +170,7 @@ template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI = false, bool WR = fa
 #endif
 __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB : 2) k_mass_tp(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
+  if (p.mode && (*p.mode & 3u) != 3u) return;  // gated on the probe's cell-loop mode (CG1 x DG gather path)
   if (FIX) {  // no CTA of the optimistic launch saw a coordinate DoF that is not straight
     grid_dep_wait();  // launched as a dependent of that launch
     int any = 0;
@@ -934,6 +935,58 @@ cudaError_t launch_dgp_kind(const MassDGPLaunch &p, cudaStream_t s) {
   }
 }
 
+// CG1 x DG recorded DoFs (the gather path's fix-up): b of vertex a, layer l,
+// node beta = the sum over the cells around a of entry (a, beta) of prism
+// (c, l)'s element vector by the general 6-point rule, in ascending cell
+// order; one warp per 32-DoF record, one lane per DoF.
+template <int NV>
+__global__ void __launch_bounds__(kWarps * 32) k_cgdg_general(const MassTPLaunch p, const int2 *__restrict__ list,
+                                                              const unsigned int *__restrict__ count, unsigned int cap,
+                                                              FastDiv dcol, FastDiv col) {
+  grid_dep_wait();  // a programmatic dependent of the launch before it
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int nrec = min(*count, cap);
+  for (unsigned int e = blockIdx.x * kWarps + warp; e < nrec; e += gridDim.x * kWarps) {
+    const int2 en = list[e];
+    if ((((unsigned int)en.y) >> lane & 1u) == 0u) continue;
+    const uint32_t d = (uint32_t)en.x + (uint32_t)lane;
+    const uint32_t q = fdiv(d, dcol);
+    const uint32_t r = d - q * dcol.d;
+    const int l = (int)(NV == 2 ? r >> 1 : r), beta = (int)(NV == 2 ? r & 1u : 0u);
+    const int32_t v0 = (int32_t)(q * col.d);  // coordinate DoF of vertex q at level 0
+    double acc = 0.0;
+    for (int32_t t = __ldg(p.vcrow + q); t < __ldg(p.vcrow + q + 1); ++t) {
+      const int64_t c = __ldg(p.vcells + t);
+      int ia = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (__ldg(p.cmap + c * 6 + 2 * k) == v0) ia = k;
+      double Xl[6][3], fl[3 * NV], out[3 * NV];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const int64_t cd = (int64_t)__ldg(p.cmap + c * 6 + i) + (int64_t)l * p.coff[i];
+        Xl[i][0] = __ldg(p.X + 3 * cd + 0);
+        Xl[i][1] = __ldg(p.X + 3 * cd + 1);
+        Xl[i][2] = __ldg(p.X + 3 * cd + 2);
+      }
+#pragma unroll
+      for (int i = 0; i < 3 * NV; ++i) fl[i] = __ldg(p.f + __ldg(p.fmap + c * p.k + p.slot[i]) + (int64_t)l * p.off[i]);
+      tp_general<3, NV>(Xl, fl, out);
+      acc += out[ia * NV + beta];
+    }
+    p.b[d] = acc;
+  }
+}
+
+// In cell-loop mode only: b cleared, then the (unflagged) cell kernel with
+// FP64 reductions.
+__global__ void __launch_bounds__(256) k_tp_clear_cells(double *__restrict__ b, int64_t n,
+                                                        const unsigned int *__restrict__ mode) {
+  if ((*mode & 3u) != 3u) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = 0.0;
+}
+
 }  // namespace
 
 // The flagged form runs on constant layers when the mesh has base
@@ -943,6 +996,18 @@ cudaError_t launch_dgp_kind(const MassDGPLaunch &p, cudaStream_t s) {
 // from the stream-ordered pool; otherwise every lane loads its coordinates.
 cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
+  // CG1 x DG0 / CG1 x DG1 with WRITE on constant layers from
+  // EXT_GATHER_MIN_LAYERS layers: the gather path (no atomics, no clearing;
+  // EXTMESH_TP_CGDG=0, read once per process, keeps the cell kernel)
+  static int cgdg_env = -1;
+  if (cgdg_env < 0) {
+    const char *ev = getenv("EXTMESH_TP_CGDG");
+    cgdg_env = (ev && ev[0] == '0') ? 0 : 1;
+  }
+  if (cgdg_env == 1 && p.overwrite && p.nh == 3 && !p.hown && !p.vcont && !p.cell_layers && p.vrow && p.vnbr &&
+      p.vedge && p.vcrow && p.vcells && p.nvent > 0 && p.layers >= EXT_GATHER_MIN_LAYERS &&
+      (double)p.nf < 2147483647.0 && (double)p.ncoord < 2147483647.0)
+    return launch_mass_cgdg(p, s);
   // DG x CG1 takes the atomic form (FP64 reductions into the shared facet
   // DoFs, b cleared first for WRITE), which measured 5-10 % faster at 10 and
   // 100 layers than the level kernel that merges the shared DoFs in
@@ -1052,3 +1117,42 @@ cudaError_t launch_mass_dgp(const MassDGPLaunch &p, cudaStream_t s) {
   if (p.ncells == 0) return cudaSuccess;
   return p.cell_layers ? launch_dgp_kind<true>(p, s) : launch_dgp_kind<false>(p, s);
 }
+
+cudaError_t launch_cgdg_general(const MassTPLaunch &p, const int2 *list, const unsigned int *count, unsigned int cap,
+                                cudaStream_t s) {
+  static int sms = 0, res[2] = {0, 0};
+  const int w = p.nv == 2 ? 1 : 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (res[w] == 0) {
+    if (p.nv == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res[w], k_cgdg_general<2>, kWarps * 32, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res[w], k_cgdg_general<1>, kWarps * 32, 0);
+    if (res[w] < 1) res[w] = 1;
+  }
+  const dim3 grid((unsigned)(sms * res[w])), block(kWarps * 32);
+  const FastDiv dcol = make_fastdiv((uint32_t)(p.nv * p.layers)), col = make_fastdiv((uint32_t)(p.layers + 1));
+  if (p.nv == 2) return launch_dependent(k_cgdg_general<2>, grid, block, 0, s, p, list, count, cap, dcol, col);
+  return launch_dependent(k_cgdg_general<1>, grid, block, 0, s, p, list, count, cap, dcol, col);
+}
+
+cudaError_t launch_tp_cells_gated(const MassTPLaunch &p, const unsigned int *mode, cudaStream_t s) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int64_t gb = (p.nf + 255) / 256;
+  if (gb > (int64_t)sms * 8) gb = (int64_t)sms * 8;
+  k_tp_clear_cells<<<(unsigned)(gb > 0 ? gb : 1), 256, 0, s>>>(p.b, p.nf, mode);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  MassTPLaunch q = p;
+  q.mode = mode;
+  q.vflags = nullptr;
+  return launch_tp_pair<false, false>(q, s);
+}
+

@@ -588,7 +588,35 @@ def check_tp_access(gm, cs, sp, X, f, ref, absr):
     close(host(b), ref, absr)
 
 
-@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1", "DG0xCG1", "DG1xDG1", "DG1xDG0"])
+@pytest.mark.parametrize("name", ["CG1xDG0", "CG1xDG1"])
+@pytest.mark.parametrize("kind", ["flat", "terrain", "wavy", "tilted"])
+def test_mass_tp_cgdg_geometry(name, kind):
+    """CG1 x DG0 and CG1 x DG1 with WRITE from 32 layers take the gather path
+    of the P1xP1 launch (row weights from this launch's coordinates, the
+    gather beside the straightness flags): on a flat extrusion the flat
+    gather, on terrain-following levels the depth-weighted gather with the
+    model check, on bent levels and leaning columns the probe's cell-loop
+    mode, where the nine-space cell kernel runs (b cleared first).  INC keeps
+    the cell kernel on every geometry.  All match the oracle."""
+    n, layers = 24, 40
+    m = meshgen.tri_mesh(n, seed=660, order="rcm")
+    gm = E.Mesh(m.cells, m.xy, layers)
+    csp, X = O.coords(m.cells, m.xy, layers)
+    if kind != "flat":
+        X = meshgen.level_coords(m, layers, seed=661, kind=kind).reshape(-1)
+    h = {"CG1": O.CG1, "DG0": O.DG0, "DG1": O.DG1}
+    osp = O.number(m.cells, m.nverts, layers, O.DELTA[name])
+    f = meshgen.uniform_field(osp.ndofs, 662)
+    ref, absr = np.zeros(osp.ndofs), np.zeros(osp.ndofs)
+    O.set_tp_element(h[name[:3]], h[name[4:]])
+    O.par_loop(O.K_MASS_TP, m.cells, layers, [(csp, X, 3, O.READ), (osp, f, 1, O.READ), (osp, ref, 1, O.INC, absr)])
+    cs = E.Space(gm, "CG1xCG1", ncomp=3)
+    sp = E.Space(gm, O.DELTA[name])
+    check_tp_access(gm, cs, sp, X, f, ref, absr)
+
+
+@pytest.mark.parametrize("name", ["DG0xDG0", "CG1xDG1", "DG1xCG1", "DG0xDG1", "DG0xCG1", "DG1xDG1", "DG1xDG0",
+                                  "CG1xDG0"])
 def test_mass_tp_flags_partial(name):
     """Over a million (column, layer) items the nine-space kernels take their
     flagged form (one straightness bit per coordinate DoF against the base
@@ -597,8 +625,10 @@ def test_mass_tp_flags_partial(name):
     must send exactly the prisms that touch them to the general 6-point rule.
     With WRITE the DG x DG spaces take the optimistic form (closed form for
     every prism beside the flag pass, then a fix-up launch over the prisms
-    whose flags are not all set), so the NaN that WRITE starts from must be
-    overwritten everywhere and the moved prisms must come out of the fix-up."""
+    whose flags are not all set) and CG1 x DG the gather path (its fix-up
+    recomputes the DoFs next to a moved DoF with the general rule), so the
+    NaN that WRITE starts from must be overwritten everywhere and the moved
+    prisms must come out of the fix-ups."""
     n, layers = 72, 100
     m = meshgen.tri_mesh(n, seed=650, order="rcm")
     gm = E.Mesh(m.cells, m.xy, layers)
