@@ -152,6 +152,22 @@ def cgdg_gather(name: str, layers: int, write: bool = True) -> bool:
             and os.environ.get("EXTMESH_TP_CGDG", "") != "0")
 
 
+# FP64 operations per (column, level) item of the optimistic DG x CG1 form
+# (the DoFs of a level formed once from three levels of f: 3 per node for the
+# column matrix, 1 product (DG0) or the node sum and its product, 6 (DG1))
+DGCG_ITEM_OPS = {"DG0xCG1": 4, "DG1xCG1": 15}
+
+
+def dgcg_optimistic(name: str, layers: int, items: int, write: bool = True) -> bool:
+    """DG0 x CG1 / DG1 x CG1 with WRITE from 8 to 1,024 layers run the
+    optimistic level form when the flags run (a million cell-layers or more,
+    EXTMESH_TP_FLAGS and EXTMESH_TP_OPTIMISTIC not 0)."""
+    env = os.environ.get("EXTMESH_TP_FLAGS", "")
+    flagged = env == "1" or (env != "0" and items >= 1_000_000)
+    return (write and flagged and name in DGCG_ITEM_OPS and 8 <= layers <= 1024
+            and os.environ.get("EXTMESH_TP_OPTIMISTIC", "") != "0")
+
+
 def cgdg_ops(nverts: int, nedges: int, ncells: int, layers: int, nv: int) -> int:
     """FP64 operations of the CG1 x DG gather path: one per vertex-row entry
     and DoF layer (V + 2E entries, nv DoFs per layer), two per DoF for the
@@ -168,6 +184,8 @@ def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False)
     in one launch, then the fix-up launch)."""
     if cgdg_gather(name, layers, write):
         return 9  # the gather path: levels, probe, sigma, rows, gather, fix-up, general, clear, cell kernel
+    if dgcg_optimistic(name, layers, items, write):
+        return 3  # areas and level tables, the optimistic pass, the fix-up
     env = os.environ.get("EXTMESH_TP_FLAGS", "")
     flagged = env == "1" or (env != "0" and items >= 1_000_000)
     dgdg = name[:2] == "DG" and name[4:6] == "DG"
@@ -1103,6 +1121,8 @@ def run_cfg6(args, rank, world, local):
                     work = p1_ops(V * (L + 1), C * (L + 1), C, L)
                 elif cgdg_gather(name, L):
                     work = cgdg_ops(V, euler_edges(V, C), C, L, 2 if name == "CG1xDG1" else 1)
+                elif dgcg_optimistic(name, L, C * L):
+                    work = DGCG_ITEM_OPS[name] * C * (L + 1) + 5 * C
                 else:
                     work = ops * C * L
                 vb_paper = 24 * V * (L + 1) + 16 * sp.ndofs

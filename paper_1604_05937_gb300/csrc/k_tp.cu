@@ -369,6 +369,9 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
 #ifndef EXT_TP_DGDG_MAX_LAYERS
 #define EXT_TP_DGDG_MAX_LAYERS 2048  // the level tables of the optimistic form live in shared memory
 #endif
+#ifndef EXT_TP_DGCG_MAX_LAYERS
+#define EXT_TP_DGCG_MAX_LAYERS 1024  // DG x CG1: four tables per level in shared memory
+#endif
 // Optimistic WRITE form for DG x DG on constant layers (every DoF of b
 // belongs to one cell-layer).  The flagged form's two passes (straightness
 // flags over the coordinate field, then the element vectors) have no data
@@ -389,8 +392,21 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_SMALL_MINB 
 // the straightness flags are checked against (the vertex of a level-0
 // coordinate DoF d is d / (layers + 1)): a prism whose six flags are set has
 // exactly these x, y at both of its levels.
+// With ztab (the DG x CG1 fix-up's tables): also z of the reference column
+// at every level and hlay[l] = |z_{l+1} - z_l| (as k_tp_levels).
 __global__ void __launch_bounds__(256) k_tp_area2(const int32_t *__restrict__ cmap, const double *__restrict__ xy,
-                                                  FastDiv colv, int64_t ncells, double *__restrict__ area2) {
+                                                  FastDiv colv, int64_t ncells, double *__restrict__ area2,
+                                                  const double *__restrict__ X = nullptr, int layers = 0,
+                                                  double *__restrict__ ztab = nullptr,
+                                                  double *__restrict__ hlay = nullptr) {
+  if (ztab) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m <= layers) {
+      const double z = X[3 * m + 2];
+      ztab[m] = z;
+      if (m < layers) hlay[m] = fabs(X[3 * (m + 1) + 2] - z);
+    }
+  }
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
     double x[3], y[3];
 #pragma unroll
@@ -519,6 +535,9 @@ __global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB :
       }
     }
   }
+  // a thread that took only flag chunks still waits for k_tp_area2 before it
+  // ends, so that the launches after this one find it complete as well
+  if (!waited) grid_dep_wait();
   // one word per CTA (every CTA writes its own, so nothing needs clearing first)
   if (bad && lane == 0) cta_bad = 1;
   __syncthreads();
@@ -552,6 +571,168 @@ cudaError_t launch_tp_dgdg(const MassTPLaunch &p, const double *area2, uint32_t 
   const int64_t nic = (p.ncells * (int64_t)p.layers + 32 * dgdg_ui(NH * NV) - 1) / (32 * dgdg_ui(NH * NV));
   return launch_dependent(k_tp_dgdg<NH, NV>, dim3((unsigned)blocks), dim3(kWarps * 32), smem, s, p, area2, flags,
                           badv, make_fastdiv((uint32_t)(p.layers + 1)), make_fastdiv((uint32_t)p.layers), nfc, nic);
+}
+
+// Optimistic WRITE form for DG x CG1 on constant layers (horizontal DG0 or
+// DG1, vertical CG1: the DoFs of a cell column are its own, consecutive
+// layers share their facet DoFs).  Summed over the two prisms at level m of a
+// straight column, the element vectors give
+//   b_{m,a} = coef (g_a + [NH = 3] sum_a' g_a'),
+//   g_a = lo_m f_{m-1,a} + mid_m f_{m,a} + hi_m f_{m+1,a}
+// with (lo, mid, hi) = (|h_{m-1}|, 2 (|h_{m-1}| + |h_m|), |h_m|) (zero beyond
+// the column's ends) and coef = |2A| x the element's constant (1/12 for DG0,
+// 1/144 for DG1), so one lane per (column, level) item writes the NH DoFs of
+// its level once: no atomics and no clearing of b, 4 (DG0) or 15 (DG1) FP64
+// operations per item.  The DoF of node a at level m is the column's first
+// DoF + NH m + a (Algorithm 1: the NH facet DoFs of a level together).  As in
+// k_tp_dgdg the straightness flags are set in the same launch (flag chunks
+// interleaved with item chunks), |2A| comes from k_tp_area2 and the level
+// table from the reference column; the fix-up (k_mass_tp_levels with FIX)
+// rewrites every column not straight at every level.
+template <int NH>
+__global__ void __launch_bounds__(kWarps * 32, NH == 1 ? 4 : 3)
+    k_dgcg_opt(const MassTPLaunch p, const double *__restrict__ area2, uint32_t *__restrict__ flags,
+               int32_t *__restrict__ badv, FastDiv colv, int64_t nfc, int64_t nic) {
+  constexpr int UF = 2, UI = 2;  // flag words, items per lane per chunk
+  // level table of the reference column: z, lo, mid, hi per level
+  extern __shared__ double lvl[];
+  const int L1 = p.layers + 1;
+  double *ztab = lvl, *tlo = lvl + L1, *tmid = lvl + 2 * L1, *thi = lvl + 3 * L1;
+  __shared__ int cta_bad;
+  for (int m = threadIdx.x; m < L1; m += blockDim.x) ztab[m] = __ldg(p.X + 3 * (int64_t)m + 2);
+  if (threadIdx.x == 0) cta_bad = 0;
+  __syncthreads();
+  for (int m = threadIdx.x; m < L1; m += blockDim.x) {
+    const double lo = m > 0 ? fabs(ztab[m] - ztab[m - 1]) : 0.0;
+    const double hi = m < p.layers ? fabs(ztab[m + 1] - ztab[m]) : 0.0;
+    tlo[m] = lo;
+    thi[m] = hi;
+    tmid[m] = 2.0 * (lo + hi);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t ncoord = (uint32_t)p.ncoord, nwords = (uint32_t)((p.ncoord + 31) / 32);
+  const uint32_t nitems = (uint32_t)(p.ncells * (int64_t)L1);
+  const int64_t nch = nfc + nic;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  bool bad = false, waited = false;
+  const int64_t j0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  int64_t fb = j0 * nfc / nch, r = j0 * nfc - fb * nch;
+  const int64_t qw = wstride * nfc / nch, rw = wstride * nfc - qw * nch;
+  for (int64_t j = j0; j < nch; j += wstride) {
+    const bool flag_chunk = r + nfc >= nch;
+    const int64_t fcur = fb;
+    fb += qw;
+    r += rw;
+    if (r >= nch) {
+      r -= nch;
+      ++fb;
+    }
+    if (flag_chunk) {
+      const uint32_t d0 = (uint32_t)fcur * (uint32_t)(UF * 32) + (uint32_t)lane;
+      long long x[UF], y[UF], z[UF], rx[UF], ry[UF], rz[UF];
+      bool v[UF];
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t d = d0 + (uint32_t)(u * 32);
+        v[u] = d < ncoord;
+        x[u] = y[u] = z[u] = rx[u] = ry[u] = rz[u] = 0;
+        if (v[u]) {
+          const uint32_t q = fdiv(d, colv);
+          const uint32_t m = d - q * colv.d;
+          const double *xp = p.X + 3 * (size_t)d;
+          const double *bp = p.base_xy + 2 * (size_t)q;
+          x[u] = __double_as_longlong(__ldg(xp + 0));
+          y[u] = __double_as_longlong(__ldg(xp + 1));
+          z[u] = __double_as_longlong(__ldg(xp + 2));
+          rx[u] = __double_as_longlong(__ldg(bp + 0));
+          ry[u] = __double_as_longlong(__ldg(bp + 1));
+          rz[u] = __double_as_longlong(ztab[m]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UF; ++u) {
+        const uint32_t w = (uint32_t)fcur * (uint32_t)UF + (uint32_t)u;
+        const unsigned int word = __ballot_sync(0xffffffffu, v[u] && x[u] == rx[u] && y[u] == ry[u] && z[u] == rz[u]);
+        const unsigned int want = __ballot_sync(0xffffffffu, v[u]);
+        if (w < nwords) {
+          if (lane == 0) flags[w] = word;
+          bad |= word != want;
+        }
+      }
+    } else {
+      if (!waited) {  // launched as a dependent of k_tp_area2: its |2A| must be complete
+        grid_dep_wait();
+        waited = true;
+      }
+      const uint32_t i0 = (uint32_t)(j - fcur) * (uint32_t)(32 * UI) + (uint32_t)lane;
+      int64_t dof[UI];
+      double fc[UI][NH], fp[UI][NH], fn[UI][NH], co[UI];
+      int ms[UI];
+      bool v[UI];
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+        const uint32_t it = i0 + (uint32_t)(u * 32);
+        v[u] = it < nitems;
+        co[u] = 0.0;
+        ms[u] = 0;
+        dof[u] = 0;
+        if (v[u]) {
+          const uint32_t c = fdiv(it, colv);
+          ms[u] = (int)(it - c * colv.d);
+          co[u] = fmul(__ldg(area2 + c), p.scale, p.k1);
+          dof[u] = (int64_t)__ldg(p.fmap + (int64_t)c * p.k + p.slot[0]) + (int64_t)NH * ms[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+#pragma unroll
+        for (int a = 0; a < NH; ++a) {
+          fc[u][a] = v[u] ? __ldg(p.f + dof[u] + a) : 0.0;
+          fp[u][a] = v[u] && ms[u] > 0 ? __ldg(p.f + dof[u] - NH + a) : 0.0;
+          fn[u][a] = v[u] && ms[u] < p.layers ? __ldg(p.f + dof[u] + NH + a) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UI; ++u) {
+        if (!v[u]) continue;
+        const int m = ms[u];
+        double g[NH];
+#pragma unroll
+        for (int a = 0; a < NH; ++a) g[a] = fma(tlo[m], fp[u][a], fma(tmid[m], fc[u][a], fmul(thi[m], fn[u][a], p.k1)));
+        if (NH == 1) {
+          p.b[dof[u]] = fmul(co[u], g[0], p.k1);
+        } else {
+          const double cS = fmul(co[u], fadd(fadd(g[0], g[1 % NH], p.k1), g[2 % NH], p.k1), p.k1);
+#pragma unroll
+          for (int a = 0; a < NH; ++a) p.b[dof[u] + a] = fma(co[u], g[a], cS);
+        }
+      }
+    }
+  }
+  if (!waited) grid_dep_wait();  // as in k_tp_dgdg: the later launches rely on k_tp_area2 being complete
+  if (bad && lane == 0) cta_bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) badv[blockIdx.x] = cta_bad;
+}
+
+template <int NH>
+int64_t dgcg_grid(const MassTPLaunch &p, size_t smem) {
+  static int resident = 0, sms = 0;
+  static size_t at = 0;
+  if (resident == 0 || at != smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_dgcg_opt<NH>, kWarps * 32, smem);
+    if (resident < 1) resident = 1;
+    at = smem;
+  }
+  const int64_t nfc = ((p.ncoord + 31) / 32 + 1) / 2;
+  const int64_t nic = (p.ncells * ((int64_t)p.layers + 1) + 63) / 64;
+  int64_t blocks = (nfc + nic + kWarps - 1) / kWarps;
+  if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
+  return blocks < 1 ? 1 : blocks;
 }
 
 template <int NH, int NV, bool VAR, bool FLAGS, bool MULTI, bool WR = false, bool FIX = false>
@@ -608,9 +789,18 @@ cudaError_t launch_tp_pair(const MassTPLaunch &p, cudaStream_t s) {
 // shuffle (the step's last lane to the next step).  Every DoF is then formed
 // in registers by one lane and written once: stored (WR) or added with one
 // fire-and-forget reduction.
-template <int NH, bool FLAGS, bool WR>
+// FIX (with FLAGS and WR): the fix-up of the optimistic DG x CG1 form, which
+// rewrites only the columns not straight at every level (and returns at once
+// when no CTA of that launch saw a coordinate DoF that is not straight).
+template <int NH, bool FLAGS, bool WR, bool FIX = false>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPLaunch p, int cpw) {
   __shared__ TPCol cols[kWarps][kMaxCols];
+  if (FIX) {
+    grid_dep_wait();  // launched as a dependent of the optimistic launch
+    int any = 0;
+    for (int i = threadIdx.x; i < p.nbadv; i += blockDim.x) any |= __ldg(p.badv + i);
+    if (!__syncthreads_or(any)) return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int layers = p.layers, L1 = layers + 1;
   const int64_t ngroups = (p.ncells + cpw - 1) / cpw;
@@ -733,7 +923,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPL
           carry[a] = last;
           bot[a] += up;
         }
-        if (base + u * 32 + lane < nitems) {
+        if (base + u * 32 + lane < nitems && !(FIX && ci.allok)) {  // FIX: straight columns keep their values
 #pragma unroll
           for (int a = 0; a < NH; ++a) {
             const int64_t d = m < layers ? (int64_t)ci.fm[2 * a] + (int64_t)m * p.off[2 * a]
@@ -748,7 +938,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_mass_tp_levels(const MassTPL
   }
 }
 
-template <int NH, bool FLAGS, bool WR>
+template <int NH, bool FLAGS, bool WR, bool FIX = false>
 cudaError_t launch_tp_levels(const MassTPLaunch &p, cudaStream_t s) {
   const double L1 = (double)p.layers + 1.0;
   int cpw = (int)((EXT_TP_ITEMS + L1 - 1.0) / L1);
@@ -761,11 +951,14 @@ cudaError_t launch_tp_levels(const MassTPLaunch &p, cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_tp_levels<NH, FLAGS, WR>, kWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_mass_tp_levels<NH, FLAGS, WR, FIX>, kWarps * 32, 0);
     if (resident < 1) resident = 1;
   }
   if (blocks > (int64_t)resident * sms) blocks = (int64_t)resident * sms;
-  k_mass_tp_levels<NH, FLAGS, WR><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
+  if (FIX)
+    return launch_dependent(k_mass_tp_levels<NH, FLAGS, WR, FIX>, dim3((unsigned)blocks), dim3(kWarps * 32), 0, s, p,
+                            cpw);
+  k_mass_tp_levels<NH, FLAGS, WR, FIX><<<(unsigned)blocks, kWarps * 32, 0, s>>>(p, cpw);
   return cudaGetLastError();
 }
 
@@ -1021,48 +1214,96 @@ cudaError_t launch_mass_tp(const MassTPLaunch &p, cudaStream_t s) {
   // the forms that add into shared DoFs with atomics (horizontal CG1, variable
   // layers) clear b first for WRITE
   const bool owned = p.hown && !p.cell_layers && (!p.vcont || levels_env == 1);
-  if (p.overwrite && !owned) {
-    const cudaError_t ez = cudaMemsetAsync(p.b, 0, sizeof(double) * (size_t)p.nf, s);
-    if (ez != cudaSuccess) return ez;
-  }
-  if (p.cell_layers) return launch_tp_pair<true, false>(p, s);
   static int flags_env = -1;
   if (flags_env < 0) {
     const char *ev = getenv("EXTMESH_TP_FLAGS");
     flags_env = (ev && ev[0] == '1') ? 1 : ((ev && ev[0] == '0') ? 0 : 2);
   }
   const double items = (double)p.ncells * (double)p.layers;
-  const bool want = p.base_xy && p.ncoord > 0 && flags_env != 0 && (flags_env == 1 || items >= 1.0e6);
-  // the optimistic form (WRITE, DG x DG, constant layers from
-  // EXT_TP_MULTI_LAYERS to EXT_TP_DGDG_MAX_LAYERS, a mesh with |2A| per base
-  // cell; EXTMESH_TP_OPTIMISTIC=0, read once per process, turns it off):
-  // 32-bit item and DoF indices
+  const bool want = !p.cell_layers && p.base_xy && p.ncoord > 0 && flags_env != 0 && (flags_env == 1 || items >= 1.0e6);
+  // the optimistic forms (WRITE, constant layers from EXT_TP_MULTI_LAYERS,
+  // 32-bit item and DoF indices; EXTMESH_TP_OPTIMISTIC=0, read once per
+  // process, turns them off): DG x DG (every DoF in one cell-layer) up to
+  // EXT_TP_DGDG_MAX_LAYERS layers, DG x CG1 (the level-merged form, no
+  // clearing of b) up to EXT_TP_DGCG_MAX_LAYERS
   static int opt_env = -1;
   if (opt_env < 0) {
     const char *ev = getenv("EXTMESH_TP_OPTIMISTIC");
     opt_env = (ev && ev[0] == '0') ? 0 : 1;
   }
-  const bool optimistic = want && opt_env == 1 && owned && !p.vcont && p.overwrite &&
-                          p.layers >= EXT_TP_MULTI_LAYERS && p.layers <= EXT_TP_DGDG_MAX_LAYERS &&
-                          items < 2147483647.0 && (double)p.ncoord < 2147483647.0;
+  const bool opt_common = want && opt_env == 1 && p.overwrite && p.hown && p.layers >= EXT_TP_MULTI_LAYERS &&
+                          (double)p.ncells * (double)(p.layers + 1) < 2147483647.0 &&
+                          (double)p.ncoord < 2147483647.0 && (double)p.nf < 2147483647.0;
+  const bool optimistic = opt_common && !p.vcont && p.layers <= EXT_TP_DGDG_MAX_LAYERS;
+  const bool opt_dgcg = opt_common && p.vcont && p.layers <= EXT_TP_DGCG_MAX_LAYERS;
   char *scr = nullptr;
   const size_t fbytes = (sizeof(uint32_t) * (size_t)((p.ncoord + 31) / 32) + 255) & ~(size_t)255;
   const size_t zbytes = (sizeof(double) * (size_t)(p.layers + 1) + 255) & ~(size_t)255;
-  const size_t smem = sizeof(double) * (size_t)(2 * p.layers + 1);
+  const size_t smem = optimistic ? sizeof(double) * (size_t)(2 * p.layers + 1)
+                                 : sizeof(double) * 4 * (size_t)(p.layers + 1);  // DG x CG1: z, lo, mid, hi
   int64_t oblocks = 0;
   if (optimistic) {
     if (p.nh == 1 && p.nv == 1) oblocks = dgdg_grid<1, 1>(p, smem);
     else if (p.nh == 1) oblocks = dgdg_grid<1, 2>(p, smem);
     else if (p.nv == 1) oblocks = dgdg_grid<3, 1>(p, smem);
     else oblocks = dgdg_grid<3, 2>(p, smem);
+  } else if (opt_dgcg) {
+    oblocks = p.nh == 1 ? dgcg_grid<1>(p, smem) : dgcg_grid<3>(p, smem);
   }
   const size_t abytes = (sizeof(double) * (size_t)p.ncells + 255) & ~(size_t)255;
-  const size_t sbytes = optimistic ? ((sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255) + abytes : 2 * zbytes;
+  const size_t sbytes = (optimistic || opt_dgcg)
+                            ? ((sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255) + abytes + (opt_dgcg ? 2 * zbytes : 0)
+                            : 2 * zbytes;
   if (want && cudaMallocAsync(reinterpret_cast<void **>(&scr), fbytes + sbytes, s) != cudaSuccess) {
     (void)cudaGetLastError();  // not sticky: the plain form needs no scratch
     scr = nullptr;
   }
+  if (p.overwrite && !owned && !(scr && opt_dgcg)) {
+    const cudaError_t ez = cudaMemsetAsync(p.b, 0, sizeof(double) * (size_t)p.nf, s);
+    if (ez != cudaSuccess) {
+      if (scr) (void)cudaFreeAsync(scr, s);
+      return ez;
+    }
+  }
+  if (p.cell_layers) return launch_tp_pair<true, false>(p, s);
   if (!scr) return owned ? launch_tp_owned<false>(p, s) : launch_tp_pair<false, false>(p, s);
+  if (opt_dgcg) {
+    MassTPLaunch q = p;
+    uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
+    double *area2 = reinterpret_cast<double *>(scr + fbytes);
+    int32_t *badv = reinterpret_cast<int32_t *>(scr + fbytes + abytes);
+    static int sms_c = 0;
+    if (sms_c == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms_c, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int64_t ga = (p.ncells + 255) / 256;
+    if (ga > (int64_t)sms_c * 8) ga = (int64_t)sms_c * 8;
+    if (ga * 256 < (int64_t)p.layers + 1) ga = ((int64_t)p.layers + 1 + 255) / 256;
+    const FastDiv colv = make_fastdiv((uint32_t)(p.layers + 1));
+    // |2A| per cell, and the fix-up's level tables in the same launch
+    double *ztab = reinterpret_cast<double *>(scr + fbytes + abytes + ((sizeof(int32_t) * (size_t)oblocks + 255) & ~(size_t)255));
+    double *hlay = ztab + zbytes / sizeof(double);
+    k_tp_area2<<<(unsigned)ga, 256, 0, s>>>(p.cmap, p.base_xy, colv, p.ncells, area2, p.X, p.layers, ztab, hlay);
+    cudaError_t e = cudaGetLastError();
+    const int64_t nfc = ((p.ncoord + 31) / 32 + 1) / 2;
+    const int64_t nic = (p.ncells * ((int64_t)p.layers + 1) + 63) / 64;
+    if (e == cudaSuccess)
+      e = p.nh == 1 ? launch_dependent(k_dgcg_opt<1>, dim3((unsigned)oblocks), dim3(kWarps * 32), smem, s, q, area2,
+                                       flags, badv, colv, nfc, nic)
+                    : launch_dependent(k_dgcg_opt<3>, dim3((unsigned)oblocks), dim3(kWarps * 32), smem, s, q, area2,
+                                       flags, badv, colv, nfc, nic);
+    // the fix-up: the level kernel over the columns not straight at every level
+    q.vflags = flags;
+    q.hlay = hlay;
+    q.badv = badv;
+    q.nbadv = (int32_t)oblocks;
+    if (e == cudaSuccess)
+      e = p.nh == 1 ? launch_tp_levels<1, true, true, true>(q, s) : launch_tp_levels<3, true, true, true>(q, s);
+    const cudaError_t ef = cudaFreeAsync(scr, s);
+    return e != cudaSuccess ? e : ef;
+  }
   MassTPLaunch q = p;
   uint32_t *flags = reinterpret_cast<uint32_t *>(scr);
   q.vflags = flags;
