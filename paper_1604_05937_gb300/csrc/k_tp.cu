@@ -420,13 +420,19 @@ __global__ void __launch_bounds__(256) k_tp_area2(const int32_t *__restrict__ cm
 }
 
 // flag words per lane per flag chunk, items per lane per element chunk (for
-// DG0 x DG0 sized so that 4 CTAs of 256 threads stay resident per SM; 2 CTAs
+// DG0 x DG0 sized so that 4 CTAs of 256 threads stay resident per SM; 3 CTAs
 // for the element vectors of 2, 3 and 6 DoFs)
+#ifndef EXT_TP_DGDG_UIK
+#define EXT_TP_DGDG_UIK 2  // element vectors of 2, 3 and 6 DoFs: items per lane per element chunk
+#endif
+#ifndef EXT_TP_DGDG_MINBK
+#define EXT_TP_DGDG_MINBK 3  // and their resident CTAs per SM (4 items and 2 CTAs: 13-16 % slower at 100 layers)
+#endif
 __host__ __device__ constexpr int dgdg_uf(int k) { return k == 1 ? EXT_TP_DGDG_UF1 : 4; }
-__host__ __device__ constexpr int dgdg_ui(int k) { return k == 1 ? EXT_TP_DGDG_UI1 : 4; }
+__host__ __device__ constexpr int dgdg_ui(int k) { return k == 1 ? EXT_TP_DGDG_UI1 : EXT_TP_DGDG_UIK; }
 
 template <int NH, int NV>
-__global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB : 2)
+__global__ void __launch_bounds__(kWarps * 32, NH * NV == 1 ? EXT_TP_DGDG_MINB : EXT_TP_DGDG_MINBK)
     k_tp_dgdg(const MassTPLaunch p, const double *__restrict__ area2, uint32_t *__restrict__ flags,
               int32_t *__restrict__ badv, FastDiv colv, FastDiv lay, int64_t nfc, int64_t nic) {
   constexpr int UF = dgdg_uf(NH * NV), UI = dgdg_ui(NH * NV), K = NH * NV;
