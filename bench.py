@@ -180,8 +180,8 @@ def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False)
     base coordinates: the level table, the straightness flags and the cell
     kernel from a million (column, layer) items (EXTMESH_TP_FLAGS=1 / 0: at any
     size / never), the cell kernel alone otherwise; with WRITE on a DG x DG
-    space from 8 to 2048 layers the optimistic form (flags and element vectors
-    in one launch, then the fix-up launch)."""
+    space from 8 to 2048 layers the optimistic form (the area pass, flags and
+    element vectors in one launch, then the fix-up launch)."""
     if cgdg_gather(name, layers, write):
         return 9  # the gather path: levels, probe, sigma, rows, gather, fix-up, general, clear, cell kernel
     if dgcg_optimistic(name, layers, items, write):
@@ -190,7 +190,7 @@ def tp_kernels(items: int, layers: int = 1, name: str = "", write: bool = False)
     flagged = env == "1" or (env != "0" and items >= 1_000_000)
     dgdg = name[:2] == "DG" and name[4:6] == "DG"
     if flagged and write and dgdg and 8 <= layers <= 2048 and os.environ.get("EXTMESH_TP_OPTIMISTIC", "") != "0":
-        return 2
+        return 3  # areas, the optimistic pass, the fix-up
     return 3 if flagged else 1
 
 
