@@ -1002,11 +1002,9 @@ def run_cfg5(args, rank, world, local):
         ops += PRISM_U2V_OPS[3] * m.ncells * L
         cells_total += m.ncells * L
     # the first plan times the candidates (EXTMESH_TUNE=force, its result
-    # stored in the tuning cache); the second plan of the same workload reads
-    # its parameters from the cache
-    cache_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
-    if cache_dir and "EXTMESH_TUNE_CACHE" not in os.environ:
-        os.environ["EXTMESH_TUNE_CACHE"] = os.path.join(cache_dir, "batch_tune.jsonl")
+    # stored in the tuning cache: EXTMESH_TUNE_CACHE, else the user's cache
+    # folder); the second plan of the same workload reads its parameters from
+    # the cache
     os.environ["EXTMESH_TUNE"] = "force"
     t0 = time.time()
     tuned = E.Batch(meshes, E.EXT_K_U2V_FWDADJ, per, params=None)
